@@ -1,0 +1,210 @@
+"""CPU oracle for the checkerboard Metropolis sweep (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline and
+reference legs may import this package.  The product path (the CUDA library in
+``paper_1006_3865_gb300``) never does, and the two share no code: the oracle is
+plain C (``spn_oracle.c``) written from the paper's Eq. 1-2 and the sub-lattice
+procedure of Sec. 3, loaded here through ctypes.
+
+Every wrapper takes and returns numpy arrays; see ``spn_oracle.c`` for the exact
+definitions (site order, colours, Philox counters, thresholds, exchange rule).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spn_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``spn_oracle.c`` with gcc (OpenMP if available) and return the path."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    try:
+        subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + ["-o", tmp, _SRC, "-lm"], check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            u32, u64, i64, dbl, cint, vp = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p)
+            L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+            L.orc_philox4x32_10.restype = None
+            L.orc_site_word.argtypes = [u64, u32, u32, cint, cint, cint, u64]
+            L.orc_site_word.restype = u32
+            L.orc_metropolis_u.argtypes = [u64, u32, u32, cint, u64]
+            L.orc_metropolis_u.restype = u32
+            L.orc_hot_word.argtypes = [u64, u32, cint, u64]
+            L.orc_hot_word.restype = u32
+            L.orc_threshold.argtypes = [dbl, cint]
+            L.orc_threshold.restype = u64
+            L.orc_accept.argtypes = [dbl, cint, u32]
+            L.orc_accept.restype = cint
+            L.orc_delta_e.argtypes = [cint, vp, vp, vp, i64]
+            L.orc_delta_e.restype = cint
+            L.orc_observables.argtypes = [cint, vp, vp, vp, vp, vp]
+            L.orc_observables.restype = cint
+            L.orc_init_hot.argtypes = [cint, vp, u64, u32, vp]
+            L.orc_init_hot.restype = cint
+            L.orc_sweeps.argtypes = [cint, vp, vp, vp, dbl, u64, u32, u32, i64, vp, vp, vp, vp]
+            L.orc_sweeps.restype = cint
+            L.orc_ea_init_hot.argtypes = [vp, cint, u64, u32, vp]
+            L.orc_ea_init_hot.restype = cint
+            L.orc_ea_observables.argtypes = [vp, cint, vp, vp, vp, vp]
+            L.orc_ea_observables.restype = cint
+            L.orc_ea_sweeps.argtypes = [vp, cint, vp, vp, vp, vp, vp, u64, u32, u32, i64, cint, vp]
+            L.orc_ea_sweeps.restype = cint
+            L.orc_num_threads.argtypes = []
+            L.orc_num_threads.restype = cint
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dims(dims) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+
+
+def _bonds(bonds):
+    return None if bonds is None else np.ascontiguousarray(bonds, dtype=np.uint64)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle: {what} rejected its arguments (rc={rc})")
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def site_word(seed: int, stream: int, t: int, colour: int, p_hi: int, p_lo: int, m: int) -> int:
+    return int(lib().orc_site_word(seed, stream, t, colour, p_hi, p_lo, m))
+
+
+def metropolis_u(seed: int, stream: int, sweep: int, colour: int, m: int) -> int:
+    return int(lib().orc_metropolis_u(seed, stream, sweep, colour, m))
+
+
+def hot_word(seed: int, stream: int, colour: int, m: int) -> int:
+    return int(lib().orc_hot_word(seed, stream, colour, m))
+
+
+def threshold(beta: float, dE: int) -> int:
+    return int(lib().orc_threshold(float(beta), int(dE)))
+
+
+def accept(beta: float, dE: int, u: int) -> bool:
+    return bool(lib().orc_accept(float(beta), int(dE), int(u)))
+
+
+def delta_e(dims, spins: np.ndarray, n: int, bonds=None) -> int:
+    d = _dims(dims)
+    s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+    return int(lib().orc_delta_e(len(d), _p(d), _p(s), _p(_bonds(bonds)), int(n)))
+
+
+def observables(dims, spins: np.ndarray, bonds=None) -> tuple[int, int]:
+    d = _dims(dims)
+    s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+    E = np.zeros(1, np.int64)
+    M = np.zeros(1, np.int64)
+    _check(lib().orc_observables(len(d), _p(d), _p(s), _p(_bonds(bonds)), _p(E), _p(M)), "observables")
+    return int(E[0]), int(M[0])
+
+
+def init_hot(dims, seed: int, stream: int = 0) -> np.ndarray:
+    d = _dims(dims)
+    s = np.zeros(int(np.prod(d)), dtype=np.int8)
+    _check(lib().orc_init_hot(len(d), _p(d), seed, stream, _p(s)), "init_hot")
+    return s
+
+
+def sweeps(dims, spins: np.ndarray, beta: float, nsweeps: int, seed: int, stream: int = 0,
+           sweep0: int = 0, bonds=None, E: int | None = None, M: int | None = None):
+    """Run ``nsweeps`` sweeps in place on ``spins`` (flat int8, site order n).
+
+    Returns (E, M, traceE, traceM) with the per-sweep integer trace."""
+    d = _dims(dims)
+    if spins.dtype != np.int8 or not spins.flags.c_contiguous:
+        raise TypeError("spins must be a contiguous int8 array")
+    b = _bonds(bonds)
+    if E is None or M is None:
+        E, M = observables(d, spins, b)
+    Ea = np.array([E], np.int64)
+    Ma = np.array([M], np.int64)
+    tE = np.zeros(max(nsweeps, 1), np.int64)
+    tM = np.zeros(max(nsweeps, 1), np.int64)
+    _check(lib().orc_sweeps(len(d), _p(d), _p(spins), _p(b), float(beta), seed, stream, sweep0, int(nsweeps),
+                            _p(Ea), _p(Ma), _p(tE), _p(tM)), "sweeps")
+    return int(Ea[0]), int(Ma[0]), tE[:nsweeps], tM[:nsweeps]
+
+
+def ea_init_hot(dims, nsamples: int, seed: int, stream0: int = 0) -> np.ndarray:
+    d = _dims(dims)
+    N = int(np.prod(d))
+    sp = np.zeros((nsamples, N), dtype=np.uint32)
+    _check(lib().orc_ea_init_hot(_p(d), nsamples, seed, stream0, _p(sp)), "ea_init_hot")
+    return sp
+
+
+def ea_observables(dims, words: np.ndarray, bonds: np.ndarray):
+    """Per-replica (E, M), each of shape [nsamples, 32], indexed by slot."""
+    d = _dims(dims)
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    ns = w.shape[0]
+    E = np.zeros((ns, 32), np.int64)
+    M = np.zeros((ns, 32), np.int64)
+    _check(lib().orc_ea_observables(_p(d), ns, _p(w), _p(_bonds(bonds)), _p(E), _p(M)), "ea_observables")
+    return E, M
+
+
+def ea_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, temp_of_slot: np.ndarray,
+              slot_of_temp: np.ndarray, nsweeps: int, seed: int, stream0: int = 0, sweep0: int = 0,
+              exchange_every: int = 0, acc: np.ndarray | None = None):
+    """Multi-spin coded sweeps, in place on ``words`` [nsamples, N] and the slot maps."""
+    d = _dims(dims)
+    for a, dt in ((words, np.uint32), (temp_of_slot, np.uint8), (slot_of_temp, np.uint8)):
+        if a.dtype != dt or not a.flags.c_contiguous:
+            raise TypeError("ea_sweeps: in/out arrays must be contiguous with the documented dtypes")
+    be = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+    if be.shape != (32,):
+        raise ValueError("ea_sweeps: 32 betas required")
+    if acc is not None and (acc.dtype != np.int64 or not acc.flags.c_contiguous):
+        raise TypeError("acc must be contiguous int64")
+    _check(lib().orc_ea_sweeps(_p(d), words.shape[0], _p(words), _p(_bonds(bonds)), _p(be), _p(temp_of_slot),
+                               _p(slot_of_temp), seed, stream0, sweep0, int(nsweeps), int(exchange_every),
+                               _p(acc)), "ea_sweeps")

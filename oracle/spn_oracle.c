@@ -1,0 +1,404 @@
+/*
+ * spn_oracle.c -- CPU oracle for the checkerboard Metropolis sweep of
+ * nearest-neighbour Ising-type lattices (M. Weigel, "Simulating spin models on
+ * GPU", Sec. 3 Eq. 1-2 and the sub-lattice procedure; Sec. 4 for the 3D model and
+ * the +-J Edwards-Anderson spin glass with multi-spin coding).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the tests, the smoke check and
+ * the CPU-baseline / reference legs of the benchmark load this library.  It
+ * shares no code, header, table or helper with the CUDA library: both sides are
+ * written independently from the same definitions.
+ *
+ * Plain, slow, obviously correct: every site is visited by a straight loop, the
+ * local field is summed from its 2*d neighbours, the Metropolis probability is
+ * the integer threshold of Eq. 2, and random numbers come from Philox4x32-10
+ * (Salmon, Moraes, Dror, Shaw, SC'11) written from its published definition.
+ * The only parallelism is an OpenMP loop over the sites of one colour; sites of
+ * one colour are independent (Sec. 3), so the result does not depend on the
+ * thread count.
+ *
+ * Definitions fixed here where the paper is silent (each one is a reading that
+ * the GPU library follows too):
+ *   lattice   extents L[0..d-1], all even; site n = x + Lx*(y + Ly*z);
+ *             colour c(n) = (x+y+z) & 1; within-colour index m = n >> 1.
+ *   energy    E = -sum_n sum_dir J(n,dir) s_n s_{n+e_dir}   (Eq. 1, each bond once)
+ *             M = sum_n s_n.
+ *   bonds     optional; bit (n % 64) of word [dir*nw + n/64] set <=> J(n,dir) = -1,
+ *             nw = ceil(N/64).  Without bonds J = +1 (the ferromagnet of Eq. 1).
+ *   threshold thr(beta, dE) = floor(exp(-beta*dE) * 2^32) for dE > 0 (Eq. 2),
+ *             a value in [0, 2^32]; dE <= 0 is always accepted.
+ *   random    R(c0,c1,c2,c3) = Philox4x32-10 with key (seed lo32, seed hi32).
+ *             For a site with within-colour index m, group g = m >> 3, word
+ *             (m >> 1) & 3, half m & 1 (0 = bits 0..15, 1 = bits 16..31).
+ *             A "site word" is hi16 << 16 | lo16, where hi16 / lo16 are that
+ *             half of R(g, t, c | (p_hi << 1), stream) / R(g, t, c | (p_lo << 1), stream).
+ *               Metropolis u at sweep t, colour c:  p_hi = 0, p_lo = 1
+ *               hot-start word (t = 0):              p_hi = 2, p_lo = 3
+ *             The 32-bit u is therefore uniform; drawing it in two halves lets
+ *             a GPU thread decide from the high half alone unless it ties the
+ *             threshold's high half.
+ *   hot start s_n = -1 if bit 31 of the hot-start word is set, else +1.
+ *   sweep t   colour 0, then colour 1; a site of colour c flips iff dE <= 0 or
+ *             u < thr(beta, dE); E and M are updated by every accepted flip.
+ *
+ * Multi-spin coded EA (Sec. 4, "asynchronous multi-spin coding"):
+ *   one uint32 per (sample, site); bit j is the replica held in temperature slot
+ *   j (1 <=> spin -1).  All 32 replicas of a sample share the site's u.  Slot j
+ *   runs at beta[temp_of_slot[j]]; betas are indexed by ascending temperature
+ *   (non-increasing beta).  Hot start: the replica bits are the hot-start word.
+ *   Replica exchange after every X-th sweep (step e = (t+1)/X - 1): for the
+ *   temperature pairs (k, k+1) with k = e mod 2, 4, ... accept iff
+ *   D = (beta_k - beta_{k+1}) * (E_k - E_{k+1}) >= 0 or
+ *   u < floor(exp(D) * 2^32) with u = word k & 3 of R(k >> 2, e, 4 << 1, stream);
+ *   an accepted pair swaps the slots of the two temperatures.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TWO32 4294967296.0
+
+/* ---------------------------------------------------------------- Philox */
+
+/* Philox4x32 with 10 rounds, Salmon et al. SC'11: each round multiplies words 0
+ * and 2 by two fixed odd constants, swaps the words and mixes the high halves of
+ * the products with the other two words and the round key; the key is bumped by
+ * the two Weyl constants between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)x2;
+    uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+    uint32_t y1 = (uint32_t)p1;
+    uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+    uint32_t y3 = (uint32_t)p0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static uint32_t half_of(uint64_t seed, uint64_t m, uint32_t t, uint32_t c2, uint32_t stream) {
+  uint32_t ctr[4] = {(uint32_t)(m >> 3), t, c2, stream};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  orc_philox4x32_10(ctr, key, w);
+  uint32_t x = w[(m >> 1) & 3];
+  return (m & 1) ? (x >> 16) : (x & 0xffffu);
+}
+
+/* 32-bit site word, see the header: purposes p_hi / p_lo select the counter's
+ * third word c | (p << 1). */
+uint32_t orc_site_word(uint64_t seed, uint32_t stream, uint32_t t, int colour, int p_hi, int p_lo,
+                       uint64_t m) {
+  uint32_t hi = half_of(seed, m, t, (uint32_t)colour | ((uint32_t)p_hi << 1), stream);
+  uint32_t lo = half_of(seed, m, t, (uint32_t)colour | ((uint32_t)p_lo << 1), stream);
+  return (hi << 16) | lo;
+}
+
+uint32_t orc_metropolis_u(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, uint64_t m) {
+  return orc_site_word(seed, stream, sweep, colour, 0, 1, m);
+}
+
+uint32_t orc_hot_word(uint64_t seed, uint32_t stream, int colour, uint64_t m) {
+  return orc_site_word(seed, stream, 0, colour, 2, 3, m);
+}
+
+/* ------------------------------------------------------- Metropolis rule */
+
+/* Eq. 2: p_acc = min[1, exp(-beta dE)], as the integer threshold
+ * floor(exp(-beta dE) 2^32); a move with dE > 0 is accepted iff u < thr. */
+uint64_t orc_threshold(double beta, int dE) {
+  if (dE <= 0) return (uint64_t)1 << 32;
+  double a = beta * (double)dE;
+  double x = exp(-a) * ORC_TWO32;
+  return (uint64_t)floor(x);
+}
+
+int orc_accept(double beta, int dE, uint32_t u) {
+  if (dE <= 0) return 1;
+  return (uint64_t)u < orc_threshold(beta, dE);
+}
+
+/* ---------------------------------------------------------- the lattice */
+
+typedef struct {
+  int nd;
+  int64_t L[3];
+  int64_t N;
+  int64_t nw;
+} lat_t;
+
+static int lat_make(lat_t* g, int nd, const int64_t* L) {
+  if (nd < 2 || nd > 3) return -1;
+  g->nd = nd;
+  g->N = 1;
+  for (int d = 0; d < 3; ++d) {
+    g->L[d] = d < nd ? L[d] : 1;
+    if (d < nd && (g->L[d] < 2 || (g->L[d] & 1))) return -1;
+    g->N *= g->L[d];
+  }
+  g->nw = (g->N + 63) / 64;
+  return 0;
+}
+
+static void lat_coords(const lat_t* g, int64_t n, int64_t x[3]) {
+  x[0] = n % g->L[0];
+  x[1] = (n / g->L[0]) % g->L[1];
+  x[2] = n / (g->L[0] * g->L[1]);
+}
+
+static int64_t lat_index(const lat_t* g, const int64_t x[3]) {
+  return x[0] + g->L[0] * (x[1] + g->L[1] * x[2]);
+}
+
+/* Neighbour of n one step along direction d, forward (dir = +1) or back. */
+static int64_t lat_step(const lat_t* g, int64_t n, int d, int dir) {
+  int64_t x[3];
+  lat_coords(g, n, x);
+  x[d] = (x[d] + dir + g->L[d]) % g->L[d];
+  return lat_index(g, x);
+}
+
+static int lat_colour(const lat_t* g, int64_t n) {
+  int64_t x[3];
+  lat_coords(g, n, x);
+  return (int)((x[0] + x[1] + x[2]) & 1);
+}
+
+static int bond_J(const lat_t* g, const uint64_t* bonds, int64_t n, int d) {
+  if (!bonds) return 1;
+  uint64_t w = bonds[(int64_t)d * g->nw + (n >> 6)];
+  return ((w >> (n & 63)) & 1) ? -1 : 1;
+}
+
+/* Local field h_n = sum_d [J(n,d) s_{n+e_d} + J(n-e_d,d) s_{n-e_d}]. */
+static int local_field(const lat_t* g, const int8_t* s, const uint64_t* bonds, int64_t n) {
+  int h = 0;
+  for (int d = 0; d < g->nd; ++d) {
+    int64_t f = lat_step(g, n, d, +1);
+    int64_t b = lat_step(g, n, d, -1);
+    h += bond_J(g, bonds, n, d) * s[f];
+    h += bond_J(g, bonds, b, d) * s[b];
+  }
+  return h;
+}
+
+int orc_delta_e(int nd, const int64_t* L, const int8_t* s, const uint64_t* bonds, int64_t n) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return 0;
+  return 2 * s[n] * local_field(&g, s, bonds, n);
+}
+
+/* Eq. 1: E = -sum over bonds J s_i s_j (each bond once, through the forward
+ * direction of its first site), M = sum s. */
+int orc_observables(int nd, const int64_t* L, const int8_t* s, const uint64_t* bonds, int64_t* E,
+                    int64_t* M) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  int64_t e = 0, m = 0;
+  for (int64_t n = 0; n < g.N; ++n) {
+    m += s[n];
+    for (int d = 0; d < g.nd; ++d) e -= (int64_t)bond_J(&g, bonds, n, d) * s[n] * s[lat_step(&g, n, d, +1)];
+  }
+  *E = e;
+  *M = m;
+  return 0;
+}
+
+int orc_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, int8_t* s) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  for (int64_t n = 0; n < g.N; ++n) {
+    uint32_t w = orc_hot_word(seed, stream, lat_colour(&g, n), (uint64_t)(n >> 1));
+    s[n] = (w >> 31) ? -1 : 1;
+  }
+  return 0;
+}
+
+/* One half-sweep: every site of colour c decides from the state at the start of
+ * the half-sweep.  Its neighbours all have the other colour, so an in-place loop
+ * is the same as a simultaneous update (Sec. 3). */
+static void half_sweep(const lat_t* g, int8_t* s, const uint64_t* bonds, const uint64_t* thr,
+                       uint64_t seed, uint32_t stream, uint32_t sweep, int c, int64_t* dEsum,
+                       int64_t* dMsum) {
+  int64_t de = 0, dm = 0;
+#pragma omp parallel for reduction(+ : de, dm) schedule(static)
+  for (int64_t n = 0; n < g->N; ++n) {
+    if (lat_colour(g, n) != c) continue;
+    int dE = 2 * s[n] * local_field(g, s, bonds, n);
+    int acc;
+    if (dE <= 0) {
+      acc = 1;
+    } else {
+      uint32_t u = orc_metropolis_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
+      acc = (uint64_t)u < thr[dE / 4];
+    }
+    if (acc) {
+      dm += -2 * s[n];
+      s[n] = (int8_t)(-s[n]);
+      de += dE;
+    }
+  }
+  *dEsum += de;
+  *dMsum += dm;
+}
+
+/* nsweeps sweeps starting at global sweep index sweep0.  E and M are the running
+ * sums (in/out); traceE/traceM, if given, receive E and M after each sweep. */
+int orc_sweeps(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, double beta, uint64_t seed,
+               uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* E, int64_t* M,
+               int64_t* traceE, int64_t* traceM) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  uint64_t thr[4];
+  for (int k = 0; k < 4; ++k) thr[k] = orc_threshold(beta, 4 * k);
+  for (int64_t t = 0; t < nsweeps; ++t) {
+    uint32_t sweep = sweep0 + (uint32_t)t;
+    int64_t de = 0, dm = 0;
+    half_sweep(&g, s, bonds, thr, seed, stream, sweep, 0, &de, &dm);
+    half_sweep(&g, s, bonds, thr, seed, stream, sweep, 1, &de, &dm);
+    *E += de;
+    *M += dm;
+    if (traceE) traceE[t] = *E;
+    if (traceM) traceM[t] = *M;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------- multi-spin coded EA */
+
+/* Replica bit j of a site word, as a spin +-1. */
+static int rep_spin(uint32_t w, int j) { return ((w >> j) & 1) ? -1 : 1; }
+
+int orc_ea_init_hot(const int64_t* L, int nsamples, uint64_t seed, uint32_t stream0, uint32_t* sp) {
+  lat_t g;
+  if (lat_make(&g, 3, L)) return -1;
+  for (int i = 0; i < nsamples; ++i)
+    for (int64_t n = 0; n < g.N; ++n)
+      sp[(int64_t)i * g.N + n] = orc_hot_word(seed, stream0 + (uint32_t)i, lat_colour(&g, n), (uint64_t)(n >> 1));
+  return 0;
+}
+
+/* Energy and magnetisation of every replica of every sample, indexed by slot:
+ * E[i*32 + j], M[i*32 + j]. */
+int orc_ea_observables(const int64_t* L, int nsamples, const uint32_t* sp, const uint64_t* bonds,
+                       int64_t* E, int64_t* M) {
+  lat_t g;
+  if (lat_make(&g, 3, L)) return -1;
+  for (int i = 0; i < nsamples; ++i) {
+    const uint32_t* w = sp + (int64_t)i * g.N;
+    const uint64_t* J = bonds + (int64_t)i * 3 * g.nw;
+    for (int j = 0; j < 32; ++j) {
+      int64_t e = 0, m = 0;
+      for (int64_t n = 0; n < g.N; ++n) {
+        int sn = rep_spin(w[n], j);
+        m += sn;
+        for (int d = 0; d < 3; ++d) e -= (int64_t)bond_J(&g, J, n, d) * sn * rep_spin(w[lat_step(&g, n, d, +1)], j);
+      }
+      E[i * 32 + j] = e;
+      M[i * 32 + j] = m;
+    }
+  }
+  return 0;
+}
+
+/* One exchange step e for one sample (temperatures indexed by ascending T).
+ * Eslot: energies by slot; slot_of_temp / temp_of_slot: the permutation (in/out);
+ * acc: per-pair acceptance counters (may be NULL). */
+static void exchange_step(const double* betas, const int64_t* Eslot, uint8_t* slot_of_temp,
+                          uint8_t* temp_of_slot, uint64_t seed, uint32_t stream, uint32_t e, int64_t* acc) {
+  int64_t Et[32];
+  for (int t = 0; t < 32; ++t) Et[t] = Eslot[slot_of_temp[t]];
+  for (int k = (int)(e & 1); k + 1 < 32; k += 2) {
+    double D = (betas[k] - betas[k + 1]) * (double)(Et[k] - Et[k + 1]);
+    int accept;
+    if (D >= 0) {
+      accept = 1;
+    } else {
+      uint32_t ctr[4] = {(uint32_t)k >> 2, e, 4u << 1, stream};
+      uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+      uint32_t w[4];
+      orc_philox4x32_10(ctr, key, w);
+      uint64_t thr = (uint64_t)floor(exp(D) * ORC_TWO32);
+      accept = (uint64_t)w[k & 3] < thr;
+    }
+    if (accept) {
+      uint8_t a = slot_of_temp[k], b = slot_of_temp[k + 1];
+      slot_of_temp[k] = b;
+      slot_of_temp[k + 1] = a;
+      temp_of_slot[b] = (uint8_t)k;
+      temp_of_slot[a] = (uint8_t)(k + 1);
+      if (acc) acc[k] += 1;
+    }
+  }
+}
+
+/* nsweeps multi-spin coded sweeps of nsamples samples (sample i uses stream
+ * stream0 + i), from global sweep index sweep0, with replica exchange after every
+ * exchange_every-th sweep (0 = never).  temp_of_slot / slot_of_temp: [sample][32],
+ * in/out.  acc: [sample][32] exchange acceptance counters (may be NULL). */
+int orc_ea_sweeps(const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
+                  uint8_t* temp_of_slot, uint8_t* slot_of_temp, uint64_t seed, uint32_t stream0,
+                  uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
+  lat_t g;
+  if (lat_make(&g, 3, L)) return -1;
+  uint64_t thr[32][4];
+  for (int t = 0; t < 32; ++t)
+    for (int k = 0; k < 4; ++k) thr[t][k] = orc_threshold(betas[t], 4 * k);
+  int64_t* Eslot = (int64_t*)malloc(sizeof(int64_t) * 32);
+  int64_t* Mslot = (int64_t*)malloc(sizeof(int64_t) * 32);
+  for (int i = 0; i < nsamples; ++i) {
+    uint32_t* w = sp + (int64_t)i * g.N;
+    const uint64_t* J = bonds + (int64_t)i * 3 * g.nw;
+    uint8_t* pi = temp_of_slot + 32 * i;
+    uint8_t* tau = slot_of_temp + 32 * i;
+    uint32_t stream = stream0 + (uint32_t)i;
+    for (int64_t t = 0; t < nsweeps; ++t) {
+      uint32_t sweep = sweep0 + (uint32_t)t;
+      for (int c = 0; c < 2; ++c) {
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < g.N; ++n) {
+          if (lat_colour(&g, n) != c) continue;
+          uint32_t u = orc_metropolis_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
+          uint32_t flip = 0;
+          for (int j = 0; j < 32; ++j) {
+            int sn = rep_spin(w[n], j);
+            int h = 0;
+            for (int d = 0; d < 3; ++d) {
+              int64_t f = lat_step(&g, n, d, +1), b = lat_step(&g, n, d, -1);
+              h += bond_J(&g, J, n, d) * rep_spin(w[f], j);
+              h += bond_J(&g, J, b, d) * rep_spin(w[b], j);
+            }
+            int dE = 2 * sn * h;
+            int a = dE <= 0 || (uint64_t)u < thr[pi[j]][dE / 4];
+            if (a) flip |= 1u << j;
+          }
+          w[n] ^= flip;
+        }
+      }
+      if (exchange_every > 0 && ((int64_t)sweep + 1) % exchange_every == 0) {
+        uint32_t e = (uint32_t)(((int64_t)sweep + 1) / exchange_every - 1);
+        orc_ea_observables(L, 1, w, J, Eslot, Mslot);
+        exchange_step(betas, Eslot, tau, pi, seed, stream, e, acc ? acc + 32 * i : NULL);
+      }
+    }
+  }
+  free(Eslot);
+  free(Mslot);
+  return 0;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  extern int omp_get_max_threads(void);
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
