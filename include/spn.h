@@ -1,0 +1,138 @@
+/*
+ * spn.h -- C ABI of libspn, checkerboard Metropolis sweeps of nearest-neighbour
+ * Ising-type lattices on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the single-spin-flip Metropolis simulation of the Ising model
+ * (M. Weigel, "Simulating spin models on GPU", Sec. 3): Hamiltonian Eq. 1,
+ * H = -J sum_<ij> s_i s_j with s_i = +-1 on square (2D) and simple-cubic (3D)
+ * lattices with periodic boundaries; acceptance Eq. 2, p = min[1, exp(-beta dE)];
+ * the two sub-lattices of the checkerboard decomposition are updated one after
+ * the other because the sites of one colour are independent.  Sec. 4 extends it
+ * to the 3D model and to the +-J Edwards-Anderson spin glass with many disorder
+ * samples multi-spin coded into machine words.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SPN_OK (0) on success, a negative SPN_E_* code on failure.
+ *     spn_last_error() gives a message for the calling thread's last failure.
+ *     No C++ exception crosses this boundary.
+ *   - dims: int32[2] (2D) or int32[3] (3D), x fastest; every extent even, >= 2.
+ *     Site n = x + Lx*(y + Ly*z); colour c(n) = (x+y+z) & 1; m = n >> 1.
+ *   - Spins on the host are int8 +-1 in site order.  Couplings ("bonds") are
+ *     bit-packed uint64 words [sample][dir][ceil(N/64)], bit (n % 64) of word
+ *     n / 64 set iff J(n, dir) = -1 for the bond from n to n + e_dir.
+ *   - Memory: the library owns every device buffer it allocates; host buffers
+ *     passed in are read (or written) during the call only.  Device-pointer
+ *     entry points (spn_dev_*) never allocate and never free.
+ *   - Randomness: Philox4x32-10 keyed by the 64-bit seed; counters (group m>>3,
+ *     sweep, colour | purpose<<1, stream).  A site's 32-bit Metropolis number is
+ *     (high 16 bits from purpose 0) << 16 | (low 16 bits from purpose 1); a
+ *     move with dE > 0 is accepted iff u < floor(exp(-beta dE) * 2^32).  Results
+ *     are bit-identical for a given (seed, stream, sweep index, beta).
+ *   - A handle is not thread-safe; a server is.
+ */
+#ifndef SPN_H
+#define SPN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum spn_status {
+  SPN_OK = 0,
+  SPN_E_ARG = -1,      /* invalid argument (null pointer, odd extent, wrong size ...) */
+  SPN_E_NOMEM = -2,    /* device or host allocation failed */
+  SPN_E_BUDGET = -3,   /* a served job does not fit the server's HBM budget */
+  SPN_E_CUDA = -4,     /* a CUDA runtime call failed (message in spn_last_error) */
+  SPN_E_TIMEOUT = -5,  /* a bounded device wait ran out (no hang, state preserved) */
+  SPN_E_STATE = -6,    /* call not valid for this handle's model or state */
+  SPN_E_NOTFOUND = -7  /* unknown ticket */
+};
+
+enum spn_model {
+  SPN_ISING2D = 1,   /* square lattice, J = +1 (Eq. 1) */
+  SPN_ISING3D = 2,   /* simple cubic, J = +1 (Sec. 4) */
+  SPN_EA3D_PMJ = 3   /* simple cubic, J = +-1 per bond (Sec. 4, spin glass) */
+};
+
+enum spn_init { SPN_INIT_HOT = 0, SPN_INIT_COLD = 1 };
+
+typedef struct spn_ctx* spn_handle;
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* spn_last_error(void);
+
+/* Library version string and the device it runs on (prints nothing). */
+const char* spn_version(void);
+
+/* ------------------------------------------------------------------------
+ * Single lattice (Sec. 3 procedure; Eq. 1-2)
+ * ---------------------------------------------------------------------- */
+
+/* Create a lattice of `model` with extents `dims`, hot start from Philox
+ * (stream 0).  couplings: NULL for the Ising models; for SPN_EA3D_PMJ one
+ * sample of bit-packed bonds [3][ceil(N/64)] (copied).  Errors: SPN_E_ARG for
+ * odd/too small extents or a missing/unexpected coupling array, SPN_E_NOMEM,
+ * SPN_E_CUDA. */
+int spn_create(spn_handle* out, int model, const int32_t* dims, const void* couplings, uint64_t seed);
+
+/* As spn_create with an explicit Philox stream id and start (SPN_INIT_HOT or
+ * SPN_INIT_COLD = all +1). */
+int spn_create_ex(spn_handle* out, int model, const int32_t* dims, const void* couplings, uint64_t seed,
+                  uint32_t stream, int init);
+
+/* Run nsweeps sweeps at inverse temperature beta >= 0 (may be +inf) on the
+ * handle's stream, asynchronously.  Sweep k of the handle's life uses sweep
+ * counter k.  Each sweep updates colour 0, then colour 1 (Sec. 3); energy and
+ * magnetisation change by the accepted moves and are recorded per sweep. */
+int spn_sweep(spn_handle h, double beta, int64_t nsweeps);
+
+/* Current integer energy E = -sum J s_i s_j (Eq. 1, each bond once) and
+ * magnetisation M = sum s_i (synchronises the handle's stream). */
+int spn_observables(spn_handle h, int64_t* E, int64_t* M);
+
+/* Recompute E and M from the spins with a full reduction (independent of the
+ * incremental bookkeeping; synchronises). */
+int spn_recompute(spn_handle h, int64_t* E, int64_t* M);
+
+/* Per-sweep trace of (E, M) after every sweep since creation, oldest first:
+ * writes min(cap, total) entries and the total count to *n (synchronises). */
+int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n);
+
+/* Copy the spins (int8 +-1, site order) into host_out; bytes must be N. */
+int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes);
+
+/* Replace the spins from a host buffer of N int8 +-1 values; E and M are
+ * recomputed.  The sweep counter is kept. */
+int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes);
+
+/* Number of sweeps done so far (the next sweep's counter). */
+int spn_sweep_count(spn_handle h, uint64_t* count);
+
+/* Make the handle use an existing CUDA stream (cudaStream_t as void*; NULL =
+ * the legacy default stream).  The caller keeps ownership of the stream. */
+int spn_set_stream(spn_handle h, void* cuda_stream);
+
+/* Wait for the handle's queued work. */
+int spn_sync(spn_handle h);
+
+/* Release the handle and its device memory (synchronises first). */
+int spn_destroy(spn_handle h);
+
+/* Tile configuration of the streaming sweep kernel for this handle
+ * (tile_x: sites per tile row, multiple of 16; tile_y: rows per slice in 3D;
+ * seg: slices per CTA, 0 = automatic).  Results never depend on it. */
+int spn_set_tiling(spn_handle h, int32_t tile_x, int32_t tile_y, int32_t seg);
+
+/* Which kernel path the handle uses: 0 = generic global-memory sweep,
+ * 1 = streaming shared-memory sweep, 2 = shared-memory-resident sweep. */
+int spn_get_path(spn_handle h, int32_t* path);
+int spn_set_path(spn_handle h, int32_t path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPN_H */

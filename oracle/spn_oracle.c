@@ -202,6 +202,7 @@ int orc_observables(int nd, const int64_t* L, const int8_t* s, const uint64_t* b
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
   int64_t e = 0, m = 0;
+#pragma omp parallel for reduction(+ : e, m) schedule(static)
   for (int64_t n = 0; n < g.N; ++n) {
     m += s[n];
     for (int d = 0; d < g.nd; ++d) e -= (int64_t)bond_J(&g, bonds, n, d) * s[n] * s[lat_step(&g, n, d, +1)];
@@ -214,6 +215,7 @@ int orc_observables(int nd, const int64_t* L, const int8_t* s, const uint64_t* b
 int orc_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, int8_t* s) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
+#pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < g.N; ++n) {
     uint32_t w = orc_hot_word(seed, stream, lat_colour(&g, n), (uint64_t)(n >> 1));
     s[n] = (w >> 31) ? -1 : 1;

@@ -1,0 +1,358 @@
+// C ABI of libspn (declared in include/spn.h): single-lattice handles.
+//
+// A handle owns its device buffers: two int8 spin buffers (ping-pong for the
+// streaming kernel), optional per-site bond bytes, a per-sweep (dE, dM) delta
+// array and an error word.  Sweeps are queued on the handle's stream; the host
+// folds the per-sweep deltas into E, M and the trace when it is asked for them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "spn.h"
+#include "spn_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SPN_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SPN_CUDA(call, what)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+int check_dims(int model, const int32_t* dims, spn::Lattice& g) {
+  if (!dims) return fail(SPN_E_ARG, "dims is NULL");
+  if (model != SPN_ISING2D && model != SPN_ISING3D && model != SPN_EA3D_PMJ)
+    return fail(SPN_E_ARG, "unknown model %d", model);
+  g.nd = model == SPN_ISING2D ? 2 : 3;
+  g.Lx = dims[0];
+  g.Ly = dims[1];
+  g.Lz = g.nd == 3 ? dims[2] : 1;
+  const int ext[3] = {g.Lx, g.Ly, g.Lz};
+  for (int d = 0; d < g.nd; ++d)
+    if (ext[d] < 2 || (ext[d] & 1)) return fail(SPN_E_ARG, "extent %d along axis %d must be even and >= 2", ext[d], d);
+  g.N = (int64_t)g.Lx * g.Ly * g.Lz;
+  if (g.N >= ((int64_t)1 << 35)) return fail(SPN_E_ARG, "lattice too large (%lld sites)", (long long)g.N);
+  return SPN_OK;
+}
+
+// Bit-packed [dir][ceil(N/64)] words -> per-site byte, bit d set iff J(n, d) = -1.
+std::vector<uint8_t> unpack_site_bonds(const uint64_t* words, int nd, int64_t N) {
+  const int64_t nw = (N + 63) / 64;
+  std::vector<uint8_t> out((size_t)N, 0);
+  for (int d = 0; d < nd; ++d)
+    for (int64_t n = 0; n < N; ++n)
+      if ((words[d * nw + (n >> 6)] >> (n & 63)) & 1) out[(size_t)n] |= (uint8_t)(1u << d);
+  return out;
+}
+
+void pick_default_path(spn_ctx* h) {
+  const spn::Lattice& g = h->g;
+  int tx = g.Lx;
+  while (tx > 8192 && tx % 2 == 0 && (tx / 2) % 16 == 0) tx /= 2;
+  int ty = 16;
+  if (g.nd == 3) {
+    while (ty > 1 && g.Ly % ty) ty /= 2;
+  }
+  if (g.nd == 3 && g.Lx > 1024) tx = 1024 - (1024 % 16);
+  if (g.Lx % tx) tx = g.Lx;
+  h->tile_x = tx;
+  h->tile_y = ty;
+  h->seg = 0;
+  h->path = spn::stream_path_supported(g, tx, ty) && g.N >= (1 << 16) ? spn::kPathStream : spn::kPathGeneric;
+}
+
+int ensure_acc(spn_ctx* h, int64_t n) {
+  // deltas for sweeps [folded, sweeps + n)
+  const int64_t need = (int64_t)(h->sweeps - h->folded) + n;
+  if (need <= h->acc_cap) return SPN_OK;
+  int64_t cap = h->acc_cap ? h->acc_cap : 1024;
+  while (cap < need) cap *= 2;
+  unsigned long long* p = nullptr;
+  SPN_CUDA(cudaMalloc(&p, (size_t)cap * 2 * sizeof(unsigned long long)), "cudaMalloc(trace)");
+  SPN_CUDA(cudaMemsetAsync(p, 0, (size_t)cap * 2 * sizeof(unsigned long long), h->st), "cudaMemsetAsync");
+  const int64_t live = (int64_t)(h->sweeps - h->folded);
+  if (live > 0 && h->d_acc)
+    SPN_CUDA(cudaMemcpyAsync(p, h->d_acc, (size_t)live * 2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                             h->st),
+             "cudaMemcpyAsync(trace)");
+  if (h->d_acc) {
+    cudaStreamSynchronize(h->st);
+    cudaFree(h->d_acc);
+  }
+  h->d_acc = p;
+  h->acc_cap = cap;
+  return SPN_OK;
+}
+
+// Fold the device deltas of all sweeps so far into E, M and the host trace.
+int fold(spn_ctx* h) {
+  SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  int err = 0;
+  SPN_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy(err)");
+  if (err) return fail(SPN_E_TIMEOUT, "a bounded device wait ran out in a sweep kernel (code %d)", err);
+  const int64_t live = (int64_t)(h->sweeps - h->folded);
+  if (live <= 0) return SPN_OK;
+  std::vector<unsigned long long> d((size_t)live * 2);
+  SPN_CUDA(cudaMemcpy(d.data(), h->d_acc, d.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost),
+           "cudaMemcpy(trace)");
+  for (int64_t i = 0; i < live; ++i) {
+    h->E += (int64_t)d[2 * i];
+    h->M += (int64_t)d[2 * i + 1];
+    h->traceE.push_back(h->E);
+    h->traceM.push_back(h->M);
+  }
+  h->folded = h->sweeps;
+  SPN_CUDA(cudaMemsetAsync(h->d_acc, 0, (size_t)h->acc_cap * 2 * sizeof(unsigned long long), h->st),
+           "cudaMemsetAsync(trace)");
+  return SPN_OK;
+}
+
+int recompute(spn_ctx* h, int64_t* E, int64_t* M) {
+  SPN_CUDA(spn::launch_observables(h->g, h->spins[h->cur], h->d_obs, h->st), "observables");
+  unsigned long long r[2];
+  SPN_CUDA(cudaMemcpyAsync(r, h->d_obs, sizeof r, cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync(obs)");
+  SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  *E = (int64_t)r[0];
+  *M = (int64_t)r[1];
+  return SPN_OK;
+}
+
+void destroy(spn_ctx* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  cudaFree(h->spins[0]);
+  cudaFree(h->spins[1]);
+  cudaFree(h->d_bonds);
+  cudaFree(h->d_acc);
+  cudaFree(h->d_err);
+  cudaFree(h->d_obs);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* spn_last_error(void) { return g_last_error.c_str(); }
+
+const char* spn_version(void) { return "libspn 0.1 (sm_103a)"; }
+
+int spn_create_ex(spn_handle* out, int model, const int32_t* dims, const void* couplings, uint64_t seed,
+                  uint32_t stream, int init) {
+  if (!out) return fail(SPN_E_ARG, "out is NULL");
+  *out = nullptr;
+  spn::Lattice g;
+  int rc = check_dims(model, dims, g);
+  if (rc) return rc;
+  if (model == SPN_EA3D_PMJ && !couplings) return fail(SPN_E_ARG, "SPN_EA3D_PMJ needs couplings");
+  if (model != SPN_EA3D_PMJ && couplings) return fail(SPN_E_ARG, "Ising models take no couplings");
+  if (init != SPN_INIT_HOT && init != SPN_INIT_COLD) return fail(SPN_E_ARG, "unknown init %d", init);
+  spn_ctx* h = new (std::nothrow) spn_ctx;
+  if (!h) return fail(SPN_E_NOMEM, "host allocation failed");
+  h->model = model;
+  h->g = g;
+  h->seed = seed;
+  h->stream_id = stream;
+  auto bail = [&](int code) {
+    destroy(h);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->spins[0], (size_t)g.N)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(spins)"));
+  if ((e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(err)"));
+  if ((e = cudaMalloc(&h->d_obs, 2 * sizeof(unsigned long long))) != cudaSuccess)
+    return bail(cuda_fail(e, "cudaMalloc(obs)"));
+  if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
+  if (couplings) {
+    std::vector<uint8_t> sb = unpack_site_bonds(static_cast<const uint64_t*>(couplings), g.nd, g.N);
+    if ((e = cudaMalloc(&h->d_bonds, (size_t)g.N)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(bonds)"));
+    if ((e = cudaMemcpy(h->d_bonds, sb.data(), (size_t)g.N, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(cuda_fail(e, "cudaMemcpy(bonds)"));
+    h->g.bonds = h->d_bonds;
+  }
+  pick_default_path(h);
+  if (h->path == spn::kPathStream)
+    if ((e = cudaMalloc(&h->spins[1], (size_t)g.N)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(spins)"));
+  if (init == SPN_INIT_HOT) {
+    if ((e = spn::launch_init_hot(h->g, h->spins[0], seed, stream, h->st)) != cudaSuccess)
+      return bail(cuda_fail(e, "init"));
+  } else {
+    if ((e = cudaMemsetAsync(h->spins[0], 1, (size_t)g.N, h->st)) != cudaSuccess) return bail(cuda_fail(e, "init"));
+  }
+  if ((rc = ensure_acc(h, 1024))) return bail(rc);
+  int64_t E, M;
+  if ((rc = recompute(h, &E, &M))) return bail(rc);
+  h->E = E;
+  h->M = M;
+  *out = h;
+  return SPN_OK;
+}
+
+int spn_create(spn_handle* out, int model, const int32_t* dims, const void* couplings, uint64_t seed) {
+  return spn_create_ex(out, model, dims, couplings, seed, 0, SPN_INIT_HOT);
+}
+
+int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (!(beta >= 0.0)) return fail(SPN_E_ARG, "beta must be >= 0 (got %g)", beta);
+  if (nsweeps < 0) return fail(SPN_E_ARG, "nsweeps must be >= 0");
+  if (nsweeps == 0) return SPN_OK;
+  if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return fail(SPN_E_ARG, "sweep counter would exceed 2^32");
+  int rc = ensure_acc(h, nsweeps);
+  if (rc) return rc;
+  const spn::ThrTab T = spn::make_thresholds(beta);
+  const spn::PhiloxKeys K = spn::philox_keys(h->seed);
+  spn::StreamGeom geo{};
+  if (h->path == spn::kPathStream) geo = spn::stream_geometry(h->g, h->tile_x, h->tile_y, h->seg);
+  for (int64_t t = 0; t < nsweeps; ++t) {
+    const uint32_t sweep = (uint32_t)(h->sweeps + t);
+    unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);
+    cudaError_t e;
+    if (h->path == spn::kPathStream) {
+      e = spn::launch_sweep_stream(h->g, h->spins[h->cur], h->spins[h->cur ^ 1], geo, T, K, h->stream_id, sweep,
+                                   acc, h->d_err, h->st);
+      if (e == cudaSuccess) h->cur ^= 1;
+    } else {
+      e = spn::launch_sweep_generic(h->g, h->spins[h->cur], T, K, h->stream_id, sweep, acc, h->st);
+    }
+    if (e != cudaSuccess) {
+      h->sweeps += (uint64_t)t;
+      return cuda_fail(e, "sweep launch");
+    }
+  }
+  h->sweeps += (uint64_t)nsweeps;
+  return SPN_OK;
+}
+
+int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
+  if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
+  int rc = fold(h);
+  if (rc) return rc;
+  *E = h->E;
+  *M = h->M;
+  return SPN_OK;
+}
+
+int spn_recompute(spn_handle h, int64_t* E, int64_t* M) {
+  if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
+  return recompute(h, E, M);
+}
+
+int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n) {
+  if (!h || !n || cap < 0 || (cap > 0 && (!E || !M))) return fail(SPN_E_ARG, "bad trace arguments");
+  int rc = fold(h);
+  if (rc) return rc;
+  const int64_t total = (int64_t)h->traceE.size();
+  const int64_t k = cap < total ? cap : total;
+  if (k > 0) {
+    std::memcpy(E, h->traceE.data(), (size_t)k * sizeof(int64_t));
+    std::memcpy(M, h->traceM.data(), (size_t)k * sizeof(int64_t));
+  }
+  *n = total;
+  return SPN_OK;
+}
+
+int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
+  if (!h || !host_out) return fail(SPN_E_ARG, "NULL argument");
+  if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
+  SPN_CUDA(cudaMemcpyAsync(host_out, h->spins[h->cur], bytes, cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync");
+  SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  return SPN_OK;
+}
+
+int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
+  if (!h || !host_in) return fail(SPN_E_ARG, "NULL argument");
+  if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
+  for (size_t i = 0; i < bytes; ++i)
+    if (host_in[i] != 1 && host_in[i] != -1) return fail(SPN_E_ARG, "spin %zu is not +-1", i);
+  int rc = fold(h);
+  if (rc) return rc;
+  SPN_CUDA(cudaMemcpyAsync(h->spins[h->cur], host_in, bytes, cudaMemcpyHostToDevice, h->st), "cudaMemcpyAsync");
+  int64_t E, M;
+  if ((rc = recompute(h, &E, &M))) return rc;
+  h->E = E;
+  h->M = M;
+  return SPN_OK;
+}
+
+int spn_sweep_count(spn_handle h, uint64_t* count) {
+  if (!h || !count) return fail(SPN_E_ARG, "NULL argument");
+  *count = h->sweeps;
+  return SPN_OK;
+}
+
+int spn_set_stream(spn_handle h, void* cuda_stream) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  h->st = static_cast<cudaStream_t>(cuda_stream);
+  return SPN_OK;
+}
+
+int spn_sync(spn_handle h) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  return SPN_OK;
+}
+
+int spn_destroy(spn_handle h) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  destroy(h);
+  return SPN_OK;
+}
+
+int spn_set_tiling(spn_handle h, int32_t tile_x, int32_t tile_y, int32_t seg) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (!spn::stream_path_supported(h->g, tile_x, h->g.nd == 3 ? tile_y : 1))
+    return fail(SPN_E_ARG, "tiling %d x %d does not divide the lattice", tile_x, tile_y);
+  spn::StreamGeom geo = spn::stream_geometry(h->g, tile_x, h->g.nd == 3 ? tile_y : 1, seg);
+  const int nA = (h->g.nd == 3 ? tile_y + 2 : 1) * (tile_x / 16);
+  if (geo.threads > 512 || nA > geo.threads * 2 || geo.smem > 227 * 1024)
+    return fail(SPN_E_ARG, "tiling %d x %d too large for one CTA", tile_x, tile_y);
+  h->tile_x = tile_x;
+  h->tile_y = h->g.nd == 3 ? tile_y : 1;
+  h->seg = seg;
+  return SPN_OK;
+}
+
+int spn_get_path(spn_handle h, int32_t* path) {
+  if (!h || !path) return fail(SPN_E_ARG, "NULL argument");
+  *path = h->path;
+  return SPN_OK;
+}
+
+int spn_set_path(spn_handle h, int32_t path) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (path == spn::kPathStream) {
+    if (!spn::stream_path_supported(h->g, h->tile_x, h->g.nd == 3 ? h->tile_y : 1))
+      return fail(SPN_E_ARG, "streaming path needs Lx %% 16 == 0 and no bonds");
+    if (!h->spins[1]) SPN_CUDA(cudaMalloc(&h->spins[1], (size_t)h->g.N), "cudaMalloc(spins)");
+  } else if (path != spn::kPathGeneric) {
+    return fail(SPN_E_ARG, "unknown path %d", path);
+  }
+  h->path = path;
+  return SPN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Internal declarations of libspn: handle layout, kernel parameter blocks and
+// launchers shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "philox.cuh"
+
+namespace spn {
+
+// Metropolis thresholds of Eq. 2 split into 16-bit halves, indexed by dE / 4
+// (1 .. 3): a move with energy change dE > 0 is accepted iff
+// u_hi < hi[dE/4], or u_hi == hi[dE/4] and u_lo < lo[dE/4]; hi may be 0x10000.
+struct ThrTab {
+  uint32_t hi[4];
+  uint32_t lo[4];
+};
+
+// floor(exp(-beta * dE) * 2^32) in [0, 2^32] (host, IEEE double).
+uint64_t boltzmann_threshold(double beta, int dE);
+ThrTab make_thresholds(double beta);
+
+// Kernel paths of a single lattice.
+enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2 };
+
+// Streaming-kernel geometry; see ising.cu.
+struct StreamGeom {
+  int TX, TY, nseg, threads, nbuf;
+  size_t smem;
+};
+
+struct Lattice {
+  int nd = 2;
+  int Lx = 0, Ly = 0, Lz = 1;
+  int64_t N = 0;
+  const uint8_t* bonds = nullptr;  // per-site byte, bit d set iff J(n, d) = -1 (null: J = +1)
+};
+
+// Launchers (all asynchronous on `st`).  acc points at two int64 (dE, dM) that
+// the sweep adds its accepted moves to; err is a device error word.
+cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t stream_id, cudaStream_t st);
+cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long long* out2, cudaStream_t st);
+cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const ThrTab& T, const PhiloxKeys& K,
+                                 uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st);
+bool stream_path_supported(const Lattice& g, int TX, int TY);
+StreamGeom stream_geometry(const Lattice& g, int TX, int TY, int nseg);
+cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out, const StreamGeom& geo,
+                                const ThrTab& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                unsigned long long* acc, int* err, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace spn
+
+struct spn_ctx {
+  int model = 0;
+  spn::Lattice g;
+  uint64_t seed = 0;
+  uint32_t stream_id = 0;
+  int8_t* spins[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint8_t* d_bonds = nullptr;
+  cudaStream_t st = nullptr;
+  int path = spn::kPathGeneric;
+  int tile_x = 0, tile_y = 0, seg = 0;
+  uint64_t sweeps = 0;
+  // incremental bookkeeping: device deltas (dE, dM) per sweep since `folded`
+  unsigned long long* d_acc = nullptr;
+  int64_t acc_cap = 0;
+  uint64_t folded = 0;  // sweeps already folded into the host trace
+  int64_t E = 0, M = 0;  // observables after `folded` sweeps
+  std::vector<int64_t> traceE, traceM;
+  int* d_err = nullptr;
+  unsigned long long* d_obs = nullptr;
+};

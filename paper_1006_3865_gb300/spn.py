@@ -1,0 +1,216 @@
+"""Thin ctypes binding of libspn (the C ABI in ``include/spn.h``).
+
+Argument marshalling only: every step of a sweep runs in the CUDA kernels of
+``libspn.so``.  ``load()`` fails loudly when the library has not been built or
+cannot be loaded; there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libspn.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "spn.h")
+
+SPN_OK = 0
+SPN_E_ARG = -1
+SPN_E_NOMEM = -2
+SPN_E_BUDGET = -3
+SPN_E_CUDA = -4
+SPN_E_TIMEOUT = -5
+SPN_E_STATE = -6
+SPN_E_NOTFOUND = -7
+
+SPN_ISING2D = 1
+SPN_ISING3D = 2
+SPN_EA3D_PMJ = 3
+
+SPN_INIT_HOT = 0
+SPN_INIT_COLD = 1
+
+PATH_GENERIC = 0
+PATH_STREAM = 1
+PATH_RESIDENT = 2
+
+_lock = threading.Lock()
+_lib = None
+
+_c = ctypes
+_vp, _i32, _i64, _u32, _u64, _dbl, _sz = (_c.c_void_p, _c.c_int32, _c.c_int64, _c.c_uint32, _c.c_uint64,
+                                          _c.c_double, _c.c_size_t)
+_P = _c.POINTER
+
+# name -> (restype, argtypes); every entry is an extern "C" function of spn.h
+_SIGNATURES = {
+    "spn_last_error": (_c.c_char_p, []),
+    "spn_version": (_c.c_char_p, []),
+    "spn_create": (_c.c_int, [_P(_vp), _c.c_int, _vp, _vp, _u64]),
+    "spn_create_ex": (_c.c_int, [_P(_vp), _c.c_int, _vp, _vp, _u64, _u32, _c.c_int]),
+    "spn_sweep": (_c.c_int, [_vp, _dbl, _i64]),
+    "spn_observables": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
+    "spn_recompute": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
+    "spn_trace": (_c.c_int, [_vp, _vp, _vp, _i64, _P(_i64)]),
+    "spn_get_spins": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_set_spins": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_sweep_count": (_c.c_int, [_vp, _P(_u64)]),
+    "spn_set_stream": (_c.c_int, [_vp, _vp]),
+    "spn_sync": (_c.c_int, [_vp]),
+    "spn_destroy": (_c.c_int, [_vp]),
+    "spn_set_tiling": (_c.c_int, [_vp, _i32, _i32, _i32]),
+    "spn_get_path": (_c.c_int, [_vp, _P(_i32)]),
+    "spn_set_path": (_c.c_int, [_vp, _i32]),
+}
+
+
+class SpnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libspn error {code}: {msg}")
+        self.code = code
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/spn.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spn_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str | None = None):
+    """Load libspn.so (build it first with paper_1006_3865_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libspn.so not found at {p}: run __graft_entry__.build() "
+                               "(or paper_1006_3865_gb300.build.build()) first; there is no CPU fallback")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != SPN_OK:
+        raise SpnError(rc, load().spn_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+def _dims(dims) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+
+
+def _stream_ptr(stream) -> int | None:
+    """cudaStream_t of a torch.cuda.Stream (or an int / None)."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Lattice:
+    """One lattice handle (spn_create ... spn_destroy)."""
+
+    def __init__(self, model: int, dims, seed: int, couplings: np.ndarray | None = None, stream_id: int = 0,
+                 init: int = SPN_INIT_HOT):
+        self._lib = load()
+        self.model = model
+        self.dims = tuple(int(d) for d in dims)
+        self.N = int(np.prod(self.dims))
+        d = _dims(dims)
+        b = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.uint64)
+        h = _vp()
+        _check(self._lib.spn_create_ex(_c.byref(h), model, _ptr(d), _ptr(b), seed, stream_id, init))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def sweep(self, beta: float, nsweeps: int):
+        _check(self._lib.spn_sweep(self._h, float(beta), int(nsweeps)))
+
+    def observables(self) -> tuple[int, int]:
+        E, M = _i64(), _i64()
+        _check(self._lib.spn_observables(self._h, _c.byref(E), _c.byref(M)))
+        return E.value, M.value
+
+    def recompute(self) -> tuple[int, int]:
+        E, M = _i64(), _i64()
+        _check(self._lib.spn_recompute(self._h, _c.byref(E), _c.byref(M)))
+        return E.value, M.value
+
+    def trace(self) -> tuple[np.ndarray, np.ndarray]:
+        n = _i64()
+        _check(self._lib.spn_trace(self._h, None, None, 0, _c.byref(n)))
+        E = np.zeros(n.value, np.int64)
+        M = np.zeros(n.value, np.int64)
+        _check(self._lib.spn_trace(self._h, _ptr(E), _ptr(M), n.value, _c.byref(n)))
+        return E, M
+
+    def get_spins(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.N, dtype=np.int8)
+        if out.dtype != np.int8 or out.size != self.N or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous int8 array of N elements")
+        _check(self._lib.spn_get_spins(self._h, _ptr(out), self.N))
+        return out
+
+    def set_spins(self, spins: np.ndarray):
+        s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+        _check(self._lib.spn_set_spins(self._h, _ptr(s), s.size))
+
+    def sweep_count(self) -> int:
+        c = _u64()
+        _check(self._lib.spn_sweep_count(self._h, _c.byref(c)))
+        return c.value
+
+    def set_stream(self, stream):
+        _check(self._lib.spn_set_stream(self._h, _stream_ptr(stream)))
+
+    def sync(self):
+        _check(self._lib.spn_sync(self._h))
+
+    def set_tiling(self, tile_x: int, tile_y: int = 0, seg: int = 0):
+        _check(self._lib.spn_set_tiling(self._h, tile_x, tile_y, seg))
+
+    @property
+    def path(self) -> int:
+        p = _i32()
+        _check(self._lib.spn_get_path(self._h, _c.byref(p)))
+        return p.value
+
+    @path.setter
+    def path(self, value: int):
+        _check(self._lib.spn_set_path(self._h, int(value)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.spn_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

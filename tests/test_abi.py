@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every function of include/spn.h;
+host-side argument checks reject bad input before any device work (no GPU
+needed)."""
+
+from __future__ import annotations
+
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1006_3865_gb300 import build as spn_build
+from paper_1006_3865_gb300 import spn
+
+
+@pytest.fixture(scope="module")
+def lib():
+    spn_build.build()
+    return spn.load()
+
+
+def test_every_header_function_is_exported_and_bound(lib):
+    declared = spn.header_functions()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", spn.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for name in declared:
+        assert name in exported, f"{name} declared in spn.h but not exported"
+        assert name in spn._SIGNATURES, f"{name} has no binding"
+        getattr(lib, name)
+    assert set(spn._SIGNATURES) <= set(declared)
+
+
+def _create(lib, model, dims, couplings=None, init=0):
+    h = ctypes.c_void_p()
+    d = np.asarray(dims, dtype=np.int32)
+    c = None if couplings is None else couplings.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.spn_create_ex(ctypes.byref(h), model, d.ctypes.data_as(ctypes.c_void_p), c, 1, 0, init)
+    return rc, lib.spn_last_error().decode()
+
+
+@pytest.mark.parametrize("model,dims", [(1, (3, 4)), (1, (4, 0)), (2, (4, 4, 5)), (2, (4, 2, -2)), (1, (1, 2))])
+def test_odd_or_empty_extents_are_rejected(lib, model, dims):
+    rc, msg = _create(lib, model, dims)
+    assert rc == spn.SPN_E_ARG and "even" in msg
+
+
+def test_bad_model_and_couplings_are_rejected(lib):
+    assert _create(lib, 7, (4, 4))[0] == spn.SPN_E_ARG
+    assert _create(lib, spn.SPN_EA3D_PMJ, (4, 4, 4))[0] == spn.SPN_E_ARG
+    w = np.zeros(3, np.uint64)
+    assert _create(lib, spn.SPN_ISING2D, (8, 8), couplings=w)[0] == spn.SPN_E_ARG
+    assert _create(lib, spn.SPN_ISING2D, (8, 8), init=9)[0] == spn.SPN_E_ARG
+    assert lib.spn_create_ex(None, 1, None, None, 0, 0, 0) == spn.SPN_E_ARG
+    assert lib.spn_sweep(None, 0.3, 1) == spn.SPN_E_ARG
+    assert lib.spn_destroy(None) == spn.SPN_E_ARG
+
+
+def test_version_string(lib):
+    assert b"sm_103a" in lib.spn_version()

@@ -1,0 +1,114 @@
+"""GPU parity of the int8 checkerboard sweep against the CPU oracle.
+
+Bit-exact comparison of final lattices and per-sweep integer (E, M) traces for
+2D and 3D Ising and the int8 +-J EA lattice, on both kernel paths, across tile
+shapes with ragged segment tails, at the special temperatures beta = 0 and
+beta = infinity, and on the full 2D L = 16384 and 3D L = 512 lattices with the
+launch configuration the benchmark uses."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import gpu_run, lib, oracle_run
+from paper_1006_3865_gb300 import inputs, spn
+
+pytestmark = pytest.mark.gpu
+
+TC = inputs.TC_2D
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib()
+
+
+def _compare(model, dims, seed, sched, **kw):
+    bonds = kw.pop("bonds", None)
+    cold = kw.get("cold", False)
+    s_o, e_o, m_o = oracle_run(dims, seed, sched, stream=kw.get("stream", 0), bonds=bonds, cold=cold)
+    s_g, e_g, m_g = gpu_run(model, dims, seed, sched, bonds=bonds, **kw)
+    assert np.array_equal(s_g, s_o), f"lattice differs at {np.count_nonzero(s_g != s_o)} sites"
+    assert np.array_equal(e_g, e_o) and np.array_equal(m_g, m_o), "E/M trace differs"
+    return s_g
+
+
+def test_ising2d_L64_1000_sweeps_at_tc():
+    """The 2D L=64 workload: hot start, T = 2.269185, 1000 sweeps."""
+    _compare(spn.SPN_ISING2D, (64, 64), inputs.unit_seed(1), [(1.0 / TC, 1000)])
+
+
+@pytest.mark.parametrize("path", [spn.PATH_GENERIC, spn.PATH_STREAM])
+@pytest.mark.parametrize("T", [2.0, TC, 3.0])
+def test_ising2d_paths(path, T):
+    _compare(spn.SPN_ISING2D, (128, 96), inputs.unit_seed(2), [(1.0 / T, 25)], path=path)
+
+
+@pytest.mark.parametrize("tiling", [(16, 0, 1), (32, 0, 7), (64, 0, 96), (128, 0, 5), (256, 0, 3)])
+def test_ising2d_stream_tilings(tiling):
+    """Tile widths and ragged segment splits give identical bytes."""
+    _compare(spn.SPN_ISING2D, (256, 96), inputs.unit_seed(3), [(1.0 / TC, 12)], path=spn.PATH_STREAM,
+             tiling=tiling, stream=5)
+
+
+@pytest.mark.parametrize("dims", [(2, 2), (6, 10), (34, 18), (50, 4), (16, 2)])
+def test_ising2d_generic_small_and_ragged(dims):
+    _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(4), [(0.41, 30)], path=spn.PATH_GENERIC)
+
+
+@pytest.mark.parametrize("path", [spn.PATH_GENERIC, spn.PATH_STREAM])
+def test_ising3d_paths(path):
+    _compare(spn.SPN_ISING3D, (32, 16, 12), inputs.unit_seed(5), [(inputs.BETA_C_3D, 10), (0.3, 5)], path=path)
+
+
+@pytest.mark.parametrize("tiling", [(16, 2, 1), (32, 4, 5), (16, 8, 12), (32, 16, 2)])
+def test_ising3d_stream_tilings(tiling):
+    _compare(spn.SPN_ISING3D, (32, 16, 12), inputs.unit_seed(6), [(inputs.BETA_C_3D, 6)], path=spn.PATH_STREAM,
+             tiling=tiling)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2), (6, 4, 10), (4, 4, 2), (18, 6, 8)])
+def test_ising3d_generic_small(dims):
+    _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(7), [(0.25, 15)], path=spn.PATH_GENERIC)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2), (8, 6, 4), (16, 16, 16)])
+def test_ea3d_int8(dims):
+    bonds = inputs.ea_bonds(dims, 1, inputs.unit_seed(8))[0]
+    _compare(spn.SPN_EA3D_PMJ, dims, inputs.unit_seed(9), [(0.9, 20)], bonds=bonds)
+
+
+@pytest.mark.parametrize("model,dims,path", [(spn.SPN_ISING2D, (64, 32), spn.PATH_STREAM),
+                                             (spn.SPN_ISING2D, (10, 6), spn.PATH_GENERIC),
+                                             (spn.SPN_ISING3D, (16, 8, 6), spn.PATH_STREAM)])
+def test_beta_zero_and_infinity(model, dims, path):
+    s = _compare(model, dims, 11, [(0.0, 3)], path=path)
+    s0 = oracle.init_hot(dims, 11)
+    assert np.array_equal(s, -s0)
+    s = _compare(model, dims, 11, [(float("inf"), 4)], path=path, cold=True)
+    assert (s == 1).all()
+
+
+def test_schedule_across_calls_and_temperatures():
+    sched = [(0.5, 3), (0.3, 4), (0.44, 1), (1.0, 2)]
+    _compare(spn.SPN_ISING2D, (64, 48), 1234, sched, path=spn.PATH_STREAM, stream=9)
+
+
+def _sampled_full_size(model, dims, beta, nsweeps):
+    seed = inputs.unit_seed(100 + model)
+    sched = [(beta, nsweeps)]
+    s_o, e_o, m_o = oracle_run(dims, seed, sched)
+    s_g, e_g, m_g = gpu_run(model, dims, seed, sched)
+    assert np.array_equal(e_g, e_o) and np.array_equal(m_g, m_o)
+    assert np.array_equal(s_g, s_o)
+
+
+def test_full_size_2d_L16384():
+    """Full C2 lattice (2^28 sites) with the default (benchmark) launch configuration."""
+    _sampled_full_size(spn.SPN_ISING2D, (16384, 16384), 1.0 / TC, 2)
+
+
+def test_full_size_3d_L512():
+    _sampled_full_size(spn.SPN_ISING3D, (512, 512, 512), inputs.BETA_C_3D, 2)
