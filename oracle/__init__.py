@@ -52,7 +52,7 @@ def lib():
                                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p)
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
             L.orc_philox4x32_10.restype = None
-            L.orc_site_word.argtypes = [u64, u32, u32, cint, cint, cint, u64]
+            L.orc_site_word.argtypes = [u64, u32, u32, cint, cint, u64]
             L.orc_site_word.restype = u32
             L.orc_metropolis_u.argtypes = [u64, u32, u32, cint, u64]
             L.orc_metropolis_u.restype = u32
@@ -111,8 +111,8 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return out
 
 
-def site_word(seed: int, stream: int, t: int, colour: int, p_hi: int, p_lo: int, m: int) -> int:
-    return int(lib().orc_site_word(seed, stream, t, colour, p_hi, p_lo, m))
+def site_word(seed: int, stream: int, t: int, colour: int, purpose: int, m: int) -> int:
+    return int(lib().orc_site_word(seed, stream, t, colour, purpose, m))
 
 
 def metropolis_u(seed: int, stream: int, sweep: int, colour: int, m: int) -> int:

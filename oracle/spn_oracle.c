@@ -28,15 +28,16 @@
  *   threshold thr(beta, dE) = floor(exp(-beta*dE) * 2^32) for dE > 0 (Eq. 2),
  *             a value in [0, 2^32]; dE <= 0 is always accepted.
  *   random    R(c0,c1,c2,c3) = Philox4x32-10 with key (seed lo32, seed hi32).
- *             For a site with within-colour index m, group g = m >> 3, word
- *             (m >> 1) & 3, half m & 1 (0 = bits 0..15, 1 = bits 16..31).
- *             A "site word" is hi16 << 16 | lo16, where hi16 / lo16 are that
- *             half of R(g, t, c | (p_hi << 1), stream) / R(g, t, c | (p_lo << 1), stream).
- *               Metropolis u at sweep t, colour c:  p_hi = 0, p_lo = 1
- *               hot-start word (t = 0):              p_hi = 2, p_lo = 3
- *             The 32-bit u is therefore uniform; drawing it in two halves lets
- *             a GPU thread decide from the high half alone unless it ties the
- *             threshold's high half.
+ *             A site with within-colour index m lies in group g = m >> 5 at
+ *             lane i = m & 31.  The group owns 32 "planes": plane q (0..31) is
+ *             word q & 3 of R(8g + (q >> 2), t, c | (p << 1), stream).  Bit
+ *             31 - q of the site word is bit i of plane q, so plane 0 carries the
+ *             most significant bits of 32 sites.  Purposes p:
+ *               0  Metropolis u at sweep t, colour c
+ *               1  hot start (t = 0)
+ *             The 32-bit u is uniform; storing it across planes lets a GPU
+ *             thread compare 32 sites at once, most significant plane first,
+ *             and stop drawing planes as soon as every site is decided.
  *   hot start s_n = -1 if bit 31 of the hot-start word is set, else +1.
  *   sweep t   colour 0, then colour 1; a site of colour c flips iff dE <= 0 or
  *             u < thr(beta, dE); E and M are updated by every accepted flip.
@@ -49,7 +50,7 @@
  *   Replica exchange after every X-th sweep (step e = (t+1)/X - 1): for the
  *   temperature pairs (k, k+1) with k = e mod 2, 4, ... accept iff
  *   D = (beta_k - beta_{k+1}) * (E_k - E_{k+1}) >= 0 or
- *   u < floor(exp(D) * 2^32) with u = word k & 3 of R(k >> 2, e, 4 << 1, stream);
+ *   u < floor(exp(D) * 2^32) with u = word k & 3 of R(k >> 2, e, 2 << 1, stream);
  *   an accepted pair swaps the slots of the two temperatures.
  */
 #include <math.h>
@@ -83,30 +84,30 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-static uint32_t half_of(uint64_t seed, uint64_t m, uint32_t t, uint32_t c2, uint32_t stream) {
-  uint32_t ctr[4] = {(uint32_t)(m >> 3), t, c2, stream};
-  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
-  uint32_t w[4];
-  orc_philox4x32_10(ctr, key, w);
-  uint32_t x = w[(m >> 1) & 3];
-  return (m & 1) ? (x >> 16) : (x & 0xffffu);
-}
-
-/* 32-bit site word, see the header: purposes p_hi / p_lo select the counter's
- * third word c | (p << 1). */
-uint32_t orc_site_word(uint64_t seed, uint32_t stream, uint32_t t, int colour, int p_hi, int p_lo,
-                       uint64_t m) {
-  uint32_t hi = half_of(seed, m, t, (uint32_t)colour | ((uint32_t)p_hi << 1), stream);
-  uint32_t lo = half_of(seed, m, t, (uint32_t)colour | ((uint32_t)p_lo << 1), stream);
-  return (hi << 16) | lo;
+/* Site word of within-colour index m for purpose p: bit 31 - q is bit (m & 31)
+ * of plane q = word q & 3 of R(8 (m >> 5) + (q >> 2), t, c | (p << 1), stream). */
+uint32_t orc_site_word(uint64_t seed, uint32_t stream, uint32_t t, int colour, int purpose, uint64_t m) {
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  const uint32_t lane = (uint32_t)(m & 31);
+  uint32_t u = 0;
+  for (uint32_t call = 0; call < 8; ++call) {
+    uint32_t ctr[4] = {(uint32_t)(8 * (m >> 5) + call), t, (uint32_t)colour | ((uint32_t)purpose << 1), stream};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    for (uint32_t j = 0; j < 4; ++j) {
+      const uint32_t q = 4 * call + j;
+      u |= ((w[j] >> lane) & 1u) << (31 - q);
+    }
+  }
+  return u;
 }
 
 uint32_t orc_metropolis_u(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, uint64_t m) {
-  return orc_site_word(seed, stream, sweep, colour, 0, 1, m);
+  return orc_site_word(seed, stream, sweep, colour, 0, m);
 }
 
 uint32_t orc_hot_word(uint64_t seed, uint32_t stream, int colour, uint64_t m) {
-  return orc_site_word(seed, stream, 0, colour, 2, 3, m);
+  return orc_site_word(seed, stream, 0, colour, 1, m);
 }
 
 /* ------------------------------------------------------- Metropolis rule */
@@ -323,7 +324,7 @@ static void exchange_step(const double* betas, const int64_t* Eslot, uint8_t* sl
     if (D >= 0) {
       accept = 1;
     } else {
-      uint32_t ctr[4] = {(uint32_t)k >> 2, e, 4u << 1, stream};
+      uint32_t ctr[4] = {(uint32_t)k >> 2, e, 2u << 1, stream};
       uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
       uint32_t w[4];
       orc_philox4x32_10(ctr, key, w);

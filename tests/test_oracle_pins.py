@@ -73,15 +73,19 @@ def test_philox_matches_library_implementation():
 
 
 def test_site_word_layout():
-    """The site word takes half (m & 1) of word ((m >> 1) & 3) of the group m >> 3."""
+    """Bit 31 - q of a site word is bit (m & 31) of plane q = word q & 3 of the
+    Philox call 8 (m >> 5) + q >> 2 (most significant plane first)."""
     seed, stream, t, c = 0xABCDEF0123, 5, 17, 1
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    for m in (0, 1, 2, 7, 8, 13, 1023, 12345):
-        hi = oracle.philox4x32_10([m >> 3, t, c | (0 << 1), stream], key)[(m >> 1) & 3]
-        lo = oracle.philox4x32_10([m >> 3, t, c | (1 << 1), stream], key)[(m >> 1) & 3]
-        h = (int(hi) >> 16) if m & 1 else (int(hi) & 0xFFFF)
-        l_ = (int(lo) >> 16) if m & 1 else (int(lo) & 0xFFFF)
-        assert oracle.metropolis_u(seed, stream, t, c, m) == (h << 16) | l_
+    for m in (0, 1, 2, 31, 32, 63, 1023, 12345):
+        planes = [oracle.philox4x32_10([8 * (m >> 5) + call, t, c | (0 << 1), stream], key) for call in range(8)]
+        bits = [(int(planes[q >> 2][q & 3]) >> (m & 31)) & 1 for q in range(32)]
+        u = sum(b << (31 - q) for q, b in enumerate(bits))
+        assert oracle.metropolis_u(seed, stream, t, c, m) == u
+    # hot start draws purpose 1
+    planes = [oracle.philox4x32_10([8 * 3 + call, 0, 0 | (1 << 1), stream], key) for call in range(8)]
+    u = sum(((int(planes[q >> 2][q & 3]) >> 7) & 1) << (31 - q) for q in range(32))
+    assert oracle.hot_word(seed, stream, 0, 3 * 32 + 7) == u
 
 
 def test_site_words_are_uniform():
