@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the checkerboard Metropolis sweep on GB300 (spin-flip attempts/ns).
+
+One step is the plain large-lattice workload, every part of the hot path:
+  * 2D Ising L = 16384 (2^28 int8 spins), for each T in {2.0, 2.269185, 3.0}:
+    Philox hot start + E/M reduction, then 200 sweeps (colour 0, colour 1);
+  * 3D Ising L = 512 (2^27 spins) at beta = 0.221654: hot start, 100 sweeps.
+Attempts per step: 3 * 200 * 2^28 + 100 * 2^27 = 1.745e11.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
+replica of the step on its GPU (the path does not shard: replicas only) and the
+value is the total attempts of all ranks over the slowest rank's time.
+
+  value        device-timed (CUDA events on the sweep stream), lattices resident.
+  e2e          the same work through the public API with the initial lattices
+               copied from pinned host memory and the final lattices and E/M
+               read back every step (wall clock, synchronised).
+  roofline     the 2D streaming sweep kernel: 2 algorithmic bytes per attempt
+               (one read, one write) over its average launch time, against the
+               measured HBM copy bandwidth.
+  cpu_baseline the CPU oracle (OpenMP, all host cores) on a bounded sample.
+  --impl reference  times the CPU oracle itself on a bounded sample per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/ns on 1 GB300 (plain vs batched/served); p99 request latency"
+UNIT = "attempts/ns"
+TEMPS_2D = (2.0, 2.269185, 3.0)
+L2D, SWEEPS_2D = 16384, 200
+L3D, SWEEPS_3D, BETA_3D = 512, 100, 0.221654
+ATTEMPTS_PER_STEP = len(TEMPS_2D) * SWEEPS_2D * L2D * L2D + SWEEPS_3D * L3D ** 3
+WORKLOAD = ("2D Ising L=16384 (hot start, T in {2.0, 2.269185, 3.0}, 200 sweeps each) + "
+            "3D Ising L=512 (hot start, beta=0.221654, 100 sweeps)")
+PROFILE_2D = os.path.join(ROOT, "profiles", "sweep_stream_2d_L16384.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1006_3865_gb300", "csrc", "ising.cu")
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-case", choices=["2d", "3d"], default=None,
+                   help="run only a few sweeps of one lattice (for ncu captures) and exit")
+    p.add_argument("--profile-sweeps", type=int, default=3)
+    return p.parse_args()
+
+
+def run_profile_case(a):
+    """A handful of sweep launches of one full-size lattice, nothing else."""
+    import torch
+
+    from paper_1006_3865_gb300 import build as spn_build
+    from paper_1006_3865_gb300 import inputs, spn
+
+    spn_build.build()
+    spn.load()
+    if a.profile_case == "2d":
+        lat = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(1))
+        beta = 1.0 / TEMPS_2D[1]
+    else:
+        lat = spn.Lattice(spn.SPN_ISING3D, (L3D, L3D, L3D), inputs.unit_seed(2))
+        beta = BETA_3D
+    lat.sweep(beta, a.profile_sweeps)
+    print("profile case", a.profile_case, "E, M =", lat.observables(), flush=True)
+    lat.close()
+    torch.cuda.synchronize()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _profile_traffic():
+    """Per-launch DRAM bytes of the 2D sweep kernel from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled."""
+    try:
+        text = open(PROFILE_2D).read()
+        sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text).group(1)
+        tb = float(re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text).group(1))
+    except Exception:
+        return None
+    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    return tb if cur == sha else None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch.distributed as dist
+
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dist.init_process_group("nccl" if os.environ.get("SPN_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return dist, rank, ws, local
+
+
+def _cpu_baseline(sweeps: int = 1):
+    """Oracle on a bounded sample: hot start + `sweeps` sweeps of the 2D L=16384
+    lattice at T_c and of the 3D L=512 lattice (all host cores)."""
+    import oracle
+
+    oracle.build()
+    att = 0
+    t0 = time.perf_counter()
+    s = oracle.init_hot((L2D, L2D), 1)
+    oracle.sweeps((L2D, L2D), s, 1.0 / TEMPS_2D[1], sweeps, 1)
+    att += sweeps * L2D * L2D
+    del s
+    s = oracle.init_hot((L3D, L3D, L3D), 2)
+    oracle.sweeps((L3D, L3D, L3D), s, BETA_3D, sweeps, 2)
+    att += sweeps * L3D ** 3
+    dt = time.perf_counter() - t0
+    return {"value": att / (dt * 1e9), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"hot start + {sweeps} sweep(s) of 2D L=16384 at T=2.269185 and of 3D L=512 at "
+                      f"beta=0.221654 ({att:.3g} attempts, {dt:.1f} s)"}
+
+
+def run_reference(a):
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    sample = 1
+    for _ in range(a.warmup):
+        _cpu_baseline(sample)
+    vals, secs, att = [], 0.0, 0
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        r = _cpu_baseline(sample)
+        secs += time.perf_counter() - t0
+        vals.append(r["value"])
+    step_att = sample * (L2D * L2D + L3D ** 3)
+    value = a.steps * step_att / (secs * 1e9)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_per_step": f"hot start + {sample} sweep of each lattice",
+                      "parallelism": f"replicas{ws}"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"hot start + {sample} sweep of 2D L=16384 and 3D L=512 per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = _args()
+    if a.profile_case:
+        run_profile_case(a)
+        return
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    if a.warmup < 3:
+        raise SystemExit("warmup must be >= 3")
+    dist, rank, ws, local = _dist()
+    import numpy as np
+    import torch
+
+    from paper_1006_3865_gb300 import build as spn_build
+    from paper_1006_3865_gb300 import inputs, spn
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    spn_build.build()
+    spn.load()
+    stream = torch.cuda.Stream()
+    seeds2 = [inputs.unit_seed(1000 * rank + i) for i in range(len(TEMPS_2D))]
+    seed3 = inputs.unit_seed(1000 * rank + 99)
+    lat2 = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), seeds2[0])
+    lat3 = spn.Lattice(spn.SPN_ISING3D, (L3D, L3D, L3D), seed3)
+    lat2.set_stream(stream)
+    lat3.set_stream(stream)
+
+    def step(evs=None):
+        for i, T in enumerate(TEMPS_2D):
+            lat2.reinit(seeds2[i])
+            if evs is not None:
+                evs[i][0].record(stream)
+            lat2.sweep(1.0 / T, SWEEPS_2D)
+            if evs is not None:
+                evs[i][1].record(stream)
+        lat3.reinit(seed3)
+        if evs is not None:
+            evs[3][0].record(stream)
+        lat3.sweep(BETA_3D, SWEEPS_3D)
+        if evs is not None:
+            evs[3][1].record(stream)
+        lat2.observables()
+        lat3.observables()
+
+    def barrier():
+        if dist is not None:
+            t = torch.zeros(1, device="cuda")
+            dist.all_reduce(t)
+        torch.cuda.synchronize()
+
+    for _ in range(a.warmup):
+        step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    kevs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(4)] for _ in range(a.steps)]
+    n0 = spn.launch_count()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(a.steps):
+        step(kevs[k])
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = spn.launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * a.steps * ATTEMPTS_PER_STEP / (ms * 1e6)
+    # dominant kernel: the 2D streaming sweep, SWEEPS_2D launches per block
+    blk = [kevs[k][i][0].elapsed_time(kevs[k][i][1]) for k in range(a.steps) for i in range(len(TEMPS_2D))]
+    launch_ms = statistics.mean(blk) / SWEEPS_2D
+    alg_bytes = 2.0 * L2D * L2D
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    blk3 = [kevs[k][3][0].elapsed_time(kevs[k][3][1]) for k in range(a.steps)]
+    launch3_ms = statistics.mean(blk3) / SWEEPS_3D
+
+    # end to end through the public API: pinned host lattices in, lattices + E/M out
+    e2e = None
+    if not a.no_e2e:
+        rng = np.random.Generator(np.random.PCG64(inputs.unit_seed(7 + rank)))
+        h_in2 = [torch.from_numpy(rng.choice(np.array([-1, 1], np.int8), size=L2D * L2D)).pin_memory()
+                 for _ in TEMPS_2D]
+        h_in3 = torch.from_numpy(rng.choice(np.array([-1, 1], np.int8), size=L3D ** 3)).pin_memory()
+        h_out2 = torch.empty(L2D * L2D, dtype=torch.int8).pin_memory()
+        h_out3 = torch.empty(L3D ** 3, dtype=torch.int8).pin_memory()
+
+        def e2e_step():
+            res = []
+            for i, T in enumerate(TEMPS_2D):
+                lat2.reinit(seeds2[i])
+                lat2.set_spins(h_in2[i].numpy())
+                lat2.sweep(1.0 / T, SWEEPS_2D)
+                lat2.get_spins(h_out2.numpy())
+                res.append(lat2.observables())
+            lat3.reinit(seed3)
+            lat3.set_spins(h_in3.numpy())
+            lat3.sweep(BETA_3D, SWEEPS_3D)
+            lat3.get_spins(h_out3.numpy())
+            res.append(lat3.observables())
+            return res
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            e2e_step()
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        nbytes = len(TEMPS_2D) * L2D * L2D + L3D ** 3
+        trace_bytes = 16 * (len(TEMPS_2D) * SWEEPS_2D + SWEEPS_3D)
+        e2e = {"value": ws * a.steps * ATTEMPTS_PER_STEP / (dt * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 4 * 16 + trace_bytes}
+
+    lat2.close()
+    lat3.close()
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        cpu = _cpu_baseline(1)
+    if rank != 0:
+        return
+    traffic = _profile_traffic()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "attempts_per_step": ATTEMPTS_PER_STEP,
+                   "l2": "inputs larger than L2 (ping-pong buffers 2 x 256 MiB and 2 x 128 MiB)",
+                   "parallelism": f"replicas{ws}", "launches_per_step": launches // a.steps,
+                   "sweep_ms_2d": launch_ms, "sweep_ms_3d": launch3_ms,
+                   "attempts_per_ns_2d": L2D * L2D / (launch_ms * 1e6),
+                   "attempts_per_ns_3d": L3D ** 3 / (launch3_ms * 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "k_sweep_stream<2> (2D L=16384)", "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

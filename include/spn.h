@@ -104,9 +104,16 @@ int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n);
 /* Copy the spins (int8 +-1, site order) into host_out; bytes must be N. */
 int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes);
 
-/* Replace the spins from a host buffer of N int8 +-1 values; E and M are
- * recomputed.  The sweep counter is kept. */
+/* Replace the spins from a host buffer of N int8 +-1 values (pinned memory
+ * makes the copy asynchronous-fast); E and M are recomputed on the device, which
+ * also rejects values other than +-1 with SPN_E_ARG.  The sweep counter is
+ * kept. */
 int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes);
+
+/* Start a new run on the same handle: re-initialise the spins (hot start from
+ * Philox with the given seed and stream, or cold), reset the sweep counter to
+ * 0 and clear the trace.  Device memory is reused (no allocation). */
+int spn_reinit(spn_handle h, uint64_t seed, uint32_t stream, int init);
 
 /* Number of sweeps done so far (the next sweep's counter). */
 int spn_sweep_count(spn_handle h, uint64_t* count);
@@ -121,15 +128,21 @@ int spn_sync(spn_handle h);
 /* Release the handle and its device memory (synchronises first). */
 int spn_destroy(spn_handle h);
 
-/* Tile configuration of the streaming sweep kernel for this handle
- * (tile_x: sites per tile row, multiple of 16; tile_y: rows per slice in 3D;
- * seg: slices per CTA, 0 = automatic).  Results never depend on it. */
-int spn_set_tiling(spn_handle h, int32_t tile_x, int32_t tile_y, int32_t seg);
+/* Geometry of the streaming sweep kernel for this handle: tile_y = rows per
+ * band in 3D (divides Ly; ignored in 2D), step_slices = slices (2D rows, 3D
+ * planes) advanced per pipeline step (0 = automatic), seg = number of segments
+ * the streamed axis is cut into, one CTA each per band (0 = automatic).  The
+ * results never depend on it.  SPN_E_ARG if it does not fit one CTA. */
+int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t seg);
 
 /* Which kernel path the handle uses: 0 = generic global-memory sweep,
  * 1 = streaming shared-memory sweep, 2 = shared-memory-resident sweep. */
 int spn_get_path(spn_handle h, int32_t* path);
 int spn_set_path(spn_handle h, int32_t path);
+
+/* Number of kernels this library has launched in the process so far (all
+ * handles); a diagnostic for benchmarks. */
+int spn_launch_count(uint64_t* count);
 
 #ifdef __cplusplus
 }

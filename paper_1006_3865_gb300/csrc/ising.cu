@@ -1,28 +1,35 @@
 // Checkerboard Metropolis kernels for int8 Ising-type lattices (Weigel, Sec. 3,
 // Eq. 1-2; Sec. 4 for 3D and +-J couplings).
 //
-//   k_init_hot        hot start from Philox (purpose "init").
+//   k_init_hot        hot start from Philox (purpose 1, most significant plane).
 //   k_observables     full reduction of E (Eq. 1) and M.
-//   k_sweep_generic   one colour of the sweep in place in global memory, one
-//                     thread per group of 8 same-colour sites; any even extents,
-//                     optional +-J bonds.  The reference order of updates
-//                     (colour 0 then colour 1) is realised by two launches.
-//   k_sweep_stream    both colours of one sweep in a single pass.  A CTA owns an
-//                     x-tile (3D: x-y tile) and a segment of slices along the
-//                     slowest axis (2D: rows, 3D: z planes).  Slices plus a
-//                     two-site halo stream into a ring of shared-memory buffers
-//                     with bulk asynchronous copies (cp.async.bulk completing on
-//                     an mbarrier).  Colour 0 is updated on the tile plus a
-//                     one-site ring (the ring repeats the neighbours' work with
-//                     the same counters, so it is bit-identical), colour 1 on the
-//                     tile; the result goes to the other ping-pong buffer.
+//   k_sweep_generic   one colour of a sweep in place in global memory; a thread
+//                     owns one group of 32 same-colour sites.  Any even extents,
+//                     optional +-J bonds.  Two launches per sweep realise the
+//                     order colour 0, then colour 1.
+//   k_sweep_stream    both colours of one sweep in one pass (Lx % 64 == 0, no
+//                     bonds).  A CTA owns full-width rows (3D: a band of rows)
+//                     and a segment of slices along the slowest axis (2D: rows,
+//                     3D: z planes).  Raw int8 slices stream into a ring of
+//                     shared-memory buffers through bulk asynchronous copies
+//                     (cp.async.bulk, completion on mbarriers); each slice is
+//                     converted once into colour-separated bit words, colour 0
+//                     is updated on the slices plus a one-slice / one-row ring
+//                     (repeating a neighbour's work with the same counters, so
+//                     it is bit-identical), colour 1 on the owned part, and the
+//                     result is expanded back to int8 into the other buffer.
 //
-// Spins are int8 +-1 (0x01 / 0xFF).  Bit 1 of a byte is set iff the spin is -1,
-// so (a ^ b) & 0x02 marks an anti-aligned pair; four bytes are handled per
-// 32-bit operation.
+// Bit-sliced Metropolis: bit i of a 32-bit word is one site (1 = spin -1).
+// The anti-aligned neighbours of 32 sites are counted with a handful of logic
+// operations; every site then belongs to one class q = dE/4 and is accepted iff
+// dE <= 0 or u < thr(q).  The 32-bit u of a site is stored across 32 Philox
+// planes, most significant first (bit 31 - p of u = lane bit of plane p), so the
+// comparison of all 32 sites runs plane by plane and stops as soon as every
+// site is decided; planes are drawn four at a time (one Philox call).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -38,17 +45,25 @@ uint64_t boltzmann_threshold(double beta, int dE) {
   return (uint64_t)std::floor(x);
 }
 
-ThrTab make_thresholds(double beta) {
-  ThrTab T{};
-  T.hi[0] = 0x10000u;
-  T.lo[0] = 0;
+DevThr make_thresholds(double beta) {
+  DevThr T{};
   for (int q = 1; q < 4; ++q) {
-    uint64_t t = boltzmann_threshold(beta, 4 * q);
-    T.hi[q] = (uint32_t)(t >> 16);
-    T.lo[q] = (uint32_t)(t & 0xffffu);
+    const uint64_t t = boltzmann_threshold(beta, 4 * q);
+    if (t >= ((uint64_t)1 << 32)) {
+      T.always |= 1u << q;
+      T.t[q] = 0xffffffffu;
+    } else {
+      T.t[q] = (uint32_t)t;
+    }
   }
   return T;
 }
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int device_sm_count() {
   static int sms = 0;
@@ -63,21 +78,6 @@ int device_sm_count() {
 
 // ------------------------------------------------------------------ helpers
 
-// 16-bit high half of the Metropolis u of within-colour index m, from the
-// group's Philox output.
-__device__ __forceinline__ uint32_t half16(const U4& P, uint32_t i) {
-  const uint32_t w = u4_word(P, (int)(i >> 1));
-  return (i & 1) ? (w >> 16) : (w & 0xffffu);
-}
-
-// Selected 17-bit high threshold for class idx = dE/4 (idx <= 0: always).
-__device__ __forceinline__ uint32_t thr_hi(int idx, const ThrTab& T) {
-  return idx <= 0 ? 0x10000u : (idx == 1 ? T.hi[1] : (idx == 2 ? T.hi[2] : T.hi[3]));
-}
-__device__ __forceinline__ uint32_t thr_lo(int idx, const ThrTab& T) {
-  return idx == 1 ? T.lo[1] : (idx == 2 ? T.lo[2] : T.lo[3]);
-}
-
 __device__ __forceinline__ void warp_reduce_add2(long long& a, long long& b) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -86,7 +86,7 @@ __device__ __forceinline__ void warp_reduce_add2(long long& a, long long& b) {
   }
 }
 
-// Block-wide sum of (a, b), one atomic per warp.
+// Block-wide sum of (a, b), one atomic pair per warp.
 __device__ __forceinline__ void block_accumulate(long long a, long long b, unsigned long long* out2) {
   warp_reduce_add2(a, b);
   if ((threadIdx.x & 31) == 0 && (a | b)) {
@@ -95,9 +95,9 @@ __device__ __forceinline__ void block_accumulate(long long a, long long b, unsig
   }
 }
 
+// Site of colour c with within-colour index m: n = 2m or 2m + 1 (Lx even, so
+// both share y and z).
 __device__ __forceinline__ int64_t site_of(int64_t m, int c, int Lx, int Ly) {
-  // Site of colour c with within-colour index m: n = 2m or 2m + 1 (Lx even,
-  // so both share x >> 1, y and z).
   const int64_t n0 = 2 * m;
   const int64_t r = n0 / Lx;  // y + Ly * z
   const int y = (int)(r % Ly);
@@ -105,20 +105,208 @@ __device__ __forceinline__ int64_t site_of(int64_t m, int c, int Lx, int Ly) {
   return n0 + ((c ^ (y + z)) & 1);
 }
 
+// Metropolis decision for 32 sites.  cls[q-1]: sites whose move has dE = 4q > 0;
+// acc: sites already accepted (dE <= 0).  Plane p of the group (counter c0 + p/4)
+// holds bit 31 - p of every site's u; a site of class q is accepted iff
+// u < T.t[q] (or T.always has bit q).  Planes are compared from the most
+// significant down until no site is undecided anywhere in the warp.  Must be
+// called by all 32 lanes of a warp together.
+template <int NC>
+__device__ __forceinline__ uint32_t lazy_accept(uint32_t acc, const uint32_t (&cls)[NC], const DevThr& T,
+                                                const PhiloxKeys& K, uint32_t c0, uint32_t sweep, uint32_t c2,
+                                                uint32_t stream_id) {
+  uint32_t eq[NC];
+  uint32_t pend = 0;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const bool always = (T.always >> (q + 1)) & 1u;
+    acc |= always ? cls[q] : 0u;
+    eq[q] = always ? 0u : cls[q];
+    pend |= eq[q];
+  }
+#pragma unroll 1
+  for (uint32_t call = 0; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
+    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
+    const uint32_t planes[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = planes[j];
+      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        if ((T.t[q + 1] >> bit) & 1u) {  // threshold bit 1: a 0 bit of u decides "below"
+          acc |= eq[q] & ~u;
+          eq[q] &= u;
+        } else {
+          eq[q] &= ~u;
+        }
+      }
+    }
+    pend = 0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pend |= eq[q];
+  }
+  return acc;
+}
+
+// First stage of the decision: planes 0..7 (two Philox calls, drawn together)
+// for every word.  On return acc holds the sites already accepted and eq[q]
+// the sites of class q+1 whose u still ties the threshold on all 8 planes.
+template <int NC>
+__device__ __forceinline__ void decide_first(uint32_t& acc, uint32_t (&eq)[NC], const uint32_t (&cls)[NC],
+                                             const DevThr& T, const PhiloxKeys& K, uint32_t c0, uint32_t sweep,
+                                             uint32_t c2, uint32_t stream_id) {
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const bool always = (T.always >> (q + 1)) & 1u;
+    acc |= always ? cls[q] : 0u;
+    eq[q] = always ? 0u : cls[q];
+  }
+  const U4 P0 = philox10(c0, sweep, c2, stream_id, K);
+  const U4 P1 = philox10(c0 + 1u, sweep, c2, stream_id, K);
+  const uint32_t planes[8] = {P0.x, P0.y, P0.z, P0.w, P1.x, P1.y, P1.z, P1.w};
+  // Compare the top 8 bits of u with those of the threshold, least significant
+  // plane first: "below" after plane p is maj(~u_p, t_p, below so far); "equal"
+  // keeps the sites whose bits all match.
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    uint32_t below = 0, equal = 0xffffffffu;
+#pragma unroll
+    for (int p = 7; p >= 0; --p) {
+      const uint32_t tm = 0u - ((T.t[q + 1] >> (31 - p)) & 1u);
+      const uint32_t nu = ~planes[p];
+      below = (nu & tm) | (nu & below) | (tm & below);
+      equal &= ~(planes[p] ^ tm);
+    }
+    acc |= eq[q] & below;
+    eq[q] &= equal;
+  }
+}
+
+// Remaining planes 8..31 for sites still tied after the first stage; returns
+// the sites among eq that are accepted.  Called by whole warps (votes).
+template <int NC>
+__device__ __forceinline__ uint32_t decide_tail(uint32_t (&eq)[NC], const DevThr& T, const PhiloxKeys& K,
+                                               uint32_t c0, uint32_t sweep, uint32_t c2, uint32_t stream_id) {
+  uint32_t acc = 0, pend = 0;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) pend |= eq[q];
+#pragma unroll 1
+  for (uint32_t call = 2; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
+    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
+    const uint32_t planes[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = planes[j];
+      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        if ((T.t[q + 1] >> bit) & 1u) {
+          acc |= eq[q] & ~u;
+          eq[q] &= u;
+        } else {
+          eq[q] &= ~u;
+        }
+      }
+    }
+    pend = 0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pend |= eq[q];
+  }
+  return acc;
+}
+
+// Classes of one 32-site word from the anti-aligned counts k = s0 + 2 s1 + 4 s2
+// out of 2*ND neighbours: cls[q-1] = sites with dE = 4q > 0; returns the sites
+// with dE <= 0 (always accepted).
+template <int ND>
+__device__ __forceinline__ uint32_t classes(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t valid,
+                                            uint32_t (&cls)[ND]) {
+  if constexpr (ND == 2) {
+    const uint32_t hi = s1 | s2;  // k >= 2
+    cls[0] = s0 & ~hi & valid;    // k = 1, dE = 4
+    cls[1] = ~s0 & ~hi & valid;   // k = 0, dE = 8
+    return hi & valid;
+  } else {
+    cls[0] = ~s0 & s1 & ~s2 & valid;  // k = 2, dE = 4
+    cls[1] = s0 & ~s1 & ~s2 & valid;  // k = 1, dE = 8
+    cls[2] = ~s0 & ~s1 & ~s2 & valid;  // k = 0, dE = 12
+    return (s2 | (s0 & s1)) & valid;   // k >= 3
+  }
+}
+
+// dE = sum 4 (ND - k) and dM = sum -2 s over the accepted sites of a word.
+template <int ND>
+__device__ __forceinline__ void tally(uint32_t acc, uint32_t b, uint32_t s0, uint32_t s1, uint32_t s2, int& de,
+                                      int& dm) {
+  const int nf = __popc(acc);
+  de += 4 * (ND * nf - (__popc(acc & s0) + 2 * __popc(acc & s1) + 4 * __popc(acc & s2)));
+  dm += 2 * (2 * __popc(acc & b) - nf);
+}
+
+// Bit-sliced count of anti-aligned neighbours: inputs are the neighbour words
+// XOR-ed with the centre (1 = anti-aligned); output k = s0 + 2 s1 + 4 s2.
+__device__ __forceinline__ void count4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t& s0, uint32_t& s1,
+                                       uint32_t& s2) {
+  const uint32_t h1 = a ^ b, c1 = a & b, h2 = c ^ d, c2 = c & d;
+  const uint32_t c3 = h1 & h2;
+  s0 = h1 ^ h2;
+  s1 = c1 ^ c2 ^ c3;
+  s2 = c1 & c2;
+}
+
+__device__ __forceinline__ void count6(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e, uint32_t f,
+                                       uint32_t& s0, uint32_t& s1, uint32_t& s2) {
+  const uint32_t x1 = a ^ b ^ c, y1 = (a & b) | (c & (a ^ b));
+  const uint32_t x2 = d ^ e ^ f, y2 = (d & e) | (f & (d ^ e));
+  s0 = x1 ^ x2;
+  const uint32_t cc = x1 & x2;
+  s1 = y1 ^ y2 ^ cc;
+  s2 = (y1 & y2) | (cc & (y1 ^ y2));
+}
+
+// Classes and decision for one 32-site word: b = spin bits, k = (s0, s1, s2)
+// anti-aligned counts out of 2*ND neighbours, valid = sites present.  Returns
+// the accepted sites; adds dE = sum 4 (ND - k) and dM = sum -2 s of the flips.
+template <int ND>
+__device__ __forceinline__ uint32_t decide_word(uint32_t b, uint32_t s0, uint32_t s1, uint32_t s2, uint32_t valid,
+                                                const DevThr& T, const PhiloxKeys& K, uint32_t c0, uint32_t sweep,
+                                                uint32_t c2, uint32_t stream_id, int& de, int& dm) {
+  uint32_t acc, cls[ND];
+  if constexpr (ND == 2) {
+    // k = 0 -> dE = 8 (class 2), k = 1 -> dE = 4 (class 1), k >= 2 -> dE <= 0
+    const uint32_t hi = s1 | s2;
+    cls[0] = s0 & ~hi & valid;
+    cls[1] = ~s0 & ~hi & valid;
+    acc = hi & valid;
+  } else {
+    // k = 0 -> class 3, 1 -> class 2, 2 -> class 1, k >= 3 -> dE <= 0
+    cls[0] = ~s0 & s1 & ~s2 & valid;
+    cls[1] = s0 & ~s1 & ~s2 & valid;
+    cls[2] = ~s0 & ~s1 & ~s2 & valid;
+    acc = (s2 | (s0 & s1)) & valid;
+  }
+  acc = lazy_accept<ND>(acc, cls, T, K, c0, sweep, c2, stream_id);
+  const int nf = __popc(acc);
+  de += 4 * (ND * nf - (__popc(acc & s0) + 2 * __popc(acc & s1) + 4 * __popc(acc & s2)));
+  dm += 2 * (2 * __popc(acc & b) - nf);
+  return acc;
+}
+
 // ---------------------------------------------------------------- init / E, M
 
 __global__ void k_init_hot(int8_t* __restrict__ s, int Lx, int Ly, int64_t N, PhiloxKeys K, uint32_t stream_id) {
   const int64_t half = N >> 1;
-  const int64_t ngroups = (half + 7) >> 3;
+  const int64_t ngroups = (half + 31) >> 5;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 2 * ngroups;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(t & 1);
-    const int64_t gidx = t >> 1;
-    const U4 P = philox10((uint32_t)gidx, 0u, (uint32_t)c | (kInitHi << 1), stream_id, K);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int64_t m = gidx * 8 + i;
-      if (m < half) s[site_of(m, c, Lx, Ly)] = (half16(P, i) >> 15) ? (int8_t)-1 : (int8_t)1;
+    const int64_t g = t >> 1;
+    const uint32_t plane0 = philox10((uint32_t)(8 * g), 0u, (uint32_t)c | (kInit << 1), stream_id, K).x;
+    for (int i = 0; i < 32; ++i) {
+      const int64_t m = g * 32 + i;
+      if (m >= half) break;
+      s[site_of(m, c, Lx, Ly)] = ((plane0 >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
     }
   }
 }
@@ -128,14 +316,16 @@ __device__ __forceinline__ int bond_sign(const uint8_t* __restrict__ bonds, int6
 }
 
 __global__ void k_observables(const int8_t* __restrict__ s, const uint8_t* __restrict__ bonds, int nd, int Lx,
-                              int Ly, int Lz, int64_t N, unsigned long long* out2) {
+                              int Ly, int Lz, int64_t N, unsigned long long* out2, int* bad) {
   long long e = 0, m = 0;
+  int invalid = 0;
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(n % Lx);
     const int64_t r = n / Lx;
     const int y = (int)(r % Ly);
     const int z = (int)(r / Ly);
     const int sn = s[n];
+    invalid |= (sn != 1 && sn != -1);
     m += sn;
     const int64_t nx = n - x + (x + 1 == Lx ? 0 : x + 1);
     const int64_t ny = n + (int64_t)((y + 1 == Ly ? 0 : y + 1) - y) * Lx;
@@ -146,97 +336,97 @@ __global__ void k_observables(const int8_t* __restrict__ s, const uint8_t* __res
       e -= (long long)bond_sign(bonds, n, 2) * sn * s[nz];
     }
   }
+  if (invalid && bad) atomicExch(bad, 1);
   block_accumulate(e, m, out2);
 }
 
 cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t stream_id, cudaStream_t st) {
-  const int64_t work = 2 * (((g.N >> 1) + 7) >> 3);
+  const int64_t work = 2 * (((g.N >> 1) + 31) >> 5);
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((work + threads - 1) / threads, (int64_t)device_sm_count() * 32);
   k_init_hot<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(s, g.Lx, g.Ly, g.N, philox_keys(seed),
                                                                          stream_id);
+  count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long long* out2, cudaStream_t st) {
+cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long long* out2, int* bad,
+                               cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((g.N + threads - 1) / threads, (int64_t)device_sm_count() * 16);
   k_observables<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(s, g.bonds, g.nd, g.Lx, g.Ly, g.Lz,
-                                                                           g.N, out2);
+                                                                           g.N, out2, bad);
+  count_launches(1);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ generic sweep
 
-// One colour c of sweep `sweep`, in place: a thread decides the 8 sites of one
-// Philox group (within-colour indices 8g .. 8g+7).
+// One colour c of sweep `sweep`, in place: a thread owns the group of 32 sites
+// with within-colour indices 32 g .. 32 g + 31.
 template <int ND>
 __global__ void k_sweep_generic(int8_t* __restrict__ s, const uint8_t* __restrict__ bonds, int Lx, int Ly, int Lz,
-                                int64_t N, int c, ThrTab T, PhiloxKeys K, uint32_t stream_id, uint32_t sweep,
+                                int64_t N, int c, DevThr T, PhiloxKeys K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc) {
   const int64_t half = N >> 1;
-  const int64_t ngroups = (half + 7) >> 3;
-  long long de = 0, dm = 0;
-  for (int64_t gidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gidx < ngroups;
-       gidx += (int64_t)gridDim.x * blockDim.x) {
-    const U4 P = philox10((uint32_t)gidx, sweep, (uint32_t)c | (kMetroHi << 1), stream_id, K);
-    bool have_lo = false;
-    U4 Q{0, 0, 0, 0};
-#pragma unroll 1
-    for (int i = 0; i < 8; ++i) {
-      const int64_t m = gidx * 8 + i;
-      if (m >= half) break;
-      const int64_t n = site_of(m, c, Lx, Ly);
-      const int x = (int)(n % Lx);
-      const int64_t r = n / Lx;
-      const int y = (int)(r % Ly);
-      const int z = (int)(r / Ly);
-      const int sn = s[n];
-      const int64_t xm = n - x + (x == 0 ? Lx - 1 : x - 1), xp = n - x + (x + 1 == Lx ? 0 : x + 1);
-      const int64_t ym = n + (int64_t)((y == 0 ? Ly - 1 : y - 1) - y) * Lx;
-      const int64_t yp = n + (int64_t)((y + 1 == Ly ? 0 : y + 1) - y) * Lx;
-      int h = bond_sign(bonds, n, 0) * s[xp] + bond_sign(bonds, xm, 0) * s[xm] + bond_sign(bonds, n, 1) * s[yp] +
-              bond_sign(bonds, ym, 1) * s[ym];
-      if (ND == 3) {
-        const int64_t LxLy = (int64_t)Lx * Ly;
-        const int64_t zm = n + (int64_t)((z == 0 ? Lz - 1 : z - 1) - z) * LxLy;
-        const int64_t zp = n + (int64_t)((z + 1 == Lz ? 0 : z + 1) - z) * LxLy;
-        h += bond_sign(bonds, n, 2) * s[zp] + bond_sign(bonds, zm, 2) * s[zm];
-      }
-      const int dE = 2 * sn * h;
-      const int idx = dE / 4;
-      bool accept;
-      if (idx <= 0) {
-        accept = true;
-      } else {
-        const uint32_t uh = half16(P, (uint32_t)i);
-        const uint32_t th = thr_hi(idx, T);
-        if (uh != th) {
-          accept = uh < th;
-        } else {
-          if (!have_lo) {
-            Q = philox10((uint32_t)gidx, sweep, (uint32_t)c | (kMetroLo << 1), stream_id, K);
-            have_lo = true;
-          }
-          accept = half16(Q, (uint32_t)i) < thr_lo(idx, T);
+  const int64_t ngroups = (half + 31) >> 5;
+  int de = 0, dm = 0;
+  // warp-uniform trip count: the decision votes across the warp
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31);
+  for (int64_t g0 = base; g0 < ngroups; g0 += stride) {
+    const int64_t g = g0 + (threadIdx.x & 31);
+    uint32_t bits = 0, s0 = 0, s1 = 0, s2 = 0, valid = 0;
+    if (g < ngroups) {
+      for (int i = 0; i < 32; ++i) {
+        const int64_t m = g * 32 + i;
+        if (m >= half) break;
+        const int64_t n = site_of(m, c, Lx, Ly);
+        const int x = (int)(n % Lx);
+        const int64_t r = n / Lx;
+        const int y = (int)(r % Ly);
+        const int z = (int)(r / Ly);
+        const int sn = s[n];
+        const int64_t xm = n - x + (x == 0 ? Lx - 1 : x - 1), xp = n - x + (x + 1 == Lx ? 0 : x + 1);
+        const int64_t ym = n + (int64_t)((y == 0 ? Ly - 1 : y - 1) - y) * Lx;
+        const int64_t yp = n + (int64_t)((y + 1 == Ly ? 0 : y + 1) - y) * Lx;
+        int h = bond_sign(bonds, n, 0) * s[xp] + bond_sign(bonds, xm, 0) * s[xm] +
+                bond_sign(bonds, n, 1) * s[yp] + bond_sign(bonds, ym, 1) * s[ym];
+        if (ND == 3) {
+          const int64_t LxLy = (int64_t)Lx * Ly;
+          const int64_t zm = n + (int64_t)((z == 0 ? Lz - 1 : z - 1) - z) * LxLy;
+          const int64_t zp = n + (int64_t)((z + 1 == Lz ? 0 : z + 1) - z) * LxLy;
+          h += bond_sign(bonds, n, 2) * s[zp] + bond_sign(bonds, zm, 2) * s[zm];
         }
+        const int k = (2 * ND - sn * h) / 2;  // anti-aligned (unsatisfied) bonds
+        const uint32_t bit = 1u << i;
+        valid |= bit;
+        bits |= sn < 0 ? bit : 0u;
+        s0 |= (k & 1) ? bit : 0u;
+        s1 |= (k & 2) ? bit : 0u;
+        s2 |= (k & 4) ? bit : 0u;
       }
-      if (accept) {
-        s[n] = (int8_t)(-sn);
-        de += dE;
-        dm -= 2 * sn;
+    }
+    const uint32_t flips = decide_word<ND>(bits, s0, s1, s2, valid, T, K, (uint32_t)(8 * g), sweep,
+                                           (uint32_t)c | (kMetropolis << 1), stream_id, de, dm);
+    if (flips) {
+      for (int i = 0; i < 32; ++i) {
+        if ((flips >> i) & 1u) {
+          const int64_t n = site_of(g * 32 + i, c, Lx, Ly);
+          s[n] = (int8_t)(-s[n]);
+        }
       }
     }
   }
   block_accumulate(de, dm, acc);
 }
 
-cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const ThrTab& T, const PhiloxKeys& K,
+cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, const PhiloxKeys& K,
                                  uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st) {
-  const int64_t ngroups = ((g.N >> 1) + 7) >> 3;
-  const int threads = 256;
+  const int64_t ngroups = ((g.N >> 1) + 31) >> 5;
+  const int threads = 128;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ngroups + threads - 1) / threads,
                                                                 (int64_t)device_sm_count() * 16));
   for (int c = 0; c < 2; ++c) {
@@ -247,6 +437,7 @@ cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const ThrTab& T, c
       k_sweep_generic<2><<<(unsigned)blocks, threads, 0, st>>>(s, g.bonds, g.Lx, g.Ly, g.Lz, g.N, c, T, K,
                                                                stream_id, sweep, acc);
   }
+  count_launches(2);
   return cudaGetLastError();
 }
 
@@ -254,14 +445,9 @@ cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const ThrTab& T, c
 
 namespace {
 
-constexpr int kNbuf = 6;             // slice buffers in the ring (prefetch distance 2)
-constexpr int kMaxA = 2;             // colour-0 chunks a thread holds between barriers
-constexpr uint32_t kAnti = 0x02020202u;
 constexpr unsigned kWaitLimit = 1u << 22;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -284,8 +470,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bulk asynchronous copy global -> shared (the TMA engine, non-tensor form);
-// both addresses 16-byte aligned and bytes a multiple of 16.
+// Bulk asynchronous copy global -> shared (TMA engine, non-tensor form); both
+// addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -295,370 +481,490 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Four int8 spins (0x01 / 0xFF) -> four bits (1 = -1) at bits 0..3 in byte
+// order: bit 1 of byte k moves to bit 28 + k in one multiply (no carries).
+__device__ __forceinline__ uint32_t sign_bits4(uint32_t w) { return ((w & 0x02020202u) * 0x08102040u) >> 28; }
 
 struct StreamArgs {
   const int8_t* in;
   int8_t* out;
   int Lx, Ly, Lz;
-  int TX, TY;  // TY = 1 in 2D
-  int nseg;
+  int TY;      // rows per band (3D); 1 in 2D
+  int R;       // slices per step
+  int nseg;    // segments along the streamed axis
   int S;       // slices along the streamed axis (2D: Ly, 3D: Lz)
+  int nraw;    // raw slice buffers
+  int nbit;    // bit slice buffers
   uint32_t sweep, stream_id;
   PhiloxKeys K;
-  ThrTab T;
+  DevThr T;
   unsigned long long* acc;
   int* err;
 };
 
-// Metropolis update of the colour-c sites of one 16-byte chunk.  C: the chunk,
-// V: NV vertical neighbour chunks, lb / rb: the bytes left / right of the
-// chunk, par: byte parity of the colour-c sites, P: Philox high-half output of
-// the chunk's group.  Returns the new chunk; adds dE, dM of accepted moves.
-template <int NV>
-__device__ __forceinline__ uint4 chunk_update(uint4 C, const uint4 (&V)[NV], uint32_t lb, uint32_t rb, int par,
-                                              const U4& P, uint32_t gidx, uint32_t c, const StreamArgs& a,
-                                              int& de, int& dm) {
-  constexpr int ND = NV / 2 + 1;
-  const uint32_t w[4] = {C.x, C.y, C.z, C.w};
-  uint32_t kx[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t lw = __funnelshift_l(j == 0 ? (lb << 24) : w[j - 1], w[j], 8);
-    const uint32_t rw = __funnelshift_r(w[j], j == 3 ? rb : w[j + 1], 8);
-    uint32_t x = ((w[j] ^ lw) & kAnti) + ((w[j] ^ rw) & kAnti);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const uint32_t vw = j == 0 ? V[v].x : j == 1 ? V[v].y : j == 2 ? V[v].z : V[v].w;
-      x += (w[j] ^ vw) & kAnti;
-    }
-    kx[j] = x;  // byte b holds 2 * (number of anti-aligned neighbours of site b)
-  }
-  uint32_t F[4] = {0, 0, 0, 0};
-  uint32_t ties = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int j = i >> 1;
-    const int b = par + 2 * (i & 1);
-    const int k = (int)((kx[j] >> (8 * b + 1)) & 0xfu);
-    const int idx = ND - k;  // dE / 4
-    const uint32_t uh = half16(P, (uint32_t)i);
-    const uint32_t th = thr_hi(idx, a.T);
-    const bool acc = uh < th;
-    ties |= (uh == th) ? (1u << i) : 0u;
-    if (acc) {
-      F[j] |= 0xfeu << (8 * b);
-      de += 4 * idx;
-      dm += ((w[j] >> (8 * b)) & 0x2u) ? 2 : -2;
-    }
-  }
-  if (ties) {  // rare (probability ~2^-16 per site): draw the low halves
-    const U4 Q = philox10(gidx, a.sweep, c | (kMetroLo << 1), a.stream_id, a.K);
-#pragma unroll 1
-    for (int i = 0; i < 8; ++i) {
-      if (!((ties >> i) & 1)) continue;
-      const int j = i >> 1;
-      const int b = par + 2 * (i & 1);
-      const int k = (int)((kx[j] >> (8 * b + 1)) & 0xfu);
-      const int idx = ND - k;
-      if (half16(Q, (uint32_t)i) < thr_lo(idx, a.T)) {
-        F[j] |= 0xfeu << (8 * b);
-        de += 4 * idx;
-        dm += ((w[j] >> (8 * b)) & 0x2u) ? 2 : -2;
-      }
-    }
-  }
-  return make_uint4(w[0] ^ F[0], w[1] ^ F[1], w[2] ^ F[2], w[3] ^ F[3]);
-}
+constexpr int kRounds = 2;  // items of one kind a thread handles per step
 
-__device__ __forceinline__ uint4 lds16(const uint8_t* p) { return *reinterpret_cast<const uint4*>(p); }
+#ifndef SPN_STREAM_MIN_BLOCKS
+#define SPN_STREAM_MIN_BLOCKS 2  // resident CTAs the register allocation aims for (512 threads each)
+#endif
 
-// Vertical neighbours of the chunk at p: the same chunk in the previous and
-// next slice (pm, pp) and, in 3D, in the rows above and below (p -+ RS).
-template <int ND>
-__device__ __forceinline__ void load_vertical(uint4 (&V)[ND == 3 ? 4 : 2], const uint8_t* p, const uint8_t* pm,
-                                              const uint8_t* pp, int RS) {
-  if constexpr (ND == 3) {
-    V[0] = lds16(p - RS);
-    V[1] = lds16(p + RS);
-    V[2] = lds16(pm);
-    V[3] = lds16(pp);
-  } else {
-    V[0] = lds16(pm);
-    V[1] = lds16(pp);
-  }
+// A thread's item of one kind (conversion span, colour-0 word, colour-1 word)
+// within a step: slice k (0 .. R-1), band row r, word j; fixed for the launch.
+struct Item {
+  int k, r, j;
+  bool live;
+};
+
+__device__ __forceinline__ Item item_of(int it, int per, int W, int n, int rowoff) {
+  Item x;
+  x.live = it < n;
+  const int itc = x.live ? it : 0;
+  x.k = itc / per;
+  const int rem = itc - x.k * per;
+  x.r = rem / W + rowoff;
+  x.j = rem - (rem / W) * W;
+  return x;
 }
 
 template <int ND>
-__global__ void __launch_bounds__(512) k_sweep_stream(StreamArgs a) {
+__global__ void __launch_bounds__(512, SPN_STREAM_MIN_BLOCKS) k_sweep_stream(StreamArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr int YH = (ND == 3) ? 2 : 0;       // y-halo rows on each side
-  const int RS = a.TX + 32;                  // bytes per buffered row
-  const int R = (ND == 3) ? a.TY + 4 : 1;    // rows per slice buffer
-  const int SB = ((R * RS) + 127) & ~127;    // bytes per slice buffer
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kNbuf * SB);
+  constexpr int YH = (ND == 3) ? 2 : 0;
+  const int Lx = a.Lx;
+  const int W = Lx >> 6;                     // words per parity per row
+  const int RSL = (ND == 3) ? a.TY + 4 : 1;  // rows per slice
+  const int rowsA = (ND == 3) ? a.TY + 2 : 1;
+  const int rowsB = (ND == 3) ? a.TY : 1;
+  const int rawBytes = RSL * Lx;
+  const int rawStride = (rawBytes + 127) & ~127;
+  const int bitWords = RSL * 2 * W;  // bit slice: E then O words per row
+  uint8_t* raw = smem;
+  uint32_t* bitbuf = reinterpret_cast<uint32_t*>(smem + (size_t)a.nraw * rawStride);
+  uint2* lut = reinterpret_cast<uint2*>(bitbuf + (size_t)a.nbit * bitWords);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256);
+  const int qcap = kRounds * blockDim.x;                               // one entry per item at most
+  uint4* qe = reinterpret_cast<uint4*>(smem + (((size_t)a.nraw * rawStride + (size_t)a.nbit * bitWords * 4 +
+                                                 256 * 8 + (size_t)a.nraw * 8 + 15) & ~(size_t)15));
+  int* qslot_of = reinterpret_cast<int*>(qe + qcap);
+  uint32_t* late = reinterpret_cast<uint32_t*>(qslot_of + qcap);
   __shared__ int s_abort;
+  __shared__ int s_qcount;
+  int* qcount = &s_qcount;
 
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int x0 = blockIdx.x * a.TX;
-  const int y0 = (ND == 3) ? blockIdx.y * a.TY : 0;
-  const int seg = blockIdx.z;
+  const int lane = tid & 31;
+  const int y0 = (ND == 3) ? blockIdx.x * a.TY : 0;
+  const int seg = blockIdx.y;
   const int zs = (int)(((int64_t)seg * a.S) / a.nseg);
   const int ze = (int)(((int64_t)(seg + 1) * a.S) / a.nseg);
   const int H = ze - zs;
-  const int nload = H + 4;                   // slices zs-2 .. ze+1
-  const int nck = a.TX >> 4;                 // chunks per row
-  const int64_t sliceStride = (int64_t)a.Lx * ((ND == 3) ? a.Ly : 1);
-  const uint32_t sliceBytes = (uint32_t)(R * RS);
+  const int nload = H + 4;  // local slices li = 0 .. H + 3 <-> global zs - 2 + li
+  const int64_t sliceStride = (int64_t)Lx * ((ND == 3) ? a.Ly : 1);
 
+  // int8 byte patterns of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e4 | o4 << 4
+  for (int i = tid; i < 256; i += nth) {
+    uint32_t lo = 0, hi = 0;
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t eb = ((i >> k) & 1) ? 0xffu : 0x01u;
+      const uint32_t ob = ((i >> (4 + k)) & 1) ? 0xffu : 0x01u;
+      const uint32_t pair = eb | (ob << 8);
+      if (k < 2) lo |= pair << (16 * k); else hi |= pair << (16 * (k - 2));
+    }
+    lut[i] = make_uint2(lo, hi);
+  }
   if (tid == 0) {
     s_abort = 0;
-    for (int b = 0; b < kNbuf; ++b) mbar_init(&bars[b], 1);
+    s_qcount = 0;
+    for (int b = 0; b < a.nraw; ++b) mbar_init(&bars[b], 1);
     fence_mbar_init();
   }
+
+  // Static item maps (slice k of the step, row, word) for the three kinds.
+  Item ic[kRounds], ia[kRounds], ib[kRounds];
+#pragma unroll
+  for (int q = 0; q < kRounds; ++q) {
+    ic[q] = item_of(tid + q * nth, RSL * W, W, a.R * RSL * W, 0);
+    ia[q] = item_of(tid + q * nth, rowsA * W, W, a.R * rowsA * W, ND == 3 ? -1 : 0);
+    ib[q] = item_of(tid + q * nth, rowsB * W, W, a.R * rowsB * W, 0);
+  }
+  const int roundsC = (a.R * RSL * W + nth - 1) / nth;
+  const int roundsA = (a.R * rowsA * W + nth - 1) / nth;
+  const int roundsB = (a.R * rowsB * W + nth - 1) / nth;
   __syncthreads();
 
-  auto gslice = [&](int li) { int z = zs - 2 + li; z %= a.S; if (z < 0) z += a.S; return z; };
-  auto buf = [&](int li) { return smem + (li % kNbuf) * SB; };
+  auto wrapS = [&](int z) { return z < 0 ? z + a.S : (z >= a.S ? z - a.S : z); };
+  auto wrapY = [&](int y) { return y < 0 ? y + a.Ly : (y >= a.Ly ? y - a.Ly : y); };
+  auto bslot = [&](int li) { return li % a.nbit; };  // per step only (uniform)
 
-  // Issue the copies of local slice li into its buffer (warp 0).
+  // Issue the bulk copies of local slice li (warp 0).
   auto issue = [&](int li) {
     if (li >= nload || tid >= 32) return;
-    uint8_t* B = buf(li);
-    uint64_t* bar = &bars[li % kNbuf];
+    uint8_t* B = raw + (size_t)(li % a.nraw) * rawStride;
+    uint64_t* bar = &bars[li % a.nraw];
     if (tid == 0) {
       fence_proxy_async();
-      mbar_arrive_expect_tx(bar, sliceBytes);
+      mbar_arrive_expect_tx(bar, (uint32_t)rawBytes);
     }
     __syncwarp();
-    const int gz = gslice(li);
-    const int xl = (x0 - 16 + a.Lx) % a.Lx, xr = (x0 + a.TX) % a.Lx;
-    for (int r = tid; r < R; r += 32) {
-      int gy;
-      if (ND == 3) { gy = (y0 - YH + r) % a.Ly; if (gy < 0) gy += a.Ly; } else { gy = 0; }
-      const int8_t* row = a.in + (int64_t)gz * sliceStride + (int64_t)gy * a.Lx;
-      uint8_t* d = B + r * RS;
-      bulk_g2s(d, row + xl, 16, bar);
-      bulk_g2s(d + 16, row + x0, (uint32_t)a.TX, bar);
-      bulk_g2s(d + 16 + a.TX, row + xr, 16, bar);
+    const int gz = wrapS(zs - 2 + li);
+    for (int r = tid; r < RSL; r += 32) {
+      const int gy = (ND == 3) ? wrapY(y0 - YH + r) : 0;
+      bulk_g2s(B + (size_t)r * Lx, a.in + (int64_t)gz * sliceStride + (int64_t)gy * Lx, (uint32_t)Lx, bar);
     }
   };
 
-  // Bounded wait for local slice li; on timeout every thread learns it.
-  auto wait_slice = [&](int li) -> bool {
-    const uint32_t parity = (uint32_t)((li / kNbuf) & 1);
-    unsigned n = 0;
-    while (!mbar_try_wait(&bars[li % kNbuf], parity)) {
-      if (++n > kWaitLimit) { s_abort = 1; break; }
+  auto wait_raw = [&](int l0, int ns) -> bool {
+    for (int li = l0; li < l0 + ns; ++li) {
+      const uint32_t parity = (uint32_t)((li / a.nraw) & 1);
+      unsigned n = 0;
+      while (!mbar_try_wait(&bars[li % a.nraw], parity)) {
+        if (++n > kWaitLimit) {
+          s_abort = 1;
+          break;
+        }
+      }
     }
     return __syncthreads_or(s_abort) != 0;
   };
 
-  for (int li = 0; li < kNbuf; ++li) issue(li);
+  // Raw slices l0 .. l0+ns-1 -> bit words E (even x) and O (odd x) per row.
+  auto convert = [&](int l0, int ns) {
+    const int rbase = l0 % a.nraw, bbase = bslot(l0);
+#pragma unroll
+    for (int q = 0; q < kRounds; ++q) {
+      const Item x = ic[q];
+      if (q < roundsC && x.live && x.k < ns) {
+        int rs = rbase + x.k;
+        if (rs >= a.nraw) rs -= a.nraw;
+        int bs = bbase + x.k;
+        if (bs >= a.nbit) bs -= a.nbit;
+        const uint8_t* span = raw + (size_t)rs * rawStride + (size_t)x.r * Lx + 64 * x.j;
+        uint32_t E = 0, O = 0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          // rotate the 16-byte chunk order by lane so a quarter warp hits distinct banks
+          const int cv = (v + (lane >> 1)) & 3;
+          const uint4 qv = *reinterpret_cast<const uint4*>(span + 16 * cv);
+          const uint32_t w[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const int t = 2 * cv + p;  // sites 8t .. 8t+7 of the span
+            const uint32_t ev = __byte_perm(w[2 * p], w[2 * p + 1], 0x6420);
+            const uint32_t od = __byte_perm(w[2 * p], w[2 * p + 1], 0x7531);
+            E |= sign_bits4(ev) << (4 * t);
+            O |= sign_bits4(od) << (4 * t);
+          }
+        }
+        uint32_t* row = bitbuf + (size_t)bs * bitWords + (size_t)x.r * 2 * W;
+        row[x.j] = E;
+        row[W + x.j] = O;
+      }
+    }
+  };
 
   int de = 0, dm = 0;
-  const int rowsA = (ND == 3) ? a.TY + 2 : 1;   // colour-0 rows: -1 .. TY (3D)
-  const int nA = rowsA * nck;
-  const int nRing = (ND == 3) ? a.TY : 1;       // one colour-0 ring site per owned row
-  const int nB = ((ND == 3) ? a.TY : 1) * nck;
 
-  // ---- colour-0 pass on local slice li (reads li-1, li, li+1), two barriers.
-  auto passA = [&](int li) {
-    const uint8_t* Bm = buf(li - 1);
-    uint8_t* B0 = buf(li);
-    const uint8_t* Bp = buf(li + 1);
-    const int gz = gslice(li);
-    const bool owned = (li >= 2 && li < H + 2);
-    uint4 res[kMaxA];
-    int rr[kMaxA], kk[kMaxA];
+  // Per-word state between the first decision stage and the final write.
+  struct WordState {
+    uint32_t b, s0, s1, s2, acc;
+    int par;
+    bool pending;
+  };
+
+  auto slot_plus = [&](int s, int d) {
+    s += d;
+    return s >= a.nbit ? s - a.nbit : s;
+  };
+
+  // Neighbour counts, classes and the first 8 planes of the colour-c word of
+  // item x in local slice li (bit slot bs); pushes a tie to the CTA queue.
+  auto prepare = [&](const Item& x, int li, int bs, int c, int qslot) {
+    const int bm = bs == 0 ? a.nbit - 1 : bs - 1, bp = slot_plus(bs, 1);
+    const int gz = wrapS(zs - 2 + li);
+    const int gy = (ND == 3) ? wrapY(y0 + x.r) : gz;
+    const int gzz = (ND == 3) ? gz : 0;
+    const int par = (gy + gzz + c) & 1;
+    const int ro = (x.r + YH) * 2 * W;
+    const uint32_t* row = bitbuf + (size_t)bs * bitWords + ro;
+    const uint32_t* same = row + par * W;
+    const uint32_t* other = row + (W - par * W);
+    const int j = x.j;
+    WordState w;
+    w.b = same[j];
+    const int jm = j == 0 ? W - 1 : j - 1, jp = j + 1 == W ? 0 : j + 1;
+    uint32_t left, right;
+    if (par == 0) {
+      right = other[j];
+      left = __funnelshift_l(other[jm], other[j], 1);  // (O_j << 1) | (O_{j-1} >> 31)
+    } else {
+      left = other[j];
+      right = __funnelshift_r(other[j], other[jp], 1);  // (E_j >> 1) | (E_{j+1} << 31)
+    }
+    const uint32_t zm = bitbuf[(size_t)bm * bitWords + ro + par * W + j];
+    const uint32_t zp = bitbuf[(size_t)bp * bitWords + ro + par * W + j];
+    const uint32_t b = w.b;
+    if constexpr (ND == 3) {
+      const uint32_t ym = same[j - 2 * W];
+      const uint32_t yp = same[j + 2 * W];
+      count6(b ^ left, b ^ right, b ^ ym, b ^ yp, b ^ zm, b ^ zp, w.s0, w.s1, w.s2);
+    } else {
+      count4(b ^ left, b ^ right, b ^ zm, b ^ zp, w.s0, w.s1, w.s2);
+    }
+    uint32_t cls[ND], eq[ND];
+    w.acc = classes<ND>(w.s0, w.s1, w.s2, 0xffffffffu, cls);
+    const uint32_t c0 = 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)(gy + a.Ly * gzz));
+    decide_first<ND>(w.acc, eq, cls, a.T, a.K, c0, a.sweep, (uint32_t)c | (kMetropolis << 1), a.stream_id);
+    uint32_t any = 0;
 #pragma unroll
-    for (int q = 0; q < kMaxA; ++q) {
-      const int it = tid + q * nth;
-      rr[q] = -100;
-      if (it < nA) {
-        const int r = (ND == 3) ? it / nck - 1 : 0;
-        const int k = it - (r + ((ND == 3) ? 1 : 0)) * nck;
-        int gy;
-        if (ND == 3) { gy = (y0 + r) % a.Ly; if (gy < 0) gy += a.Ly; } else { gy = gz; }
+    for (int q = 0; q < ND; ++q) any |= eq[q];
+    w.pending = any != 0;
+    if (w.pending) {
+      const int e = atomicAdd(qcount, 1);
+      qe[e] = make_uint4(c0, eq[0], eq[1], ND == 3 ? eq[ND - 1] : 0u);
+      qslot_of[e] = qslot;
+    }
+    w.par = par;
+    return w;
+  };
+
+  // Planes 8.. for the queued words, whole warps at a time.
+  auto tail = [&](int c) {
+    const int n = *qcount;
+    for (int base = tid & ~31; base < n; base += nth) {
+      const int e = base + lane;
+      uint32_t eq[ND];
+      uint32_t c0 = 0;
+#pragma unroll
+      for (int q = 0; q < ND; ++q) eq[q] = 0;
+      if (e < n) {
+        const uint4 v = qe[e];
+        c0 = v.x;
+        eq[0] = v.y;
+        eq[1] = v.z;
+        if constexpr (ND == 3) eq[2] = v.w;
+      }
+      const uint32_t accepted =
+          decide_tail<ND>(eq, a.T, a.K, c0, a.sweep, (uint32_t)c | (kMetropolis << 1), a.stream_id);
+      if (e < n) late[qslot_of[e]] = accepted;
+    }
+  };
+
+  // Colour 0 on local slices l0 .. l0+ns-1: rows -1 .. TY (3D) of each slice.
+  auto passA = [&](int l0, int ns) {
+    const int base = bslot(l0);
+    WordState st[kRounds];
+    int where[kRounds];
+    bool own[kRounds];
+#pragma unroll
+    for (int q = 0; q < kRounds; ++q) {
+      where[q] = -1;
+      own[q] = false;
+      const Item x = ia[q];
+      if (q < roundsA && x.live && x.k < ns) {
+        const int li = l0 + x.k;
+        const int bs = slot_plus(base, x.k);
+        st[q] = prepare(x, li, bs, 0, q * nth + tid);
+        own[q] = li >= 2 && li < H + 2 && (ND == 2 || (x.r >= 0 && x.r < a.TY));
+        where[q] = bs * bitWords + (x.r + YH) * 2 * W + st[q].par * W + x.j;
+      }
+    }
+    __syncthreads();
+    tail(0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kRounds; ++q) {
+      if (where[q] >= 0) {
+        WordState& w = st[q];
+        if (w.pending) w.acc |= late[q * nth + tid];
+        if (own[q]) tally<ND>(w.acc, w.b, w.s0, w.s1, w.s2, de, dm);
+        bitbuf[where[q]] = w.b ^ w.acc;
+      }
+    }
+    if (tid == 0) *qcount = 0;  // no pushes before the next barrier
+    __syncthreads();
+  };
+
+  // Colour 1 on local slices l0 .. l0+ns-1, owned rows; final rows to global.
+  auto passB = [&](int l0, int ns) {
+    const int base = bslot(l0);
+    WordState st[kRounds];
+    int bsq[kRounds];
+#pragma unroll
+    for (int q = 0; q < kRounds; ++q) {
+      bsq[q] = -1;
+      const Item x = ib[q];
+      if (q < roundsB && x.live && x.k < ns) {
+        const int li = l0 + x.k;
+        bsq[q] = slot_plus(base, x.k);
+        st[q] = prepare(x, li, bsq[q], 1, q * nth + tid);
+      }
+    }
+    __syncthreads();
+    tail(1);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kRounds; ++q) {
+      if (bsq[q] >= 0) {
+        const Item x = ib[q];
+        WordState& w = st[q];
+        if (w.pending) w.acc |= late[q * nth + tid];
+        tally<ND>(w.acc, w.b, w.s0, w.s1, w.s2, de, dm);
+        const uint32_t nw = w.b ^ w.acc;
+        const uint32_t* row = bitbuf + (size_t)bsq[q] * bitWords + (x.r + YH) * 2 * W;
+        const uint32_t E = w.par == 0 ? nw : row[x.j];
+        const uint32_t O = w.par == 0 ? row[W + x.j] : nw;
+        const int li = l0 + x.k;
+        const int gz = wrapS(zs - 2 + li);
+        const int gy = (ND == 3) ? y0 + x.r : gz;
         const int gzz = (ND == 3) ? gz : 0;
-        const int par = (gy + gzz) & 1;  // colour 0
-        const uint8_t* p = B0 + (r + YH) * RS + 16 + 16 * k;
-        uint4 V[ND == 3 ? 4 : 2];
-        load_vertical<ND>(V, p, Bm + (p - B0), Bp + (p - B0), RS);
-        const uint32_t gidx = (uint32_t)((x0 >> 4) + k + (int64_t)(a.Lx >> 4) * (gy + (int64_t)a.Ly * gzz));
-        const U4 P = philox10(gidx, a.sweep, 0u | (kMetroHi << 1), a.stream_id, a.K);
-        int lde = 0, ldm = 0;
-        res[q] = chunk_update(lds16(p), V, p[-1], p[16], par, P, gidx, 0u, a, lde, ldm);
-        const bool own = owned && (ND == 2 || (r >= 0 && r < a.TY));
-        if (own) { de += lde; dm += ldm; }
-        rr[q] = r;
-        kk[q] = k;
-      }
-    }
-    // ring: the colour-0 one of x = x0 - 1 and x = x0 + TX in each owned row
-    int ring_pos = -1;
-    uint8_t ring_val = 0;
-    int ring_r = 0;
-    if (tid < nRing) {
-      const int r = (ND == 3) ? tid : 0;
-      int gy;
-      if (ND == 3) { gy = (y0 + r) % a.Ly; } else { gy = gz; }
-      const int gzz = (ND == 3) ? gz : 0;
-      const int xl = (x0 - 1 + a.Lx) % a.Lx;
-      const bool left = ((xl + gy + gzz) & 1) == 0;
-      const int gx = left ? xl : (x0 + a.TX) % a.Lx;
-      const int pos = left ? 15 : 16 + a.TX;
-      const uint8_t* p = B0 + (r + YH) * RS + pos;
-      const uint32_t sv = p[0];
-      uint32_t k = ((sv ^ p[-1]) & 2u) + ((sv ^ p[1]) & 2u) + ((sv ^ Bm[p - B0]) & 2u) + ((sv ^ Bp[p - B0]) & 2u);
-      if (ND == 3) k += ((sv ^ p[-RS]) & 2u) + ((sv ^ p[RS]) & 2u);
-      const int idx = ND - (int)(k >> 1);
-      const int64_t n = (int64_t)gx + (int64_t)a.Lx * (gy + (int64_t)a.Ly * gzz);
-      const int64_t m = n >> 1;
-      const uint32_t gidx = (uint32_t)(m >> 3);
-      const uint32_t i = (uint32_t)(m & 7);
-      const U4 P = philox10(gidx, a.sweep, 0u | (kMetroHi << 1), a.stream_id, a.K);
-      const uint32_t uh = half16(P, i), th = thr_hi(idx, a.T);
-      bool acc = uh < th;
-      if (uh == th) {
-        const U4 Q = philox10(gidx, a.sweep, 0u | (kMetroLo << 1), a.stream_id, a.K);
-        acc = half16(Q, i) < thr_lo(idx, a.T);
-      }
-      ring_pos = pos;
-      ring_r = r;
-      ring_val = acc ? (uint8_t)(sv ^ 0xfeu) : (uint8_t)sv;
-    }
-    __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(a.out + (int64_t)gzz * sliceStride + (int64_t)gy * Lx + 64 * x.j);
 #pragma unroll
-    for (int q = 0; q < kMaxA; ++q)
-      if (rr[q] != -100) *reinterpret_cast<uint4*>(B0 + (rr[q] + YH) * RS + 16 + 16 * kk[q]) = res[q];
-    if (ring_pos >= 0) B0[(ring_r + YH) * RS + ring_pos] = ring_val;
-    __syncthreads();
-  };
-
-  // ---- colour-1 pass on local slice li, result to global memory.
-  auto passB = [&](int li) {
-    const uint8_t* Bm = buf(li - 1);
-    const uint8_t* B0 = buf(li);
-    const uint8_t* Bp = buf(li + 1);
-    const int gz = gslice(li);
-    for (int it = tid; it < nB; it += nth) {
-      const int r = (ND == 3) ? it / nck : 0;
-      const int k = it - r * nck;
-      const int gy = (ND == 3) ? y0 + r : gz;
-      const int gzz = (ND == 3) ? gz : 0;
-      const int par = (gy + gzz + 1) & 1;
-      const uint8_t* p = B0 + (r + YH) * RS + 16 + 16 * k;
-      uint4 V[ND == 3 ? 4 : 2];
-      load_vertical<ND>(V, p, Bm + (p - B0), Bp + (p - B0), RS);
-      const uint32_t gidx = (uint32_t)((x0 >> 4) + k + (int64_t)(a.Lx >> 4) * (gy + (int64_t)a.Ly * gzz));
-      const U4 P = philox10(gidx, a.sweep, 1u | (kMetroHi << 1), a.stream_id, a.K);
-      const uint4 o = chunk_update(lds16(p), V, p[-1], p[16], par, P, gidx, 1u, a, de, dm);
-      int8_t* dst = a.out + (int64_t)gzz * sliceStride + (int64_t)gy * a.Lx + x0 + 16 * k;
-      *reinterpret_cast<uint4*>(dst) = o;
+        for (int v = 0; v < 4; ++v) {
+          const uint2 lo = lut[((E >> (8 * v)) & 0xfu) | (((O >> (8 * v)) & 0xfu) << 4)];
+          const uint2 hi = lut[((E >> (8 * v + 4)) & 0xfu) | (((O >> (8 * v + 4)) & 0xfu) << 4)];
+          dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+        }
+      }
     }
+    if (tid == 0) *qcount = 0;  // the next pushes follow the next step's conversion barrier
   };
 
-  // Local slice li (global zs - 2 + li) lives in buffer li % kNbuf.  Step t
-  // produces slice zs + t (local t + 2): colour 0 on local t + 3 (it needs old
-  // t + 2 .. t + 4), then colour 1 on local t + 2 (mid t + 1 .. t + 3).  After
-  // step t local t + 1 is dead and its buffer takes local t + 1 + kNbuf.
-  int issued = kNbuf < nload ? kNbuf : nload;
+  // Prologue: slices zs-2 .. zs+1 (local 0..3), colour 0 on zs-1 and zs.
+  const int first = a.nraw < nload ? a.nraw : nload;
+  for (int li = 0; li < first; ++li) issue(li);
+  int issued = first;
   bool abort = false;
-  for (int li = 0; li <= 3 && !abort; ++li) abort = wait_slice(li);
-  if (!abort) passA(1);
-  if (!abort) passA(2);
-  if (!abort) { issue(kNbuf); issued = kNbuf + 1 < nload ? kNbuf + 1 : nload; }
-  for (int t = 0; t < H && !abort; ++t) {
-    abort = wait_slice(t + 4);
+  for (int li = 0; li < 4 && !abort; ++li) {  // one slice at a time: the raw ring may hold fewer than 4
+    abort = wait_raw(li, 1);
     if (abort) break;
-    passA(t + 3);     // colour 0 on slice z+1
-    passB(t + 2);     // colour 1 on slice z -> global
-    __syncthreads();  // every thread is past passB(t + 2)
-    issue(t + 1 + kNbuf);
-    issued = t + 2 + kNbuf < nload ? t + 2 + kNbuf : nload;
+    convert(li, 1);
+    __syncthreads();
+    issue(li + a.nraw);
+    issued = (li + 1 + a.nraw < nload) ? li + 1 + a.nraw : nload;
+  }
+  if (!abort) {
+    passA(1, 1);
+    passA(2, 1);
+  }
+  // Step: outputs o in [b0, b0 + ns) (local li = o + 2).
+  for (int b0 = 0; b0 < H && !abort; b0 += a.R) {
+    const int ns = (b0 + a.R < H) ? a.R : H - b0;
+    abort = wait_raw(b0 + 4, ns);
+    if (abort) break;
+    convert(b0 + 4, ns);
+    __syncthreads();
+    for (int li = b0 + 4; li < b0 + 4 + ns; ++li) issue(li + a.nraw);
+    issued = (b0 + 4 + ns + a.nraw < nload) ? b0 + 4 + ns + a.nraw : nload;
+    passA(b0 + 3, ns);
+    passB(b0 + 2, ns);
   }
 
   if (abort) {
     if (tid == 0) {
       atomicExch(a.err, 1);
       // let the copies still in flight land before the CTA exits (bounded)
-      for (int li = issued > kNbuf ? issued - kNbuf : 0; li < issued; ++li) {
+      for (int li = issued > a.nraw ? issued - a.nraw : 0; li < issued; ++li) {
         unsigned n = 0;
-        while (!mbar_try_wait(&bars[li % kNbuf], (uint32_t)((li / kNbuf) & 1)) && ++n < kWaitLimit) {
+        while (!mbar_try_wait(&bars[li % a.nraw], (uint32_t)((li / a.nraw) & 1)) && ++n < kWaitLimit) {
         }
       }
     }
     __syncthreads();
     return;
   }
-  long long lde = de, ldm = dm;
-  block_accumulate(lde, ldm, a.acc);
+  block_accumulate(de, dm, a.acc);
 }
 
 }  // namespace
 
-bool stream_path_supported(const Lattice& g, int TX, int TY) {
+bool stream_path_supported(const Lattice& g, int TY) {
   if (g.bonds) return false;
-  if (g.Lx % 16 || TX <= 0 || TX % 16 || g.Lx % TX) return false;
+  if (g.Lx % 64) return false;
   if (g.nd == 3 && (TY <= 0 || g.Ly % TY)) return false;
+  const int RSL = g.nd == 3 ? TY + 4 : 1;
+  if ((int64_t)RSL * g.Lx * 3 > 200 * 1024) return false;  // a few raw slices must fit in shared memory
   return true;
 }
 
-StreamGeom stream_geometry(const Lattice& g, int TX, int TY, int nseg) {
+StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg) {
   StreamGeom s{};
-  s.TX = TX;
   s.TY = g.nd == 3 ? TY : 1;
-  const int R = g.nd == 3 ? TY + 4 : 1;
-  const int SB = ((R * (TX + 32)) + 127) & ~127;
-  s.nbuf = kNbuf;
-  s.smem = (size_t)kNbuf * SB + kNbuf * sizeof(uint64_t);
-  const int nck = TX / 16;
-  const int nA = (g.nd == 3 ? TY + 2 : 1) * nck;
-  int th = 32;
-  while (th * kMaxA < nA || th < (g.nd == 3 ? TY : 1)) th += 32;
-  s.threads = std::min(512, std::max(th, std::min(512, nck * (g.nd == 3 ? TY : 1))));
+  const int W = g.Lx / 64;
+  const int RSL = g.nd == 3 ? TY + 4 : 1;
   const int S = g.nd == 3 ? g.Lz : g.Ly;
+  const int perB = (g.nd == 3 ? TY : 1) * W;
+  const bool automatic = R <= 0;
+  if (automatic) R = std::max(1, std::min(S, 1024 / std::max(1, perB)));  // two colour-1 words per thread
+  const size_t rawStride = (size_t)((RSL * g.Lx + 127) & ~127);
+  auto smem_of = [&](int r, int nraw) {  // + the tie queue (16 + 4 + 4 bytes per item), sized for 512 threads
+    return (((size_t)nraw * rawStride + (size_t)(2 * r + 3) * RSL * 2 * W * 4 + 256 * 8 + (size_t)nraw * 8 + 15) &
+            ~(size_t)15) + (size_t)kRounds * 512 * 24;
+  };
+  const size_t cap = 233472 / 2 - 1024;  // two CTAs per SM (228 KB per SM, 1 KB reserved per CTA)
+  while (automatic && R > 1 && smem_of(R, R) > cap) --R;
+  s.R = R;
+  s.nbit = 2 * R + 3;
+  s.nraw = std::max(3, 2 * R);  // a raw slice is issued once the slice nraw before it is converted
+  while (smem_of(R, s.nraw) > cap && s.nraw > std::max(1, R)) s.nraw -= 1;
+  s.smem = smem_of(R, s.nraw);
+  const int nC = R * RSL * W, nA = R * (g.nd == 3 ? TY + 2 : 1) * W, nB = R * perB;
+  const int need = (std::max(nC, std::max(nA, nB)) + kRounds - 1) / kRounds;
+  int th = std::max(need, std::min(nB, 512));
+  th = ((th + 31) / 32) * 32;
+  s.threads = std::min(512, std::max(64, th));
   if (nseg <= 0) {
-    const int tiles = (g.Lx / TX) * (g.nd == 3 ? g.Ly / TY : 1);
-    const int want = device_sm_count() * 4;
+    const int tiles = g.nd == 3 ? g.Ly / TY : 1;
+    const int want = device_sm_count() * 2;
     nseg = std::max(1, std::min(S, (want + tiles - 1) / tiles));
   }
   s.nseg = std::min(nseg, S);
   return s;
 }
 
+bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
+  const int W = g.Lx / 64;
+  const int RSL = g.nd == 3 ? geo.TY + 4 : 1;
+  const int nC = geo.R * RSL * W, nA = geo.R * (g.nd == 3 ? geo.TY + 2 : 1) * W, nB = geo.R * (g.nd == 3 ? geo.TY : 1) * W;
+  const int cap = geo.threads * kRounds;
+  return geo.threads <= 512 && geo.threads % 32 == 0 && nC <= cap && nA <= cap && nB <= cap &&
+         geo.smem <= 227 * 1024 && geo.nraw >= geo.R && geo.nbit >= 2 * geo.R + 3 && geo.nseg >= 1;
+}
+
 cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out, const StreamGeom& geo,
-                                const ThrTab& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st) {
+  if (!stream_geometry_ok(g, geo)) return cudaErrorInvalidConfiguration;
   StreamArgs a;
   a.in = in;
   a.out = out;
   a.Lx = g.Lx;
   a.Ly = g.Ly;
   a.Lz = g.Lz;
-  a.TX = geo.TX;
   a.TY = geo.TY;
+  a.R = geo.R;
   a.nseg = geo.nseg;
   a.S = g.nd == 3 ? g.Lz : g.Ly;
+  a.nraw = geo.nraw;
+  a.nbit = geo.nbit;
   a.sweep = sweep;
   a.stream_id = stream_id;
   a.K = K;
   a.T = T;
   a.acc = acc;
   a.err = err;
-  const int nck = geo.TX / 16;
-  const int nA = (g.nd == 3 ? geo.TY + 2 : 1) * nck;
-  if (nA > geo.threads * kMaxA || geo.threads > 512) return cudaErrorInvalidConfiguration;
-  dim3 grid(g.Lx / geo.TX, g.nd == 3 ? g.Ly / geo.TY : 1, geo.nseg);
+  dim3 grid(g.nd == 3 ? g.Ly / geo.TY : 1, geo.nseg);
   if (g.nd == 3) {
     cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
+    cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     k_sweep_stream<3><<<grid, geo.threads, geo.smem, st>>>(a);
   } else {
     cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
+    cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     k_sweep_stream<2><<<grid, geo.threads, geo.smem, st>>>(a);
   }
+  count_launches(1);
   return cudaGetLastError();
 }
 

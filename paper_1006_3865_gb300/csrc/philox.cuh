@@ -55,11 +55,9 @@ __device__ __forceinline__ uint32_t u4_word(const U4& v, int i) {
 
 // Purposes carried in bits 1.. of the third counter word (bit 0 is the colour).
 enum : uint32_t {
-  kMetroHi = 0u,   // high 16 bits of the Metropolis u
-  kMetroLo = 1u,   // low 16 bits of the Metropolis u (drawn only on a tie)
-  kInitHi = 2u,    // hot start, high half
-  kInitLo = 3u,    // hot start, low half
-  kExchange = 4u,  // replica exchange (full 32-bit words)
+  kMetropolis = 0u,  // Metropolis u, stored across 32 bit planes
+  kInit = 1u,        // hot start (most significant plane)
+  kExchange = 2u,    // replica exchange (full 32-bit words)
 };
 
 }  // namespace spn

@@ -69,18 +69,13 @@ std::vector<uint8_t> unpack_site_bonds(const uint64_t* words, int nd, int64_t N)
 
 void pick_default_path(spn_ctx* h) {
   const spn::Lattice& g = h->g;
-  int tx = g.Lx;
-  while (tx > 8192 && tx % 2 == 0 && (tx / 2) % 16 == 0) tx /= 2;
-  int ty = 16;
-  if (g.nd == 3) {
+  int ty = 32;
+  if (g.nd == 3)
     while (ty > 1 && g.Ly % ty) ty /= 2;
-  }
-  if (g.nd == 3 && g.Lx > 1024) tx = 1024 - (1024 % 16);
-  if (g.Lx % tx) tx = g.Lx;
-  h->tile_x = tx;
-  h->tile_y = ty;
+  h->tile_y = g.nd == 3 ? ty : 1;
+  h->step_slices = 0;
   h->seg = 0;
-  h->path = spn::stream_path_supported(g, tx, ty) && g.N >= (1 << 16) ? spn::kPathStream : spn::kPathGeneric;
+  h->path = spn::stream_path_supported(g, h->tile_y) && g.N >= (1 << 16) ? spn::kPathStream : spn::kPathGeneric;
 }
 
 int ensure_acc(spn_ctx* h, int64_t n) {
@@ -130,10 +125,15 @@ int fold(spn_ctx* h) {
 }
 
 int recompute(spn_ctx* h, int64_t* E, int64_t* M) {
-  SPN_CUDA(spn::launch_observables(h->g, h->spins[h->cur], h->d_obs, h->st), "observables");
-  unsigned long long r[2];
-  SPN_CUDA(cudaMemcpyAsync(r, h->d_obs, sizeof r, cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync(obs)");
+  SPN_CUDA(cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->st), "cudaMemsetAsync");
+  SPN_CUDA(spn::launch_observables(h->g, h->spins[h->cur], h->d_obs, h->d_bad, h->st), "observables");
+  unsigned long long r[3];
+  SPN_CUDA(cudaMemcpyAsync(r, h->d_obs, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->st),
+           "cudaMemcpyAsync(obs)");
+  int bad = 0;
+  SPN_CUDA(cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync(bad)");
   SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  if (bad) return fail(SPN_E_ARG, "spin values other than +-1 in the lattice");
   *E = (int64_t)r[0];
   *M = (int64_t)r[1];
   return SPN_OK;
@@ -147,6 +147,7 @@ void destroy(spn_ctx* h) {
   cudaFree(h->d_bonds);
   cudaFree(h->d_acc);
   cudaFree(h->d_err);
+  cudaFree(h->d_bad);
   cudaFree(h->d_obs);
   delete h;
 }
@@ -182,6 +183,7 @@ int spn_create_ex(spn_handle* out, int model, const int32_t* dims, const void* c
   cudaError_t e;
   if ((e = cudaMalloc(&h->spins[0], (size_t)g.N)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(spins)"));
   if ((e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(err)"));
+  if ((e = cudaMalloc(&h->d_bad, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(bad)"));
   if ((e = cudaMalloc(&h->d_obs, 2 * sizeof(unsigned long long))) != cudaSuccess)
     return bail(cuda_fail(e, "cudaMalloc(obs)"));
   if ((e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->st)) != cudaSuccess) return bail(cuda_fail(e, "memset"));
@@ -222,10 +224,13 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
   if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return fail(SPN_E_ARG, "sweep counter would exceed 2^32");
   int rc = ensure_acc(h, nsweeps);
   if (rc) return rc;
-  const spn::ThrTab T = spn::make_thresholds(beta);
+  const spn::DevThr T = spn::make_thresholds(beta);
   const spn::PhiloxKeys K = spn::philox_keys(h->seed);
   spn::StreamGeom geo{};
-  if (h->path == spn::kPathStream) geo = spn::stream_geometry(h->g, h->tile_x, h->tile_y, h->seg);
+  if (h->path == spn::kPathStream) {
+    geo = spn::stream_geometry(h->g, h->tile_y, h->step_slices, h->seg);
+    if (!spn::stream_geometry_ok(h->g, geo)) return fail(SPN_E_STATE, "streaming geometry does not fit one CTA");
+  }
   for (int64_t t = 0; t < nsweeps; ++t) {
     const uint32_t sweep = (uint32_t)(h->sweeps + t);
     unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);
@@ -285,8 +290,6 @@ int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
 int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
   if (!h || !host_in) return fail(SPN_E_ARG, "NULL argument");
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
-  for (size_t i = 0; i < bytes; ++i)
-    if (host_in[i] != 1 && host_in[i] != -1) return fail(SPN_E_ARG, "spin %zu is not +-1", i);
   int rc = fold(h);
   if (rc) return rc;
   SPN_CUDA(cudaMemcpyAsync(h->spins[h->cur], host_in, bytes, cudaMemcpyHostToDevice, h->st), "cudaMemcpyAsync");
@@ -294,6 +297,34 @@ int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
   if ((rc = recompute(h, &E, &M))) return rc;
   h->E = E;
   h->M = M;
+  return SPN_OK;
+}
+
+int spn_reinit(spn_handle h, uint64_t seed, uint32_t stream, int init) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (init != SPN_INIT_HOT && init != SPN_INIT_COLD) return fail(SPN_E_ARG, "unknown init %d", init);
+  int rc = fold(h);
+  if (rc) return rc;
+  h->seed = seed;
+  h->stream_id = stream;
+  h->sweeps = 0;
+  h->folded = 0;
+  h->traceE.clear();
+  h->traceM.clear();
+  if (init == SPN_INIT_HOT)
+    SPN_CUDA(spn::launch_init_hot(h->g, h->spins[h->cur], seed, stream, h->st), "init");
+  else
+    SPN_CUDA(cudaMemsetAsync(h->spins[h->cur], 1, (size_t)h->g.N, h->st), "init");
+  int64_t E, M;
+  if ((rc = recompute(h, &E, &M))) return rc;
+  h->E = E;
+  h->M = M;
+  return SPN_OK;
+}
+
+int spn_launch_count(uint64_t* count) {
+  if (!count) return fail(SPN_E_ARG, "NULL argument");
+  *count = spn::launch_count();
   return SPN_OK;
 }
 
@@ -322,16 +353,16 @@ int spn_destroy(spn_handle h) {
   return SPN_OK;
 }
 
-int spn_set_tiling(spn_handle h, int32_t tile_x, int32_t tile_y, int32_t seg) {
+int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t seg) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
-  if (!spn::stream_path_supported(h->g, tile_x, h->g.nd == 3 ? tile_y : 1))
-    return fail(SPN_E_ARG, "tiling %d x %d does not divide the lattice", tile_x, tile_y);
-  spn::StreamGeom geo = spn::stream_geometry(h->g, tile_x, h->g.nd == 3 ? tile_y : 1, seg);
-  const int nA = (h->g.nd == 3 ? tile_y + 2 : 1) * (tile_x / 16);
-  if (geo.threads > 512 || nA > geo.threads * 2 || geo.smem > 227 * 1024)
-    return fail(SPN_E_ARG, "tiling %d x %d too large for one CTA", tile_x, tile_y);
-  h->tile_x = tile_x;
-  h->tile_y = h->g.nd == 3 ? tile_y : 1;
+  const int ty = h->g.nd == 3 ? tile_y : 1;
+  if (step_slices < 0 || seg < 0) return fail(SPN_E_ARG, "negative tiling parameter");
+  if (!spn::stream_path_supported(h->g, ty))
+    return fail(SPN_E_ARG, "band of %d rows does not divide the lattice or Lx %% 64 != 0", tile_y);
+  const spn::StreamGeom geo = spn::stream_geometry(h->g, ty, step_slices, seg);
+  if (!spn::stream_geometry_ok(h->g, geo)) return fail(SPN_E_ARG, "tiling too large for one CTA");
+  h->tile_y = ty;
+  h->step_slices = step_slices;
   h->seg = seg;
   return SPN_OK;
 }
@@ -345,8 +376,8 @@ int spn_get_path(spn_handle h, int32_t* path) {
 int spn_set_path(spn_handle h, int32_t path) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
   if (path == spn::kPathStream) {
-    if (!spn::stream_path_supported(h->g, h->tile_x, h->g.nd == 3 ? h->tile_y : 1))
-      return fail(SPN_E_ARG, "streaming path needs Lx %% 16 == 0 and no bonds");
+    if (!spn::stream_path_supported(h->g, h->tile_y))
+      return fail(SPN_E_ARG, "streaming path needs Lx %% 64 == 0, a dividing band and no bonds");
     if (!h->spins[1]) SPN_CUDA(cudaMalloc(&h->spins[1], (size_t)h->g.N), "cudaMalloc(spins)");
   } else if (path != spn::kPathGeneric) {
     return fail(SPN_E_ARG, "unknown path %d", path);

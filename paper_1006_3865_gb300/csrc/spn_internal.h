@@ -11,24 +11,25 @@
 
 namespace spn {
 
-// Metropolis thresholds of Eq. 2 split into 16-bit halves, indexed by dE / 4
-// (1 .. 3): a move with energy change dE > 0 is accepted iff
-// u_hi < hi[dE/4], or u_hi == hi[dE/4] and u_lo < lo[dE/4]; hi may be 0x10000.
-struct ThrTab {
-  uint32_t hi[4];
-  uint32_t lo[4];
+// Metropolis thresholds of Eq. 2 for the classes q = dE / 4 = 1 .. 3: a move
+// of class q is accepted iff u < t[q], or always when bit q of `always` is set
+// (floor(exp(-beta dE) 2^32) = 2^32, beta ~ 0).
+struct DevThr {
+  uint32_t t[4];
+  uint32_t always;
 };
 
 // floor(exp(-beta * dE) * 2^32) in [0, 2^32] (host, IEEE double).
 uint64_t boltzmann_threshold(double beta, int dE);
-ThrTab make_thresholds(double beta);
+DevThr make_thresholds(double beta);
 
 // Kernel paths of a single lattice.
 enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2 };
 
-// Streaming-kernel geometry; see ising.cu.
+// Streaming-kernel geometry (see ising.cu): TY rows per band (3D), R slices
+// per step, nseg segments along the streamed axis, raw / bit slice buffers.
 struct StreamGeom {
-  int TX, TY, nseg, threads, nbuf;
+  int TY, R, nseg, threads, nraw, nbit;
   size_t smem;
 };
 
@@ -42,16 +43,19 @@ struct Lattice {
 // Launchers (all asynchronous on `st`).  acc points at two int64 (dE, dM) that
 // the sweep adds its accepted moves to; err is a device error word.
 cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t stream_id, cudaStream_t st);
-cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long long* out2, cudaStream_t st);
-cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const ThrTab& T, const PhiloxKeys& K,
+cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long long* out2, int* bad, cudaStream_t st);
+cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, const PhiloxKeys& K,
                                  uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st);
-bool stream_path_supported(const Lattice& g, int TX, int TY);
-StreamGeom stream_geometry(const Lattice& g, int TX, int TY, int nseg);
+bool stream_path_supported(const Lattice& g, int TY);
+StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg);
+bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
 cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out, const StreamGeom& geo,
-                                const ThrTab& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st);
 
 int device_sm_count();
+void count_launches(uint64_t n);
+uint64_t launch_count();
 
 }  // namespace spn
 
@@ -65,7 +69,7 @@ struct spn_ctx {
   uint8_t* d_bonds = nullptr;
   cudaStream_t st = nullptr;
   int path = spn::kPathGeneric;
-  int tile_x = 0, tile_y = 0, seg = 0;
+  int tile_y = 0, step_slices = 0, seg = 0;
   uint64_t sweeps = 0;
   // incremental bookkeeping: device deltas (dE, dM) per sweep since `folded`
   unsigned long long* d_acc = nullptr;
@@ -74,5 +78,6 @@ struct spn_ctx {
   int64_t E = 0, M = 0;  // observables after `folded` sweeps
   std::vector<int64_t> traceE, traceM;
   int* d_err = nullptr;
+  int* d_bad = nullptr;
   unsigned long long* d_obs = nullptr;
 };

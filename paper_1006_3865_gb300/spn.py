@@ -65,6 +65,8 @@ _SIGNATURES = {
     "spn_set_tiling": (_c.c_int, [_vp, _i32, _i32, _i32]),
     "spn_get_path": (_c.c_int, [_vp, _P(_i32)]),
     "spn_set_path": (_c.c_int, [_vp, _i32]),
+    "spn_reinit": (_c.c_int, [_vp, _u64, _u32, _c.c_int]),
+    "spn_launch_count": (_c.c_int, [_P(_u64)]),
 }
 
 
@@ -122,6 +124,13 @@ def _stream_ptr(stream) -> int | None:
     return int(stream.cuda_stream)
 
 
+def launch_count() -> int:
+    """Kernels launched by libspn in this process so far."""
+    c = _u64()
+    _check(load().spn_launch_count(_c.byref(c)))
+    return c.value
+
+
 class Lattice:
     """One lattice handle (spn_create ... spn_destroy)."""
 
@@ -173,6 +182,9 @@ class Lattice:
     def set_spins(self, spins: np.ndarray):
         s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
         _check(self._lib.spn_set_spins(self._h, _ptr(s), s.size))
+
+    def reinit(self, seed: int, stream_id: int = 0, init: int = SPN_INIT_HOT):
+        _check(self._lib.spn_reinit(self._h, seed, stream_id, init))
 
     def sweep_count(self) -> int:
         c = _u64()

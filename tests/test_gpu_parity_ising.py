@@ -46,9 +46,9 @@ def test_ising2d_paths(path, T):
     _compare(spn.SPN_ISING2D, (128, 96), inputs.unit_seed(2), [(1.0 / T, 25)], path=path)
 
 
-@pytest.mark.parametrize("tiling", [(16, 0, 1), (32, 0, 7), (64, 0, 96), (128, 0, 5), (256, 0, 3)])
+@pytest.mark.parametrize("tiling", [(0, 1, 1), (0, 2, 7), (0, 4, 96), (0, 3, 5), (0, 8, 3), (0, 1, 0)])
 def test_ising2d_stream_tilings(tiling):
-    """Tile widths and ragged segment splits give identical bytes."""
+    """Rows per step and ragged segment splits give identical bytes."""
     _compare(spn.SPN_ISING2D, (256, 96), inputs.unit_seed(3), [(1.0 / TC, 12)], path=spn.PATH_STREAM,
              tiling=tiling, stream=5)
 
@@ -60,13 +60,19 @@ def test_ising2d_generic_small_and_ragged(dims):
 
 @pytest.mark.parametrize("path", [spn.PATH_GENERIC, spn.PATH_STREAM])
 def test_ising3d_paths(path):
-    _compare(spn.SPN_ISING3D, (32, 16, 12), inputs.unit_seed(5), [(inputs.BETA_C_3D, 10), (0.3, 5)], path=path)
+    _compare(spn.SPN_ISING3D, (64, 16, 12), inputs.unit_seed(5), [(inputs.BETA_C_3D, 10), (0.3, 5)], path=path)
 
 
-@pytest.mark.parametrize("tiling", [(16, 2, 1), (32, 4, 5), (16, 8, 12), (32, 16, 2)])
+@pytest.mark.parametrize("tiling", [(2, 1, 1), (4, 2, 5), (8, 1, 12), (16, 3, 2), (16, 1, 0)])
 def test_ising3d_stream_tilings(tiling):
-    _compare(spn.SPN_ISING3D, (32, 16, 12), inputs.unit_seed(6), [(inputs.BETA_C_3D, 6)], path=spn.PATH_STREAM,
+    """Band heights, slices per step and segment splits give identical bytes."""
+    _compare(spn.SPN_ISING3D, (64, 16, 12), inputs.unit_seed(6), [(inputs.BETA_C_3D, 6)], path=spn.PATH_STREAM,
              tiling=tiling)
+
+
+def test_ising3d_stream_wide_rows():
+    _compare(spn.SPN_ISING3D, (192, 8, 6), inputs.unit_seed(12), [(0.25, 4)], path=spn.PATH_STREAM,
+             tiling=(4, 1, 2))
 
 
 @pytest.mark.parametrize("dims", [(2, 2, 2), (6, 4, 10), (4, 4, 2), (18, 6, 8)])
@@ -82,7 +88,7 @@ def test_ea3d_int8(dims):
 
 @pytest.mark.parametrize("model,dims,path", [(spn.SPN_ISING2D, (64, 32), spn.PATH_STREAM),
                                              (spn.SPN_ISING2D, (10, 6), spn.PATH_GENERIC),
-                                             (spn.SPN_ISING3D, (16, 8, 6), spn.PATH_STREAM)])
+                                             (spn.SPN_ISING3D, (64, 8, 6), spn.PATH_STREAM)])
 def test_beta_zero_and_infinity(model, dims, path):
     s = _compare(model, dims, 11, [(0.0, 3)], path=path)
     s0 = oracle.init_hot(dims, 11)
