@@ -144,6 +144,35 @@ int spn_set_path(spn_handle h, int32_t path);
  * handles); a diagnostic for benchmarks. */
 int spn_launch_count(uint64_t* count);
 
+/* ------------------------------------------------------------------------
+ * Sweeps without device allocation
+ * ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart of this entry point: it exists for callers that
+ * must not let a library allocate device memory -- a host framework whose
+ * caching allocator has reserved the device memory (a raw cudaMalloc would fail
+ * or fragment its pool), plugin hosts that only hand out buffers, and
+ * latency-critical loops in which cudaMalloc / cudaFree would synchronise the
+ * device.
+ *
+ * Runs nsweeps sweeps (model SPN_ISING2D or SPN_ISING3D, J = +1) of the lattice
+ * d_spins (device, N int8 +-1 in site order, updated in place) at inverse
+ * temperature beta, with Philox seed / stream id and sweep counters sweep0 ..
+ * sweep0 + nsweeps - 1 -- the same results as a handle created with this seed
+ * and stream that has done sweep0 sweeps.  d_trace (device, 2 * nsweeps int64)
+ * receives the change (dE, dM) of every sweep.  cuda_stream: cudaStream_t as
+ * void* (NULL = legacy default stream).  Returns when the sweeps are done.
+ *
+ * It allocates nothing: its scratch (a second lattice for the ping-pong
+ * streaming kernel and an error word) is a fixed 16 MiB static device array
+ * that every GPU loading the library holds until the process exits, so N is
+ * limited to 16,777,216 sites (SPN_E_ARG beyond).  The first call on a device
+ * looks up that array's device address; make it before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other threads or
+ * streams) race and corrupt each other's results. */
+int spn_sweep_noalloc(int model, const int32_t* dims, int8_t* d_spins, double beta, uint64_t seed,
+                      uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* d_trace, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

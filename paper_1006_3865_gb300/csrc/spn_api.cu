@@ -154,6 +154,8 @@ void destroy(spn_ctx* h) {
 
 }  // namespace
 
+void spn::set_last_error(const char* msg) { g_last_error = msg; }
+
 extern "C" {
 
 const char* spn_last_error(void) { return g_last_error.c_str(); }

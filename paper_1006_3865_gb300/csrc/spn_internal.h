@@ -55,6 +55,7 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
 
 int device_sm_count();
 void count_launches(uint64_t n);
+void set_last_error(const char* msg);  // the thread's spn_last_error() message
 uint64_t launch_count();
 
 }  // namespace spn

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "spn_set_path": (_c.c_int, [_vp, _i32]),
     "spn_reinit": (_c.c_int, [_vp, _u64, _u32, _c.c_int]),
     "spn_launch_count": (_c.c_int, [_P(_u64)]),
+    "spn_sweep_noalloc": (_c.c_int, [_c.c_int, _vp, _vp, _dbl, _u64, _u32, _u32, _i64, _vp, _vp]),
 }
 
 
@@ -129,6 +130,14 @@ def launch_count() -> int:
     c = _u64()
     _check(load().spn_launch_count(_c.byref(c)))
     return c.value
+
+
+def sweep_noalloc(model: int, dims, d_spins: int, beta: float, seed: int, stream_id: int, sweep0: int,
+                  nsweeps: int, d_trace: int, cuda_stream=None):
+    """spn_sweep_noalloc on caller-owned device buffers (raw device pointers as ints)."""
+    d = _dims(dims)
+    _check(load().spn_sweep_noalloc(model, _ptr(d), d_spins, float(beta), seed, stream_id, sweep0, int(nsweeps),
+                                    d_trace, _stream_ptr(cuda_stream)))
 
 
 class Lattice:
