@@ -70,6 +70,10 @@ def lib():
             L.orc_init_hot.restype = cint
             L.orc_sweeps.argtypes = [cint, vp, vp, vp, dbl, u64, u32, u32, i64, vp, vp, vp, vp]
             L.orc_sweeps.restype = cint
+            L.orc_sweeps_ex.argtypes = [cint, vp, vp, vp, dbl, u64, u32, u32, i64, cint, vp, vp, vp, vp]
+            L.orc_sweeps_ex.restype = cint
+            L.orc_msc_u.argtypes = [u64, u32, u32, cint, u64]
+            L.orc_msc_u.restype = u32
             L.orc_ea_init_hot.argtypes = [vp, cint, u64, u32, vp]
             L.orc_ea_init_hot.restype = cint
             L.orc_ea_observables.argtypes = [vp, cint, vp, vp, vp, vp]
@@ -153,11 +157,16 @@ def init_hot(dims, seed: int, stream: int = 0) -> np.ndarray:
     return s
 
 
+def msc_u(seed: int, stream: int, sweep: int, colour: int, m: int) -> int:
+    return int(lib().orc_msc_u(seed, stream, sweep, colour, m))
+
+
 def sweeps(dims, spins: np.ndarray, beta: float, nsweeps: int, seed: int, stream: int = 0,
-           sweep0: int = 0, bonds=None, E: int | None = None, M: int | None = None):
+           sweep0: int = 0, bonds=None, E: int | None = None, M: int | None = None, msc_u_words: bool = False):
     """Run ``nsweeps`` sweeps in place on ``spins`` (flat int8, site order n).
 
-    Returns (E, M, traceE, traceM) with the per-sweep integer trace."""
+    Returns (E, M, traceE, traceM) with the per-sweep integer trace.  With
+    ``msc_u_words`` the sites draw u as the multi-spin coded path does."""
     d = _dims(dims)
     if spins.dtype != np.int8 or not spins.flags.c_contiguous:
         raise TypeError("spins must be a contiguous int8 array")
@@ -168,8 +177,8 @@ def sweeps(dims, spins: np.ndarray, beta: float, nsweeps: int, seed: int, stream
     Ma = np.array([M], np.int64)
     tE = np.zeros(max(nsweeps, 1), np.int64)
     tM = np.zeros(max(nsweeps, 1), np.int64)
-    _check(lib().orc_sweeps(len(d), _p(d), _p(spins), _p(b), float(beta), seed, stream, sweep0, int(nsweeps),
-                            _p(Ea), _p(Ma), _p(tE), _p(tM)), "sweeps")
+    _check(lib().orc_sweeps_ex(len(d), _p(d), _p(spins), _p(b), float(beta), seed, stream, sweep0, int(nsweeps),
+                               1 if msc_u_words else 0, _p(Ea), _p(Ma), _p(tE), _p(tM)), "sweeps")
     return int(Ea[0]), int(Ma[0]), tE[:nsweeps], tM[:nsweeps]
 
 

@@ -38,13 +38,17 @@
  *             The 32-bit u is uniform; storing it across planes lets a GPU
  *             thread compare 32 sites at once, most significant plane first,
  *             and stop drawing planes as soon as every site is decided.
+ *             Purpose 3 (multi-spin coded EA) uses plain words instead: the u
+ *             of within-colour index m is word m & 3 of R(m >> 2, t, c | 3 << 1,
+ *             stream), one word per site shared by the sample's 32 replicas.
  *   hot start s_n = -1 if bit 31 of the hot-start word is set, else +1.
  *   sweep t   colour 0, then colour 1; a site of colour c flips iff dE <= 0 or
  *             u < thr(beta, dE); E and M are updated by every accepted flip.
  *
  * Multi-spin coded EA (Sec. 4, "asynchronous multi-spin coding"):
  *   one uint32 per (sample, site); bit j is the replica held in temperature slot
- *   j (1 <=> spin -1).  All 32 replicas of a sample share the site's u.  Slot j
+ *   j (1 <=> spin -1).  All 32 replicas of a sample share the site's u (purpose
+ *   3 words, stream = sample).  Slot j
  *   runs at beta[temp_of_slot[j]]; betas are indexed by ascending temperature
  *   (non-increasing beta).  Hot start: the replica bits are the hot-start word.
  *   Replica exchange after every X-th sweep (step e = (t+1)/X - 1): for the
@@ -108,6 +112,15 @@ uint32_t orc_metropolis_u(uint64_t seed, uint32_t stream, uint32_t sweep, int co
 
 uint32_t orc_hot_word(uint64_t seed, uint32_t stream, int colour, uint64_t m) {
   return orc_site_word(seed, stream, 0, colour, 1, m);
+}
+
+/* Multi-spin coded Metropolis u: word m & 3 of R(m >> 2, sweep, c | 3 << 1, stream). */
+uint32_t orc_msc_u(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, uint64_t m) {
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {(uint32_t)(m >> 2), sweep, (uint32_t)colour | (3u << 1), stream};
+  uint32_t w[4];
+  orc_philox4x32_10(ctr, key, w);
+  return w[m & 3];
 }
 
 /* ------------------------------------------------------- Metropolis rule */
@@ -228,7 +241,7 @@ int orc_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, int8_
  * the half-sweep.  Its neighbours all have the other colour, so an in-place loop
  * is the same as a simultaneous update (Sec. 3). */
 static void half_sweep(const lat_t* g, int8_t* s, const uint64_t* bonds, const uint64_t* thr,
-                       uint64_t seed, uint32_t stream, uint32_t sweep, int c, int64_t* dEsum,
+                       uint64_t seed, uint32_t stream, uint32_t sweep, int c, int umode, int64_t* dEsum,
                        int64_t* dMsum) {
   int64_t de = 0, dm = 0;
 #pragma omp parallel for reduction(+ : de, dm) schedule(static)
@@ -239,7 +252,8 @@ static void half_sweep(const lat_t* g, int8_t* s, const uint64_t* bonds, const u
     if (dE <= 0) {
       acc = 1;
     } else {
-      uint32_t u = orc_metropolis_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
+      uint32_t u = umode ? orc_msc_u(seed, stream, sweep, c, (uint64_t)(n >> 1))
+                         : orc_metropolis_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
       acc = (uint64_t)u < thr[dE / 4];
     }
     if (acc) {
@@ -253,10 +267,13 @@ static void half_sweep(const lat_t* g, int8_t* s, const uint64_t* bonds, const u
 }
 
 /* nsweeps sweeps starting at global sweep index sweep0.  E and M are the running
- * sums (in/out); traceE/traceM, if given, receive E and M after each sweep. */
-int orc_sweeps(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, double beta, uint64_t seed,
-               uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* E, int64_t* M,
-               int64_t* traceE, int64_t* traceM) {
+ * sums (in/out); traceE/traceM, if given, receive E and M after each sweep.
+ * umode 0 draws u from the Ising bit planes (purpose 0), umode 1 from the
+ * multi-spin coded words (purpose 3) -- the latter lets a scalar run reproduce
+ * one replica of a multi-spin coded sample. */
+int orc_sweeps_ex(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, double beta, uint64_t seed,
+                  uint32_t stream, uint32_t sweep0, int64_t nsweeps, int umode, int64_t* E, int64_t* M,
+                  int64_t* traceE, int64_t* traceM) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
   uint64_t thr[4];
@@ -264,14 +281,20 @@ int orc_sweeps(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, doubl
   for (int64_t t = 0; t < nsweeps; ++t) {
     uint32_t sweep = sweep0 + (uint32_t)t;
     int64_t de = 0, dm = 0;
-    half_sweep(&g, s, bonds, thr, seed, stream, sweep, 0, &de, &dm);
-    half_sweep(&g, s, bonds, thr, seed, stream, sweep, 1, &de, &dm);
+    half_sweep(&g, s, bonds, thr, seed, stream, sweep, 0, umode, &de, &dm);
+    half_sweep(&g, s, bonds, thr, seed, stream, sweep, 1, umode, &de, &dm);
     *E += de;
     *M += dm;
     if (traceE) traceE[t] = *E;
     if (traceM) traceM[t] = *M;
   }
   return 0;
+}
+
+int orc_sweeps(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, double beta, uint64_t seed,
+               uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* E, int64_t* M,
+               int64_t* traceE, int64_t* traceM) {
+  return orc_sweeps_ex(nd, L, s, bonds, beta, seed, stream, sweep0, nsweeps, 0, E, M, traceE, traceM);
 }
 
 /* ------------------------------------------------- multi-spin coded EA */
@@ -368,7 +391,7 @@ int orc_ea_sweeps(const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* 
 #pragma omp parallel for schedule(static)
         for (int64_t n = 0; n < g.N; ++n) {
           if (lat_colour(&g, n) != c) continue;
-          uint32_t u = orc_metropolis_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
+          uint32_t u = orc_msc_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
           uint32_t flip = 0;
           for (int j = 0; j < 32; ++j) {
             int sn = rep_spin(w[n], j);

@@ -88,6 +88,15 @@ def test_site_word_layout():
     assert oracle.hot_word(seed, stream, 0, 3 * 32 + 7) == u
 
 
+def test_msc_u_layout():
+    """The multi-spin coded u of index m is word m & 3 of the call m >> 2 (purpose 3)."""
+    seed, stream, t, c = 0x1234, 9, 3, 1
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for m in (0, 1, 3, 4, 1000, 77777):
+        w = oracle.philox4x32_10([m >> 2, t, c | (3 << 1), stream], key)
+        assert oracle.msc_u(seed, stream, t, c, m) == int(w[m & 3])
+
+
 def test_site_words_are_uniform():
     """Bits of the Metropolis words are balanced (5 sigma) across sites and sweeps."""
     seed = inputs.unit_seed(3)
@@ -417,7 +426,8 @@ def test_msc_replicas_equal_scalar_runs(ferro):
     for i in range(ns):
         for j in (0, 5, 17, 31):
             s = (1 - 2 * ((w0[i] >> np.uint32(j)) & np.uint32(1)).astype(np.int8)).astype(np.int8)
-            oracle.sweeps(dims, s, betas[pi[i][j]], 7, seed, stream=i, bonds=None if ferro else bonds[i])
+            oracle.sweeps(dims, s, betas[pi[i][j]], 7, seed, stream=i, bonds=None if ferro else bonds[i],
+                          msc_u_words=True)
             got = (1 - 2 * ((words[i] >> np.uint32(j)) & np.uint32(1)).astype(np.int8)).astype(np.int8)
             assert np.array_equal(got, s), (i, j)
 
