@@ -145,6 +145,46 @@ int spn_set_path(spn_handle h, int32_t path);
 int spn_launch_count(uint64_t* count);
 
 /* ------------------------------------------------------------------------
+ * Batched +-J Edwards-Anderson samples, multi-spin coded, with replica
+ * exchange (Sec. 4: many disorder realisations at once, asynchronous
+ * multi-spin coding; the exchange rule is Hukushima-Nemoto parallel tempering)
+ * ---------------------------------------------------------------------- */
+
+/* Create a batch of nsamples 3D +-J samples (model must be SPN_EA3D_PMJ) of
+ * extents dims, each holding 32 replicas at the 32 inverse temperatures betas
+ * (nbeta = 32, non-increasing, i.e. ascending temperature, each >= 1e-6).
+ * Replica j of sample i lives in bit j (its temperature slot) of the sample's
+ * 32-bit site words; on the device two samples share one uint64 word (64
+ * replicas per word).  couplings: bit-packed bonds [sample][3][ceil(N/64)]
+ * (copied).  The replica bits start from the hot-start words of Philox stream
+ * i; slot j starts at temperature j.  exchange_every = X > 0 exchanges the
+ * temperature pairs (k, k+1), k = e mod 2, e mod 2 + 2, ..., after every X-th
+ * sweep (step e), accepting iff (beta_k - beta_k+1)(E_k - E_k+1) >= 0 or
+ * u < floor(exp(that) 2^32); 0 = never.  A sample must fit one CTA's shared
+ * memory (5 bytes per site, about 44,000 sites: L <= 34).  SPN_E_ARG otherwise. */
+int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
+                     const double* betas, int nbeta, uint64_t seed, int exchange_every);
+
+/* Run nsweeps multi-spin coded sweeps (colour 0, then colour 1; the 32
+ * replicas of a site share its Philox word) with the exchanges due. */
+int spn_batch_sweep(spn_handle h, int64_t nsweeps);
+
+/* Site words [sample][N] (bit j = replica in slot j, 1 = spin -1). */
+int spn_batch_get_words(spn_handle h, uint32_t* out, size_t count);
+int spn_batch_set_words(spn_handle h, const uint32_t* in, size_t count);
+
+/* Temperature index of every slot, [sample][32]; set requires permutations. */
+int spn_batch_get_slots(spn_handle h, uint8_t* temp_of_slot, size_t count);
+int spn_batch_set_slots(spn_handle h, const uint8_t* temp_of_slot, size_t count);
+
+/* Energy (Eq. 1 with J = +-1) and magnetisation of every replica by slot,
+ * [sample][32], recomputed from the words on the device. */
+int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count);
+
+/* Accepted exchanges of pair (k, k+1) per sample, [sample][32] (entry 31 = 0). */
+int spn_batch_exchange_counts(spn_handle h, int64_t* acc, size_t count);
+
+/* ------------------------------------------------------------------------
  * Sweeps without device allocation
  * ---------------------------------------------------------------------- */
 

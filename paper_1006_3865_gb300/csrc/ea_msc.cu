@@ -1,0 +1,614 @@
+// Multi-spin coded +-J Edwards-Anderson spin glass with replica exchange
+// (Weigel, Sec. 4: many disorder realisations at once with asynchronous
+// multi-spin coding; parallel tempering is the batched workload of this
+// library, with the standard pair-exchange rule of Hukushima and Nemoto).
+//
+// Storage: a batch of S disorder samples, each with 32 replicas held in the
+// 32 temperature slots of one word per site.  In device memory two samples
+// share a 64-bit word (bits 0-31 sample 2p, bits 32-63 sample 2p+1), so each
+// uint64 carries 64 replicas.  Bonds: one byte per site and sample, bit d set
+// iff J(n, d) = -1 (forward bond to n + e_d), bit 3 + d iff J(n - e_d, d) = -1.
+//
+// k_ea_resident: one CTA per sample keeps the sample's whole word lattice and
+// bonds in shared memory (colour-separated: even-x and odd-x words per row) for
+// all sweeps of a launch.  Per site: the six neighbour words XOR the bond masks
+// give the unsatisfied bonds of all 32 replicas; a bit-sliced adder counts them;
+// replicas with dE = 12 - 4k > 0 accept iff u < thr(beta of their temperature,
+// dE).  The thresholds of one dE level grow with the temperature index, so the
+// accepting temperatures form a suffix: a 5-step search over the 32 sorted
+// thresholds gives its start and a 33-entry table, kept in step with the slot
+// permutation, turns it into the slot mask.  After every X-th sweep the CTA
+// counts unsatisfied bonds per replica, takes the exchange decisions of the
+// even or odd temperature pairs with host-built tables of
+// floor(exp(dbeta * dE) 2^32), and updates the permutation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "philox.cuh"
+#include "spn.h"
+#include "spn_internal.h"
+
+namespace spn {
+
+// Exact division by a launch-invariant 32-bit divisor (Granlund-Montgomery
+// round-up method): q = (t + ((n - t) >> 1)) >> s with t = umulhi(n, m).
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+static FastDiv fastdiv(uint32_t d) {
+  FastDiv f{d, 0, 0};
+  if (d <= 1) return f;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;  // l = ceil(log2 d) >= 1
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  f.s = l - 1;
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  if (f.d <= 1) return n;
+  const uint32_t t = __umulhi(n, f.m);
+  return (t + ((n - t) >> 1)) >> f.s;
+}
+
+struct EaArgs {
+  uint64_t* words;            // [pairs][N] uint64
+  const uint8_t* bonds;       // [S][N] bond bytes (site order)
+  uint8_t* temp_of_slot;      // [S][32]
+  unsigned long long* xacc;   // [S][32] accepted exchanges per pair
+  const uint32_t* xtab;       // concatenated exchange tables
+  int xoff[32];               // offset of pair k's table in xtab
+  int xlen[32];               // its length (d = 1 .. xlen), 0 with xalways[k]
+  uint32_t xalways;           // bit k: pair k has equal betas (always accept)
+  uint32_t thr[3][32];        // thr[q-1][t] for dE = 4q, non-decreasing in t
+  int Lx, Ly, Lz, N;
+  FastDiv div_h, div_ly;      // by Lx / 2 and by Ly
+  uint32_t sweep0;
+  int nsweeps;
+  int exchange_every;
+  int nsamples;
+  PhiloxKeys K;
+  int* err;
+};
+
+// colour-separated shared-memory word index of site (x, y, z)
+__device__ __forceinline__ int ea_slot(int x, int row, int h) { return (row * 2 + (x & 1)) * h + (x >> 1); }
+
+__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int N = a.N, h = a.Lx >> 1, nrow = a.Ly * a.Lz;
+  uint32_t* sp = reinterpret_cast<uint32_t*>(smem);           // N words
+  uint8_t* bb = smem + (size_t)N * 4;                         // N bond bytes
+  uint32_t* thr = reinterpret_cast<uint32_t*>(smem + (((size_t)N * 5 + 15) & ~(size_t)15));  // 96
+  uint32_t* suffix = thr + 96;                                // 33 (+3 pad)
+  uint32_t* ucount = suffix + 36;                             // 32 unsatisfied-bond counts
+  uint8_t* tos = reinterpret_cast<uint8_t*>(ucount + 32);     // 32 temp_of_slot
+  uint8_t* sot = tos + 32;                                    // 32 slot_of_temp
+  int* xcount = reinterpret_cast<int*>(sot + 32);             // 32 accepted exchanges this launch
+
+  const int sample = blockIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
+  const int pair = sample >> 1, half = sample & 1;
+  const uint32_t* gw = reinterpret_cast<const uint32_t*>(a.words + (size_t)pair * N) + half;
+  const uint8_t* gb = a.bonds + (size_t)sample * N;
+
+  // load the sample into the colour-separated layout
+  for (int n = tid; n < N; n += nth) {
+    const int x = n % a.Lx, row = n / a.Lx;
+    const int q = ea_slot(x, row, h);
+    sp[q] = gw[2 * (size_t)n];
+    bb[q] = gb[n];
+  }
+  for (int i = tid; i < 96; i += nth) thr[i] = a.thr[i / 32][i % 32];
+  if (tid < 32) {
+    tos[tid] = a.temp_of_slot[sample * 32 + tid];
+    xcount[tid] = 0;
+  }
+  __syncthreads();
+  if (tid < 32) sot[tos[tid]] = (uint8_t)tid;
+  __syncthreads();
+  if (tid < 32) {  // suffix[t0] = slots of temperatures t >= t0
+    uint32_t v = 1u << sot[tid];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t w = __shfl_down_sync(0xffffffffu, v, o);
+      if (tid + o < 32) v |= w;
+    }
+    suffix[tid] = v;
+    if (tid == 0) suffix[32] = 0;
+  }
+  __syncthreads();
+
+  const int halfN = N >> 1;
+  for (int it = 0; it < a.nsweeps; ++it) {
+    const uint32_t sweep = a.sweep0 + (uint32_t)it;
+    for (int c = 0; c < 2; ++c) {
+      for (int m = tid; m < halfN; m += nth) {
+        const uint32_t row = fdiv((uint32_t)m, a.div_h);
+        const int k = m - (int)row * h;
+        const uint32_t z = fdiv(row, a.div_ly);
+        const int y = (int)row - (int)z * a.Ly;
+        const int par = (c ^ (y + (int)z)) & 1;
+        const int x = 2 * k + par;
+        const int q = ea_slot(x, (int)row, h);
+        const uint32_t s = sp[q];
+        const uint32_t bits = bb[q];
+        // neighbours (other parity in the row for x; same parity in rows y +- 1, z +- 1)
+        const int xm = x == 0 ? a.Lx - 1 : x - 1, xp = x + 1 == a.Lx ? 0 : x + 1;
+        const int rym = y == 0 ? (int)row + a.Ly - 1 : (int)row - 1;
+        const int ryp = y + 1 == a.Ly ? (int)row - a.Ly + 1 : (int)row + 1;
+        const int rzm = z == 0 ? (int)row + nrow - a.Ly : (int)row - a.Ly;
+        const int rzp = (int)z + 1 == a.Lz ? (int)row - nrow + a.Ly : (int)row + a.Ly;
+        const uint32_t nxp = sp[ea_slot(xp, (int)row, h)], nxm = sp[ea_slot(xm, (int)row, h)];
+        const uint32_t nyp = sp[ea_slot(x, ryp, h)], nym = sp[ea_slot(x, rym, h)];
+        const uint32_t nzp = sp[ea_slot(x, rzp, h)], nzm = sp[ea_slot(x, rzm, h)];
+        // bond masks: bits 0..2 forward, 3..5 backward
+        const uint32_t ux = s ^ nxp ^ (0u - (bits & 1u));
+        const uint32_t uy = s ^ nyp ^ (0u - ((bits >> 1) & 1u));
+        const uint32_t uz = s ^ nzp ^ (0u - ((bits >> 2) & 1u));
+        const uint32_t vx = s ^ nxm ^ (0u - ((bits >> 3) & 1u));
+        const uint32_t vy = s ^ nym ^ (0u - ((bits >> 4) & 1u));
+        const uint32_t vz = s ^ nzm ^ (0u - ((bits >> 5) & 1u));
+        // bit-sliced count of unsatisfied bonds k = s0 + 2 s1 + 4 s2 (0..6)
+        const uint32_t x1 = ux ^ uy ^ uz, y1 = (ux & uy) | (uz & (ux ^ uy));
+        const uint32_t x2 = vx ^ vy ^ vz, y2 = (vx & vy) | (vz & (vx ^ vy));
+        const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
+        const uint32_t s1 = y1 ^ y2 ^ cc, s2 = (y1 & y2) | (cc & (y1 ^ y2));
+        // u of this site (one word per site, shared by the 32 replicas)
+        const U4 P = philox10((uint32_t)m >> 2, sweep, (uint32_t)c | (3u << 1), (uint32_t)sample, a.K);
+        const uint32_t u = u4_word(P, m & 3);
+        // accepting temperatures per level: count thresholds <= u (sorted), suffix mask
+        uint32_t A[3];
+#pragma unroll
+        for (int lv = 0; lv < 3; ++lv) {
+          const uint32_t* tl = thr + 32 * lv;
+          int cnt = 0;
+          cnt += (tl[cnt + 15] <= u) ? 16 : 0;
+          cnt += (tl[cnt + 7] <= u) ? 8 : 0;
+          cnt += (tl[cnt + 3] <= u) ? 4 : 0;
+          cnt += (tl[cnt + 1] <= u) ? 2 : 0;
+          cnt += (tl[cnt] <= u) ? 1 : 0;
+          cnt += (cnt == 31 && tl[31] <= u) ? 1 : 0;  // all 32 thresholds <= u
+          A[lv] = suffix[cnt];
+        }
+        // k >= 3: dE <= 0; k = 2: dE = 4 (level 0); k = 1: 8 (level 1); k = 0: 12 (level 2)
+        const uint32_t always = s2 | (s0 & s1);
+        const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
+        const uint32_t acc = always | (k2 & A[0]) | (k1 & A[1]) | (k0 & A[2]);
+        sp[q] = s ^ acc;
+      }
+      __syncthreads();
+    }
+    const int X = a.exchange_every;
+    if (X > 0 && ((int64_t)sweep + 1) % X == 0) {
+      const uint32_t e = (uint32_t)(((int64_t)sweep + 1) / X - 1);
+      // unsatisfied forward bonds of every replica, bit-sliced per thread
+      if (tid < 32) ucount[tid] = 0;
+      __syncthreads();
+      uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int n = tid; n < N; n += nth) {
+        const int x = n % a.Lx, r = n / a.Lx;
+        const int y = r % a.Ly, z = r / a.Ly;
+        const int q = ea_slot(x, r, h);
+        const uint32_t s = sp[q];
+        const uint32_t bits = bb[q];
+        const int xp = x + 1 == a.Lx ? 0 : x + 1;
+        const int ryp = y + 1 == a.Ly ? r - a.Ly + 1 : r + 1;
+        const int rzp = z + 1 == a.Lz ? r - nrow + a.Ly : r + a.Ly;
+        const uint32_t w3[3] = {s ^ sp[ea_slot(xp, r, h)] ^ (0u - (bits & 1u)),
+                                s ^ sp[ea_slot(x, ryp, h)] ^ (0u - ((bits >> 1) & 1u)),
+                                s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u))};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          uint32_t carry = w3[d];
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const uint32_t t = cnt[b] & carry;
+            cnt[b] ^= carry;
+            carry = t;
+          }
+        }
+      }
+      // per-replica totals (at most 255 per thread: 3 bonds x 85 sites per thread at most)
+      for (int j = 0; j < 32; ++j) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) v |= ((cnt[b] >> j) & 1u) << b;
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if (lane == 0 && v) atomicAdd(&ucount[j], v);
+      }
+      __syncthreads();
+      if (tid < 32) {
+        // pairs (kk, kk+1) with kk = e mod 2, e mod 2 + 2, ...; lane tid takes kk = tid
+        const int kk = tid;
+        bool accept = false;
+        const bool mine = kk + 1 < 32 && ((kk & 1) == (int)(e & 1));
+        if (mine) {
+          const int sa = sot[kk], sb = sot[kk + 1];
+          const int d = (int)ucount[sb] - (int)ucount[sa];  // (E_k - E_k+1) = -2 d
+          if (((a.xalways >> kk) & 1u) || d <= 0) {
+            accept = true;
+          } else if (d <= a.xlen[kk]) {
+            const U4 P = philox10((uint32_t)kk >> 2, e, kExchange << 1, (uint32_t)sample, a.K);
+            accept = u4_word(P, kk & 3) < a.xtab[a.xoff[kk] + d - 1];
+          }
+        }
+        // every lane reads the current map before any swap is written
+        const int s_self = sot[tid];
+        const bool up = __shfl_up_sync(0xffffffffu, accept ? 1 : 0, 1) != 0;  // lane kk+1 learns of kk's swap
+        const int s_below = __shfl_up_sync(0xffffffffu, s_self, 1);
+        const int s_above = __shfl_down_sync(0xffffffffu, s_self, 1);
+        int new_slot = s_self;
+        if (mine && accept) new_slot = s_above;
+        if (tid > 0 && up) new_slot = s_below;
+        __syncwarp();
+        sot[tid] = (uint8_t)new_slot;
+        __syncwarp();
+        tos[new_slot] = (uint8_t)tid;
+        if (mine && accept) xcount[kk] += 1;
+        uint32_t v = 1u << new_slot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t w = __shfl_down_sync(0xffffffffu, v, o);
+          if (tid + o < 32) v |= w;
+        }
+        suffix[tid] = v;
+      }
+      __syncthreads();
+    }
+  }
+
+  // write back
+  uint32_t* gwo = reinterpret_cast<uint32_t*>(a.words + (size_t)pair * N) + half;
+  for (int n = tid; n < N; n += nth) {
+    const int x = n % a.Lx, row = n / a.Lx;
+    gwo[2 * (size_t)n] = sp[ea_slot(x, row, h)];
+  }
+  if (tid < 32) {
+    a.temp_of_slot[sample * 32 + tid] = tos[tid];
+    a.xacc[sample * 32 + tid] += (unsigned long long)xcount[tid];
+  }
+}
+
+// hot start: the replica bits of site n are its 32-bit hot-start word, bit
+// 31 - q = bit (m & 31) of plane q = word q & 3 of R(8 (m >> 5) + q / 4, 0, c | 1 << 1, sample)
+__global__ void k_ea_init(uint64_t* words, int Lx, int Ly, int N, int nsamples, PhiloxKeys K) {
+  const int64_t total = (int64_t)nsamples * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int sample = (int)(i / N);
+    const int n = (int)(i - (int64_t)sample * N);
+    const int x = n % Lx, r = n / Lx, y = r % Ly, z = r / Ly;
+    const int c = (x + y + z) & 1;
+    const uint32_t m = (uint32_t)n >> 1;
+    uint32_t u = 0;
+    for (uint32_t call = 0; call < 8; ++call) {
+      const U4 P = philox10(8u * (m >> 5) + call, 0u, (uint32_t)c | (kInit << 1), (uint32_t)sample, K);
+      const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) u |= ((pl[j] >> (m & 31)) & 1u) << (31 - (4 * call + j));
+    }
+    uint32_t* w = reinterpret_cast<uint32_t*>(words + (size_t)(sample >> 1) * N) + (sample & 1);
+    w[2 * (size_t)n] = u;
+  }
+}
+
+// per-replica E and M by slot: E = 2 U - 3N (U unsatisfied forward bonds), M = N - 2 (#spins -1)
+__global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, int Lx, int Ly, int Lz, int N,
+                                 long long* E, long long* M) {
+  __shared__ unsigned long long su[32], sm[32];
+  const int sample = blockIdx.x, tid = threadIdx.x;
+  if (tid < 32) su[tid] = sm[tid] = 0;
+  __syncthreads();
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(words + (size_t)(sample >> 1) * N) + (sample & 1);
+  const uint8_t* bb = bonds + (size_t)sample * N;
+  for (int n = tid; n < N; n += blockDim.x) {
+    const int x = n % Lx, r = n / Lx, y = r % Ly, z = r / Ly;
+    const uint32_t s = w[2 * (size_t)n];
+    const int np[3] = {n - x + (x + 1 == Lx ? 0 : x + 1), n + ((y + 1 == Ly ? 0 : y + 1) - y) * Lx,
+                       n + ((z + 1 == Lz ? 0 : z + 1) - z) * Lx * Ly};
+    for (int j = 0; j < 32; ++j) {
+      unsigned long long un = 0;
+      for (int d = 0; d < 3; ++d) {
+        const uint32_t bit = ((s ^ w[2 * (size_t)np[d]]) >> j) & 1u;
+        un += bit ^ ((bb[n] >> d) & 1u);
+      }
+      if (un) atomicAdd(&su[j], un);
+      if ((s >> j) & 1u) atomicAdd(&sm[j], 1ull);
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    E[sample * 32 + tid] = 2 * (long long)su[tid] - 3 * (long long)N;
+    M[sample * 32 + tid] = (long long)N - 2 * (long long)sm[tid];
+  }
+}
+
+}  // namespace spn
+
+// ---------------------------------------------------------------- the ABI
+
+struct EaBatch {
+  int L[3];
+  int N, nsamples, exchange_every;
+  uint64_t seed;
+  double betas[32];
+  uint64_t* d_words = nullptr;
+  uint8_t* d_bonds = nullptr;
+  uint8_t* d_tos = nullptr;
+  unsigned long long* d_xacc = nullptr;
+  uint32_t* d_xtab = nullptr;
+  int* d_err = nullptr;
+  spn::EaArgs args{};
+  size_t smem = 0;
+  int threads = 0;
+};
+
+namespace {
+
+int ea_fail(int code, const char* msg) {
+  spn::set_last_error(msg);
+  return code;
+}
+
+size_t ea_smem(int N) { return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4; }
+
+}  // namespace
+
+void spn_ea_free(EaBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_words);
+  cudaFree(b->d_bonds);
+  cudaFree(b->d_tos);
+  cudaFree(b->d_xacc);
+  cudaFree(b->d_xtab);
+  cudaFree(b->d_err);
+  delete b;
+}
+
+extern "C" {
+
+int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
+                     const double* betas, int nbeta, uint64_t seed, int exchange_every) {
+  if (!out || !dims || !couplings || !betas) return ea_fail(SPN_E_ARG, "NULL argument");
+  *out = nullptr;
+  if (model != SPN_EA3D_PMJ) return ea_fail(SPN_E_ARG, "batches are multi-spin coded SPN_EA3D_PMJ samples");
+  if (nsamples < 1) return ea_fail(SPN_E_ARG, "nsamples must be >= 1");
+  if (nbeta != 32) return ea_fail(SPN_E_ARG, "the temperature ladder has exactly 32 betas (one per word bit)");
+  if (exchange_every < 0) return ea_fail(SPN_E_ARG, "exchange_every must be >= 0");
+  for (int d = 0; d < 3; ++d)
+    if (dims[d] < 2 || (dims[d] & 1)) return ea_fail(SPN_E_ARG, "every extent must be even and >= 2");
+  const int64_t N = (int64_t)dims[0] * dims[1] * dims[2];
+  if (ea_smem((int)std::min<int64_t>(N, 1 << 30)) > 227 * 1024 || N > (1 << 20))
+    return ea_fail(SPN_E_ARG, "a sample must fit in one CTA's shared memory (about 44,000 sites)");
+  for (int t = 0; t < 32; ++t) {
+    if (!(betas[t] >= 1e-6) || !std::isfinite(betas[t]))
+      return ea_fail(SPN_E_ARG, "ladder betas must be finite and >= 1e-6");
+    if (t > 0 && betas[t] > betas[t - 1])
+      return ea_fail(SPN_E_ARG, "betas must be non-increasing (temperatures ascending)");
+  }
+  EaBatch* b = new (std::nothrow) EaBatch;
+  if (!b) return ea_fail(SPN_E_NOMEM, "host allocation failed");
+  for (int d = 0; d < 3; ++d) b->L[d] = dims[d];
+  b->N = (int)N;
+  b->nsamples = nsamples;
+  b->exchange_every = exchange_every;
+  b->seed = seed;
+  std::memcpy(b->betas, betas, sizeof b->betas);
+  auto bail = [&](int code, const char* msg) {
+    spn_ea_free(b);
+    return ea_fail(code, msg);
+  };
+  const int pairs = (nsamples + 1) / 2;
+  // bond bytes: bit d forward J(n,d) = -1, bit 3+d backward J(n - e_d, d) = -1
+  std::vector<uint8_t> bb((size_t)nsamples * N, 0);
+  const int64_t nw = (N + 63) / 64;
+  const uint64_t* J = static_cast<const uint64_t*>(couplings);
+  for (int s = 0; s < nsamples; ++s) {
+    for (int64_t n = 0; n < N; ++n) {
+      const int x = (int)(n % dims[0]), y = (int)((n / dims[0]) % dims[1]), z = (int)(n / ((int64_t)dims[0] * dims[1]));
+      const int64_t back[3] = {n - x + (x == 0 ? dims[0] - 1 : x - 1),
+                               n + (int64_t)((y == 0 ? dims[1] - 1 : y - 1) - y) * dims[0],
+                               n + (int64_t)((z == 0 ? dims[2] - 1 : z - 1) - z) * dims[0] * dims[1]};
+      uint8_t v = 0;
+      for (int d = 0; d < 3; ++d) {
+        const uint64_t* Jd = J + ((int64_t)s * 3 + d) * nw;
+        if ((Jd[n >> 6] >> (n & 63)) & 1) v |= (uint8_t)(1u << d);
+        if ((Jd[back[d] >> 6] >> (back[d] & 63)) & 1) v |= (uint8_t)(8u << d);
+      }
+      bb[(size_t)s * N + n] = v;
+    }
+  }
+  // exchange tables: pair k, d = 1 .. len: floor(exp((b_k - b_k+1) * (-2d)) 2^32)
+  std::vector<uint32_t> tab;
+  spn::EaArgs& A = b->args;
+  A.xalways = 0;
+  for (int k = 0; k < 31; ++k) {
+    const double db = betas[k] - betas[k + 1];
+    A.xoff[k] = (int)tab.size();
+    A.xlen[k] = 0;
+    if (db == 0.0) {
+      A.xalways |= 1u << k;
+      continue;
+    }
+    for (int64_t d = 1;; ++d) {
+      const double D = db * (double)(-2 * d);
+      const uint64_t t = (uint64_t)std::floor(std::exp(D) * 4294967296.0);
+      if (t == 0) break;
+      tab.push_back((uint32_t)t);
+      if (tab.size() > (size_t)1 << 22) return bail(SPN_E_ARG, "ladder spacing too small for the exchange tables");
+    }
+    A.xlen[k] = (int)tab.size() - A.xoff[k];
+  }
+  A.xoff[31] = (int)tab.size();
+  A.xlen[31] = 0;
+  if (tab.empty()) tab.push_back(0);
+  for (int q = 1; q <= 3; ++q)
+    for (int t = 0; t < 32; ++t) {
+      const uint64_t v = spn::boltzmann_threshold(betas[t], 4 * q);
+      A.thr[q - 1][t] = (uint32_t)std::min<uint64_t>(v, 0xffffffffull);  // < 2^32 for beta >= 1e-6
+    }
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_words, (size_t)pairs * N * 8)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_bonds, bb.size())) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_tos, (size_t)nsamples * 32)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_xacc, (size_t)nsamples * 32 * 8)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_xtab, tab.size() * 4)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  if ((e = cudaMalloc(&b->d_err, 4)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  std::vector<uint8_t> tos((size_t)nsamples * 32);
+  for (size_t i = 0; i < tos.size(); ++i) tos[i] = (uint8_t)(i % 32);
+  if (cudaMemcpy(b->d_bonds, bb.data(), bb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_tos, tos.data(), tos.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_xtab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->d_xacc, 0, (size_t)nsamples * 32 * 8) != cudaSuccess ||
+      cudaMemset(b->d_words, 0, (size_t)pairs * N * 8) != cudaSuccess || cudaMemset(b->d_err, 0, 4) != cudaSuccess)
+    return bail(SPN_E_CUDA, "copying the batch to the device");
+  const spn::PhiloxKeys K = spn::philox_keys(seed);
+  spn::k_ea_init<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsamples * N / 256 + 1, spn::device_sm_count() * 32)), 256>>>(
+      b->d_words, dims[0], dims[1], (int)N, nsamples, K);
+  spn::count_launches(1);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(SPN_E_CUDA, cudaGetErrorString(e));
+  A.words = b->d_words;
+  A.bonds = b->d_bonds;
+  A.temp_of_slot = b->d_tos;
+  A.xacc = b->d_xacc;
+  A.xtab = b->d_xtab;
+  A.Lx = dims[0];
+  A.Ly = dims[1];
+  A.Lz = dims[2];
+  A.N = (int)N;
+  A.div_h = spn::fastdiv((uint32_t)(dims[0] / 2));
+  A.div_ly = spn::fastdiv((uint32_t)dims[1]);
+  A.exchange_every = exchange_every;
+  A.nsamples = nsamples;
+  A.K = K;
+  A.err = b->d_err;
+  b->smem = ea_smem((int)N);
+  b->threads = N >= 16384 ? 1024 : (N >= 4096 ? 512 : 256);
+  spn_ctx* h = new (std::nothrow) spn_ctx;
+  if (!h) return bail(SPN_E_NOMEM, "host allocation failed");
+  h->model = model;
+  h->seed = seed;
+  h->ea = b;
+  *out = h;
+  return SPN_OK;
+}
+
+int spn_batch_sweep(spn_handle h, int64_t nsweeps) {
+  if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
+  if (nsweeps < 0) return ea_fail(SPN_E_ARG, "nsweeps must be >= 0");
+  EaBatch* b = h->ea;
+  if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return ea_fail(SPN_E_ARG, "sweep counter would exceed 2^32");
+  cudaFuncSetAttribute(spn::k_ea_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  int64_t done = 0;
+  while (done < nsweeps) {  // bounded launches keep each kernel well under a second
+    const int n = (int)std::min<int64_t>(nsweeps - done, 2000);
+    spn::EaArgs a = b->args;
+    a.sweep0 = (uint32_t)(h->sweeps + done);
+    a.nsweeps = n;
+    spn::k_ea_resident<<<b->nsamples, b->threads, b->smem, h->st>>>(a);
+    spn::count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ea_fail(SPN_E_CUDA, cudaGetErrorString(e));
+    done += n;
+  }
+  h->sweeps += (uint64_t)nsweeps;
+  return SPN_OK;
+}
+
+int spn_batch_get_words(spn_handle h, uint32_t* out, size_t count) {
+  if (!h || !h->ea || !out) return ea_fail(SPN_E_ARG, "bad arguments");
+  EaBatch* b = h->ea;
+  if (count != (size_t)b->nsamples * b->N) return ea_fail(SPN_E_ARG, "count must be nsamples * N");
+  const int pairs = (b->nsamples + 1) / 2;
+  std::vector<uint64_t> w((size_t)pairs * b->N);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(w.data(), b->d_words, w.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ea_fail(SPN_E_CUDA, "reading the words");
+  for (int s = 0; s < b->nsamples; ++s)
+    for (int n = 0; n < b->N; ++n)
+      out[(size_t)s * b->N + n] = (uint32_t)(w[(size_t)(s >> 1) * b->N + n] >> (32 * (s & 1)));
+  return SPN_OK;
+}
+
+int spn_batch_set_words(spn_handle h, const uint32_t* in, size_t count) {
+  if (!h || !h->ea || !in) return ea_fail(SPN_E_ARG, "bad arguments");
+  EaBatch* b = h->ea;
+  if (count != (size_t)b->nsamples * b->N) return ea_fail(SPN_E_ARG, "count must be nsamples * N");
+  const int pairs = (b->nsamples + 1) / 2;
+  std::vector<uint64_t> w((size_t)pairs * b->N, 0);
+  for (int s = 0; s < b->nsamples; ++s)
+    for (int n = 0; n < b->N; ++n)
+      w[(size_t)(s >> 1) * b->N + n] |= (uint64_t)in[(size_t)s * b->N + n] << (32 * (s & 1));
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(b->d_words, w.data(), w.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    return ea_fail(SPN_E_CUDA, "writing the words");
+  return SPN_OK;
+}
+
+int spn_batch_get_slots(spn_handle h, uint8_t* temp_of_slot, size_t count) {
+  if (!h || !h->ea || !temp_of_slot) return ea_fail(SPN_E_ARG, "bad arguments");
+  if (count != (size_t)h->ea->nsamples * 32) return ea_fail(SPN_E_ARG, "count must be nsamples * 32");
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(temp_of_slot, h->ea->d_tos, count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ea_fail(SPN_E_CUDA, "reading the slot maps");
+  return SPN_OK;
+}
+
+int spn_batch_set_slots(spn_handle h, const uint8_t* temp_of_slot, size_t count) {
+  if (!h || !h->ea || !temp_of_slot) return ea_fail(SPN_E_ARG, "bad arguments");
+  if (count != (size_t)h->ea->nsamples * 32) return ea_fail(SPN_E_ARG, "count must be nsamples * 32");
+  for (int s = 0; s < h->ea->nsamples; ++s) {
+    uint32_t seen = 0;
+    for (int j = 0; j < 32; ++j) {
+      const uint8_t t = temp_of_slot[s * 32 + j];
+      if (t >= 32 || ((seen >> t) & 1u)) return ea_fail(SPN_E_ARG, "each sample's map must be a permutation of 0..31");
+      seen |= 1u << t;
+    }
+  }
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(h->ea->d_tos, temp_of_slot, count, cudaMemcpyHostToDevice) != cudaSuccess)
+    return ea_fail(SPN_E_CUDA, "writing the slot maps");
+  return SPN_OK;
+}
+
+int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count) {
+  if (!h || !h->ea || !E || !M) return ea_fail(SPN_E_ARG, "bad arguments");
+  EaBatch* b = h->ea;
+  if (count != (size_t)b->nsamples * 32) return ea_fail(SPN_E_ARG, "count must be nsamples * 32");
+  long long *dE = nullptr, *dM = nullptr;
+  if (cudaMalloc(&dE, count * 8) != cudaSuccess || cudaMalloc(&dM, count * 8) != cudaSuccess) {
+    cudaFree(dE);
+    return ea_fail(SPN_E_NOMEM, "cudaMalloc");
+  }
+  spn::k_ea_observables<<<b->nsamples, 256, 0, h->st>>>(b->d_words, b->d_bonds, b->L[0], b->L[1], b->L[2], b->N, dE,
+                                                       dM);
+  spn::count_launches(1);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess) e = cudaMemcpy(E, dE, count * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(M, dM, count * 8, cudaMemcpyDeviceToHost);
+  cudaFree(dE);
+  cudaFree(dM);
+  return e == cudaSuccess ? SPN_OK : ea_fail(SPN_E_CUDA, cudaGetErrorString(e));
+}
+
+int spn_batch_exchange_counts(spn_handle h, int64_t* acc, size_t count) {
+  if (!h || !h->ea || !acc) return ea_fail(SPN_E_ARG, "bad arguments");
+  if (count != (size_t)h->ea->nsamples * 32) return ea_fail(SPN_E_ARG, "count must be nsamples * 32");
+  if (cudaStreamSynchronize(h->st) != cudaSuccess ||
+      cudaMemcpy(acc, h->ea->d_xacc, count * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ea_fail(SPN_E_CUDA, "reading the exchange counts");
+  return SPN_OK;
+}
+
+}  // extern "C"

@@ -142,6 +142,7 @@ int recompute(spn_ctx* h, int64_t* E, int64_t* M) {
 void destroy(spn_ctx* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
+  spn_ea_free(h->ea);
   cudaFree(h->spins[0]);
   cudaFree(h->spins[1]);
   cudaFree(h->d_bonds);
@@ -220,6 +221,7 @@ int spn_create(spn_handle* out, int model, const int32_t* dims, const void* coup
 
 int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (!(beta >= 0.0)) return fail(SPN_E_ARG, "beta must be >= 0 (got %g)", beta);
   if (nsweeps < 0) return fail(SPN_E_ARG, "nsweeps must be >= 0");
   if (nsweeps == 0) return SPN_OK;
@@ -255,6 +257,7 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
 
 int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
   if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   int rc = fold(h);
   if (rc) return rc;
   *E = h->E;
@@ -264,11 +267,13 @@ int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
 
 int spn_recompute(spn_handle h, int64_t* E, int64_t* M) {
   if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   return recompute(h, E, M);
 }
 
 int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n) {
   if (!h || !n || cap < 0 || (cap > 0 && (!E || !M))) return fail(SPN_E_ARG, "bad trace arguments");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   int rc = fold(h);
   if (rc) return rc;
   const int64_t total = (int64_t)h->traceE.size();
@@ -283,6 +288,7 @@ int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n) {
 
 int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
   if (!h || !host_out) return fail(SPN_E_ARG, "NULL argument");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
   SPN_CUDA(cudaMemcpyAsync(host_out, h->spins[h->cur], bytes, cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync");
   SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
@@ -291,6 +297,7 @@ int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
 
 int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
   if (!h || !host_in) return fail(SPN_E_ARG, "NULL argument");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
   int rc = fold(h);
   if (rc) return rc;
@@ -304,6 +311,7 @@ int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
 
 int spn_reinit(spn_handle h, uint64_t seed, uint32_t stream, int init) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (init != SPN_INIT_HOT && init != SPN_INIT_COLD) return fail(SPN_E_ARG, "unknown init %d", init);
   int rc = fold(h);
   if (rc) return rc;
@@ -357,6 +365,7 @@ int spn_destroy(spn_handle h) {
 
 int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t seg) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   const int ty = h->g.nd == 3 ? tile_y : 1;
   if (step_slices < 0 || seg < 0) return fail(SPN_E_ARG, "negative tiling parameter");
   if (!spn::stream_path_supported(h->g, ty))
@@ -377,6 +386,7 @@ int spn_get_path(spn_handle h, int32_t* path) {
 
 int spn_set_path(spn_handle h, int32_t path) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (path == spn::kPathStream) {
     if (!spn::stream_path_supported(h->g, h->tile_y))
       return fail(SPN_E_ARG, "streaming path needs Lx %% 64 == 0, a dividing band and no bonds");

@@ -60,8 +60,12 @@ uint64_t launch_count();
 
 }  // namespace spn
 
+struct EaBatch;                // multi-spin coded EA batch (ea_msc.cu)
+void spn_ea_free(EaBatch* b);
+
 struct spn_ctx {
   int model = 0;
+  EaBatch* ea = nullptr;  // set for batch handles (spn_create_batch)
   spn::Lattice g;
   uint64_t seed = 0;
   uint32_t stream_id = 0;

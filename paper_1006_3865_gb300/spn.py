@@ -68,6 +68,14 @@ _SIGNATURES = {
     "spn_reinit": (_c.c_int, [_vp, _u64, _u32, _c.c_int]),
     "spn_launch_count": (_c.c_int, [_P(_u64)]),
     "spn_sweep_noalloc": (_c.c_int, [_c.c_int, _vp, _vp, _dbl, _u64, _u32, _u32, _i64, _vp, _vp]),
+    "spn_create_batch": (_c.c_int, [_P(_vp), _c.c_int, _vp, _c.c_int, _vp, _vp, _c.c_int, _u64, _c.c_int]),
+    "spn_batch_sweep": (_c.c_int, [_vp, _i64]),
+    "spn_batch_get_words": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_batch_set_words": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_batch_get_slots": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_batch_set_slots": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_batch_energies": (_c.c_int, [_vp, _vp, _vp, _sz]),
+    "spn_batch_exchange_counts": (_c.c_int, [_vp, _vp, _sz]),
 }
 
 
@@ -235,3 +243,69 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class EABatch:
+    """Multi-spin coded +-J EA samples with replica exchange (spn_create_batch)."""
+
+    def __init__(self, dims, couplings: np.ndarray, betas, seed: int, exchange_every: int = 10):
+        self._lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.N = int(np.prod(self.dims))
+        J = np.ascontiguousarray(couplings, dtype=np.uint64)
+        self.nsamples = int(J.shape[0])
+        b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+        d = _dims(dims)
+        h = _vp()
+        _check(self._lib.spn_create_batch(_c.byref(h), SPN_EA3D_PMJ, _ptr(d), self.nsamples, _ptr(J), _ptr(b),
+                                          int(b.size), seed, int(exchange_every)))
+        self._h = h
+
+    def sweep(self, nsweeps: int):
+        _check(self._lib.spn_batch_sweep(self._h, int(nsweeps)))
+
+    def words(self) -> np.ndarray:
+        out = np.empty((self.nsamples, self.N), dtype=np.uint32)
+        _check(self._lib.spn_batch_get_words(self._h, _ptr(out), out.size))
+        return out
+
+    def set_words(self, words: np.ndarray):
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        _check(self._lib.spn_batch_set_words(self._h, _ptr(w), w.size))
+
+    def slots(self) -> np.ndarray:
+        out = np.empty((self.nsamples, 32), dtype=np.uint8)
+        _check(self._lib.spn_batch_get_slots(self._h, _ptr(out), out.size))
+        return out
+
+    def set_slots(self, temp_of_slot: np.ndarray):
+        t = np.ascontiguousarray(temp_of_slot, dtype=np.uint8)
+        _check(self._lib.spn_batch_set_slots(self._h, _ptr(t), t.size))
+
+    def energies(self) -> tuple[np.ndarray, np.ndarray]:
+        E = np.empty((self.nsamples, 32), np.int64)
+        M = np.empty((self.nsamples, 32), np.int64)
+        _check(self._lib.spn_batch_energies(self._h, _ptr(E), _ptr(M), E.size))
+        return E, M
+
+    def exchange_counts(self) -> np.ndarray:
+        out = np.empty((self.nsamples, 32), np.int64)
+        _check(self._lib.spn_batch_exchange_counts(self._h, _ptr(out), out.size))
+        return out
+
+    def set_stream(self, stream):
+        _check(self._lib.spn_set_stream(self._h, _stream_ptr(stream)))
+
+    def sync(self):
+        _check(self._lib.spn_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.spn_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
