@@ -145,6 +145,55 @@ int spn_set_path(spn_handle h, int32_t path);
 int spn_launch_count(uint64_t* count);
 
 /* ------------------------------------------------------------------------
+ * Batched runs of many independent lattices (uneven sizes, temperatures and
+ * sweep counts; Sec. 3 procedure for each)
+ * ---------------------------------------------------------------------- */
+
+/* One lattice of a batched run: model SPN_ISING2D or SPN_ISING3D, extents
+ * dims (dims[2] ignored in 2D), inverse temperature beta >= 0, nsweeps sweeps
+ * from the hot start of Philox (seed, stream). */
+typedef struct spn_job {
+  int32_t model;
+  int32_t dims[3];
+  double beta;
+  int64_t nsweeps;
+  uint64_t seed;
+  uint32_t stream;
+  int32_t reserved; /* 0 */
+} spn_job;
+
+typedef struct spn_multi_ctx* spn_multi;
+
+enum spn_run_mode {
+  SPN_RUN_BATCHED = 0, /* one persistent resident launch per lattice shape, all shapes concurrent, CUDA graph */
+  SPN_RUN_LOOP = 1     /* the plain per-instance launch loop (one launch per sweep) */
+};
+
+/* Allocate the lattices and traces of njobs jobs (copied).  Every lattice must
+ * fit the resident kernel: Lx in {2, 4, 8, 16, 32} or a multiple of 64, and its
+ * bits (N / 8 bytes) in a cluster of at most 8 CTAs x 200 KB; SPN_E_ARG
+ * otherwise. */
+int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs);
+
+/* Run every job from its hot start (asynchronous on the run's stream).  Both
+ * modes give bit-identical lattices and traces; the first batched run captures
+ * a CUDA graph that later runs replay. */
+int spn_multi_run(spn_multi m, int mode);
+
+/* Wait for the run; SPN_E_TIMEOUT if a bounded device wait ran out. */
+int spn_multi_sync(spn_multi m);
+
+/* Result of job `job` after a run (synchronises): its int8 lattice (bytes =
+ * N, or spins = NULL) and E, M after each of its first min(cap, nsweeps)
+ * sweeps (or E = M = NULL). */
+int spn_multi_result(spn_multi m, int job, int8_t* spins, size_t bytes, int64_t* E, int64_t* M, int64_t cap);
+
+/* Use an existing CUDA stream for the runs (the graph is captured again). */
+int spn_multi_set_stream(spn_multi m, void* cuda_stream);
+
+int spn_multi_destroy(spn_multi m);
+
+/* ------------------------------------------------------------------------
  * Batched +-J Edwards-Anderson samples, multi-spin coded, with replica
  * exchange (Sec. 4: many disorder realisations at once, asynchronous
  * multi-spin coding; the exchange rule is Hukushima-Nemoto parallel tempering)

@@ -1,0 +1,343 @@
+// Batched runs of many independent lattices (uneven sizes, temperatures and
+// sweep counts) with one persistent, shared-memory-resident kernel.
+//
+// k_resident<ND, CLUSTER> pops instances from a queue (longest first).  A CTA,
+// or a thread-block cluster of CS CTAs when the lattice is too large for one
+// CTA, holds the whole lattice bit-packed in shared memory -- even-x and odd-x
+// words per row, the layout of the streaming kernel -- and runs every sweep of
+// the instance there: hot start, E/M, colour 0, colour 1, the per-sweep E/M
+// trace, and the int8 result at the end.  Each CTA of a cluster owns a band of
+// rows and reads its neighbours' boundary rows through distributed shared
+// memory; a cluster barrier separates the two colours.  The update order, the
+// Philox planes and the thresholds are those of every other path, so results
+// are bit-identical to one-instance-at-a-time runs.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "philox.cuh"
+#include "spn_internal.h"
+#include "sweep_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace spn {
+
+namespace {
+
+// Metropolis decision of a partial (Lx < 64) or full word whose site bit i is
+// lane o + i of its Philox group: planes are shifted right by o.
+template <int NC>
+__device__ __forceinline__ uint32_t lazy_accept_shifted(uint32_t acc, const uint32_t (&cls)[NC], const DevThr& T,
+                                                        const PhiloxKeys& K, uint32_t c0, uint32_t sweep, uint32_t c2,
+                                                        uint32_t stream_id, uint32_t o) {
+  uint32_t eq[NC];
+  uint32_t pend = 0;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const bool always = (T.always >> (q + 1)) & 1u;
+    acc |= always ? cls[q] : 0u;
+    eq[q] = always ? 0u : cls[q];
+    pend |= eq[q];
+  }
+#pragma unroll 1
+  for (uint32_t call = 0; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
+    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
+    const uint32_t planes[4] = {P.x >> o, P.y >> o, P.z >> o, P.w >> o};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = planes[j];
+      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const uint32_t tm = 0u - ((T.t[q + 1] >> bit) & 1u);
+        acc |= eq[q] & ~u & tm;
+        eq[q] &= ~(u ^ tm);
+      }
+    }
+    pend = 0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pend |= eq[q];
+  }
+  return acc;
+}
+
+template <int ND, bool CLUSTER>
+__global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int s_idx;
+  __shared__ long long s_em[2];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int Lx = a.Lx, Ly = a.Ly, Lz = ND == 3 ? a.Lz : 1;
+  const int nrow = Ly * Lz;
+  const int W = Lx >= 64 ? Lx >> 6 : 1;
+  const int vb = Lx >= 64 ? 32 : Lx >> 1;  // valid bits per word
+  const uint32_t vmask = vb == 32 ? 0xffffffffu : ((1u << vb) - 1u);
+  int CS = 1, rank = 0;
+  if constexpr (CLUSTER) {
+    CS = (int)cg::this_cluster().num_blocks();
+    rank = (int)cg::this_cluster().block_rank();
+  }
+  const int rpc = nrow / CS;  // rows owned by this CTA
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem);  // rpc rows x 2W words
+  uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)rpc * 2 * W);
+
+  for (int i = tid; i < 256; i += nth) {
+    uint32_t lo = 0, hi = 0;
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t eb = ((i >> k) & 1) ? 0xffu : 0x01u;
+      const uint32_t ob = ((i >> (4 + k)) & 1) ? 0xffu : 0x01u;
+      const uint32_t pair = eb | (ob << 8);
+      if (k < 2) lo |= pair << (16 * k); else hi |= pair << (16 * (k - 2));
+    }
+    lut[i] = make_uint2(lo, hi);
+  }
+
+  auto sync_all = [&]() {
+    if constexpr (CLUSTER) cg::this_cluster().sync(); else __syncthreads();
+  };
+  // word pointer of global row r (possibly in another CTA of the cluster)
+  auto row_ptr = [&](int r) -> uint32_t* {
+    const int owner = r / rpc, lr = r - owner * rpc;
+    uint32_t* base = bits + (size_t)lr * 2 * W;
+    if constexpr (CLUSTER) {
+      if (owner != rank) return cg::this_cluster().map_shared_rank(base, owner);
+    }
+    return base;
+  };
+
+  while (true) {
+    // the cluster's rank-0 CTA takes the next instance from the queue
+    if (rank == 0 && tid == 0) s_idx = atomicAdd(a.counter, 1);
+    sync_all();
+    int idx;
+    if constexpr (CLUSTER) {
+      idx = *cg::this_cluster().map_shared_rank(&s_idx, 0);
+    } else {
+      idx = s_idx;
+    }
+    sync_all();  // everybody has read s_idx before it is overwritten
+    if (idx >= a.ninst) break;
+    const ResInst in = a.inst[a.order[idx]];
+    const PhiloxKeys K = philox_keys(in.seed);
+    const int r0 = rank * rpc;
+
+    // ---- load: hot start from Philox or the int8 lattice
+    const int wordsOwn = rpc * 2 * W;
+    for (int it = tid; it < wordsOwn; it += nth) {
+      const int lr = it / (2 * W);
+      const int rem = it - lr * 2 * W;
+      const int p = rem / W, j = rem - p * W;
+      const int r = r0 + lr;
+      const int y = r % Ly, z = r / Ly;
+      uint32_t wv = 0;
+      if (in.init_hot) {
+        const int c = (y + z + p) & 1;
+        const uint32_t mstart = (uint32_t)(Lx >> 1) * (uint32_t)r + 32u * (uint32_t)j;
+        const uint32_t plane0 = philox10(8u * (mstart >> 5), 0u, (uint32_t)c | (kInit << 1), in.stream, K).x;
+        wv = (plane0 >> (mstart & 31)) & vmask;
+      } else {
+        const int8_t* row = in.spins + (int64_t)r * Lx;
+        for (int i = 0; i < vb; ++i) wv |= (row[64 * j + 2 * i + p] < 0 ? 1u : 0u) << i;
+      }
+      bits[(size_t)lr * 2 * W + p * W + j] = wv;
+    }
+    if (tid < 2) s_em[tid] = 0;
+    sync_all();
+
+    // anti-aligned counts of word j (parity par) of row r
+    auto counts = [&](int r, int j, int par, uint32_t b, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
+      const uint32_t* row = row_ptr(r);
+      const uint32_t* other = row + (1 - par) * W;
+      uint32_t left, right;
+      if (W >= 2) {
+        const int jm = j == 0 ? W - 1 : j - 1, jp = j + 1 == W ? 0 : j + 1;
+        if (par == 0) {
+          right = other[j];
+          left = __funnelshift_l(other[jm], other[j], 1);
+        } else {
+          left = other[j];
+          right = __funnelshift_r(other[j], other[jp], 1);
+        }
+      } else {  // the row is one word: rotate within vb bits
+        const uint32_t o = other[0];
+        if (par == 0) {
+          right = o;
+          left = ((o << 1) | (o >> (vb - 1))) & vmask;
+        } else {
+          left = o;
+          right = ((o >> 1) | (o << (vb - 1))) & vmask;
+        }
+      }
+      const int y = r % Ly, z = r / Ly;
+      const int rym = y == 0 ? r + Ly - 1 : r - 1, ryp = y + 1 == Ly ? r - Ly + 1 : r + 1;
+      const uint32_t ym = row_ptr(rym)[par * W + j], yp = row_ptr(ryp)[par * W + j];
+      if constexpr (ND == 3) {
+        const int rzm = z == 0 ? r + nrow - Ly : r - Ly, rzp = z + 1 == Lz ? r - nrow + Ly : r + Ly;
+        const uint32_t zm = row_ptr(rzm)[par * W + j], zp = row_ptr(rzp)[par * W + j];
+        count6(b ^ left, b ^ right, b ^ ym, b ^ yp, b ^ zm, b ^ zp, s0, s1, s2);
+      } else {
+        count4(b ^ left, b ^ right, b ^ ym, b ^ yp, s0, s1, s2);
+      }
+    };
+
+    // ---- E and M of the start (E = -sum over colour-1 sites of (2ND - 2k))
+    {
+      long long e = 0, m = 0;
+      const int items = rpc * W;
+      for (int it = tid; it < items; it += nth) {
+        const int lr = it / W, j = it - lr * W;
+        const int r = r0 + lr;
+        const int y = r % Ly, z = r / Ly;
+        for (int p = 0; p < 2; ++p) {
+          const uint32_t b = bits[(size_t)lr * 2 * W + p * W + j];
+          m += vb - 2 * __popc(b & vmask);
+          if (((y + z + p) & 1) == 1) {  // colour 1
+            uint32_t s0, s1, s2;
+            counts(r, j, p, b, s0, s1, s2);
+            e += -2LL * ND * vb + 2LL * (__popc(s0 & vmask) + 2 * __popc(s1 & vmask) + 4 * __popc(s2 & vmask));
+          }
+        }
+      }
+      warp_reduce_add2(e, m);
+      if ((tid & 31) == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&s_em[0]), (unsigned long long)e);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&s_em[1]), (unsigned long long)m);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        atomicAdd(in.em0 + 0, (unsigned long long)s_em[0]);
+        atomicAdd(in.em0 + 1, (unsigned long long)s_em[1]);
+      }
+    }
+
+    // ---- sweeps
+    const int items = rpc * W;
+    const int rounds = (items + nth - 1) / nth;
+    for (int t = 0; t < in.nsweeps; ++t) {
+      const uint32_t sweep = in.sweep0 + (uint32_t)t;
+      int de = 0, dm = 0;
+      for (int c = 0; c < 2; ++c) {
+        for (int q = 0; q < rounds; ++q) {  // warp-uniform trip count (votes in the decision)
+          const int it = tid + q * nth;
+          const bool live = it < items;
+          const int itc = live ? it : 0;
+          const int lr = itc / W, j = itc - lr * W;
+          const int r = r0 + lr;
+          const int y = r % Ly, z = r / Ly;
+          const int par = (y + z + c) & 1;
+          uint32_t* wp = bits + (size_t)lr * 2 * W + par * W + j;
+          const uint32_t b = *wp;
+          uint32_t s0, s1, s2;
+          counts(r, j, par, b, s0, s1, s2);
+          const uint32_t valid = live ? vmask : 0u;
+          uint32_t cls[ND];
+          const uint32_t acc0 = classes<ND>(s0, s1, s2, valid, cls);
+          const uint32_t mstart = (uint32_t)(Lx >> 1) * (uint32_t)r + 32u * (uint32_t)j;
+          const uint32_t flips = lazy_accept_shifted<ND>(acc0, cls, in.T, K, 8u * (mstart >> 5), sweep,
+                                                          (uint32_t)c | (kMetropolis << 1), in.stream, mstart & 31);
+          if (live) {
+            tally<ND>(flips, b, s0, s1, s2, de, dm);
+            *wp = b ^ flips;  // only this thread reads or writes this colour-c word in this phase
+          }
+        }
+        sync_all();
+      }
+      long long lde = de, ldm = dm;
+      warp_reduce_add2(lde, ldm);
+      if ((tid & 31) == 0 && (lde | ldm)) {
+        atomicAdd(in.trace + 2 * t + 0, (unsigned long long)lde);
+        atomicAdd(in.trace + 2 * t + 1, (unsigned long long)ldm);
+      }
+    }
+
+    // ---- result: int8 lattice of the own rows
+    for (int it = tid; it < rpc * W; it += nth) {
+      const int lr = it / W, j = it - lr * W;
+      const int r = r0 + lr;
+      const uint32_t E = bits[(size_t)lr * 2 * W + j], O = bits[(size_t)lr * 2 * W + W + j];
+      int8_t* row = in.spins + (int64_t)r * Lx;
+      if (Lx >= 64) {
+        uint4* dst = reinterpret_cast<uint4*>(row + 64 * j);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const uint2 lo = lut[((E >> (8 * v)) & 0xfu) | (((O >> (8 * v)) & 0xfu) << 4)];
+          const uint2 hi = lut[((E >> (8 * v + 4)) & 0xfu) | (((O >> (8 * v + 4)) & 0xfu) << 4)];
+          dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+        }
+      } else {
+        for (int i = 0; i < vb; ++i) {
+          row[2 * i] = ((E >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
+          row[2 * i + 1] = ((O >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
+        }
+      }
+    }
+    sync_all();  // the bits are reused by the next instance
+  }
+}
+
+}  // namespace
+
+bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs) {
+  if (!(Lx == 2 || Lx == 4 || Lx == 8 || Lx == 16 || Lx == 32 || (Lx % 64 == 0))) return false;
+  const int nrow = Ly * (nd == 3 ? Lz : 1);
+  if (cs < 1 || cs > 8 || nrow % cs) return false;
+  return resident_smem(nd, Lx, Ly, Lz, cs) <= 200 * 1024;
+}
+
+size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs) {
+  const int W = Lx >= 64 ? Lx / 64 : 1;
+  const int nrow = Ly * (nd == 3 ? Lz : 1);
+  return (size_t)(nrow / cs) * 2 * W * 4 + 256 * 8;
+}
+
+int resident_cluster_size(int nd, int Lx, int Ly, int Lz) {
+  for (int cs = 1; cs <= 8; cs *= 2)
+    if (resident_supported(nd, Lx, Ly, Lz, cs)) return cs;
+  return 0;
+}
+
+cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, cudaStream_t st) {
+  const size_t smem = resident_smem(nd, a.Lx, a.Ly, a.Lz, cs);
+  void (*fn)(ResArgs) = nullptr;
+  if (nd == 3)
+    fn = cs > 1 ? k_resident<3, true> : k_resident<3, false>;
+  else
+    fn = cs > 1 ? k_resident<2, true> : k_resident<2, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ctas / cs * cs), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (cs > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  e = cudaLaunchKernelEx(&cfg, fn, a);
+  count_launches(1);
+  return e;
+}
+
+int resident_max_ctas(int nd, int cs, int threads, size_t smem) {
+  void (*fn)(ResArgs) = nullptr;
+  if (nd == 3)
+    fn = cs > 1 ? k_resident<3, true> : k_resident<3, false>;
+  else
+    fn = cs > 1 ? k_resident<2, true> : k_resident<2, false>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (per_sm <= 0) per_sm = 1;
+  return per_sm * device_sm_count();
+}
+
+}  // namespace spn

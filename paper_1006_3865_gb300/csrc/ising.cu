@@ -35,6 +35,7 @@
 
 #include "philox.cuh"
 #include "spn_internal.h"
+#include "sweep_common.cuh"
 
 namespace spn {
 
@@ -74,223 +75,6 @@ int device_sm_count() {
     if (sms <= 0) sms = 1;
   }
   return sms;
-}
-
-// ------------------------------------------------------------------ helpers
-
-__device__ __forceinline__ void warp_reduce_add2(long long& a, long long& b) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-}
-
-// Block-wide sum of (a, b), one atomic pair per warp.
-__device__ __forceinline__ void block_accumulate(long long a, long long b, unsigned long long* out2) {
-  warp_reduce_add2(a, b);
-  if ((threadIdx.x & 31) == 0 && (a | b)) {
-    atomicAdd(out2 + 0, (unsigned long long)a);
-    atomicAdd(out2 + 1, (unsigned long long)b);
-  }
-}
-
-// Site of colour c with within-colour index m: n = 2m or 2m + 1 (Lx even, so
-// both share y and z).
-__device__ __forceinline__ int64_t site_of(int64_t m, int c, int Lx, int Ly) {
-  const int64_t n0 = 2 * m;
-  const int64_t r = n0 / Lx;  // y + Ly * z
-  const int y = (int)(r % Ly);
-  const int z = (int)(r / Ly);
-  return n0 + ((c ^ (y + z)) & 1);
-}
-
-// Metropolis decision for 32 sites.  cls[q-1]: sites whose move has dE = 4q > 0;
-// acc: sites already accepted (dE <= 0).  Plane p of the group (counter c0 + p/4)
-// holds bit 31 - p of every site's u; a site of class q is accepted iff
-// u < T.t[q] (or T.always has bit q).  Planes are compared from the most
-// significant down until no site is undecided anywhere in the warp.  Must be
-// called by all 32 lanes of a warp together.
-template <int NC>
-__device__ __forceinline__ uint32_t lazy_accept(uint32_t acc, const uint32_t (&cls)[NC], const DevThr& T,
-                                                const PhiloxKeys& K, uint32_t c0, uint32_t sweep, uint32_t c2,
-                                                uint32_t stream_id) {
-  uint32_t eq[NC];
-  uint32_t pend = 0;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    const bool always = (T.always >> (q + 1)) & 1u;
-    acc |= always ? cls[q] : 0u;
-    eq[q] = always ? 0u : cls[q];
-    pend |= eq[q];
-  }
-#pragma unroll 1
-  for (uint32_t call = 0; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
-    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
-    const uint32_t planes[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t u = planes[j];
-      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        if ((T.t[q + 1] >> bit) & 1u) {  // threshold bit 1: a 0 bit of u decides "below"
-          acc |= eq[q] & ~u;
-          eq[q] &= u;
-        } else {
-          eq[q] &= ~u;
-        }
-      }
-    }
-    pend = 0;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) pend |= eq[q];
-  }
-  return acc;
-}
-
-// First stage of the decision: planes 0..7 (two Philox calls, drawn together)
-// for every word.  On return acc holds the sites already accepted and eq[q]
-// the sites of class q+1 whose u still ties the threshold on all 8 planes.
-template <int NC>
-__device__ __forceinline__ void decide_first(uint32_t& acc, uint32_t (&eq)[NC], const uint32_t (&cls)[NC],
-                                             const DevThr& T, const PhiloxKeys& K, uint32_t c0, uint32_t sweep,
-                                             uint32_t c2, uint32_t stream_id) {
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    const bool always = (T.always >> (q + 1)) & 1u;
-    acc |= always ? cls[q] : 0u;
-    eq[q] = always ? 0u : cls[q];
-  }
-  const U4 P0 = philox10(c0, sweep, c2, stream_id, K);
-  const U4 P1 = philox10(c0 + 1u, sweep, c2, stream_id, K);
-  const uint32_t planes[8] = {P0.x, P0.y, P0.z, P0.w, P1.x, P1.y, P1.z, P1.w};
-  // Compare the top 8 bits of u with those of the threshold, least significant
-  // plane first: "below" after plane p is maj(~u_p, t_p, below so far); "equal"
-  // keeps the sites whose bits all match.
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    uint32_t below = 0, equal = 0xffffffffu;
-#pragma unroll
-    for (int p = 7; p >= 0; --p) {
-      const uint32_t tm = 0u - ((T.t[q + 1] >> (31 - p)) & 1u);
-      const uint32_t nu = ~planes[p];
-      below = (nu & tm) | (nu & below) | (tm & below);
-      equal &= ~(planes[p] ^ tm);
-    }
-    acc |= eq[q] & below;
-    eq[q] &= equal;
-  }
-}
-
-// Remaining planes 8..31 for sites still tied after the first stage; returns
-// the sites among eq that are accepted.  Called by whole warps (votes).
-template <int NC>
-__device__ __forceinline__ uint32_t decide_tail(uint32_t (&eq)[NC], const DevThr& T, const PhiloxKeys& K,
-                                               uint32_t c0, uint32_t sweep, uint32_t c2, uint32_t stream_id) {
-  uint32_t acc = 0, pend = 0;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) pend |= eq[q];
-#pragma unroll 1
-  for (uint32_t call = 2; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
-    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
-    const uint32_t planes[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t u = planes[j];
-      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        if ((T.t[q + 1] >> bit) & 1u) {
-          acc |= eq[q] & ~u;
-          eq[q] &= u;
-        } else {
-          eq[q] &= ~u;
-        }
-      }
-    }
-    pend = 0;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) pend |= eq[q];
-  }
-  return acc;
-}
-
-// Classes of one 32-site word from the anti-aligned counts k = s0 + 2 s1 + 4 s2
-// out of 2*ND neighbours: cls[q-1] = sites with dE = 4q > 0; returns the sites
-// with dE <= 0 (always accepted).
-template <int ND>
-__device__ __forceinline__ uint32_t classes(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t valid,
-                                            uint32_t (&cls)[ND]) {
-  if constexpr (ND == 2) {
-    const uint32_t hi = s1 | s2;  // k >= 2
-    cls[0] = s0 & ~hi & valid;    // k = 1, dE = 4
-    cls[1] = ~s0 & ~hi & valid;   // k = 0, dE = 8
-    return hi & valid;
-  } else {
-    cls[0] = ~s0 & s1 & ~s2 & valid;  // k = 2, dE = 4
-    cls[1] = s0 & ~s1 & ~s2 & valid;  // k = 1, dE = 8
-    cls[2] = ~s0 & ~s1 & ~s2 & valid;  // k = 0, dE = 12
-    return (s2 | (s0 & s1)) & valid;   // k >= 3
-  }
-}
-
-// dE = sum 4 (ND - k) and dM = sum -2 s over the accepted sites of a word.
-template <int ND>
-__device__ __forceinline__ void tally(uint32_t acc, uint32_t b, uint32_t s0, uint32_t s1, uint32_t s2, int& de,
-                                      int& dm) {
-  const int nf = __popc(acc);
-  de += 4 * (ND * nf - (__popc(acc & s0) + 2 * __popc(acc & s1) + 4 * __popc(acc & s2)));
-  dm += 2 * (2 * __popc(acc & b) - nf);
-}
-
-// Bit-sliced count of anti-aligned neighbours: inputs are the neighbour words
-// XOR-ed with the centre (1 = anti-aligned); output k = s0 + 2 s1 + 4 s2.
-__device__ __forceinline__ void count4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t& s0, uint32_t& s1,
-                                       uint32_t& s2) {
-  const uint32_t h1 = a ^ b, c1 = a & b, h2 = c ^ d, c2 = c & d;
-  const uint32_t c3 = h1 & h2;
-  s0 = h1 ^ h2;
-  s1 = c1 ^ c2 ^ c3;
-  s2 = c1 & c2;
-}
-
-__device__ __forceinline__ void count6(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e, uint32_t f,
-                                       uint32_t& s0, uint32_t& s1, uint32_t& s2) {
-  const uint32_t x1 = a ^ b ^ c, y1 = (a & b) | (c & (a ^ b));
-  const uint32_t x2 = d ^ e ^ f, y2 = (d & e) | (f & (d ^ e));
-  s0 = x1 ^ x2;
-  const uint32_t cc = x1 & x2;
-  s1 = y1 ^ y2 ^ cc;
-  s2 = (y1 & y2) | (cc & (y1 ^ y2));
-}
-
-// Classes and decision for one 32-site word: b = spin bits, k = (s0, s1, s2)
-// anti-aligned counts out of 2*ND neighbours, valid = sites present.  Returns
-// the accepted sites; adds dE = sum 4 (ND - k) and dM = sum -2 s of the flips.
-template <int ND>
-__device__ __forceinline__ uint32_t decide_word(uint32_t b, uint32_t s0, uint32_t s1, uint32_t s2, uint32_t valid,
-                                                const DevThr& T, const PhiloxKeys& K, uint32_t c0, uint32_t sweep,
-                                                uint32_t c2, uint32_t stream_id, int& de, int& dm) {
-  uint32_t acc, cls[ND];
-  if constexpr (ND == 2) {
-    // k = 0 -> dE = 8 (class 2), k = 1 -> dE = 4 (class 1), k >= 2 -> dE <= 0
-    const uint32_t hi = s1 | s2;
-    cls[0] = s0 & ~hi & valid;
-    cls[1] = ~s0 & ~hi & valid;
-    acc = hi & valid;
-  } else {
-    // k = 0 -> class 3, 1 -> class 2, 2 -> class 1, k >= 3 -> dE <= 0
-    cls[0] = ~s0 & s1 & ~s2 & valid;
-    cls[1] = s0 & ~s1 & ~s2 & valid;
-    cls[2] = ~s0 & ~s1 & ~s2 & valid;
-    acc = (s2 | (s0 & s1)) & valid;
-  }
-  acc = lazy_accept<ND>(acc, cls, T, K, c0, sweep, c2, stream_id);
-  const int nf = __popc(acc);
-  de += 4 * (ND * nf - (__popc(acc & s0) + 2 * __popc(acc & s1) + 4 * __popc(acc & s2)));
-  dm += 2 * (2 * __popc(acc & b) - nf);
-  return acc;
 }
 
 // ---------------------------------------------------------------- init / E, M
@@ -444,48 +228,6 @@ cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, c
 // ---------------------------------------------------------- streaming sweep
 
 namespace {
-
-constexpr unsigned kWaitLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bulk asynchronous copy global -> shared (TMA engine, non-tensor form); both
-// addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Four int8 spins (0x01 / 0xFF) -> four bits (1 = -1) at bits 0..3 in byte
-// order: bit 1 of byte k moves to bit 28 + k in one multiply (no carries).
-__device__ __forceinline__ uint32_t sign_bits4(uint32_t w) { return ((w & 0x02020202u) * 0x08102040u) >> 28; }
 
 struct StreamArgs {
   const int8_t* in;

@@ -53,6 +53,34 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st);
 
+// One instance of a batched resident run (batched.cu).
+struct ResInst {
+  int8_t* spins;               // device int8 lattice, result written back
+  unsigned long long* trace;   // [nsweeps][2] per-sweep (dE, dM), zeroed by the caller
+  unsigned long long* em0;     // [2] start (E, M), zeroed by the caller
+  uint64_t seed;
+  uint32_t stream;
+  uint32_t sweep0;
+  int nsweeps;
+  int init_hot;                // 1: hot start from Philox; 0: start from `spins`
+  DevThr T;
+};
+
+struct ResArgs {
+  const ResInst* inst;  // all instances of one launch share nd and extents
+  int ninst;
+  const int* order;     // queue order (longest first)
+  int* counter;         // queue head, zeroed by the caller
+  int Lx, Ly, Lz;
+  int* err;
+};
+
+bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs);
+size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs);
+int resident_cluster_size(int nd, int Lx, int Ly, int Lz);  // 0: does not fit a cluster of <= 8 CTAs
+int resident_max_ctas(int nd, int cs, int threads, size_t smem);
+cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, cudaStream_t st);
+
 int device_sm_count();
 void count_launches(uint64_t n);
 void set_last_error(const char* msg);  // the thread's spn_last_error() message

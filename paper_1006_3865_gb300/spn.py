@@ -34,6 +34,9 @@ SPN_EA3D_PMJ = 3
 SPN_INIT_HOT = 0
 SPN_INIT_COLD = 1
 
+SPN_RUN_BATCHED = 0
+SPN_RUN_LOOP = 1
+
 PATH_GENERIC = 0
 PATH_STREAM = 1
 PATH_RESIDENT = 2
@@ -68,6 +71,12 @@ _SIGNATURES = {
     "spn_reinit": (_c.c_int, [_vp, _u64, _u32, _c.c_int]),
     "spn_launch_count": (_c.c_int, [_P(_u64)]),
     "spn_sweep_noalloc": (_c.c_int, [_c.c_int, _vp, _vp, _dbl, _u64, _u32, _u32, _i64, _vp, _vp]),
+    "spn_multi_create": (_c.c_int, [_P(_vp), _vp, _c.c_int]),
+    "spn_multi_run": (_c.c_int, [_vp, _c.c_int]),
+    "spn_multi_sync": (_c.c_int, [_vp]),
+    "spn_multi_result": (_c.c_int, [_vp, _c.c_int, _vp, _sz, _vp, _vp, _i64]),
+    "spn_multi_set_stream": (_c.c_int, [_vp, _vp]),
+    "spn_multi_destroy": (_c.c_int, [_vp]),
     "spn_create_batch": (_c.c_int, [_P(_vp), _c.c_int, _vp, _c.c_int, _vp, _vp, _c.c_int, _u64, _c.c_int]),
     "spn_batch_sweep": (_c.c_int, [_vp, _i64]),
     "spn_batch_get_words": (_c.c_int, [_vp, _vp, _sz]),
@@ -77,6 +86,14 @@ _SIGNATURES = {
     "spn_batch_energies": (_c.c_int, [_vp, _vp, _vp, _sz]),
     "spn_batch_exchange_counts": (_c.c_int, [_vp, _vp, _sz]),
 }
+
+
+class Job(ctypes.Structure):
+    """spn_job: one lattice of a batched run."""
+
+    _fields_ = [("model", ctypes.c_int32), ("dims", ctypes.c_int32 * 3), ("beta", ctypes.c_double),
+                ("nsweeps", ctypes.c_int64), ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
+                ("reserved", ctypes.c_int32)]
 
 
 class SpnError(RuntimeError):
@@ -302,6 +319,53 @@ class EABatch:
     def close(self):
         if getattr(self, "_h", None):
             _check(self._lib.spn_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """Batched run of many independent lattices (spn_multi_*)."""
+
+    def __init__(self, jobs):
+        """jobs: iterable of (model, dims, beta, nsweeps, seed, stream)."""
+        self._lib = load()
+        arr = (Job * len(jobs))()
+        self.shapes = []
+        for k, (model, dims, beta, nsweeps, seed, stream) in enumerate(jobs):
+            d = list(dims) + [1] * (3 - len(dims))
+            arr[k] = Job(model, (ctypes.c_int32 * 3)(*d), float(beta), int(nsweeps), int(seed), int(stream), 0)
+            self.shapes.append((tuple(int(x) for x in dims), int(nsweeps)))
+        h = _vp()
+        _check(self._lib.spn_multi_create(_c.byref(h), ctypes.cast(arr, _vp), len(jobs)))
+        self._h = h
+
+    def run(self, mode: int = SPN_RUN_BATCHED):
+        _check(self._lib.spn_multi_run(self._h, mode))
+
+    def sync(self):
+        _check(self._lib.spn_multi_sync(self._h))
+
+    def set_stream(self, stream):
+        _check(self._lib.spn_multi_set_stream(self._h, _stream_ptr(stream)))
+
+    def result(self, job: int, spins: bool = True, trace: bool = True):
+        dims, ns = self.shapes[job]
+        N = int(np.prod(dims))
+        s = np.empty(N, np.int8) if spins else None
+        E = np.empty(ns, np.int64) if trace else None
+        M = np.empty(ns, np.int64) if trace else None
+        _check(self._lib.spn_multi_result(self._h, job, _ptr(s), N if spins else 0, _ptr(E), _ptr(M),
+                                          ns if trace else 0))
+        return s, E, M
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.spn_multi_destroy(self._h))
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,94 @@
+"""Batched runs of many uneven lattices: the persistent resident kernel (one
+CTA, or a cluster of CTAs sharing rows through distributed shared memory)
+against the CPU oracle and against the per-instance launch loop, bit for bit."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import lib
+from paper_1006_3865_gb300 import inputs, spn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    lib()
+
+
+def _jobs_small():
+    rng = np.random.default_rng(11)
+    jobs = []
+    shapes = [(2, (32, 32)), (2, (64, 64)), (2, (128, 64)), (2, (256, 256)), (2, (16, 8)), (2, (2, 2)),
+              (3, (16, 16, 16)), (3, (64, 8, 4)), (2, (64, 64)), (2, (1024, 1024))]
+    for k, (nd, dims) in enumerate(shapes):
+        model = spn.SPN_ISING2D if nd == 2 else spn.SPN_ISING3D
+        T = float(rng.uniform(1.5, 3.5)) if nd == 2 else float(rng.uniform(3.5, 5.5))
+        jobs.append((model, dims, 1.0 / T, int(rng.integers(3, 40)), inputs.unit_seed(900 + k), k))
+    return jobs
+
+
+def test_batched_matches_oracle():
+    jobs = _jobs_small()
+    m = spn.Multi(jobs)
+    m.run(spn.SPN_RUN_BATCHED)
+    for k, (model, dims, beta, ns, seed, stream) in enumerate(jobs):
+        s, E, M = m.result(k)
+        so = oracle.init_hot(dims, seed, stream)
+        _, _, tE, tM = oracle.sweeps(dims, so, beta, ns, seed, stream=stream)
+        assert np.array_equal(s, so), (k, dims)
+        assert np.array_equal(E, tE) and np.array_equal(M, tM), (k, dims)
+    m.close()
+
+
+def test_batched_equals_loop_and_replays():
+    jobs = _jobs_small()
+    m = spn.Multi(jobs)
+    m.run(spn.SPN_RUN_LOOP)
+    loop = [m.result(k) for k in range(len(jobs))]
+    for _ in range(2):  # the second batched run replays the captured graph
+        m.run(spn.SPN_RUN_BATCHED)
+        for k in range(len(jobs)):
+            s, E, M = m.result(k)
+            assert np.array_equal(s, loop[k][0]) and np.array_equal(E, loop[k][1]) and np.array_equal(M, loop[k][2])
+    m.close()
+
+
+def test_cluster_resident_2048():
+    """L = 2048 needs a 4-CTA cluster (512 KB of bits); compare with the loop."""
+    jobs = [(spn.SPN_ISING2D, (2048, 2048), 1.0 / 2.3, 6, inputs.unit_seed(1), 0),
+            (spn.SPN_ISING2D, (2048, 2048), 1.0 / 1.7, 5, inputs.unit_seed(2), 1)]
+    m = spn.Multi(jobs)
+    m.run(spn.SPN_RUN_LOOP)
+    loop = [m.result(k) for k in range(2)]
+    m.run(spn.SPN_RUN_BATCHED)
+    for k in range(2):
+        s, E, M = m.result(k)
+        assert np.array_equal(s, loop[k][0]) and np.array_equal(E, loop[k][1])
+    s, E, M = m.result(1)
+    so = oracle.init_hot((2048, 2048), jobs[1][4], 1)
+    _, _, tE, tM = oracle.sweeps((2048, 2048), so, jobs[1][2], 5, jobs[1][4], stream=1)
+    assert np.array_equal(s, so) and np.array_equal(E, tE)
+    m.close()
+
+
+def test_uneven_batch_subset_against_loop():
+    """A 64-instance slice of the uneven workload (L = 2^k, k in 5..11)."""
+    inst = inputs.uneven_batch(64)
+    jobs = [(spn.SPN_ISING2D, i.dims, i.beta, min(i.nsweeps, 60), i.seed, i.stream) for i in inst]
+    m = spn.Multi(jobs)
+    m.run(spn.SPN_RUN_BATCHED)
+    bat = [m.result(k) for k in range(len(jobs))]
+    m.run(spn.SPN_RUN_LOOP)
+    for k in range(len(jobs)):
+        s, E, M = m.result(k)
+        assert np.array_equal(s, bat[k][0]) and np.array_equal(E, bat[k][1]) and np.array_equal(M, bat[k][2]), k
+    m.close()
+
+
+def test_rejects_unsupported_shapes():
+    with pytest.raises(spn.SpnError):
+        spn.Multi([(spn.SPN_ISING2D, (48, 48), 0.4, 3, 1, 0)])
