@@ -234,6 +234,69 @@ int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count);
 int spn_batch_exchange_counts(spn_handle h, int64_t* acc, size_t count);
 
 /* ------------------------------------------------------------------------
+ * Served requests with continuous batching
+ * ---------------------------------------------------------------------- */
+
+/* A simulation request.  Ising (SPN_ISING2D / SPN_ISING3D): beta, nsweeps from
+ * the hot start of (seed, stream).  EA (SPN_EA3D_PMJ, one disorder sample):
+ * betas = 32 ladder betas, couplings = [3][ceil(N/64)] bond words, replica
+ * exchange every exchange_every sweeps, seed; stream is ignored (sample 0).
+ * Everything pointed to is copied by spn_submit. */
+typedef struct spn_request {
+  int32_t model;
+  int32_t dims[3];
+  double beta;
+  const double* betas;
+  int64_t nsweeps;
+  uint64_t seed;
+  uint32_t stream;
+  int32_t exchange_every;
+  const void* couplings;
+} spn_request;
+
+/* state: 0 queued, 1 admitted (running), 2 done, 3 failed (status = error code).
+ * E, M: final energy and magnetisation (EA: the replica at the lowest
+ * temperature).  Times in seconds on the server's monotonic clock. */
+typedef struct spn_result {
+  int32_t status;
+  int32_t state;
+  int64_t sweeps;
+  int64_t E;
+  int64_t M;
+  double t_submit;
+  double t_admit;
+  double t_done;
+} spn_result;
+
+typedef struct spn_server_ctx* spn_server;
+
+/* Start a server that admits jobs while their device memory (lattices, ping-
+ * pong buffers, accumulators) fits hbm_budget_bytes.  A scheduler thread
+ * advances every admitted job by a window of sweeps per round; jobs of the same
+ * lattice shape share one persistent resident launch, the others run on a pool
+ * of streams, and jobs arriving during a round join the next one. */
+int spn_server_create(spn_server* out, size_t hbm_budget_bytes);
+
+/* Queue a request (copied) and return its ticket at once; never waits for the
+ * GPU.  SPN_E_BUDGET if the job alone exceeds the budget. */
+int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 once the ticket's job is finished or failed; out
+ * (may be NULL) receives its state and times. */
+int spn_poll(spn_server s, uint64_t ticket, int* done, spn_result* out);
+
+/* The result of a finished job: Ising N int8 spins; EA N uint32 replica words
+ * followed by 32 bytes temp_of_slot. */
+int spn_server_fetch(spn_server s, uint64_t ticket, void* out, size_t bytes);
+
+/* Aggregate counters: attempted spin flips done, seconds the scheduler spent in
+ * rounds, rounds, device bytes currently charged to the budget. */
+int spn_server_stats(spn_server s, uint64_t* attempts, double* busy_seconds, uint64_t* rounds, size_t* used_bytes);
+
+/* Stop accepting work, finish the admitted jobs, release everything. */
+int spn_server_destroy(spn_server s);
+
+/* ------------------------------------------------------------------------
  * Sweeps without device allocation
  * ---------------------------------------------------------------------- */
 

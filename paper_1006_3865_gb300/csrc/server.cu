@@ -1,0 +1,533 @@
+// Request server with continuous batching (spn_server_* ABI).
+//
+// Clients submit jobs at any time; spn_submit copies the request and returns a
+// ticket without touching the GPU.  A scheduler thread works in rounds: it
+// admits queued jobs while their device memory fits the HBM budget (stream-
+// ordered allocations), then advances every admitted job by one window of
+// sweeps.  Ising jobs whose lattice fits the resident kernel share one
+// persistent launch per lattice shape; other Ising shapes and the
+// multi-spin coded EA jobs get their own launches on a pool of streams, so the
+// whole round overlaps on the device.  Jobs that arrive during a round join the
+// next one.  A finished job's lattice and energy are copied to host memory, its
+// device memory returns to the budget, and spn_poll reports it with its
+// submit / admit / done times.  A window only splits the sweep sequence, and
+// the random numbers are counters of (seed, stream, sweep, site), so a job's
+// result does not depend on what else runs with it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "spn.h"
+#include "spn_internal.h"
+
+namespace {
+
+double now_s() {
+  using clk = std::chrono::steady_clock;
+  static const clk::time_point t0 = clk::now();
+  return std::chrono::duration<double>(clk::now() - t0).count();
+}
+
+int sfail(int code, const char* msg) {
+  spn::set_last_error(msg);
+  return code;
+}
+
+enum JobState { kPending = 0, kAdmitted = 1, kDone = 2, kFailed = 3 };
+
+struct Job {
+  uint64_t ticket = 0;
+  spn_request req{};
+  std::vector<double> betas;
+  std::vector<uint64_t> bonds;
+  int state = kPending;
+  int status = SPN_OK;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int64_t done = 0;  // sweeps done
+  size_t bytes = 0;  // device bytes charged to the budget
+  int nd = 2;
+  int64_t N = 0;
+  int cs = 0;        // resident cluster size (0: not resident)
+  bool streaming = false;
+  spn::StreamGeom geo{};
+  int8_t* d_spins = nullptr;
+  int8_t* d_scratch = nullptr;
+  unsigned long long* d_acc = nullptr;  // window deltas / start E, M
+  spn_handle ea = nullptr;
+  int stream_slot = 0;
+  // results
+  int64_t E = 0, M = 0;
+  std::vector<int8_t> spins;
+  std::vector<uint32_t> words;
+  std::vector<uint8_t> slots;
+};
+
+}  // namespace
+
+struct spn_server_ctx {
+  size_t budget = 0;
+  size_t used = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Job>> pending;
+  std::vector<std::shared_ptr<Job>> active;
+  std::map<uint64_t, std::shared_ptr<Job>> all;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  int device = 0;
+  cudaStream_t main = nullptr;
+  std::vector<cudaStream_t> pool;
+  std::vector<cudaEvent_t> pool_done;
+  cudaEvent_t fork = nullptr;
+  spn::ResInst* d_inst = nullptr;  // per-round resident instances
+  int* d_order = nullptr;
+  int* d_counters = nullptr;
+  int* d_err = nullptr;
+  size_t inst_cap = 0;
+  int64_t window_attempts = (int64_t)1 << 27;  // about this many attempts per job per round
+  std::atomic<unsigned long long> attempts{0};
+  std::atomic<unsigned long long> rounds{0};
+  double busy = 0;
+};
+
+namespace {
+
+size_t job_bytes(const Job& j) {
+  if (j.req.model == SPN_EA3D_PMJ) return (size_t)j.N * 9 + 64 * 1024;  // words + bond bytes + tables
+  size_t b = (size_t)j.N + 4096;
+  if (j.streaming) b += (size_t)j.N;
+  return b;
+}
+
+void release(spn_server_ctx* s, Job& j) {
+  if (j.d_spins) cudaFreeAsync(j.d_spins, s->main);
+  if (j.d_scratch) cudaFreeAsync(j.d_scratch, s->main);
+  if (j.d_acc) cudaFreeAsync(j.d_acc, s->main);
+  j.d_spins = j.d_scratch = nullptr;
+  j.d_acc = nullptr;
+  if (j.ea) {
+    spn_destroy(j.ea);
+    j.ea = nullptr;
+  }
+}
+
+// Allocate and initialise an admitted job (scheduler thread).
+int admit(spn_server_ctx* s, Job& j) {
+  const spn_request& r = j.req;
+  if (r.model == SPN_EA3D_PMJ) {
+    int rc = spn_create_batch(&j.ea, SPN_EA3D_PMJ, r.dims, 1, j.bonds.data(), j.betas.data(), 32, r.seed,
+                              r.exchange_every);
+    if (rc) return rc;
+    return spn_set_stream(j.ea, s->pool[j.stream_slot]);
+  }
+  spn::Lattice g;
+  g.nd = j.nd;
+  g.Lx = r.dims[0];
+  g.Ly = r.dims[1];
+  g.Lz = j.nd == 3 ? r.dims[2] : 1;
+  g.N = j.N;
+  if (cudaMallocAsync(&j.d_spins, (size_t)j.N, s->main) != cudaSuccess) return SPN_E_NOMEM;
+  if (cudaMallocAsync(&j.d_acc, 4096, s->main) != cudaSuccess) return SPN_E_NOMEM;
+  if (j.streaming && cudaMallocAsync(&j.d_scratch, (size_t)j.N, s->main) != cudaSuccess) return SPN_E_NOMEM;
+  if (spn::launch_init_hot(g, j.d_spins, r.seed, r.stream, s->main) != cudaSuccess) return SPN_E_CUDA;
+  return SPN_OK;
+}
+
+// Final E, M and the host copies of a finished job.
+int finish(spn_server_ctx* s, Job& j) {
+  if (j.ea) {
+    const size_t n = (size_t)j.N;
+    j.words.resize(n);
+    j.slots.resize(32);
+    std::vector<int64_t> E(32), M(32);
+    int rc = spn_batch_get_words(j.ea, j.words.data(), n);
+    if (!rc) rc = spn_batch_get_slots(j.ea, j.slots.data(), 32);
+    if (!rc) rc = spn_batch_energies(j.ea, E.data(), M.data(), 32);
+    if (rc) return rc;
+    int s0 = 0;  // slot of the lowest temperature
+    for (int k = 0; k < 32; ++k)
+      if (j.slots[k] == 0) s0 = k;
+    j.E = E[s0];
+    j.M = M[s0];
+    return SPN_OK;
+  }
+  spn::Lattice g;
+  g.nd = j.nd;
+  g.Lx = j.req.dims[0];
+  g.Ly = j.req.dims[1];
+  g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
+  g.N = j.N;
+  if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, s->main) != cudaSuccess) return SPN_E_CUDA;
+  unsigned long long em[2];
+  j.spins.resize((size_t)j.N);
+  if (cudaMemcpyAsync(em, j.d_acc, 16, cudaMemcpyDeviceToHost, s->main) != cudaSuccess ||
+      cudaMemcpyAsync(j.spins.data(), j.d_spins, (size_t)j.N, cudaMemcpyDeviceToHost, s->main) != cudaSuccess ||
+      cudaStreamSynchronize(s->main) != cudaSuccess)
+    return SPN_E_CUDA;
+  j.E = (int64_t)em[0];
+  j.M = (int64_t)em[1];
+  return SPN_OK;
+}
+
+// One round: a window of sweeps for every active job.
+int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(s->fork, s->main)) != cudaSuccess) return SPN_E_CUDA;
+  for (cudaStream_t p : s->pool) cudaStreamWaitEvent(p, s->fork, 0);
+  // resident jobs, grouped by shape
+  std::map<std::tuple<int, int, int, int>, std::vector<Job*>> groups;
+  std::vector<int64_t> win(act.size());
+  for (size_t k = 0; k < act.size(); ++k) {
+    Job& j = *act[k];
+    const int64_t per = std::max<int64_t>(1, s->window_attempts / std::max<int64_t>(1, j.N));
+    win[k] = std::min<int64_t>(per, j.req.nsweeps - j.done);
+    if (j.cs > 0) groups[{j.nd, j.req.dims[0], j.req.dims[1], j.nd == 3 ? j.req.dims[2] : 1}].push_back(&j);
+  }
+  std::vector<spn::ResInst> inst;
+  std::vector<std::tuple<int, int, int, int, int, size_t, size_t>> launches;  // nd, Lx, Ly, Lz, cs, first, count
+  for (auto& kv : groups) {
+    const size_t first = inst.size();
+    for (Job* j : kv.second) {
+      const int64_t w = std::min<int64_t>(std::max<int64_t>(1, s->window_attempts / std::max<int64_t>(1, j->N)),
+                                          j->req.nsweeps - j->done);
+      spn::ResInst r{};
+      r.spins = j->d_spins;
+      r.trace = j->d_acc;
+      r.em0 = j->d_acc + 2 * 250;
+      r.seed = j->req.seed;
+      r.stream = j->req.stream;
+      r.sweep0 = (uint32_t)j->done;
+      r.nsweeps = (int)std::min<int64_t>(w, 250);  // the per-job accumulator holds 250 sweeps
+      r.init_hot = 0;
+      r.T = spn::make_thresholds(j->req.beta);
+      inst.push_back(r);
+    }
+    launches.emplace_back(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                          kv.second.front()->cs, first, kv.second.size());
+  }
+  if (!inst.empty()) {
+    if (inst.size() > s->inst_cap) {
+      cudaFree(s->d_inst);
+      cudaFree(s->d_order);
+      cudaFree(s->d_counters);
+      s->inst_cap = inst.size() * 2;
+      if (cudaMalloc(&s->d_inst, s->inst_cap * sizeof(spn::ResInst)) != cudaSuccess ||
+          cudaMalloc(&s->d_order, s->inst_cap * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&s->d_counters, s->inst_cap * sizeof(int)) != cudaSuccess)
+        return SPN_E_NOMEM;
+    }
+    if (cudaMemcpyAsync(s->d_inst, inst.data(), inst.size() * sizeof(spn::ResInst), cudaMemcpyHostToDevice,
+                        s->main) != cudaSuccess ||
+        cudaMemsetAsync(s->d_counters, 0, launches.size() * sizeof(int), s->main) != cudaSuccess)
+      return SPN_E_CUDA;
+    for (auto& j : act)
+      if (j->cs > 0) cudaMemsetAsync(j->d_acc, 0, 4096, s->main);
+    for (size_t li = 0; li < launches.size(); ++li) {
+      int nd, Lx, Ly, Lz, cs;
+      size_t first, count;
+      std::tie(nd, Lx, Ly, Lz, cs, first, count) = launches[li];
+      // the order array holds local indices into the group's instance slice
+      std::vector<int> ord(count);
+      for (size_t i = 0; i < count; ++i) ord[i] = (int)i;
+      cudaMemcpyAsync(s->d_order + first, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice, s->main);
+      spn::ResArgs a{};
+      a.inst = s->d_inst + first;
+      a.ninst = (int)count;
+      a.order = s->d_order + first;
+      a.counter = s->d_counters + li;
+      a.Lx = Lx;
+      a.Ly = Ly;
+      a.Lz = Lz;
+      a.err = s->d_err;
+      const int W = Lx >= 64 ? Lx / 64 : 1;
+      const int items = Ly * (nd == 3 ? Lz : 1) / cs * W;
+      const int threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
+      const size_t smem = spn::resident_smem(nd, Lx, Ly, Lz, cs);
+      const int ctas = std::max(cs, std::min<int>(spn::resident_max_ctas(nd, cs, threads, smem), (int)count * cs));
+      if ((e = spn::launch_resident(a, nd, cs, threads, ctas, s->main)) != cudaSuccess) return SPN_E_CUDA;
+    }
+  }
+  // the rest: own launches on the stream pool
+  for (size_t k = 0; k < act.size(); ++k) {
+    Job& j = *act[k];
+    if (j.cs > 0) continue;
+    cudaStream_t st = s->pool[j.stream_slot];
+    const int64_t w = win[k];
+    if (j.ea) {
+      if (spn_batch_sweep(j.ea, w)) return SPN_E_CUDA;
+      continue;
+    }
+    spn::Lattice g;
+    g.nd = j.nd;
+    g.Lx = j.req.dims[0];
+    g.Ly = j.req.dims[1];
+    g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
+    g.N = j.N;
+    const spn::DevThr T = spn::make_thresholds(j.req.beta);
+    const spn::PhiloxKeys K = spn::philox_keys(j.req.seed);
+    for (int64_t t = 0; t < w; ++t) {
+      const uint32_t sweep = (uint32_t)(j.done + t);
+      if (j.streaming) {  // ping-pong: the current lattice is always d_spins
+        e = spn::launch_sweep_stream(g, j.d_spins, j.d_scratch, j.geo, T, K, j.req.stream, sweep, j.d_acc, s->d_err,
+                                     st);
+        std::swap(j.d_spins, j.d_scratch);
+      } else {
+        e = spn::launch_sweep_generic(g, j.d_spins, T, K, j.req.stream, sweep, j.d_acc, st);
+      }
+      if (e != cudaSuccess) return SPN_E_CUDA;
+    }
+  }
+  for (size_t p = 0; p < s->pool.size(); ++p) {
+    cudaEventRecord(s->pool_done[p], s->pool[p]);
+    cudaStreamWaitEvent(s->main, s->pool_done[p], 0);
+  }
+  int err = 0;
+  if (cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->main) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s->main)) != cudaSuccess)
+    return SPN_E_CUDA;
+  if (err) return SPN_E_TIMEOUT;  // a bounded device wait ran out
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (size_t k = 0; k < act.size(); ++k) {
+    Job& j = *act[k];
+    const int64_t w = j.cs > 0 ? std::min<int64_t>(win[k], 250) : win[k];
+    j.done += w;
+    s->attempts += (unsigned long long)(j.N * w * (j.ea ? 32 : 1));
+  }
+  return SPN_OK;
+}
+
+void scheduler(spn_server_ctx* s) {
+  cudaSetDevice(s->device);
+  while (true) {
+    std::vector<std::shared_ptr<Job>> admitted_now;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv.wait(lock, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
+      if (s->stop && s->pending.empty() && s->active.empty()) return;
+      // admission against the budget, first come first served
+      while (!s->pending.empty()) {
+        std::shared_ptr<Job> j = s->pending.front();
+        if (s->used + j->bytes > s->budget) break;
+        s->pending.pop_front();
+        s->used += j->bytes;
+        j->state = kAdmitted;
+        j->t_admit = now_s();
+        admitted_now.push_back(j);
+      }
+    }
+    for (auto& j : admitted_now) {
+      j->stream_slot = (int)(j->ticket % s->pool.size());
+      int rc = admit(s, *j);
+      std::lock_guard<std::mutex> lock(s->mu);
+      if (rc) {
+        release(s, *j);
+        j->state = kFailed;
+        j->status = rc;
+        j->t_done = now_s();
+        s->used -= j->bytes;
+      } else {
+        s->active.push_back(j);
+      }
+    }
+    std::vector<std::shared_ptr<Job>> act;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      act = s->active;
+    }
+    if (act.empty()) continue;
+    const double t0 = now_s();
+    int rc = run_round(s, act);
+    s->busy += now_s() - t0;
+    s->rounds += 1;
+    std::vector<std::shared_ptr<Job>> still;
+    for (auto& j : act) {
+      if (rc == SPN_OK && j->done < j->req.nsweeps) {
+        still.push_back(j);
+        continue;
+      }
+      int frc = rc ? rc : finish(s, *j);
+      release(s, *j);
+      std::lock_guard<std::mutex> lock(s->mu);
+      j->status = frc;
+      j->state = frc ? kFailed : kDone;
+      j->t_done = now_s();
+      s->used -= j->bytes;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->active = still;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
+  if (!out || hbm_budget_bytes == 0) return sfail(SPN_E_ARG, "bad arguments");
+  *out = nullptr;
+  spn_server_ctx* s = new (std::nothrow) spn_server_ctx;
+  if (!s) return sfail(SPN_E_NOMEM, "host allocation failed");
+  s->budget = hbm_budget_bytes;
+  cudaGetDevice(&s->device);
+  if (cudaStreamCreateWithFlags(&s->main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&s->d_err, 4) != cudaSuccess || cudaMemset(s->d_err, 0, 4) != cudaSuccess) {
+    delete s;
+    return sfail(SPN_E_CUDA, "server set-up failed");
+  }
+  for (int i = 0; i < 8; ++i) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    s->pool.push_back(st);
+    s->pool_done.push_back(ev);
+  }
+  s->worker = std::thread(scheduler, s);
+  *out = s;
+  return SPN_OK;
+}
+
+int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket) {
+  if (!s || !req || !ticket) return sfail(SPN_E_ARG, "NULL argument");
+  auto j = std::make_shared<Job>();
+  j->req = *req;
+  j->req.betas = nullptr;
+  j->req.couplings = nullptr;
+  const int model = req->model;
+  if (model != SPN_ISING2D && model != SPN_ISING3D && model != SPN_EA3D_PMJ)
+    return sfail(SPN_E_ARG, "unknown model");
+  j->nd = model == SPN_ISING2D ? 2 : 3;
+  const int ext[3] = {req->dims[0], req->dims[1], j->nd == 3 ? req->dims[2] : 1};
+  for (int d = 0; d < j->nd; ++d)
+    if (ext[d] < 2 || (ext[d] & 1)) return sfail(SPN_E_ARG, "every extent must be even and >= 2");
+  if (req->nsweeps < 1 || req->nsweeps > 0xffffffffLL) return sfail(SPN_E_ARG, "nsweeps must be >= 1");
+  j->N = (int64_t)ext[0] * ext[1] * ext[2];
+  if (model == SPN_EA3D_PMJ) {
+    if (!req->betas || !req->couplings) return sfail(SPN_E_ARG, "EA requests need 32 betas and couplings");
+    j->betas.assign(req->betas, req->betas + 32);
+    const size_t nw = (size_t)((j->N + 63) / 64);
+    j->bonds.assign(static_cast<const uint64_t*>(req->couplings), static_cast<const uint64_t*>(req->couplings) + 3 * nw);
+  } else {
+    if (!(req->beta >= 0.0)) return sfail(SPN_E_ARG, "beta must be >= 0");
+    j->cs = spn::resident_cluster_size(j->nd, ext[0], ext[1], ext[2]);
+    if (!j->cs) {
+      spn::Lattice g;
+      g.nd = j->nd;
+      g.Lx = ext[0];
+      g.Ly = ext[1];
+      g.Lz = ext[2];
+      g.N = j->N;
+      int ty = 32;
+      if (j->nd == 3)
+        while (ty > 1 && ext[1] % ty) ty /= 2;
+      if (j->nd == 2) ty = 1;
+      if (spn::stream_path_supported(g, ty)) {
+        j->geo = spn::stream_geometry(g, ty, 0, 0);
+        j->streaming = spn::stream_geometry_ok(g, j->geo);
+      }
+    }
+  }
+  j->bytes = job_bytes(*j);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (j->bytes > s->budget) return sfail(SPN_E_BUDGET, "the job alone exceeds the server's HBM budget");
+  j->ticket = s->next_ticket++;
+  j->t_submit = now_s();
+  s->pending.push_back(j);
+  s->all[j->ticket] = j;
+  *ticket = j->ticket;
+  s->cv.notify_one();
+  return SPN_OK;
+}
+
+int spn_poll(spn_server s, uint64_t ticket, int* done, spn_result* out) {
+  if (!s || !done) return sfail(SPN_E_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return sfail(SPN_E_NOTFOUND, "unknown ticket");
+  const Job& j = *it->second;
+  *done = j.state == kDone || j.state == kFailed;
+  if (out) {
+    std::memset(out, 0, sizeof *out);
+    out->status = j.status;
+    out->state = j.state;
+    out->sweeps = j.done;
+    if (j.state == kDone) {  // written by the scheduler before the state changes
+      out->E = j.E;
+      out->M = j.M;
+    }
+    out->t_submit = j.t_submit;
+    out->t_admit = j.t_admit;
+    out->t_done = j.t_done;
+  }
+  return SPN_OK;
+}
+
+int spn_server_fetch(spn_server s, uint64_t ticket, void* out, size_t bytes) {
+  if (!s || !out) return sfail(SPN_E_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return sfail(SPN_E_NOTFOUND, "unknown ticket");
+  Job& j = *it->second;
+  if (j.state != kDone) return sfail(SPN_E_STATE, "the job is not done");
+  if (j.req.model == SPN_EA3D_PMJ) {
+    const size_t need = j.words.size() * 4 + 32;
+    if (bytes != need) return sfail(SPN_E_ARG, "EA results are N uint32 words followed by 32 slot bytes");
+    std::memcpy(out, j.words.data(), j.words.size() * 4);
+    std::memcpy(static_cast<uint8_t*>(out) + j.words.size() * 4, j.slots.data(), 32);
+  } else {
+    if (bytes != j.spins.size()) return sfail(SPN_E_ARG, "bytes must be N");
+    std::memcpy(out, j.spins.data(), bytes);
+  }
+  return SPN_OK;
+}
+
+int spn_server_stats(spn_server s, uint64_t* attempts, double* busy_seconds, uint64_t* rounds, size_t* used_bytes) {
+  if (!s) return sfail(SPN_E_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (attempts) *attempts = s->attempts.load();
+  if (busy_seconds) *busy_seconds = s->busy;
+  if (rounds) *rounds = s->rounds.load();
+  if (used_bytes) *used_bytes = s->used;
+  return SPN_OK;
+}
+
+int spn_server_destroy(spn_server s) {
+  if (!s) return sfail(SPN_E_ARG, "NULL argument");
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+    s->pending.clear();
+    s->cv.notify_one();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->all) release(s, *kv.second);
+  cudaStreamSynchronize(s->main);
+  for (size_t i = 0; i < s->pool.size(); ++i) {
+    cudaStreamDestroy(s->pool[i]);
+    cudaEventDestroy(s->pool_done[i]);
+  }
+  cudaFree(s->d_inst);
+  cudaFree(s->d_order);
+  cudaFree(s->d_counters);
+  cudaFree(s->d_err);
+  cudaEventDestroy(s->fork);
+  cudaStreamDestroy(s->main);
+  delete s;
+  return SPN_OK;
+}
+
+}  // extern "C"

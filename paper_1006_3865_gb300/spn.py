@@ -77,6 +77,12 @@ _SIGNATURES = {
     "spn_multi_result": (_c.c_int, [_vp, _c.c_int, _vp, _sz, _vp, _vp, _i64]),
     "spn_multi_set_stream": (_c.c_int, [_vp, _vp]),
     "spn_multi_destroy": (_c.c_int, [_vp]),
+    "spn_server_create": (_c.c_int, [_P(_vp), _sz]),
+    "spn_submit": (_c.c_int, [_vp, _vp, _P(_u64)]),
+    "spn_poll": (_c.c_int, [_vp, _u64, _P(_c.c_int), _vp]),
+    "spn_server_fetch": (_c.c_int, [_vp, _u64, _vp, _sz]),
+    "spn_server_stats": (_c.c_int, [_vp, _P(_u64), _P(_dbl), _P(_u64), _P(_sz)]),
+    "spn_server_destroy": (_c.c_int, [_vp]),
     "spn_create_batch": (_c.c_int, [_P(_vp), _c.c_int, _vp, _c.c_int, _vp, _vp, _c.c_int, _u64, _c.c_int]),
     "spn_batch_sweep": (_c.c_int, [_vp, _i64]),
     "spn_batch_get_words": (_c.c_int, [_vp, _vp, _sz]),
@@ -94,6 +100,22 @@ class Job(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("dims", ctypes.c_int32 * 3), ("beta", ctypes.c_double),
                 ("nsweeps", ctypes.c_int64), ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
                 ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    """spn_request."""
+
+    _fields_ = [("model", ctypes.c_int32), ("dims", ctypes.c_int32 * 3), ("beta", ctypes.c_double),
+                ("betas", ctypes.c_void_p), ("nsweeps", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_uint32), ("exchange_every", ctypes.c_int32), ("couplings", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    """spn_result."""
+
+    _fields_ = [("status", ctypes.c_int32), ("state", ctypes.c_int32), ("sweeps", ctypes.c_int64),
+                ("E", ctypes.c_int64), ("M", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class SpnError(RuntimeError):
@@ -366,6 +388,62 @@ class Multi:
     def close(self):
         if getattr(self, "_h", None):
             _check(self._lib.spn_multi_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (spn_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int):
+        self._lib = load()
+        h = _vp()
+        _check(self._lib.spn_server_create(_c.byref(h), int(hbm_budget_bytes)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, model: int, dims, nsweeps: int, seed: int, beta: float = 0.0, stream: int = 0,
+               betas=None, couplings=None, exchange_every: int = 10) -> int:
+        d = list(dims) + [1] * (3 - len(dims))
+        b = None if betas is None else np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+        c = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.uint64)
+        r = Request(model, (ctypes.c_int32 * 3)(*d), float(beta), None if b is None else b.ctypes.data,
+                    int(nsweeps), int(seed), int(stream), int(exchange_every), None if c is None else c.ctypes.data)
+        t = _u64()
+        _check(self._lib.spn_submit(self._h, _c.byref(r), _c.byref(t)))
+        self._keep[t.value] = (model, tuple(int(x) for x in dims))
+        return t.value
+
+    def poll(self, ticket: int):
+        done = _c.c_int()
+        res = Result()
+        _check(self._lib.spn_poll(self._h, ticket, _c.byref(done), _c.byref(res)))
+        return bool(done.value), res
+
+    def fetch(self, ticket: int):
+        model, dims = self._keep[ticket]
+        N = int(np.prod(dims))
+        if model == SPN_EA3D_PMJ:
+            buf = np.empty(N * 4 + 32, np.uint8)
+            _check(self._lib.spn_server_fetch(self._h, ticket, _ptr(buf), buf.size))
+            return buf[:N * 4].view(np.uint32).copy(), buf[N * 4:].copy()
+        out = np.empty(N, np.int8)
+        _check(self._lib.spn_server_fetch(self._h, ticket, _ptr(out), N))
+        return out
+
+    def stats(self):
+        a, b, r, u = _u64(), _dbl(), _u64(), _sz()
+        _check(self._lib.spn_server_stats(self._h, _c.byref(a), _c.byref(b), _c.byref(r), _c.byref(u)))
+        return {"attempts": a.value, "busy_s": b.value, "rounds": r.value, "used_bytes": u.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.spn_server_destroy(self._h))
             self._h = None
 
     def __del__(self):
