@@ -49,7 +49,7 @@ ATTEMPTS_PER_STEP = len(TEMPS_2D) * SWEEPS_2D * L2D * L2D + SWEEPS_3D * L3D ** 3
 WORKLOAD = ("2D Ising L=16384 (hot start, T in {2.0, 2.269185, 3.0}, 200 sweeps each) + "
             "3D Ising L=512 (hot start, beta=0.221654, 100 sweeps)")
 PROFILE_2D = os.path.join(ROOT, "profiles", "sweep_stream_2d_L16384.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1006_3865_gb300", "csrc", "ising.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1006_3865_gb300", "csrc", "stream.cu")
 
 
 def _args():

@@ -30,6 +30,7 @@ enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2 };
 // per step, nseg segments along the streamed axis, raw / bit slice buffers.
 struct StreamGeom {
   int TY, R, nseg, threads, nraw, nbit;
+  int roundsC, roundsA, roundsB, qcap;  // words per thread per phase; tie-queue entries per warp
   size_t smem;
 };
 
