@@ -91,24 +91,23 @@ template <int ND>
 __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArgs a) {
   constexpr int NC = ND;  // classes with dE > 0: dE = 4 (q + 1), q < NC
   extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ int s_cnt[4];  // tie pools: colour 0 of even / odd steps, colour 1 of even / odd steps
   const int Lx = a.Lx, W = Lx >> 6, W2 = 2 * W;
+  const int R = a.R, nbit = a.nbit, nraw = a.nraw, qcap = a.qcap;
   const int RSL = (ND == 3) ? a.TY + 4 : 1;    // rows per slice: band + 2 halo rows on each side
   const int rowsA = (ND == 3) ? a.TY + 2 : 1;  // colour-0 rows: band + 1 ring row on each side
   const int rowsB = (ND == 3) ? a.TY : 1;      // colour-1 rows: the band
+  const int rowOffA = (ND == 3) ? -1 : 0;
   const int rawBytes = RSL * Lx;
   const int rawStride = (rawBytes + 127) & ~127;
   const int sliceWords = RSL * W2;
   uint8_t* raw = smem;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)a.nraw * rawStride);
-  uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)a.nbit * sliceWords);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)nraw * rawStride);
+  uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)nbit * sliceWords);
   uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256);
+  uint32_t* pools = reinterpret_cast<uint32_t*>(bars + nraw);  // 4 x [off | c0 | eq[NC]] x qcap
 
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
-  // the warp's tie queue: word index (bit 31: owned), counter, tied sites per class
-  uint32_t* q_off = reinterpret_cast<uint32_t*>(bars + a.nraw) + (size_t)(tid >> 5) * (2 + NC) * a.qcap;
-  uint32_t* q_c0 = q_off + a.qcap;
-  uint32_t* q_eq = q_c0 + a.qcap;
-
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
   const int y0 = (ND == 3) ? blockIdx.x * a.TY : 0;
   const int zs = (int)(((int64_t)blockIdx.y * a.S) / a.nseg);
   const int ze = (int)(((int64_t)(blockIdx.y + 1) * a.S) / a.nseg);
@@ -125,16 +124,17 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArg
     }
     lut[i] = make_uint2(lo, hi);
   }
+  if (tid < 4) s_cnt[tid] = 0;
   if (tid == 0) {
-    for (int b = 0; b < a.nraw; ++b) mbar_init(&bars[b], 1);
+    for (int b = 0; b < nraw; ++b) mbar_init(&bars[b], 1);
     fence_mbar_init();
   }
   uint32_t ic[kMaxRounds], ia[kMaxRounds], ib[kMaxRounds];
 #pragma unroll
   for (int q = 0; q < kMaxRounds; ++q) {
-    ic[q] = item_of(tid + q * nth, RSL, W, a.R * RSL * W);
-    ia[q] = item_of(tid + q * nth, rowsA, W, a.R * rowsA * W);
-    ib[q] = item_of(tid + q * nth, rowsB, W, a.R * rowsB * W);
+    ic[q] = item_of(tid + q * nth, RSL, W, R * RSL * W);
+    ia[q] = item_of(tid + q * nth, rowsA, W, R * rowsA * W);
+    ib[q] = item_of(tid + q * nth, rowsB, W, R * rowsB * W);
   }
   // chunk order of the 64-byte span rotated by lane pair: a quarter warp reads
   // 8 distinct 4-bank groups; rot_sel undoes the rotation on the gathered bytes
@@ -145,51 +145,65 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArg
 
   auto wrapS = [&](int z) { return z < 0 ? z + a.S : (z >= a.S ? z - a.S : z); };
   auto wrapY = [&](int y) { return y < 0 ? y + a.Ly : (y >= a.Ly ? y - a.Ly : y); };
+  // bit slot of local slice b0 + d, given sb = b0 mod nbit and -nbit < d < 2 nbit
+  auto slot = [&](int sb, int d) {
+    int s = sb + d;
+    s = s < 0 ? s + nbit : s;
+    return s >= nbit ? s - nbit : s;
+  };
 
-  // Bulk copies of local slice li into its raw slot (warp 0).
-  auto issue = [&](int li) {
-    if (li >= nload) return;
-    uint8_t* B = raw + (size_t)(li % a.nraw) * rawStride;
-    uint64_t* bar = &bars[li % a.nraw];
-    if (lane == 0) {
-      fence_proxy_async();  // earlier generic reads of the slot before the async writes
-      mbar_arrive_expect_tx(bar, (uint32_t)rawBytes);
-    }
-    __syncwarp();
-    const int64_t gz = wrapS(zs - 2 + li);
-    for (int r = lane; r < RSL; r += 32) {
-      const int gy = (ND == 3) ? wrapY(y0 - 2 + r) : 0;
-      bulk_g2s(B + (size_t)r * Lx, a.in + gz * sliceStride + (int64_t)gy * Lx, (uint32_t)Lx, bar);
+  // Raw ring (uniform state): slices [0, conv) converted, [0, issued) requested;
+  // cslot / cpar: slot and mbarrier phase of the next slice to convert.
+  int conv = 0, issued = 0, islot = 0, cslot = 0;
+  uint32_t cpar = 0;
+  auto issue_upto = [&]() {
+    const int lim = conv + nraw < nload ? conv + nraw : nload;
+    for (; issued < lim; ++issued) {
+      if (tid < 32) {
+        uint8_t* B = raw + (size_t)islot * rawStride;
+        uint64_t* bar = &bars[islot];
+        if (lane == 0) {
+          fence_proxy_async();  // earlier generic reads of the slot before the async writes
+          mbar_arrive_expect_tx(bar, (uint32_t)rawBytes);
+        }
+        __syncwarp();
+        const int64_t gz = wrapS(zs - 2 + issued);
+        for (int r = lane; r < RSL; r += 32) {
+          const int gy = (ND == 3) ? wrapY(y0 - 2 + r) : 0;
+          bulk_g2s(B + (size_t)r * Lx, a.in + gz * sliceStride + (int64_t)gy * Lx, (uint32_t)Lx, bar);
+        }
+      }
+      if (++islot == nraw) islot = 0;
     }
   };
 
-  // Wait (bounded) for raw slices l0 .. l0 + ns - 1; false if a wait ran out.
-  auto wait_raw = [&](int l0, int ns) -> bool {
+  // Wait (bounded) for raw slices li0 .. li0 + ns - 1 (the next ones in order)
+  // and turn them into bit words; false if a wait ran out.
+  auto convert = [&](int li0, int ns, int sb, int b0) -> bool {
     bool ok = true;
-    for (int li = l0; li < l0 + ns; ++li) {
-      const uint32_t parity = (uint32_t)((li / a.nraw) & 1);
+    int rs = cslot;
+    uint32_t ph = cpar;
+    for (int k = 0; k < ns; ++k) {
       unsigned n = 0;
-      while (!mbar_try_wait(&bars[li % a.nraw], parity)) {
+      while (!mbar_try_wait(&bars[rs], ph)) {
         if (++n > kWaitLimit) {
           ok = false;
           break;
         }
       }
+      if (++rs == nraw) {
+        rs = 0;
+        ph ^= 1u;
+      }
     }
-    return ok;
-  };
-
-  // Raw slices l0 .. l0 + ns - 1 -> bit words.
-  auto convert = [&](int l0, int ns) {
-    int rbase = l0 % a.nraw, bbase = l0 % a.nbit;
 #pragma unroll
     for (int q = 0; q < kMaxRounds; ++q) {
       const uint32_t x = ic[q];
       if (q < a.roundsC && it_live(x, ns)) {
-        int rs = rbase + it_ks(x), bs = bbase + it_ks(x);
-        if (rs >= a.nraw) rs -= a.nraw;
-        if (bs >= a.nbit) bs -= a.nbit;
-        const uint8_t* span = raw + (size_t)rs * rawStride + (size_t)it_r(x) * Lx + 64 * it_j(x);
+        int r = cslot + it_ks(x);
+        if (r >= nraw) r -= nraw;
+        const int bs = slot(sb, li0 + it_ks(x) - b0);
+        const uint8_t* span = raw + (size_t)r * rawStride + (size_t)it_r(x) * Lx + 64 * it_j(x);
         uint32_t pe[4], po[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -202,37 +216,53 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArg
         row[W] = __byte_perm(top_bytes(po[0], po[1], po[2], po[3]), 0u, rot_sel);
       }
     }
+    cslot = rs;
+    cpar = ph;
+    conv = li0 + ns;
+    return ok;
   };
 
   int de = 0, dm = 0;
 
-  // Update colour c on local slices l0 .. l0 + ns - 1 for the items xs; the
-  // words are rewritten in place (a colour-c word reads only colour 1 - c
-  // words).  Ties on the top 8 bits go to the warp's queue and are settled at
-  // the end by whole-warp Philox calls.
-  auto phase = [&](const uint32_t (&xs)[kMaxRounds], int rounds, int l0, int ns, int c, int rowOff) {
-    const int bbase = l0 % a.nbit;
-    int qn = 0;
+  // Apply the late-accepted sites of a tied word and count them if owned.
+  auto settle = [&](uint32_t w, bool own, uint32_t late, const uint32_t (&eq0)[NC]) {
+    const uint32_t cur = bits[w];  // the tied sites still hold their old spins
+    bits[w] = cur ^ late;
+    if (own) {
+      int d = 0;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) d += 4 * (k + 1) * __popc(late & eq0[k]);
+      de += d;
+      dm += 2 * (2 * __popc(late & cur) - __popc(late));
+    }
+  };
+
+  // First decision stage of colour c on local slices li0 .. li0 + ns - 1 for the
+  // items xs: every word is rewritten in place (a colour-c word reads only
+  // colour 1 - c words) with the sites settled by the top 8 bits; words with
+  // ties go to tie pool `pool`, which whole warps finish after the next barrier.
+  auto phase = [&](const uint32_t (&xs)[kMaxRounds], int rounds, int li0, int ns, int c, int rowOff, int sb, int b0,
+                   int pool) {
+    uint32_t* P = pools + (size_t)pool * (2 + NC) * qcap;
+    const uint32_t c2 = (uint32_t)c | (kMetropolis << 1);
 #pragma unroll
     for (int q = 0; q < kMaxRounds; ++q) {
       if (q >= rounds) break;  // uniform
       const uint32_t x = xs[q];
-      const bool live = it_live(x, ns);
       uint32_t eq[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) eq[k] = 0;
       uint32_t woff = 0, c0 = 0;
       bool own = false;
-      if (live) {
-        const int li = l0 + it_ks(x);
-        int bs = bbase + it_ks(x);
-        if (bs >= a.nbit) bs -= a.nbit;
-        const int bm = bs == 0 ? a.nbit - 1 : bs - 1, bp = bs + 1 == a.nbit ? 0 : bs + 1;
+      if (it_live(x, ns)) {
+        const int li = li0 + it_ks(x);
+        const int bs = slot(sb, li - b0);
+        const int bm = bs == 0 ? nbit - 1 : bs - 1, bp = bs + 1 == nbit ? 0 : bs + 1;
         const int gz = wrapS(zs - 2 + li);
-        const int rb = it_r(x) + rowOff;                    // band row (-1 .. TY for colour 0 in 3D)
+        const int rb = it_r(x) + rowOff;                           // band row
         const int gy = (ND == 3) ? wrapY(y0 + rb) : 0;
         const int par = (((ND == 3) ? y0 + rb : 0) + gz + c) & 1;  // 0: E word, 1: O word
-        const int rr = (ND == 3) ? rb + 2 : 0;          // row within the slice
+        const int rr = (ND == 3) ? rb + 2 : 0;                     // row within the slice
         const int j = it_j(x);
         const int rowBase = bs * sliceWords + rr * W2;
         woff = (uint32_t)(rowBase + par * W + j);
@@ -259,7 +289,6 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArg
           eq[k] = always ? 0u : cls[k];
         }
         c0 = 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)((ND == 3) ? gy + a.Ly * gz : gz));
-        const uint32_t c2 = (uint32_t)c | (kMetropolis << 1);
         const U4 P0 = philox10(c0, a.sweep, c2, a.stream_id, a.K);
         const U4 P1 = philox10(c0 + 1u, a.sweep, c2, a.stream_id, a.K);
         const uint32_t pl[8] = {P0.x, P0.y, P0.z, P0.w, P1.x, P1.y, P1.z, P1.w};
@@ -287,64 +316,69 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArg
       for (int k = 0; k < NC; ++k) any |= eq[k];
       const unsigned vote = __ballot_sync(0xffffffffu, any != 0u);
       if (vote) {
-        if (any) {
-          const int e = qn + __popc(vote & ((1u << lane) - 1u));
-          q_off[e] = woff | (own ? 0x80000000u : 0u);
-          q_c0[e] = c0;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s_cnt[pool], __popc(vote));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int e = base + __popc(vote & ((1u << lane) - 1u));
+        const bool ovf = any != 0u && e >= qcap;
+        if (any != 0u && !ovf) {
+          P[e] = woff | ((uint32_t)c << 30) | (own ? 0x80000000u : 0u);
+          P[qcap + e] = c0;
 #pragma unroll
-          for (int k = 0; k < NC; ++k) q_eq[k * a.qcap + e] = eq[k];
+          for (int k = 0; k < NC; ++k) P[(2 + k) * qcap + e] = eq[k];
         }
-        qn += __popc(vote);
+        if (__any_sync(0xffffffffu, ovf)) {  // the pool is full: settle these words here
+          uint32_t e2[NC], e0[NC];
+#pragma unroll
+          for (int k = 0; k < NC; ++k) e0[k] = e2[k] = ovf ? eq[k] : 0u;
+          const uint32_t late = decide_tail<NC>(e2, a.T, a.K, c0, a.sweep, c2, a.stream_id);
+          if (ovf) settle(woff, own, late, e0);
+        }
       }
     }
-    __syncwarp();
-    // ties: planes 8 .. 31 for the queued words, one word per lane
-    for (int base = 0; base < qn; base += 32) {
-      const int e = base + lane;
+  };
+
+  // Planes 8 .. 31 for the words of two tie pools, one word per lane, packed
+  // into as few warps as possible.
+  auto tails = [&](int pa, int pb) {
+    const int na = s_cnt[pa] < qcap ? s_cnt[pa] : qcap;
+    const int nb = s_cnt[pb] < qcap ? s_cnt[pb] : qcap;
+    for (int base = warp * 32; base < na + nb; base += nwarps * 32) {
+      const int v = base + lane;
       uint32_t eq[NC], eq0[NC];
       uint32_t c0 = 0, off = 0;
 #pragma unroll
       for (int k = 0; k < NC; ++k) eq[k] = 0;
-      if (e < qn) {
-        off = q_off[e];
-        c0 = q_c0[e];
+      if (v < na + nb) {
+        const uint32_t* P = pools + (size_t)(v < na ? pa : pb) * (2 + NC) * qcap;
+        const int e = v < na ? v : v - na;
+        off = P[e];
+        c0 = P[qcap + e];
 #pragma unroll
-        for (int k = 0; k < NC; ++k) eq[k] = q_eq[k * a.qcap + e];
+        for (int k = 0; k < NC; ++k) eq[k] = P[(2 + k) * qcap + e];
       }
 #pragma unroll
       for (int k = 0; k < NC; ++k) eq0[k] = eq[k];
-      const uint32_t late = decide_tail<NC>(eq, a.T, a.K, c0, a.sweep, (uint32_t)c | (kMetropolis << 1), a.stream_id);
-      if (e < qn) {
-        const uint32_t w = off & 0x7fffffffu;
-        const uint32_t cur = bits[w];  // the tied sites still hold their old spins
-        bits[w] = cur ^ late;
-        if (off >> 31) {
-          int d = 0;
-#pragma unroll
-          for (int k = 0; k < NC; ++k) d += 4 * (k + 1) * __popc(late & eq0[k]);
-          de += d;
-          dm += 2 * (2 * __popc(late & cur) - __popc(late));
-        }
-      }
+      const uint32_t c2 = ((off >> 30) & 1u) | (kMetropolis << 1);
+      const uint32_t late = decide_tail<NC>(eq, a.T, a.K, c0, a.sweep, c2, a.stream_id);
+      if (v < na + nb) settle(off & 0x3fffffffu, (off >> 31) != 0u, late, eq0);
     }
-    __syncwarp();
   };
 
-  // Finished words of colour-1 items -> int8 rows in global memory.
-  auto output = [&](int l0, int ns) {
-    const int bbase = l0 % a.nbit;
+  // Finished colour-1 rows (both colours final) -> int8 rows in global memory.
+  auto output = [&](int li0, int ns, int sb, int b0) {
 #pragma unroll
     for (int q = 0; q < kMaxRounds; ++q) {
       const uint32_t x = ib[q];
       if (q < a.roundsB && it_live(x, ns)) {
-        int bs = bbase + it_ks(x);
-        if (bs >= a.nbit) bs -= a.nbit;
+        const int li = li0 + it_ks(x);
+        const int bs = slot(sb, li - b0);
         const int rr = (ND == 3) ? it_r(x) + 2 : 0;
         const uint32_t* row = bits + (size_t)bs * sliceWords + (size_t)rr * W2 + it_j(x);
         const uint32_t E = row[0], O = row[W];
         const uint32_t X = (E & 0x0f0f0f0fu) | ((O << 4) & 0xf0f0f0f0u);  // byte v: sites 16v .. 16v + 7
         const uint32_t Y = ((E >> 4) & 0x0f0f0f0fu) | (O & 0xf0f0f0f0u);  // byte v: sites 16v + 8 .. 16v + 15
-        const int gz = wrapS(zs - 2 + l0 + it_ks(x));
+        const int gz = wrapS(zs - 2 + li);
         const int gy = (ND == 3) ? y0 + it_r(x) : 0;
         uint4* dst = reinterpret_cast<uint4*>(a.out + (int64_t)gz * sliceStride + (int64_t)gy * Lx + 64 * it_j(x));
 #pragma unroll
@@ -357,48 +391,65 @@ __global__ void __launch_bounds__(kMaxThreads, 2) k_sweep_stream(const StreamArg
     }
   };
 
-  // Prologue: local slices 0 .. 3 converted, colour 0 on slices 1 and 2.
-  int issued = a.nraw < nload ? a.nraw : nload;  // slices 0 .. issued - 1 requested (uniform)
-  if (tid < 32)
-    for (int li = 0; li < issued; ++li) issue(li);
+  // Schedule.  Step t (b0 = t R) has two windows between barriers:
+  //   W1: ties of colour 0 of step t-1 and colour 1 of step t-1;
+  //       colour 0, first stage, on slices b0+R+3 .. b0+2R+2;
+  //   W2: int8 output of the colour-1 slices of step t-1;
+  //       colour 1, first stage, on slices b0+2 .. b0+R+1;
+  //       conversion of slices b0+2R+4 .. b0+3R+3.
+  // Colour 0 runs a full step ahead, so its ties are settled before colour 1
+  // reads it; 4R+2 bit slots hold every slice a window touches.
+  issue_upto();
   bool ok = true;
-  for (int li = 0; li < 4 && ok; ++li) {
-    const bool mine = wait_raw(li, 1);
-    convert(li, 1);
+  const int pro = 2 * R + 4 < nload ? 2 * R + 4 : nload;
+  for (int li = 0; li < pro && ok; ++li) {
+    const bool mine = convert(li, 1, 0, 0);
     ok = __syncthreads_and(mine);
-    if (ok && li + a.nraw < nload) {
-      if (tid < 32) issue(li + a.nraw);
-      issued = li + a.nraw + 1;
-    }
+    if (ok) issue_upto();
   }
   if (ok) {
-    for (int l = 1; l < 3; l += a.R) phase(ia, a.roundsA, l, (3 - l) < a.R ? 3 - l : a.R, 0, (ND == 3) ? -1 : 0);
-    __syncthreads();
-    // Steps of R slices: outputs are local slices b0 + 2 .. b0 + 1 + ns.
-    for (int b0 = 0; b0 < H && ok; b0 += a.R) {
-      const int ns = (b0 + a.R < H) ? a.R : H - b0;
-      const bool mine = wait_raw(b0 + 4, ns);
-      convert(b0 + 4, ns);
-      ok = __syncthreads_and(mine);
-      if (!ok) break;
-      for (int li = b0 + 4; li < b0 + 4 + ns; ++li)
-        if (li + a.nraw < nload) {
-          if (tid < 32) issue(li + a.nraw);
-          issued = li + a.nraw + 1;
-        }
-      phase(ia, a.roundsA, b0 + 3, ns, 0, (ND == 3) ? -1 : 0);
-      __syncthreads();
-      phase(ib, a.roundsB, b0 + 2, ns, 1, 0);
-      output(b0 + 2, ns);
+    const int last = R + 2 < H + 2 ? R + 2 : H + 2;  // colour 0 on slices 1 .. R+2 (ties: pool 1, step -1)
+    for (int l = 1; l <= last; l += R) phase(ia, a.roundsA, l, (last - l + 1) < R ? last - l + 1 : R, 0, rowOffA, 0, 0, 1);
+  }
+  ok = __syncthreads_and(ok);
+  const int nsteps = (H + R - 1) / R;
+  int sb = 0;  // b0 mod nbit
+  for (int t = 0; ok && t <= nsteps; ++t) {
+    const int b0 = t * R;
+    const int pe = t & 1, po = pe ^ 1;
+    tails(po, 2 + po);  // pools of step t-1
+    if (t < nsteps) {
+      const int first = b0 + R + 3, last = b0 + 2 * R + 2 < H + 2 ? b0 + 2 * R + 2 : H + 2;
+      if (first <= last) phase(ia, a.roundsA, first, last - first + 1, 0, rowOffA, sb, b0, pe);
     }
+    __syncthreads();
+    if (tid == 0) {
+      s_cnt[po] = 0;
+      s_cnt[2 + po] = 0;
+    }
+    if (t >= 1) {
+      const int first = b0 - R + 2, last = b0 + 1 < H + 1 ? b0 + 1 : H + 1;
+      output(first, last - first + 1, sb, b0);
+    }
+    bool mine = true;
+    if (t < nsteps) {
+      const int first = b0 + 2, last = b0 + R + 1 < H + 1 ? b0 + R + 1 : H + 1;
+      phase(ib, a.roundsB, first, last - first + 1, 1, 0, sb, b0, 2 + pe);
+      const int cf = b0 + 2 * R + 4, cl = b0 + 3 * R + 3 < nload - 1 ? b0 + 3 * R + 3 : nload - 1;
+      if (cf <= cl) mine = convert(cf, cl - cf + 1, sb, b0);
+    }
+    ok = __syncthreads_and(mine);
+    if (ok) issue_upto();
+    sb += R;
+    if (sb >= nbit) sb -= nbit;
   }
   if (!ok) {  // uniform: every thread saw the same barrier result
     if (tid == 0) {
       atomicExch(a.err, 1);
       // let the copies still in flight land before the CTA exits (bounded)
-      for (int li = issued > a.nraw ? issued - a.nraw : 0; li < issued; ++li) {
+      for (int li = issued > nraw ? issued - nraw : 0; li < issued; ++li) {
         unsigned n = 0;
-        while (!mbar_try_wait(&bars[li % a.nraw], (uint32_t)((li / a.nraw) & 1)) && ++n < kWaitLimit) {
+        while (!mbar_try_wait(&bars[li % nraw], (uint32_t)((li / nraw) & 1)) && ++n < kWaitLimit) {
         }
       }
     }
@@ -426,10 +477,14 @@ size_t smem_bytes(const Lattice& g, int TY, int R, int nraw, int threads, int qc
   const int W = g.Lx / 64;
   const int RSL = g.nd == 3 ? TY + 4 : 1;
   const size_t rawStride = (size_t)((RSL * g.Lx + 127) & ~127);
-  const size_t bitsB = (size_t)(2 * R + 3) * RSL * 2 * W * 4;
-  const size_t q = (size_t)(threads / 32) * (2 + g.nd) * qcap * 4;
+  const size_t bitsB = (size_t)(4 * R + 2) * RSL * 2 * W * 4;
+  const size_t q = (size_t)4 * (2 + g.nd) * qcap * 4;
   return (size_t)nraw * rawStride + bitsB + 256 * 8 + (size_t)nraw * 8 + q;
 }
+
+// Entries of one tie pool: a quarter of a phase's words, about twice the
+// expected number of ties (one site in 256 of the positive-dE sites).
+int pool_cap(int threads, int ra, int rb) { return std::max(64, (threads * std::max(ra, rb) / 4 + 31) / 32 * 32); }
 
 void phase_counts(const Lattice& g, int TY, int R, int& nC, int& nA, int& nB) {
   const int W = g.Lx / 64;
@@ -467,21 +522,21 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg) {
       const int th = threads_for(r);
       int rc, ra, rb;
       if (rounds_for(r, th, rc, ra, rb) > kMaxRounds) continue;
-      if (smem_bytes(g, s.TY, r, 2 * r, th, 32 * std::max(ra, rb)) <= (size_t)kSmemCap) {
+      if (smem_bytes(g, s.TY, r, 2 * r, th, pool_cap(th, ra, rb)) <= (size_t)kSmemCap) {
         R = r;
         break;
       }
     }
   }
   s.R = R;
-  s.nbit = 2 * R + 3;
+  s.nbit = 4 * R + 2;
   s.threads = threads_for(R);
   int rc, ra, rb;
   rounds_for(R, s.threads, rc, ra, rb);
   s.roundsC = rc;
   s.roundsA = ra;
   s.roundsB = rb;
-  s.qcap = 32 * std::max(ra, rb);
+  s.qcap = pool_cap(s.threads, ra, rb);
   s.nraw = 2 * R;  // a slice is requested one step before it is converted
   while (s.nraw > R && smem_bytes(g, s.TY, R, s.nraw, s.threads, s.qcap) > (size_t)kSmemCap) --s.nraw;
   s.smem = smem_bytes(g, s.TY, R, s.nraw, s.threads, s.qcap);
@@ -502,9 +557,9 @@ bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
   if (nC > cap || nA > cap || nB > cap) return false;
   if (geo.roundsC * geo.threads < nC || geo.roundsA * geo.threads < nA || geo.roundsB * geo.threads < nB) return false;
   if (geo.roundsC > kMaxRounds || geo.roundsA > kMaxRounds || geo.roundsB > kMaxRounds) return false;
-  if (geo.qcap < 32 * std::max(geo.roundsA, geo.roundsB)) return false;
+  if (geo.qcap < 32 || geo.qcap % 32) return false;
   if (geo.smem != smem_bytes(g, geo.TY, geo.R, geo.nraw, geo.threads, geo.qcap)) return false;
-  return geo.smem <= 227 * 1024 && geo.nraw >= geo.R && geo.nbit >= 2 * geo.R + 3 && geo.nseg >= 1 &&
+  return geo.smem <= 227 * 1024 && geo.nraw >= geo.R && geo.nbit == 4 * geo.R + 2 && geo.nseg >= 1 &&
          geo.nseg <= (g.nd == 3 ? g.Lz : g.Ly);
 }
 
