@@ -49,6 +49,9 @@ ATTEMPTS_PER_STEP = len(TEMPS_2D) * SWEEPS_2D * L2D * L2D + SWEEPS_3D * L3D ** 3
 WORKLOAD = ("2D Ising L=16384 (hot start, T in {2.0, 2.269185, 3.0}, 200 sweeps each) + "
             "3D Ising L=512 (hot start, beta=0.221654, 100 sweeps)")
 PROFILE_2D = os.path.join(ROOT, "profiles", "sweep_stream_2d_L16384.md")
+EA_L, EA_SAMPLES, EA_SWEEPS, EA_EVERY = 32, 1024, 10000, 10
+SERVED_REQUESTS = 400  # prefix of the 2000-request stream served by default (bounded run time)
+LOOP_SUBSET = 256  # instances of the uneven batch timed through the per-instance launch loop
 KERNEL_SRC = os.path.join(ROOT, "paper_1006_3865_gb300", "csrc", "stream.cu")
 
 
@@ -63,6 +66,12 @@ def _args():
     p.add_argument("--profile-case", choices=["2d", "3d"], default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
+    p.add_argument("--forms", default="batched,ea,served",
+                   help="extra forms measured after the plain step (comma list; empty for none)")
+    p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
+    p.add_argument("--ea-sweeps", type=int, default=EA_SWEEPS)
+    p.add_argument("--served-requests", type=int, default=SERVED_REQUESTS,
+                   help="requests of the 2000-request stream served (a prefix)")
     return p.parse_args()
 
 
@@ -194,6 +203,141 @@ def _cpu_baseline(sweeps: int = 1):
                       f"beta=0.221654 ({att:.3g} attempts, {dt:.1f} s)"}
 
 
+def _timed(stream, fn):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def form_batched(stream):
+    """4096 uneven 2D instances (L = 2^5 .. 2^11, T on [1.5, 3.5], 100 .. 2000
+    sweeps, hot starts): one persistent resident kernel per lattice shape under a
+    CUDA graph, against the per-instance launch loop on a subset."""
+    import numpy as np
+
+    from paper_1006_3865_gb300 import inputs, spn
+
+    inst = inputs.uneven_batch()
+    jobs = [(spn.SPN_ISING2D, i.dims, i.beta, i.nsweeps, i.seed, k) for k, i in enumerate(inst)]
+    att = sum(i.dims[0] * i.dims[1] * i.nsweeps for i in inst)
+    m = spn.Multi(jobs)
+    m.set_stream(stream)
+    m.run(spn.SPN_RUN_BATCHED)  # captures the graph
+    ms = _timed(stream, lambda: m.run(spn.SPN_RUN_BATCHED))
+    m.close()
+    sub = jobs[:LOOP_SUBSET]
+    att_sub = sum(i.dims[0] * i.dims[1] * i.nsweeps for i in inst[:LOOP_SUBSET])
+    ms_sub = {}
+    res = {}
+    for mode, name in ((spn.SPN_RUN_LOOP, "loop"), (spn.SPN_RUN_BATCHED, "batched")):
+        m = spn.Multi(sub)
+        m.set_stream(stream)
+        m.run(mode)
+        ms_sub[name] = _timed(stream, lambda: m.run(mode))
+        res[name] = [m.result(k) for k in (0, LOOP_SUBSET // 2, LOOP_SUBSET - 1)]
+        m.close()
+    same = all(np.array_equal(x, y) for a, b in zip(res["loop"], res["batched"]) for x, y in zip(a, b))
+    return {"value": att / (ms * 1e6), "unit": UNIT, "ms": ms, "attempts": att,
+            "workload": "4096 uneven 2D Ising instances, L = 2^k (k uniform on 5..11), T uniform on [1.5, 3.5], "
+                        "sweeps uniform on [100, 2000], hot starts; persistent resident kernel under CUDA graphs",
+            "subset": {"instances": LOOP_SUBSET, "attempts": att_sub,
+                       "batched": att_sub / (ms_sub["batched"] * 1e6), "loop": att_sub / (ms_sub["loop"] * 1e6),
+                       "identical_results": same}}
+
+
+def form_ea(stream, sweeps):
+    """3D +-J EA, L = 32, 1024 disorder samples, 32 temperatures geometric on
+    [0.2, 2.0] per sample, multi-spin coded (2 samples x 32 temperature slots per
+    64-bit word), replica exchange every 10 sweeps on the device."""
+    from paper_1006_3865_gb300 import inputs, spn
+
+    dims = (EA_L, EA_L, EA_L)
+    bonds = inputs.ea_bonds(dims, EA_SAMPLES, inputs.unit_seed(0xEA))
+    b = spn.EABatch(dims, bonds, inputs.geometric_ladder(0.2, 2.0), inputs.unit_seed(0xEB), exchange_every=EA_EVERY)
+    b.set_stream(stream)
+    b.sweep(EA_EVERY)
+    ms = _timed(stream, lambda: b.sweep(sweeps))
+    b.close()
+    att = EA_SAMPLES * 32 * EA_L ** 3 * sweeps
+    return {"value": att / (ms * 1e6), "unit": UNIT, "ms": ms, "attempts": att, "sweeps": sweeps,
+            "workload": f"3D +-J EA L={EA_L}, {EA_SAMPLES} samples x 32 temperatures on [0.2, 2.0], multi-spin "
+                        f"coded, exchange every {EA_EVERY} sweeps, {sweeps} sweeps (attempts count every replica)"}
+
+
+def form_served(n_requests, budget_bytes=120 * 10**9):
+    """Poisson stream of 2000 requests (mean gap 0.5 ms) mixing 2D Ising (L
+    64..4096), 3D Ising (L 16..256) and 3D EA (L 8..32, 32-temperature ladders),
+    T on [0.5, 4.0], 1e2..1e4 sweeps; admission against a 120 GB budget."""
+    import numpy as np
+
+    from paper_1006_3865_gb300 import inputs, spn
+
+    reqs = inputs.served_stream()[:n_requests]
+    srv = spn.Server(budget_bytes)
+    tickets = []
+    pending = set()
+    att = 0
+    t0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        while time.perf_counter() - t0 < r.arrival_s:
+            pass
+        if r.model == 3:
+            t = srv.submit(spn.SPN_EA3D_PMJ, r.dims, r.nsweeps, r.seed, betas=r.betas, couplings=r.bonds[0],
+                           exchange_every=EA_EVERY)
+            att += 32 * int(np.prod(r.dims)) * r.nsweeps
+        else:
+            t = srv.submit(r.model, r.dims, r.nsweeps, r.seed, beta=r.beta, stream=k)
+            att += int(np.prod(r.dims)) * r.nsweeps
+        tickets.append(t)
+        pending.add(t)
+    while pending:
+        for t in list(pending):
+            if srv.poll(t)[0]:
+                pending.discard(t)
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    lat = []
+    first, last = None, 0.0
+    for t in tickets:
+        done, res = srv.poll(t)
+        if res.status != 0:
+            raise RuntimeError(f"served request {t} failed with status {res.status}")
+        lat.append(res.t_done - res.t_submit)
+        first = res.t_submit if first is None else min(first, res.t_submit)
+        last = max(last, res.t_done)
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat) * 1e3
+    span = last - first
+    return {"value": att / (span * 1e9), "unit": UNIT, "requests": len(reqs), "attempts": att,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "span_s": span, "wall_s": wall, "rounds": st["rounds"],
+            "offered": att / (reqs[-1].arrival_s * 1e9),
+            "workload": f"first {len(reqs)} of 2000 Poisson requests, mean gap 0.5 ms: 2D Ising L 64..4096, 3D Ising L 16..256, 3D EA "
+                        "L 8..32 (32-T ladders on [T, 10T]), T on [0.5, 4.0], sweeps 1e2..1e4 log-uniform; "
+                        "120 GB budget; latency = submit -> result on the host"}
+
+
+def run_forms(a, stream):
+    out = {}
+    for f in [x for x in a.forms.split(",") if x]:
+        if f == "batched":
+            out["batched"] = form_batched(stream)
+        elif f == "ea":
+            out["ea"] = form_ea(stream, a.ea_sweeps)
+        elif f == "served":
+            out["served"] = form_served(a.served_requests)
+        else:
+            raise SystemExit(f"unknown form {f}")
+    return out
+
+
 def run_reference(a):
     dist, rank, ws, _ = _dist()
     if rank != 0:
@@ -246,6 +390,9 @@ def main():
     spn_build.build()
     spn.load()
     stream = torch.cuda.Stream()
+    if a.forms_only:
+        print(json.dumps({"forms": run_forms(a, stream)}), flush=True)
+        return
     seeds2 = [inputs.unit_seed(1000 * rank + i) for i in range(len(TEMPS_2D))]
     seed3 = inputs.unit_seed(1000 * rank + 99)
     lat2 = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), seeds2[0])
@@ -352,6 +499,7 @@ def main():
 
     lat2.close()
     lat3.close()
+    forms = run_forms(a, stream) if rank == 0 else None
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         cpu = _cpu_baseline(1)
@@ -375,6 +523,7 @@ def main():
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "forms": forms,
     }
     print(json.dumps(out), flush=True)
 
