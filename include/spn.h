@@ -21,13 +21,20 @@
  *     bit-packed uint64 words [sample][dir][ceil(N/64)], bit (n % 64) of word
  *     n / 64 set iff J(n, dir) = -1 for the bond from n to n + e_dir.
  *   - Memory: the library owns every device buffer it allocates; host buffers
- *     passed in are read (or written) during the call only.  Device-pointer
- *     entry points (spn_dev_*) never allocate and never free.
- *   - Randomness: Philox4x32-10 keyed by the 64-bit seed; counters (group m>>3,
- *     sweep, colour | purpose<<1, stream).  A site's 32-bit Metropolis number is
- *     (high 16 bits from purpose 0) << 16 | (low 16 bits from purpose 1); a
- *     move with dE > 0 is accepted iff u < floor(exp(-beta dE) * 2^32).  Results
- *     are bit-identical for a given (seed, stream, sweep index, beta).
+ *     passed in are read (or written) during the call only.  The device-pointer
+ *     entry point spn_sweep_noalloc never allocates and never frees.
+ *   - Randomness: Philox4x32-10 keyed by the 64-bit seed.  Each row of the
+ *     lattice is cut into 64-site words; the sites of one colour in word j of
+ *     row r = y + Ly z form group g = j + ceil(Lx / 64) r, site x at lane
+ *     (x & 63) >> 1.  Plane q (0..31) of a group is word q & 3 of
+ *     R(8 g + q / 4, sweep, colour | purpose << 1, stream); bit 31 - q of a
+ *     site's 32-bit number is its lane's bit of plane q (purpose 0: Metropolis,
+ *     1: hot start, which takes bit 31 as "spin -1").  A move with dE > 0 is
+ *     accepted iff u < floor(exp(-beta dE) * 2^32) (Eq. 2).  The multi-spin
+ *     coded EA sweep uses word m & 3 of R(m >> 2, sweep, colour | 3 << 1,
+ *     sample) for within-colour index m; replica exchange word k & 3 of
+ *     R(k >> 2, step, 2 << 1, sample).  Results are bit-identical for a given
+ *     (seed, stream, sweep index, beta) on every path.
  *   - A handle is not thread-safe; a server is.
  */
 #ifndef SPN_H
@@ -170,9 +177,9 @@ enum spn_run_mode {
 };
 
 /* Allocate the lattices and traces of njobs jobs (copied).  Every lattice must
- * fit the resident kernel: Lx in {2, 4, 8, 16, 32} or a multiple of 64, and its
- * bits (N / 8 bytes) in a cluster of at most 8 CTAs x 200 KB; SPN_E_ARG
- * otherwise. */
+ * fit the resident kernel: its bits (2 ceil(Lx / 64) words per row) in a cluster
+ * of at most 8 CTAs x 200 KB, the rows split evenly among the cluster's CTAs;
+ * SPN_E_ARG otherwise. */
 int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs);
 
 /* Run every job from its hot start (asynchronous on the run's stream).  Both

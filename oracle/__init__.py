@@ -116,6 +116,7 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def site_word(seed: int, stream: int, t: int, colour: int, purpose: int, m: int) -> int:
+    """Plane word of site key m (the within-colour index when Lx % 64 == 0)."""
     return int(lib().orc_site_word(seed, stream, t, colour, purpose, m))
 
 

@@ -28,11 +28,16 @@
  *   threshold thr(beta, dE) = floor(exp(-beta*dE) * 2^32) for dE > 0 (Eq. 2),
  *             a value in [0, 2^32]; dE <= 0 is always accepted.
  *   random    R(c0,c1,c2,c3) = Philox4x32-10 with key (seed lo32, seed hi32).
- *             A site with within-colour index m lies in group g = m >> 5 at
- *             lane i = m & 31.  The group owns 32 "planes": plane q (0..31) is
+ *             Each row (y, z) of the lattice is cut into words of 64 sites,
+ *             x = 64 j .. 64 j + 63 (the last word of a row is shorter when
+ *             Lx is not a multiple of 64); the sites of one colour in word j
+ *             of row r = y + Ly z form group g = j + ceil(Lx / 64) r, site x
+ *             at lane i = (x & 63) >> 1.  The site key is k = 32 g + i; when
+ *             Lx is a multiple of 64 it equals the within-colour index m.  The
+ *             group owns 32 "planes": plane q (0..31) is
  *             word q & 3 of R(8g + (q >> 2), t, c | (p << 1), stream).  Bit
  *             31 - q of the site word is bit i of plane q, so plane 0 carries the
- *             most significant bits of 32 sites.  Purposes p:
+ *             most significant bits of the group's sites.  Purposes p:
  *               0  Metropolis u at sweep t, colour c
  *               1  hot start (t = 0)
  *             The 32-bit u is uniform; storing it across planes lets a GPU
@@ -88,8 +93,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Site word of within-colour index m for purpose p: bit 31 - q is bit (m & 31)
- * of plane q = word q & 3 of R(8 (m >> 5) + (q >> 2), t, c | (p << 1), stream). */
+/* Site word of site key m for purpose p: bit 31 - q is bit (m & 31) of plane q
+ * = word q & 3 of R(8 (m >> 5) + (q >> 2), t, c | (p << 1), stream). */
 uint32_t orc_site_word(uint64_t seed, uint32_t stream, uint32_t t, int colour, int purpose, uint64_t m) {
   const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
   const uint32_t lane = (uint32_t)(m & 31);
@@ -179,6 +184,13 @@ static int64_t lat_step(const lat_t* g, int64_t n, int d, int dir) {
   return lat_index(g, x);
 }
 
+/* Site key of n: 32 (word of its row, counted over all rows) + lane. */
+static uint64_t lat_key(const lat_t* g, int64_t n) {
+  const int64_t x = n % g->L[0], row = n / g->L[0];
+  const int64_t words = (g->L[0] + 63) / 64;
+  return (uint64_t)(32 * ((x >> 6) + words * row) + ((x & 63) >> 1));
+}
+
 static int lat_colour(const lat_t* g, int64_t n) {
   int64_t x[3];
   lat_coords(g, n, x);
@@ -231,7 +243,7 @@ int orc_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, int8_
   if (lat_make(&g, nd, L)) return -1;
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < g.N; ++n) {
-    uint32_t w = orc_hot_word(seed, stream, lat_colour(&g, n), (uint64_t)(n >> 1));
+    uint32_t w = orc_hot_word(seed, stream, lat_colour(&g, n), lat_key(&g, n));
     s[n] = (w >> 31) ? -1 : 1;
   }
   return 0;
@@ -253,7 +265,7 @@ static void half_sweep(const lat_t* g, int8_t* s, const uint64_t* bonds, const u
       acc = 1;
     } else {
       uint32_t u = umode ? orc_msc_u(seed, stream, sweep, c, (uint64_t)(n >> 1))
-                         : orc_metropolis_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
+                         : orc_metropolis_u(seed, stream, sweep, c, lat_key(g, n));
       acc = (uint64_t)u < thr[dE / 4];
     }
     if (acc) {
@@ -307,7 +319,7 @@ int orc_ea_init_hot(const int64_t* L, int nsamples, uint64_t seed, uint32_t stre
   if (lat_make(&g, 3, L)) return -1;
   for (int i = 0; i < nsamples; ++i)
     for (int64_t n = 0; n < g.N; ++n)
-      sp[(int64_t)i * g.N + n] = orc_hot_word(seed, stream0 + (uint32_t)i, lat_colour(&g, n), (uint64_t)(n >> 1));
+      sp[(int64_t)i * g.N + n] = orc_hot_word(seed, stream0 + (uint32_t)i, lat_colour(&g, n), lat_key(&g, n));
   return 0;
 }
 

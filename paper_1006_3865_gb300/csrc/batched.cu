@@ -27,43 +27,6 @@ namespace spn {
 
 namespace {
 
-// Metropolis decision of a partial (Lx < 64) or full word whose site bit i is
-// lane o + i of its Philox group: planes are shifted right by o.
-template <int NC>
-__device__ __forceinline__ uint32_t lazy_accept_shifted(uint32_t acc, const uint32_t (&cls)[NC], const DevThr& T,
-                                                        const PhiloxKeys& K, uint32_t c0, uint32_t sweep, uint32_t c2,
-                                                        uint32_t stream_id, uint32_t o) {
-  uint32_t eq[NC];
-  uint32_t pend = 0;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    const bool always = (T.always >> (q + 1)) & 1u;
-    acc |= always ? cls[q] : 0u;
-    eq[q] = always ? 0u : cls[q];
-    pend |= eq[q];
-  }
-#pragma unroll 1
-  for (uint32_t call = 0; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
-    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
-    const uint32_t planes[4] = {P.x >> o, P.y >> o, P.z >> o, P.w >> o};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t u = planes[j];
-      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const uint32_t tm = 0u - ((T.t[q + 1] >> bit) & 1u);
-        acc |= eq[q] & ~u & tm;
-        eq[q] &= ~(u ^ tm);
-      }
-    }
-    pend = 0;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) pend |= eq[q];
-  }
-  return acc;
-}
-
 template <int ND, bool CLUSTER>
 __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -72,9 +35,13 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int Lx = a.Lx, Ly = a.Ly, Lz = ND == 3 ? a.Lz : 1;
   const int nrow = Ly * Lz;
-  const int W = Lx >= 64 ? Lx >> 6 : 1;
-  const int vb = Lx >= 64 ? 32 : Lx >> 1;  // valid bits per word
-  const uint32_t vmask = vb == 32 ? 0xffffffffu : ((1u << vb) - 1u);
+  // A row is W words per parity; every word holds 32 sites but the last, which
+  // holds vbl (its unused high bits stay zero).
+  const int W = (Lx + 63) >> 6;
+  const int vbl = (Lx - 64 * (W - 1)) >> 1;
+  auto vbits = [&](int j) { return j == W - 1 ? vbl : 32; };
+  auto vmaskj = [&](int j) { return j == W - 1 && vbl < 32 ? ((1u << vbl) - 1u) : 0xffffffffu; };
+  const bool vec_io = (Lx & 63) == 0;  // whole 64-byte spans, 16-byte aligned
   int CS = 1, rank = 0;
   if constexpr (CLUSTER) {
     CS = (int)cg::this_cluster().num_blocks();
@@ -135,11 +102,12 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
       uint32_t wv = 0;
       if (in.init_hot) {
         const int c = (y + z + p) & 1;
-        const uint32_t mstart = (uint32_t)(Lx >> 1) * (uint32_t)r + 32u * (uint32_t)j;
-        const uint32_t plane0 = philox10(8u * (mstart >> 5), 0u, (uint32_t)c | (kInit << 1), in.stream, K).x;
-        wv = (plane0 >> (mstart & 31)) & vmask;
+        const uint32_t plane0 =
+            philox10(8u * ((uint32_t)j + (uint32_t)W * (uint32_t)r), 0u, (uint32_t)c | (kInit << 1), in.stream, K).x;
+        wv = plane0 & vmaskj(j);
       } else {
         const int8_t* row = in.spins + (int64_t)r * Lx;
+        const int vb = vbits(j);
         for (int i = 0; i < vb; ++i) wv |= (row[64 * j + 2 * i + p] < 0 ? 1u : 0u) << i;
       }
       bits[(size_t)lr * 2 * W + p * W + j] = wv;
@@ -151,25 +119,16 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
     auto counts = [&](int r, int j, int par, uint32_t b, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
       const uint32_t* row = row_ptr(r);
       const uint32_t* other = row + (1 - par) * W;
+      const uint32_t o = other[j];
       uint32_t left, right;
-      if (W >= 2) {
-        const int jm = j == 0 ? W - 1 : j - 1, jp = j + 1 == W ? 0 : j + 1;
-        if (par == 0) {
-          right = other[j];
-          left = __funnelshift_l(other[jm], other[j], 1);
-        } else {
-          left = other[j];
-          right = __funnelshift_r(other[j], other[jp], 1);
-        }
-      } else {  // the row is one word: rotate within vb bits
-        const uint32_t o = other[0];
-        if (par == 0) {
-          right = o;
-          left = ((o << 1) | (o >> (vb - 1))) & vmask;
-        } else {
-          left = o;
-          right = ((o >> 1) | (o << (vb - 1))) & vmask;
-        }
+      if (par == 0) {  // even x: x + 1 is odd lane i; x - 1 is odd lane i - 1, or the previous word's last site
+        const int jm = j == 0 ? W - 1 : j - 1;
+        right = o;
+        left = (o << 1) | ((other[jm] >> (vbits(jm) - 1)) & 1u);
+      } else {  // odd x: x - 1 is even lane i; x + 1 is even lane i + 1, or the next word's first site
+        const int jp = j + 1 == W ? 0 : j + 1;
+        left = o;
+        right = (o >> 1) | ((other[jp] & 1u) << (vbits(j) - 1));
       }
       const int y = r % Ly, z = r / Ly;
       const int rym = y == 0 ? r + Ly - 1 : r - 1, ryp = y + 1 == Ly ? r - Ly + 1 : r + 1;
@@ -191,6 +150,8 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
         const int lr = it / W, j = it - lr * W;
         const int r = r0 + lr;
         const int y = r % Ly, z = r / Ly;
+        const int vb = vbits(j);
+        const uint32_t vmask = vmaskj(j);
         for (int p = 0; p < 2; ++p) {
           const uint32_t b = bits[(size_t)lr * 2 * W + p * W + j];
           m += vb - 2 * __popc(b & vmask);
@@ -232,12 +193,11 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
           const uint32_t b = *wp;
           uint32_t s0, s1, s2;
           counts(r, j, par, b, s0, s1, s2);
-          const uint32_t valid = live ? vmask : 0u;
+          const uint32_t valid = live ? vmaskj(j) : 0u;
           uint32_t cls[ND];
           const uint32_t acc0 = classes<ND>(s0, s1, s2, valid, cls);
-          const uint32_t mstart = (uint32_t)(Lx >> 1) * (uint32_t)r + 32u * (uint32_t)j;
-          const uint32_t flips = lazy_accept_shifted<ND>(acc0, cls, in.T, K, 8u * (mstart >> 5), sweep,
-                                                          (uint32_t)c | (kMetropolis << 1), in.stream, mstart & 31);
+          const uint32_t flips = lazy_accept<ND>(acc0, cls, in.T, K, 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)r),
+                                                 sweep, (uint32_t)c | (kMetropolis << 1), in.stream);
           if (live) {
             tally<ND>(flips, b, s0, s1, s2, de, dm);
             *wp = b ^ flips;  // only this thread reads or writes this colour-c word in this phase
@@ -259,7 +219,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
       const int r = r0 + lr;
       const uint32_t E = bits[(size_t)lr * 2 * W + j], O = bits[(size_t)lr * 2 * W + W + j];
       int8_t* row = in.spins + (int64_t)r * Lx;
-      if (Lx >= 64) {
+      if (vec_io) {
         uint4* dst = reinterpret_cast<uint4*>(row + 64 * j);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -268,9 +228,10 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
           dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
         }
       } else {
+        const int vb = vbits(j);
         for (int i = 0; i < vb; ++i) {
-          row[2 * i] = ((E >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
-          row[2 * i + 1] = ((O >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
+          row[64 * j + 2 * i] = ((E >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
+          row[64 * j + 2 * i + 1] = ((O >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
         }
       }
     }
@@ -281,14 +242,14 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
 }  // namespace
 
 bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs) {
-  if (!(Lx == 2 || Lx == 4 || Lx == 8 || Lx == 16 || Lx == 32 || (Lx % 64 == 0))) return false;
+  if (Lx < 2 || (Lx & 1)) return false;
   const int nrow = Ly * (nd == 3 ? Lz : 1);
   if (cs < 1 || cs > 8 || nrow % cs) return false;
   return resident_smem(nd, Lx, Ly, Lz, cs) <= 200 * 1024;
 }
 
 size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs) {
-  const int W = Lx >= 64 ? Lx / 64 : 1;
+  const int W = (Lx + 63) / 64;
   const int nrow = Ly * (nd == 3 ? Lz : 1);
   return (size_t)(nrow / cs) * 2 * W * 4 + 256 * 8;
 }

@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) {
 
 // hot start: the replica bits of site n are its 32-bit hot-start word, bit
 // 31 - q = bit (m & 31) of plane q = word q & 3 of R(8 (m >> 5) + q / 4, 0, c | 1 << 1, sample)
+// for the site key m = 32 (x / 64 + ceil(Lx / 64) r) + (x % 64) / 2 of row r
 __global__ void k_ea_init(uint64_t* words, int Lx, int Ly, int N, int nsamples, PhiloxKeys K) {
   const int64_t total = (int64_t)nsamples * N;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -290,7 +291,7 @@ __global__ void k_ea_init(uint64_t* words, int Lx, int Ly, int N, int nsamples, 
     const int n = (int)(i - (int64_t)sample * N);
     const int x = n % Lx, r = n / Lx, y = r % Ly, z = r / Ly;
     const int c = (x + y + z) & 1;
-    const uint32_t m = (uint32_t)n >> 1;
+    const uint32_t m = 32u * (uint32_t)((x >> 6) + ((Lx + 63) >> 6) * r) + (uint32_t)((x & 63) >> 1);  // site key
     uint32_t u = 0;
     for (uint32_t call = 0; call < 8; ++call) {
       const U4 P = philox10(8u * (m >> 5) + call, 0u, (uint32_t)c | (kInit << 1), (uint32_t)sample, K);

@@ -69,18 +69,23 @@ int device_sm_count() {
 
 // ---------------------------------------------------------------- init / E, M
 
-__global__ void k_init_hot(int8_t* __restrict__ s, int Lx, int Ly, int64_t N, PhiloxKeys K, uint32_t stream_id) {
-  const int64_t half = N >> 1;
-  const int64_t ngroups = (half + 31) >> 5;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 2 * ngroups;
-       t += (int64_t)gridDim.x * blockDim.x) {
+// Hot start: one thread per group (row r, 64-site word j, colour c); site
+// x = 64 j + 2 i + par of the group takes bit i of plane 0 of its group.
+__global__ void k_init_hot(int8_t* __restrict__ s, int Lx, int Ly, int64_t nrow, PhiloxKeys K, uint32_t stream_id) {
+  const int W = (Lx + 63) >> 6;
+  const int64_t total = 2 * nrow * W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(t & 1);
-    const int64_t g = t >> 1;
+    const int64_t g = t >> 1;  // j + W r
+    const int64_t r = g / W;
+    const int j = (int)(g - r * W);
+    const int par = (int)((c + r % Ly + r / Ly) & 1);
     const uint32_t plane0 = philox10((uint32_t)(8 * g), 0u, (uint32_t)c | (kInit << 1), stream_id, K).x;
+    int8_t* row = s + r * Lx;
     for (int i = 0; i < 32; ++i) {
-      const int64_t m = g * 32 + i;
-      if (m >= half) break;
-      s[site_of(m, c, Lx, Ly)] = ((plane0 >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
+      const int x = 64 * j + 2 * i + par;
+      if (x >= Lx) break;
+      row[x] = ((plane0 >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
     }
   }
 }
@@ -115,10 +120,11 @@ __global__ void k_observables(const int8_t* __restrict__ s, const uint8_t* __res
 }
 
 cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t stream_id, cudaStream_t st) {
-  const int64_t work = 2 * (((g.N >> 1) + 31) >> 5);
+  const int64_t nrow = g.N / g.Lx;
+  const int64_t work = 2 * nrow * ((g.Lx + 63) / 64);
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((work + threads - 1) / threads, (int64_t)device_sm_count() * 32);
-  k_init_hot<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(s, g.Lx, g.Ly, g.N, philox_keys(seed),
+  k_init_hot<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(s, g.Lx, g.Ly, nrow, philox_keys(seed),
                                                                          stream_id);
   count_launches(1);
   return cudaGetLastError();
@@ -138,14 +144,15 @@ cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long 
 
 // ------------------------------------------------------------ generic sweep
 
-// One colour c of sweep `sweep`, in place: a thread owns the group of 32 sites
-// with within-colour indices 32 g .. 32 g + 31.
+// One colour c of sweep `sweep`, in place: a thread owns the sites of colour c
+// in one 64-site word of one row (group g = j + ceil(Lx/64) r, up to 32 sites).
 template <int ND>
 __global__ void k_sweep_generic(int8_t* __restrict__ s, const uint8_t* __restrict__ bonds, int Lx, int Ly, int Lz,
-                                int64_t N, int c, DevThr T, PhiloxKeys K, uint32_t stream_id, uint32_t sweep,
+                                int64_t nrow, int c, DevThr T, PhiloxKeys K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc) {
-  const int64_t half = N >> 1;
-  const int64_t ngroups = (half + 31) >> 5;
+  const int W = (Lx + 63) >> 6;
+  const int64_t ngroups = nrow * W;
+  const int64_t LxLy = (int64_t)Lx * Ly;
   int de = 0, dm = 0;
   // warp-uniform trip count: the decision votes across the warp
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -153,25 +160,29 @@ __global__ void k_sweep_generic(int8_t* __restrict__ s, const uint8_t* __restric
   for (int64_t g0 = base; g0 < ngroups; g0 += stride) {
     const int64_t g = g0 + (threadIdx.x & 31);
     uint32_t bits = 0, s0 = 0, s1 = 0, s2 = 0, valid = 0;
+    int64_t rowbase = 0;
+    int j = 0, par = 0;
     if (g < ngroups) {
+      const int64_t r = g / W;
+      j = (int)(g - r * W);
+      const int y = (int)(r % Ly), z = (int)(r / Ly);
+      par = (c + y + z) & 1;
+      rowbase = r * Lx;
+      const int64_t dym = (int64_t)((y == 0 ? Ly - 1 : y - 1) - y) * Lx;
+      const int64_t dyp = (int64_t)((y + 1 == Ly ? 0 : y + 1) - y) * Lx;
+      const int64_t dzm = (int64_t)((z == 0 ? Lz - 1 : z - 1) - z) * LxLy;
+      const int64_t dzp = (int64_t)((z + 1 == Lz ? 0 : z + 1) - z) * LxLy;
       for (int i = 0; i < 32; ++i) {
-        const int64_t m = g * 32 + i;
-        if (m >= half) break;
-        const int64_t n = site_of(m, c, Lx, Ly);
-        const int x = (int)(n % Lx);
-        const int64_t r = n / Lx;
-        const int y = (int)(r % Ly);
-        const int z = (int)(r / Ly);
+        const int x = 64 * j + 2 * i + par;
+        if (x >= Lx) break;
+        const int64_t n = rowbase + x;
         const int sn = s[n];
-        const int64_t xm = n - x + (x == 0 ? Lx - 1 : x - 1), xp = n - x + (x + 1 == Lx ? 0 : x + 1);
-        const int64_t ym = n + (int64_t)((y == 0 ? Ly - 1 : y - 1) - y) * Lx;
-        const int64_t yp = n + (int64_t)((y + 1 == Ly ? 0 : y + 1) - y) * Lx;
+        const int64_t xm = rowbase + (x == 0 ? Lx - 1 : x - 1), xp = rowbase + (x + 1 == Lx ? 0 : x + 1);
+        const int64_t ym = n + dym, yp = n + dyp;
         int h = bond_sign(bonds, n, 0) * s[xp] + bond_sign(bonds, xm, 0) * s[xm] +
                 bond_sign(bonds, n, 1) * s[yp] + bond_sign(bonds, ym, 1) * s[ym];
         if (ND == 3) {
-          const int64_t LxLy = (int64_t)Lx * Ly;
-          const int64_t zm = n + (int64_t)((z == 0 ? Lz - 1 : z - 1) - z) * LxLy;
-          const int64_t zp = n + (int64_t)((z + 1 == Lz ? 0 : z + 1) - z) * LxLy;
+          const int64_t zm = n + dzm, zp = n + dzp;
           h += bond_sign(bonds, n, 2) * s[zp] + bond_sign(bonds, zm, 2) * s[zm];
         }
         const int k = (2 * ND - sn * h) / 2;  // anti-aligned (unsatisfied) bonds
@@ -188,7 +199,7 @@ __global__ void k_sweep_generic(int8_t* __restrict__ s, const uint8_t* __restric
     if (flips) {
       for (int i = 0; i < 32; ++i) {
         if ((flips >> i) & 1u) {
-          const int64_t n = site_of(g * 32 + i, c, Lx, Ly);
+          const int64_t n = rowbase + 64 * j + 2 * i + par;
           s[n] = (int8_t)(-s[n]);
         }
       }
@@ -199,16 +210,17 @@ __global__ void k_sweep_generic(int8_t* __restrict__ s, const uint8_t* __restric
 
 cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, const PhiloxKeys& K,
                                  uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st) {
-  const int64_t ngroups = ((g.N >> 1) + 31) >> 5;
+  const int64_t nrow = g.N / g.Lx;
+  const int64_t ngroups = nrow * ((g.Lx + 63) / 64);
   const int threads = 128;
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ngroups + threads - 1) / threads,
                                                                 (int64_t)device_sm_count() * 16));
   for (int c = 0; c < 2; ++c) {
     if (g.nd == 3)
-      k_sweep_generic<3><<<(unsigned)blocks, threads, 0, st>>>(s, g.bonds, g.Lx, g.Ly, g.Lz, g.N, c, T, K,
+      k_sweep_generic<3><<<(unsigned)blocks, threads, 0, st>>>(s, g.bonds, g.Lx, g.Ly, g.Lz, nrow, c, T, K,
                                                                stream_id, sweep, acc);
     else
-      k_sweep_generic<2><<<(unsigned)blocks, threads, 0, st>>>(s, g.bonds, g.Lx, g.Ly, g.Lz, g.N, c, T, K,
+      k_sweep_generic<2><<<(unsigned)blocks, threads, 0, st>>>(s, g.bonds, g.Lx, g.Ly, g.Lz, nrow, c, T, K,
                                                                stream_id, sweep, acc);
   }
   count_launches(2);

@@ -197,12 +197,12 @@ int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs) {
     Group g;
     std::tie(g.nd, g.Lx, g.Ly, g.Lz) = kv.first;
     g.cs = spn::resident_cluster_size(g.nd, g.Lx, g.Ly, g.Lz);
-    if (g.cs == 0) return bail(SPN_E_ARG, "a job lattice does not fit the resident batched kernel (Lx in {2..32} "
-                                          "or a multiple of 64, at most 8 x 200 KB of bits)");
+    if (g.cs == 0) return bail(SPN_E_ARG, "a job lattice does not fit the resident batched kernel (at most "
+                                          "8 x 200 KB of bits, rows divisible among the cluster)");
     g.jobs = kv.second;
     std::stable_sort(g.jobs.begin(), g.jobs.end(),
                      [&](int a, int b) { return m->jobs[a].nsweeps > m->jobs[b].nsweeps; });
-    const int W = g.Lx >= 64 ? g.Lx / 64 : 1;
+    const int W = (g.Lx + 63) / 64;
     const int items = g.Ly * (g.nd == 3 ? g.Lz : 1) / g.cs * W;
     g.threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
     const size_t smem = spn::resident_smem(g.nd, g.Lx, g.Ly, g.Lz, g.cs);

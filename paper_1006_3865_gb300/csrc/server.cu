@@ -252,7 +252,7 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
       a.Ly = Ly;
       a.Lz = Lz;
       a.err = s->d_err;
-      const int W = Lx >= 64 ? Lx / 64 : 1;
+      const int W = (Lx + 63) / 64;
       const int items = Ly * (nd == 3 ? Lz : 1) / cs * W;
       const int threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
       const size_t smem = spn::resident_smem(nd, Lx, Ly, Lz, cs);

@@ -30,16 +30,6 @@ static __device__ __forceinline__ void block_accumulate(long long a, long long b
   }
 }
 
-// Site of colour c with within-colour index m: n = 2m or 2m + 1 (Lx even, so
-// both share y and z).
-static __device__ __forceinline__ int64_t site_of(int64_t m, int c, int Lx, int Ly) {
-  const int64_t n0 = 2 * m;
-  const int64_t r = n0 / Lx;  // y + Ly * z
-  const int y = (int)(r % Ly);
-  const int z = (int)(r / Ly);
-  return n0 + ((c ^ (y + z)) & 1);
-}
-
 // Metropolis decision for 32 sites.  cls[q-1]: sites whose move has dE = 4q > 0;
 // acc: sites already accepted (dE <= 0).  Plane p of the group (counter c0 + p/4)
 // holds bit 31 - p of every site's u; a site of class q is accepted iff

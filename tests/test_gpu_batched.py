@@ -23,7 +23,8 @@ def _jobs_small():
     rng = np.random.default_rng(11)
     jobs = []
     shapes = [(2, (32, 32)), (2, (64, 64)), (2, (128, 64)), (2, (256, 256)), (2, (16, 8)), (2, (2, 2)),
-              (3, (16, 16, 16)), (3, (64, 8, 4)), (2, (64, 64)), (2, (1024, 1024))]
+              (3, (16, 16, 16)), (3, (64, 8, 4)), (2, (64, 64)), (2, (1024, 1024)),
+              (2, (34, 18)), (2, (130, 6)), (2, (202, 100)), (3, (6, 4, 10)), (3, (70, 6, 4)), (2, (1000, 998))]
     for k, (nd, dims) in enumerate(shapes):
         model = spn.SPN_ISING2D if nd == 2 else spn.SPN_ISING3D
         T = float(rng.uniform(1.5, 3.5)) if nd == 2 else float(rng.uniform(3.5, 5.5))
@@ -90,5 +91,7 @@ def test_uneven_batch_subset_against_loop():
 
 
 def test_rejects_unsupported_shapes():
-    with pytest.raises(spn.SpnError):
-        spn.Multi([(spn.SPN_ISING2D, (48, 48), 0.4, 3, 1, 0)])
+    with pytest.raises(spn.SpnError):  # 4 MB of bits: more than a cluster of 8 CTAs holds
+        spn.Multi([(spn.SPN_ISING2D, (8192, 4096), 0.4, 3, 1, 0)])
+    with pytest.raises(spn.SpnError):  # odd extent
+        spn.Multi([(spn.SPN_ISING2D, (48, 47), 0.4, 3, 1, 0)])
