@@ -178,7 +178,7 @@ enum spn_run_mode {
 
 /* Allocate the lattices and traces of njobs jobs (copied).  Every lattice must
  * fit the resident kernel: its bits (2 ceil(Lx / 64) words per row) in a cluster
- * of at most 8 CTAs x 200 KB, the rows split evenly among the cluster's CTAs;
+ * of at most 8 CTAs x 200 KB, the rows split among the cluster's CTAs;
  * SPN_E_ARG otherwise. */
 int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs);
 

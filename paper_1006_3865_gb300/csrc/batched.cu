@@ -33,23 +33,20 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
   __shared__ int s_idx;
   __shared__ long long s_em[2];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int Lx = a.Lx, Ly = a.Ly, Lz = ND == 3 ? a.Lz : 1;
-  const int nrow = Ly * Lz;
-  // A row is W words per parity; every word holds 32 sites but the last, which
+  // Extents of the current instance (instances of one launch may differ).  A
+  // row is W words per parity; every word holds 32 sites but the last, which
   // holds vbl (its unused high bits stay zero).
-  const int W = (Lx + 63) >> 6;
-  const int vbl = (Lx - 64 * (W - 1)) >> 1;
+  int Lx = 2, Ly = 2, Lz = 1, nrow = 2, W = 1, vbl = 1, rpc = 2, own = 2;
+  bool vec_io = false;  // whole 64-byte spans, 16-byte aligned
   auto vbits = [&](int j) { return j == W - 1 ? vbl : 32; };
   auto vmaskj = [&](int j) { return j == W - 1 && vbl < 32 ? ((1u << vbl) - 1u) : 0xffffffffu; };
-  const bool vec_io = (Lx & 63) == 0;  // whole 64-byte spans, 16-byte aligned
   int CS = 1, rank = 0;
   if constexpr (CLUSTER) {
     CS = (int)cg::this_cluster().num_blocks();
     rank = (int)cg::this_cluster().block_rank();
   }
-  const int rpc = nrow / CS;  // rows owned by this CTA
-  uint32_t* bits = reinterpret_cast<uint32_t*>(smem);  // rpc rows x 2W words
-  uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)rpc * 2 * W);
+  uint2* lut = reinterpret_cast<uint2*>(smem);               // 256 entries
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + 2048);  // rpc rows x 2W words
 
   for (int i = tid; i < 256; i += nth) {
     uint32_t lo = 0, hi = 0;
@@ -89,10 +86,19 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
     if (idx >= a.ninst) break;
     const ResInst in = a.inst[a.order[idx]];
     const PhiloxKeys K = philox_keys(in.seed);
+    Lx = in.Lx;
+    Ly = in.Ly;
+    Lz = ND == 3 ? in.Lz : 1;
+    nrow = Ly * Lz;
+    W = (Lx + 63) >> 6;
+    vbl = (Lx - 64 * (W - 1)) >> 1;
+    vec_io = (Lx & 63) == 0;
+    rpc = (nrow + CS - 1) / CS;  // rows per CTA; the last CTA of a cluster may own fewer
     const int r0 = rank * rpc;
+    own = nrow - r0 < rpc ? (nrow - r0 > 0 ? nrow - r0 : 0) : rpc;
 
     // ---- load: hot start from Philox or the int8 lattice
-    const int wordsOwn = rpc * 2 * W;
+    const int wordsOwn = own * 2 * W;
     for (int it = tid; it < wordsOwn; it += nth) {
       const int lr = it / (2 * W);
       const int rem = it - lr * 2 * W;
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
     // ---- E and M of the start (E = -sum over colour-1 sites of (2ND - 2k))
     {
       long long e = 0, m = 0;
-      const int items = rpc * W;
+      const int items = own * W;
       for (int it = tid; it < items; it += nth) {
         const int lr = it / W, j = it - lr * W;
         const int r = r0 + lr;
@@ -168,14 +174,14 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&s_em[1]), (unsigned long long)m);
       }
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0 && in.em0) {
         atomicAdd(in.em0 + 0, (unsigned long long)s_em[0]);
         atomicAdd(in.em0 + 1, (unsigned long long)s_em[1]);
       }
     }
 
     // ---- sweeps
-    const int items = rpc * W;
+    const int items = own * W;
     const int rounds = (items + nth - 1) / nth;
     for (int t = 0; t < in.nsweeps; ++t) {
       const uint32_t sweep = in.sweep0 + (uint32_t)t;
@@ -207,14 +213,14 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
       }
       long long lde = de, ldm = dm;
       warp_reduce_add2(lde, ldm);
-      if ((tid & 31) == 0 && (lde | ldm)) {
+      if ((tid & 31) == 0 && (lde | ldm) && in.trace) {
         atomicAdd(in.trace + 2 * t + 0, (unsigned long long)lde);
         atomicAdd(in.trace + 2 * t + 1, (unsigned long long)ldm);
       }
     }
 
     // ---- result: int8 lattice of the own rows
-    for (int it = tid; it < rpc * W; it += nth) {
+    for (int it = tid; it < own * W; it += nth) {
       const int lr = it / W, j = it - lr * W;
       const int r = r0 + lr;
       const uint32_t E = bits[(size_t)lr * 2 * W + j], O = bits[(size_t)lr * 2 * W + W + j];
@@ -244,14 +250,14 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
 bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs) {
   if (Lx < 2 || (Lx & 1)) return false;
   const int nrow = Ly * (nd == 3 ? Lz : 1);
-  if (cs < 1 || cs > 8 || nrow % cs) return false;
+  if (cs < 1 || cs > 8 || nrow < cs) return false;
   return resident_smem(nd, Lx, Ly, Lz, cs) <= 200 * 1024;
 }
 
 size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs) {
   const int W = (Lx + 63) / 64;
   const int nrow = Ly * (nd == 3 ? Lz : 1);
-  return (size_t)(nrow / cs) * 2 * W * 4 + 256 * 8;
+  return (size_t)((nrow + cs - 1) / cs) * 2 * W * 4 + 256 * 8;
 }
 
 int resident_cluster_size(int nd, int Lx, int Ly, int Lz) {
@@ -260,8 +266,7 @@ int resident_cluster_size(int nd, int Lx, int Ly, int Lz) {
   return 0;
 }
 
-cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, cudaStream_t st) {
-  const size_t smem = resident_smem(nd, a.Lx, a.Ly, a.Lz, cs);
+cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, size_t smem, cudaStream_t st) {
   void (*fn)(ResArgs) = nullptr;
   if (nd == 3)
     fn = cs > 1 ? k_resident<3, true> : k_resident<3, false>;

@@ -36,12 +36,6 @@
 
 namespace spn {
 
-// Exact division by a launch-invariant 32-bit divisor (Granlund-Montgomery
-// round-up method): q = (t + ((n - t) >> 1)) >> s with t = umulhi(n, m).
-struct FastDiv {
-  uint32_t d, m, s;
-};
-
 static FastDiv fastdiv(uint32_t d) {
   FastDiv f{d, 0, 0};
   if (d <= 1) return f;
@@ -58,30 +52,12 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
   return (t + ((n - t) >> 1)) >> f.s;
 }
 
-struct EaArgs {
-  uint64_t* words;            // [pairs][N] uint64
-  const uint8_t* bonds;       // [S][N] bond bytes (site order)
-  uint8_t* temp_of_slot;      // [S][32]
-  unsigned long long* xacc;   // [S][32] accepted exchanges per pair
-  const uint32_t* xtab;       // concatenated exchange tables
-  int xoff[32];               // offset of pair k's table in xtab
-  int xlen[32];               // its length (d = 1 .. xlen), 0 with xalways[k]
-  uint32_t xalways;           // bit k: pair k has equal betas (always accept)
-  uint32_t thr[3][32];        // thr[q-1][t] for dE = 4q, non-decreasing in t
-  int Lx, Ly, Lz, N;
-  FastDiv div_h, div_ly;      // by Lx / 2 and by Ly
-  uint32_t sweep0;
-  int nsweeps;
-  int exchange_every;
-  int nsamples;
-  PhiloxKeys K;
-  int* err;
-};
 
 // colour-separated shared-memory word index of site (x, y, z)
 __device__ __forceinline__ int ea_slot(int x, int row, int h) { return (row * 2 + (x & 1)) * h + (x >> 1); }
 
-__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) {
+// One sample (CTA) of a batch launch, or one served job of a multi-job launch.
+__device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int N = a.N, h = a.Lx >> 1, nrow = a.Ly * a.Lz;
   uint32_t* sp = reinterpret_cast<uint32_t*>(smem);           // N words
@@ -93,7 +69,6 @@ __global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) {
   uint8_t* sot = tos + 32;                                    // 32 slot_of_temp
   int* xcount = reinterpret_cast<int*>(sot + 32);             // 32 accepted exchanges this launch
 
-  const int sample = blockIdx.x;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
   const int pair = sample >> 1, half = sample & 1;
   const uint32_t* gw = reinterpret_cast<const uint32_t*>(a.words + (size_t)pair * N) + half;
@@ -281,6 +256,11 @@ __global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) { ea_run(a, blockIdx.x); }
+
+// Served jobs of one lattice size, one single-sample job per CTA.
+__global__ void __launch_bounds__(1024) k_ea_jobs(const EaArgs* __restrict__ list) { ea_run(list[blockIdx.x], 0); }
+
 // hot start: the replica bits of site n are its 32-bit hot-start word, bit
 // 31 - q = bit (m & 31) of plane q = word q & 3 of R(8 (m >> 5) + q / 4, 0, c | 1 << 1, sample)
 // for the site key m = 32 (x / 64 + ceil(Lx / 64) r) + (x % 64) / 2 of row r
@@ -376,6 +356,31 @@ void spn_ea_free(EaBatch* b) {
   cudaFree(b->d_err);
   delete b;
 }
+
+namespace spn {
+
+int ea_window_args(spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* threads) {
+  if (!h || !h->ea || h->ea->nsamples != 1) return SPN_E_STATE;
+  if (nsweeps < 0 || h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return SPN_E_ARG;
+  EaBatch* b = h->ea;
+  *out = b->args;
+  out->sweep0 = (uint32_t)h->sweeps;
+  out->nsweeps = (int)nsweeps;
+  *smem = b->smem;
+  *threads = b->threads;
+  h->sweeps += (uint64_t)nsweeps;
+  return SPN_OK;
+}
+
+cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_ea_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_ea_jobs<<<n, threads, smem, st>>>(d_list);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace spn
 
 extern "C" {
 

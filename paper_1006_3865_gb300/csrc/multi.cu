@@ -30,6 +30,7 @@ int mfail(int code, const char* msg) {
 
 struct Group {
   int nd, Lx, Ly, Lz, cs, threads, ctas;
+  size_t smem = 0;
   std::vector<int> jobs;  // job indices, longest first
   spn::ResInst* d_inst = nullptr;
   int* d_order = nullptr;
@@ -96,11 +97,8 @@ cudaError_t enqueue_batched(spn_multi_ctx* m) {
     a.ninst = (int)g.jobs.size();
     a.order = g.d_order;
     a.counter = m->d_counters + gi;
-    a.Lx = g.Lx;
-    a.Ly = g.Ly;
-    a.Lz = g.Lz;
     a.err = m->d_err;
-    if ((e = spn::launch_resident(a, g.nd, g.cs, g.threads, g.ctas, g.st)) != cudaSuccess) return e;
+    if ((e = spn::launch_resident(a, g.nd, g.cs, g.threads, g.ctas, g.smem, g.st)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(g.done, g.st)) != cudaSuccess) return e;
   }
   for (Group& g : m->groups)
@@ -203,9 +201,10 @@ int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs) {
     std::stable_sort(g.jobs.begin(), g.jobs.end(),
                      [&](int a, int b) { return m->jobs[a].nsweeps > m->jobs[b].nsweeps; });
     const int W = (g.Lx + 63) / 64;
-    const int items = g.Ly * (g.nd == 3 ? g.Lz : 1) / g.cs * W;
+    const int items = (g.Ly * (g.nd == 3 ? g.Lz : 1) + g.cs - 1) / g.cs * W;
     g.threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
     const size_t smem = spn::resident_smem(g.nd, g.Lx, g.Ly, g.Lz, g.cs);
+    g.smem = smem;
     const int maxc = spn::resident_max_ctas(g.nd, g.cs, g.threads, smem);
     g.ctas = std::max(g.cs, std::min<int>(maxc, (int)g.jobs.size() * g.cs));
     std::vector<spn::ResInst> inst(g.jobs.size());
@@ -222,6 +221,9 @@ int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs) {
       r.sweep0 = 0;
       r.nsweeps = (int)j.nsweeps;
       r.init_hot = 1;
+      r.Lx = g.Lx;
+      r.Ly = g.Ly;
+      r.Lz = g.Lz;
       r.T = spn::make_thresholds(j.beta);
       order[k] = (int)k;
     }

@@ -56,6 +56,7 @@ struct Job {
   int status = SPN_OK;
   double t_submit = 0, t_admit = 0, t_done = 0;
   int64_t done = 0;  // sweeps done
+  int64_t window = 0;  // sweeps of the current round
   size_t bytes = 0;  // device bytes charged to the budget
   int nd = 2;
   int64_t N = 0;
@@ -93,11 +94,14 @@ struct spn_server_ctx {
   std::vector<cudaEvent_t> pool_done;
   cudaEvent_t fork = nullptr;
   spn::ResInst* d_inst = nullptr;  // per-round resident instances
+  spn::EaArgs* d_ea = nullptr;     // per-round EA job blocks
+  size_t ea_cap = 0;
   int* d_order = nullptr;
   int* d_counters = nullptr;
   int* d_err = nullptr;
   size_t inst_cap = 0;
-  int64_t window_attempts = (int64_t)1 << 27;  // about this many attempts per job per round
+  int64_t window_attempts = (int64_t)1 << 26;  // at least this many attempts per job per round
+  int64_t round_attempts = (int64_t)1 << 35;   // about this many attempts per round in all
   std::atomic<unsigned long long> attempts{0};
   std::atomic<unsigned long long> rounds{0};
   double busy = 0;
@@ -187,36 +191,53 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   cudaError_t e;
   if ((e = cudaEventRecord(s->fork, s->main)) != cudaSuccess) return SPN_E_CUDA;
   for (cudaStream_t p : s->pool) cudaStreamWaitEvent(p, s->fork, 0);
-  // resident jobs, grouped by shape
-  std::map<std::tuple<int, int, int, int>, std::vector<Job*>> groups;
+  // resident jobs: one persistent launch per (dimension, cluster size), all
+  // shapes together, longest window first; each launch on its own pool stream
+  std::map<std::pair<int, int>, std::vector<Job*>> groups;
   std::vector<int64_t> win(act.size());
+  // a round is about round_attempts spread over the active jobs (at least
+  // window_attempts each), so a few large jobs still get long windows
+  const int64_t per_job = std::max<int64_t>(s->window_attempts, s->round_attempts / (int64_t)act.size());
   for (size_t k = 0; k < act.size(); ++k) {
     Job& j = *act[k];
-    const int64_t per = std::max<int64_t>(1, s->window_attempts / std::max<int64_t>(1, j.N));
+    const int64_t per = std::max<int64_t>(1, per_job / std::max<int64_t>(1, j.N));
     win[k] = std::min<int64_t>(per, j.req.nsweeps - j.done);
-    if (j.cs > 0) groups[{j.nd, j.req.dims[0], j.req.dims[1], j.nd == 3 ? j.req.dims[2] : 1}].push_back(&j);
+    j.window = win[k];
+    if (j.cs > 0) groups[{j.nd, j.cs}].push_back(&j);
   }
   std::vector<spn::ResInst> inst;
-  std::vector<std::tuple<int, int, int, int, int, size_t, size_t>> launches;  // nd, Lx, Ly, Lz, cs, first, count
+  std::vector<int> order;
+  struct Launch {
+    int nd, cs, threads;
+    size_t first, count, smem;
+  };
+  std::vector<Launch> launches;
   for (auto& kv : groups) {
-    const size_t first = inst.size();
-    for (Job* j : kv.second) {
-      const int64_t w = std::min<int64_t>(std::max<int64_t>(1, s->window_attempts / std::max<int64_t>(1, j->N)),
-                                          j->req.nsweeps - j->done);
+    std::vector<Job*>& js = kv.second;
+    std::stable_sort(js.begin(), js.end(), [](const Job* x, const Job* y) { return x->N * x->window > y->N * y->window; });
+    Launch L{kv.first.first, kv.first.second, 64, inst.size(), js.size(), 0};
+    for (size_t k = 0; k < js.size(); ++k) {
+      Job* j = js[k];
       spn::ResInst r{};
       r.spins = j->d_spins;
-      r.trace = j->d_acc;
-      r.em0 = j->d_acc + 2 * 250;
+      r.trace = nullptr;  // the server reads E and M at the end
+      r.em0 = nullptr;
       r.seed = j->req.seed;
       r.stream = j->req.stream;
       r.sweep0 = (uint32_t)j->done;
-      r.nsweeps = (int)std::min<int64_t>(w, 250);  // the per-job accumulator holds 250 sweeps
+      r.nsweeps = (int)j->window;
       r.init_hot = 0;
+      r.Lx = j->req.dims[0];
+      r.Ly = j->req.dims[1];
+      r.Lz = j->nd == 3 ? j->req.dims[2] : 1;
       r.T = spn::make_thresholds(j->req.beta);
       inst.push_back(r);
+      order.push_back((int)k);
+      const int items = (r.Ly * r.Lz + L.cs - 1) / L.cs * ((r.Lx + 63) / 64);
+      L.threads = std::max(L.threads, std::min(512, (items + 31) / 32 * 32));
+      L.smem = std::max(L.smem, spn::resident_smem(L.nd, r.Lx, r.Ly, r.Lz, L.cs));
     }
-    launches.emplace_back(std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
-                          kv.second.front()->cs, first, kv.second.size());
+    launches.push_back(L);
   }
   if (!inst.empty()) {
     if (inst.size() > s->inst_cap) {
@@ -231,45 +252,75 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
     }
     if (cudaMemcpyAsync(s->d_inst, inst.data(), inst.size() * sizeof(spn::ResInst), cudaMemcpyHostToDevice,
                         s->main) != cudaSuccess ||
-        cudaMemsetAsync(s->d_counters, 0, launches.size() * sizeof(int), s->main) != cudaSuccess)
+        cudaMemcpyAsync(s->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s->main) !=
+            cudaSuccess ||
+        cudaMemsetAsync(s->d_counters, 0, launches.size() * sizeof(int), s->main) != cudaSuccess ||
+        cudaEventRecord(s->fork, s->main) != cudaSuccess)
       return SPN_E_CUDA;
-    for (auto& j : act)
-      if (j->cs > 0) cudaMemsetAsync(j->d_acc, 0, 4096, s->main);
     for (size_t li = 0; li < launches.size(); ++li) {
-      int nd, Lx, Ly, Lz, cs;
-      size_t first, count;
-      std::tie(nd, Lx, Ly, Lz, cs, first, count) = launches[li];
-      // the order array holds local indices into the group's instance slice
-      std::vector<int> ord(count);
-      for (size_t i = 0; i < count; ++i) ord[i] = (int)i;
-      cudaMemcpyAsync(s->d_order + first, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice, s->main);
+      const Launch& L = launches[li];
+      cudaStream_t st = s->pool[li % s->pool.size()];
+      cudaStreamWaitEvent(st, s->fork, 0);
       spn::ResArgs a{};
-      a.inst = s->d_inst + first;
-      a.ninst = (int)count;
-      a.order = s->d_order + first;
+      a.inst = s->d_inst + L.first;
+      a.ninst = (int)L.count;
+      a.order = s->d_order + L.first;  // local indices into the launch's slice
       a.counter = s->d_counters + li;
-      a.Lx = Lx;
-      a.Ly = Ly;
-      a.Lz = Lz;
       a.err = s->d_err;
-      const int W = (Lx + 63) / 64;
-      const int items = Ly * (nd == 3 ? Lz : 1) / cs * W;
-      const int threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
-      const size_t smem = spn::resident_smem(nd, Lx, Ly, Lz, cs);
-      const int ctas = std::max(cs, std::min<int>(spn::resident_max_ctas(nd, cs, threads, smem), (int)count * cs));
-      if ((e = spn::launch_resident(a, nd, cs, threads, ctas, s->main)) != cudaSuccess) return SPN_E_CUDA;
+      const int ctas =
+          std::max(L.cs, std::min<int>(spn::resident_max_ctas(L.nd, L.cs, L.threads, L.smem), (int)L.count * L.cs));
+      if ((e = spn::launch_resident(a, L.nd, L.cs, L.threads, ctas, L.smem, st)) != cudaSuccess) return SPN_E_CUDA;
     }
   }
-  // the rest: own launches on the stream pool
+  // EA jobs: one launch per lattice size, one CTA per job (at most 2000 sweeps a launch)
+  {
+    std::map<int64_t, std::vector<size_t>> ea_groups;
+    for (size_t k = 0; k < act.size(); ++k)
+      if (act[k]->ea) {
+        win[k] = std::min<int64_t>(win[k], 2000);
+        act[k]->window = win[k];
+        ea_groups[act[k]->N].push_back(k);
+      }
+    std::vector<spn::EaArgs> args;
+    std::vector<std::tuple<size_t, size_t, int, size_t>> el;  // first, count, threads, smem
+    for (auto& kv : ea_groups) {
+      const size_t first = args.size();
+      int threads = 0;
+      size_t smem = 0;
+      for (size_t k : kv.second) {
+        spn::EaArgs a;
+        if (spn::ea_window_args(act[k]->ea, win[k], &a, &smem, &threads) != SPN_OK) return SPN_E_STATE;
+        args.push_back(a);
+      }
+      el.emplace_back(first, kv.second.size(), threads, smem);
+    }
+    if (!args.empty()) {
+      if (args.size() > s->ea_cap) {
+        cudaFree(s->d_ea);
+        s->ea_cap = args.size() * 2;
+        if (cudaMalloc(&s->d_ea, s->ea_cap * sizeof(spn::EaArgs)) != cudaSuccess) return SPN_E_NOMEM;
+      }
+      if (cudaMemcpyAsync(s->d_ea, args.data(), args.size() * sizeof(spn::EaArgs), cudaMemcpyHostToDevice,
+                          s->main) != cudaSuccess ||
+          cudaEventRecord(s->fork, s->main) != cudaSuccess)
+        return SPN_E_CUDA;
+      for (size_t gi = 0; gi < el.size(); ++gi) {
+        size_t first, count, smem;
+        int threads;
+        std::tie(first, count, threads, smem) = el[gi];
+        cudaStream_t st = s->pool[(s->pool.size() - 1 - gi % s->pool.size())];
+        cudaStreamWaitEvent(st, s->fork, 0);
+        if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, threads, smem, st)) != cudaSuccess)
+          return SPN_E_CUDA;
+      }
+    }
+  }
+  // large Ising lattices: own launches on the stream pool
   for (size_t k = 0; k < act.size(); ++k) {
     Job& j = *act[k];
-    if (j.cs > 0) continue;
+    if (j.cs > 0 || j.ea) continue;
     cudaStream_t st = s->pool[j.stream_slot];
     const int64_t w = win[k];
-    if (j.ea) {
-      if (spn_batch_sweep(j.ea, w)) return SPN_E_CUDA;
-      continue;
-    }
     spn::Lattice g;
     g.nd = j.nd;
     g.Lx = j.req.dims[0];
@@ -302,7 +353,7 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   std::lock_guard<std::mutex> lock(s->mu);
   for (size_t k = 0; k < act.size(); ++k) {
     Job& j = *act[k];
-    const int64_t w = j.cs > 0 ? std::min<int64_t>(win[k], 250) : win[k];
+    const int64_t w = win[k];
     j.done += w;
     s->attempts += (unsigned long long)(j.N * w * (j.ea ? 32 : 1));
   }
@@ -521,6 +572,7 @@ int spn_server_destroy(spn_server s) {
     cudaEventDestroy(s->pool_done[i]);
   }
   cudaFree(s->d_inst);
+  cudaFree(s->d_ea);
   cudaFree(s->d_order);
   cudaFree(s->d_counters);
   cudaFree(s->d_err);

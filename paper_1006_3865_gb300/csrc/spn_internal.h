@@ -57,22 +57,22 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
 // One instance of a batched resident run (batched.cu).
 struct ResInst {
   int8_t* spins;               // device int8 lattice, result written back
-  unsigned long long* trace;   // [nsweeps][2] per-sweep (dE, dM), zeroed by the caller
-  unsigned long long* em0;     // [2] start (E, M), zeroed by the caller
+  unsigned long long* trace;   // [nsweeps][2] per-sweep (dE, dM), zeroed by the caller; may be null
+  unsigned long long* em0;     // [2] start (E, M), zeroed by the caller; may be null
   uint64_t seed;
   uint32_t stream;
   uint32_t sweep0;
   int nsweeps;
   int init_hot;                // 1: hot start from Philox; 0: start from `spins`
+  int Lx, Ly, Lz;              // extents (Lz = 1 in 2D); the launch's shared memory fits the largest
   DevThr T;
 };
 
 struct ResArgs {
-  const ResInst* inst;  // all instances of one launch share nd and extents
+  const ResInst* inst;  // all instances of one launch share nd and the cluster size
   int ninst;
   const int* order;     // queue order (longest first)
   int* counter;         // queue head, zeroed by the caller
-  int Lx, Ly, Lz;
   int* err;
 };
 
@@ -80,12 +80,48 @@ bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs);
 size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs);
 int resident_cluster_size(int nd, int Lx, int Ly, int Lz);  // 0: does not fit a cluster of <= 8 CTAs
 int resident_max_ctas(int nd, int cs, int threads, size_t smem);
-cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, cudaStream_t st);
+cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, size_t smem, cudaStream_t st);
 
 int device_sm_count();
 void count_launches(uint64_t n);
 void set_last_error(const char* msg);  // the thread's spn_last_error() message
 uint64_t launch_count();
+
+}  // namespace spn
+
+namespace spn {
+
+// Exact division by a launch-invariant 32-bit divisor (Granlund-Montgomery
+// round-up method): q = (t + ((n - t) >> 1)) >> s with t = umulhi(n, m).
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+struct EaArgs {
+  uint64_t* words;            // [pairs][N] uint64
+  const uint8_t* bonds;       // [S][N] bond bytes (site order)
+  uint8_t* temp_of_slot;      // [S][32]
+  unsigned long long* xacc;   // [S][32] accepted exchanges per pair
+  const uint32_t* xtab;       // concatenated exchange tables
+  int xoff[32];               // offset of pair k's table in xtab
+  int xlen[32];               // its length (d = 1 .. xlen), 0 with xalways[k]
+  uint32_t xalways;           // bit k: pair k has equal betas (always accept)
+  uint32_t thr[3][32];        // thr[q-1][t] for dE = 4q, non-decreasing in t
+  int Lx, Ly, Lz, N;
+  FastDiv div_h, div_ly;      // by Lx / 2 and by Ly
+  uint32_t sweep0;
+  int nsweeps;
+  int exchange_every;
+  int nsamples;
+  PhiloxKeys K;
+  int* err;
+};
+
+// Served multi-spin coded EA jobs (single-sample batch handles): the
+// parameter block of the next `nsweeps` sweeps of h (its sweep counter
+// advances), and one launch running many such blocks, one CTA each.
+int ea_window_args(struct spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* threads);
+cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int threads, size_t smem, cudaStream_t st);
 
 }  // namespace spn
 
