@@ -19,6 +19,8 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -47,6 +49,8 @@ int sfail(int code, const char* msg) {
 
 enum JobState { kPending = 0, kAdmitted = 1, kDone = 2, kFailed = 3 };
 
+constexpr int kPoolStreams = 32;  // concurrent launches of one round
+
 struct Job {
   uint64_t ticket = 0;
   spn_request req{};
@@ -61,10 +65,13 @@ struct Job {
   int nd = 2;
   int64_t N = 0;
   int cs = 0;        // resident cluster size (0: not resident)
-  bool streaming = false;
+  bool streaming = false;  // pitched ping-pong lattices (rows padded to 64 bytes) for the streaming sweep
+  int pitch = 0;
   spn::StreamGeom geo{};
   int8_t* d_spins = nullptr;
   int8_t* d_scratch = nullptr;
+  int8_t* d_p0 = nullptr;  // pitched lattice (current)
+  int8_t* d_p1 = nullptr;  // pitched ping-pong partner
   unsigned long long* d_acc = nullptr;  // window deltas / start E, M
   spn_handle ea = nullptr;
   int stream_slot = 0;
@@ -102,9 +109,11 @@ struct spn_server_ctx {
   size_t inst_cap = 0;
   int64_t window_attempts = (int64_t)1 << 26;  // at least this many attempts per job per round
   int64_t round_attempts = (int64_t)1 << 35;   // about this many attempts per round in all
+  int64_t stream_sites = (int64_t)1 << 20;     // Ising jobs from this many sites up stream (if not resident)
   std::atomic<unsigned long long> attempts{0};
   std::atomic<unsigned long long> rounds{0};
   double busy = 0;
+  std::FILE* trace = nullptr;  // per-round log when SPN_SERVER_TRACE names a file
 };
 
 namespace {
@@ -112,15 +121,17 @@ namespace {
 size_t job_bytes(const Job& j) {
   if (j.req.model == SPN_EA3D_PMJ) return (size_t)j.N * 9 + 64 * 1024;  // words + bond bytes + tables
   size_t b = (size_t)j.N + 4096;
-  if (j.streaming) b += (size_t)j.N;
+  if (j.streaming) b += 2 * (size_t)j.pitch * (size_t)(j.N / j.req.dims[0]);
   return b;
 }
 
 void release(spn_server_ctx* s, Job& j) {
   if (j.d_spins) cudaFreeAsync(j.d_spins, s->main);
   if (j.d_scratch) cudaFreeAsync(j.d_scratch, s->main);
+  if (j.d_p0) cudaFreeAsync(j.d_p0, s->main);
+  if (j.d_p1) cudaFreeAsync(j.d_p1, s->main);
   if (j.d_acc) cudaFreeAsync(j.d_acc, s->main);
-  j.d_spins = j.d_scratch = nullptr;
+  j.d_spins = j.d_scratch = j.d_p0 = j.d_p1 = nullptr;
   j.d_acc = nullptr;
   if (j.ea) {
     spn_destroy(j.ea);
@@ -145,8 +156,16 @@ int admit(spn_server_ctx* s, Job& j) {
   g.N = j.N;
   if (cudaMallocAsync(&j.d_spins, (size_t)j.N, s->main) != cudaSuccess) return SPN_E_NOMEM;
   if (cudaMallocAsync(&j.d_acc, 4096, s->main) != cudaSuccess) return SPN_E_NOMEM;
-  if (j.streaming && cudaMallocAsync(&j.d_scratch, (size_t)j.N, s->main) != cudaSuccess) return SPN_E_NOMEM;
   if (spn::launch_init_hot(g, j.d_spins, r.seed, r.stream, s->main) != cudaSuccess) return SPN_E_CUDA;
+  if (j.streaming) {
+    const size_t nrow = (size_t)(j.N / g.Lx), pb = (size_t)j.pitch * nrow;
+    if (cudaMallocAsync(&j.d_p0, pb, s->main) != cudaSuccess || cudaMallocAsync(&j.d_p1, pb, s->main) != cudaSuccess)
+      return SPN_E_NOMEM;
+    if (cudaMemsetAsync(j.d_p0, 1, pb, s->main) != cudaSuccess ||
+        cudaMemcpy2DAsync(j.d_p0, (size_t)j.pitch, j.d_spins, (size_t)g.Lx, (size_t)g.Lx, nrow, cudaMemcpyDeviceToDevice,
+                          s->main) != cudaSuccess)
+      return SPN_E_CUDA;
+  }
   return SPN_OK;
 }
 
@@ -174,6 +193,10 @@ int finish(spn_server_ctx* s, Job& j) {
   g.Ly = j.req.dims[1];
   g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
   g.N = j.N;
+  if (j.streaming &&
+      cudaMemcpy2DAsync(j.d_spins, (size_t)g.Lx, j.d_p0, (size_t)j.pitch, (size_t)g.Lx, (size_t)(j.N / g.Lx),
+                        cudaMemcpyDeviceToDevice, s->main) != cudaSuccess)
+    return SPN_E_CUDA;
   if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, s->main) != cudaSuccess) return SPN_E_CUDA;
   unsigned long long em[2];
   j.spins.resize((size_t)j.N);
@@ -200,7 +223,8 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   const int64_t per_job = std::max<int64_t>(s->window_attempts, s->round_attempts / (int64_t)act.size());
   for (size_t k = 0; k < act.size(); ++k) {
     Job& j = *act[k];
-    const int64_t per = std::max<int64_t>(1, per_job / std::max<int64_t>(1, j.N));
+    const int64_t units = j.ea ? 32 * j.N : j.N;  // attempts of one sweep (every replica of an EA job)
+    const int64_t per = std::max<int64_t>(1, per_job / std::max<int64_t>(1, units));
     win[k] = std::min<int64_t>(per, j.req.nsweeps - j.done);
     j.window = win[k];
     if (j.cs > 0) groups[{j.nd, j.cs}].push_back(&j);
@@ -327,14 +351,14 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
     g.Ly = j.req.dims[1];
     g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
     g.N = j.N;
+    g.pitch = j.streaming ? j.pitch : 0;
     const spn::DevThr T = spn::make_thresholds(j.req.beta);
     const spn::PhiloxKeys K = spn::philox_keys(j.req.seed);
     for (int64_t t = 0; t < w; ++t) {
       const uint32_t sweep = (uint32_t)(j.done + t);
-      if (j.streaming) {  // ping-pong: the current lattice is always d_spins
-        e = spn::launch_sweep_stream(g, j.d_spins, j.d_scratch, j.geo, T, K, j.req.stream, sweep, j.d_acc, s->d_err,
-                                     st);
-        std::swap(j.d_spins, j.d_scratch);
+      if (j.streaming) {  // ping-pong: the current lattice is always d_p0
+        e = spn::launch_sweep_stream(g, j.d_p0, j.d_p1, j.geo, T, K, j.req.stream, sweep, j.d_acc, s->d_err, st);
+        std::swap(j.d_p0, j.d_p1);
       } else {
         e = spn::launch_sweep_generic(g, j.d_spins, T, K, j.req.stream, sweep, j.d_acc, st);
       }
@@ -401,8 +425,19 @@ void scheduler(spn_server_ctx* s) {
     if (act.empty()) continue;
     const double t0 = now_s();
     int rc = run_round(s, act);
-    s->busy += now_s() - t0;
+    const double t1 = now_s();
+    s->busy += t1 - t0;
     s->rounds += 1;
+    if (s->trace) {  // one line per round: start, seconds, jobs, attempts, resident / streaming / EA / other jobs
+      int nr = 0, ns = 0, ne = 0, no = 0;
+      long long att = 0;
+      for (auto& j : act) {
+        att += (long long)j->N * j->window * (j->ea ? 32 : 1);
+        if (j->ea) ++ne; else if (j->cs > 0) ++nr; else if (j->streaming) ++ns; else ++no;
+      }
+      std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d\n", t0, t1 - t0, act.size(), att, nr, ns, ne, no);
+      std::fflush(s->trace);
+    }
     std::vector<std::shared_ptr<Job>> still;
     for (auto& j : act) {
       if (rc == SPN_OK && j->done < j->req.nsweeps) {
@@ -439,7 +474,7 @@ int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
     delete s;
     return sfail(SPN_E_CUDA, "server set-up failed");
   }
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < kPoolStreams; ++i) {
     cudaStream_t st;
     cudaEvent_t ev;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -447,6 +482,7 @@ int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
     s->pool.push_back(st);
     s->pool_done.push_back(ev);
   }
+  if (const char* path = std::getenv("SPN_SERVER_TRACE")) s->trace = std::fopen(path, "w");
   s->worker = std::thread(scheduler, s);
   *out = s;
   return SPN_OK;
@@ -474,23 +510,30 @@ int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket) {
     j->bonds.assign(static_cast<const uint64_t*>(req->couplings), static_cast<const uint64_t*>(req->couplings) + 3 * nw);
   } else {
     if (!(req->beta >= 0.0)) return sfail(SPN_E_ARG, "beta must be >= 0");
+    // lattices resident in the shared memory of one CTA or cluster share
+    // persistent launches; larger ones stream (rows padded to 64 bytes)
+    spn::Lattice g;
+    g.nd = j->nd;
+    g.Lx = ext[0];
+    g.Ly = ext[1];
+    g.Lz = ext[2];
+    g.N = j->N;
+    g.pitch = (ext[0] + 63) / 64 * 64;
+    int ty = 32;
+    if (j->nd == 3)
+      while (ty > 1 && ext[1] % ty) ty /= 2;
+    if (j->nd == 2) ty = 1;
     j->cs = spn::resident_cluster_size(j->nd, ext[0], ext[1], ext[2]);
-    if (!j->cs) {
-      spn::Lattice g;
-      g.nd = j->nd;
-      g.Lx = ext[0];
-      g.Ly = ext[1];
-      g.Lz = ext[2];
-      g.N = j->N;
-      int ty = 32;
-      if (j->nd == 3)
-        while (ty > 1 && ext[1] % ty) ty /= 2;
-      if (j->nd == 2) ty = 1;
-      if (spn::stream_path_supported(g, ty)) {
-        j->geo = spn::stream_geometry(g, ty, 0, 0);
-        j->streaming = spn::stream_geometry_ok(g, j->geo);
-      }
+    if (j->cs == 0 && j->N >= s->stream_sites && spn::stream_path_supported(g, ty)) {
+      const int S = j->nd == 3 ? ext[2] : ext[1];
+      const int tiles = j->nd == 3 ? ext[1] / ty : 1;
+      // >= 32 slices a CTA: concurrent jobs fill the GPU, and few halo slices are re-read
+      const int nseg = std::max(1, std::min(S / 32, 4 * spn::device_sm_count() / tiles));
+      j->geo = spn::stream_geometry(g, ty, 0, nseg);
+      j->streaming = spn::stream_geometry_ok(g, j->geo);
+      j->pitch = g.pitch;
     }
+
   }
   j->bytes = job_bytes(*j);
   std::lock_guard<std::mutex> lock(s->mu);
@@ -577,6 +620,7 @@ int spn_server_destroy(spn_server s) {
   cudaFree(s->d_counters);
   cudaFree(s->d_err);
   cudaEventDestroy(s->fork);
+  if (s->trace) std::fclose(s->trace);
   cudaStreamDestroy(s->main);
   delete s;
   return SPN_OK;

@@ -39,6 +39,7 @@ struct Lattice {
   int Lx = 0, Ly = 0, Lz = 1;
   int64_t N = 0;
   const uint8_t* bonds = nullptr;  // per-site byte, bit d set iff J(n, d) = -1 (null: J = +1)
+  int pitch = 0;                   // streaming sweep only: bytes per row in memory (0: Lx, dense)
 };
 
 // Launchers (all asynchronous on `st`).  acc points at two int64 (dE, dM) that

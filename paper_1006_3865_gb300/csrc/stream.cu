@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "philox.cuh"
 #include "spn_internal.h"
@@ -54,6 +55,8 @@ struct StreamArgs {
   const int8_t* in;
   int8_t* out;
   int Lx, Ly, S;  // S: slices along the slowest axis (Ly in 2D, Lz in 3D)
+  int P;          // bytes per row in memory (a multiple of 64, >= Lx)
+  int vbl;        // sites per colour in the last 64-site word of a row (1 .. 32)
   int TY, R, nseg, nraw, nbit;
   int roundsC, roundsA, roundsB;
   uint32_t sweep, stream_id;
@@ -123,12 +126,13 @@ template <int ND>
 __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(const StreamArgs a) {
   constexpr int NC = ND;  // classes with dE > 0: dE = 4 (q + 1), q < NC
   extern __shared__ __align__(128) uint8_t smem[];
-  const int Lx = a.Lx, W = Lx >> 6, W2 = 2 * W;
+  const int P = a.P, W = P >> 6, W2 = 2 * W, vbl = a.vbl;
+  const uint32_t vmaskl = vbl == 32 ? 0xffffffffu : ((1u << vbl) - 1u);  // valid lanes of a row's last word
   const int R = a.R, nbit = a.nbit, nraw = a.nraw, S = a.S;
   const int RSL = (ND == 3) ? a.TY + 4 : 1;    // rows per slice: band + 2 halo rows on each side
   const int rowsA = (ND == 3) ? a.TY + 2 : 1;  // colour-0 rows: band + 1 ring row on each side
   const int rowsB = (ND == 3) ? a.TY : 1;      // colour-1 rows: the band
-  const int rawBytes = RSL * Lx;
+  const int rawBytes = RSL * P;
   const int rawStride = (rawBytes + 127) & ~127;
   const int sliceWords = RSL * W2;
   uint8_t* raw = smem;
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
   const int ze = (int)(((int64_t)(blockIdx.y + 1) * S) / a.nseg);
   const int H = ze - zs;
   const int nload = H + 4;  // local slices li = 0 .. H + 3 <-> global zs - 2 + li
-  const int64_t sliceStride = (int64_t)Lx * ((ND == 3) ? a.Ly : 1);
+  const int64_t sliceStride = (int64_t)P * ((ND == 3) ? a.Ly : 1);
 
   // int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
   for (int i = tid; i < 256; i += nth) {
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
     {
       const int per = RSL * W, ks = i / per, r = (i - ks * per) / W, j = i - ks * per - r * W;
       cOff[q] = pack_item(i, R * per, ks, (uint32_t)(r * W2 + j));
-      cRaw[q] = (uint32_t)(r * Lx + 64 * j) >> 4;
+      cRaw[q] = ((uint32_t)(r * P + 64 * j) >> 4) | (j == W - 1 ? 0x80000000u : 0u);  // bit 31: last word
     }
     {
       const int per = rowsA * W, ks = i / per, r = (i - ks * per) / W, j = i - ks * per - r * W;
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
       bOff[q] = pack_item(i, R * per, ks, (uint32_t)(((ND == 3) ? (r + 2) * W2 : 0) + j));
       bC0[q] = 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)((ND == 3) ? gy : 0));
       bFl[q] = (uint32_t)((y0 + r) & 1) | 2u | (j == 0 ? 4u : 0u) | (j == W - 1 ? 8u : 0u);
-      bOut[q] = (uint32_t)(((ND == 3) ? gy * Lx : 0) + 64 * j);
+      bOut[q] = (uint32_t)(((ND == 3) ? gy * P : 0) + 64 * j);
     }
   }
   // chunk order of the 64-byte span rotated by lane pair: a quarter warp reads
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
         const int64_t gz = wrapS(zs - 2 + issued);
         for (int r = lane; r < RSL; r += 32) {
           const int gy = (ND == 3) ? wrapY(y0 - 2 + r) : 0;
-          bulk_g2s(B + (size_t)r * Lx, a.in + gz * sliceStride + (int64_t)gy * Lx, (uint32_t)Lx, bar);
+          bulk_g2s(B + (size_t)r * P, a.in + gz * sliceStride + (int64_t)gy * P, (uint32_t)P, bar);
         }
       }
       if (++islot == nraw) islot = 0;
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
         r -= r >= nraw ? nraw : 0;
         int sl = sfirst + ks;
         sl -= sl >= nbit ? nbit : 0;
-        const uint32_t span = (uint32_t)r * (uint32_t)(rawStride >> 4) + cRaw[q];
+        const uint32_t span = (uint32_t)r * (uint32_t)(rawStride >> 4) + (cRaw[q] & 0x7fffffffu);
         uint32_t pe[4], po[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -261,8 +265,9 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
           po[v] = gather_o(c.x, c.y, c.z, c.w);
         }
         uint32_t* row = bits + (uint32_t)sl * (uint32_t)sliceWords + (x & 0xffffffu);
-        row[0] = __byte_perm(top_bytes(pe[0], pe[1], pe[2], pe[3]), 0u, rot_sel);
-        row[W] = __byte_perm(top_bytes(po[0], po[1], po[2], po[3]), 0u, rot_sel);
+        const uint32_t keep = (cRaw[q] >> 31) ? vmaskl : 0xffffffffu;  // padding sites of a row stay 0
+        row[0] = __byte_perm(top_bytes(pe[0], pe[1], pe[2], pe[3]), 0u, rot_sel) & keep;
+        row[W] = __byte_perm(top_bytes(po[0], po[1], po[2], po[3]), 0u, rot_sel) & keep;
       }
     }
     cslot = rs;
@@ -302,8 +307,10 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
         oj = bits[other];
         const int dj = par ? ((fl & 8u) ? 1 - W : 1) : ((fl & 4u) ? W - 1 : -1);
         const uint32_t on = bits[other + (uint32_t)dj];
-        const uint32_t left = par ? oj : __funnelshift_l(on, oj, 1);   // x - 1
-        const uint32_t right = par ? __funnelshift_r(oj, on, 1) : oj;  // x + 1
+        // x - 1 of lane 0 is the last site of the previous word; x + 1 of the
+        // last lane is the first site of the next word (periodic in x)
+        const uint32_t left = par ? oj : (oj << 1) | ((on >> (((fl & 4u) ? vbl : 32) - 1)) & 1u);
+        const uint32_t right = par ? (oj >> 1) | ((on & 1u) << (((fl & 8u) ? vbl : 32) - 1)) : oj;
         const uint32_t zm = bits[sl == 0 ? woff + (uint32_t)((nbit - 1) * sliceWords) : woff - (uint32_t)sliceWords];
         const uint32_t zp = bits[sl == nbit - 1 ? woff - (uint32_t)((nbit - 1) * sliceWords) : woff + (uint32_t)sliceWords];
         if constexpr (ND == 3) {
@@ -313,7 +320,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
           count4(b ^ left, b ^ right, b ^ zm, b ^ zp, s0, s1, s2);
         }
         uint32_t cls[NC];
-        acc = classes<ND>(s0, s1, s2, 0xffffffffu, cls);
+        acc = classes<ND>(s0, s1, s2, (fl & 8u) ? vmaskl : 0xffffffffu, cls);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           const bool always = (a.always >> (k + 1)) & 1u;
@@ -421,28 +428,31 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
 
 }  // namespace
 
+static int pitch_of(const Lattice& g) { return g.pitch ? g.pitch : g.Lx; }
+
 bool stream_path_supported(const Lattice& g, int TY) {
   if (g.bonds) return false;
-  if (g.Lx % 64) return false;
+  const int P = pitch_of(g);
+  if (g.Lx < 2 || (g.Lx & 1) || P % 64 || P < g.Lx || P - g.Lx >= 64) return false;
   if (g.nd == 3 && (TY < 2 || TY > 250 || (TY & 1) || g.Ly % TY)) return false;
-  if (g.Lx / 64 > 65535) return false;
+  if (P / 64 > 65535) return false;
   const int RSL = g.nd == 3 ? TY + 4 : 1;
-  if ((int64_t)RSL * g.Lx * 2 > 96 * 1024) return false;  // two raw slices must fit beside the rest
+  if ((int64_t)RSL * P * 2 > 96 * 1024) return false;  // two raw slices must fit beside the rest
   return true;
 }
 
 namespace {
 
 size_t smem_bytes(const Lattice& g, int TY, int R, int nraw) {
-  const int W = g.Lx / 64;
+  const int W = pitch_of(g) / 64;
   const int RSL = g.nd == 3 ? TY + 4 : 1;
-  const size_t rawStride = (size_t)((RSL * g.Lx + 127) & ~127);
+  const size_t rawStride = (size_t)((RSL * pitch_of(g) + 127) & ~127);
   const size_t bitsB = (size_t)(2 * R + 3) * RSL * 2 * W * 4;
   return (size_t)nraw * rawStride + bitsB + 256 * 8 + (size_t)nraw * 8;
 }
 
 void phase_counts(const Lattice& g, int TY, int R, int& nC, int& nA, int& nB) {
-  const int W = g.Lx / 64;
+  const int W = pitch_of(g) / 64;
   nC = R * (g.nd == 3 ? TY + 4 : 1) * W;
   nA = R * (g.nd == 3 ? TY + 2 : 1) * W;
   nB = R * (g.nd == 3 ? TY : 1) * W;
@@ -515,6 +525,8 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
   a.in = in;
   a.out = out;
   a.Lx = g.Lx;
+  a.P = pitch_of(g);
+  a.vbl = (g.Lx - (a.P - 64)) / 2;
   a.Ly = g.Ly;
   a.S = g.nd == 3 ? g.Lz : g.Ly;
   a.TY = geo.TY;
@@ -534,15 +546,29 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
   a.acc = acc;
   a.err = err;
   dim3 grid(g.nd == 3 ? g.Ly / geo.TY : 1, geo.nseg);
-  if (g.nd == 3) {
-    cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
-    cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    k_sweep_stream<3><<<grid, geo.threads, geo.smem, st>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
-    cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    k_sweep_stream<2><<<grid, geo.threads, geo.smem, st>>>(a);
+  // function attributes are set once per device and raised only when a launch needs more
+  static std::mutex mu;
+  static int smem_set[128][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    int& cur = smem_set[dev & 127][g.nd == 3 ? 1 : 0];
+    if ((int)geo.smem > cur) {
+      if (g.nd == 3) {
+        cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
+        cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      } else {
+        cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
+        cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
+      cur = (int)geo.smem;
+    }
   }
+  if (g.nd == 3)
+    k_sweep_stream<3><<<grid, geo.threads, geo.smem, st>>>(a);
+  else
+    k_sweep_stream<2><<<grid, geo.threads, geo.smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
