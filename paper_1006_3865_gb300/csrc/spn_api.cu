@@ -67,8 +67,33 @@ std::vector<uint8_t> unpack_site_bonds(const uint64_t* words, int nd, int64_t N)
   return out;
 }
 
+// The lattice as the streaming sweep sees it: rows padded to 64 bytes unless
+// Lx is a multiple of 64.
+spn::Lattice stream_lattice(const spn_ctx* h) {
+  spn::Lattice g = h->g;
+  g.pitch = (g.Lx % 64) ? (g.Lx + 63) / 64 * 64 : 0;
+  return g;
+}
+
+// Device buffers the streaming path needs: the ping-pong partner, or the two
+// padded staging lattices.
+int ensure_stream_buffers(spn_ctx* h) {
+  const spn::Lattice g = stream_lattice(h);
+  if (g.pitch) {
+    const size_t bytes = (size_t)g.pitch * (size_t)(g.N / g.Lx);
+    for (int i = 0; i < 2; ++i)
+      if (!h->staged[i]) {
+        SPN_CUDA(cudaMalloc(&h->staged[i], bytes), "cudaMalloc(staged)");
+        SPN_CUDA(cudaMemset(h->staged[i], 1, bytes), "cudaMemset(staged)");
+      }
+  } else if (!h->spins[1]) {
+    SPN_CUDA(cudaMalloc(&h->spins[1], (size_t)g.N), "cudaMalloc(spins)");
+  }
+  return SPN_OK;
+}
+
 void pick_default_path(spn_ctx* h) {
-  const spn::Lattice& g = h->g;
+  const spn::Lattice g = stream_lattice(h);
   int ty = 32;
   if (g.nd == 3)
     while (ty > 1 && g.Ly % ty) ty /= 2;
@@ -145,6 +170,8 @@ void destroy(spn_ctx* h) {
   spn_ea_free(h->ea);
   cudaFree(h->spins[0]);
   cudaFree(h->spins[1]);
+  cudaFree(h->staged[0]);
+  cudaFree(h->staged[1]);
   cudaFree(h->d_bonds);
   cudaFree(h->d_acc);
   cudaFree(h->d_err);
@@ -199,7 +226,7 @@ int spn_create_ex(spn_handle* out, int model, const int32_t* dims, const void* c
   }
   pick_default_path(h);
   if (h->path == spn::kPathStream)
-    if ((e = cudaMalloc(&h->spins[1], (size_t)g.N)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(spins)"));
+    if ((rc = ensure_stream_buffers(h))) return bail(rc);
   if (init == SPN_INIT_HOT) {
     if ((e = spn::launch_init_hot(h->g, h->spins[0], seed, stream, h->st)) != cudaSuccess)
       return bail(cuda_fail(e, "init"));
@@ -231,15 +258,28 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
   const spn::DevThr T = spn::make_thresholds(beta);
   const spn::PhiloxKeys K = spn::philox_keys(h->seed);
   spn::StreamGeom geo{};
+  const spn::Lattice gs = stream_lattice(h);
+  const bool staged = h->path == spn::kPathStream && gs.pitch != 0;
+  const size_t nrow = (size_t)(h->g.N / h->g.Lx);
+  int sc = 0;  // current staged lattice
   if (h->path == spn::kPathStream) {
-    geo = spn::stream_geometry(h->g, h->tile_y, h->step_slices, h->seg);
-    if (!spn::stream_geometry_ok(h->g, geo)) return fail(SPN_E_STATE, "streaming geometry does not fit one CTA");
+    geo = spn::stream_geometry(gs, h->tile_y, h->step_slices, h->seg);
+    if (!spn::stream_geometry_ok(gs, geo)) return fail(SPN_E_STATE, "streaming geometry does not fit one CTA");
+    if ((rc = ensure_stream_buffers(h))) return rc;
+    if (staged)
+      SPN_CUDA(cudaMemcpy2DAsync(h->staged[0], (size_t)gs.pitch, h->spins[h->cur], (size_t)gs.Lx, (size_t)gs.Lx, nrow,
+                                 cudaMemcpyDeviceToDevice, h->st),
+               "staging the lattice");
   }
   for (int64_t t = 0; t < nsweeps; ++t) {
     const uint32_t sweep = (uint32_t)(h->sweeps + t);
     unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);
     cudaError_t e;
-    if (h->path == spn::kPathStream) {
+    if (staged) {
+      e = spn::launch_sweep_stream(gs, h->staged[sc], h->staged[sc ^ 1], geo, T, K, h->stream_id, sweep, acc,
+                                   h->d_err, h->st);
+      if (e == cudaSuccess) sc ^= 1;
+    } else if (h->path == spn::kPathStream) {
       e = spn::launch_sweep_stream(h->g, h->spins[h->cur], h->spins[h->cur ^ 1], geo, T, K, h->stream_id, sweep,
                                    acc, h->d_err, h->st);
       if (e == cudaSuccess) h->cur ^= 1;
@@ -248,9 +288,16 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
     }
     if (e != cudaSuccess) {
       h->sweeps += (uint64_t)t;
+      if (staged && t > 0)
+        cudaMemcpy2DAsync(h->spins[h->cur], (size_t)gs.Lx, h->staged[sc], (size_t)gs.pitch, (size_t)gs.Lx, nrow,
+                          cudaMemcpyDeviceToDevice, h->st);
       return cuda_fail(e, "sweep launch");
     }
   }
+  if (staged)
+    SPN_CUDA(cudaMemcpy2DAsync(h->spins[h->cur], (size_t)gs.Lx, h->staged[sc], (size_t)gs.pitch, (size_t)gs.Lx, nrow,
+                               cudaMemcpyDeviceToDevice, h->st),
+             "unstaging the lattice");
   h->sweeps += (uint64_t)nsweeps;
   return SPN_OK;
 }
@@ -368,10 +415,11 @@ int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t se
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   const int ty = h->g.nd == 3 ? tile_y : 1;
   if (step_slices < 0 || seg < 0) return fail(SPN_E_ARG, "negative tiling parameter");
-  if (!spn::stream_path_supported(h->g, ty))
-    return fail(SPN_E_ARG, "band of %d rows does not divide the lattice or Lx %% 64 != 0", tile_y);
-  const spn::StreamGeom geo = spn::stream_geometry(h->g, ty, step_slices, seg);
-  if (!spn::stream_geometry_ok(h->g, geo)) return fail(SPN_E_ARG, "tiling too large for one CTA");
+  const spn::Lattice gs = stream_lattice(h);
+  if (!spn::stream_path_supported(gs, ty))
+    return fail(SPN_E_ARG, "band of %d rows does not divide the lattice (or the lattice has bonds)", tile_y);
+  const spn::StreamGeom geo = spn::stream_geometry(gs, ty, step_slices, seg);
+  if (!spn::stream_geometry_ok(gs, geo)) return fail(SPN_E_ARG, "tiling too large for one CTA");
   h->tile_y = ty;
   h->step_slices = step_slices;
   h->seg = seg;
@@ -388,9 +436,10 @@ int spn_set_path(spn_handle h, int32_t path) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (path == spn::kPathStream) {
-    if (!spn::stream_path_supported(h->g, h->tile_y))
-      return fail(SPN_E_ARG, "streaming path needs Lx %% 64 == 0, a dividing band and no bonds");
-    if (!h->spins[1]) SPN_CUDA(cudaMalloc(&h->spins[1], (size_t)h->g.N), "cudaMalloc(spins)");
+    if (!spn::stream_path_supported(stream_lattice(h), h->tile_y))
+      return fail(SPN_E_ARG, "streaming path needs a dividing band and no bonds");
+    const int rc = ensure_stream_buffers(h);
+    if (rc) return rc;
   } else if (path != spn::kPathGeneric) {
     return fail(SPN_E_ARG, "unknown path %d", path);
   }

@@ -137,6 +137,9 @@ struct spn_ctx {
   uint32_t stream_id = 0;
   int8_t* spins[2] = {nullptr, nullptr};
   int cur = 0;
+  // streaming sweep of a lattice whose Lx is not a multiple of 64: the lattice
+  // is staged into rows padded to 64 bytes for the sweeps of one spn_sweep call
+  int8_t* staged[2] = {nullptr, nullptr};
   uint8_t* d_bonds = nullptr;
   cudaStream_t st = nullptr;
   int path = spn::kPathGeneric;

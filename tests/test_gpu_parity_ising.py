@@ -53,6 +53,20 @@ def test_ising2d_stream_tilings(tiling):
              tiling=tiling, stream=5)
 
 
+@pytest.mark.parametrize("dims,tiling", [((130, 96), None), ((1000, 70), (0, 2, 5)), ((66, 40), (0, 1, 3)),
+                                         ((2, 64), None), ((126, 8), (0, 3, 2))])
+def test_ising2d_stream_padded_rows(dims, tiling):
+    """Row lengths that are not multiples of 64 stream from rows padded to 64 bytes."""
+    _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(13), [(1.0 / TC, 9), (0.3, 2)], path=spn.PATH_STREAM,
+             tiling=tiling, stream=4)
+
+
+@pytest.mark.parametrize("dims,tiling", [((70, 16, 12), (4, 1, 3)), ((6, 8, 10), (8, 2, 0)), ((202, 4, 6), None)])
+def test_ising3d_stream_padded_rows(dims, tiling):
+    _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(14), [(inputs.BETA_C_3D, 6)], path=spn.PATH_STREAM,
+             tiling=tiling)
+
+
 @pytest.mark.parametrize("dims", [(2, 2), (6, 10), (34, 18), (50, 4), (16, 2)])
 def test_ising2d_generic_small_and_ragged(dims):
     _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(4), [(0.41, 30)], path=spn.PATH_GENERIC)
