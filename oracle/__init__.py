@@ -72,6 +72,8 @@ def lib():
             L.orc_sweeps.restype = cint
             L.orc_sweeps_ex.argtypes = [cint, vp, vp, vp, dbl, u64, u32, u32, i64, cint, vp, vp, vp, vp]
             L.orc_sweeps_ex.restype = cint
+            L.orc_sweeps_dc.argtypes = [cint, vp, vp, vp, cint, dbl, u64, u32, u32, i64, vp, vp, vp, vp]
+            L.orc_sweeps_dc.restype = cint
             L.orc_msc_u.argtypes = [u64, u32, u32, cint, u64]
             L.orc_msc_u.restype = u32
             L.orc_ea_init_hot.argtypes = [vp, cint, u64, u32, vp]
@@ -180,6 +182,25 @@ def sweeps(dims, spins: np.ndarray, beta: float, nsweeps: int, seed: int, stream
     tM = np.zeros(max(nsweeps, 1), np.int64)
     _check(lib().orc_sweeps_ex(len(d), _p(d), _p(spins), _p(b), float(beta), seed, stream, sweep0, int(nsweeps),
                                1 if msc_u_words else 0, _p(Ea), _p(Ma), _p(tE), _p(tM)), "sweeps")
+    return int(Ea[0]), int(Ma[0]), tE[:nsweeps], tM[:nsweeps]
+
+
+def sweeps_dc(dims, spins: np.ndarray, tile, hits: int, beta: float, nsweeps: int, seed: int, stream: int = 0,
+              sweep0: int = 0, E: int | None = None, M: int | None = None):
+    """Double-checkerboard sweeps with `hits`-fold multi-hit on tiles of extent
+    `tile` (Sec. 3), in place.  Returns (E, M, traceE, traceM)."""
+    d = _dims(dims)
+    T = _dims(tile)
+    if spins.dtype != np.int8 or not spins.flags.c_contiguous:
+        raise TypeError("spins must be a contiguous int8 array")
+    if E is None or M is None:
+        E, M = observables(d, spins)
+    Ea = np.array([E], np.int64)
+    Ma = np.array([M], np.int64)
+    tE = np.zeros(max(nsweeps, 1), np.int64)
+    tM = np.zeros(max(nsweeps, 1), np.int64)
+    _check(lib().orc_sweeps_dc(len(d), _p(d), _p(spins), _p(T), int(hits), float(beta), seed, stream, sweep0,
+                               int(nsweeps), _p(Ea), _p(Ma), _p(tE), _p(tM)), "sweeps_dc")
     return int(Ea[0]), int(Ma[0]), tE[:nsweeps], tM[:nsweeps]
 
 

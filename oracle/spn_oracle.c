@@ -40,6 +40,8 @@
  *             most significant bits of the group's sites.  Purposes p:
  *               0  Metropolis u at sweep t, colour c
  *               1  hot start (t = 0)
+ *               4  Metropolis u of the double-checkerboard order at hit h of
+ *                  sweep t (counter word 1 = t * hits + h)
  *             The 32-bit u is uniform; storing it across planes lets a GPU
  *             thread compare 32 sites at once, most significant plane first,
  *             and stop drawing planes as soon as every site is decided.
@@ -307,6 +309,62 @@ int orc_sweeps(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, doubl
                uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* E, int64_t* M,
                int64_t* traceE, int64_t* traceM) {
   return orc_sweeps_ex(nd, L, s, bonds, beta, seed, stream, sweep0, nsweeps, 0, E, M, traceE, traceM);
+}
+
+/* ------------------------------------------- double checkerboard (Sec. 3) */
+
+/* Tile parity of site n for tiles of T[0] x T[1] (x T[2]) sites: the parity of
+ * the tile's coordinates (the "coarse" checkerboard). */
+static int dc_tile_parity(const lat_t* g, const int64_t* T, int64_t n) {
+  int64_t x[3];
+  lat_coords(g, n, x);
+  return (int)((x[0] / T[0] + x[1] / T[1] + (g->nd == 3 ? x[2] / T[2] : 0)) & 1);
+}
+
+/* Sec. 3, the double-checkerboard procedure with the generalised multi-hit:
+ * the lattice is cut into coarse tiles, coloured like a checkerboard; a sweep
+ * takes the tiles of parity 0, then those of parity 1, and within them runs
+ * `hits` times over: every site of colour 0 (the fine checkerboard), then every
+ * site of colour 1.  Sites updated together are never neighbours: they share a
+ * colour, and a tile's boundary layer belongs to tiles of the other parity.
+ * The u of a site at hit h of sweep t is its purpose-4 plane word with counter
+ * word 1 = t hits + h.  Every extent must be a multiple of its tile edge, with
+ * an even number of tiles along each axis. */
+int orc_sweeps_dc(int nd, const int64_t* L, int8_t* s, const int64_t* T, int hits, double beta, uint64_t seed,
+                  uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* E, int64_t* M, int64_t* traceE,
+                  int64_t* traceM) {
+  lat_t g;
+  if (lat_make(&g, nd, L) || hits < 1) return -1;
+  for (int d = 0; d < nd; ++d)
+    if (T[d] < 1 || L[d] % T[d] || (L[d] / T[d]) % 2) return -1;
+  uint64_t thr[4];
+  for (int k = 0; k < 4; ++k) thr[k] = orc_threshold(beta, 4 * k);
+  for (int64_t t = 0; t < nsweeps; ++t) {
+    const uint64_t sweep = (uint64_t)sweep0 + (uint64_t)t;
+    int64_t de = 0, dm = 0;
+    for (int P = 0; P < 2; ++P)
+      for (int h = 0; h < hits; ++h)
+        for (int c = 0; c < 2; ++c) {
+          const uint32_t ctr = (uint32_t)(sweep * (uint64_t)hits + (uint64_t)h);
+#pragma omp parallel for reduction(+ : de, dm) schedule(static)
+          for (int64_t n = 0; n < g.N; ++n) {
+            if (lat_colour(&g, n) != c || dc_tile_parity(&g, T, n) != P) continue;
+            const int dE = 2 * s[n] * local_field(&g, s, NULL, n);
+            int acc = 1;
+            if (dE > 0) acc = (uint64_t)orc_site_word(seed, stream, ctr, c, 4, lat_key(&g, n)) < thr[dE / 4];
+            if (acc) {
+              dm += -2 * s[n];
+              s[n] = (int8_t)(-s[n]);
+              de += dE;
+            }
+          }
+        }
+    *E += de;
+    *M += dm;
+    if (traceE) traceE[t] = *E;
+    if (traceM) traceM[t] = *M;
+  }
+  return 0;
 }
 
 /* ------------------------------------------------- multi-spin coded EA */
