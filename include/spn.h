@@ -98,6 +98,17 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps);
 
 /* Current integer energy E = -sum J s_i s_j (Eq. 1, each bond once) and
  * magnetisation M = sum s_i (synchronises the handle's stream). */
+/* The paper's own update order (Sec. 3): the double-checkerboard sweep with
+ * the generalised multi-hit.  The lattice is cut into tiles of
+ * tile[0] x tile[1] (x tile[2]) sites, tile[0] a multiple of 64 and an even
+ * number of tiles along every axis; a sweep takes the tiles of even, then odd
+ * tile parity, and in each updates the colour-0 sites, then the colour-1 sites,
+ * `hits` times over.  Random numbers are the bit-plane words of purpose 4 at
+ * counter sweep * hits + hit.  Each call appends nsweeps entries to the trace
+ * and advances the sweep counter like spn_sweep.  Ising lattices without bonds
+ * whose Lx is a multiple of 64; SPN_E_ARG otherwise. */
+int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile, int32_t hits);
+
 int spn_observables(spn_handle h, int64_t* E, int64_t* M);
 
 /* Recompute E and M from the spins with a full reduction (independent of the

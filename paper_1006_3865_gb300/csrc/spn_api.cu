@@ -302,6 +302,35 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
   return SPN_OK;
 }
 
+int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile, int32_t hits) {
+  if (!h || !tile) return fail(SPN_E_ARG, "NULL argument");
+  if (h->ea || h->model == SPN_EA3D_PMJ) return fail(SPN_E_STATE, "the double-checkerboard sweep is for Ising lattices");
+  if (!(beta >= 0.0)) return fail(SPN_E_ARG, "beta must be >= 0 (got %g)", beta);
+  if (nsweeps < 0 || hits < 1) return fail(SPN_E_ARG, "nsweeps must be >= 0 and hits >= 1");
+  if (nsweeps == 0) return SPN_OK;
+  const int tz = h->g.nd == 3 ? tile[2] : 1;
+  if (!spn::dc_supported(h->g, tile[0], tile[1], tz))
+    return fail(SPN_E_ARG, "tiles must have Tx a multiple of 64 and an even number of tiles along every axis");
+  if ((h->sweeps + (uint64_t)nsweeps) * (uint64_t)hits > 0xffffffffull)
+    return fail(SPN_E_ARG, "sweep counter times hits would exceed 2^32");
+  int rc = ensure_acc(h, nsweeps);
+  if (rc) return rc;
+  const spn::DevThr T = spn::make_thresholds(beta);
+  const spn::PhiloxKeys K = spn::philox_keys(h->seed);
+  for (int64_t t = 0; t < nsweeps; ++t) {
+    const uint32_t sweep = (uint32_t)(h->sweeps + t);
+    unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);
+    const cudaError_t e = spn::launch_sweep_dc(h->g, h->spins[h->cur], tile[0], tile[1], tz, hits, T, K,
+                                               h->stream_id, sweep, acc, h->st);
+    if (e != cudaSuccess) {
+      h->sweeps += (uint64_t)t;
+      return cuda_fail(e, "double-checkerboard launch");
+    }
+  }
+  h->sweeps += (uint64_t)nsweeps;
+  return SPN_OK;
+}
+
 int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
   if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");

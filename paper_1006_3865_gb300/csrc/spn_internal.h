@@ -49,6 +49,13 @@ cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long 
 cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, const PhiloxKeys& K,
                                  uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st);
 bool stream_path_supported(const Lattice& g, int TY);
+// Double-checkerboard sweep (tiles Tx x Ty (x Tz), Tx a multiple of 64, an even
+// number of tiles per axis, dense int8 lattice, no bonds): both tile parities
+// of one sweep, `hits` updates of each colour per tile.
+bool dc_supported(const Lattice& g, int Tx, int Ty, int Tz);
+cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz, int hits, const DevThr& T,
+                            const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
+                            cudaStream_t st);
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg);
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
 cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out, const StreamGeom& geo,

@@ -67,51 +67,6 @@ struct StreamArgs {
   int* err;
 };
 
-// 64 int8 spins (16 little-endian words, 4 consecutive sites each) -> the E word
-// (even sites) and O word (odd sites).  Bits 1..7 of a spin byte are its sign,
-// so site k of a group of 8 same-parity sites is taken at a distinct bit of x
-// and one multiply by two shifts moves the 8 sign bits, in order and without
-// carries, into bits 24..31.
-__device__ __forceinline__ uint32_t gather_e(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
-  const uint32_t x = (w0 & 0x00020002u) | (w1 & 0x00080008u) | (w2 & 0x00200020u) | (w3 & 0x00800080u);
-  return x * ((1u << 23) + (1u << 8));
-}
-__device__ __forceinline__ uint32_t gather_o(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
-  const uint32_t x = (w0 & 0x02000200u) | (w1 & 0x08000800u) | (w2 & 0x20002000u) | (w3 & 0x80008000u);
-  return x * ((1u << 15) + 1u);
-}
-
-// Top bytes of four products -> one word, product v in byte v.
-__device__ __forceinline__ uint32_t top_bytes(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
-  return __byte_perm(__byte_perm(p0, p1, 0x0073), __byte_perm(p2, p3, 0x0073), 0x5410);
-}
-
-// Planes 12 .. 31 for the sites still tied after the first stage; whole warps.
-template <int NC>
-__device__ __noinline__ uint32_t rest_planes(uint32_t (&eq)[NC], const StreamArgs& a, uint32_t c0, uint32_t c2) {
-  uint32_t acc = 0;
-#pragma unroll 1
-  for (uint32_t call = kFirstCalls; call < 8u; ++call) {
-    uint32_t pend = 0;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) pend |= eq[k];
-    if (!__any_sync(0xffffffffu, pend != 0u)) break;
-    const U4 P = philox10(c0 + call, a.sweep, c2, a.stream_id, a.K);
-    const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t u = pl[j];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const uint32_t tm = a.tm[k][4 * call + j];
-        acc |= eq[k] & ~u & tm;
-        eq[k] &= ~(u ^ tm);
-      }
-    }
-  }
-  return acc;
-}
-
 // Per-thread work items, fixed for the launch (item i = thread + q * threads of a
 // phase covers slice i / (rows W) of the step, row (i / W) % rows, word i % W).
 //   offset word: bits 0..23 word offset within a slice, 24..30 slice of the step,
@@ -123,7 +78,7 @@ __device__ __forceinline__ uint32_t pack_item(int i, int total, int ks, uint32_t
 }
 
 template <int ND>
-__global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(const StreamArgs a) {
+__global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(const __grid_constant__ StreamArgs a) {
   constexpr int NC = ND;  // classes with dE > 0: dE = 4 (q + 1), q < NC
   extern __shared__ __align__(128) uint8_t smem[];
   const int P = a.P, W = P >> 6, W2 = 2 * W, vbl = a.vbl;
@@ -356,7 +311,8 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
       uint32_t pend = 0;
 #pragma unroll
       for (int k = 0; k < NC; ++k) pend |= eq[k];
-      if (__any_sync(0xffffffffu, pend != 0u)) acc |= rest_planes<NC>(eq, a, c0, c2);
+      if (__any_sync(0xffffffffu, pend != 0u))
+        acc |= rest_planes<NC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id, kFirstCalls);
       if (live) {
         const uint32_t nb = b ^ acc;
         bits[woff] = nb;

@@ -262,4 +262,52 @@ static __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.m
 static __device__ __forceinline__ uint32_t sign_bits4(uint32_t w) { return ((w & 0x02020202u) * 0x08102040u) >> 28; }
 
 
+// 64 int8 spins (16 little-endian words, 4 consecutive sites each) -> the E word
+// (even sites) and O word (odd sites).  Bits 1..7 of a spin byte are its sign,
+// so site k of a group of 8 same-parity sites is taken at a distinct bit of x
+// and one multiply by two shifts moves the 8 sign bits, in order and without
+// carries, into bits 24..31.
+static __device__ __forceinline__ uint32_t gather_e(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  const uint32_t x = (w0 & 0x00020002u) | (w1 & 0x00080008u) | (w2 & 0x00200020u) | (w3 & 0x00800080u);
+  return x * ((1u << 23) + (1u << 8));
+}
+static __device__ __forceinline__ uint32_t gather_o(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
+  const uint32_t x = (w0 & 0x02000200u) | (w1 & 0x08000800u) | (w2 & 0x20002000u) | (w3 & 0x80008000u);
+  return x * ((1u << 15) + 1u);
+}
+
+// Top bytes of four products -> one word, product v in byte v.
+static __device__ __forceinline__ uint32_t top_bytes(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
+  return __byte_perm(__byte_perm(p0, p1, 0x0073), __byte_perm(p2, p3, 0x0073), 0x5410);
+}
+
+// Planes 4 first_call .. 31 for the sites still tied after a first decision
+// stage (tm[q][p]: 0 / ~0 = bit 31 - p of the class-q threshold); whole warps.
+template <int NC>
+__device__ __noinline__ uint32_t rest_planes(uint32_t (&eq)[NC], const uint32_t (*tm)[32], const PhiloxKeys& K,
+                                             uint32_t c0, uint32_t c1, uint32_t c2, uint32_t stream_id,
+                                             uint32_t first_call) {
+  uint32_t acc = 0;
+#pragma unroll 1
+  for (uint32_t call = first_call; call < 8u; ++call) {
+    uint32_t pend = 0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) pend |= eq[k];
+    if (!__any_sync(0xffffffffu, pend != 0u)) break;
+    const U4 P = philox10(c0 + call, c1, c2, stream_id, K);
+    const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t u = pl[j];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const uint32_t t = tm[k][4 * call + j];
+        acc |= eq[k] & ~u & t;
+        eq[k] &= ~(u ^ t);
+      }
+    }
+  }
+  return acc;
+}
+
 }  // namespace spn

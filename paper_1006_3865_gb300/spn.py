@@ -56,6 +56,7 @@ _SIGNATURES = {
     "spn_create": (_c.c_int, [_P(_vp), _c.c_int, _vp, _vp, _u64]),
     "spn_create_ex": (_c.c_int, [_P(_vp), _c.c_int, _vp, _vp, _u64, _u32, _c.c_int]),
     "spn_sweep": (_c.c_int, [_vp, _dbl, _i64]),
+    "spn_sweep_dc": (_c.c_int, [_vp, _dbl, _i64, _P(_i32), _i32]),
     "spn_observables": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
     "spn_recompute": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
     "spn_trace": (_c.c_int, [_vp, _vp, _vp, _i64, _P(_i64)]),
@@ -208,6 +209,11 @@ class Lattice:
 
     def sweep(self, beta: float, nsweeps: int):
         _check(self._lib.spn_sweep(self._h, float(beta), int(nsweeps)))
+
+    def sweep_dc(self, beta: float, nsweeps: int, tile, hits: int = 1):
+        """Double-checkerboard sweeps with `hits`-fold multi-hit (spn_sweep_dc)."""
+        t = (_c.c_int32 * 3)(*(list(tile) + [1] * (3 - len(tile))))
+        _check(self._lib.spn_sweep_dc(self._h, float(beta), int(nsweeps), t, int(hits)))
 
     def observables(self) -> tuple[int, int]:
         E, M = _i64(), _i64()
