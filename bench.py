@@ -66,7 +66,7 @@ def _args():
     p.add_argument("--profile-case", choices=["2d", "3d"], default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
-    p.add_argument("--forms", default="batched,ea,served",
+    p.add_argument("--forms", default="batched,ea,served,dc",
                    help="extra forms measured after the plain step (comma list; empty for none)")
     p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
     p.add_argument("--ea-sweeps", type=int, default=EA_SWEEPS)
@@ -324,6 +324,28 @@ def form_served(n_requests, budget_bytes=120 * 10**9):
                         "120 GB budget; latency = submit -> result on the host"}
 
 
+def form_dc(stream, tiles=((256, 64), (512, 128), (64, 64)), hits=(1, 2, 4), sweeps=20):
+    """The paper's double-checkerboard order (Sec. 3) with k-fold multi-hit on
+    the 2D L = 16384 lattice at T_c: attempts/ns for each tile shape and k
+    (k hits per sweep, so N k attempts per sweep)."""
+    from paper_1006_3865_gb300 import inputs, spn
+
+    lat = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(55))
+    lat.set_stream(stream)
+    beta = 1.0 / TEMPS_2D[1]
+    out = {}
+    for tile in tiles:
+        for k in hits:
+            lat.sweep_dc(beta, 2, tile, k)
+            ms = _timed(stream, lambda: lat.sweep_dc(beta, sweeps, tile, k))
+            out[f"{tile[0]}x{tile[1]}_k{k}"] = L2D * L2D * k * sweeps / (ms * 1e6)
+    lat.close()
+    best = max(out, key=out.get)
+    return {"value": out[best], "unit": UNIT, "best": best, "by_tile_and_hits": out,
+            "workload": f"2D Ising L={L2D} at T=2.269185, double-checkerboard tiles x hits, {sweeps} sweeps each "
+                        "(attempts count every hit)"}
+
+
 def run_forms(a, stream):
     out = {}
     for f in [x for x in a.forms.split(",") if x]:
@@ -333,6 +355,8 @@ def run_forms(a, stream):
             out["ea"] = form_ea(stream, a.ea_sweeps)
         elif f == "served":
             out["served"] = form_served(a.served_requests)
+        elif f == "dc":
+            out["double_checkerboard"] = form_dc(stream)
         else:
             raise SystemExit(f"unknown form {f}")
     return out
