@@ -63,7 +63,7 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-case", choices=["2d", "3d"], default=None,
+    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc"], default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
     p.add_argument("--forms", default="batched,ea,served,dc",
@@ -84,6 +84,22 @@ def run_profile_case(a):
 
     spn_build.build()
     spn.load()
+    if a.profile_case == "ea":  # the full 1024-sample L = 32 batch, a few sweeps per launch
+        dims = (EA_L, EA_L, EA_L)
+        b = spn.EABatch(dims, inputs.ea_bonds(dims, EA_SAMPLES, inputs.unit_seed(0xEA)),
+                        inputs.geometric_ladder(0.2, 2.0), inputs.unit_seed(0xEB), exchange_every=EA_EVERY)
+        for _ in range(3):
+            b.sweep(a.profile_sweeps)
+        b.sync()
+        print("profile case ea done", flush=True)
+        b.close()
+        return
+    if a.profile_case == "dc":  # double checkerboard on 2D L = 16384, 64 x 64 tiles, 4 hits
+        lat = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(3))
+        lat.sweep_dc(1.0 / TEMPS_2D[1], a.profile_sweeps, (64, 64), 4)
+        print("profile case dc E, M =", lat.observables(), flush=True)
+        lat.close()
+        return
     if a.profile_case == "2d":
         lat = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(1))
         beta = 1.0 / TEMPS_2D[1]
