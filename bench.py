@@ -186,6 +186,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(dist, value: float, device: str = "cuda") -> float:
+    """The largest of every rank's value (the slowest rank's time); the value
+    itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, steps: int, attempts_per_step: int, ms: float) -> float:
+    """Whole-job attempts/ns: every rank's attempts over the slowest rank's time."""
+    return ws * steps * attempts_per_step / (ms * 1e6)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -482,11 +499,8 @@ def main():
     clocks = sampler.stop()
     launches = spn.launch_count() - n0
     ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * a.steps * ATTEMPTS_PER_STEP / (ms * 1e6)
+    ms = max_over_ranks(dist, ms)
+    value = job_value(ws, a.steps, ATTEMPTS_PER_STEP, ms)
     # dominant kernel: the 2D streaming sweep, SWEEPS_2D launches per block
     blk = [kevs[k][i][0].elapsed_time(kevs[k][i][1]) for k in range(a.steps) for i in range(len(TEMPS_2D))]
     launch_ms = statistics.mean(blk) / SWEEPS_2D
@@ -528,10 +542,7 @@ def main():
             e2e_step()
         barrier()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dist, dt)
         nbytes = len(TEMPS_2D) * L2D * L2D + L3D ** 3
         trace_bytes = 16 * (len(TEMPS_2D) * SWEEPS_2D + SWEEPS_3D)
         e2e = {"value": ws * a.steps * ATTEMPTS_PER_STEP / (dt * 1e9), "unit": UNIT,

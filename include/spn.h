@@ -109,6 +109,16 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps);
  * whose Lx is a multiple of 64; SPN_E_ARG otherwise. */
 int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile, int32_t hits);
 
+/* Test support for failure detection; the paper has no counterpart.  In the
+ * next streaming-sweep launch (in any handle of the process) the copy of each
+ * CTA's first slice is never issued, so the wait for it runs out after `polls`
+ * polls (the bound every wait of that launch uses).  The kernel then records
+ * the failure, waits (bounded) for the copies it did issue and returns; no
+ * device fault occurs, the context stays usable, and the next spn_observables /
+ * spn_trace / spn_sync of that handle returns SPN_E_TIMEOUT.  Only tests call
+ * this. */
+int spn_test_expire_next_waits(uint32_t polls);
+
 int spn_observables(spn_handle h, int64_t* E, int64_t* M);
 
 /* Recompute E and M from the spins with a full reduction (independent of the

@@ -331,6 +331,11 @@ int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile
   return SPN_OK;
 }
 
+int spn_test_expire_next_waits(uint32_t polls) {
+  spn::stream_expire_next_waits(polls);
+  return SPN_OK;
+}
+
 int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
   if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");

@@ -49,6 +49,9 @@ cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long 
 cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, const PhiloxKeys& K,
                                  uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st);
 bool stream_path_supported(const Lattice& g, int TY);
+// Test support: every bounded wait of the next streaming launch runs out after
+// `polls` polls (its barriers expect more bytes than its copies bring).
+void stream_expire_next_waits(uint32_t polls);
 // Double-checkerboard sweep (tiles Tx x Ty (x Tz), Tx a multiple of 64, an even
 // number of tiles per axis, dense int8 lattice, no bonds): both tile parities
 // of one sweep, `hits` updates of each colour per tile.

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "spn_create_ex": (_c.c_int, [_P(_vp), _c.c_int, _vp, _vp, _u64, _u32, _c.c_int]),
     "spn_sweep": (_c.c_int, [_vp, _dbl, _i64]),
     "spn_sweep_dc": (_c.c_int, [_vp, _dbl, _i64, _P(_i32), _i32]),
+    "spn_test_expire_next_waits": (_c.c_int, [_u32]),
     "spn_observables": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
     "spn_recompute": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
     "spn_trace": (_c.c_int, [_vp, _vp, _vp, _i64, _P(_i64)]),
