@@ -63,10 +63,10 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc"], default=None,
+    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d"], default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
-    p.add_argument("--forms", default="batched,ea,served,dc",
+    p.add_argument("--forms", default="batched,ea,served,dc,packed",
                    help="extra forms measured after the plain step (comma list; empty for none)")
     p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
     p.add_argument("--ea-sweeps", type=int, default=EA_SWEEPS)
@@ -100,12 +100,14 @@ def run_profile_case(a):
         print("profile case dc E, M =", lat.observables(), flush=True)
         lat.close()
         return
-    if a.profile_case == "2d":
+    if a.profile_case in ("2d", "packed2d"):
         lat = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(1))
         beta = 1.0 / TEMPS_2D[1]
     else:
         lat = spn.Lattice(spn.SPN_ISING3D, (L3D, L3D, L3D), inputs.unit_seed(2))
         beta = BETA_3D
+    if a.profile_case.startswith("packed"):
+        lat.path = spn.PATH_PACKED
     lat.sweep(beta, a.profile_sweeps)
     print("profile case", a.profile_case, "E, M =", lat.observables(), flush=True)
     lat.close()
@@ -379,6 +381,59 @@ def form_dc(stream, tiles=((256, 64), (512, 128), (64, 64)), hits=(1, 2, 4), swe
                         "(attempts count every hit)"}
 
 
+def form_packed(stream):
+    """The plain step's lattices held at one bit per spin (the packed path):
+    2D L = 16384 at the three temperatures (200 sweeps each, from the hot start)
+    and 3D L = 512 (100 sweeps).  L2 is flushed (a 512 MiB write) before every
+    sweep, since the packed ping-pong buffers (2 x 32 MiB, 2 x 16 MiB) would fit
+    in it; each sweep is timed alone.  The first sweep of each run includes
+    packing the int8 hot start."""
+    import torch
+
+    from paper_1006_3865_gb300 import inputs, spn
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    peak, peak_kind = _peaks()
+
+    def run(lat, beta, n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        with torch.cuda.stream(stream):
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                lat.sweep(beta, 1)
+                e1.record(stream)
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    lat2 = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(60))
+    lat3 = spn.Lattice(spn.SPN_ISING3D, (L3D, L3D, L3D), inputs.unit_seed(61))
+    for lat in (lat2, lat3):
+        lat.set_stream(stream)
+        lat.path = spn.PATH_PACKED
+    run(lat2, 1.0 / TEMPS_2D[1], 3)  # warm-up
+    run(lat3, BETA_3D, 3)
+    ms2, ms3 = [], []
+    for i, T in enumerate(TEMPS_2D):
+        lat2.reinit(inputs.unit_seed(60 + i))
+        ms2 += run(lat2, 1.0 / T, SWEEPS_2D)
+    lat3.reinit(inputs.unit_seed(61))
+    ms3 = run(lat3, BETA_3D, SWEEPS_3D)
+    lat2.close()
+    lat3.close()
+    tot = sum(ms2) + sum(ms3)
+    sweep2 = statistics.mean(ms2[1:])  # the first sweep of a run also packs
+    sweep3 = statistics.mean(ms3[1:])
+    att2 = L2D * L2D / (sweep2 * 1e6)
+    return {"value": ATTEMPTS_PER_STEP / (tot * 1e6), "unit": UNIT, "ms": tot, "attempts": ATTEMPTS_PER_STEP,
+            "sweep_ms_2d": sweep2, "sweep_ms_3d": sweep3, "attempts_per_ns_2d": att2,
+            "attempts_per_ns_3d": L3D ** 3 / (sweep3 * 1e6),
+            "hbm": {"bytes_per_attempt": 0.25, "achieved_gbs_2d": 0.25 * att2, "peak": peak, "peak_kind": peak_kind,
+                    "frac_2d": 0.25 * att2 / peak},
+            "l2": "flushed before every sweep (512 MiB write, outside the timed sweep)",
+            "workload": WORKLOAD + "; lattices stored at 1 bit per spin (bit-packed path)"}
+
+
 def run_forms(a, stream):
     out = {}
     for f in [x for x in a.forms.split(",") if x]:
@@ -390,6 +445,8 @@ def run_forms(a, stream):
             out["served"] = form_served(a.served_requests)
         elif f == "dc":
             out["double_checkerboard"] = form_dc(stream)
+        elif f == "packed":
+            out["packed"] = form_packed(stream)
         else:
             raise SystemExit(f"unknown form {f}")
     return out

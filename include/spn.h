@@ -164,7 +164,15 @@ int spn_destroy(spn_handle h);
 int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t seg);
 
 /* Which kernel path the handle uses: 0 = generic global-memory sweep,
- * 1 = streaming shared-memory sweep, 2 = shared-memory-resident sweep. */
+ * 1 = streaming shared-memory sweep, 2 = shared-memory-resident sweep,
+ * 3 = bit-packed streaming sweep.  Path 3 keeps the lattice in HBM as one bit
+ * per spin between sweeps (row r = y + Ly z: ceil(Lx/64) words of the even-x
+ * sites, as many of the odd-x sites, zero words up to a multiple of 4; a set
+ * bit is spin -1); spn_sweep packs the int8 lattice on entry when needed, and
+ * the calls that read spins (spn_get_spins, spn_recompute, the other paths)
+ * unpack it first.  Results never depend on the path.  spn_set_path fails
+ * with SPN_E_ARG if the path does not support the lattice (bonds, a band that
+ * does not divide Ly). */
 int spn_get_path(spn_handle h, int32_t* path);
 int spn_set_path(spn_handle h, int32_t path);
 

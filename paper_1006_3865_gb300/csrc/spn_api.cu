@@ -92,6 +92,26 @@ int ensure_stream_buffers(spn_ctx* h) {
   return SPN_OK;
 }
 
+// Bit-packed path: both packed buffers, padding words zeroed once (the sweep
+// writes data words only).
+int ensure_packed_buffers(spn_ctx* h) {
+  const size_t bytes = (size_t)spn::packed_row_words(h->g.Lx) * 4 * (size_t)(h->g.N / h->g.Lx);
+  for (int i = 0; i < 2; ++i)
+    if (!h->packed[i]) {
+      SPN_CUDA(cudaMalloc(&h->packed[i], bytes), "cudaMalloc(packed)");
+      SPN_CUDA(cudaMemsetAsync(h->packed[i], 0, bytes, h->st), "cudaMemsetAsync(packed)");
+    }
+  return SPN_OK;
+}
+
+// Make the int8 buffer current again after packed sweeps.
+int unpack_if_live(spn_ctx* h) {
+  if (!h->packed_live) return SPN_OK;
+  SPN_CUDA(spn::launch_unpack(h->g, h->packed[h->pcur], h->spins[h->cur], h->st), "unpack");
+  h->packed_live = false;
+  return SPN_OK;
+}
+
 void pick_default_path(spn_ctx* h) {
   const spn::Lattice g = stream_lattice(h);
   int ty = 32;
@@ -150,6 +170,7 @@ int fold(spn_ctx* h) {
 }
 
 int recompute(spn_ctx* h, int64_t* E, int64_t* M) {
+  if (int rc = unpack_if_live(h)) return rc;
   SPN_CUDA(cudaMemsetAsync(h->d_bad, 0, sizeof(int), h->st), "cudaMemsetAsync");
   SPN_CUDA(spn::launch_observables(h->g, h->spins[h->cur], h->d_obs, h->d_bad, h->st), "observables");
   unsigned long long r[3];
@@ -172,6 +193,8 @@ void destroy(spn_ctx* h) {
   cudaFree(h->spins[1]);
   cudaFree(h->staged[0]);
   cudaFree(h->staged[1]);
+  cudaFree(h->packed[0]);
+  cudaFree(h->packed[1]);
   cudaFree(h->d_bonds);
   cudaFree(h->d_acc);
   cudaFree(h->d_err);
@@ -262,6 +285,17 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
   const bool staged = h->path == spn::kPathStream && gs.pitch != 0;
   const size_t nrow = (size_t)(h->g.N / h->g.Lx);
   int sc = 0;  // current staged lattice
+  if (h->path == spn::kPathPacked) {
+    geo = spn::stream_geometry(h->g, h->tile_y, h->step_slices, h->seg, true);
+    if (!spn::stream_geometry_ok(h->g, geo)) return fail(SPN_E_STATE, "packed geometry does not fit one CTA");
+    if ((rc = ensure_packed_buffers(h))) return rc;
+    if (!h->packed_live) {
+      SPN_CUDA(spn::launch_pack(h->g, h->spins[h->cur], h->packed[h->pcur], h->st), "pack");
+      h->packed_live = true;
+    }
+  } else if ((rc = unpack_if_live(h))) {
+    return rc;
+  }
   if (h->path == spn::kPathStream) {
     geo = spn::stream_geometry(gs, h->tile_y, h->step_slices, h->seg);
     if (!spn::stream_geometry_ok(gs, geo)) return fail(SPN_E_STATE, "streaming geometry does not fit one CTA");
@@ -275,7 +309,11 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
     const uint32_t sweep = (uint32_t)(h->sweeps + t);
     unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);
     cudaError_t e;
-    if (staged) {
+    if (h->path == spn::kPathPacked) {
+      e = spn::launch_sweep_stream(h->g, h->packed[h->pcur], h->packed[h->pcur ^ 1], geo, T, K, h->stream_id, sweep,
+                                   acc, h->d_err, h->st);
+      if (e == cudaSuccess) h->pcur ^= 1;
+    } else if (staged) {
       e = spn::launch_sweep_stream(gs, h->staged[sc], h->staged[sc ^ 1], geo, T, K, h->stream_id, sweep, acc,
                                    h->d_err, h->st);
       if (e == cudaSuccess) sc ^= 1;
@@ -315,6 +353,7 @@ int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile
     return fail(SPN_E_ARG, "sweep counter times hits would exceed 2^32");
   int rc = ensure_acc(h, nsweeps);
   if (rc) return rc;
+  if ((rc = unpack_if_live(h))) return rc;
   const spn::DevThr T = spn::make_thresholds(beta);
   const spn::PhiloxKeys K = spn::philox_keys(h->seed);
   for (int64_t t = 0; t < nsweeps; ++t) {
@@ -371,6 +410,7 @@ int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
   if (!h || !host_out) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
+  if (int rc = unpack_if_live(h)) return rc;
   SPN_CUDA(cudaMemcpyAsync(host_out, h->spins[h->cur], bytes, cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync");
   SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
   return SPN_OK;
@@ -382,6 +422,7 @@ int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
   int rc = fold(h);
   if (rc) return rc;
+  h->packed_live = false;  // the new spins replace the packed lattice
   SPN_CUDA(cudaMemcpyAsync(h->spins[h->cur], host_in, bytes, cudaMemcpyHostToDevice, h->st), "cudaMemcpyAsync");
   int64_t E, M;
   if ((rc = recompute(h, &E, &M))) return rc;
@@ -402,6 +443,7 @@ int spn_reinit(spn_handle h, uint64_t seed, uint32_t stream, int init) {
   h->folded = 0;
   h->traceE.clear();
   h->traceM.clear();
+  h->packed_live = false;
   if (init == SPN_INIT_HOT)
     SPN_CUDA(spn::launch_init_hot(h->g, h->spins[h->cur], seed, stream, h->st), "init");
   else
@@ -449,10 +491,11 @@ int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t se
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   const int ty = h->g.nd == 3 ? tile_y : 1;
   if (step_slices < 0 || seg < 0) return fail(SPN_E_ARG, "negative tiling parameter");
-  const spn::Lattice gs = stream_lattice(h);
-  if (!spn::stream_path_supported(gs, ty))
+  const bool packed = h->path == spn::kPathPacked;
+  const spn::Lattice gs = packed ? h->g : stream_lattice(h);
+  if (!spn::stream_path_supported(gs, ty, packed))
     return fail(SPN_E_ARG, "band of %d rows does not divide the lattice (or the lattice has bonds)", tile_y);
-  const spn::StreamGeom geo = spn::stream_geometry(gs, ty, step_slices, seg);
+  const spn::StreamGeom geo = spn::stream_geometry(gs, ty, step_slices, seg, packed);
   if (!spn::stream_geometry_ok(gs, geo)) return fail(SPN_E_ARG, "tiling too large for one CTA");
   h->tile_y = ty;
   h->step_slices = step_slices;
@@ -473,6 +516,13 @@ int spn_set_path(spn_handle h, int32_t path) {
     if (!spn::stream_path_supported(stream_lattice(h), h->tile_y))
       return fail(SPN_E_ARG, "streaming path needs a dividing band and no bonds");
     const int rc = ensure_stream_buffers(h);
+    if (rc) return rc;
+  } else if (path == spn::kPathPacked) {
+    if (!spn::stream_path_supported(h->g, h->tile_y, true))
+      return fail(SPN_E_ARG, "bit-packed path needs a dividing band and no bonds");
+    const spn::StreamGeom geo = spn::stream_geometry(h->g, h->tile_y, h->step_slices, h->seg, true);
+    if (!spn::stream_geometry_ok(h->g, geo)) return fail(SPN_E_ARG, "bit-packed tiling too large for one CTA");
+    const int rc = ensure_packed_buffers(h);
     if (rc) return rc;
   } else if (path != spn::kPathGeneric) {
     return fail(SPN_E_ARG, "unknown path %d", path);

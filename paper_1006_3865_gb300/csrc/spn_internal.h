@@ -24,11 +24,13 @@ uint64_t boltzmann_threshold(double beta, int dE);
 DevThr make_thresholds(double beta);
 
 // Kernel paths of a single lattice.
-enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2 };
+enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2, kPathPacked = 3 };
 
-// Streaming-kernel geometry (see ising.cu): TY rows per band (3D), R slices
-// per step, nseg segments along the streamed axis, raw / bit slice buffers.
+// Streaming-kernel geometry (stream.cu): TY rows per band (3D), R slices per
+// step, nseg segments along the streamed axis, raw / bit slice buffers; packed:
+// the lattice is stored as bit words (rows of packed_row_words(Lx) words).
 struct StreamGeom {
+  int packed;
   int TY, R, nseg, threads, nraw, nbit;
   int roundsC, roundsA, roundsB, qcap;  // words per thread per phase; tie-queue entries per warp
   size_t smem;
@@ -48,7 +50,14 @@ cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t
 cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long long* out2, int* bad, cudaStream_t st);
 cudaError_t launch_sweep_generic(const Lattice& g, int8_t* s, const DevThr& T, const PhiloxKeys& K,
                                  uint32_t stream_id, uint32_t sweep, unsigned long long* acc, cudaStream_t st);
-bool stream_path_supported(const Lattice& g, int TY);
+bool stream_path_supported(const Lattice& g, int TY, bool packed = false);
+// Bit-packed storage: row r (= y + Ly z) holds W = ceil(Lx / 64) words of the
+// even-x sites (bit i of word j: x = 64 j + 2 i, set iff the spin is -1), then W
+// words of the odd-x sites (x = 64 j + 2 i + 1), then zero words up to a
+// multiple of 4 words; bits beyond Lx are 0.
+int packed_row_words(int Lx);
+cudaError_t launch_pack(const Lattice& g, const int8_t* s, uint32_t* w, cudaStream_t st);
+cudaError_t launch_unpack(const Lattice& g, const uint32_t* w, int8_t* s, cudaStream_t st);
 // Test support: every bounded wait of the next streaming launch runs out after
 // `polls` polls (its barriers expect more bytes than its copies bring).
 void stream_expire_next_waits(uint32_t polls);
@@ -59,9 +68,9 @@ bool dc_supported(const Lattice& g, int Tx, int Ty, int Tz);
 cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz, int hits, const DevThr& T,
                             const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                             cudaStream_t st);
-StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg);
+StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed = false);
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
-cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out, const StreamGeom& geo,
+cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, const StreamGeom& geo,
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st);
 
@@ -150,6 +159,11 @@ struct spn_ctx {
   // streaming sweep of a lattice whose Lx is not a multiple of 64: the lattice
   // is staged into rows padded to 64 bytes for the sweeps of one spn_sweep call
   int8_t* staged[2] = {nullptr, nullptr};
+  // bit-packed path: the lattice lives in packed[pcur] while packed_live (the
+  // int8 buffer is then stale until the next call that needs it)
+  uint32_t* packed[2] = {nullptr, nullptr};
+  int pcur = 0;
+  bool packed_live = false;
   uint8_t* d_bonds = nullptr;
   cudaStream_t st = nullptr;
   int path = spn::kPathGeneric;

@@ -53,10 +53,11 @@ constexpr int kSmemCap = 233472 / kCtasPerSm - 1024;  // 228 KB per SM, 1 KB res
 constexpr int kFirstCalls = SPN_FIRST_CALLS;  // Philox calls of the first decision stage (4 planes each)
 
 struct StreamArgs {
-  const int8_t* in;
-  int8_t* out;
+  const void* in;  // int8 rows of P bytes, or bit-packed rows of RS words
+  void* out;
   int Lx, Ly, S;  // S: slices along the slowest axis (Ly in 2D, Lz in 3D)
-  int P;          // bytes per row in memory (a multiple of 64, >= Lx)
+  int P;          // int8: bytes per row in memory (a multiple of 64, >= Lx); packed: 64 ceil(Lx / 64)
+  int RS;         // packed: words per row (E words, O words, zero padding; a multiple of 4)
   int vbl;        // sites per colour in the last 64-site word of a row (1 .. 32)
   int TY, R, nseg, nraw, nbit;
   int roundsC, roundsA, roundsB;
@@ -80,23 +81,27 @@ __device__ __forceinline__ uint32_t pack_item(int i, int total, int ks, uint32_t
   return off | ((uint32_t)ks << 24) | (i < total ? 0x80000000u : 0u);
 }
 
-template <int ND>
+// PACKED: the lattice lives in HBM as bit words (row r: E words 0 .. W-1, O
+// words W .. 2W-1, zero padding to RS words), copied straight into the bit slots
+// (one mbarrier per slot) and written back as words; no int8 conversion.
+template <int ND, bool PACKED>
 __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(const __grid_constant__ StreamArgs a) {
   constexpr int NC = ND;  // classes with dE > 0: dE = 4 (q + 1), q < NC
   extern __shared__ __align__(128) uint8_t smem[];
-  const int P = a.P, W = P >> 6, W2 = 2 * W, vbl = a.vbl;
+  const int P = a.P, W = P >> 6, W2 = PACKED ? a.RS : 2 * W, vbl = a.vbl;
   const uint32_t vmaskl = vbl == 32 ? 0xffffffffu : ((1u << vbl) - 1u);  // valid lanes of a row's last word
   const int R = a.R, nbit = a.nbit, nraw = a.nraw, S = a.S;
   const int RSL = (ND == 3) ? a.TY + 4 : 1;    // rows per slice: band + 2 halo rows on each side
   const int rowsA = (ND == 3) ? a.TY + 2 : 1;  // colour-0 rows: band + 1 ring row on each side
   const int rowsB = (ND == 3) ? a.TY : 1;      // colour-1 rows: the band
-  const int rawBytes = RSL * P;
-  const int rawStride = (rawBytes + 127) & ~127;
+  const int rowBytes = PACKED ? W2 * 4 : P;  // bytes of one row copy
+  const int rawBytes = RSL * rowBytes;        // bytes of one slice copy
+  const int rawStride = PACKED ? 0 : (rawBytes + 127) & ~127;
   const int sliceWords = RSL * W2;
   uint8_t* raw = smem;
   uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)nraw * rawStride);
   uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)nbit * sliceWords);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lut + (PACKED ? 0 : 256));
   const uint4* raw16 = reinterpret_cast<const uint4*>(smem);
 
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
@@ -105,10 +110,10 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
   const int ze = (int)(((int64_t)(blockIdx.y + 1) * S) / a.nseg);
   const int H = ze - zs;
   const int nload = H + 4;  // local slices li = 0 .. H + 3 <-> global zs - 2 + li
-  const int64_t sliceStride = (int64_t)P * ((ND == 3) ? a.Ly : 1);
+  const int64_t sliceStride = (int64_t)rowBytes * ((ND == 3) ? a.Ly : 1);  // bytes
 
   // int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
-  for (int i = tid; i < 256; i += nth) {
+  for (int i = tid; i < (PACKED ? 0 : 256); i += nth) {
     uint32_t lo = 0, hi = 0;
     for (int k = 0; k < 4; ++k) {
       const uint32_t pair = (((i >> k) & 1) ? 0xffu : 0x01u) | ((((i >> (4 + k)) & 1) ? 0xffu : 0x01u) << 8);
@@ -122,13 +127,13 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
   }
 
   // ---- per-thread items
-  uint32_t cOff[kMaxRounds], cRaw[kMaxRounds];               // conversion
+  uint32_t cOff[kMaxRounds] = {}, cRaw[kMaxRounds] = {};     // conversion (int8 only)
   uint32_t aOff[kMaxRounds], aC0[kMaxRounds], aFl[kMaxRounds];  // colour 0
   uint32_t bOff[kMaxRounds], bC0[kMaxRounds], bFl[kMaxRounds], bOut[kMaxRounds];  // colour 1
 #pragma unroll
   for (int q = 0; q < kMaxRounds; ++q) {
     const int i = tid + q * nth;
-    {
+    if (!PACKED) {
       const int per = RSL * W, ks = i / per, r = (i - ks * per) / W, j = i - ks * per - r * W;
       cOff[q] = pack_item(i, R * per, ks, (uint32_t)(r * W2 + j));
       cRaw[q] = ((uint32_t)(r * P + 64 * j) >> 4) | (j == W - 1 ? 0x80000000u : 0u);  // bit 31: last word
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
       bOff[q] = pack_item(i, R * per, ks, (uint32_t)(((ND == 3) ? (r + 2) * W2 : 0) + j));
       bC0[q] = 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)((ND == 3) ? gy : 0));
       bFl[q] = (uint32_t)((y0 + r) & 1) | 2u | (j == 0 ? 4u : 0u) | (j == W - 1 ? 8u : 0u);
-      bOut[q] = (uint32_t)(((ND == 3) ? gy * P : 0) + 64 * j);
+      bOut[q] = PACKED ? (uint32_t)(((ND == 3) ? gy * W2 : 0) + j) : (uint32_t)(((ND == 3) ? gy * P : 0) + 64 * j);
     }
   }
   // chunk order of the 64-byte span rotated by lane pair: a quarter warp reads
@@ -161,15 +166,19 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
   auto wrapS = [&](int z) { return z < 0 ? z + S : (z >= S ? z - S : z); };
   auto wrapY = [&](int y) { return y < 0 ? y + a.Ly : (y >= a.Ly ? y - a.Ly : y); };
 
-  // Raw ring (uniform state): slices [0, conv) converted, [0, issued) requested;
-  // cslot / cpar: slot and mbarrier phase of the next slice to convert.
-  int conv = 0, issued = 0, islot = 0, cslot = 0;
+  // Copy ring (uniform state): slices [0, conv) converted (packed: arrived),
+  // [0, issued) requested, [0, dead) no longer read; cslot / cpar: slot and
+  // mbarrier phase of the next slice to convert.  int8 slices go to a ring of
+  // nraw raw slots; packed slices straight to their bit slot (nraw = nbit).
+  int conv = 0, issued = 0, islot = 0, cslot = 0, dead = 0;
   uint32_t cpar = 0;
   auto issue_upto = [&]() {
-    const int lim = conv + nraw < nload ? conv + nraw : nload;
+    const int free_from = PACKED ? dead : conv;
+    const int lim = free_from + nraw < nload ? free_from + nraw : nload;
     for (; issued < lim; ++issued) {
       if (tid < 32) {
-        uint8_t* B = raw + (size_t)islot * rawStride;
+        uint8_t* B = PACKED ? reinterpret_cast<uint8_t*>(bits + (size_t)islot * sliceWords)
+                            : raw + (size_t)islot * rawStride;
         uint64_t* bar = &bars[islot];
         if (lane == 0) {
           fence_proxy_async();  // earlier generic reads of the slot before the async writes
@@ -180,7 +189,9 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
         const bool skip = a.skip_first && issued == 0;  // its barrier then never completes
         for (int r = lane; r < RSL && !skip; r += 32) {
           const int gy = (ND == 3) ? wrapY(y0 - 2 + r) : 0;
-          bulk_g2s(B + (size_t)r * P, a.in + gz * sliceStride + (int64_t)gy * P, (uint32_t)P, bar);
+          bulk_g2s(B + (size_t)r * rowBytes,
+                   static_cast<const uint8_t*>(a.in) + gz * sliceStride + (int64_t)gy * rowBytes,
+                   (uint32_t)rowBytes, bar);
         }
       }
       if (++islot == nraw) islot = 0;
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
     for (int q = 0; q < kMaxRounds; ++q) {
       const uint32_t x = cOff[q];
       const int ks = (int)((x >> 24) & 0x7fu);
-      if (q < a.roundsC && (x >> 31) && ks < ns) {
+      if (!PACKED && q < a.roundsC && (x >> 31) && ks < ns) {
         int r = cslot + ks;
         r -= r >= nraw ? nraw : 0;
         int sl = sfirst + ks;
@@ -325,23 +336,33 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
         if (c == 1) {
           const int par = (int)((flq[q] + (uint32_t)gz + 1u) & 1u);
           const uint32_t E = par ? oj : nb, O = par ? nb : oj;
-          const uint32_t X = (E & 0x0f0f0f0fu) | ((O << 4) & 0xf0f0f0f0u);  // byte v: sites 16v .. 16v + 7
-          const uint32_t Y = ((E >> 4) & 0x0f0f0f0fu) | (O & 0xf0f0f0f0u);  // byte v: sites 16v + 8 .. 16v + 15
-          uint4* dst = reinterpret_cast<uint4*>(a.out + (int64_t)gz * sliceStride + bOut[q]);
+          if constexpr (PACKED) {
+            uint32_t* dst =
+                reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(a.out) + (int64_t)gz * sliceStride) + bOut[q];
+            dst[0] = E;
+            dst[W] = O;
+          } else {
+            const uint32_t X = (E & 0x0f0f0f0fu) | ((O << 4) & 0xf0f0f0f0u);  // byte v: sites 16v .. 16v + 7
+            const uint32_t Y = ((E >> 4) & 0x0f0f0f0fu) | (O & 0xf0f0f0f0u);  // byte v: sites 16v + 8 .. 16v + 15
+            uint4* dst =
+                reinterpret_cast<uint4*>(static_cast<int8_t*>(a.out) + (int64_t)gz * sliceStride + bOut[q]);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const uint2 lo = lut[(X >> (8 * v)) & 0xffu];
-            const uint2 hi = lut[(Y >> (8 * v)) & 0xffu];
-            dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+            for (int v = 0; v < 4; ++v) {
+              const uint2 lo = lut[(X >> (8 * v)) & 0xffu];
+              const uint2 hi = lut[(Y >> (8 * v)) & 0xffu];
+              dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+            }
           }
         }
       }
     }
   };
 
-  // Schedule: step b0 converts slices b0+4 .. b0+3+ns, updates colour 0 on
-  // b0+3 .. b0+2+ns and colour 1 (with the int8 output) on b0+2 .. b0+1+ns;
-  // 2R+3 bit slots hold every slice a step touches.
+  // Schedule: step b0 converts (packed: waits for) slices b0+4 .. b0+3+ns,
+  // updates colour 0 on b0+3 .. b0+2+ns and colour 1 (with the output) on
+  // b0+2 .. b0+1+ns; 2R+3 bit slots hold every slice a step touches, and a
+  // packed slice is requested as soon as the slice two steps back in its slot
+  // is no longer read.
   issue_upto();
   bool ok = true;
   const int pro = 4 < nload ? 4 : nload;
@@ -364,6 +385,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
     const bool mine = convert(b0 + 4, ns, slot(4));
     ok = __syncthreads_and(mine);
     if (!ok) break;
+    dead = b0 + 1;  // every thread is past the previous step: slices <= b0 are no longer read
     issue_upto();
     phase(aOff, aC0, aFl, a.roundsA, b0 + 3, ns, slot(3), wrapS(zs + 1 + b0), 0);
     __syncthreads();
@@ -390,48 +412,67 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
 
 static int pitch_of(const Lattice& g) { return g.pitch ? g.pitch : g.Lx; }
 
+int packed_row_words(int Lx) { return (2 * ((Lx + 63) / 64) + 3) & ~3; }
+
 static std::atomic<uint32_t> g_expire_next{0};
 
 void stream_expire_next_waits(uint32_t polls) { g_expire_next.store(polls ? polls : 1); }
 
-bool stream_path_supported(const Lattice& g, int TY) {
+namespace {
+
+// Row copy in bytes and the smem row stride in words for a storage form.
+int row_bytes(const Lattice& g, bool packed) { return packed ? 4 * packed_row_words(g.Lx) : pitch_of(g); }
+int row_stride_words(const Lattice& g, bool packed) {
+  return packed ? packed_row_words(g.Lx) : 2 * (pitch_of(g) / 64);
+}
+
+}  // namespace
+
+bool stream_path_supported(const Lattice& g, int TY, bool packed) {
   if (g.bonds) return false;
-  const int P = pitch_of(g);
-  if (g.Lx < 2 || (g.Lx & 1) || P % 64 || P < g.Lx || P - g.Lx >= 64) return false;
+  if (g.Lx < 2 || (g.Lx & 1)) return false;
+  if (!packed) {
+    const int P = pitch_of(g);
+    if (P % 64 || P < g.Lx || P - g.Lx >= 64) return false;
+  } else if (g.pitch) {
+    return false;  // packed rows carry their own padding
+  }
   if (g.nd == 3 && (TY < 2 || TY > 250 || (TY & 1) || g.Ly % TY)) return false;
-  if (P / 64 > 65535) return false;
+  if ((g.Lx + 63) / 64 > 65535) return false;
   const int RSL = g.nd == 3 ? TY + 4 : 1;
-  if ((int64_t)RSL * P * 2 > 96 * 1024) return false;  // two raw slices must fit beside the rest
+  if (!packed && (int64_t)RSL * pitch_of(g) * 2 > 96 * 1024) return false;  // two raw slices fit beside the rest
+  if (packed && (int64_t)RSL * row_bytes(g, true) * 5 > 160 * 1024) return false;  // five bit slots fit one CTA
   return true;
 }
 
 namespace {
 
-size_t smem_bytes(const Lattice& g, int TY, int R, int nraw) {
-  const int W = pitch_of(g) / 64;
+size_t smem_bytes(const Lattice& g, int TY, int R, int nraw, bool packed) {
   const int RSL = g.nd == 3 ? TY + 4 : 1;
+  const size_t bitsB = (size_t)(2 * R + 3) * RSL * row_stride_words(g, packed) * 4;
+  if (packed) return bitsB + (size_t)(2 * R + 3) * 8;
   const size_t rawStride = (size_t)((RSL * pitch_of(g) + 127) & ~127);
-  const size_t bitsB = (size_t)(2 * R + 3) * RSL * 2 * W * 4;
   return (size_t)nraw * rawStride + bitsB + 256 * 8 + (size_t)nraw * 8;
 }
 
-void phase_counts(const Lattice& g, int TY, int R, int& nC, int& nA, int& nB) {
-  const int W = pitch_of(g) / 64;
-  nC = R * (g.nd == 3 ? TY + 4 : 1) * W;
+void phase_counts(const Lattice& g, int TY, int R, bool packed, int& nC, int& nA, int& nB) {
+  const int W = (g.Lx + 63) / 64;
+  nC = packed ? 0 : R * (g.nd == 3 ? TY + 4 : 1) * W;
   nA = R * (g.nd == 3 ? TY + 2 : 1) * W;
   nB = R * (g.nd == 3 ? TY : 1) * W;
 }
 
 }  // namespace
 
-StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg) {
+StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed) {
   StreamGeom s{};
+  s.packed = packed ? 1 : 0;
   s.TY = g.nd == 3 ? TY : 1;
   const int S = g.nd == 3 ? g.Lz : g.Ly;
   const int maxT = max_threads(g.nd);
   auto threads_for = [&](int r) {  // at most kMaxRounds words per thread and phase
     int nC, nA, nB;
-    phase_counts(g, s.TY, r, nC, nA, nB);
+    phase_counts(g, s.TY, r, packed, nC, nA, nB);
     const int th = ((std::max(nC, std::max(nA, nB)) + kMaxRounds - 1) / kMaxRounds + 31) / 32 * 32;
     return std::max(64, th);
   };
@@ -442,8 +483,8 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg) {
     R = 1;
     for (int r = 1; r <= std::min(S, 64); ++r) {
       int nC, nA, nB;
-      phase_counts(g, s.TY, r, nC, nA, nB);
-      if (threads_for(r) > maxT || smem_bytes(g, s.TY, r, 2 * r) > (size_t)kSmemCap) break;
+      phase_counts(g, s.TY, r, packed, nC, nA, nB);
+      if (threads_for(r) > maxT || smem_bytes(g, s.TY, r, 2 * r, packed) > (size_t)kSmemCap) break;
       R = r;
       if (nA >= 128) break;
     }
@@ -452,14 +493,18 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg) {
   s.nbit = 2 * R + 3;
   s.threads = std::min(maxT, threads_for(R));
   int nC, nA, nB;
-  phase_counts(g, s.TY, R, nC, nA, nB);
+  phase_counts(g, s.TY, R, packed, nC, nA, nB);
   s.roundsC = (nC + s.threads - 1) / s.threads;
   s.roundsA = (nA + s.threads - 1) / s.threads;
   s.roundsB = (nB + s.threads - 1) / s.threads;
   s.qcap = 0;
-  s.nraw = 2 * R;  // a slice is requested about one step before it is converted
-  while (s.nraw > R && smem_bytes(g, s.TY, R, s.nraw) > (size_t)kSmemCap) --s.nraw;
-  s.smem = smem_bytes(g, s.TY, R, s.nraw);
+  if (packed) {
+    s.nraw = s.nbit;  // copies land in the bit slots
+  } else {
+    s.nraw = 2 * R;  // a slice is requested about one step before it is converted
+    while (s.nraw > R && smem_bytes(g, s.TY, R, s.nraw, false) > (size_t)kSmemCap) --s.nraw;
+  }
+  s.smem = smem_bytes(g, s.TY, R, s.nraw, packed);
   if (nseg <= 0) {
     const int tiles = g.nd == 3 ? g.Ly / s.TY : 1;
     const int want = device_sm_count() * kCtasPerSm;
@@ -470,17 +515,19 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg) {
 }
 
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
+  const bool packed = geo.packed != 0;
   if (geo.R < 1 || geo.R > 127 || geo.threads < 32 || geo.threads > max_threads(g.nd) || geo.threads % 32) return false;
   int nC, nA, nB;
-  phase_counts(g, geo.TY, geo.R, nC, nA, nB);
+  phase_counts(g, geo.TY, geo.R, packed, nC, nA, nB);
   if (geo.roundsC * geo.threads < nC || geo.roundsA * geo.threads < nA || geo.roundsB * geo.threads < nB) return false;
   if (geo.roundsC > kMaxRounds || geo.roundsA > kMaxRounds || geo.roundsB > kMaxRounds) return false;
-  if (geo.smem != smem_bytes(g, geo.TY, geo.R, geo.nraw)) return false;
-  return geo.smem <= 227 * 1024 && geo.nraw >= geo.R && geo.nbit == 2 * geo.R + 3 && geo.nseg >= 1 &&
+  if (geo.smem != smem_bytes(g, geo.TY, geo.R, geo.nraw, packed)) return false;
+  if (packed ? geo.nraw != geo.nbit : geo.nraw < geo.R) return false;
+  return geo.smem <= 227 * 1024 && geo.nbit == 2 * geo.R + 3 && geo.nseg >= 1 &&
          geo.nseg <= (g.nd == 3 ? g.Lz : g.Ly);
 }
 
-cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out, const StreamGeom& geo,
+cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, const StreamGeom& geo,
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st) {
   if (!stream_geometry_ok(g, geo)) return cudaErrorInvalidConfiguration;
@@ -489,7 +536,8 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
   a.in = in;
   a.out = out;
   a.Lx = g.Lx;
-  a.P = pitch_of(g);
+  a.P = geo.packed ? 64 * ((g.Lx + 63) / 64) : pitch_of(g);
+  a.RS = geo.packed ? packed_row_words(g.Lx) : 0;
   a.vbl = (g.Lx - (a.P - 64)) / 2;
   a.Ly = g.Ly;
   a.S = g.nd == 3 ? g.Lz : g.Ly;
@@ -521,27 +569,93 @@ cudaError_t launch_sweep_stream(const Lattice& g, const int8_t* in, int8_t* out,
   dim3 grid(g.nd == 3 ? g.Ly / geo.TY : 1, geo.nseg);
   // function attributes are set once per device and raised only when a launch needs more
   static std::mutex mu;
-  static int smem_set[128][2] = {};
+  static int smem_set[128][4] = {};
   int dev = 0;
   cudaGetDevice(&dev);
+  const int variant = (g.nd == 3 ? 1 : 0) + (geo.packed ? 2 : 0);
+  auto kernel = [&]() -> void (*)(StreamArgs) {
+    switch (variant) {
+      case 0: return k_sweep_stream<2, false>;
+      case 1: return k_sweep_stream<3, false>;
+      case 2: return k_sweep_stream<2, true>;
+      default: return k_sweep_stream<3, true>;
+    }
+  }();
   {
     std::lock_guard<std::mutex> lock(mu);
-    int& cur = smem_set[dev & 127][g.nd == 3 ? 1 : 0];
+    int& cur = smem_set[dev & 127][variant];
     if ((int)geo.smem > cur) {
-      if (g.nd == 3) {
-        cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
-        cudaFuncSetAttribute(k_sweep_stream<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      } else {
-        cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
-        cudaFuncSetAttribute(k_sweep_stream<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      }
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)geo.smem);
+      cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       cur = (int)geo.smem;
     }
   }
-  if (g.nd == 3)
-    k_sweep_stream<3><<<grid, geo.threads, geo.smem, st>>>(a);
-  else
-    k_sweep_stream<2><<<grid, geo.threads, geo.smem, st>>>(a);
+  kernel<<<grid, geo.threads, geo.smem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---- conversion between int8 rows and bit-packed rows (warp per 64-site word)
+
+namespace {
+
+__global__ void k_pack(const int8_t* __restrict__ s, uint32_t* __restrict__ w, int Lx, int W, int RS, int64_t units) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {
+    const int64_t row = u / W;
+    const int j = (int)(u - row * W);
+    const int x = 64 * j + 2 * lane;
+    uint32_t pair = 0x0101u;  // padding sites: +1, bit 0
+    if (x < Lx) pair = *reinterpret_cast<const uint16_t*>(s + row * Lx + x);
+    const uint32_t e = __ballot_sync(0xffffffffu, (pair & 0x80u) != 0u);    // x even: spin -1
+    const uint32_t o = __ballot_sync(0xffffffffu, (pair & 0x8000u) != 0u);  // x odd
+    uint32_t* dst = w + row * RS;
+    if (lane == 0) dst[j] = e;
+    if (lane == 1) dst[W + j] = o;
+    if (j == W - 1 && lane < RS - 2 * W) dst[2 * W + lane] = 0u;
+  }
+}
+
+__global__ void k_unpack(const uint32_t* __restrict__ w, int8_t* __restrict__ s, int Lx, int W, int RS, int64_t units) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {
+    const int64_t row = u / W;
+    const int j = (int)(u - row * W);
+    const int x = 64 * j + 2 * lane;
+    const uint32_t e = w[row * RS + j], o = w[row * RS + W + j];
+    if (x < Lx) {
+      const uint32_t lo = ((e >> lane) & 1u) ? 0xffu : 0x01u, hi = ((o >> lane) & 1u) ? 0xff00u : 0x0100u;
+      *reinterpret_cast<uint16_t*>(s + row * Lx + x) = (uint16_t)(lo | hi);
+    }
+  }
+}
+
+int conv_blocks(int64_t units) {
+  const int64_t want = (units + 7) / 8;  // 8 warps per block
+  const int64_t cap = (int64_t)device_sm_count() * 16;
+  return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const Lattice& g, const int8_t* s, uint32_t* w, cudaStream_t st) {
+  if ((g.Lx & 1) || ((uintptr_t)s & 1)) return cudaErrorInvalidValue;
+  const int W = (g.Lx + 63) / 64;
+  const int64_t units = g.N / g.Lx * W;
+  if (units == 0) return cudaSuccess;
+  k_pack<<<conv_blocks(units), 256, 0, st>>>(s, w, g.Lx, W, packed_row_words(g.Lx), units);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const Lattice& g, const uint32_t* w, int8_t* s, cudaStream_t st) {
+  if ((g.Lx & 1) || ((uintptr_t)s & 1)) return cudaErrorInvalidValue;
+  const int W = (g.Lx + 63) / 64;
+  const int64_t units = g.N / g.Lx * W;
+  if (units == 0) return cudaSuccess;
+  k_unpack<<<conv_blocks(units), 256, 0, st>>>(w, s, g.Lx, W, packed_row_words(g.Lx), units);
   count_launches(1);
   return cudaGetLastError();
 }

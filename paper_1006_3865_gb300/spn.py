@@ -40,6 +40,7 @@ SPN_RUN_LOOP = 1
 PATH_GENERIC = 0
 PATH_STREAM = 1
 PATH_RESIDENT = 2
+PATH_PACKED = 3
 
 _lock = threading.Lock()
 _lib = None
@@ -260,8 +261,8 @@ class Lattice:
     def sync(self):
         _check(self._lib.spn_sync(self._h))
 
-    def set_tiling(self, tile_x: int, tile_y: int = 0, seg: int = 0):
-        _check(self._lib.spn_set_tiling(self._h, tile_x, tile_y, seg))
+    def set_tiling(self, tile_y: int, step_slices: int = 0, seg: int = 0):
+        _check(self._lib.spn_set_tiling(self._h, tile_y, step_slices, seg))
 
     @property
     def path(self) -> int:

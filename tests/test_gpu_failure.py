@@ -1,5 +1,5 @@
-"""Failure detection without a device fault: a streaming launch whose first
-slice is never copied gives up its bounded wait, records the failure and
+"""Failure detection without a device fault: a streaming launch (int8 or
+bit-packed) whose first slice is never copied gives up its bounded wait, records the failure and
 returns; the host reports SPN_E_TIMEOUT, and the context keeps working."""
 
 from __future__ import annotations
@@ -18,10 +18,11 @@ def _lib():
     lib()
 
 
+@pytest.mark.parametrize("path", [spn.PATH_STREAM, spn.PATH_PACKED])
 @pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (256, 256)), (spn.SPN_ISING3D, (64, 16, 12))])
-def test_bounded_wait_runs_out_and_reports_timeout(model, dims):
+def test_bounded_wait_runs_out_and_reports_timeout(model, dims, path):
     lat = spn.Lattice(model, dims, 5)
-    lat.path = spn.PATH_STREAM
+    lat.path = path
     spn.load().spn_test_expire_next_waits(256)
     lat.sweep(0.44, 1)
     with pytest.raises(spn.SpnError) as e:
@@ -31,5 +32,5 @@ def test_bounded_wait_runs_out_and_reports_timeout(model, dims):
     # the context is still healthy: a fresh lattice matches the oracle bit for bit
     seed = inputs.unit_seed(61)
     s_o, e_o, m_o = oracle_run(dims, seed, [(0.3, 3)])
-    s_g, e_g, m_g = gpu_run(model, dims, seed, [(0.3, 3)], path=spn.PATH_STREAM)
+    s_g, e_g, m_g = gpu_run(model, dims, seed, [(0.3, 3)], path=path)
     assert np.array_equal(s_g, s_o) and np.array_equal(e_g, e_o) and np.array_equal(m_g, m_o)
