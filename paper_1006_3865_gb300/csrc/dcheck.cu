@@ -170,19 +170,7 @@ __global__ void __launch_bounds__(512) k_sweep_dc(const __grid_constant__ DcArgs
             pl[4 * call + 2] = P.z;
             pl[4 * call + 3] = P.w;
           }
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            uint32_t below = 0, equal = 0xffffffffu;
-#pragma unroll
-            for (int p = 4 * kDcFirstCalls - 1; p >= 0; --p) {
-              const uint32_t tm = a.tm[k][p];
-              const uint32_t nu = ~pl[p];
-              below = (nu & tm) | (nu & below) | (tm & below);
-              equal &= ~(pl[p] ^ tm);
-            }
-            acc |= eq[k] & below;
-            eq[k] &= equal;
-          }
+          compare_top<NC, 4 * kDcFirstCalls>(acc, eq, pl, a.tm);
         }
         uint32_t pend = 0;
 #pragma unroll

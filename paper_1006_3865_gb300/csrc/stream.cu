@@ -307,21 +307,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
           pl[4 * call + 2] = P.z;
           pl[4 * call + 3] = P.w;
         }
-        // u < t on the top planes, least significant plane first:
-        // below' = maj(~u_p, t_p, below), equal &= (u_p == t_p)
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          uint32_t below = 0, equal = 0xffffffffu;
-#pragma unroll
-          for (int p = 4 * kFirstCalls - 1; p >= 0; --p) {
-            const uint32_t tm = a.tm[k][p];
-            const uint32_t nu = ~pl[p];
-            below = (nu & tm) | (nu & below) | (tm & below);
-            equal &= ~(pl[p] ^ tm);
-          }
-          acc |= eq[k] & below;
-          eq[k] &= equal;
-        }
+        compare_top<NC, 4 * kFirstCalls>(acc, eq, pl, a.tm);
       }
       uint32_t pend = 0;
 #pragma unroll

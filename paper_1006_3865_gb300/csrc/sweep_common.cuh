@@ -141,6 +141,33 @@ __device__ __forceinline__ uint32_t decide_tail(uint32_t (&eq)[NC], const DevThr
   return acc;
 }
 
+// u < t on the top NP bit planes for all 32 sites of a word at once, with t
+// the threshold of each site's own class (the class masks eq[k] are disjoint,
+// so one selected threshold plane serves every class).  Least significant
+// plane first: below' = maj(~u_p, t_p, below); equal keeps the sites whose NP
+// bits all match.  tm[k][p] is 0 / ~0 for bit 31 - p of class k's threshold.
+// The sites found below join acc; eq keeps only the sites still tied.
+template <int NC, int NP>
+__device__ __forceinline__ void compare_top(uint32_t& acc, uint32_t (&eq)[NC], const uint32_t (&pl)[NP],
+                                            const uint32_t (*tm)[32]) {
+  uint32_t below = 0, equal = 0xffffffffu;
+#pragma unroll
+  for (int p = NP - 1; p >= 0; --p) {
+    uint32_t t = tm[0][p];
+#pragma unroll
+    for (int k = 1; k < NC; ++k) t = (eq[k] & tm[k][p]) | (~eq[k] & t);
+    const uint32_t nu = ~pl[p];
+    below = (nu & t) | (nu & below) | (t & below);
+    equal &= ~(pl[p] ^ t);
+  }
+  uint32_t any = 0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) any |= eq[k];
+  acc |= any & below;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) eq[k] &= equal;
+}
+
 // Classes of one 32-site word from the anti-aligned counts k = s0 + 2 s1 + 4 s2
 // out of 2*ND neighbours: cls[q-1] = sites with dE = 4q > 0; returns the sites
 // with dE <= 0 (always accepted).
