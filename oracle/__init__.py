@@ -76,12 +76,14 @@ def lib():
             L.orc_sweeps_dc.restype = cint
             L.orc_msc_u.argtypes = [u64, u32, u32, cint, u64]
             L.orc_msc_u.restype = u32
-            L.orc_ea_init_hot.argtypes = [vp, cint, u64, u32, vp]
+            L.orc_ea_init_hot.argtypes = [cint, vp, cint, u64, u32, vp]
             L.orc_ea_init_hot.restype = cint
-            L.orc_ea_observables.argtypes = [vp, cint, vp, vp, vp, vp]
+            L.orc_ea_observables.argtypes = [cint, vp, cint, vp, vp, vp, vp]
             L.orc_ea_observables.restype = cint
-            L.orc_ea_sweeps.argtypes = [vp, cint, vp, vp, vp, vp, vp, u64, u32, u32, i64, cint, vp]
+            L.orc_ea_sweeps.argtypes = [cint, vp, cint, vp, vp, vp, vp, vp, u64, u32, u32, i64, cint, vp]
             L.orc_ea_sweeps.restype = cint
+            L.orc_ea_overlap.argtypes = [cint, vp, cint, vp, vp, vp]
+            L.orc_ea_overlap.restype = cint
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = cint
             _lib = L
@@ -208,7 +210,7 @@ def ea_init_hot(dims, nsamples: int, seed: int, stream0: int = 0) -> np.ndarray:
     d = _dims(dims)
     N = int(np.prod(d))
     sp = np.zeros((nsamples, N), dtype=np.uint32)
-    _check(lib().orc_ea_init_hot(_p(d), nsamples, seed, stream0, _p(sp)), "ea_init_hot")
+    _check(lib().orc_ea_init_hot(len(d), _p(d), nsamples, seed, stream0, _p(sp)), "ea_init_hot")
     return sp
 
 
@@ -219,7 +221,7 @@ def ea_observables(dims, words: np.ndarray, bonds: np.ndarray):
     ns = w.shape[0]
     E = np.zeros((ns, 32), np.int64)
     M = np.zeros((ns, 32), np.int64)
-    _check(lib().orc_ea_observables(_p(d), ns, _p(w), _p(_bonds(bonds)), _p(E), _p(M)), "ea_observables")
+    _check(lib().orc_ea_observables(len(d), _p(d), ns, _p(w), _p(_bonds(bonds)), _p(E), _p(M)), "ea_observables")
     return E, M
 
 
@@ -236,6 +238,28 @@ def ea_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, temp_of_slot: n
         raise ValueError("ea_sweeps: 32 betas required")
     if acc is not None and (acc.dtype != np.int64 or not acc.flags.c_contiguous):
         raise TypeError("acc must be contiguous int64")
-    _check(lib().orc_ea_sweeps(_p(d), words.shape[0], _p(words), _p(_bonds(bonds)), _p(be), _p(temp_of_slot),
+    _check(lib().orc_ea_sweeps(len(d), _p(d), words.shape[0], _p(words), _p(_bonds(bonds)), _p(be), _p(temp_of_slot),
                                _p(slot_of_temp), seed, stream0, sweep0, int(nsweeps), int(exchange_every),
                                _p(acc)), "ea_sweeps")
+
+
+def ea_overlap(dims, words: np.ndarray, slot_of_temp: np.ndarray) -> np.ndarray:
+    """Overlaps q[p, t] = sum_n s_n^(2p)(t) s_n^(2p+1)(t) of the replica pairs
+    (samples 2p, 2p+1) at every temperature index t; shape [nsamples // 2, 32]."""
+    d = _dims(dims)
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    sot = np.ascontiguousarray(slot_of_temp, dtype=np.uint8)
+    if w.shape[0] % 2 or sot.shape != (w.shape[0], 32):
+        raise ValueError("ea_overlap: an even number of samples and [nsamples, 32] slot maps")
+    q = np.zeros((w.shape[0] // 2, 32), np.int64)
+    _check(lib().orc_ea_overlap(len(d), _p(d), w.shape[0] // 2, _p(w), _p(sot), _p(q)), "ea_overlap")
+    return q
+
+
+def binder(q2: np.ndarray, q4: np.ndarray) -> np.ndarray:
+    """Binder cumulant of the overlap per temperature, g = (3 - [<q^4>] / [<q^2>]^2) / 2,
+    from per-pair thermal moments <q^2>, <q^4> (shape [pairs, T]); [.] is the
+    average over pairs (disorder realisations)."""
+    m2 = np.mean(np.asarray(q2, dtype=np.float64), axis=0)
+    m4 = np.mean(np.asarray(q4, dtype=np.float64), axis=0)
+    return 0.5 * (3.0 - m4 / (m2 * m2))

@@ -52,7 +52,8 @@
  *   sweep t   colour 0, then colour 1; a site of colour c flips iff dE <= 0 or
  *             u < thr(beta, dE); E and M are updated by every accepted flip.
  *
- * Multi-spin coded EA (Sec. 4, "asynchronous multi-spin coding"):
+ * Multi-spin coded EA (Sec. 4, "asynchronous multi-spin coding"), on the
+ *   square (nd = 2) or simple cubic (nd = 3) lattice:
  *   one uint32 per (sample, site); bit j is the replica held in temperature slot
  *   j (1 <=> spin -1).  All 32 replicas of a sample share the site's u (purpose
  *   3 words, stream = sample).  Slot j
@@ -372,9 +373,9 @@ int orc_sweeps_dc(int nd, const int64_t* L, int8_t* s, const int64_t* T, int hit
 /* Replica bit j of a site word, as a spin +-1. */
 static int rep_spin(uint32_t w, int j) { return ((w >> j) & 1) ? -1 : 1; }
 
-int orc_ea_init_hot(const int64_t* L, int nsamples, uint64_t seed, uint32_t stream0, uint32_t* sp) {
+int orc_ea_init_hot(int nd, const int64_t* L, int nsamples, uint64_t seed, uint32_t stream0, uint32_t* sp) {
   lat_t g;
-  if (lat_make(&g, 3, L)) return -1;
+  if (lat_make(&g, nd, L)) return -1;
   for (int i = 0; i < nsamples; ++i)
     for (int64_t n = 0; n < g.N; ++n)
       sp[(int64_t)i * g.N + n] = orc_hot_word(seed, stream0 + (uint32_t)i, lat_colour(&g, n), lat_key(&g, n));
@@ -383,19 +384,19 @@ int orc_ea_init_hot(const int64_t* L, int nsamples, uint64_t seed, uint32_t stre
 
 /* Energy and magnetisation of every replica of every sample, indexed by slot:
  * E[i*32 + j], M[i*32 + j]. */
-int orc_ea_observables(const int64_t* L, int nsamples, const uint32_t* sp, const uint64_t* bonds,
+int orc_ea_observables(int nd, const int64_t* L, int nsamples, const uint32_t* sp, const uint64_t* bonds,
                        int64_t* E, int64_t* M) {
   lat_t g;
-  if (lat_make(&g, 3, L)) return -1;
+  if (lat_make(&g, nd, L)) return -1;
   for (int i = 0; i < nsamples; ++i) {
     const uint32_t* w = sp + (int64_t)i * g.N;
-    const uint64_t* J = bonds + (int64_t)i * 3 * g.nw;
+    const uint64_t* J = bonds + (int64_t)i * nd * g.nw;
     for (int j = 0; j < 32; ++j) {
       int64_t e = 0, m = 0;
       for (int64_t n = 0; n < g.N; ++n) {
         int sn = rep_spin(w[n], j);
         m += sn;
-        for (int d = 0; d < 3; ++d) e -= (int64_t)bond_J(&g, J, n, d) * sn * rep_spin(w[lat_step(&g, n, d, +1)], j);
+        for (int d = 0; d < nd; ++d) e -= (int64_t)bond_J(&g, J, n, d) * sn * rep_spin(w[lat_step(&g, n, d, +1)], j);
       }
       E[i * 32 + j] = e;
       M[i * 32 + j] = m;
@@ -439,11 +440,11 @@ static void exchange_step(const double* betas, const int64_t* Eslot, uint8_t* sl
  * stream0 + i), from global sweep index sweep0, with replica exchange after every
  * exchange_every-th sweep (0 = never).  temp_of_slot / slot_of_temp: [sample][32],
  * in/out.  acc: [sample][32] exchange acceptance counters (may be NULL). */
-int orc_ea_sweeps(const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
+int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
                   uint8_t* temp_of_slot, uint8_t* slot_of_temp, uint64_t seed, uint32_t stream0,
                   uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
   lat_t g;
-  if (lat_make(&g, 3, L)) return -1;
+  if (lat_make(&g, nd, L)) return -1;
   uint64_t thr[32][4];
   for (int t = 0; t < 32; ++t)
     for (int k = 0; k < 4; ++k) thr[t][k] = orc_threshold(betas[t], 4 * k);
@@ -451,7 +452,7 @@ int orc_ea_sweeps(const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* 
   int64_t* Mslot = (int64_t*)malloc(sizeof(int64_t) * 32);
   for (int i = 0; i < nsamples; ++i) {
     uint32_t* w = sp + (int64_t)i * g.N;
-    const uint64_t* J = bonds + (int64_t)i * 3 * g.nw;
+    const uint64_t* J = bonds + (int64_t)i * nd * g.nw;
     uint8_t* pi = temp_of_slot + 32 * i;
     uint8_t* tau = slot_of_temp + 32 * i;
     uint32_t stream = stream0 + (uint32_t)i;
@@ -466,7 +467,7 @@ int orc_ea_sweeps(const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* 
           for (int j = 0; j < 32; ++j) {
             int sn = rep_spin(w[n], j);
             int h = 0;
-            for (int d = 0; d < 3; ++d) {
+            for (int d = 0; d < nd; ++d) {
               int64_t f = lat_step(&g, n, d, +1), b = lat_step(&g, n, d, -1);
               h += bond_J(&g, J, n, d) * rep_spin(w[f], j);
               h += bond_J(&g, J, b, d) * rep_spin(w[b], j);
@@ -480,13 +481,35 @@ int orc_ea_sweeps(const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* 
       }
       if (exchange_every > 0 && ((int64_t)sweep + 1) % exchange_every == 0) {
         uint32_t e = (uint32_t)(((int64_t)sweep + 1) / exchange_every - 1);
-        orc_ea_observables(L, 1, w, J, Eslot, Mslot);
+        orc_ea_observables(nd, L, 1, w, J, Eslot, Mslot);
         exchange_step(betas, Eslot, tau, pi, seed, stream, e, acc ? acc + 32 * i : NULL);
       }
     }
   }
   free(Eslot);
   free(Mslot);
+  return 0;
+}
+
+/* Spin-glass overlap of replica pairs (Sec. 4: many disorder realisations at
+ * once; two replicas of one realisation give its overlap): samples 2p and
+ * 2p + 1 are two replicas of pair p.  For every temperature index t,
+ * q[p*32 + t] = sum_n s_n^(2p)(t) s_n^(2p+1)(t), where s^(i)(t) is the replica of
+ * sample i held in slot slot_of_temp[i*32 + t].  A plain double loop. */
+int orc_ea_overlap(int nd, const int64_t* L, int npairs, const uint32_t* sp, const uint8_t* slot_of_temp,
+                   int64_t* q) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  for (int p = 0; p < npairs; ++p) {
+    const uint32_t* wa = sp + (int64_t)(2 * p) * g.N;
+    const uint32_t* wb = sp + (int64_t)(2 * p + 1) * g.N;
+    for (int t = 0; t < 32; ++t) {
+      const int ja = slot_of_temp[(2 * p) * 32 + t], jb = slot_of_temp[(2 * p + 1) * 32 + t];
+      int64_t sum = 0;
+      for (int64_t n = 0; n < g.N; ++n) sum += (int64_t)rep_spin(wa[n], ja) * rep_spin(wb[n], jb);
+      q[p * 32 + t] = sum;
+    }
+  }
   return 0;
 }
 
