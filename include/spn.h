@@ -61,7 +61,8 @@ enum spn_status {
 enum spn_model {
   SPN_ISING2D = 1,   /* square lattice, J = +1 (Eq. 1) */
   SPN_ISING3D = 2,   /* simple cubic, J = +1 (Sec. 4) */
-  SPN_EA3D_PMJ = 3   /* simple cubic, J = +-1 per bond (Sec. 4, spin glass) */
+  SPN_EA3D_PMJ = 3,  /* simple cubic, J = +-1 per bond (Sec. 4, spin glass) */
+  SPN_EA2D_PMJ = 4   /* square lattice, J = +-1 per bond (batches only: spn_create_batch) */
 };
 
 enum spn_init { SPN_INIT_HOT = 0, SPN_INIT_COLD = 1 };
@@ -235,12 +236,13 @@ int spn_multi_destroy(spn_multi m);
  * multi-spin coding; the exchange rule is Hukushima-Nemoto parallel tempering)
  * ---------------------------------------------------------------------- */
 
-/* Create a batch of nsamples 3D +-J samples (model must be SPN_EA3D_PMJ) of
- * extents dims, each holding 32 replicas at the 32 inverse temperatures betas
+/* Create a batch of nsamples +-J samples, simple cubic (SPN_EA3D_PMJ, dims
+ * int32[3]) or square (SPN_EA2D_PMJ, dims int32[2]), of extents dims, each
+ * holding 32 replicas at the 32 inverse temperatures betas
  * (nbeta = 32, non-increasing, i.e. ascending temperature, each >= 1e-6).
  * Replica j of sample i lives in bit j (its temperature slot) of the sample's
  * 32-bit site words; on the device two samples share one uint64 word (64
- * replicas per word).  couplings: bit-packed bonds [sample][3][ceil(N/64)]
+ * replicas per word).  couplings: bit-packed bonds [sample][d][ceil(N/64)], d = 3 or 2
  * (copied).  The replica bits start from the hot-start words of Philox stream
  * i; slot j starts at temperature j.  exchange_every = X > 0 exchanges the
  * temperature pairs (k, k+1), k = e mod 2, e mod 2 + 2, ..., after every X-th
@@ -268,6 +270,29 @@ int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count);
 
 /* Accepted exchanges of pair (k, k+1) per sample, [sample][32] (entry 31 = 0). */
 int spn_batch_exchange_counts(spn_handle h, int64_t* acc, size_t count);
+
+/* Spin-glass overlap of replica pairs (Sec. 4's many disorder realisations;
+ * two replicas of one realisation give its overlap).  Samples 2p and 2p+1 of
+ * the batch are the two replicas of pair p: the batch needs an even number of
+ * samples, and the couplings of 2p and 2p+1 must be identical (SPN_E_STATE
+ * otherwise).  Enqueues one measurement on the handle's stream (asynchronous,
+ * one kernel): for every pair p and temperature index t,
+ *   q = sum_n s_n^(2p)(t) s_n^(2p+1)(t),
+ * s^(i)(t) being the replica of sample i at temperature t; the device keeps q
+ * and adds q^2 and q^4 to per-(pair, t) sums. */
+int spn_batch_measure_overlap(spn_handle h);
+
+/* The measurements so far (synchronises).  count = nsamples / 2 * 32; any
+ * output may be NULL.  nmeas: measurements taken; q_last[p*32 + t]: q of the
+ * last one; q2_sum[p*32 + t]: sum of q^2 (exact, uint64); q4_sum[2*(p*32 + t)]
+ * and [2*(p*32 + t) + 1]: low and high 64 bits of the exact sum of q^4.  The
+ * Binder cumulant g(t) = (3 - [<q^4>] / [<q^2>]^2) / 2 follows from these
+ * (<.> = mean over measurements, [.] = mean over pairs). */
+int spn_batch_overlap(spn_handle h, int64_t* nmeas, int64_t* q_last, uint64_t* q2_sum, uint64_t* q4_sum,
+                      size_t count);
+
+/* Clear the overlap sums and the measurement count (synchronises). */
+int spn_batch_overlap_reset(spn_handle h);
 
 /* ------------------------------------------------------------------------
  * Served requests with continuous batching

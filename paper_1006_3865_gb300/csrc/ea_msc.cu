@@ -3,6 +3,7 @@
 // multi-spin coding; parallel tempering is the batched workload of this
 // library, with the standard pair-exchange rule of Hukushima and Nemoto).
 //
+// Square (2D, 4 bonds per site) and simple cubic (3D, 6 bonds) lattices.
 // Storage: a batch of S disorder samples, each with 32 replicas held in the
 // 32 temperature slots of one word per site.  In device memory two samples
 // share a 64-bit word (bits 0-31 sample 2p, bits 32-63 sample 2p+1), so each
@@ -11,10 +12,10 @@
 //
 // k_ea_resident: one CTA per sample keeps the sample's whole word lattice and
 // bonds in shared memory (colour-separated: even-x and odd-x words per row) for
-// all sweeps of a launch.  Per site: the six neighbour words XOR the bond masks
+// all sweeps of a launch.  Per site: the 2 ND neighbour words XOR the bond masks
 // give the unsatisfied bonds of all 32 replicas; a bit-sliced adder counts them;
-// replicas with dE = 12 - 4k > 0 accept iff u < thr(beta of their temperature,
-// dE).  The thresholds of one dE level grow with the temperature index, so the
+// replicas with dE = 4 (ND - k) > 0 accept iff u < thr(beta of their
+// temperature, dE).  The thresholds of one dE level grow with the temperature index, so the
 // accepting temperatures form a suffix: a 5-step search over the 32 sorted
 // thresholds gives its start and a 33-entry table, kept in step with the slot
 // permutation, turns it into the slot mask.  After every X-th sweep the CTA
@@ -57,6 +58,7 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
 __device__ __forceinline__ int ea_slot(int x, int row, int h) { return (row * 2 + (x & 1)) * h + (x >> 1); }
 
 // One sample (CTA) of a batch launch, or one served job of a multi-job launch.
+template <int ND>
 __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int N = a.N, h = a.Lx >> 1, nrow = a.Ly * a.Lz;
@@ -108,7 +110,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
       for (int m = tid; m < halfN; m += nth) {
         const uint32_t row = fdiv((uint32_t)m, a.div_h);
         const int k = m - (int)row * h;
-        const uint32_t z = fdiv(row, a.div_ly);
+        const uint32_t z = ND == 3 ? fdiv(row, a.div_ly) : 0u;
         const int y = (int)row - (int)z * a.Ly;
         const int par = (c ^ (y + (int)z)) & 1;
         const int x = 2 * k + par;
@@ -119,19 +121,21 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
         const int xm = x == 0 ? a.Lx - 1 : x - 1, xp = x + 1 == a.Lx ? 0 : x + 1;
         const int rym = y == 0 ? (int)row + a.Ly - 1 : (int)row - 1;
         const int ryp = y + 1 == a.Ly ? (int)row - a.Ly + 1 : (int)row + 1;
-        const int rzm = z == 0 ? (int)row + nrow - a.Ly : (int)row - a.Ly;
-        const int rzp = (int)z + 1 == a.Lz ? (int)row - nrow + a.Ly : (int)row + a.Ly;
         const uint32_t nxp = sp[ea_slot(xp, (int)row, h)], nxm = sp[ea_slot(xm, (int)row, h)];
         const uint32_t nyp = sp[ea_slot(x, ryp, h)], nym = sp[ea_slot(x, rym, h)];
-        const uint32_t nzp = sp[ea_slot(x, rzp, h)], nzm = sp[ea_slot(x, rzm, h)];
         // bond masks: bits 0..2 forward, 3..5 backward
         const uint32_t ux = s ^ nxp ^ (0u - (bits & 1u));
         const uint32_t uy = s ^ nyp ^ (0u - ((bits >> 1) & 1u));
-        const uint32_t uz = s ^ nzp ^ (0u - ((bits >> 2) & 1u));
         const uint32_t vx = s ^ nxm ^ (0u - ((bits >> 3) & 1u));
         const uint32_t vy = s ^ nym ^ (0u - ((bits >> 4) & 1u));
-        const uint32_t vz = s ^ nzm ^ (0u - ((bits >> 5) & 1u));
-        // bit-sliced count of unsatisfied bonds k = s0 + 2 s1 + 4 s2 (0..6)
+        uint32_t uz = 0, vz = 0;
+        if constexpr (ND == 3) {
+          const int rzm = z == 0 ? (int)row + nrow - a.Ly : (int)row - a.Ly;
+          const int rzp = (int)z + 1 == a.Lz ? (int)row - nrow + a.Ly : (int)row + a.Ly;
+          uz = s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u));
+          vz = s ^ sp[ea_slot(x, rzm, h)] ^ (0u - ((bits >> 5) & 1u));
+        }
+        // bit-sliced count of unsatisfied bonds k = s0 + 2 s1 + 4 s2 (0..2 ND)
         const uint32_t x1 = ux ^ uy ^ uz, y1 = (ux & uy) | (uz & (ux ^ uy));
         const uint32_t x2 = vx ^ vy ^ vz, y2 = (vx & vy) | (vz & (vx ^ vy));
         const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
@@ -140,9 +144,9 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
         const U4 P = philox10((uint32_t)m >> 2, sweep, (uint32_t)c | (3u << 1), (uint32_t)sample, a.K);
         const uint32_t u = u4_word(P, m & 3);
         // accepting temperatures per level: count thresholds <= u (sorted), suffix mask
-        uint32_t A[3];
+        uint32_t A[ND];
 #pragma unroll
-        for (int lv = 0; lv < 3; ++lv) {
+        for (int lv = 0; lv < ND; ++lv) {
           const uint32_t* tl = thr + 32 * lv;
           int cnt = 0;
           cnt += (tl[cnt + 15] <= u) ? 16 : 0;
@@ -153,10 +157,14 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
           cnt += (cnt == 31 && tl[31] <= u) ? 1 : 0;  // all 32 thresholds <= u
           A[lv] = suffix[cnt];
         }
-        // k >= 3: dE <= 0; k = 2: dE = 4 (level 0); k = 1: 8 (level 1); k = 0: 12 (level 2)
-        const uint32_t always = s2 | (s0 & s1);
+        // dE = 4 (ND - k): k >= ND accepts always; k = ND - 1 - lv takes level lv (dE = 4 (lv + 1))
         const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
-        const uint32_t acc = always | (k2 & A[0]) | (k1 & A[1]) | (k0 & A[2]);
+        uint32_t acc;
+        if constexpr (ND == 3) {
+          acc = (s2 | (s0 & s1)) | (k2 & A[0]) | (k1 & A[1]) | (k0 & A[2]);
+        } else {
+          acc = (s1 | s2) | (k1 & A[0]) | (k0 & A[1]);
+        }
         sp[q] = s ^ acc;
       }
       __syncthreads();
@@ -176,12 +184,15 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
         const uint32_t bits = bb[q];
         const int xp = x + 1 == a.Lx ? 0 : x + 1;
         const int ryp = y + 1 == a.Ly ? r - a.Ly + 1 : r + 1;
-        const int rzp = z + 1 == a.Lz ? r - nrow + a.Ly : r + a.Ly;
-        const uint32_t w3[3] = {s ^ sp[ea_slot(xp, r, h)] ^ (0u - (bits & 1u)),
-                                s ^ sp[ea_slot(x, ryp, h)] ^ (0u - ((bits >> 1) & 1u)),
-                                s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u))};
+        uint32_t w3[ND];
+        w3[0] = s ^ sp[ea_slot(xp, r, h)] ^ (0u - (bits & 1u));
+        w3[1] = s ^ sp[ea_slot(x, ryp, h)] ^ (0u - ((bits >> 1) & 1u));
+        if constexpr (ND == 3) {
+          const int rzp = z + 1 == a.Lz ? r - nrow + a.Ly : r + a.Ly;
+          w3[2] = s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u));
+        }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
+        for (int d = 0; d < ND; ++d) {
           uint32_t carry = w3[d];
 #pragma unroll
           for (int b = 0; b < 8; ++b) {
@@ -191,7 +202,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
           }
         }
       }
-      // per-replica totals (at most 255 per thread: 3 bonds x 85 sites per thread at most)
+      // per-replica totals (at most 255 per thread: ND bonds x at most 46 sites per thread)
       for (int j = 0; j < 32; ++j) {
         uint32_t v = 0;
 #pragma unroll
@@ -256,10 +267,14 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) { ea_run(a, blockIdx.x); }
+template <int ND>
+__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) { ea_run<ND>(a, blockIdx.x); }
 
 // Served jobs of one lattice size, one single-sample job per CTA.
-__global__ void __launch_bounds__(1024) k_ea_jobs(const EaArgs* __restrict__ list) { ea_run(list[blockIdx.x], 0); }
+template <int ND>
+__global__ void __launch_bounds__(1024) k_ea_jobs(const EaArgs* __restrict__ list) {
+  ea_run<ND>(list[blockIdx.x], 0);
+}
 
 // hot start: the replica bits of site n are its 32-bit hot-start word, bit
 // 31 - q = bit (m & 31) of plane q = word q & 3 of R(8 (m >> 5) + q / 4, 0, c | 1 << 1, sample)
@@ -284,8 +299,8 @@ __global__ void k_ea_init(uint64_t* words, int Lx, int Ly, int N, int nsamples, 
   }
 }
 
-// per-replica E and M by slot: E = 2 U - 3N (U unsatisfied forward bonds), M = N - 2 (#spins -1)
-__global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, int Lx, int Ly, int Lz, int N,
+// per-replica E and M by slot: E = 2 U - nd N (U unsatisfied forward bonds), M = N - 2 (#spins -1)
+__global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, int nd, int Lx, int Ly, int Lz, int N,
                                  long long* E, long long* M) {
   __shared__ unsigned long long su[32], sm[32];
   const int sample = blockIdx.x, tid = threadIdx.x;
@@ -300,7 +315,7 @@ __global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, in
                        n + ((z + 1 == Lz ? 0 : z + 1) - z) * Lx * Ly};
     for (int j = 0; j < 32; ++j) {
       unsigned long long un = 0;
-      for (int d = 0; d < 3; ++d) {
+      for (int d = 0; d < nd; ++d) {
         const uint32_t bit = ((s ^ w[2 * (size_t)np[d]]) >> j) & 1u;
         un += bit ^ ((bb[n] >> d) & 1u);
       }
@@ -310,8 +325,68 @@ __global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, in
   }
   __syncthreads();
   if (tid < 32) {
-    E[sample * 32 + tid] = 2 * (long long)su[tid] - 3 * (long long)N;
+    E[sample * 32 + tid] = 2 * (long long)su[tid] - (long long)nd * N;
     M[sample * 32 + tid] = (long long)N - 2 * (long long)sm[tid];
+  }
+}
+
+// 32 x 32 bit matrix across a warp: lane r holds row r on entry, column r
+// (bit i = element (i, r)) on return.  Stage j swaps the off-diagonal j x j
+// blocks between lanes r and r ^ j.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
+  const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0, j = 16; k < 5; ++k, j >>= 1) {
+    const uint32_t m = masks[k];
+    const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+    v = (lane & j) ? (((o >> j) & m) | (v & ~m)) : ((v & m) | ((o << j) & ~m));
+  }
+  return v;
+}
+
+// Overlap of replica pair p (samples 2p and 2p+1 share the 64-bit words of
+// pair p): q(t) = N - 2 D(t), D(t) = sites where the two replicas at
+// temperature t differ.  A warp takes 32 sites at a time, transposes both
+// halves so that lane j holds slot j's bits of the 32 sites, and lane t counts
+// the differing bits of the slots its temperature occupies in the two samples.
+// q, q^2 and q^4 (128-bit) are accumulated per (pair, t).  One CTA per pair.
+__global__ void __launch_bounds__(256) k_ea_overlap(const uint64_t* __restrict__ words,
+                                                    const uint8_t* __restrict__ temp_of_slot, int N,
+                                                    long long* q_last, unsigned long long* q2_sum,
+                                                    unsigned long long* q4_sum) {
+  __shared__ int sa[32], sb[32];
+  __shared__ unsigned int D[32];
+  const int p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  if (tid < 32) {
+    sa[temp_of_slot[(2 * p) * 32 + tid]] = tid;  // slot of each temperature, sample 2p
+    sb[temp_of_slot[(2 * p + 1) * 32 + tid]] = tid;
+    D[tid] = 0;
+  }
+  __syncthreads();
+  const int ja = sa[lane], jb = sb[lane];  // lane t: the slots of temperature t
+  const uint64_t* w = words + (size_t)p * N;
+  unsigned int d = 0;
+  for (int base = warp * 32; base < N; base += nwarp * 32) {
+    const int n = base + lane;
+    const uint64_t v = n < N ? w[n] : 0ull;  // absent sites agree
+    const uint32_t pa = warp_transpose32((uint32_t)v, lane);
+    const uint32_t pb = warp_transpose32((uint32_t)(v >> 32), lane);
+    const uint32_t xa = __shfl_sync(0xffffffffu, pa, ja);
+    const uint32_t xb = __shfl_sync(0xffffffffu, pb, jb);
+    d += (unsigned int)__popc(xa ^ xb);
+  }
+  atomicAdd(&D[lane], d);
+  __syncthreads();
+  if (tid < 32) {
+    const size_t i = (size_t)p * 32 + tid;
+    const long long q = (long long)N - 2 * (long long)D[tid];
+    const unsigned long long q2 = (unsigned long long)(q * q);
+    q_last[i] = q;
+    q2_sum[i] += q2;
+    const unsigned long long lo = q2 * q2, hi = __umul64hi(q2, q2);
+    const unsigned long long s = q4_sum[2 * i] + lo;
+    q4_sum[2 * i + 1] += hi + (s < lo ? 1ull : 0ull);
+    q4_sum[2 * i] = s;
   }
 }
 
@@ -320,8 +395,14 @@ __global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, in
 // ---------------------------------------------------------------- the ABI
 
 struct EaBatch {
+  int nd;
   int L[3];
   int N, nsamples, exchange_every;
+  bool pairs_share_bonds = false;  // samples 2p, 2p+1 have identical couplings (replica pairs)
+  long long* d_qlast = nullptr;    // overlap measurement: [pairs][32] last q
+  unsigned long long* d_q2 = nullptr;  // [pairs][32] sum of q^2
+  unsigned long long* d_q4 = nullptr;  // [pairs][32][2] sum of q^4 (low, high 64 bits)
+  int64_t nmeas = 0;
   uint64_t seed;
   double betas[32];
   uint64_t* d_words = nullptr;
@@ -354,6 +435,9 @@ void spn_ea_free(EaBatch* b) {
   cudaFree(b->d_xacc);
   cudaFree(b->d_xtab);
   cudaFree(b->d_err);
+  cudaFree(b->d_qlast);
+  cudaFree(b->d_q2);
+  cudaFree(b->d_q4);
   delete b;
 }
 
@@ -372,10 +456,11 @@ int ea_window_args(spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* 
   return SPN_OK;
 }
 
-cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_ea_jobs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, size_t smem, cudaStream_t st) {
+  auto kern = nd == 2 ? k_ea_jobs<2> : k_ea_jobs<3>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_ea_jobs<<<n, threads, smem, st>>>(d_list);
+  kern<<<n, threads, smem, st>>>(d_list);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -388,13 +473,16 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
                      const double* betas, int nbeta, uint64_t seed, int exchange_every) {
   if (!out || !dims || !couplings || !betas) return ea_fail(SPN_E_ARG, "NULL argument");
   *out = nullptr;
-  if (model != SPN_EA3D_PMJ) return ea_fail(SPN_E_ARG, "batches are multi-spin coded SPN_EA3D_PMJ samples");
+  if (model != SPN_EA3D_PMJ && model != SPN_EA2D_PMJ)
+    return ea_fail(SPN_E_ARG, "batches are multi-spin coded SPN_EA3D_PMJ or SPN_EA2D_PMJ samples");
+  const int nd = model == SPN_EA2D_PMJ ? 2 : 3;
+  const int ext[3] = {dims[0], dims[1], nd == 3 ? dims[2] : 1};
   if (nsamples < 1) return ea_fail(SPN_E_ARG, "nsamples must be >= 1");
   if (nbeta != 32) return ea_fail(SPN_E_ARG, "the temperature ladder has exactly 32 betas (one per word bit)");
   if (exchange_every < 0) return ea_fail(SPN_E_ARG, "exchange_every must be >= 0");
-  for (int d = 0; d < 3; ++d)
-    if (dims[d] < 2 || (dims[d] & 1)) return ea_fail(SPN_E_ARG, "every extent must be even and >= 2");
-  const int64_t N = (int64_t)dims[0] * dims[1] * dims[2];
+  for (int d = 0; d < nd; ++d)
+    if (ext[d] < 2 || (ext[d] & 1)) return ea_fail(SPN_E_ARG, "every extent must be even and >= 2");
+  const int64_t N = (int64_t)ext[0] * ext[1] * ext[2];
   if (ea_smem((int)std::min<int64_t>(N, 1 << 30)) > 227 * 1024 || N > (1 << 20))
     return ea_fail(SPN_E_ARG, "a sample must fit in one CTA's shared memory (about 44,000 sites)");
   for (int t = 0; t < 32; ++t) {
@@ -405,7 +493,8 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   }
   EaBatch* b = new (std::nothrow) EaBatch;
   if (!b) return ea_fail(SPN_E_NOMEM, "host allocation failed");
-  for (int d = 0; d < 3; ++d) b->L[d] = dims[d];
+  b->nd = nd;
+  for (int d = 0; d < 3; ++d) b->L[d] = ext[d];
   b->N = (int)N;
   b->nsamples = nsamples;
   b->exchange_every = exchange_every;
@@ -422,19 +511,22 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   const uint64_t* J = static_cast<const uint64_t*>(couplings);
   for (int s = 0; s < nsamples; ++s) {
     for (int64_t n = 0; n < N; ++n) {
-      const int x = (int)(n % dims[0]), y = (int)((n / dims[0]) % dims[1]), z = (int)(n / ((int64_t)dims[0] * dims[1]));
-      const int64_t back[3] = {n - x + (x == 0 ? dims[0] - 1 : x - 1),
-                               n + (int64_t)((y == 0 ? dims[1] - 1 : y - 1) - y) * dims[0],
-                               n + (int64_t)((z == 0 ? dims[2] - 1 : z - 1) - z) * dims[0] * dims[1]};
+      const int x = (int)(n % ext[0]), y = (int)((n / ext[0]) % ext[1]), z = (int)(n / ((int64_t)ext[0] * ext[1]));
+      const int64_t back[3] = {n - x + (x == 0 ? ext[0] - 1 : x - 1),
+                               n + (int64_t)((y == 0 ? ext[1] - 1 : y - 1) - y) * ext[0],
+                               n + (int64_t)((z == 0 ? ext[2] - 1 : z - 1) - z) * ext[0] * ext[1]};
       uint8_t v = 0;
-      for (int d = 0; d < 3; ++d) {
-        const uint64_t* Jd = J + ((int64_t)s * 3 + d) * nw;
+      for (int d = 0; d < nd; ++d) {
+        const uint64_t* Jd = J + ((int64_t)s * nd + d) * nw;
         if ((Jd[n >> 6] >> (n & 63)) & 1) v |= (uint8_t)(1u << d);
         if ((Jd[back[d] >> 6] >> (back[d] & 63)) & 1) v |= (uint8_t)(8u << d);
       }
       bb[(size_t)s * N + n] = v;
     }
   }
+  b->pairs_share_bonds = nsamples % 2 == 0;
+  for (int p = 0; b->pairs_share_bonds && p < nsamples / 2; ++p)
+    b->pairs_share_bonds = std::memcmp(&bb[(size_t)(2 * p) * N], &bb[(size_t)(2 * p + 1) * N], (size_t)N) == 0;
   // exchange tables: pair k, d = 1 .. len: floor(exp((b_k - b_k+1) * (-2d)) 2^32)
   std::vector<uint32_t> tab;
   spn::EaArgs& A = b->args;
@@ -481,7 +573,7 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
     return bail(SPN_E_CUDA, "copying the batch to the device");
   const spn::PhiloxKeys K = spn::philox_keys(seed);
   spn::k_ea_init<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsamples * N / 256 + 1, spn::device_sm_count() * 32)), 256>>>(
-      b->d_words, dims[0], dims[1], (int)N, nsamples, K);
+      b->d_words, ext[0], ext[1], (int)N, nsamples, K);
   spn::count_launches(1);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(SPN_E_CUDA, cudaGetErrorString(e));
   A.words = b->d_words;
@@ -489,12 +581,13 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   A.temp_of_slot = b->d_tos;
   A.xacc = b->d_xacc;
   A.xtab = b->d_xtab;
-  A.Lx = dims[0];
-  A.Ly = dims[1];
-  A.Lz = dims[2];
+  A.nd = nd;
+  A.Lx = ext[0];
+  A.Ly = ext[1];
+  A.Lz = ext[2];
   A.N = (int)N;
-  A.div_h = spn::fastdiv((uint32_t)(dims[0] / 2));
-  A.div_ly = spn::fastdiv((uint32_t)dims[1]);
+  A.div_h = spn::fastdiv((uint32_t)(ext[0] / 2));
+  A.div_ly = spn::fastdiv((uint32_t)ext[1]);
   A.exchange_every = exchange_every;
   A.nsamples = nsamples;
   A.K = K;
@@ -515,14 +608,15 @@ int spn_batch_sweep(spn_handle h, int64_t nsweeps) {
   if (nsweeps < 0) return ea_fail(SPN_E_ARG, "nsweeps must be >= 0");
   EaBatch* b = h->ea;
   if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return ea_fail(SPN_E_ARG, "sweep counter would exceed 2^32");
-  cudaFuncSetAttribute(spn::k_ea_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  auto kern = b->nd == 2 ? spn::k_ea_resident<2> : spn::k_ea_resident<3>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   int64_t done = 0;
   while (done < nsweeps) {  // bounded launches keep each kernel well under a second
     const int n = (int)std::min<int64_t>(nsweeps - done, 2000);
     spn::EaArgs a = b->args;
     a.sweep0 = (uint32_t)(h->sweeps + done);
     a.nsweeps = n;
-    spn::k_ea_resident<<<b->nsamples, b->threads, b->smem, h->st>>>(a);
+    kern<<<b->nsamples, b->threads, b->smem, h->st>>>(a);
     spn::count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ea_fail(SPN_E_CUDA, cudaGetErrorString(e));
@@ -597,7 +691,7 @@ int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count) {
     cudaFree(dE);
     return ea_fail(SPN_E_NOMEM, "cudaMalloc");
   }
-  spn::k_ea_observables<<<b->nsamples, 256, 0, h->st>>>(b->d_words, b->d_bonds, b->L[0], b->L[1], b->L[2], b->N, dE,
+  spn::k_ea_observables<<<b->nsamples, 256, 0, h->st>>>(b->d_words, b->d_bonds, b->nd, b->L[0], b->L[1], b->L[2], b->N, dE,
                                                        dM);
   spn::count_launches(1);
   cudaError_t e = cudaStreamSynchronize(h->st);
@@ -614,6 +708,63 @@ int spn_batch_exchange_counts(spn_handle h, int64_t* acc, size_t count) {
   if (cudaStreamSynchronize(h->st) != cudaSuccess ||
       cudaMemcpy(acc, h->ea->d_xacc, count * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return ea_fail(SPN_E_CUDA, "reading the exchange counts");
+  return SPN_OK;
+}
+
+int spn_batch_measure_overlap(spn_handle h) {
+  if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
+  EaBatch* b = h->ea;
+  if (!b->pairs_share_bonds)
+    return ea_fail(SPN_E_STATE, "overlaps need an even number of samples with samples 2p, 2p+1 sharing couplings");
+  const size_t n = (size_t)b->nsamples / 2 * 32;
+  if (!b->d_qlast) {
+    if (cudaMalloc(&b->d_qlast, n * 8) != cudaSuccess || cudaMalloc(&b->d_q2, n * 8) != cudaSuccess ||
+        cudaMalloc(&b->d_q4, n * 16) != cudaSuccess)
+      return ea_fail(SPN_E_NOMEM, "cudaMalloc(overlap)");
+    if (cudaMemsetAsync(b->d_qlast, 0, n * 8, h->st) != cudaSuccess ||
+        cudaMemsetAsync(b->d_q2, 0, n * 8, h->st) != cudaSuccess ||
+        cudaMemsetAsync(b->d_q4, 0, n * 16, h->st) != cudaSuccess)
+      return ea_fail(SPN_E_CUDA, "clearing the overlap sums");
+  }
+  spn::k_ea_overlap<<<b->nsamples / 2, 256, 0, h->st>>>(b->d_words, b->d_tos, b->N, b->d_qlast, b->d_q2, b->d_q4);
+  spn::count_launches(1);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ea_fail(SPN_E_CUDA, cudaGetErrorString(e));
+  b->nmeas += 1;
+  return SPN_OK;
+}
+
+int spn_batch_overlap(spn_handle h, int64_t* nmeas, int64_t* q_last, uint64_t* q2_sum, uint64_t* q4_sum,
+                      size_t count) {
+  if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
+  EaBatch* b = h->ea;
+  if (count != (size_t)b->nsamples / 2 * 32) return ea_fail(SPN_E_ARG, "count must be nsamples / 2 * 32");
+  if (nmeas) *nmeas = b->nmeas;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return ea_fail(SPN_E_CUDA, "synchronising");
+  if (!b->d_qlast) {  // nothing measured yet
+    if (q_last) std::memset(q_last, 0, count * 8);
+    if (q2_sum) std::memset(q2_sum, 0, count * 8);
+    if (q4_sum) std::memset(q4_sum, 0, count * 16);
+    return SPN_OK;
+  }
+  if ((q_last && cudaMemcpy(q_last, b->d_qlast, count * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (q2_sum && cudaMemcpy(q2_sum, b->d_q2, count * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (q4_sum && cudaMemcpy(q4_sum, b->d_q4, count * 16, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return ea_fail(SPN_E_CUDA, "reading the overlaps");
+  return SPN_OK;
+}
+
+int spn_batch_overlap_reset(spn_handle h) {
+  if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
+  EaBatch* b = h->ea;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return ea_fail(SPN_E_CUDA, "synchronising");
+  b->nmeas = 0;
+  if (b->d_qlast) {
+    const size_t n = (size_t)b->nsamples / 2 * 32;
+    if (cudaMemset(b->d_qlast, 0, n * 8) != cudaSuccess || cudaMemset(b->d_q2, 0, n * 8) != cudaSuccess ||
+        cudaMemset(b->d_q4, 0, n * 16) != cudaSuccess)
+      return ea_fail(SPN_E_CUDA, "clearing the overlap sums");
+  }
   return SPN_OK;
 }
 

@@ -334,7 +334,7 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
         std::tie(first, count, threads, smem) = el[gi];
         cudaStream_t st = s->pool[(s->pool.size() - 1 - gi % s->pool.size())];
         cudaStreamWaitEvent(st, s->fork, 0);
-        if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, threads, smem, st)) != cudaSuccess)
+        if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, 3, threads, smem, st)) != cudaSuccess)
           return SPN_E_CUDA;
       }
     }

@@ -127,6 +127,7 @@ struct EaArgs {
   int xlen[32];               // its length (d = 1 .. xlen), 0 with xalways[k]
   uint32_t xalways;           // bit k: pair k has equal betas (always accept)
   uint32_t thr[3][32];        // thr[q-1][t] for dE = 4q, non-decreasing in t
+  int nd;                     // 2: square lattice (Lz = 1), 3: simple cubic
   int Lx, Ly, Lz, N;
   FastDiv div_h, div_ly;      // by Lx / 2 and by Ly
   uint32_t sweep0;
@@ -141,7 +142,7 @@ struct EaArgs {
 // parameter block of the next `nsweeps` sweeps of h (its sweep counter
 // advances), and one launch running many such blocks, one CTA each.
 int ea_window_args(struct spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* threads);
-cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, size_t smem, cudaStream_t st);
 
 }  // namespace spn
 

@@ -30,6 +30,7 @@ SPN_E_NOTFOUND = -7
 SPN_ISING2D = 1
 SPN_ISING3D = 2
 SPN_EA3D_PMJ = 3
+SPN_EA2D_PMJ = 4
 
 SPN_INIT_HOT = 0
 SPN_INIT_COLD = 1
@@ -94,6 +95,9 @@ _SIGNATURES = {
     "spn_batch_set_slots": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_energies": (_c.c_int, [_vp, _vp, _vp, _sz]),
     "spn_batch_exchange_counts": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_batch_measure_overlap": (_c.c_int, [_vp]),
+    "spn_batch_overlap": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _sz]),
+    "spn_batch_overlap_reset": (_c.c_int, [_vp]),
 }
 
 
@@ -304,7 +308,8 @@ class EABatch:
         b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
         d = _dims(dims)
         h = _vp()
-        _check(self._lib.spn_create_batch(_c.byref(h), SPN_EA3D_PMJ, _ptr(d), self.nsamples, _ptr(J), _ptr(b),
+        model = SPN_EA2D_PMJ if len(self.dims) == 2 else SPN_EA3D_PMJ
+        _check(self._lib.spn_create_batch(_c.byref(h), model, _ptr(d), self.nsamples, _ptr(J), _ptr(b),
                                           int(b.size), seed, int(exchange_every)))
         self._h = h
 
@@ -339,6 +344,34 @@ class EABatch:
         out = np.empty((self.nsamples, 32), np.int64)
         _check(self._lib.spn_batch_exchange_counts(self._h, _ptr(out), out.size))
         return out
+
+    def measure_overlap(self):
+        """Enqueue one overlap measurement of the replica pairs (samples 2p, 2p+1)."""
+        _check(self._lib.spn_batch_measure_overlap(self._h))
+
+    def overlap(self) -> dict:
+        """The overlap measurements so far: nmeas, the last q [pairs, 32], the
+        exact integer sums of q^2 and q^4 (Python ints, [pairs][32]), the
+        moments <q^2>, <q^4> per pair and temperature, and the Binder cumulant
+        per temperature g = (3 - [<q^4>] / [<q^2>]^2) / 2 over the pairs."""
+        P = self.nsamples // 2
+        n = _c.c_int64()
+        q = np.empty((P, 32), np.int64)
+        q2 = np.empty((P, 32), np.uint64)
+        q4 = np.empty((P, 32, 2), np.uint64)
+        _check(self._lib.spn_batch_overlap(self._h, _c.byref(n), _ptr(q), _ptr(q2), _ptr(q4), P * 32))
+        s2 = [[int(q2[p, t]) for t in range(32)] for p in range(P)]
+        s4 = [[int(q4[p, t, 0]) | (int(q4[p, t, 1]) << 64) for t in range(32)] for p in range(P)]
+        out = {"nmeas": int(n.value), "q_last": q, "q2_sum": s2, "q4_sum": s4}
+        if n.value > 0:
+            m2 = np.array([[x / n.value for x in row] for row in s2])
+            m4 = np.array([[x / n.value for x in row] for row in s4])
+            out["q2"], out["q4"] = m2, m4
+            out["binder"] = 0.5 * (3.0 - m4.mean(axis=0) / m2.mean(axis=0) ** 2)
+        return out
+
+    def overlap_reset(self):
+        _check(self._lib.spn_batch_overlap_reset(self._h))
 
     def set_stream(self, stream):
         _check(self._lib.spn_set_stream(self._h, _stream_ptr(stream)))
