@@ -66,7 +66,8 @@ def _args():
     p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d"], default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
-    p.add_argument("--forms", default="batched,ea,served,dc,packed",
+    p.add_argument("--profile-L", type=int, default=0, help="lattice extent of a 2d / packed2d profile case")
+    p.add_argument("--forms", default="batched,ea,served,dc,packed,overlap",
                    help="extra forms measured after the plain step (comma list; empty for none)")
     p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
     p.add_argument("--ea-sweeps", type=int, default=EA_SWEEPS)
@@ -101,7 +102,8 @@ def run_profile_case(a):
         lat.close()
         return
     if a.profile_case in ("2d", "packed2d"):
-        lat = spn.Lattice(spn.SPN_ISING2D, (L2D, L2D), inputs.unit_seed(1))
+        L = a.profile_L or L2D
+        lat = spn.Lattice(spn.SPN_ISING2D, (L, L), inputs.unit_seed(1))
         beta = 1.0 / TEMPS_2D[1]
     else:
         lat = spn.Lattice(spn.SPN_ISING3D, (L3D, L3D, L3D), inputs.unit_seed(2))
@@ -434,6 +436,44 @@ def form_packed(stream):
             "workload": WORKLOAD + "; lattices stored at 1 bit per spin (bit-packed path)"}
 
 
+def form_overlap(stream, sweeps=2000, every=10):
+    """Replica-pair overlaps with parallel tempering: 2D +-J EA L = 128 and 3D
+    L = 32, 1024 samples each as 512 pairs of replicas sharing couplings, 32
+    temperatures, exchange every 10 sweeps; q measured on the device every 10
+    sweeps (q, q^2, q^4 sums per pair and temperature).  attempts/ns with the
+    measurements, without them, and the time of one measurement."""
+    import numpy as np
+
+    from paper_1006_3865_gb300 import inputs, spn
+
+    out = {}
+    for name, dims, ladder in (("2d_L128", (128, 128), (0.3, 3.0)), ("3d_L32", (EA_L, EA_L, EA_L), (0.2, 2.0))):
+        pairs = EA_SAMPLES // 2
+        bonds = np.repeat(inputs.ea_bonds(dims, pairs, inputs.unit_seed(0xE2)), 2, axis=0)
+        b = spn.EABatch(dims, bonds, inputs.geometric_ladder(*ladder), inputs.unit_seed(0xE3), exchange_every=EA_EVERY)
+        b.set_stream(stream)
+        b.sweep(every)
+        b.measure_overlap()
+
+        def with_meas():
+            for _ in range(sweeps // every):
+                b.sweep(every)
+                b.measure_overlap()
+
+        ms_meas = _timed(stream, with_meas)
+        ms_plain = _timed(stream, lambda: b.sweep(sweeps))
+        ms_one = _timed(stream, lambda: [b.measure_overlap() for _ in range(100)]) / 100
+        r = b.overlap()
+        b.close()
+        att = EA_SAMPLES * 32 * int(np.prod(dims)) * sweeps
+        out[name] = {"attempts_per_ns": att / (ms_meas * 1e6), "attempts_per_ns_no_measure": att / (ms_plain * 1e6),
+                     "measure_ms": ms_one, "measurements": r["nmeas"],
+                     "binder_lowest_T": float(r["binder"][0]), "binder_highest_T": float(r["binder"][31])}
+    return {"value": out["2d_L128"]["attempts_per_ns"], "unit": UNIT, "by_lattice": out,
+            "workload": f"+-J EA 2D L=128 and 3D L=32, {EA_SAMPLES // 2} replica pairs x 32 temperatures, "
+                        f"multi-spin coded, exchange every {EA_EVERY}, overlap every {every} sweeps, {sweeps} sweeps"}
+
+
 def run_forms(a, stream):
     out = {}
     for f in [x for x in a.forms.split(",") if x]:
@@ -447,6 +487,8 @@ def run_forms(a, stream):
             out["double_checkerboard"] = form_dc(stream)
         elif f == "packed":
             out["packed"] = form_packed(stream)
+        elif f == "overlap":
+            out["overlap"] = form_overlap(stream)
         else:
             raise SystemExit(f"unknown form {f}")
     return out
