@@ -84,6 +84,17 @@ def lib():
             L.orc_ea_sweeps.restype = cint
             L.orc_ea_overlap.argtypes = [cint, vp, cint, vp, vp, vp]
             L.orc_ea_overlap.restype = cint
+            flt = ctypes.c_float
+            L.orc_heis_exp.argtypes = [flt]
+            L.orc_heis_exp.restype = flt
+            L.orc_heis_proposal.argtypes = [u64, u32, u32, cint, cint, u64, vp]
+            L.orc_heis_proposal.restype = cint
+            L.orc_heis_init_hot.argtypes = [cint, vp, u64, u32, vp]
+            L.orc_heis_init_hot.restype = cint
+            L.orc_heis_observables.argtypes = [cint, vp, vp, vp, vp]
+            L.orc_heis_observables.restype = cint
+            L.orc_heis_sweeps.argtypes = [cint, vp, vp, dbl, u64, u32, u32, i64, vp, vp, vp, vp]
+            L.orc_heis_sweeps.restype = cint
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = cint
             _lib = L
@@ -263,3 +274,51 @@ def binder(q2: np.ndarray, q4: np.ndarray) -> np.ndarray:
     m2 = np.mean(np.asarray(q2, dtype=np.float64), axis=0)
     m4 = np.mean(np.asarray(q4, dtype=np.float64), axis=0)
     return 0.5 * (3.0 - m4 / (m2 * m2))
+
+
+# ---- Heisenberg spins (binary32 vectors, [N, 3])
+
+def heis_exp(x: float) -> np.float32:
+    """The deterministic binary32 exp of the Heisenberg acceptance (x <= 0)."""
+    return np.float32(lib().orc_heis_exp(float(np.float32(x))))
+
+
+def heis_proposal(seed: int, stream: int, t: int, colour: int, purpose: int, m: int):
+    """Marsaglia proposal of site key m (purpose 5: Metropolis, 7: hot start), or None."""
+    out = np.zeros(3, np.float32)
+    ok = lib().orc_heis_proposal(seed, stream, t, colour, purpose, m, _p(out))
+    return out if ok else None
+
+
+def heis_init_hot(dims, seed: int, stream: int = 0) -> np.ndarray:
+    d = _dims(dims)
+    S = np.zeros((int(np.prod(d)), 3), np.float32)
+    _check(lib().orc_heis_init_hot(len(d), _p(d), seed, stream, _p(S)), "heis_init_hot")
+    return S
+
+
+def heis_observables(dims, S: np.ndarray):
+    """(E, M[3]) in binary64, summed in site order."""
+    d = _dims(dims)
+    s = np.ascontiguousarray(S, dtype=np.float32)
+    E = np.zeros(1, np.float64)
+    M = np.zeros(3, np.float64)
+    _check(lib().orc_heis_observables(len(d), _p(d), _p(s), _p(E), _p(M)), "heis_observables")
+    return float(E[0]), M
+
+
+def heis_sweeps(dims, S: np.ndarray, beta: float, nsweeps: int, seed: int, stream: int = 0, sweep0: int = 0,
+                E: float | None = None, M=None):
+    """Heisenberg sweeps in place on S (binary32 [N, 3]).  Returns (E, M, traceE, traceM[n, 3])."""
+    d = _dims(dims)
+    if S.dtype != np.float32 or not S.flags.c_contiguous or S.shape != (int(np.prod(d)), 3):
+        raise TypeError("S must be a contiguous float32 [N, 3] array")
+    if E is None or M is None:
+        E, M = heis_observables(d, S)
+    Ea = np.array([E], np.float64)
+    Ma = np.array(M, np.float64).copy()
+    tE = np.zeros(max(nsweeps, 1), np.float64)
+    tM = np.zeros((max(nsweeps, 1), 3), np.float64)
+    _check(lib().orc_heis_sweeps(len(d), _p(d), _p(S), float(beta), seed, stream, sweep0, int(nsweeps), _p(Ea),
+                                 _p(Ma), _p(tE), _p(tM)), "heis_sweeps")
+    return float(Ea[0]), Ma, tE[:nsweeps], tM[:nsweeps]

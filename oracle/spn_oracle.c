@@ -65,12 +65,17 @@
  *   u < floor(exp(D) * 2^32) with u = word k & 3 of R(k >> 2, e, 2 << 1, stream);
  *   an accepted pair swaps the slots of the two temperatures.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define ORC_TWO32 4294967296.0
+
+#if FLT_EVAL_METHOD != 0
+#error "the Heisenberg oracle needs float expressions evaluated in float"
+#endif
 
 /* ---------------------------------------------------------------- Philox */
 
@@ -510,6 +515,179 @@ int orc_ea_overlap(int nd, const int64_t* L, int npairs, const uint32_t* sp, con
       q[p * 32 + t] = sum;
     }
   }
+  return 0;
+}
+
+/* ------------------------------------------ Heisenberg spins (Sec. 4 outlook) */
+
+/* The classical O(3) Heisenberg model H = -sum_<ij> S_i . S_j (J = 1, |S| = 1),
+ * the continuous-spin generalisation the paper names for single-precision GPU
+ * arithmetic, with the same checkerboard Metropolis sweep: a site of colour c
+ * proposes a new direction S' uniformly on the sphere and takes it iff
+ * dE = -(S' - S) . h <= 0 or u < exp(-beta dE), h the sum of its 2 nd
+ * neighbours.  Spins are binary32 (x, y, z) per site.  Every floating-point step
+ * is one IEEE-754 binary32 operation (+, -, *, sqrt, round-to-integral), rounded
+ * to nearest, in the order written (left to right), never fused (this file is
+ * built with -ffp-contract=off and evaluates float expressions in float); no
+ * library transcendental is called, so any implementation doing the same
+ * operations gets the same bits.
+ *   random  proposals: call k = 0..7 is R(m, t, c | 5 << 1 | k << 4, stream),
+ *           m = n >> 1; tries 2k and 2k+1 take words (0, 1) and (2, 3); hot
+ *           start: the same with purpose 7 and t = 0.  Metropolis u: word m & 3
+ *           of R(m >> 2, t, c | 6 << 1, stream).  A word w gives the binary32
+ *           value (w >> 8) 2^-24 in [0, 1) exactly.
+ *   beta    rounded once to binary32. */
+
+static float f32_bits_pow2(int k) { /* 2^k for -126 <= k <= 127, exactly */
+  uint32_t b = (uint32_t)(127 + k) << 23;
+  float f;
+  memcpy(&f, &b, sizeof f);
+  return f;
+}
+
+/* exp(x) for x <= 0: Cody-Waite reduction (Cody and Waite, "Software Manual for
+ * the Elementary Functions", 1980) x = k ln2 + r, k the nearest integer to
+ * x log2(e) and ln 2 split into a 16-bit high part (so k ln2_hi is exact) and
+ * the rest; e^r by its Taylor polynomial of degree 7 in Horner form; times 2^k.
+ * x < -87 gives 0 (the result would leave the normal range). */
+float orc_heis_exp(float x) {
+  const float log2e = (float)(1.0 / 0.6931471805599453);
+  const float ln2_hi = 45426.0f / 65536.0f;
+  const float ln2_lo = (float)(0.6931471805599453 - 45426.0 / 65536.0);
+  const float c[8] = {1.0f, 1.0f, 0.5f, (float)(1.0 / 6.0), (float)(1.0 / 24.0), (float)(1.0 / 120.0),
+                      (float)(1.0 / 720.0), (float)(1.0 / 5040.0)};
+  if (x < -87.0f) return 0.0f;
+  if (x > 0.0f) return 1.0f; /* not used: the sweep only asks for dE > 0 */
+  const float kf = rintf(x * log2e);
+  const float r = (x - kf * ln2_hi) - kf * ln2_lo;
+  float p = c[7];
+  for (int i = 6; i >= 0; --i) p = p * r + c[i];
+  return p * f32_bits_pow2((int)kf);
+}
+
+static float word_unit(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+/* Marsaglia's uniform point on the sphere (Ann. Math. Stat. 43, 645 (1972)) from
+ * the purpose-p words of site m: v1, v2 = 2 (w >> 8) 2^-24 - 1 in [-1, 1); the
+ * first try with s = v1^2 + v2^2 < 1 gives S = (2 v1 sqrt(1-s), 2 v2 sqrt(1-s),
+ * 1 - 2 s).  Returns 0 if all 16 tries fail (then there is no proposal). */
+int orc_heis_proposal(uint64_t seed, uint32_t stream, uint32_t t, int colour, int purpose, uint64_t m, float out[3]) {
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (uint32_t k = 0; k < 8; ++k) {
+    uint32_t ctr[4] = {(uint32_t)m, t, (uint32_t)colour | ((uint32_t)purpose << 1) | (k << 4), stream};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    for (int j = 0; j < 2; ++j) {
+      const float v1 = (float)(w[2 * j] >> 8) * (1.0f / 8388608.0f) - 1.0f;
+      const float v2 = (float)(w[2 * j + 1] >> 8) * (1.0f / 8388608.0f) - 1.0f;
+      const float ss = v1 * v1 + v2 * v2;
+      if (ss < 1.0f) {
+        const float f = 2.0f * sqrtf(1.0f - ss);
+        out[0] = v1 * f;
+        out[1] = v2 * f;
+        out[2] = 1.0f - 2.0f * ss;
+        return 1;
+      }
+    }
+  }
+  return 0;
+}
+
+int orc_heis_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, float* S) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  for (int64_t n = 0; n < g.N; ++n) {
+    float v[3] = {0.0f, 0.0f, 1.0f};
+    orc_heis_proposal(seed, stream, 0, lat_colour(&g, n), 7, (uint64_t)(n >> 1), v);
+    S[3 * n] = v[0];
+    S[3 * n + 1] = v[1];
+    S[3 * n + 2] = v[2];
+  }
+  return 0;
+}
+
+/* E = -sum_n sum_d S_n . S_{n+e_d} and M = sum_n S_n, in binary64 in site order
+ * (products of two binary32 values are exact in binary64). */
+int orc_heis_observables(int nd, const int64_t* L, const float* S, double* E, double* M) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  double e = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+  for (int64_t n = 0; n < g.N; ++n) {
+    for (int d = 0; d < nd; ++d) {
+      const int64_t f = lat_step(&g, n, d, +1);
+      e -= (double)S[3 * n] * S[3 * f] + (double)S[3 * n + 1] * S[3 * f + 1] + (double)S[3 * n + 2] * S[3 * f + 2];
+    }
+    mx += S[3 * n];
+    my += S[3 * n + 1];
+    mz += S[3 * n + 2];
+  }
+  *E = e;
+  M[0] = mx;
+  M[1] = my;
+  M[2] = mz;
+  return 0;
+}
+
+/* nsweeps sweeps from global sweep index sweep0.  E and M (in/out) are advanced
+ * by the accepted moves, in site order; traceE[s], traceM[3 s ..] after sweep s. */
+int orc_heis_sweeps(int nd, const int64_t* L, float* S, double beta, uint64_t seed, uint32_t stream, uint32_t sweep0,
+                    int64_t nsweeps, double* E, double* M, double* traceE, double* traceM) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  const float bf = (float)beta;
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  double* dE = (double*)malloc(sizeof(double) * 4 * (size_t)g.N);
+  if (!dE) return -1;
+  for (int64_t t = 0; t < nsweeps; ++t) {
+    const uint32_t sweep = sweep0 + (uint32_t)t;
+    for (int c = 0; c < 2; ++c) {
+#pragma omp parallel for schedule(static)
+      for (int64_t n = 0; n < g.N; ++n) {
+        double* rec = dE + 4 * n;
+        rec[0] = rec[1] = rec[2] = rec[3] = 0.0;
+        if (lat_colour(&g, n) != c) continue;
+        float h[3] = {0.0f, 0.0f, 0.0f};
+        for (int d = 0; d < nd; ++d) {
+          const int64_t b = lat_step(&g, n, d, -1), f = lat_step(&g, n, d, +1);
+          for (int i = 0; i < 3; ++i) {
+            h[i] = h[i] + S[3 * b + i];
+            h[i] = h[i] + S[3 * f + i];
+          }
+        }
+        float p[3];
+        if (!orc_heis_proposal(seed, stream, sweep, c, 5, (uint64_t)(n >> 1), p)) continue;
+        float ds[3];
+        for (int i = 0; i < 3; ++i) ds[i] = p[i] - S[3 * n + i];
+        float dot = ds[0] * h[0];
+        dot = dot + ds[1] * h[1];
+        dot = dot + ds[2] * h[2];
+        const float de = -dot;
+        int accept = de <= 0.0f;
+        if (!accept) {
+          const uint64_t m = (uint64_t)(n >> 1);
+          uint32_t ctr[4] = {(uint32_t)(m >> 2), sweep, (uint32_t)c | (6u << 1), stream};
+          uint32_t w[4];
+          orc_philox4x32_10(ctr, key, w);
+          accept = word_unit(w[m & 3]) < orc_heis_exp(-(bf * de));
+        }
+        if (accept) {
+          rec[0] = de;
+          for (int i = 0; i < 3; ++i) {
+            rec[1 + i] = ds[i];
+            S[3 * n + i] = p[i];
+          }
+        }
+      }
+      for (int64_t n = 0; n < g.N; ++n) {
+        *E += dE[4 * n];
+        for (int i = 0; i < 3; ++i) M[i] += dE[4 * n + 1 + i];
+      }
+    }
+    if (traceE) traceE[t] = *E;
+    if (traceM)
+      for (int i = 0; i < 3; ++i) traceM[3 * t + i] = M[i];
+  }
+  free(dE);
   return 0;
 }
 
