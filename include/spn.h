@@ -62,7 +62,9 @@ enum spn_model {
   SPN_ISING2D = 1,   /* square lattice, J = +1 (Eq. 1) */
   SPN_ISING3D = 2,   /* simple cubic, J = +1 (Sec. 4) */
   SPN_EA3D_PMJ = 3,  /* simple cubic, J = +-1 per bond (Sec. 4, spin glass) */
-  SPN_EA2D_PMJ = 4   /* square lattice, J = +-1 per bond (batches only: spn_create_batch) */
+  SPN_EA2D_PMJ = 4,  /* square lattice, J = +-1 per bond (batches only: spn_create_batch) */
+  SPN_HEIS2D = 5,    /* square lattice, classical Heisenberg (O(3)) spins, J = +1 (Sec. 4 outlook) */
+  SPN_HEIS3D = 6     /* simple cubic, classical Heisenberg spins */
 };
 
 enum spn_init { SPN_INIT_HOT = 0, SPN_INIT_COLD = 1 };
@@ -180,6 +182,47 @@ int spn_set_path(spn_handle h, int32_t path);
 /* Number of kernels this library has launched in the process so far (all
  * handles); a diagnostic for benchmarks. */
 int spn_launch_count(uint64_t* count);
+
+/* ------------------------------------------------------------------------
+ * Classical Heisenberg spins (the continuous-spin generalisation Sec. 4 names
+ * for single-precision GPU arithmetic): H = -sum_<ij> S_i . S_j, |S| = 1.
+ * spn_create_ex(model SPN_HEIS2D / SPN_HEIS3D, couplings NULL) makes the
+ * handle (dims even, N < 2^31; hot start: every site a uniform direction, cold
+ * start: all (0, 0, 1)); spn_sweep, spn_reinit, spn_sweep_count,
+ * spn_set_stream, spn_sync and spn_destroy work on it, the int8 calls return
+ * SPN_E_STATE.  A sweep updates colour 0, then colour 1: a site proposes a
+ * direction uniform on the sphere (Marsaglia's method) and takes it iff
+ * dE = -(S' - S) . h <= 0 or u < exp(-beta dE), h the sum of its neighbours.
+ * Spins are binary32; every step is a correctly rounded binary32 operation in
+ * a fixed order and exp is Cody-Waite reduction plus a degree-7 Taylor
+ * polynomial of those operations, so lattices are reproducible bit for bit;
+ * beta is rounded to binary32.  Random words (Philox, key = seed): proposal
+ * call k = 0..7 is R(m, sweep, c | 5 << 1 | k << 4, stream), m = n >> 1,
+ * tries 2k and 2k+1 from words (0, 1) and (2, 3), a word w giving
+ * (w >> 8) 2^-23 - 1; no move after 16 failed tries; the hot start uses
+ * purpose 7 with sweep 0; u = (w >> 8) 2^-24 with w = word m & 3 of
+ * R(m >> 2, sweep, c | 6 << 1, stream).  E and M are binary64 sums of the
+ * accepted moves' binary32 dE and dS (their order varies between runs at the
+ * level of binary64 rounding).
+ * ---------------------------------------------------------------------- */
+
+/* Spins as binary32 [N][3] (x, y, z) in site order; count = 3 N.  Set copies
+ * the vectors as given (callers pass unit vectors) and recomputes E and M. */
+int spn_heis_get_spins(spn_handle h, float* xyz, size_t count);
+int spn_heis_set_spins(spn_handle h, const float* xyz, size_t count);
+
+/* E and M[3] after the sweeps so far (synchronises). */
+int spn_heis_observables(spn_handle h, double* E, double* M);
+
+/* E = -sum_n sum_d S_n . S_{n+e_d} and M recomputed from the spins on the
+ * device in binary64. */
+int spn_heis_recompute(spn_handle h, double* E, double* M);
+
+/* Per-sweep trace: E[s], M[3 s + i] after sweep s; *n = sweeps so far. */
+int spn_heis_trace(spn_handle h, double* E, double* M, int64_t cap, int64_t* n);
+
+/* Test support: the device exp of the acceptance on n host floats. */
+int spn_test_heis_exp(const float* x, float* y, size_t n);
 
 /* ------------------------------------------------------------------------
  * Batched runs of many independent lattices (uneven sizes, temperatures and

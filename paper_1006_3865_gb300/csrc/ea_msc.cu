@@ -34,25 +34,9 @@
 #include "philox.cuh"
 #include "spn.h"
 #include "spn_internal.h"
+#include "fastdiv.cuh"
 
 namespace spn {
-
-static FastDiv fastdiv(uint32_t d) {
-  FastDiv f{d, 0, 0};
-  if (d <= 1) return f;
-  uint32_t l = 0;
-  while ((1ull << l) < d) ++l;  // l = ceil(log2 d) >= 1
-  f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
-  f.s = l - 1;
-  return f;
-}
-
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
-  if (f.d <= 1) return n;
-  const uint32_t t = __umulhi(n, f.m);
-  return (t + ((n - t) >> 1)) >> f.s;
-}
-
 
 // colour-separated shared-memory word index of site (x, y, z)
 __device__ __forceinline__ int ea_slot(int x, int row, int h) { return (row * 2 + (x & 1)) * h + (x >> 1); }

@@ -1,0 +1,556 @@
+// Classical Heisenberg (O(3)) spins with the checkerboard Metropolis sweep:
+// the continuous-spin generalisation Sec. 4 names for single-precision GPU
+// arithmetic.  H = -sum_<ij> S_i . S_j (J = 1, |S| = 1), spins as binary32
+// (x, y, z, 0) per site.  A site of colour c proposes a direction uniform on the
+// sphere (Marsaglia's method) and takes it iff dE = -(S' - S) . h <= 0 or
+// u < exp(-beta dE), h the sum of its 2 nd neighbours.
+//
+// Every floating-point step is one correctly rounded binary32 operation in a
+// fixed order (the _rn intrinsics keep the compiler from fusing or reordering),
+// and exp is computed by Cody-Waite reduction and a Taylor polynomial from
+// those operations alone, so the lattice is bit-identical to any other
+// implementation of the same steps.  Random words:
+//   proposal call k (tries 2k, 2k+1 from words (0,1), (2,3)):
+//     R(m, sweep, c | 5 << 1 | k << 4, stream), m = n >> 1, at most 8 calls;
+//   hot start: the same with purpose 7 and sweep 0;
+//   Metropolis u: word m & 3 of R(m >> 2, sweep, c | 6 << 1, stream).
+//
+// One launch updates one colour.  A thread takes four consecutive
+// within-colour indices (one Metropolis Philox call serves them); a proposal
+// try that fails for some lanes is retried for the failing sites of all lanes
+// together.  Energy and magnetisation changes are summed in binary64 per CTA
+// and added to the sweep's accumulator (their summation order varies; the
+// spins do not depend on it).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fastdiv.cuh"
+#include "philox.cuh"
+#include "spn.h"
+#include "spn_internal.h"
+
+namespace spn {
+namespace {
+
+enum : uint32_t { kHeisPropose = 5u, kHeisMetropolis = 6u, kHeisInit = 7u };
+
+struct HeisArgs {
+  float4* s;
+  int nd, Lx, Ly, Lz;
+  uint32_t half;  // sites per colour
+  FastDiv div_h, div_ly;
+  float beta;
+  uint32_t sweep, stream_id, colour;
+  PhiloxKeys K;
+  double* acc;  // [4]: dE, dMx, dMy, dMz of this sweep
+};
+
+__device__ __forceinline__ float heis_exp_dev(float x) {
+  const float log2e = (float)(1.0 / 0.6931471805599453);
+  const float ln2_hi = 45426.0f / 65536.0f;
+  const float ln2_lo = (float)(0.6931471805599453 - 45426.0 / 65536.0);
+  const float c7 = (float)(1.0 / 5040.0), c6 = (float)(1.0 / 720.0), c5 = (float)(1.0 / 120.0),
+              c4 = (float)(1.0 / 24.0), c3 = (float)(1.0 / 6.0);
+  if (x < -87.0f) return 0.0f;
+  if (x > 0.0f) return 1.0f;
+  const float kf = rintf(__fmul_rn(x, log2e));
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, ln2_hi)), __fmul_rn(kf, ln2_lo));
+  float p = c7;
+  p = __fadd_rn(__fmul_rn(p, r), c6);
+  p = __fadd_rn(__fmul_rn(p, r), c5);
+  p = __fadd_rn(__fmul_rn(p, r), c4);
+  p = __fadd_rn(__fmul_rn(p, r), c3);
+  p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+  return __fmul_rn(p, __int_as_float((127 + (int)kf) << 23));
+}
+
+// One Marsaglia try from two words; true and the point if v1^2 + v2^2 < 1.
+__device__ __forceinline__ bool marsaglia_try(uint32_t w1, uint32_t w2, float3& out) {
+  const float v1 = __fsub_rn(__fmul_rn(__uint2float_rn(w1 >> 8), 1.0f / 8388608.0f), 1.0f);
+  const float v2 = __fsub_rn(__fmul_rn(__uint2float_rn(w2 >> 8), 1.0f / 8388608.0f), 1.0f);
+  const float ss = __fadd_rn(__fmul_rn(v1, v1), __fmul_rn(v2, v2));
+  if (!(ss < 1.0f)) return false;
+  const float f = __fmul_rn(2.0f, __fsqrt_rn(__fsub_rn(1.0f, ss)));
+  out = make_float3(__fmul_rn(v1, f), __fmul_rn(v2, f), __fsub_rn(1.0f, __fmul_rn(2.0f, ss)));
+  return true;
+}
+
+// Proposal call k of site m: tries 2k and 2k+1.
+__device__ __forceinline__ bool proposal_call(const PhiloxKeys& K, uint32_t m, uint32_t t, uint32_t c, uint32_t purpose,
+                                              uint32_t k, uint32_t stream, float3& out) {
+  const U4 P = philox10(m, t, c | (purpose << 1) | (k << 4), stream, K);
+  if (marsaglia_try(P.x, P.y, out)) return true;
+  return marsaglia_try(P.z, P.w, out);
+}
+
+// Site of within-colour index m of colour c.
+__device__ __forceinline__ uint32_t site_of(const HeisArgs& a, uint32_t m, uint32_t c, int& x, int& y, int& z) {
+  const uint32_t row = fdiv(m, a.div_h);
+  const int i = (int)(m - row * (uint32_t)(a.Lx >> 1));
+  z = a.nd == 3 ? (int)fdiv(row, a.div_ly) : 0;
+  y = (int)row - z * a.Ly;
+  x = 2 * i + (int)((c ^ (uint32_t)(y + z)) & 1u);
+  return (uint32_t)x + (uint32_t)a.Lx * row;
+}
+
+__device__ __forceinline__ void add3(float3& h, const float4 v) {
+  h.x = __fadd_rn(h.x, v.x);
+  h.y = __fadd_rn(h.y, v.y);
+  h.z = __fadd_rn(h.z, v.z);
+}
+
+__device__ __forceinline__ void block_add4(double v[4], double* acc) {
+  __shared__ double red[32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) red[warp][i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      double x = lane < nw ? red[lane][i] : 0.0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0 && x != 0.0) atomicAdd(&acc[i], x);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_heis_half(const HeisArgs a) {
+  const uint32_t c = a.colour;
+  const uint32_t quads = (a.half + 3u) >> 2;
+  double sum[4] = {0.0, 0.0, 0.0, 0.0};
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; __any_sync(0xffffffffu, q < quads);
+       q += gridDim.x * blockDim.x) {
+    const bool live = q < quads;
+    uint32_t n[4];
+    float3 h[4], prop[4];
+    uint32_t need = 0, tries = 0;  // sites still without a proposal; next call per site (4 bits each)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t m = 4u * q + (uint32_t)j;
+      h[j] = make_float3(0.0f, 0.0f, 0.0f);
+      n[j] = 0;
+      if (!live || m >= a.half) continue;
+      int x, y, z;
+      n[j] = site_of(a, m, c, x, y, z);
+      const int xm = x == 0 ? a.Lx - 1 : x - 1, xp = x + 1 == a.Lx ? 0 : x + 1;
+      add3(h[j], a.s[n[j] - x + xm]);
+      add3(h[j], a.s[n[j] - x + xp]);
+      const int64_t sy = a.Lx;
+      add3(h[j], a.s[y == 0 ? n[j] + (a.Ly - 1) * sy : n[j] - sy]);
+      add3(h[j], a.s[y + 1 == a.Ly ? n[j] - (a.Ly - 1) * sy : n[j] + sy]);
+      if (a.nd == 3) {
+        const int64_t sz = (int64_t)a.Lx * a.Ly;
+        add3(h[j], a.s[z == 0 ? n[j] + (a.Lz - 1) * sz : n[j] - sz]);
+        add3(h[j], a.s[z + 1 == a.Lz ? n[j] - (a.Lz - 1) * sz : n[j] + sz]);
+      }
+      if (proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop[j])) continue;
+      need |= 1u << j;
+      tries |= 1u << (4 * j);
+    }
+    // the rare sites whose first two tries missed the disc: one call per lane and round
+    while (__any_sync(0xffffffffu, need != 0u)) {
+      if (need) {
+        const int j = __ffs((int)need) - 1;
+        const uint32_t k = (tries >> (4 * j)) & 15u;
+        float3 p;
+        const bool ok = proposal_call(a.K, 4u * q + (uint32_t)j, a.sweep, c, kHeisPropose, k, a.stream_id, p);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {  // static indices keep prop and n in registers
+          if (jj != j) continue;
+          if (ok) prop[jj] = p;
+          if (!ok && k == 7u) n[jj] = 0xffffffffu;  // sixteen misses: no move for this site
+        }
+        if (ok || k == 7u) {
+          need &= ~(1u << j);
+        } else {
+          tries += 1u << (4 * j);
+        }
+      }
+    }
+    bool have_u = false;
+    U4 U{0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t m = 4u * q + (uint32_t)j;
+      if (!live || m >= a.half || n[j] == 0xffffffffu) continue;
+      const float4 s = a.s[n[j]];
+      const float dx = __fsub_rn(prop[j].x, s.x), dy = __fsub_rn(prop[j].y, s.y), dz = __fsub_rn(prop[j].z, s.z);
+      float dot = __fmul_rn(dx, h[j].x);
+      dot = __fadd_rn(dot, __fmul_rn(dy, h[j].y));
+      dot = __fadd_rn(dot, __fmul_rn(dz, h[j].z));
+      const float de = -dot;
+      bool accept = de <= 0.0f;
+      if (!accept) {
+        if (!have_u) {
+          U = philox10(q, a.sweep, c | (kHeisMetropolis << 1), a.stream_id, a.K);
+          have_u = true;
+        }
+        const float u = __fmul_rn(__uint2float_rn(u4_word(U, j) >> 8), 1.0f / 16777216.0f);
+        accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
+      }
+      if (accept) {
+        a.s[n[j]] = make_float4(prop[j].x, prop[j].y, prop[j].z, 0.0f);
+        sum[0] += (double)de;
+        sum[1] += (double)dx;
+        sum[2] += (double)dy;
+        sum[3] += (double)dz;
+      }
+    }
+  }
+  block_add4(sum, a.acc);
+}
+
+__global__ void k_heis_init(float4* s, int nd, int Lx, int Ly, int64_t N, PhiloxKeys K, uint32_t stream, int cold) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    if (cold) {
+      s[n] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
+      continue;
+    }
+    const int x = (int)(n % Lx);
+    const int64_t r = n / Lx;
+    const int y = (int)(r % Ly), z = nd == 3 ? (int)(r / Ly) : 0;
+    const uint32_t c = (uint32_t)(x + y + z) & 1u;
+    float3 p = make_float3(0.0f, 0.0f, 1.0f);
+    for (uint32_t k = 0; k < 8; ++k)
+      if (proposal_call(K, (uint32_t)(n >> 1), 0u, c, kHeisInit, k, stream, p)) break;
+    s[n] = make_float4(p.x, p.y, p.z, 0.0f);
+  }
+}
+
+// E = -sum_n sum_d S_n . S_{n+e_d}, M = sum S (binary64; products of binary32 values are exact)
+__global__ void k_heis_observables(const float4* s, int nd, int Lx, int Ly, int Lz, int64_t N, double* out) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % Lx);
+    const int64_t r = n / Lx;
+    const int y = (int)(r % Ly), z = (int)(r / Ly);
+    const float4 a = s[n];
+    const int64_t f[3] = {n - x + (x + 1 == Lx ? 0 : x + 1), n + (int64_t)((y + 1 == Ly ? 0 : y + 1) - y) * Lx,
+                          n + (int64_t)((z + 1 == Lz ? 0 : z + 1) - z) * Lx * Ly};
+    for (int d = 0; d < nd; ++d) {
+      const float4 b = s[f[d]];
+      v[0] -= (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z;
+    }
+    v[1] += a.x;
+    v[2] += a.y;
+    v[3] += a.z;
+  }
+  block_add4(v, out);
+}
+
+__global__ void k_heis_exp(const float* x, float* y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = heis_exp_dev(x[i]);
+}
+
+int grid_for(int64_t threads_needed, int per_sm) {
+  const int64_t want = (threads_needed + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)device_sm_count() * per_sm));
+}
+
+}  // namespace
+
+bool heis_dims_ok(int nd, const int32_t* dims) {
+  int64_t N = 1;
+  for (int d = 0; d < nd; ++d) {
+    if (dims[d] < 2 || (dims[d] & 1)) return false;
+    N *= dims[d];
+  }
+  return N < ((int64_t)1 << 31);
+}
+
+cudaError_t launch_heis_init(float4* s, int nd, const int* L, int64_t N, uint64_t seed, uint32_t stream, bool cold,
+                             cudaStream_t st) {
+  k_heis_init<<<grid_for(N, 8), 256, 0, st>>>(s, nd, L[0], L[1], N, philox_keys(seed), stream, cold ? 1 : 0);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float beta, uint64_t seed,
+                              uint32_t stream, uint32_t sweep, double* acc, cudaStream_t st) {
+  HeisArgs a;
+  a.s = s;
+  a.nd = nd;
+  a.Lx = L[0];
+  a.Ly = L[1];
+  a.Lz = nd == 3 ? L[2] : 1;
+  a.half = (uint32_t)(N / 2);
+  a.div_h = fastdiv((uint32_t)(L[0] / 2));
+  a.div_ly = fastdiv((uint32_t)L[1]);
+  a.beta = beta;
+  a.sweep = sweep;
+  a.stream_id = stream;
+  a.K = philox_keys(seed);
+  a.acc = acc;
+  const int grid = grid_for(((int64_t)a.half + 3) / 4, 8);
+  for (uint32_t c = 0; c < 2; ++c) {
+    a.colour = c;
+    k_heis_half<<<grid, 256, 0, st>>>(a);
+  }
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heis_observables(const float4* s, int nd, const int* L, int64_t N, double* out4,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out4, 0, 4 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  k_heis_observables<<<grid_for(N, 4), 256, 0, st>>>(s, nd, L[0], L[1], nd == 3 ? L[2] : 1, N, out4);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heis_exp(const float* x, float* y, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_heis_exp<<<(n + 255) / 256, 256, 0, st>>>(x, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace spn
+
+// ---------------------------------------------------------------- handles
+
+struct HeisState {
+  int nd = 2;
+  int L[3] = {0, 0, 1};
+  int64_t N = 0;
+  float4* d_s = nullptr;
+  double* d_acc = nullptr;  // [cap][4] per-sweep (dE, dM) since `folded`
+  int64_t acc_cap = 0;
+  uint64_t folded = 0;
+  double* d_obs = nullptr;
+  double E = 0.0, M[3] = {0.0, 0.0, 0.0};
+  std::vector<double> traceE, traceM;
+};
+
+namespace {
+
+int heis_fail(int code, const char* msg) {
+  spn::set_last_error(msg);
+  return code;
+}
+
+int heis_recompute(spn_ctx* h, double* E, double* M) {
+  HeisState* s = h->heis;
+  if (spn::launch_heis_observables(s->d_s, s->nd, s->L, s->N, s->d_obs, h->st) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "Heisenberg observables launch");
+  double r[4];
+  if (cudaMemcpyAsync(r, s->d_obs, sizeof r, cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "reading the Heisenberg observables");
+  *E = r[0];
+  for (int i = 0; i < 3; ++i) M[i] = r[1 + i];
+  return SPN_OK;
+}
+
+int heis_fold(spn_ctx* h) {
+  HeisState* s = h->heis;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return heis_fail(SPN_E_CUDA, "cudaStreamSynchronize");
+  const int64_t live = (int64_t)(h->sweeps - s->folded);
+  if (live <= 0) return SPN_OK;
+  std::vector<double> d((size_t)live * 4);
+  if (cudaMemcpy(d.data(), s->d_acc, d.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "reading the Heisenberg trace");
+  for (int64_t i = 0; i < live; ++i) {
+    s->E += d[4 * i];
+    for (int k = 0; k < 3; ++k) s->M[k] += d[4 * i + 1 + k];
+    s->traceE.push_back(s->E);
+    for (int k = 0; k < 3; ++k) s->traceM.push_back(s->M[k]);
+  }
+  s->folded = h->sweeps;
+  if (cudaMemsetAsync(s->d_acc, 0, (size_t)s->acc_cap * 4 * sizeof(double), h->st) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "clearing the Heisenberg trace");
+  return SPN_OK;
+}
+
+int heis_ensure_acc(spn_ctx* h, int64_t n) {
+  HeisState* s = h->heis;
+  const int64_t need = (int64_t)(h->sweeps - s->folded) + n;
+  if (need <= s->acc_cap) return SPN_OK;
+  int rc = heis_fold(h);  // empties the device deltas, so the buffer can be replaced
+  if (rc) return rc;
+  int64_t cap = std::max<int64_t>(1024, s->acc_cap);
+  while (cap < n) cap *= 2;
+  cudaFree(s->d_acc);
+  s->d_acc = nullptr;
+  if (cudaMalloc(&s->d_acc, (size_t)cap * 4 * sizeof(double)) != cudaSuccess)
+    return heis_fail(SPN_E_NOMEM, "cudaMalloc(Heisenberg trace)");
+  if (cudaMemsetAsync(s->d_acc, 0, (size_t)cap * 4 * sizeof(double), h->st) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "clearing the Heisenberg trace");
+  s->acc_cap = cap;
+  return SPN_OK;
+}
+
+int heis_reset(spn_ctx* h, int init) {
+  HeisState* s = h->heis;
+  if (spn::launch_heis_init(s->d_s, s->nd, s->L, s->N, h->seed, h->stream_id, init == SPN_INIT_COLD, h->st) !=
+      cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "Heisenberg init launch");
+  return heis_recompute(h, &s->E, s->M);
+}
+
+}  // namespace
+
+namespace spn {
+
+bool is_heis_model(int model) { return model == SPN_HEIS2D || model == SPN_HEIS3D; }
+
+void heis_free(HeisState* s) {
+  if (!s) return;
+  cudaFree(s->d_s);
+  cudaFree(s->d_acc);
+  cudaFree(s->d_obs);
+  delete s;
+}
+
+int heis_create(spn_ctx* h, const int32_t* dims, int init) {
+  HeisState* s = new (std::nothrow) HeisState;
+  if (!s) return heis_fail(SPN_E_NOMEM, "host allocation failed");
+  h->heis = s;
+  s->nd = h->model == SPN_HEIS3D ? 3 : 2;
+  if (!heis_dims_ok(s->nd, dims)) return heis_fail(SPN_E_ARG, "extents must be even, >= 2, and N < 2^31");
+  s->N = 1;
+  for (int d = 0; d < s->nd; ++d) {
+    s->L[d] = dims[d];
+    s->N *= dims[d];
+  }
+  if (cudaMalloc(&s->d_s, (size_t)s->N * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&s->d_obs, 4 * sizeof(double)) != cudaSuccess)
+    return heis_fail(SPN_E_NOMEM, "cudaMalloc(Heisenberg lattice)");
+  int rc = heis_ensure_acc(h, 1024);
+  if (rc) return rc;
+  return heis_reset(h, init);
+}
+
+int heis_sweep(spn_ctx* h, double beta, int64_t nsweeps) {
+  HeisState* s = h->heis;
+  int rc = heis_ensure_acc(h, nsweeps);
+  if (rc) return rc;
+  const float bf = (float)beta;
+  for (int64_t t = 0; t < nsweeps; ++t) {
+    const uint32_t sweep = (uint32_t)(h->sweeps + t);
+    double* acc = s->d_acc + 4 * (int64_t)(sweep - s->folded);
+    const cudaError_t e = launch_heis_sweep(s->d_s, s->nd, s->L, s->N, bf, h->seed, h->stream_id, sweep, acc, h->st);
+    if (e != cudaSuccess) {
+      h->sweeps += (uint64_t)t;
+      return heis_fail(SPN_E_CUDA, cudaGetErrorString(e));
+    }
+  }
+  h->sweeps += (uint64_t)nsweeps;
+  return SPN_OK;
+}
+
+int heis_reinit(spn_ctx* h, int init) {
+  HeisState* s = h->heis;
+  int rc = heis_fold(h);
+  if (rc) return rc;
+  s->traceE.clear();
+  s->traceM.clear();
+  s->folded = 0;
+  return heis_reset(h, init);
+}
+
+}  // namespace spn
+
+extern "C" {
+
+static int heis_handle(spn_handle h) {
+  if (!h) return heis_fail(SPN_E_ARG, "handle is NULL");
+  if (!h->heis) return heis_fail(SPN_E_STATE, "not a Heisenberg handle");
+  return SPN_OK;
+}
+
+int spn_heis_get_spins(spn_handle h, float* xyz, size_t count) {
+  int rc = heis_handle(h);
+  if (rc) return rc;
+  HeisState* s = h->heis;
+  if (!xyz || count != (size_t)s->N * 3) return heis_fail(SPN_E_ARG, "xyz must hold 3 N floats");
+  std::vector<float4> v((size_t)s->N);
+  if (cudaMemcpyAsync(v.data(), s->d_s, v.size() * sizeof(float4), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "reading the spins");
+  for (size_t n = 0; n < v.size(); ++n) {
+    xyz[3 * n] = v[n].x;
+    xyz[3 * n + 1] = v[n].y;
+    xyz[3 * n + 2] = v[n].z;
+  }
+  return SPN_OK;
+}
+
+int spn_heis_set_spins(spn_handle h, const float* xyz, size_t count) {
+  int rc = heis_handle(h);
+  if (rc) return rc;
+  HeisState* s = h->heis;
+  if (!xyz || count != (size_t)s->N * 3) return heis_fail(SPN_E_ARG, "xyz must hold 3 N floats");
+  if ((rc = heis_fold(h))) return rc;
+  std::vector<float4> v((size_t)s->N);
+  for (size_t n = 0; n < v.size(); ++n) v[n] = make_float4(xyz[3 * n], xyz[3 * n + 1], xyz[3 * n + 2], 0.0f);
+  if (cudaMemcpy(s->d_s, v.data(), v.size() * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "writing the spins");
+  return heis_recompute(h, &s->E, s->M);
+}
+
+int spn_heis_observables(spn_handle h, double* E, double* M) {
+  int rc = heis_handle(h);
+  if (rc) return rc;
+  if (!E || !M) return heis_fail(SPN_E_ARG, "NULL argument");
+  if ((rc = heis_fold(h))) return rc;
+  *E = h->heis->E;
+  for (int i = 0; i < 3; ++i) M[i] = h->heis->M[i];
+  return SPN_OK;
+}
+
+int spn_heis_recompute(spn_handle h, double* E, double* M) {
+  int rc = heis_handle(h);
+  if (rc) return rc;
+  if (!E || !M) return heis_fail(SPN_E_ARG, "NULL argument");
+  return heis_recompute(h, E, M);
+}
+
+int spn_heis_trace(spn_handle h, double* E, double* M, int64_t cap, int64_t* n) {
+  int rc = heis_handle(h);
+  if (rc) return rc;
+  if (!n || cap < 0 || (cap > 0 && (!E || !M))) return heis_fail(SPN_E_ARG, "bad trace arguments");
+  if ((rc = heis_fold(h))) return rc;
+  HeisState* s = h->heis;
+  const int64_t total = (int64_t)s->traceE.size();
+  const int64_t k = std::min(cap, total);
+  if (k > 0) {
+    std::memcpy(E, s->traceE.data(), (size_t)k * sizeof(double));
+    std::memcpy(M, s->traceM.data(), (size_t)k * 3 * sizeof(double));
+  }
+  *n = total;
+  return SPN_OK;
+}
+
+int spn_test_heis_exp(const float* x, float* y, size_t n) {
+  if (!x || !y) return heis_fail(SPN_E_ARG, "NULL argument");
+  if (n == 0) return SPN_OK;
+  if (n > (size_t)1 << 28) return heis_fail(SPN_E_ARG, "n too large");
+  float *dx = nullptr, *dy = nullptr;
+  cudaError_t e = cudaMalloc(&dx, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dy, n * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(dx, x, n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = spn::launch_heis_exp(dx, dy, (int)n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(y, dy, n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dy);
+  return e == cudaSuccess ? SPN_OK : heis_fail(SPN_E_CUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

@@ -189,6 +189,7 @@ void destroy(spn_ctx* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   spn_ea_free(h->ea);
+  spn::heis_free(h->heis);
   cudaFree(h->spins[0]);
   cudaFree(h->spins[1]);
   cudaFree(h->staged[0]);
@@ -217,6 +218,24 @@ int spn_create_ex(spn_handle* out, int model, const int32_t* dims, const void* c
                   uint32_t stream, int init) {
   if (!out) return fail(SPN_E_ARG, "out is NULL");
   *out = nullptr;
+  if (spn::is_heis_model(model)) {
+    if (!dims) return fail(SPN_E_ARG, "dims is NULL");
+    if (couplings) return fail(SPN_E_ARG, "Heisenberg models take no couplings");
+    if (init != SPN_INIT_HOT && init != SPN_INIT_COLD) return fail(SPN_E_ARG, "unknown init %d", init);
+    spn_ctx* h = new (std::nothrow) spn_ctx;
+    if (!h) return fail(SPN_E_NOMEM, "host allocation failed");
+    h->model = model;
+    h->seed = seed;
+    h->stream_id = stream;
+    const int rc = spn::heis_create(h, dims, init);
+    if (rc) {
+      const std::string msg = spn_last_error();
+      destroy(h);
+      return fail(rc, "%s", msg.c_str());
+    }
+    *out = h;
+    return SPN_OK;
+  }
   spn::Lattice g;
   int rc = check_dims(model, dims, g);
   if (rc) return rc;
@@ -276,6 +295,10 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
   if (nsweeps < 0) return fail(SPN_E_ARG, "nsweeps must be >= 0");
   if (nsweeps == 0) return SPN_OK;
   if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return fail(SPN_E_ARG, "sweep counter would exceed 2^32");
+  if (h->heis) {
+    if (!(beta < 3.4e38)) return fail(SPN_E_ARG, "Heisenberg beta must be finite in binary32");
+    return spn::heis_sweep(h, beta, nsweeps);
+  }
   int rc = ensure_acc(h, nsweeps);
   if (rc) return rc;
   const spn::DevThr T = spn::make_thresholds(beta);
@@ -342,7 +365,8 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
 
 int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile, int32_t hits) {
   if (!h || !tile) return fail(SPN_E_ARG, "NULL argument");
-  if (h->ea || h->model == SPN_EA3D_PMJ) return fail(SPN_E_STATE, "the double-checkerboard sweep is for Ising lattices");
+  if (h->ea || h->heis || h->model == SPN_EA3D_PMJ)
+    return fail(SPN_E_STATE, "the double-checkerboard sweep is for Ising lattices");
   if (!(beta >= 0.0)) return fail(SPN_E_ARG, "beta must be >= 0 (got %g)", beta);
   if (nsweeps < 0 || hits < 1) return fail(SPN_E_ARG, "nsweeps must be >= 0 and hits >= 1");
   if (nsweeps == 0) return SPN_OK;
@@ -378,6 +402,7 @@ int spn_test_expire_next_waits(uint32_t polls) {
 int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
   if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->heis) return fail(SPN_E_STATE, "a Heisenberg handle takes spn_heis_observables");
   int rc = fold(h);
   if (rc) return rc;
   *E = h->E;
@@ -388,12 +413,14 @@ int spn_observables(spn_handle h, int64_t* E, int64_t* M) {
 int spn_recompute(spn_handle h, int64_t* E, int64_t* M) {
   if (!h || !E || !M) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->heis) return fail(SPN_E_STATE, "a Heisenberg handle takes spn_heis_recompute");
   return recompute(h, E, M);
 }
 
 int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n) {
   if (!h || !n || cap < 0 || (cap > 0 && (!E || !M))) return fail(SPN_E_ARG, "bad trace arguments");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->heis) return fail(SPN_E_STATE, "a Heisenberg handle takes spn_heis_trace");
   int rc = fold(h);
   if (rc) return rc;
   const int64_t total = (int64_t)h->traceE.size();
@@ -409,6 +436,7 @@ int spn_trace(spn_handle h, int64_t* E, int64_t* M, int64_t cap, int64_t* n) {
 int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
   if (!h || !host_out) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->heis) return fail(SPN_E_STATE, "a Heisenberg handle takes spn_heis_get_spins");
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
   if (int rc = unpack_if_live(h)) return rc;
   SPN_CUDA(cudaMemcpyAsync(host_out, h->spins[h->cur], bytes, cudaMemcpyDeviceToHost, h->st), "cudaMemcpyAsync");
@@ -419,6 +447,7 @@ int spn_get_spins(spn_handle h, int8_t* host_out, size_t bytes) {
 int spn_set_spins(spn_handle h, const int8_t* host_in, size_t bytes) {
   if (!h || !host_in) return fail(SPN_E_ARG, "NULL argument");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->heis) return fail(SPN_E_STATE, "a Heisenberg handle takes spn_heis_set_spins");
   if (bytes != (size_t)h->g.N) return fail(SPN_E_ARG, "bytes must be N = %lld", (long long)h->g.N);
   int rc = fold(h);
   if (rc) return rc;
@@ -435,6 +464,13 @@ int spn_reinit(spn_handle h, uint64_t seed, uint32_t stream, int init) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
   if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
   if (init != SPN_INIT_HOT && init != SPN_INIT_COLD) return fail(SPN_E_ARG, "unknown init %d", init);
+  if (h->heis) {
+    h->seed = seed;
+    h->stream_id = stream;
+    const int rc = spn::heis_reinit(h, init);
+    h->sweeps = 0;
+    return rc;
+  }
   int rc = fold(h);
   if (rc) return rc;
   h->seed = seed;
@@ -488,7 +524,7 @@ int spn_destroy(spn_handle h) {
 
 int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t seg) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
-  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->ea || h->heis) return fail(SPN_E_STATE, "tiling applies to Ising lattices");
   const int ty = h->g.nd == 3 ? tile_y : 1;
   if (step_slices < 0 || seg < 0) return fail(SPN_E_ARG, "negative tiling parameter");
   const bool packed = h->path == spn::kPathPacked;
@@ -511,7 +547,7 @@ int spn_get_path(spn_handle h, int32_t* path) {
 
 int spn_set_path(spn_handle h, int32_t path) {
   if (!h) return fail(SPN_E_ARG, "handle is NULL");
-  if (h->ea) return fail(SPN_E_STATE, "a batch handle takes the spn_batch_* calls");
+  if (h->ea || h->heis) return fail(SPN_E_STATE, "kernel paths apply to Ising lattices");
   if (path == spn::kPathStream) {
     if (!spn::stream_path_supported(stream_lattice(h), h->tile_y))
       return fail(SPN_E_ARG, "streaming path needs a dividing band and no bonds");

@@ -9,6 +9,8 @@
 
 #include "philox.cuh"
 
+struct spn_ctx;  // the handle (global, as in spn.h)
+
 namespace spn {
 
 // Metropolis thresholds of Eq. 2 for the classes q = dE / 4 = 1 .. 3: a move
@@ -148,10 +150,29 @@ cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, siz
 
 struct EaBatch;                // multi-spin coded EA batch (ea_msc.cu)
 void spn_ea_free(EaBatch* b);
+struct HeisState;              // Heisenberg lattice of a handle (heis.cu)
+
+namespace spn {
+// Heisenberg handles: model SPN_HEIS2D / SPN_HEIS3D; dims checked there.
+bool is_heis_model(int model);
+bool heis_dims_ok(int nd, const int32_t* dims);
+int heis_create(::spn_ctx* h, const int32_t* dims, int init);
+int heis_sweep(::spn_ctx* h, double beta, int64_t nsweeps);
+int heis_reinit(::spn_ctx* h, int init);
+void heis_free(HeisState* s);
+cudaError_t launch_heis_init(float4* s, int nd, const int* L, int64_t N, uint64_t seed, uint32_t stream, bool cold,
+                             cudaStream_t st);
+cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float beta, uint64_t seed,
+                              uint32_t stream, uint32_t sweep, double* acc, cudaStream_t st);
+cudaError_t launch_heis_observables(const float4* s, int nd, const int* L, int64_t N, double* out4,
+                                    cudaStream_t st);
+cudaError_t launch_heis_exp(const float* x, float* y, int n, cudaStream_t st);
+}  // namespace spn
 
 struct spn_ctx {
   int model = 0;
   EaBatch* ea = nullptr;  // set for batch handles (spn_create_batch)
+  HeisState* heis = nullptr;  // set for Heisenberg handles
   spn::Lattice g;
   uint64_t seed = 0;
   uint32_t stream_id = 0;

@@ -31,6 +31,8 @@ SPN_ISING2D = 1
 SPN_ISING3D = 2
 SPN_EA3D_PMJ = 3
 SPN_EA2D_PMJ = 4
+SPN_HEIS2D = 5
+SPN_HEIS3D = 6
 
 SPN_INIT_HOT = 0
 SPN_INIT_COLD = 1
@@ -96,6 +98,12 @@ _SIGNATURES = {
     "spn_batch_energies": (_c.c_int, [_vp, _vp, _vp, _sz]),
     "spn_batch_exchange_counts": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_measure_overlap": (_c.c_int, [_vp]),
+    "spn_heis_get_spins": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_heis_set_spins": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_heis_observables": (_c.c_int, [_vp, _vp, _vp]),
+    "spn_heis_recompute": (_c.c_int, [_vp, _vp, _vp]),
+    "spn_heis_trace": (_c.c_int, [_vp, _vp, _vp, _c.c_int64, _vp]),
+    "spn_test_heis_exp": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_overlap": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _sz]),
     "spn_batch_overlap_reset": (_c.c_int, [_vp]),
 }
@@ -294,6 +302,80 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class HeisLattice:
+    """Classical Heisenberg lattice (spn_create_ex with SPN_HEIS2D / SPN_HEIS3D)."""
+
+    def __init__(self, dims, seed: int, stream_id: int = 0, init: int = SPN_INIT_HOT):
+        self._lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.N = int(np.prod(self.dims))
+        model = SPN_HEIS3D if len(self.dims) == 3 else SPN_HEIS2D
+        d = _dims(dims)
+        h = _vp()
+        _check(self._lib.spn_create_ex(_c.byref(h), model, _ptr(d), None, seed, stream_id, init))
+        self._h = h
+
+    def sweep(self, beta: float, nsweeps: int):
+        _check(self._lib.spn_sweep(self._h, float(beta), int(nsweeps)))
+
+    def reinit(self, seed: int, stream_id: int = 0, init: int = SPN_INIT_HOT):
+        _check(self._lib.spn_reinit(self._h, seed, stream_id, init))
+
+    def get_spins(self) -> np.ndarray:
+        out = np.empty((self.N, 3), np.float32)
+        _check(self._lib.spn_heis_get_spins(self._h, _ptr(out), out.size))
+        return out
+
+    def set_spins(self, S: np.ndarray):
+        s = np.ascontiguousarray(S, dtype=np.float32).reshape(-1)
+        _check(self._lib.spn_heis_set_spins(self._h, _ptr(s), s.size))
+
+    def observables(self):
+        E = _c.c_double()
+        M = np.empty(3, np.float64)
+        _check(self._lib.spn_heis_observables(self._h, _c.byref(E), _ptr(M)))
+        return E.value, M
+
+    def recompute(self):
+        E = _c.c_double()
+        M = np.empty(3, np.float64)
+        _check(self._lib.spn_heis_recompute(self._h, _c.byref(E), _ptr(M)))
+        return E.value, M
+
+    def trace(self):
+        n = _i64()
+        _check(self._lib.spn_heis_trace(self._h, None, None, 0, _c.byref(n)))
+        E = np.empty(n.value, np.float64)
+        M = np.empty((n.value, 3), np.float64)
+        _check(self._lib.spn_heis_trace(self._h, _ptr(E), _ptr(M), n.value, _c.byref(n)))
+        return E, M
+
+    def set_stream(self, stream):
+        _check(self._lib.spn_set_stream(self._h, _stream_ptr(stream)))
+
+    def sync(self):
+        _check(self._lib.spn_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(self._lib.spn_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def heis_exp_device(x: np.ndarray) -> np.ndarray:
+    """The device binary32 exp of the Heisenberg acceptance (test support)."""
+    xs = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(xs)
+    _check(load().spn_test_heis_exp(_ptr(xs), _ptr(y), xs.size))
+    return y
 
 
 class EABatch:
