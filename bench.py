@@ -63,11 +63,11 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d"], default=None,
+    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d", "heis3d"], default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
     p.add_argument("--profile-L", type=int, default=0, help="lattice extent of a 2d / packed2d profile case")
-    p.add_argument("--forms", default="batched,ea,served,dc,packed,overlap",
+    p.add_argument("--forms", default="batched,ea,served,dc,packed,overlap,heis",
                    help="extra forms measured after the plain step (comma list; empty for none)")
     p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
     p.add_argument("--ea-sweeps", type=int, default=EA_SWEEPS)
@@ -100,6 +100,12 @@ def run_profile_case(a):
         lat.sweep_dc(1.0 / TEMPS_2D[1], a.profile_sweeps, (64, 64), 4)
         print("profile case dc E, M =", lat.observables(), flush=True)
         lat.close()
+        return
+    if a.profile_case == "heis3d":  # Heisenberg spins, 3D L = 256 at beta = 0.693
+        h = spn.HeisLattice((256, 256, 256), inputs.unit_seed(9))
+        h.sweep(0.693, a.profile_sweeps)
+        print("profile case heis3d E, M =", h.observables(), flush=True)
+        h.close()
         return
     if a.profile_case in ("2d", "packed2d"):
         L = a.profile_L or L2D
@@ -474,6 +480,33 @@ def form_overlap(stream, sweeps=2000, every=10):
                         f"multi-spin coded, exchange every {EA_EVERY}, overlap every {every} sweeps, {sweeps} sweeps"}
 
 
+def form_heis(stream, sweeps=100):
+    """Classical Heisenberg spins (binary32 vectors, 16 B per site): 2D L = 4096
+    at beta = 1.0 and 3D L = 256 at beta = 0.693 (near the 3D critical point),
+    hot starts, canonical checkerboard sweeps (two launches each).  Lattices of
+    268 MB, larger than L2.  Roofline: 48 algorithmic bytes per attempt (per
+    colour pass the own site read and written and the other colour read once)
+    against the measured HBM copy bandwidth."""
+    from paper_1006_3865_gb300 import inputs, spn
+
+    peak, peak_kind = _peaks()
+    out = {}
+    for name, dims, beta in (("2d_L4096", (4096, 4096), 1.0), ("3d_L256", (256, 256, 256), 0.693)):
+        h = spn.HeisLattice(dims, inputs.unit_seed(0x4E15))
+        h.set_stream(stream)
+        h.sweep(beta, 5)
+        ms = _timed(stream, lambda: h.sweep(beta, sweeps))
+        E, _ = h.observables()
+        N = h.N
+        h.close()
+        att = N / (ms / sweeps * 1e6)
+        out[name] = {"attempts_per_ns": att, "sweep_ms": ms / sweeps, "energy_per_bond": E / (len(dims) * N),
+                     "roofline": {"bound": "hbm", "bytes_per_attempt": 48, "achieved_gbs": 48 * att, "peak": peak,
+                                  "peak_kind": peak_kind, "frac": 48 * att / peak}}
+    return {"value": out["3d_L256"]["attempts_per_ns"], "unit": UNIT, "by_lattice": out,
+            "workload": f"Heisenberg 2D L=4096 (beta 1.0) and 3D L=256 (beta 0.693), {sweeps} sweeps each"}
+
+
 def run_forms(a, stream):
     out = {}
     for f in [x for x in a.forms.split(",") if x]:
@@ -489,6 +522,8 @@ def run_forms(a, stream):
             out["packed"] = form_packed(stream)
         elif f == "overlap":
             out["overlap"] = form_overlap(stream)
+        elif f == "heis":
+            out["heisenberg"] = form_heis(stream)
         else:
             raise SystemExit(f"unknown form {f}")
     return out
