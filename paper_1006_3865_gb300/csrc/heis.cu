@@ -15,10 +15,10 @@
 //   hot start: the same with purpose 7 and sweep 0;
 //   Metropolis u: word m & 3 of R(m >> 2, sweep, c | 6 << 1, stream).
 //
-// One launch updates one colour.  A thread takes four consecutive
-// within-colour indices (one Metropolis Philox call serves them); a proposal
-// try that fails for some lanes is retried for the failing sites of all lanes
-// together.  Energy and magnetisation changes are summed in binary64 per CTA
+// One launch updates one colour, a thread per site: its seven 16-byte loads
+// are issued together, a proposal try that fails for some lanes is retried for
+// those lanes only, and the lanes of four consecutive within-colour indices
+// draw the same Metropolis Philox call (one warp instruction stream).  Energy and magnetisation changes are summed in binary64 per CTA
 // and added to the sweep's accumulator (their summation order varies; the
 // spins do not depend on it).
 #include <cuda_runtime.h>
@@ -128,87 +128,69 @@ __device__ __forceinline__ void block_add4(double v[4], double* acc) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_heis_half(const HeisArgs a) {
+__global__ void __launch_bounds__(256, 6) k_heis_half(const HeisArgs a) {
   const uint32_t c = a.colour;
-  const uint32_t quads = (a.half + 3u) >> 2;
   double sum[4] = {0.0, 0.0, 0.0, 0.0};
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; __any_sync(0xffffffffu, q < quads);
-       q += gridDim.x * blockDim.x) {
-    const bool live = q < quads;
-    uint32_t n[4];
-    float3 h[4], prop[4];
-    uint32_t need = 0, tries = 0;  // sites still without a proposal; next call per site (4 bits each)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t m = 4u * q + (uint32_t)j;
-      h[j] = make_float3(0.0f, 0.0f, 0.0f);
-      n[j] = 0;
-      if (!live || m >= a.half) continue;
+  for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; __any_sync(0xffffffffu, m < a.half);
+       m += gridDim.x * blockDim.x) {
+    bool live = m < a.half;
+    uint32_t n = 0;
+    float3 h = make_float3(0.0f, 0.0f, 0.0f);
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (live) {
       int x, y, z;
-      n[j] = site_of(a, m, c, x, y, z);
-      const int xm = x == 0 ? a.Lx - 1 : x - 1, xp = x + 1 == a.Lx ? 0 : x + 1;
-      add3(h[j], a.s[n[j] - x + xm]);
-      add3(h[j], a.s[n[j] - x + xp]);
-      const int64_t sy = a.Lx;
-      add3(h[j], a.s[y == 0 ? n[j] + (a.Ly - 1) * sy : n[j] - sy]);
-      add3(h[j], a.s[y + 1 == a.Ly ? n[j] - (a.Ly - 1) * sy : n[j] + sy]);
+      n = site_of(a, m, c, x, y, z);
+      // all loads first: seven independent 16-byte reads in flight per thread
+      const int64_t sy = a.Lx, sz = (int64_t)a.Lx * a.Ly;
+      const float4 bx = a.s[n - x + (x == 0 ? a.Lx - 1 : x - 1)];
+      const float4 fx = a.s[n - x + (x + 1 == a.Lx ? 0 : x + 1)];
+      const float4 by = a.s[y == 0 ? n + (a.Ly - 1) * sy : n - sy];
+      const float4 fy = a.s[y + 1 == a.Ly ? n - (a.Ly - 1) * sy : n + sy];
+      float4 bz = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fz = bz;
       if (a.nd == 3) {
-        const int64_t sz = (int64_t)a.Lx * a.Ly;
-        add3(h[j], a.s[z == 0 ? n[j] + (a.Lz - 1) * sz : n[j] - sz]);
-        add3(h[j], a.s[z + 1 == a.Lz ? n[j] - (a.Lz - 1) * sz : n[j] + sz]);
+        bz = a.s[z == 0 ? n + (a.Lz - 1) * sz : n - sz];
+        fz = a.s[z + 1 == a.Lz ? n - (a.Lz - 1) * sz : n + sz];
       }
-      if (proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop[j])) continue;
-      need |= 1u << j;
-      tries |= 1u << (4 * j);
+      s = a.s[n];
+      add3(h, bx);
+      add3(h, fx);
+      add3(h, by);
+      add3(h, fy);
+      if (a.nd == 3) {
+        add3(h, bz);
+        add3(h, fz);
+      }
     }
-    // the rare sites whose first two tries missed the disc: one call per lane and round
-    while (__any_sync(0xffffffffu, need != 0u)) {
+    // proposal: the first call's two tries, then one more call per round for the lanes still without one
+    float3 prop = make_float3(0.0f, 0.0f, 1.0f);
+    bool need = live && !proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop);
+    for (uint32_t k = 1; __any_sync(0xffffffffu, need); ++k) {
       if (need) {
-        const int j = __ffs((int)need) - 1;
-        const uint32_t k = (tries >> (4 * j)) & 15u;
-        float3 p;
-        const bool ok = proposal_call(a.K, 4u * q + (uint32_t)j, a.sweep, c, kHeisPropose, k, a.stream_id, p);
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {  // static indices keep prop and n in registers
-          if (jj != j) continue;
-          if (ok) prop[jj] = p;
-          if (!ok && k == 7u) n[jj] = 0xffffffffu;  // sixteen misses: no move for this site
-        }
-        if (ok || k == 7u) {
-          need &= ~(1u << j);
-        } else {
-          tries += 1u << (4 * j);
+        need = !proposal_call(a.K, m, a.sweep, c, kHeisPropose, k, a.stream_id, prop);
+        if (need && k == 7u) {  // sixteen misses: no move for this site
+          need = false;
+          live = false;
         }
       }
     }
-    bool have_u = false;
-    U4 U{0, 0, 0, 0};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t m = 4u * q + (uint32_t)j;
-      if (!live || m >= a.half || n[j] == 0xffffffffu) continue;
-      const float4 s = a.s[n[j]];
-      const float dx = __fsub_rn(prop[j].x, s.x), dy = __fsub_rn(prop[j].y, s.y), dz = __fsub_rn(prop[j].z, s.z);
-      float dot = __fmul_rn(dx, h[j].x);
-      dot = __fadd_rn(dot, __fmul_rn(dy, h[j].y));
-      dot = __fadd_rn(dot, __fmul_rn(dz, h[j].z));
-      const float de = -dot;
-      bool accept = de <= 0.0f;
-      if (!accept) {
-        if (!have_u) {
-          U = philox10(q, a.sweep, c | (kHeisMetropolis << 1), a.stream_id, a.K);
-          have_u = true;
-        }
-        const float u = __fmul_rn(__uint2float_rn(u4_word(U, j) >> 8), 1.0f / 16777216.0f);
-        accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
-      }
-      if (accept) {
-        a.s[n[j]] = make_float4(prop[j].x, prop[j].y, prop[j].z, 0.0f);
-        sum[0] += (double)de;
-        sum[1] += (double)dx;
-        sum[2] += (double)dy;
-        sum[3] += (double)dz;
-      }
+    if (!live) continue;
+    const float dx = __fsub_rn(prop.x, s.x), dy = __fsub_rn(prop.y, s.y), dz = __fsub_rn(prop.z, s.z);
+    float dot = __fmul_rn(dx, h.x);
+    dot = __fadd_rn(dot, __fmul_rn(dy, h.y));
+    dot = __fadd_rn(dot, __fmul_rn(dz, h.z));
+    const float de = -dot;
+    bool accept = de <= 0.0f;
+    if (!accept) {
+      const U4 U = philox10(m >> 2, a.sweep, c | (kHeisMetropolis << 1), a.stream_id, a.K);
+      const float u = __fmul_rn(__uint2float_rn(u4_word(U, (int)(m & 3u)) >> 8), 1.0f / 16777216.0f);
+      accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
+    }
+    if (accept) {
+      a.s[n] = make_float4(prop.x, prop.y, prop.z, 0.0f);
+      sum[0] += (double)de;
+      sum[1] += (double)dx;
+      sum[2] += (double)dy;
+      sum[3] += (double)dz;
     }
   }
   block_add4(sum, a.acc);
@@ -296,7 +278,7 @@ cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float 
   a.stream_id = stream;
   a.K = philox_keys(seed);
   a.acc = acc;
-  const int grid = grid_for(((int64_t)a.half + 3) / 4, 8);
+  const int grid = grid_for((int64_t)a.half, 6);
   for (uint32_t c = 0; c < 2; ++c) {
     a.colour = c;
     k_heis_half<<<grid, 256, 0, st>>>(a);
