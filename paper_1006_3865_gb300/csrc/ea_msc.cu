@@ -387,6 +387,9 @@ struct EaBatch {
   unsigned long long* d_q2 = nullptr;  // [pairs][32] sum of q^2
   unsigned long long* d_q4 = nullptr;  // [pairs][32][2] sum of q^4 (low, high 64 bits)
   int64_t nmeas = 0;
+  long long* d_obs = nullptr;      // [S][64] per-replica E, M of spn_batch_energies
+  bool async = false;              // device memory is stream-ordered on astream (server jobs)
+  cudaStream_t astream = nullptr;
   uint64_t seed;
   double betas[32];
   uint64_t* d_words = nullptr;
@@ -411,17 +414,28 @@ size_t ea_smem(int N) { return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 +
 
 }  // namespace
 
+namespace {
+
+cudaError_t ea_alloc(EaBatch* b, void* p, size_t bytes) {
+  void** q = static_cast<void**>(p);
+  return b->async ? cudaMallocAsync(q, bytes, b->astream) : cudaMalloc(q, bytes);
+}
+
+void ea_release(EaBatch* b, void* p) {
+  if (!p) return;
+  if (b->async)
+    cudaFreeAsync(p, b->astream);
+  else
+    cudaFree(p);
+}
+
+}  // namespace
+
 void spn_ea_free(EaBatch* b) {
   if (!b) return;
-  cudaFree(b->d_words);
-  cudaFree(b->d_bonds);
-  cudaFree(b->d_tos);
-  cudaFree(b->d_xacc);
-  cudaFree(b->d_xtab);
-  cudaFree(b->d_err);
-  cudaFree(b->d_qlast);
-  cudaFree(b->d_q2);
-  cudaFree(b->d_q4);
+  for (void* p : {(void*)b->d_words, (void*)b->d_bonds, (void*)b->d_tos, (void*)b->d_xacc, (void*)b->d_xtab,
+                  (void*)b->d_err, (void*)b->d_qlast, (void*)b->d_q2, (void*)b->d_q4, (void*)b->d_obs})
+    ea_release(b, p);
   delete b;
 }
 
@@ -451,12 +465,13 @@ cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, siz
 
 }  // namespace spn
 
-extern "C" {
+namespace {
 
-int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
-                     const double* betas, int nbeta, uint64_t seed, int exchange_every) {
-  if (!out || !dims || !couplings || !betas) return ea_fail(SPN_E_ARG, "NULL argument");
-  *out = nullptr;
+// The host-side part of a batch (validation, bond bytes, exchange tables,
+// thresholds): no CUDA call, so the server builds it on worker threads.
+int ea_prepare(spn::EaPrep& p, int model, const int32_t* dims, int nsamples, const void* couplings,
+               const double* betas, int nbeta, uint64_t seed, int exchange_every) {
+  if (!dims || !couplings || !betas) return ea_fail(SPN_E_ARG, "NULL argument");
   if (model != SPN_EA3D_PMJ && model != SPN_EA2D_PMJ)
     return ea_fail(SPN_E_ARG, "batches are multi-spin coded SPN_EA3D_PMJ or SPN_EA2D_PMJ samples");
   const int nd = model == SPN_EA2D_PMJ ? 2 : 3;
@@ -477,6 +492,8 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   }
   EaBatch* b = new (std::nothrow) EaBatch;
   if (!b) return ea_fail(SPN_E_NOMEM, "host allocation failed");
+  p.b = b;
+  p.model = model;
   b->nd = nd;
   for (int d = 0; d < 3; ++d) b->L[d] = ext[d];
   b->N = (int)N;
@@ -484,40 +501,35 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   b->exchange_every = exchange_every;
   b->seed = seed;
   std::memcpy(b->betas, betas, sizeof b->betas);
-  auto bail = [&](int code, const char* msg) {
-    spn_ea_free(b);
-    return ea_fail(code, msg);
-  };
-  const int pairs = (nsamples + 1) / 2;
   // bond bytes: bit d forward J(n,d) = -1, bit 3+d backward J(n - e_d, d) = -1
-  std::vector<uint8_t> bb((size_t)nsamples * N, 0);
+  p.bb.assign((size_t)nsamples * N, 0);
   const int64_t nw = (N + 63) / 64;
+  const int64_t sy = ext[0], sz = (int64_t)ext[0] * ext[1];
   const uint64_t* J = static_cast<const uint64_t*>(couplings);
+  auto bit = [](const uint64_t* Jd, int64_t i) { return (uint32_t)((Jd[i >> 6] >> (i & 63)) & 1u); };
   for (int s = 0; s < nsamples; ++s) {
-    for (int64_t n = 0; n < N; ++n) {
-      const int x = (int)(n % ext[0]), y = (int)((n / ext[0]) % ext[1]), z = (int)(n / ((int64_t)ext[0] * ext[1]));
-      const int64_t back[3] = {n - x + (x == 0 ? ext[0] - 1 : x - 1),
-                               n + (int64_t)((y == 0 ? ext[1] - 1 : y - 1) - y) * ext[0],
-                               n + (int64_t)((z == 0 ? ext[2] - 1 : z - 1) - z) * ext[0] * ext[1]};
-      uint8_t v = 0;
-      for (int d = 0; d < nd; ++d) {
-        const uint64_t* Jd = J + ((int64_t)s * nd + d) * nw;
-        if ((Jd[n >> 6] >> (n & 63)) & 1) v |= (uint8_t)(1u << d);
-        if ((Jd[back[d] >> 6] >> (back[d] & 63)) & 1) v |= (uint8_t)(8u << d);
-      }
-      bb[(size_t)s * N + n] = v;
-    }
+    const uint64_t* Js = J + (int64_t)s * nd * nw;
+    uint8_t* out = &p.bb[(size_t)s * N];
+    int64_t n = 0;
+    for (int z = 0; z < ext[2]; ++z)
+      for (int y = 0; y < ext[1]; ++y)
+        for (int x = 0; x < ext[0]; ++x, ++n) {
+          const int64_t back[3] = {x == 0 ? n + ext[0] - 1 : n - 1, y == 0 ? n + (ext[1] - 1) * sy : n - sy,
+                                   z == 0 ? n + (ext[2] - 1) * sz : n - sz};
+          uint32_t v = 0;
+          for (int d = 0; d < nd; ++d) v |= (bit(Js + d * nw, n) << d) | (bit(Js + d * nw, back[d]) << (3 + d));
+          out[n] = (uint8_t)v;
+        }
   }
   b->pairs_share_bonds = nsamples % 2 == 0;
-  for (int p = 0; b->pairs_share_bonds && p < nsamples / 2; ++p)
-    b->pairs_share_bonds = std::memcmp(&bb[(size_t)(2 * p) * N], &bb[(size_t)(2 * p + 1) * N], (size_t)N) == 0;
+  for (int q = 0; b->pairs_share_bonds && q < nsamples / 2; ++q)
+    b->pairs_share_bonds = std::memcmp(&p.bb[(size_t)(2 * q) * N], &p.bb[(size_t)(2 * q + 1) * N], (size_t)N) == 0;
   // exchange tables: pair k, d = 1 .. len: floor(exp((b_k - b_k+1) * (-2d)) 2^32)
-  std::vector<uint32_t> tab;
   spn::EaArgs& A = b->args;
   A.xalways = 0;
   for (int k = 0; k < 31; ++k) {
     const double db = betas[k] - betas[k + 1];
-    A.xoff[k] = (int)tab.size();
+    A.xoff[k] = (int)p.tab.size();
     A.xlen[k] = 0;
     if (db == 0.0) {
       A.xalways |= 1u << k;
@@ -527,52 +539,73 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
       const double D = db * (double)(-2 * d);
       const uint64_t t = (uint64_t)std::floor(std::exp(D) * 4294967296.0);
       if (t == 0) break;
-      tab.push_back((uint32_t)t);
-      if (tab.size() > (size_t)1 << 22) return bail(SPN_E_ARG, "ladder spacing too small for the exchange tables");
+      p.tab.push_back((uint32_t)t);
+      if (p.tab.size() > (size_t)1 << 22) return ea_fail(SPN_E_ARG, "ladder spacing too small for the exchange tables");
     }
-    A.xlen[k] = (int)tab.size() - A.xoff[k];
+    A.xlen[k] = (int)p.tab.size() - A.xoff[k];
   }
-  A.xoff[31] = (int)tab.size();
+  A.xoff[31] = (int)p.tab.size();
   A.xlen[31] = 0;
-  if (tab.empty()) tab.push_back(0);
+  if (p.tab.empty()) p.tab.push_back(0);
   for (int q = 1; q <= 3; ++q)
     for (int t = 0; t < 32; ++t) {
       const uint64_t v = spn::boltzmann_threshold(betas[t], 4 * q);
       A.thr[q - 1][t] = (uint32_t)std::min<uint64_t>(v, 0xffffffffull);  // < 2^32 for beta >= 1e-6
     }
+  return SPN_OK;
+}
+
+// The device part: memory, copies and the hot start, ordered on st.  async:
+// nothing waits for the device (server admissions); otherwise the call
+// returns with the batch initialised.  Takes the batch out of p.
+int ea_upload(spn_handle* out, spn::EaPrep& p, cudaStream_t st, bool async) {
+  *out = nullptr;
+  EaBatch* b = p.b;
+  p.b = nullptr;
+  b->async = async;
+  b->astream = st;
+  auto bail = [&](int code, const char* msg) {
+    spn_ea_free(b);
+    return ea_fail(code, msg);
+  };
+  const int nsamples = b->nsamples, pairs = (nsamples + 1) / 2;
+  const int64_t N = b->N;
+  spn::EaArgs& A = b->args;
   cudaError_t e;
-  if ((e = cudaMalloc(&b->d_words, (size_t)pairs * N * 8)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
-  if ((e = cudaMalloc(&b->d_bonds, bb.size())) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
-  if ((e = cudaMalloc(&b->d_tos, (size_t)nsamples * 32)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
-  if ((e = cudaMalloc(&b->d_xacc, (size_t)nsamples * 32 * 8)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
-  if ((e = cudaMalloc(&b->d_xtab, tab.size() * 4)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
-  if ((e = cudaMalloc(&b->d_err, 4)) != cudaSuccess) return bail(SPN_E_NOMEM, "cudaMalloc");
+  if (ea_alloc(b, &b->d_words, (size_t)pairs * N * 8) != cudaSuccess || ea_alloc(b, &b->d_bonds, p.bb.size()) ||
+      ea_alloc(b, &b->d_tos, (size_t)nsamples * 32) || ea_alloc(b, &b->d_xacc, (size_t)nsamples * 32 * 8) ||
+      ea_alloc(b, &b->d_xtab, p.tab.size() * 4) || ea_alloc(b, &b->d_err, 4) ||
+      ea_alloc(b, &b->d_obs, (size_t)nsamples * 64 * 8))
+    return bail(SPN_E_NOMEM, "allocating the batch");
   std::vector<uint8_t> tos((size_t)nsamples * 32);
   for (size_t i = 0; i < tos.size(); ++i) tos[i] = (uint8_t)(i % 32);
-  if (cudaMemcpy(b->d_bonds, bb.data(), bb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_tos, tos.data(), tos.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_xtab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(b->d_xacc, 0, (size_t)nsamples * 32 * 8) != cudaSuccess ||
-      cudaMemset(b->d_words, 0, (size_t)pairs * N * 8) != cudaSuccess || cudaMemset(b->d_err, 0, 4) != cudaSuccess)
+  // host-to-device copies from pageable memory return once the data is staged
+  if (cudaMemcpyAsync(b->d_bonds, p.bb.data(), p.bb.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_tos, tos.data(), tos.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_xtab, p.tab.data(), p.tab.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_xacc, 0, (size_t)nsamples * 32 * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_words, 0, (size_t)pairs * N * 8, st) != cudaSuccess ||
+      cudaMemsetAsync(b->d_err, 0, 4, st) != cudaSuccess)
     return bail(SPN_E_CUDA, "copying the batch to the device");
-  const spn::PhiloxKeys K = spn::philox_keys(seed);
-  spn::k_ea_init<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsamples * N / 256 + 1, spn::device_sm_count() * 32)), 256>>>(
-      b->d_words, ext[0], ext[1], (int)N, nsamples, K);
+  const spn::PhiloxKeys K = spn::philox_keys(b->seed);
+  spn::k_ea_init<<<(int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nsamples * N / 256 + 1, spn::device_sm_count() * 32)), 256, 0, st>>>(
+      b->d_words, b->L[0], b->L[1], (int)N, nsamples, K);
   spn::count_launches(1);
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(SPN_E_CUDA, cudaGetErrorString(e));
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(SPN_E_CUDA, cudaGetErrorString(e));
+  if (!async && (e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(SPN_E_CUDA, cudaGetErrorString(e));
   A.words = b->d_words;
   A.bonds = b->d_bonds;
   A.temp_of_slot = b->d_tos;
   A.xacc = b->d_xacc;
   A.xtab = b->d_xtab;
-  A.nd = nd;
-  A.Lx = ext[0];
-  A.Ly = ext[1];
-  A.Lz = ext[2];
+  A.nd = b->nd;
+  A.Lx = b->L[0];
+  A.Ly = b->L[1];
+  A.Lz = b->L[2];
   A.N = (int)N;
-  A.div_h = spn::fastdiv((uint32_t)(ext[0] / 2));
-  A.div_ly = spn::fastdiv((uint32_t)ext[1]);
-  A.exchange_every = exchange_every;
+  A.div_h = spn::fastdiv((uint32_t)(b->L[0] / 2));
+  A.div_ly = spn::fastdiv((uint32_t)b->L[1]);
+  A.exchange_every = b->exchange_every;
   A.nsamples = nsamples;
   A.K = K;
   A.err = b->d_err;
@@ -580,11 +613,44 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   b->threads = N >= 16384 ? 1024 : (N >= 4096 ? 512 : 256);
   spn_ctx* h = new (std::nothrow) spn_ctx;
   if (!h) return bail(SPN_E_NOMEM, "host allocation failed");
-  h->model = model;
-  h->seed = seed;
+  h->model = p.model;
+  h->seed = b->seed;
   h->ea = b;
+  h->st = st;
   *out = h;
   return SPN_OK;
+}
+
+int create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
+                 const double* betas, int nbeta, uint64_t seed, int exchange_every, cudaStream_t st, bool async) {
+  if (!out) return ea_fail(SPN_E_ARG, "NULL argument");
+  *out = nullptr;
+  spn::EaPrep p;
+  const int rc = ea_prepare(p, model, dims, nsamples, couplings, betas, nbeta, seed, exchange_every);
+  if (rc) return rc;
+  return ea_upload(out, p, st, async);
+}
+
+}  // namespace
+
+namespace spn {
+
+EaPrep::~EaPrep() { spn_ea_free(b); }
+
+int ea_prepare_single(EaPrep& p, int model, const int32_t* dims, const void* couplings, const double* betas,
+                      uint64_t seed, int exchange_every) {
+  return ea_prepare(p, model, dims, 1, couplings, betas, 32, seed, exchange_every);
+}
+
+int ea_upload_async(spn_handle* out, EaPrep& p, cudaStream_t st) { return ea_upload(out, p, st, true); }
+
+}  // namespace spn
+
+extern "C" {
+
+int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
+                     const double* betas, int nbeta, uint64_t seed, int exchange_every) {
+  return create_batch(out, model, dims, nsamples, couplings, betas, nbeta, seed, exchange_every, nullptr, false);
 }
 
 int spn_batch_sweep(spn_handle h, int64_t nsweeps) {
@@ -670,19 +736,14 @@ int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count) {
   if (!h || !h->ea || !E || !M) return ea_fail(SPN_E_ARG, "bad arguments");
   EaBatch* b = h->ea;
   if (count != (size_t)b->nsamples * 32) return ea_fail(SPN_E_ARG, "count must be nsamples * 32");
-  long long *dE = nullptr, *dM = nullptr;
-  if (cudaMalloc(&dE, count * 8) != cudaSuccess || cudaMalloc(&dM, count * 8) != cudaSuccess) {
-    cudaFree(dE);
-    return ea_fail(SPN_E_NOMEM, "cudaMalloc");
-  }
+  long long* dE = b->d_obs;
+  long long* dM = b->d_obs + count;
   spn::k_ea_observables<<<b->nsamples, 256, 0, h->st>>>(b->d_words, b->d_bonds, b->nd, b->L[0], b->L[1], b->L[2], b->N, dE,
                                                        dM);
   spn::count_launches(1);
-  cudaError_t e = cudaStreamSynchronize(h->st);
-  if (e == cudaSuccess) e = cudaMemcpy(E, dE, count * 8, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(M, dM, count * 8, cudaMemcpyDeviceToHost);
-  cudaFree(dE);
-  cudaFree(dM);
+  cudaError_t e = cudaMemcpyAsync(E, dE, count * 8, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(M, dM, count * 8, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   return e == cudaSuccess ? SPN_OK : ea_fail(SPN_E_CUDA, cudaGetErrorString(e));
 }
 
@@ -702,8 +763,8 @@ int spn_batch_measure_overlap(spn_handle h) {
     return ea_fail(SPN_E_STATE, "overlaps need an even number of samples with samples 2p, 2p+1 sharing couplings");
   const size_t n = (size_t)b->nsamples / 2 * 32;
   if (!b->d_qlast) {
-    if (cudaMalloc(&b->d_qlast, n * 8) != cudaSuccess || cudaMalloc(&b->d_q2, n * 8) != cudaSuccess ||
-        cudaMalloc(&b->d_q4, n * 16) != cudaSuccess)
+    if (ea_alloc(b, &b->d_qlast, n * 8) != cudaSuccess || ea_alloc(b, &b->d_q2, n * 8) != cudaSuccess ||
+        ea_alloc(b, &b->d_q4, n * 16) != cudaSuccess)
       return ea_fail(SPN_E_NOMEM, "cudaMalloc(overlap)");
     if (cudaMemsetAsync(b->d_qlast, 0, n * 8, h->st) != cudaSuccess ||
         cudaMemsetAsync(b->d_q2, 0, n * 8, h->st) != cudaSuccess ||

@@ -74,6 +74,8 @@ struct Job {
   int8_t* d_p1 = nullptr;  // pitched ping-pong partner
   unsigned long long* d_acc = nullptr;  // window deltas / start E, M
   spn_handle ea = nullptr;
+  std::unique_ptr<spn::EaPrep> prep;  // EA: host part built on a worker thread before admission
+  int prep_rc = SPN_OK;
   int stream_slot = 0;
   // results
   int64_t E = 0, M = 0;
@@ -97,6 +99,10 @@ struct spn_server_ctx {
   std::thread worker;
   int device = 0;
   cudaStream_t main = nullptr;
+  // admissions and finished-job read-back run here while a round executes; a
+  // round starts after the admissions enqueued before it (aux_ev)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t aux_ev = nullptr;
   std::vector<cudaStream_t> pool;
   std::vector<cudaEvent_t> pool_done;
   cudaEvent_t fork = nullptr;
@@ -114,6 +120,7 @@ struct spn_server_ctx {
   std::atomic<unsigned long long> rounds{0};
   double busy = 0;
   std::FILE* trace = nullptr;  // per-round log when SPN_SERVER_TRACE names a file
+  int* h_err = nullptr;        // pinned: the round's device error word, read back with the round
 };
 
 namespace {
@@ -125,12 +132,14 @@ size_t job_bytes(const Job& j) {
   return b;
 }
 
+// A job's device memory goes back in stream order on aux: its last kernels ran
+// in a round that has completed, or on aux itself (read-back).
 void release(spn_server_ctx* s, Job& j) {
-  if (j.d_spins) cudaFreeAsync(j.d_spins, s->main);
-  if (j.d_scratch) cudaFreeAsync(j.d_scratch, s->main);
-  if (j.d_p0) cudaFreeAsync(j.d_p0, s->main);
-  if (j.d_p1) cudaFreeAsync(j.d_p1, s->main);
-  if (j.d_acc) cudaFreeAsync(j.d_acc, s->main);
+  if (j.d_spins) cudaFreeAsync(j.d_spins, s->aux);
+  if (j.d_scratch) cudaFreeAsync(j.d_scratch, s->aux);
+  if (j.d_p0) cudaFreeAsync(j.d_p0, s->aux);
+  if (j.d_p1) cudaFreeAsync(j.d_p1, s->aux);
+  if (j.d_acc) cudaFreeAsync(j.d_acc, s->aux);
   j.d_spins = j.d_scratch = j.d_p0 = j.d_p1 = nullptr;
   j.d_acc = nullptr;
   if (j.ea) {
@@ -139,14 +148,15 @@ void release(spn_server_ctx* s, Job& j) {
   }
 }
 
-// Allocate and initialise an admitted job (scheduler thread).
+// Allocate and initialise an admitted job (scheduler thread), stream-ordered on
+// aux: nothing here waits for the device.
 int admit(spn_server_ctx* s, Job& j) {
   const spn_request& r = j.req;
   if (r.model == SPN_EA3D_PMJ) {
-    int rc = spn_create_batch(&j.ea, SPN_EA3D_PMJ, r.dims, 1, j.bonds.data(), j.betas.data(), 32, r.seed,
-                              r.exchange_every);
-    if (rc) return rc;
-    return spn_set_stream(j.ea, s->pool[j.stream_slot]);
+    if (j.prep_rc) return j.prep_rc;
+    const int rc = spn::ea_upload_async(&j.ea, *j.prep, s->aux);
+    j.prep.reset();
+    return rc;
   }
   spn::Lattice g;
   g.nd = j.nd;
@@ -154,22 +164,23 @@ int admit(spn_server_ctx* s, Job& j) {
   g.Ly = r.dims[1];
   g.Lz = j.nd == 3 ? r.dims[2] : 1;
   g.N = j.N;
-  if (cudaMallocAsync(&j.d_spins, (size_t)j.N, s->main) != cudaSuccess) return SPN_E_NOMEM;
-  if (cudaMallocAsync(&j.d_acc, 4096, s->main) != cudaSuccess) return SPN_E_NOMEM;
-  if (spn::launch_init_hot(g, j.d_spins, r.seed, r.stream, s->main) != cudaSuccess) return SPN_E_CUDA;
+  if (cudaMallocAsync(&j.d_spins, (size_t)j.N, s->aux) != cudaSuccess) return SPN_E_NOMEM;
+  if (cudaMallocAsync(&j.d_acc, 4096, s->aux) != cudaSuccess) return SPN_E_NOMEM;
+  if (spn::launch_init_hot(g, j.d_spins, r.seed, r.stream, s->aux) != cudaSuccess) return SPN_E_CUDA;
   if (j.streaming) {
     const size_t nrow = (size_t)(j.N / g.Lx), pb = (size_t)j.pitch * nrow;
-    if (cudaMallocAsync(&j.d_p0, pb, s->main) != cudaSuccess || cudaMallocAsync(&j.d_p1, pb, s->main) != cudaSuccess)
+    if (cudaMallocAsync(&j.d_p0, pb, s->aux) != cudaSuccess || cudaMallocAsync(&j.d_p1, pb, s->aux) != cudaSuccess)
       return SPN_E_NOMEM;
-    if (cudaMemsetAsync(j.d_p0, 1, pb, s->main) != cudaSuccess ||
+    if (cudaMemsetAsync(j.d_p0, 1, pb, s->aux) != cudaSuccess ||
         cudaMemcpy2DAsync(j.d_p0, (size_t)j.pitch, j.d_spins, (size_t)g.Lx, (size_t)g.Lx, nrow, cudaMemcpyDeviceToDevice,
-                          s->main) != cudaSuccess)
+                          s->aux) != cudaSuccess)
       return SPN_E_CUDA;
   }
   return SPN_OK;
 }
 
-// Final E, M and the host copies of a finished job.
+// Final E, M and the host copies of a finished job (its rounds have completed;
+// the read-back is ordered on aux, so it overlaps the next round).
 int finish(spn_server_ctx* s, Job& j) {
   if (j.ea) {
     const size_t n = (size_t)j.N;
@@ -195,23 +206,26 @@ int finish(spn_server_ctx* s, Job& j) {
   g.N = j.N;
   if (j.streaming &&
       cudaMemcpy2DAsync(j.d_spins, (size_t)g.Lx, j.d_p0, (size_t)j.pitch, (size_t)g.Lx, (size_t)(j.N / g.Lx),
-                        cudaMemcpyDeviceToDevice, s->main) != cudaSuccess)
+                        cudaMemcpyDeviceToDevice, s->aux) != cudaSuccess)
     return SPN_E_CUDA;
-  if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, s->main) != cudaSuccess) return SPN_E_CUDA;
+  if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, s->aux) != cudaSuccess) return SPN_E_CUDA;
   unsigned long long em[2];
   j.spins.resize((size_t)j.N);
-  if (cudaMemcpyAsync(em, j.d_acc, 16, cudaMemcpyDeviceToHost, s->main) != cudaSuccess ||
-      cudaMemcpyAsync(j.spins.data(), j.d_spins, (size_t)j.N, cudaMemcpyDeviceToHost, s->main) != cudaSuccess ||
-      cudaStreamSynchronize(s->main) != cudaSuccess)
+  if (cudaMemcpyAsync(em, j.d_acc, 16, cudaMemcpyDeviceToHost, s->aux) != cudaSuccess ||
+      cudaMemcpyAsync(j.spins.data(), j.d_spins, (size_t)j.N, cudaMemcpyDeviceToHost, s->aux) != cudaSuccess ||
+      cudaStreamSynchronize(s->aux) != cudaSuccess)
     return SPN_E_CUDA;
   j.E = (int64_t)em[0];
   j.M = (int64_t)em[1];
   return SPN_OK;
 }
 
-// One round: a window of sweeps for every active job.
-int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
+// One round: a window of sweeps for every active job.  round_launch enqueues it
+// (after the admissions on aux) and returns; round_wait waits for it.
+int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   cudaError_t e;
+  if (cudaEventRecord(s->aux_ev, s->aux) != cudaSuccess || cudaStreamWaitEvent(s->main, s->aux_ev, 0) != cudaSuccess)
+    return SPN_E_CUDA;
   if ((e = cudaEventRecord(s->fork, s->main)) != cudaSuccess) return SPN_E_CUDA;
   for (cudaStream_t p : s->pool) cudaStreamWaitEvent(p, s->fork, 0);
   // resident jobs: one persistent launch per (dimension, cluster size), all
@@ -369,29 +383,49 @@ int run_round(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
     cudaEventRecord(s->pool_done[p], s->pool[p]);
     cudaStreamWaitEvent(s->main, s->pool_done[p], 0);
   }
-  int err = 0;
-  if (cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->main) != cudaSuccess ||
-      (e = cudaStreamSynchronize(s->main)) != cudaSuccess)
+  if (cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->main) != cudaSuccess)
     return SPN_E_CUDA;
-  if (err) return SPN_E_TIMEOUT;  // a bounded device wait ran out
+  return SPN_OK;
+}
+
+int round_wait(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
+  if (cudaStreamSynchronize(s->main) != cudaSuccess) return SPN_E_CUDA;
+  if (*s->h_err) return SPN_E_TIMEOUT;  // a bounded device wait ran out
   std::lock_guard<std::mutex> lock(s->mu);
-  for (size_t k = 0; k < act.size(); ++k) {
-    Job& j = *act[k];
-    const int64_t w = win[k];
-    j.done += w;
-    s->attempts += (unsigned long long)(j.N * w * (j.ea ? 32 : 1));
+  for (auto& jp : act) {
+    Job& j = *jp;
+    j.done += j.window;
+    s->attempts += (unsigned long long)(j.N * j.window * (j.ea ? 32 : 1));
   }
   return SPN_OK;
 }
 
+// Mark a finished (or failed) job done and give its bytes back.
+void retire(spn_server_ctx* s, const std::shared_ptr<Job>& j, int rc) {
+  int frc = rc ? rc : finish(s, *j);
+  release(s, *j);
+  std::lock_guard<std::mutex> lock(s->mu);
+  j->status = frc;
+  j->state = frc ? kFailed : kDone;
+  j->t_done = now_s();
+  s->used -= j->bytes;
+}
+
+// The scheduler thread.  Each iteration launches a round over the active jobs,
+// then, while it runs, reads back the jobs the previous round completed and
+// admits queued jobs (on aux, so nothing waits for the round), and only then
+// waits for the round.  Newly admitted jobs join the next round.
 void scheduler(spn_server_ctx* s) {
   cudaSetDevice(s->device);
+  std::vector<std::shared_ptr<Job>> completed;  // finished in the last round, not yet read back
   while (true) {
-    std::vector<std::shared_ptr<Job>> admitted_now;
+    std::vector<std::shared_ptr<Job>> admitted_now, act;
     {
       std::unique_lock<std::mutex> lock(s->mu);
-      s->cv.wait(lock, [&] { return s->stop || !s->pending.empty() || !s->active.empty(); });
-      if (s->stop && s->pending.empty() && s->active.empty()) return;
+      s->cv.wait(lock, [&] {
+        return s->stop || !s->pending.empty() || !s->active.empty() || !completed.empty();
+      });
+      if (s->stop && s->pending.empty() && s->active.empty() && completed.empty()) return;
       // admission against the budget, first come first served
       while (!s->pending.empty()) {
         std::shared_ptr<Job> j = s->pending.front();
@@ -402,56 +436,75 @@ void scheduler(spn_server_ctx* s) {
         j->t_admit = now_s();
         admitted_now.push_back(j);
       }
-    }
-    for (auto& j : admitted_now) {
-      j->stream_slot = (int)(j->ticket % s->pool.size());
-      int rc = admit(s, *j);
-      std::lock_guard<std::mutex> lock(s->mu);
-      if (rc) {
-        release(s, *j);
-        j->state = kFailed;
-        j->status = rc;
-        j->t_done = now_s();
-        s->used -= j->bytes;
-      } else {
-        s->active.push_back(j);
-      }
-    }
-    std::vector<std::shared_ptr<Job>> act;
-    {
-      std::lock_guard<std::mutex> lock(s->mu);
       act = s->active;
     }
-    if (act.empty()) continue;
     const double t0 = now_s();
-    int rc = run_round(s, act);
-    const double t1 = now_s();
-    s->busy += t1 - t0;
-    s->rounds += 1;
-    if (s->trace) {  // one line per round: start, seconds, jobs, attempts, resident / streaming / EA / other jobs
-      int nr = 0, ns = 0, ne = 0, no = 0;
-      long long att = 0;
-      for (auto& j : act) {
-        att += (long long)j->N * j->window * (j->ea ? 32 : 1);
-        if (j->ea) ++ne; else if (j->cs > 0) ++nr; else if (j->streaming) ++ns; else ++no;
+    int rc = SPN_OK;
+    if (!act.empty()) rc = round_launch(s, act);
+    // host work that overlaps the round
+    for (auto& j : completed) retire(s, j, SPN_OK);
+    completed.clear();
+    // the host part of EA admissions (bond bytes, exact exchange tables) on worker threads
+    {
+      std::vector<Job*> ea;
+      for (auto& j : admitted_now)
+        if (j->req.model == SPN_EA3D_PMJ) ea.push_back(j.get());
+      auto prepare = [&](size_t k) {
+        Job& j = *ea[k];
+        j.prep.reset(new spn::EaPrep);
+        j.prep_rc = spn::ea_prepare_single(*j.prep, SPN_EA3D_PMJ, j.req.dims, j.bonds.data(), j.betas.data(),
+                                           j.req.seed, j.req.exchange_every);
+      };
+      const size_t nt = std::min<size_t>(ea.size(), std::max(1u, std::min(8u, std::thread::hardware_concurrency())));
+      if (nt <= 1) {
+        for (size_t k = 0; k < ea.size(); ++k) prepare(k);
+      } else {
+        std::atomic<size_t> next{0};
+        std::vector<std::thread> workers;
+        for (size_t t = 0; t < nt; ++t)
+          workers.emplace_back([&] {
+            for (size_t k; (k = next.fetch_add(1)) < ea.size();) prepare(k);
+          });
+        for (auto& w : workers) w.join();
       }
-      std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d\n", t0, t1 - t0, act.size(), att, nr, ns, ne, no);
-      std::fflush(s->trace);
+    }
+    std::vector<std::shared_ptr<Job>> joined;
+    for (auto& j : admitted_now) {
+      j->stream_slot = (int)(j->ticket % s->pool.size());
+      const int arc = admit(s, *j);
+      if (arc) {
+        retire(s, j, arc);
+      } else {
+        joined.push_back(j);
+      }
+    }
+    if (!act.empty() && rc == SPN_OK) rc = round_wait(s, act);
+    const double t1 = now_s();
+    if (!act.empty()) {
+      s->busy += t1 - t0;
+      s->rounds += 1;
+      if (s->trace) {  // one line per round: start, seconds, jobs, attempts, resident / streaming / EA / other jobs
+        int nr = 0, ns = 0, ne = 0, no = 0;
+        long long att = 0;
+        for (auto& j : act) {
+          att += (long long)j->N * j->window * (j->ea ? 32 : 1);
+          if (j->ea) ++ne; else if (j->cs > 0) ++nr; else if (j->streaming) ++ns; else ++no;
+        }
+        std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d\n", t0, t1 - t0, act.size(), att, nr, ns, ne, no);
+        std::fflush(s->trace);
+      }
     }
     std::vector<std::shared_ptr<Job>> still;
     for (auto& j : act) {
-      if (rc == SPN_OK && j->done < j->req.nsweeps) {
+      if (rc != SPN_OK) {
+        retire(s, j, rc);
+      } else if (j->done < j->req.nsweeps) {
         still.push_back(j);
-        continue;
+      } else {
+        completed.push_back(j);  // read back while the next round runs
       }
-      int frc = rc ? rc : finish(s, *j);
-      release(s, *j);
-      std::lock_guard<std::mutex> lock(s->mu);
-      j->status = frc;
-      j->state = frc ? kFailed : kDone;
-      j->t_done = now_s();
-      s->used -= j->bytes;
     }
+    for (auto& j : joined) still.push_back(j);
     std::lock_guard<std::mutex> lock(s->mu);
     s->active = still;
   }
@@ -469,6 +522,9 @@ int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
   s->budget = hbm_budget_bytes;
   cudaGetDevice(&s->device);
   if (cudaStreamCreateWithFlags(&s->main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->aux_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&s->h_err, sizeof(int)) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaMalloc(&s->d_err, 4) != cudaSuccess || cudaMemset(s->d_err, 0, 4) != cudaSuccess) {
     delete s;
@@ -610,6 +666,7 @@ int spn_server_destroy(spn_server s) {
   if (s->worker.joinable()) s->worker.join();
   for (auto& kv : s->all) release(s, *kv.second);
   cudaStreamSynchronize(s->main);
+  cudaStreamSynchronize(s->aux);
   for (size_t i = 0; i < s->pool.size(); ++i) {
     cudaStreamDestroy(s->pool[i]);
     cudaEventDestroy(s->pool_done[i]);
@@ -620,8 +677,11 @@ int spn_server_destroy(spn_server s) {
   cudaFree(s->d_counters);
   cudaFree(s->d_err);
   cudaEventDestroy(s->fork);
+  cudaEventDestroy(s->aux_ev);
+  cudaFreeHost(s->h_err);
   if (s->trace) std::fclose(s->trace);
   cudaStreamDestroy(s->main);
+  cudaStreamDestroy(s->aux);
   delete s;
   return SPN_OK;
 }

@@ -190,17 +190,12 @@ void destroy(spn_ctx* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   spn_ea_free(h->ea);
   spn::heis_free(h->heis);
-  cudaFree(h->spins[0]);
-  cudaFree(h->spins[1]);
-  cudaFree(h->staged[0]);
-  cudaFree(h->staged[1]);
-  cudaFree(h->packed[0]);
-  cudaFree(h->packed[1]);
-  cudaFree(h->d_bonds);
-  cudaFree(h->d_acc);
-  cudaFree(h->d_err);
-  cudaFree(h->d_bad);
-  cudaFree(h->d_obs);
+  // only what was allocated: a batch handle owns none of these, and its frees
+  // must not wait for the device
+  for (void* p : {(void*)h->spins[0], (void*)h->spins[1], (void*)h->staged[0], (void*)h->staged[1],
+                  (void*)h->packed[0], (void*)h->packed[1], (void*)h->d_bonds, (void*)h->d_acc, (void*)h->d_err,
+                  (void*)h->d_bad, (void*)h->d_obs})
+    if (p) cudaFree(p);
   delete h;
 }
 

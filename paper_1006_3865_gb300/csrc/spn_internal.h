@@ -10,6 +10,7 @@
 #include "philox.cuh"
 
 struct spn_ctx;  // the handle (global, as in spn.h)
+struct EaBatch;  // forward: multi-spin coded EA batch (ea_msc.cu)
 
 namespace spn {
 
@@ -145,6 +146,20 @@ struct EaArgs {
 // advances), and one launch running many such blocks, one CTA each.
 int ea_window_args(struct spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* threads);
 cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, size_t smem, cudaStream_t st);
+// Server admissions of single-sample EA batches in two parts: the host part
+// (validation, bond bytes, exchange tables; no CUDA call, any thread) and the
+// device part, whose allocations, copies and hot start are ordered on st and
+// never wait for the device (the handle's stream is st).
+struct EaPrep {
+  int model = 0;
+  struct ::EaBatch* b = nullptr;  // host fields filled; owned until uploaded
+  std::vector<uint8_t> bb;         // per-site bond bytes
+  std::vector<uint32_t> tab;       // exchange tables
+  ~EaPrep();
+};
+int ea_prepare_single(EaPrep& p, int model, const int32_t* dims, const void* couplings, const double* betas,
+                      uint64_t seed, int exchange_every);
+int ea_upload_async(struct ::spn_ctx** out, EaPrep& p, cudaStream_t st);
 
 }  // namespace spn
 
