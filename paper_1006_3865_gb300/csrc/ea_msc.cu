@@ -283,28 +283,55 @@ __global__ void k_ea_init(uint64_t* words, int Lx, int Ly, int N, int nsamples, 
   }
 }
 
-// per-replica E and M by slot: E = 2 U - nd N (U unsatisfied forward bonds), M = N - 2 (#spins -1)
-__global__ void k_ea_observables(const uint64_t* words, const uint8_t* bonds, int nd, int Lx, int Ly, int Lz, int N,
-                                 long long* E, long long* M) {
+// per-replica E and M by slot: E = 2 U - nd N (U unsatisfied forward bonds), M = N - 2 (#spins -1).
+// A thread adds its sites' unsatisfied-bond bits and spin bits of all 32
+// replicas into bit-sliced counters (16 planes each), then the per-replica
+// totals are read off the planes and reduced over the CTA.  One CTA per sample.
+__device__ __forceinline__ void vadd16(uint32_t (&c)[16], uint32_t w) {
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    if (!w) break;
+    const uint32_t t = c[b] & w;
+    c[b] ^= w;
+    w = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ea_observables(const uint64_t* words, const uint8_t* bonds, int nd, int Lx,
+                                                        int Ly, int Lz, int N, long long* E, long long* M) {
   __shared__ unsigned long long su[32], sm[32];
-  const int sample = blockIdx.x, tid = threadIdx.x;
+  const int sample = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
   if (tid < 32) su[tid] = sm[tid] = 0;
   __syncthreads();
   const uint32_t* w = reinterpret_cast<const uint32_t*>(words + (size_t)(sample >> 1) * N) + (sample & 1);
   const uint8_t* bb = bonds + (size_t)sample * N;
+  uint32_t cu[16], cm[16];
+#pragma unroll
+  for (int b = 0; b < 16; ++b) cu[b] = cm[b] = 0;
+  // at most 16 bits per counter: the threads of a CTA cover N <= 2^20 sites with nd <= 3 bonds each
   for (int n = tid; n < N; n += blockDim.x) {
     const int x = n % Lx, r = n / Lx, y = r % Ly, z = r / Ly;
     const uint32_t s = w[2 * (size_t)n];
     const int np[3] = {n - x + (x + 1 == Lx ? 0 : x + 1), n + ((y + 1 == Ly ? 0 : y + 1) - y) * Lx,
                        n + ((z + 1 == Lz ? 0 : z + 1) - z) * Lx * Ly};
-    for (int j = 0; j < 32; ++j) {
-      unsigned long long un = 0;
-      for (int d = 0; d < nd; ++d) {
-        const uint32_t bit = ((s ^ w[2 * (size_t)np[d]]) >> j) & 1u;
-        un += bit ^ ((bb[n] >> d) & 1u);
-      }
-      if (un) atomicAdd(&su[j], un);
-      if ((s >> j) & 1u) atomicAdd(&sm[j], 1ull);
+    for (int d = 0; d < nd; ++d) vadd16(cu, s ^ w[2 * (size_t)np[d]] ^ (0u - ((bb[n] >> d) & 1u)));
+    vadd16(cm, s);
+  }
+  for (int j = 0; j < 32; ++j) {
+    unsigned int u = 0, m = 0;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      u |= ((cu[b] >> j) & 1u) << b;
+      m |= ((cm[b] >> j) & 1u) << b;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      u += __shfl_xor_sync(0xffffffffu, u, o);
+      m += __shfl_xor_sync(0xffffffffu, m, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&su[j], (unsigned long long)u);
+      atomicAdd(&sm[j], (unsigned long long)m);
     }
   }
   __syncthreads();

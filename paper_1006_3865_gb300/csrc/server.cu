@@ -411,10 +411,10 @@ void retire(spn_server_ctx* s, const std::shared_ptr<Job>& j, int rc) {
   s->used -= j->bytes;
 }
 
-// The scheduler thread.  Each iteration launches a round over the active jobs,
-// then, while it runs, reads back the jobs the previous round completed and
-// admits queued jobs (on aux, so nothing waits for the round), and only then
-// waits for the round.  Newly admitted jobs join the next round.
+// The scheduler thread.  Each iteration reads back the jobs the previous round
+// completed, launches a round over the active jobs, admits queued jobs while
+// it runs (on aux, so nothing waits for the round), and then waits for the
+// round.  Newly admitted jobs join the next round.
 void scheduler(spn_server_ctx* s) {
   cudaSetDevice(s->device);
   std::vector<std::shared_ptr<Job>> completed;  // finished in the last round, not yet read back
@@ -438,12 +438,15 @@ void scheduler(spn_server_ctx* s) {
       }
       act = s->active;
     }
+    // read back the jobs the last round completed while the device is idle: the
+    // read-back launches a small kernel, which would wait behind a running round
+    for (auto& j : completed) retire(s, j, SPN_OK);
+    completed.clear();
     const double t0 = now_s();
     int rc = SPN_OK;
     if (!act.empty()) rc = round_launch(s, act);
-    // host work that overlaps the round
-    for (auto& j : completed) retire(s, j, SPN_OK);
-    completed.clear();
+    const double t_launched = now_s();
+    // admissions overlap the round: nothing in them waits for the device
     // the host part of EA admissions (bond bytes, exact exchange tables) on worker threads
     {
       std::vector<Job*> ea;
@@ -478,19 +481,22 @@ void scheduler(spn_server_ctx* s) {
         joined.push_back(j);
       }
     }
+    const double t_host = now_s();
     if (!act.empty() && rc == SPN_OK) rc = round_wait(s, act);
     const double t1 = now_s();
     if (!act.empty()) {
       s->busy += t1 - t0;
       s->rounds += 1;
-      if (s->trace) {  // one line per round: start, seconds, jobs, attempts, resident / streaming / EA / other jobs
+      if (s->trace) {  // one line per round: start, seconds, jobs, attempts, resident / streaming / EA / other
+                       // jobs, then seconds spent launching, on overlapped host work, and waiting
         int nr = 0, ns = 0, ne = 0, no = 0;
         long long att = 0;
         for (auto& j : act) {
           att += (long long)j->N * j->window * (j->ea ? 32 : 1);
           if (j->ea) ++ne; else if (j->cs > 0) ++nr; else if (j->streaming) ++ns; else ++no;
         }
-        std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d\n", t0, t1 - t0, act.size(), att, nr, ns, ne, no);
+        std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d %.4f %.4f %.4f %zu\n", t0, t1 - t0, act.size(), att, nr,
+                     ns, ne, no, t_launched - t0, t_host - t_launched, t1 - t_host, admitted_now.size());
         std::fflush(s->trace);
       }
     }
@@ -501,7 +507,7 @@ void scheduler(spn_server_ctx* s) {
       } else if (j->done < j->req.nsweeps) {
         still.push_back(j);
       } else {
-        completed.push_back(j);  // read back while the next round runs
+        completed.push_back(j);  // read back before the next round
       }
     }
     for (auto& j : joined) still.push_back(j);
