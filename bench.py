@@ -241,9 +241,22 @@ def _cpu_baseline(sweeps: int = 1):
     oracle.sweeps((L3D, L3D, L3D), s, BETA_3D, sweeps, 2)
     att += sweeps * L3D ** 3
     dt = time.perf_counter() - t0
-    return {"value": att / (dt * 1e9), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the paper's serial figure (one core): 2D L=64 at T_c, 1000 sweeps, and 2 sweeps of 2D L=4096
+    serial = {}
+    oracle.set_num_threads(1)
+    try:
+        for name, L, n in (("2d_L64_1000_sweeps", 64, 1000), ("2d_L4096_2_sweeps", 4096, 2)):
+            s = oracle.init_hot((L, L), 3)
+            t1 = time.perf_counter()
+            oracle.sweeps((L, L), s, 1.0 / TEMPS_2D[1], n, 3)
+            serial[name] = L * L * n / ((time.perf_counter() - t1) * 1e9)
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": att / (dt * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"hot start + {sweeps} sweep(s) of 2D L=16384 at T=2.269185 and of 3D L=512 at "
-                      f"beta=0.221654 ({att:.3g} attempts, {dt:.1f} s)"}
+                      f"beta=0.221654 ({att:.3g} attempts, {dt:.1f} s)",
+            "serial_one_core": serial}
 
 
 def _timed(stream, fn):

@@ -97,6 +97,8 @@ def lib():
             L.orc_heis_sweeps.restype = cint
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = cint
+            L.orc_set_num_threads.argtypes = [cint]
+            L.orc_set_num_threads.restype = None
             _lib = L
     return _lib
 
@@ -120,6 +122,11 @@ def _check(rc: int, what: str):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int):
+    """Threads of the oracle's OpenMP loops (1: serial)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

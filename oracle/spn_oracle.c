@@ -699,3 +699,14 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops from now on (timing support: 1 gives the serial
+ * figure); no effect without OpenMP. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
