@@ -114,13 +114,26 @@ int unpack_if_live(spn_ctx* h) {
 
 void pick_default_path(spn_ctx* h) {
   const spn::Lattice g = stream_lattice(h);
-  int ty = 32;
-  if (g.nd == 3)
-    while (ty > 1 && g.Ly % ty) ty /= 2;
-  h->tile_y = g.nd == 3 ? ty : 1;
   h->step_slices = 0;
   h->seg = 0;
-  h->path = spn::stream_path_supported(g, h->tile_y) && g.N >= (1 << 16) ? spn::kPathStream : spn::kPathGeneric;
+  bool fits = false;
+  if (g.nd == 2) {
+    h->tile_y = 1;
+    fits = spn::stream_path_supported(g, 1) && spn::stream_geometry_ok(g, spn::stream_geometry(g, 1, 0, 0));
+  } else {
+    // the tallest even band of at most 32 rows that divides Ly and fits one CTA
+    // (else the tallest dividing one, for explicit tilings)
+    h->tile_y = 0;
+    for (int ty = 32; ty >= 2 && !fits; ty -= 2) {
+      if (g.Ly % ty) continue;
+      if (!h->tile_y) h->tile_y = ty;
+      if (spn::stream_path_supported(g, ty) && spn::stream_geometry_ok(g, spn::stream_geometry(g, ty, 0, 0))) {
+        h->tile_y = ty;
+        fits = true;
+      }
+    }
+  }
+  h->path = fits && g.N >= (1 << 16) ? spn::kPathStream : spn::kPathGeneric;
 }
 
 int ensure_acc(spn_ctx* h, int64_t n) {

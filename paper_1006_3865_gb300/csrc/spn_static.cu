@@ -106,15 +106,15 @@ extern "C" int spn_sweep_noalloc(int model, const int32_t* dims, int8_t* d_spins
 
   const spn::DevThr T = spn::make_thresholds(beta);
   const spn::PhiloxKeys K = spn::philox_keys(seed);
-  int ty = 32;
-  if (g.nd == 3)
-    while (ty > 1 && g.Ly % ty) ty /= 2;
-  if (g.nd == 2) ty = 1;
-  const bool stream = spn::stream_path_supported(g, ty);
+  // the streaming sweep with the tallest band (3D: even, at most 32 rows, dividing
+  // Ly) whose geometry fits one CTA; otherwise the generic sweep
+  bool stream = false;
   spn::StreamGeom geo{};
-  if (stream) {
+  for (int ty = g.nd == 3 ? 32 : 1; ty >= 1 && !stream; ty -= (g.nd == 3 ? 2 : 1)) {
+    if (g.nd == 3 && (ty < 2 || g.Ly % ty)) continue;
+    if (!spn::stream_path_supported(g, ty)) continue;
     geo = spn::stream_geometry(g, ty, 0, 0);
-    if (!spn::stream_geometry_ok(g, geo)) return fail(SPN_E_STATE, "streaming geometry does not fit one CTA");
+    stream = spn::stream_geometry_ok(g, geo);
   }
   int8_t* bufs[2] = {d_spins, sc.lattice};
   int cur = 0;
