@@ -201,9 +201,9 @@ int spn_launch_count(uint64_t* count);
  * tries 2k and 2k+1 from words (0, 1) and (2, 3), a word w giving
  * (w >> 8) 2^-23 - 1; no move after 16 failed tries; the hot start uses
  * purpose 7 with sweep 0; u = (w >> 8) 2^-24 with w = word m & 3 of
- * R(m >> 2, sweep, c | 6 << 1, stream).  E and M are binary64 sums of the
- * accepted moves' binary32 dE and dS (their order varies between runs at the
- * level of binary64 rounding).
+ * R(m >> 2, sweep, c | 6 << 1, stream).  E and M start from a binary64
+ * recompute and add, per sweep, the exact sum of the accepted moves' binary32
+ * dE and dS each rounded to a multiple of 2^-40 (so they are reproducible).
  * ---------------------------------------------------------------------- */
 
 /* Spins as binary32 [N][3] (x, y, z) in site order; count = 3 N.  Set copies

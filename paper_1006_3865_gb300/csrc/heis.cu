@@ -18,9 +18,11 @@
 // One launch updates one colour, a thread per site: its seven 16-byte loads
 // are issued together, a proposal try that fails for some lanes is retried for
 // those lanes only, and the lanes of four consecutive within-colour indices
-// draw the same Metropolis Philox call (one warp instruction stream).  Energy and magnetisation changes are summed in binary64 per CTA
-// and added to the sweep's accumulator (their summation order varies; the
-// spins do not depend on it).
+// draw the same Metropolis Philox call (one warp instruction stream).  The
+// energy and magnetisation changes of accepted moves are added as 64-bit
+// fixed-point integers in units of 2^-40 (each binary32 dE, dS rounded once to
+// that grid), so the per-sweep sums are exact and independent of the order of
+// the atomics.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,7 +49,7 @@ struct HeisArgs {
   float beta;
   uint32_t sweep, stream_id, colour;
   PhiloxKeys K;
-  double* acc;  // [4]: dE, dMx, dMy, dMz of this sweep
+  unsigned long long* acc;  // [4]: dE, dMx, dMy, dMz of this sweep, two's complement in units of 2^-40
 };
 
 __device__ __forceinline__ float heis_exp_dev(float x) {
@@ -106,6 +108,31 @@ __device__ __forceinline__ void add3(float3& h, const float4 v) {
   h.z = __fadd_rn(h.z, v.z);
 }
 
+__device__ __forceinline__ void block_add4_fixed(long long v[4], unsigned long long* acc) {
+  __shared__ long long red[32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) red[warp][i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      long long x = lane < nw ? red[lane][i] : 0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0 && x != 0) atomicAdd(&acc[i], (unsigned long long)x);
+    }
+  }
+}
+
+// binary32 value on the 2^-40 grid (exact scaling by a power of two, one rounding)
+__device__ __forceinline__ long long fixed40(float v) { return __float2ll_rn(__fmul_rn(v, 1099511627776.0f)); }
+
 __device__ __forceinline__ void block_add4(double v[4], double* acc) {
   __shared__ double red[32][4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -130,7 +157,7 @@ __device__ __forceinline__ void block_add4(double v[4], double* acc) {
 
 __global__ void __launch_bounds__(256, 6) k_heis_half(const HeisArgs a) {
   const uint32_t c = a.colour;
-  double sum[4] = {0.0, 0.0, 0.0, 0.0};
+  long long sum[4] = {0, 0, 0, 0};
   for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; __any_sync(0xffffffffu, m < a.half);
        m += gridDim.x * blockDim.x) {
     bool live = m < a.half;
@@ -187,13 +214,13 @@ __global__ void __launch_bounds__(256, 6) k_heis_half(const HeisArgs a) {
     }
     if (accept) {
       a.s[n] = make_float4(prop.x, prop.y, prop.z, 0.0f);
-      sum[0] += (double)de;
-      sum[1] += (double)dx;
-      sum[2] += (double)dy;
-      sum[3] += (double)dz;
+      sum[0] += fixed40(de);
+      sum[1] += fixed40(dx);
+      sum[2] += fixed40(dy);
+      sum[3] += fixed40(dz);
     }
   }
-  block_add4(sum, a.acc);
+  block_add4_fixed(sum, a.acc);
 }
 
 __global__ void k_heis_init(float4* s, int nd, int Lx, int Ly, int64_t N, PhiloxKeys K, uint32_t stream, int cold) {
@@ -263,7 +290,7 @@ cudaError_t launch_heis_init(float4* s, int nd, const int* L, int64_t N, uint64_
 }
 
 cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float beta, uint64_t seed,
-                              uint32_t stream, uint32_t sweep, double* acc, cudaStream_t st) {
+                              uint32_t stream, uint32_t sweep, unsigned long long* acc, cudaStream_t st) {
   HeisArgs a;
   a.s = s;
   a.nd = nd;
@@ -312,7 +339,7 @@ struct HeisState {
   int L[3] = {0, 0, 1};
   int64_t N = 0;
   float4* d_s = nullptr;
-  double* d_acc = nullptr;  // [cap][4] per-sweep (dE, dM) since `folded`
+  unsigned long long* d_acc = nullptr;  // [cap][4] per-sweep (dE, dM) since `folded`, units of 2^-40
   int64_t acc_cap = 0;
   uint64_t folded = 0;
   double* d_obs = nullptr;
@@ -345,17 +372,18 @@ int heis_fold(spn_ctx* h) {
   if (cudaStreamSynchronize(h->st) != cudaSuccess) return heis_fail(SPN_E_CUDA, "cudaStreamSynchronize");
   const int64_t live = (int64_t)(h->sweeps - s->folded);
   if (live <= 0) return SPN_OK;
-  std::vector<double> d((size_t)live * 4);
-  if (cudaMemcpy(d.data(), s->d_acc, d.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+  std::vector<unsigned long long> d((size_t)live * 4);
+  if (cudaMemcpy(d.data(), s->d_acc, d.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
     return heis_fail(SPN_E_CUDA, "reading the Heisenberg trace");
+  const double unit = 1.0 / 1099511627776.0;  // 2^-40
   for (int64_t i = 0; i < live; ++i) {
-    s->E += d[4 * i];
-    for (int k = 0; k < 3; ++k) s->M[k] += d[4 * i + 1 + k];
+    s->E += (double)(long long)d[4 * i] * unit;
+    for (int k = 0; k < 3; ++k) s->M[k] += (double)(long long)d[4 * i + 1 + k] * unit;
     s->traceE.push_back(s->E);
     for (int k = 0; k < 3; ++k) s->traceM.push_back(s->M[k]);
   }
   s->folded = h->sweeps;
-  if (cudaMemsetAsync(s->d_acc, 0, (size_t)s->acc_cap * 4 * sizeof(double), h->st) != cudaSuccess)
+  if (cudaMemsetAsync(s->d_acc, 0, (size_t)s->acc_cap * 4 * sizeof(unsigned long long), h->st) != cudaSuccess)
     return heis_fail(SPN_E_CUDA, "clearing the Heisenberg trace");
   return SPN_OK;
 }
@@ -370,9 +398,9 @@ int heis_ensure_acc(spn_ctx* h, int64_t n) {
   while (cap < n) cap *= 2;
   cudaFree(s->d_acc);
   s->d_acc = nullptr;
-  if (cudaMalloc(&s->d_acc, (size_t)cap * 4 * sizeof(double)) != cudaSuccess)
+  if (cudaMalloc(&s->d_acc, (size_t)cap * 4 * sizeof(unsigned long long)) != cudaSuccess)
     return heis_fail(SPN_E_NOMEM, "cudaMalloc(Heisenberg trace)");
-  if (cudaMemsetAsync(s->d_acc, 0, (size_t)cap * 4 * sizeof(double), h->st) != cudaSuccess)
+  if (cudaMemsetAsync(s->d_acc, 0, (size_t)cap * 4 * sizeof(unsigned long long), h->st) != cudaSuccess)
     return heis_fail(SPN_E_CUDA, "clearing the Heisenberg trace");
   s->acc_cap = cap;
   return SPN_OK;
@@ -426,7 +454,7 @@ int heis_sweep(spn_ctx* h, double beta, int64_t nsweeps) {
   const float bf = (float)beta;
   for (int64_t t = 0; t < nsweeps; ++t) {
     const uint32_t sweep = (uint32_t)(h->sweeps + t);
-    double* acc = s->d_acc + 4 * (int64_t)(sweep - s->folded);
+    unsigned long long* acc = s->d_acc + 4 * (int64_t)(sweep - s->folded);
     const cudaError_t e = launch_heis_sweep(s->d_s, s->nd, s->L, s->N, bf, h->seed, h->stream_id, sweep, acc, h->st);
     if (e != cudaSuccess) {
       h->sweeps += (uint64_t)t;
