@@ -84,6 +84,17 @@ def test_ising3d_stream_tilings(tiling):
              tiling=tiling)
 
 
+@pytest.mark.parametrize("dims", [(1024, 32, 8), (2048, 16, 4)])
+def test_ising3d_wide_rows_default_band(dims):
+    """Rows of 16 and 32 words: the default band shrinks until the colour-0
+    words of a step fit one CTA, and the streaming sweep still runs."""
+    lat = spn.Lattice(spn.SPN_ISING3D, dims, 3)
+    assert lat.path == spn.PATH_STREAM
+    lat.close()
+    _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(15), [(inputs.BETA_C_3D, 3)])
+    _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(15), [(inputs.BETA_C_3D, 3)], path=spn.PATH_PACKED)
+
+
 def test_ising3d_stream_wide_rows():
     _compare(spn.SPN_ISING3D, (192, 8, 6), inputs.unit_seed(12), [(0.25, 4)], path=spn.PATH_STREAM,
              tiling=(4, 1, 2))
