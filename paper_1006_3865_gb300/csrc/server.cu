@@ -65,13 +65,12 @@ struct Job {
   int nd = 2;
   int64_t N = 0;
   int cs = 0;        // resident cluster size (0: not resident)
-  bool streaming = false;  // pitched ping-pong lattices (rows padded to 64 bytes) for the streaming sweep
-  int pitch = 0;
+  bool streaming = false;  // bit-packed ping-pong lattices for the streaming sweep
   spn::StreamGeom geo{};
   int8_t* d_spins = nullptr;
   int8_t* d_scratch = nullptr;
-  int8_t* d_p0 = nullptr;  // pitched lattice (current)
-  int8_t* d_p1 = nullptr;  // pitched ping-pong partner
+  uint32_t* d_p0 = nullptr;  // bit-packed lattice (current)
+  uint32_t* d_p1 = nullptr;  // bit-packed ping-pong partner
   unsigned long long* d_acc = nullptr;  // window deltas / start E, M
   spn_handle ea = nullptr;
   std::unique_ptr<spn::EaPrep> prep;  // EA: host part built on a worker thread before admission
@@ -128,7 +127,7 @@ namespace {
 size_t job_bytes(const Job& j) {
   if (j.req.model == SPN_EA3D_PMJ) return (size_t)j.N * 9 + 64 * 1024;  // words + bond bytes + tables
   size_t b = (size_t)j.N + 4096;
-  if (j.streaming) b += 2 * (size_t)j.pitch * (size_t)(j.N / j.req.dims[0]);
+  if (j.streaming) b += 2 * (size_t)spn::packed_row_words(j.req.dims[0]) * 4 * (size_t)(j.N / j.req.dims[0]);
   return b;
 }
 
@@ -140,7 +139,8 @@ void release(spn_server_ctx* s, Job& j) {
   if (j.d_p0) cudaFreeAsync(j.d_p0, s->aux);
   if (j.d_p1) cudaFreeAsync(j.d_p1, s->aux);
   if (j.d_acc) cudaFreeAsync(j.d_acc, s->aux);
-  j.d_spins = j.d_scratch = j.d_p0 = j.d_p1 = nullptr;
+  j.d_spins = j.d_scratch = nullptr;
+  j.d_p0 = j.d_p1 = nullptr;
   j.d_acc = nullptr;
   if (j.ea) {
     spn_destroy(j.ea);
@@ -167,13 +167,12 @@ int admit(spn_server_ctx* s, Job& j) {
   if (cudaMallocAsync(&j.d_spins, (size_t)j.N, s->aux) != cudaSuccess) return SPN_E_NOMEM;
   if (cudaMallocAsync(&j.d_acc, 4096, s->aux) != cudaSuccess) return SPN_E_NOMEM;
   if (spn::launch_init_hot(g, j.d_spins, r.seed, r.stream, s->aux) != cudaSuccess) return SPN_E_CUDA;
-  if (j.streaming) {
-    const size_t nrow = (size_t)(j.N / g.Lx), pb = (size_t)j.pitch * nrow;
+  if (j.streaming) {  // the hot start packed to 1 bit per spin; padding words of both buffers zero
+    const size_t pb = (size_t)spn::packed_row_words(g.Lx) * 4 * (size_t)(j.N / g.Lx);
     if (cudaMallocAsync(&j.d_p0, pb, s->aux) != cudaSuccess || cudaMallocAsync(&j.d_p1, pb, s->aux) != cudaSuccess)
       return SPN_E_NOMEM;
-    if (cudaMemsetAsync(j.d_p0, 1, pb, s->aux) != cudaSuccess ||
-        cudaMemcpy2DAsync(j.d_p0, (size_t)j.pitch, j.d_spins, (size_t)g.Lx, (size_t)g.Lx, nrow, cudaMemcpyDeviceToDevice,
-                          s->aux) != cudaSuccess)
+    if (cudaMemsetAsync(j.d_p0, 0, pb, s->aux) != cudaSuccess || cudaMemsetAsync(j.d_p1, 0, pb, s->aux) != cudaSuccess ||
+        spn::launch_pack(g, j.d_spins, j.d_p0, s->aux) != cudaSuccess)
       return SPN_E_CUDA;
   }
   return SPN_OK;
@@ -204,10 +203,7 @@ int finish(spn_server_ctx* s, Job& j) {
   g.Ly = j.req.dims[1];
   g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
   g.N = j.N;
-  if (j.streaming &&
-      cudaMemcpy2DAsync(j.d_spins, (size_t)g.Lx, j.d_p0, (size_t)j.pitch, (size_t)g.Lx, (size_t)(j.N / g.Lx),
-                        cudaMemcpyDeviceToDevice, s->aux) != cudaSuccess)
-    return SPN_E_CUDA;
+  if (j.streaming && spn::launch_unpack(g, j.d_p0, j.d_spins, s->aux) != cudaSuccess) return SPN_E_CUDA;
   if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, s->aux) != cudaSuccess) return SPN_E_CUDA;
   unsigned long long em[2];
   j.spins.resize((size_t)j.N);
@@ -365,7 +361,7 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
     g.Ly = j.req.dims[1];
     g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
     g.N = j.N;
-    g.pitch = j.streaming ? j.pitch : 0;
+    g.pitch = 0;
     const spn::DevThr T = spn::make_thresholds(j.req.beta);
     const spn::PhiloxKeys K = spn::philox_keys(j.req.seed);
     for (int64_t t = 0; t < w; ++t) {
@@ -573,27 +569,25 @@ int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket) {
   } else {
     if (!(req->beta >= 0.0)) return sfail(SPN_E_ARG, "beta must be >= 0");
     // lattices resident in the shared memory of one CTA or cluster share
-    // persistent launches; larger ones stream (rows padded to 64 bytes)
+    // persistent launches; larger ones stream from bit-packed lattices
     spn::Lattice g;
     g.nd = j->nd;
     g.Lx = ext[0];
     g.Ly = ext[1];
     g.Lz = ext[2];
     g.N = j->N;
-    g.pitch = (ext[0] + 63) / 64 * 64;
-    int ty = 32;
-    if (j->nd == 3)
-      while (ty > 1 && ext[1] % ty) ty /= 2;
-    if (j->nd == 2) ty = 1;
+    // the tallest dividing band (3D) whose bit-packed streaming geometry fits one CTA
     j->cs = spn::resident_cluster_size(j->nd, ext[0], ext[1], ext[2]);
-    if (j->cs == 0 && j->N >= s->stream_sites && spn::stream_path_supported(g, ty)) {
+    for (int ty = j->nd == 3 ? 32 : 1; j->cs == 0 && j->N >= s->stream_sites && ty >= 1 && !j->streaming;
+         ty -= (j->nd == 3 ? 2 : 1)) {
+      if (j->nd == 3 && (ty < 2 || ext[1] % ty)) continue;
+      if (!spn::stream_path_supported(g, ty, true)) continue;
       const int S = j->nd == 3 ? ext[2] : ext[1];
       const int tiles = j->nd == 3 ? ext[1] / ty : 1;
       // >= 32 slices a CTA: concurrent jobs fill the GPU, and few halo slices are re-read
       const int nseg = std::max(1, std::min(S / 32, 4 * spn::device_sm_count() / tiles));
-      j->geo = spn::stream_geometry(g, ty, 0, nseg);
+      j->geo = spn::stream_geometry(g, ty, 0, nseg, true);
       j->streaming = spn::stream_geometry_ok(g, j->geo);
-      j->pitch = g.pitch;
     }
 
   }
