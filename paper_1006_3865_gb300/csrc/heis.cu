@@ -93,10 +93,11 @@ __device__ __forceinline__ bool proposal_call(const PhiloxKeys& K, uint32_t m, u
 }
 
 // Site of within-colour index m of colour c.
+template <int ND>
 __device__ __forceinline__ uint32_t site_of(const HeisArgs& a, uint32_t m, uint32_t c, int& x, int& y, int& z) {
   const uint32_t row = fdiv(m, a.div_h);
   const int i = (int)(m - row * (uint32_t)(a.Lx >> 1));
-  z = a.nd == 3 ? (int)fdiv(row, a.div_ly) : 0;
+  z = ND == 3 ? (int)fdiv(row, a.div_ly) : 0;
   y = (int)row - z * a.Ly;
   x = 2 * i + (int)((c ^ (uint32_t)(y + z)) & 1u);
   return (uint32_t)x + (uint32_t)a.Lx * row;
@@ -155,6 +156,7 @@ __device__ __forceinline__ void block_add4(double v[4], double* acc) {
   }
 }
 
+template <int ND>
 __global__ void __launch_bounds__(256, 6) k_heis_half(const HeisArgs a) {
   const uint32_t c = a.colour;
   long long sum[4] = {0, 0, 0, 0};
@@ -166,24 +168,26 @@ __global__ void __launch_bounds__(256, 6) k_heis_half(const HeisArgs a) {
     float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (live) {
       int x, y, z;
-      n = site_of(a, m, c, x, y, z);
+      n = site_of<ND>(a, m, c, x, y, z);
       // all loads first: seven independent 16-byte reads in flight per thread
-      const int64_t sy = a.Lx, sz = (int64_t)a.Lx * a.Ly;
-      const float4 bx = a.s[n - x + (x == 0 ? a.Lx - 1 : x - 1)];
-      const float4 fx = a.s[n - x + (x + 1 == a.Lx ? 0 : x + 1)];
-      const float4 by = a.s[y == 0 ? n + (a.Ly - 1) * sy : n - sy];
-      const float4 fy = a.s[y + 1 == a.Ly ? n - (a.Ly - 1) * sy : n + sy];
+      // (32-bit site indices: N < 2^31)
+      const uint32_t sx = (uint32_t)a.Lx - 1u, sy = (uint32_t)a.Lx, wy = (uint32_t)(a.Ly - 1) * sy;
+      const float4 bx = a.s[x == 0 ? n + sx : n - 1u];
+      const float4 fx = a.s[x + 1 == a.Lx ? n - sx : n + 1u];
+      const float4 by = a.s[y == 0 ? n + wy : n - sy];
+      const float4 fy = a.s[y + 1 == a.Ly ? n - wy : n + sy];
       float4 bz = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fz = bz;
-      if (a.nd == 3) {
-        bz = a.s[z == 0 ? n + (a.Lz - 1) * sz : n - sz];
-        fz = a.s[z + 1 == a.Lz ? n - (a.Lz - 1) * sz : n + sz];
+      if constexpr (ND == 3) {
+        const uint32_t sz = sy * (uint32_t)a.Ly, wz = (uint32_t)(a.Lz - 1) * sz;
+        bz = a.s[z == 0 ? n + wz : n - sz];
+        fz = a.s[z + 1 == a.Lz ? n - wz : n + sz];
       }
       s = a.s[n];
       add3(h, bx);
       add3(h, fx);
       add3(h, by);
       add3(h, fy);
-      if (a.nd == 3) {
+      if constexpr (ND == 3) {
         add3(h, bz);
         add3(h, fz);
       }
@@ -308,7 +312,10 @@ cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float 
   const int grid = grid_for((int64_t)a.half, 6);
   for (uint32_t c = 0; c < 2; ++c) {
     a.colour = c;
-    k_heis_half<<<grid, 256, 0, st>>>(a);
+    if (nd == 3)
+      k_heis_half<3><<<grid, 256, 0, st>>>(a);
+    else
+      k_heis_half<2><<<grid, 256, 0, st>>>(a);
   }
   count_launches(2);
   return cudaGetLastError();
