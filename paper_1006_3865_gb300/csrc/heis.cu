@@ -15,10 +15,11 @@
 //   hot start: the same with purpose 7 and sweep 0;
 //   Metropolis u: word m & 3 of R(m >> 2, sweep, c | 6 << 1, stream).
 //
-// One launch updates one colour, a thread per site: its seven 16-byte loads
-// are issued together, a proposal try that fails for some lanes is retried for
-// those lanes only, and the lanes of four consecutive within-colour indices
-// draw the same Metropolis Philox call (one warp instruction stream).  The
+// One launch updates one colour; a warp takes 128 consecutive within-colour
+// indices, a site per lane at a time: a lane's seven 16-byte loads are issued
+// together, a proposal try that fails for some lanes is retried for those
+// lanes only, and each Metropolis Philox call (four sites' words) is drawn
+// once per warp and passed to the lanes by shuffles.  The
 // energy and magnetisation changes of accepted moves are added as 64-bit
 // fixed-point integers in units of 2^-40 (each binary32 dE, dS rounded once to
 // that grid), so the per-sweep sums are exact and independent of the order of
@@ -157,71 +158,81 @@ __device__ __forceinline__ void block_add4(double v[4], double* acc) {
 }
 
 template <int ND>
-__global__ void __launch_bounds__(256, 6) k_heis_half(const HeisArgs a) {
-  const uint32_t c = a.colour;
+__global__ void __launch_bounds__(256, 5) k_heis_half(const HeisArgs a) {
+  const uint32_t c = a.colour, lane = threadIdx.x & 31u;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
   long long sum[4] = {0, 0, 0, 0};
-  for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; __any_sync(0xffffffffu, m < a.half);
-       m += gridDim.x * blockDim.x) {
-    bool live = m < a.half;
-    uint32_t n = 0;
-    float3 h = make_float3(0.0f, 0.0f, 0.0f);
-    float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (live) {
-      int x, y, z;
-      n = site_of<ND>(a, m, c, x, y, z);
-      // all loads first: seven independent 16-byte reads in flight per thread
-      // (32-bit site indices: N < 2^31)
-      const uint32_t sx = (uint32_t)a.Lx - 1u, sy = (uint32_t)a.Lx, wy = (uint32_t)(a.Ly - 1) * sy;
-      const float4 bx = a.s[x == 0 ? n + sx : n - 1u];
-      const float4 fx = a.s[x + 1 == a.Lx ? n - sx : n + 1u];
-      const float4 by = a.s[y == 0 ? n + wy : n - sy];
-      const float4 fy = a.s[y + 1 == a.Ly ? n - wy : n + sy];
-      float4 bz = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fz = bz;
-      if constexpr (ND == 3) {
-        const uint32_t sz = sy * (uint32_t)a.Ly, wz = (uint32_t)(a.Lz - 1) * sz;
-        bz = a.s[z == 0 ? n + wz : n - sz];
-        fz = a.s[z + 1 == a.Lz ? n - wz : n + sz];
-      }
-      s = a.s[n];
-      add3(h, bx);
-      add3(h, fx);
-      add3(h, by);
-      add3(h, fy);
-      if constexpr (ND == 3) {
-        add3(h, bz);
-        add3(h, fz);
-      }
-    }
-    // proposal: the first call's two tries, then one more call per round for the lanes still without one
-    float3 prop = make_float3(0.0f, 0.0f, 1.0f);
-    bool need = live && !proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop);
-    for (uint32_t k = 1; __any_sync(0xffffffffu, need); ++k) {
-      if (need) {
-        need = !proposal_call(a.K, m, a.sweep, c, kHeisPropose, k, a.stream_id, prop);
-        if (need && k == 7u) {  // sixteen misses: no move for this site
-          need = false;
-          live = false;
+  // a warp takes 128 consecutive within-colour indices, 32 at a time; lane l
+  // draws the Metropolis call of indices base + 4l .. base + 4l + 3 once
+  for (uint32_t base = gwarp * 128u; base < a.half; base += nwarp * 128u) {
+    const U4 U = philox10((base >> 2) + lane, a.sweep, c | (kHeisMetropolis << 1), a.stream_id, a.K);
+#pragma unroll 1
+    for (uint32_t i = 0; i < 4; ++i) {
+      const uint32_t m = base + 32u * i + lane;
+      const int src = (int)(8u * i + (lane >> 2));  // the lane holding call m >> 2
+      const uint32_t w0 = __shfl_sync(0xffffffffu, U.x, src), w1 = __shfl_sync(0xffffffffu, U.y, src);
+      const uint32_t w2 = __shfl_sync(0xffffffffu, U.z, src), w3 = __shfl_sync(0xffffffffu, U.w, src);
+      const uint32_t uw = (m & 2u) ? ((m & 1u) ? w3 : w2) : ((m & 1u) ? w1 : w0);
+      bool live = m < a.half;
+      uint32_t n = 0;
+      float3 h = make_float3(0.0f, 0.0f, 0.0f);
+      float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (live) {
+        int x, y, z;
+        n = site_of<ND>(a, m, c, x, y, z);
+        // all loads first: seven independent 16-byte reads in flight per thread
+        // (32-bit site indices: N < 2^31)
+        const uint32_t sx = (uint32_t)a.Lx - 1u, sy = (uint32_t)a.Lx, wy = (uint32_t)(a.Ly - 1) * sy;
+        const float4 bx = a.s[x == 0 ? n + sx : n - 1u];
+        const float4 fx = a.s[x + 1 == a.Lx ? n - sx : n + 1u];
+        const float4 by = a.s[y == 0 ? n + wy : n - sy];
+        const float4 fy = a.s[y + 1 == a.Ly ? n - wy : n + sy];
+        float4 bz = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fz = bz;
+        if constexpr (ND == 3) {
+          const uint32_t sz = sy * (uint32_t)a.Ly, wz = (uint32_t)(a.Lz - 1) * sz;
+          bz = a.s[z == 0 ? n + wz : n - sz];
+          fz = a.s[z + 1 == a.Lz ? n - wz : n + sz];
+        }
+        s = a.s[n];
+        add3(h, bx);
+        add3(h, fx);
+        add3(h, by);
+        add3(h, fy);
+        if constexpr (ND == 3) {
+          add3(h, bz);
+          add3(h, fz);
         }
       }
-    }
-    if (!live) continue;
-    const float dx = __fsub_rn(prop.x, s.x), dy = __fsub_rn(prop.y, s.y), dz = __fsub_rn(prop.z, s.z);
-    float dot = __fmul_rn(dx, h.x);
-    dot = __fadd_rn(dot, __fmul_rn(dy, h.y));
-    dot = __fadd_rn(dot, __fmul_rn(dz, h.z));
-    const float de = -dot;
-    bool accept = de <= 0.0f;
-    if (!accept) {
-      const U4 U = philox10(m >> 2, a.sweep, c | (kHeisMetropolis << 1), a.stream_id, a.K);
-      const float u = __fmul_rn(__uint2float_rn(u4_word(U, (int)(m & 3u)) >> 8), 1.0f / 16777216.0f);
-      accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
-    }
-    if (accept) {
-      a.s[n] = make_float4(prop.x, prop.y, prop.z, 0.0f);
-      sum[0] += fixed40(de);
-      sum[1] += fixed40(dx);
-      sum[2] += fixed40(dy);
-      sum[3] += fixed40(dz);
+      // proposal: the first call's two tries, then one more call per round for the lanes still without one
+      float3 prop = make_float3(0.0f, 0.0f, 1.0f);
+      bool need = live && !proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop);
+      for (uint32_t k = 1; __any_sync(0xffffffffu, need); ++k) {
+        if (need) {
+          need = !proposal_call(a.K, m, a.sweep, c, kHeisPropose, k, a.stream_id, prop);
+          if (need && k == 7u) {  // sixteen misses: no move for this site
+            need = false;
+            live = false;
+          }
+        }
+      }
+      if (!live) continue;
+      const float dx = __fsub_rn(prop.x, s.x), dy = __fsub_rn(prop.y, s.y), dz = __fsub_rn(prop.z, s.z);
+      float dot = __fmul_rn(dx, h.x);
+      dot = __fadd_rn(dot, __fmul_rn(dy, h.y));
+      dot = __fadd_rn(dot, __fmul_rn(dz, h.z));
+      const float de = -dot;
+      bool accept = de <= 0.0f;
+      if (!accept) {
+        const float u = __fmul_rn(__uint2float_rn(uw >> 8), 1.0f / 16777216.0f);
+        accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
+      }
+      if (accept) {
+        a.s[n] = make_float4(prop.x, prop.y, prop.z, 0.0f);
+        sum[0] += fixed40(de);
+        sum[1] += fixed40(dx);
+        sum[2] += fixed40(dy);
+        sum[3] += fixed40(dz);
+      }
     }
   }
   block_add4_fixed(sum, a.acc);
@@ -309,7 +320,7 @@ cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float 
   a.stream_id = stream;
   a.K = philox_keys(seed);
   a.acc = acc;
-  const int grid = grid_for((int64_t)a.half, 6);
+  const int grid = grid_for(((int64_t)a.half + 3) / 4, 5);  // a thread per four sites (a warp per 128)
   for (uint32_t c = 0; c < 2; ++c) {
     a.colour = c;
     if (nd == 3)
