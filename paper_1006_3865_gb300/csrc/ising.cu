@@ -57,13 +57,12 @@ void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_rela
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int device_sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {  // initialised once, safe from several host threads
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   return sms;
 }
 
