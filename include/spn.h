@@ -271,6 +271,29 @@ int spn_multi_result(spn_multi m, int job, int8_t* spins, size_t bytes, int64_t*
 /* Use an existing CUDA stream for the runs (the graph is captured again). */
 int spn_multi_set_stream(spn_multi m, void* cuda_stream);
 
+/* Autotuner of the batched run (Sec. 4 observes that the best tile depends on
+ * L).  A trial runs the whole batch at reduced length (every job from its hot
+ * start, its sweeps scaled so that the longest job has trial_sweeps) with all
+ * lattice shapes launched together, as in a real run.  Starting from the
+ * current launch shapes, each lattice shape in turn tries every cluster size
+ * (CTAs sharing one lattice: 1, 2, 4 or 8 that fit) and thread count (64 ..
+ * 512) and keeps the one with the fastest trial (a change must win by 1%).
+ * Results never depend on the launch shape.  The choice is remembered per
+ * (shape, device) for the process, so later batches start from it.  rates
+ * (optional, count = number of shapes): the batch's trial attempts/ns after
+ * each shape was tuned.  Synchronises; the next SPN_RUN_BATCHED run captures
+ * a new graph. */
+int spn_multi_autotune(spn_multi m, int32_t trial_sweeps, double* rates, size_t count);
+
+/* Launch shapes, 7 ints per lattice shape (in the batch's own order): nd, Lx,
+ * Ly, Lz, cluster size, threads per CTA, CTAs of the launch.  count = 7 x the
+ * number of shapes. */
+int spn_multi_groups(spn_multi m, int32_t* out, size_t count);
+
+/* Set the launch shape of lattice shape `group` by hand (cluster size 1, 2, 4
+ * or 8 that fits, threads a multiple of 32 up to 512); SPN_E_ARG otherwise. */
+int spn_multi_set_launch(spn_multi m, int32_t group, int32_t cs, int32_t threads);
+
 int spn_multi_destroy(spn_multi m);
 
 /* ------------------------------------------------------------------------

@@ -11,8 +11,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <tuple>
@@ -28,9 +30,15 @@ int mfail(int code, const char* msg) {
   return code;
 }
 
+// Launch shapes chosen by the autotuner, per lattice shape and device (SM
+// count), for the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tuned;  // -> (cluster size, threads)
+
 struct Group {
   int nd, Lx, Ly, Lz, cs, threads, ctas;
   size_t smem = 0;
+  double tuned_rate = 0.0;  // attempts/ns of the autotuner's trial (0: not tuned)
   std::vector<int> jobs;  // job indices, longest first
   spn::ResInst* d_inst = nullptr;
   int* d_order = nullptr;
@@ -80,6 +88,16 @@ void multi_free(spn_multi_ctx* m) {
   cudaFree(m->d_err);
   cudaFree(m->d_obs);
   delete m;
+}
+
+// Launch shape of a group: cs CTAs (a cluster) per lattice, `threads` per CTA,
+// as many CTAs as fit the GPU (at most one cluster per job).
+void set_launch(Group& g, int cs, int threads) {
+  g.cs = cs;
+  g.threads = threads;
+  g.smem = spn::resident_smem(g.nd, g.Lx, g.Ly, g.Lz, cs);
+  const int maxc = spn::resident_max_ctas(g.nd, cs, threads, g.smem);
+  g.ctas = std::max(cs, std::min<int>(maxc, (int)g.jobs.size() * cs));
 }
 
 // zeroing + the group launches, on m->st (forks to the group streams)
@@ -200,13 +218,15 @@ int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs) {
     g.jobs = kv.second;
     std::stable_sort(g.jobs.begin(), g.jobs.end(),
                      [&](int a, int b) { return m->jobs[a].nsweeps > m->jobs[b].nsweeps; });
-    const int W = (g.Lx + 63) / 64;
-    const int items = (g.Ly * (g.nd == 3 ? g.Lz : 1) + g.cs - 1) / g.cs * W;
-    g.threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
-    const size_t smem = spn::resident_smem(g.nd, g.Lx, g.Ly, g.Lz, g.cs);
-    g.smem = smem;
-    const int maxc = spn::resident_max_ctas(g.nd, g.cs, g.threads, smem);
-    g.ctas = std::max(g.cs, std::min<int>(maxc, (int)g.jobs.size() * g.cs));
+    {
+      const int W = (g.Lx + 63) / 64;
+      const int items = (g.Ly * (g.nd == 3 ? g.Lz : 1) + g.cs - 1) / g.cs * W;
+      int cs = g.cs, threads = std::min(512, std::max(64, (items + 31) / 32 * 32));
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tuned.find({g.nd, g.Lx, g.Ly, g.Lz, spn::device_sm_count()});
+      if (it != g_tuned.end()) std::tie(cs, threads) = it->second;  // an earlier autotune of this shape
+      set_launch(g, cs, threads);
+    }
     std::vector<spn::ResInst> inst(g.jobs.size());
     std::vector<int> order(g.jobs.size());
     for (size_t k = 0; k < g.jobs.size(); ++k) {
@@ -333,6 +353,138 @@ int spn_multi_destroy(spn_multi m) {
   if (!m) return mfail(SPN_E_ARG, "NULL handle");
   cudaStreamSynchronize(m->st);
   multi_free(m);
+  return SPN_OK;
+}
+
+// The autotuner of the batched run (the best tile depends on the lattice size,
+// Sec. 4).  A trial is the whole batch at reduced length -- every job from its
+// hot start with its sweeps scaled so the longest has trial_sweeps, no traces
+// -- with all lattice shapes launched together as in a real run, so launch
+// shapes are judged by how they share the GPU.  Starting from the current
+// shapes, each lattice shape in turn tries every cluster size and thread count
+// and keeps the fastest trial (coordinate descent).
+int spn_multi_autotune(spn_multi m, int32_t trial_sweeps, double* rates, size_t count) {
+  if (!m || trial_sweeps < 1) return mfail(SPN_E_ARG, "bad arguments");
+  if (rates && count != m->groups.size()) return mfail(SPN_E_ARG, "count must be the number of lattice shapes");
+  if (cudaStreamSynchronize(m->st) != cudaSuccess) return mfail(SPN_E_CUDA, "synchronising");
+  int64_t longest = 1;
+  for (const spn_job& j : m->jobs) longest = std::max<int64_t>(longest, j.nsweeps);
+  const double scale = std::min(1.0, (double)trial_sweeps / (double)longest);
+  std::vector<spn::ResInst*> trial(m->groups.size(), nullptr);
+  double att = 0.0;
+  int rc = SPN_OK;
+  for (size_t gi = 0; gi < m->groups.size() && rc == SPN_OK; ++gi) {
+    Group& g = m->groups[gi];
+    std::vector<spn::ResInst> inst(g.jobs.size());
+    if (cudaMemcpy(inst.data(), g.d_inst, inst.size() * sizeof(spn::ResInst), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = mfail(SPN_E_CUDA, "reading the instances");
+      break;
+    }
+    for (size_t k = 0; k < inst.size(); ++k) {
+      inst[k].nsweeps = inst[k].nsweeps > 0 ? std::max(1, (int)std::lround(inst[k].nsweeps * scale)) : 0;
+      inst[k].trace = nullptr;
+      inst[k].em0 = nullptr;
+      att += (double)m->N[g.jobs[k]] * inst[k].nsweeps;
+    }
+    if (cudaMalloc(&trial[gi], inst.size() * sizeof(spn::ResInst)) != cudaSuccess ||
+        cudaMemcpy(trial[gi], inst.data(), inst.size() * sizeof(spn::ResInst), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = mfail(SPN_E_NOMEM, "trial instances");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == SPN_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = mfail(SPN_E_CUDA, "events");
+  // one trial of the current launch shapes: attempts/ns (the better of two runs)
+  auto run_trial = [&](double* rate) -> int {
+    double best = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaMemsetAsync(m->d_counters, 0, m->groups.size() * sizeof(int), m->st) != cudaSuccess ||
+          cudaEventRecord(e0, m->st) != cudaSuccess || cudaEventRecord(m->fork, m->st) != cudaSuccess)
+        return SPN_E_CUDA;
+      for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+        Group& g = m->groups[gi];
+        spn::ResArgs a{};
+        a.inst = trial[gi];
+        a.ninst = (int)g.jobs.size();
+        a.order = g.d_order;
+        a.counter = m->d_counters + gi;
+        a.err = m->d_err;
+        if (cudaStreamWaitEvent(g.st, m->fork, 0) != cudaSuccess ||
+            spn::launch_resident(a, g.nd, g.cs, g.threads, g.ctas, g.smem, g.st) != cudaSuccess ||
+            cudaEventRecord(g.done, g.st) != cudaSuccess || cudaStreamWaitEvent(m->st, g.done, 0) != cudaSuccess)
+          return SPN_E_CUDA;
+      }
+      float ms = 0.0f;
+      if (cudaEventRecord(e1, m->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        return SPN_E_CUDA;
+      best = std::max(best, att / ((double)ms * 1e6));
+    }
+    *rate = best;
+    return SPN_OK;
+  };
+  double best_rate = 0.0;
+  if (rc == SPN_OK && run_trial(&best_rate) != SPN_OK) rc = mfail(SPN_E_CUDA, "autotune trial");
+  for (size_t gi = 0; gi < m->groups.size() && rc == SPN_OK; ++gi) {
+    Group& g = m->groups[gi];
+    int best_cs = g.cs, best_t = g.threads;
+    const int cs_min = spn::resident_cluster_size(g.nd, g.Lx, g.Ly, g.Lz);
+    for (int cs = cs_min; cs <= 8 && rc == SPN_OK; cs *= 2) {
+      if (!spn::resident_supported(g.nd, g.Lx, g.Ly, g.Lz, cs)) continue;
+      const int W = (g.Lx + 63) / 64;
+      const int items = (g.Ly * (g.nd == 3 ? g.Lz : 1) + cs - 1) / cs * W;
+      for (int threads = 64; threads <= 512 && rc == SPN_OK; threads *= 2) {
+        if (threads > 64 && threads / 2 >= items) break;  // no more useful threads
+        if (cs == best_cs && threads == best_t) continue;  // the incumbent
+        set_launch(g, cs, threads);
+        double r = 0.0;
+        if (run_trial(&r) != SPN_OK) {
+          rc = mfail(SPN_E_CUDA, "autotune trial");
+        } else if (r > best_rate * 1.01) {  // a clear win only
+          best_rate = r;
+          best_cs = cs;
+          best_t = threads;
+        }
+      }
+    }
+    set_launch(g, best_cs, best_t);
+    if (rates) rates[gi] = best_rate;
+    if (rc == SPN_OK) {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tuned[{g.nd, g.Lx, g.Ly, g.Lz, spn::device_sm_count()}] = {best_cs, best_t};
+    }
+  }
+  for (spn::ResInst* p : trial) cudaFree(p);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (m->graph) {  // the next batched run captures the new launch shapes
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+  }
+  return rc;
+}
+
+int spn_multi_groups(spn_multi m, int32_t* out, size_t count) {
+  if (!m || !out || count != m->groups.size() * 7) return mfail(SPN_E_ARG, "count must be 7 per lattice shape");
+  for (size_t gi = 0; gi < m->groups.size(); ++gi) {
+    const Group& g = m->groups[gi];
+    const int32_t v[7] = {g.nd, g.Lx, g.Ly, g.Lz, g.cs, g.threads, g.ctas};
+    std::memcpy(out + 7 * gi, v, sizeof v);
+  }
+  return SPN_OK;
+}
+
+int spn_multi_set_launch(spn_multi m, int32_t group, int32_t cs, int32_t threads) {
+  if (!m || group < 0 || group >= (int)m->groups.size()) return mfail(SPN_E_ARG, "bad group index");
+  Group& g = m->groups[group];
+  if (threads < 32 || threads > 512 || threads % 32 || !spn::resident_supported(g.nd, g.Lx, g.Ly, g.Lz, cs) ||
+      (cs & (cs - 1)))
+    return mfail(SPN_E_ARG, "cluster size must be 1, 2, 4 or 8 and fit; threads a multiple of 32 up to 512");
+  if (cudaStreamSynchronize(m->st) != cudaSuccess) return mfail(SPN_E_CUDA, "synchronising");
+  set_launch(g, cs, threads);
+  if (m->graph) {
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+  }
   return SPN_OK;
 }
 

@@ -98,6 +98,9 @@ _SIGNATURES = {
     "spn_batch_energies": (_c.c_int, [_vp, _vp, _vp, _sz]),
     "spn_batch_exchange_counts": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_measure_overlap": (_c.c_int, [_vp]),
+    "spn_multi_autotune": (_c.c_int, [_vp, _i32, _vp, _sz]),
+    "spn_multi_groups": (_c.c_int, [_vp, _vp, _sz]),
+    "spn_multi_set_launch": (_c.c_int, [_vp, _i32, _i32, _i32]),
     "spn_heis_get_spins": (_c.c_int, [_vp, _vp, _sz]),
     "spn_heis_set_spins": (_c.c_int, [_vp, _vp, _sz]),
     "spn_heis_observables": (_c.c_int, [_vp, _vp, _vp]),
@@ -507,6 +510,28 @@ class Multi:
         _check(self._lib.spn_multi_result(self._h, job, _ptr(s), N if spins else 0, _ptr(E), _ptr(M),
                                           ns if trace else 0))
         return s, E, M
+
+    def groups(self) -> list[dict]:
+        """Launch shape per lattice shape: nd, dims, cluster size, threads, ctas."""
+        n = len({(len(d), d) for d, _ in self.shapes})  # the library groups jobs by (dimension, extents)
+        out = np.empty(7 * n, np.int32)
+        _check(self._lib.spn_multi_groups(self._h, _ptr(out), out.size))
+        rows = out.reshape(-1, 7)
+        return [{"nd": int(r[0]), "dims": tuple(int(x) for x in r[1:4]), "cs": int(r[4]), "threads": int(r[5]),
+                 "ctas": int(r[6])} for r in rows]
+
+    def autotune(self, trial_sweeps: int = 20) -> list[dict]:
+        """Time the launch shapes of every lattice shape and keep the fastest."""
+        g = self.groups()
+        rates = np.zeros(len(g), np.float64)
+        _check(self._lib.spn_multi_autotune(self._h, int(trial_sweeps), _ptr(rates), rates.size))
+        out = self.groups()
+        for d, r in zip(out, rates):
+            d["trial_attempts_per_ns"] = float(r)
+        return out
+
+    def set_launch(self, group: int, cs: int, threads: int):
+        _check(self._lib.spn_multi_set_launch(self._h, int(group), int(cs), int(threads)))
 
     def close(self):
         if getattr(self, "_h", None):

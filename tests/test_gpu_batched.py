@@ -95,3 +95,37 @@ def test_rejects_unsupported_shapes():
         spn.Multi([(spn.SPN_ISING2D, (8192, 4096), 0.4, 3, 1, 0)])
     with pytest.raises(spn.SpnError):  # odd extent
         spn.Multi([(spn.SPN_ISING2D, (48, 47), 0.4, 3, 1, 0)])
+
+
+def test_autotuner_candidates_give_identical_results():
+    """Every launch shape the autotuner may pick (cluster size, threads per
+    CTA) gives the same lattices and traces, and so does its choice."""
+    jobs = [(spn.SPN_ISING2D, (64, 64), 0.44, 30, inputs.unit_seed(600 + k), k) for k in range(6)]
+    jobs += [(spn.SPN_ISING2D, (512, 256), 0.4, 12, inputs.unit_seed(610 + k), 10 + k) for k in range(3)]
+    jobs += [(spn.SPN_ISING3D, (32, 16, 16), 0.22, 10, inputs.unit_seed(620 + k), 20 + k) for k in range(2)]
+    m = spn.Multi(jobs)
+    m.run(spn.SPN_RUN_BATCHED)
+    ref = [m.result(k) for k in range(len(jobs))]
+    groups = m.groups()
+    assert len(groups) == 3
+    for gi, g in enumerate(groups):
+        for cs in (1, 2, 4, 8):
+            for threads in (64, 128, 256):
+                try:
+                    m.set_launch(gi, cs, threads)
+                except spn.SpnError:
+                    continue  # that cluster size does not fit the shape
+                m.run(spn.SPN_RUN_BATCHED)
+                for k in range(len(jobs)):
+                    got = m.result(k)
+                    assert all(np.array_equal(x, y) for x, y in zip(got, ref[k])), (gi, cs, threads, k)
+    tuned = m.autotune(5)
+    assert all(t["trial_attempts_per_ns"] > 0 for t in tuned)
+    m.run(spn.SPN_RUN_BATCHED)
+    for k in range(len(jobs)):
+        assert all(np.array_equal(x, y) for x, y in zip(m.result(k), ref[k]))
+    m.close()
+    # a new batch with the same shapes starts from the tuned launch shapes
+    m2 = spn.Multi(jobs)
+    assert [(g["cs"], g["threads"]) for g in m2.groups()] == [(t["cs"], t["threads"]) for t in tuned]
+    m2.close()
