@@ -166,6 +166,18 @@ int spn_destroy(spn_handle h);
  * results never depend on it.  SPN_E_ARG if it does not fit one CTA. */
 int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t seg);
 
+/* Autotuner of the streaming sweep (Sec. 4 tunes its tile to L): for the
+ * handle's streaming path (1 or 3), time every fitting combination of band
+ * height (3D: even divisors of Ly up to 32), slices per step (automatic, 1, 2,
+ * 4) and segment count (automatic, or 2, 4, 6, 8 CTAs per SM) on trial_sweeps
+ * sweeps of a scratch copy of the lattice at beta, and set the fastest as the
+ * handle's tiling.  The handle's spins, counters and trace are untouched and
+ * results never depend on the tiling.  Choices are cached per (shape, path,
+ * device) for the process.  chosen (optional, 3 ints): tile_y, step_slices,
+ * seg as for spn_set_tiling.  SPN_E_STATE if the handle is not on a streaming
+ * path. */
+int spn_autotune(spn_handle h, double beta, int32_t trial_sweeps, int32_t* chosen);
+
 /* Which kernel path the handle uses: 0 = generic global-memory sweep,
  * 1 = streaming shared-memory sweep, 2 = shared-memory-resident sweep,
  * 3 = bit-packed streaming sweep.  Path 3 keeps the lattice in HBM as one bit

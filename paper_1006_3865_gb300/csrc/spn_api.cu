@@ -6,12 +6,16 @@
 // folds the per-sweep deltas into E, M and the trace when it is asked for them.
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "spn.h"
@@ -544,6 +548,116 @@ int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t se
   h->tile_y = ty;
   h->step_slices = step_slices;
   h->seg = seg;
+  return SPN_OK;
+}
+
+int spn_autotune(spn_handle h, double beta, int32_t trial_sweeps, int32_t* chosen) {
+  if (!h) return fail(SPN_E_ARG, "handle is NULL");
+  if (h->ea || h->heis) return fail(SPN_E_STATE, "the autotuner tunes the streaming sweep of Ising lattices");
+  if (h->path != spn::kPathStream && h->path != spn::kPathPacked)
+    return fail(SPN_E_STATE, "the handle's path is not a streaming one");
+  if (!(beta >= 0.0) || trial_sweeps < 1) return fail(SPN_E_ARG, "bad arguments");
+  const bool packed = h->path == spn::kPathPacked;
+  const spn::Lattice g = packed ? h->g : stream_lattice(h);
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int, int>, std::array<int, 3>> cache;
+  const auto key = std::make_tuple(g.nd, g.Lx, g.Ly, g.Lz, (int)packed, spn::device_sm_count());
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      h->tile_y = it->second[0];
+      h->step_slices = it->second[1];
+      h->seg = it->second[2];
+      if (chosen) std::memcpy(chosen, it->second.data(), 3 * sizeof(int32_t));
+      return SPN_OK;
+    }
+  }
+  SPN_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+  // scratch ping-pong lattices from a hot start: the handle's own state is untouched
+  const size_t rows = (size_t)(g.N / g.Lx);
+  const size_t bytes = packed ? (size_t)spn::packed_row_words(g.Lx) * 4 * rows : (size_t)(g.pitch ? g.pitch : g.Lx) * rows;
+  void* buf[2] = {nullptr, nullptr};
+  int8_t* dense = nullptr;
+  unsigned long long* acc = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SPN_OK;
+  auto cleanup = [&] {
+    cudaFree(buf[0]);
+    cudaFree(buf[1]);
+    cudaFree(dense);
+    cudaFree(acc);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&buf[0], bytes) != cudaSuccess || cudaMalloc(&buf[1], bytes) != cudaSuccess ||
+      cudaMalloc(&dense, (size_t)g.N) != cudaSuccess || cudaMalloc(&acc, 16) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return fail(SPN_E_NOMEM, "autotune scratch");
+  }
+  cudaError_t e = spn::launch_init_hot(h->g, dense, h->seed, h->stream_id, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf[0], packed ? 0 : 1, bytes, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf[1], packed ? 0 : 1, bytes, h->st);
+  if (e == cudaSuccess)
+    e = packed ? spn::launch_pack(h->g, dense, static_cast<uint32_t*>(buf[0]), h->st)
+               : cudaMemcpy2DAsync(buf[0], g.pitch ? g.pitch : g.Lx, dense, g.Lx, g.Lx, rows, cudaMemcpyDeviceToDevice,
+                                   h->st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "autotune set-up");
+  }
+  const spn::DevThr T = spn::make_thresholds(beta);
+  const spn::PhiloxKeys K = spn::philox_keys(h->seed);
+  // candidates: bands (3D), slices per step, segments per band
+  std::vector<int> tys;
+  if (g.nd == 3) {
+    for (int ty = 32; ty >= 2; ty -= 2)
+      if (g.Ly % ty == 0 && spn::stream_path_supported(g, ty, packed)) tys.push_back(ty);
+  } else {
+    tys.push_back(1);
+  }
+  const int sms = spn::device_sm_count();
+  double best = -1.0;
+  std::array<int, 3> pick = {h->tile_y, h->step_slices, h->seg};
+  for (int ty : tys) {
+    const int S = g.nd == 3 ? g.Lz : g.Ly, tiles = g.nd == 3 ? g.Ly / ty : 1;
+    for (int R : {0, 1, 2, 4}) {
+      for (int per_sm : {0, 2, 4, 6, 8}) {  // 0: the default segment count
+        const int seg = per_sm ? std::max(1, std::min(S, (per_sm * sms + tiles - 1) / tiles)) : 0;
+        const spn::StreamGeom geo = spn::stream_geometry(g, ty, R, seg, packed);
+        if (!spn::stream_geometry_ok(g, geo)) continue;
+        float ms = 0.0f;
+        int cur = 0;
+        for (int rep = 0; rep < 2 && rc == SPN_OK; ++rep) {  // the first pass warms up
+          if (cudaEventRecord(e0, h->st) != cudaSuccess) rc = SPN_E_CUDA;
+          for (int t = 0; t < trial_sweeps && rc == SPN_OK; ++t, cur ^= 1)
+            if (spn::launch_sweep_stream(g, buf[cur], buf[cur ^ 1], geo, T, K, h->stream_id, (uint32_t)t, acc, h->d_err,
+                                         h->st) != cudaSuccess)
+              rc = SPN_E_CUDA;
+          if (rc == SPN_OK && (cudaEventRecord(e1, h->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = SPN_E_CUDA;
+        }
+        if (rc != SPN_OK) break;
+        const double rate = (double)g.N * trial_sweeps / ((double)ms * 1e6);
+        if (rate > best) {
+          best = rate;
+          pick = {ty, R, seg};
+        }
+      }
+    }
+  }
+  cleanup();
+  if (rc != SPN_OK) return fail(SPN_E_CUDA, "autotune trial");
+  h->tile_y = pick[0];
+  h->step_slices = pick[1];
+  h->seg = pick[2];
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = pick;
+  }
+  if (chosen) std::memcpy(chosen, pick.data(), 3 * sizeof(int32_t));
   return SPN_OK;
 }
 

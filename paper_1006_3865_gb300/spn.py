@@ -99,6 +99,7 @@ _SIGNATURES = {
     "spn_batch_exchange_counts": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_measure_overlap": (_c.c_int, [_vp]),
     "spn_multi_autotune": (_c.c_int, [_vp, _i32, _vp, _sz]),
+    "spn_autotune": (_c.c_int, [_vp, _dbl, _i32, _vp]),
     "spn_multi_groups": (_c.c_int, [_vp, _vp, _sz]),
     "spn_multi_set_launch": (_c.c_int, [_vp, _i32, _i32, _i32]),
     "spn_heis_get_spins": (_c.c_int, [_vp, _vp, _sz]),
@@ -278,6 +279,12 @@ class Lattice:
 
     def set_tiling(self, tile_y: int, step_slices: int = 0, seg: int = 0):
         _check(self._lib.spn_set_tiling(self._h, tile_y, step_slices, seg))
+
+    def autotune(self, beta: float, trial_sweeps: int = 5) -> tuple[int, int, int]:
+        """Time the streaming tilings on a scratch copy and keep the fastest (tile_y, step_slices, seg)."""
+        out = np.zeros(3, np.int32)
+        _check(self._lib.spn_autotune(self._h, float(beta), int(trial_sweeps), _ptr(out)))
+        return tuple(int(x) for x in out)
 
     @property
     def path(self) -> int:

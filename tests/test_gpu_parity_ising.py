@@ -143,3 +143,26 @@ def test_full_size_2d_L16384():
 
 def test_full_size_3d_L512():
     _sampled_full_size(spn.SPN_ISING3D, (512, 512, 512), inputs.BETA_C_3D, 2)
+
+
+@pytest.mark.parametrize("model,dims,path", [(spn.SPN_ISING2D, (256, 96), spn.PATH_STREAM),
+                                             (spn.SPN_ISING2D, (130, 64), spn.PATH_STREAM),
+                                             (spn.SPN_ISING3D, (64, 16, 12), spn.PATH_STREAM),
+                                             (spn.SPN_ISING3D, (64, 16, 12), spn.PATH_PACKED)])
+def test_autotune_keeps_state_and_results(model, dims, path):
+    """The streaming autotuner times tilings on a scratch copy: the handle's
+    spins and counters are unchanged, and later sweeps still match the oracle."""
+    seed, beta = inputs.unit_seed(16), 0.41
+    lat = spn.Lattice(model, dims, seed)
+    lat.path = path
+    lat.sweep(beta, 3)
+    before = lat.get_spins()
+    tiling = lat.autotune(beta, 2)
+    assert len(tiling) == 3
+    assert np.array_equal(lat.get_spins(), before) and lat.sweep_count() == 3
+    lat.sweep(beta, 4)
+    s = oracle.init_hot(dims, seed)
+    _, _, tE, tM = oracle.sweeps(dims, s, beta, 7, seed)
+    gE, gM = lat.trace()
+    assert np.array_equal(lat.get_spins(), s) and np.array_equal(gE, tE) and np.array_equal(gM, tM)
+    lat.close()
