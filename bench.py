@@ -69,7 +69,7 @@ def _args():
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
     p.add_argument("--profile-L", type=int, default=0, help="lattice extent of a 2d / packed2d profile case")
-    p.add_argument("--forms", default="batched,ea,served,dc,packed,overlap,heis",
+    p.add_argument("--forms", default="batched,ea,served,dc,dc_tau,packed,overlap,heis",
                    help="extra forms measured after the plain step (comma list; empty for none)")
     p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
     p.add_argument("--ea-sweeps", type=int, default=EA_SWEEPS)
@@ -133,17 +133,19 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _profile_traffic():
+def _profile_traffic(tiling):
     """Per-launch DRAM bytes of the 2D sweep kernel from the committed ncu summary,
-    valid only while the kernel source is the one that was profiled."""
+    valid only while the kernel source and its tiling (band, slices per step,
+    segments) are the ones that were profiled."""
     try:
         text = open(PROFILE_2D).read()
         sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text).group(1)
         tb = float(re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text).group(1))
+        prof_tiling = tuple(int(x) for x in re.search(r"tiling:\s*(\d+),(\d+),(\d+)", text).groups())
     except Exception:
         return None
     cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
-    return tb if cur == sha else None
+    return tb if cur == sha and tuple(tiling) == prof_tiling else None
 
 
 class ClockSampler:
@@ -407,6 +409,79 @@ def form_dc(stream, tiles=((256, 64), (512, 128), (64, 64)), hits=(1, 2, 4), swe
                         "(attempts count every hit)"}
 
 
+def form_dc_tau(L=128, replicas=16, sweeps=100000, therm=20000, tiles=((64, 64), (64, 16)), hits=(1, 2, 4)):
+    """What the multi-hit of Sec. 3 costs in decorrelation near T_c: integrated
+    autocorrelation times of E and |M| from the per-sweep traces of independent
+    2D L = 128 lattices at T = 2.269185 (hot starts, the first `therm`
+    single-hit sweep equivalents dropped), for the canonical sweep and for the
+    double-checkerboard order with k hits per tile.  A double-checkerboard sweep
+    does k attempts per site, so tau x k is its time in single-hit sweep
+    equivalents (equal attempts); `cost` = that over the canonical sweep's tau.
+    The canonical replicas run as one batched resident launch (spn_multi), the
+    double-checkerboard replicas on their own CUDA streams."""
+    import numpy as np
+    import torch
+
+    from paper_1006_3865_gb300 import autocorr, inputs, spn
+
+    beta = 1.0 / TEMPS_2D[1]
+    streams = [torch.cuda.Stream() for _ in range(replicas)]
+    chunk = 1000
+
+    def canonical():
+        jobs = [(spn.SPN_ISING2D, (L, L), beta, sweeps, inputs.unit_seed(7100 + r), r) for r in range(replicas)]
+        m = spn.Multi(jobs)
+        t0 = time.perf_counter()
+        m.run()
+        m.sync()
+        wall = time.perf_counter() - t0
+        traces = [m.result(r, spins=False)[1:] for r in range(replicas)]
+        m.close()
+        return summarise(traces, 1, sweeps, wall)
+
+    def summarise(traces, k, n, wall):
+        drop = therm // k
+        E = np.stack([t[0][-n:][drop:] for t in traces])
+        M = np.abs(np.stack([t[1][-n:][drop:] for t in traces]))
+        tE, eE, _ = autocorr.tau_int(E)
+        tM, eM, _ = autocorr.tau_int(M)
+        return {"tau_E": tE, "tau_E_err": eE, "tau_absM": tM, "tau_absM_err": eM,
+                "tau_E_sweep_equiv": tE * k, "tau_absM_sweep_equiv": tM * k,
+                "sweeps_per_replica": n, "wall_s": wall,
+                "e_per_site": float(E.mean()) / (L * L), "absm_per_site": float(M.mean()) / (L * L)}
+
+    def run(tile, k):
+        lats = []
+        for r in range(replicas):
+            lat = spn.Lattice(spn.SPN_ISING2D, (L, L), inputs.unit_seed(7100 + r))
+            lat.set_stream(streams[r])
+            lats.append(lat)
+        n = sweeps // k  # equal attempts for every k
+        t0 = time.perf_counter()
+        for c0 in range(0, n, chunk):
+            m = min(chunk, n - c0)
+            for lat in lats:
+                lat.sweep_dc(beta, m, tile, k)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        traces = [lat.trace() for lat in lats]
+        for lat in lats:
+            lat.close()
+        return summarise(traces, k, n, wall)
+
+    out = {"canonical": canonical()}
+    base = out["canonical"]
+    for tile in tiles:
+        for k in hits:
+            r = run(tile, k)
+            r["cost_E"] = r["tau_E_sweep_equiv"] / base["tau_E"]
+            r["cost_absM"] = r["tau_absM_sweep_equiv"] / base["tau_absM"]
+            out[f"{tile[0]}x{tile[1]}_k{k}"] = r
+    return {"by_order": out,
+            "workload": f"2D Ising L={L} at T=2.269185, {replicas} replicas x {sweeps} single-hit sweep equivalents "
+                        f"(first {therm} dropped); tau_int by Sokal's window (c = 6)"}
+
+
 def form_packed(stream):
     """The plain step's lattices held at one bit per spin (the packed path):
     2D L = 16384 at the three temperatures (200 sweeps each, from the hot start)
@@ -536,6 +611,8 @@ def run_forms(a, stream):
             out["served"] = form_served(a.served_requests)
         elif f == "dc":
             out["double_checkerboard"] = form_dc(stream)
+        elif f == "dc_tau":
+            out["double_checkerboard_autocorrelation"] = form_dc_tau()
         elif f == "packed":
             out["packed"] = form_packed(stream)
         elif f == "overlap":
@@ -609,8 +686,10 @@ def main():
     lat2.set_stream(stream)
     lat3.set_stream(stream)
     # streaming tilings from the library's autotuner (scratch trials, before any timing)
+    nt0 = spn.launch_count()
     tiling2 = lat2.autotune(1.0 / TEMPS_2D[1], 4)
     tiling3 = lat3.autotune(BETA_3D, 4)
+    tuning_launches = spn.launch_count() - nt0
 
     def step(evs=None):
         for i, T in enumerate(TEMPS_2D):
@@ -726,7 +805,7 @@ def main():
         cpu = _cpu_baseline(1)
     if rank != 0:
         return
-    traffic = _profile_traffic()
+    traffic = _profile_traffic(tiling2)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -737,7 +816,8 @@ def main():
                    "sweep_ms_2d": launch_ms, "sweep_ms_3d": launch3_ms,
                    "attempts_per_ns_2d": L2D * L2D / (launch_ms * 1e6),
                    "attempts_per_ns_3d": L3D ** 3 / (launch3_ms * 1e6),
-                   "tiling_2d": tiling2, "tiling_3d": tiling3},
+                   "tiling_2d": tiling2, "tiling_3d": tiling3, "tuning_launches": tuning_launches,
+                   "launches_before_tuning": nt0},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "k_sweep_stream<2> (2D L=16384)", "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes},

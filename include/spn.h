@@ -171,7 +171,8 @@ int spn_set_tiling(spn_handle h, int32_t tile_y, int32_t step_slices, int32_t se
  * height (3D: even divisors of Ly up to 32), slices per step (automatic, 1, 2,
  * 4) and segment count (automatic, or 2, 4, 6, 8 CTAs per SM) on trial_sweeps
  * sweeps of a scratch copy of the lattice at beta, and set the fastest as the
- * handle's tiling.  The handle's spins, counters and trace are untouched and
+ * handle's tiling (the default tiling, timed first, is replaced only by one
+ * more than 1% faster).  The handle's spins, counters and trace are untouched and
  * results never depend on the tiling.  Choices are cached per (shape, path,
  * device) for the process.  chosen (optional, 3 ints): tile_y, step_slices,
  * seg as for spn_set_tiling.  SPN_E_STATE if the handle is not on a streaming

@@ -641,7 +641,10 @@ int spn_autotune(spn_handle h, double beta, int32_t trial_sweeps, int32_t* chose
         }
         if (rc != SPN_OK) break;
         const double rate = (double)g.N * trial_sweeps / ((double)ms * 1e6);
-        if (rate > best) {
+        // the first candidate (tallest band, default slices and segments) is the
+        // default tiling; another must beat the best by more than 1% (trial
+        // noise) to be taken
+        if (best < 0.0 || rate > 1.01 * best) {
           best = rate;
           pick = {ty, R, seg};
         }

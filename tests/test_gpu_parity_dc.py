@@ -55,7 +55,8 @@ def _run(dims, seed, plan, stream=0):
 
 
 @pytest.mark.parametrize("dims,tile,hits", [((128, 64), (64, 8), 1), ((128, 64), (64, 8), 3), ((256, 96), (64, 12), 2),
-                                            ((256, 40), (128, 10), 4), ((128, 6), (64, 3), 2)])
+                                            ((256, 40), (128, 10), 4), ((128, 6), (64, 3), 2),
+                                            ((128, 128), (64, 64), 4), ((128, 128), (64, 16), 2)])
 def test_dc_2d(dims, tile, hits):
     _run(dims, inputs.unit_seed(31), [("dc", 1.0 / inputs.TC_2D, 7, tile, hits)], stream=3)
 
