@@ -186,9 +186,13 @@ int spn_autotune(spn_handle h, double beta, int32_t trial_sweeps, int32_t* chose
  * sites, as many of the odd-x sites, zero words up to a multiple of 4; a set
  * bit is spin -1); spn_sweep packs the int8 lattice on entry when needed, and
  * the calls that read spins (spn_get_spins, spn_recompute, the other paths)
- * unpack it first.  Results never depend on the path.  spn_set_path fails
- * with SPN_E_ARG if the path does not support the lattice (bonds, a band that
- * does not divide Ly). */
+ * unpack it first.  Path 2 runs every sweep of one spn_sweep call in a single
+ * launch, the lattice held as bits in the shared memory of one CTA or of a
+ * cluster of up to 8 (at most 200 KB each, Ising only); it is the default for
+ * lattices of at most 65536 sites that fit one CTA, path 1 for larger ones.
+ * Results never depend on the path.  spn_set_path fails with SPN_E_ARG if the
+ * path does not support the lattice (bonds, a band that does not divide Ly, a
+ * lattice too large for path 2). */
 int spn_get_path(spn_handle h, int32_t* path);
 int spn_set_path(spn_handle h, int32_t path);
 

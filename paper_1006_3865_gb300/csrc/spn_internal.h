@@ -215,4 +215,7 @@ struct spn_ctx {
   int* d_err = nullptr;
   int* d_bad = nullptr;
   unsigned long long* d_obs = nullptr;
+  // resident path: the one-instance work list of the persistent kernel
+  spn::ResInst* d_res = nullptr;
+  int* d_resq = nullptr;  // [0] queue order (0), [1] queue head
 };

@@ -445,7 +445,8 @@ class EABatch:
         """The overlap measurements so far: nmeas, the last q [pairs, 32], the
         exact integer sums of q^2 and q^4 (Python ints, [pairs][32]), the
         moments <q^2>, <q^4> per pair and temperature, and the Binder cumulant
-        per temperature g = (3 - [<q^4>] / [<q^2>]^2) / 2 over the pairs."""
+        per temperature g = (3 - [<q^4>] / [<q^2>]^2) / 2 over the pairs (NaN
+        where [<q^2>] = 0: every pair kept q = 0, so g is undefined)."""
         P = self.nsamples // 2
         n = _c.c_int64()
         q = np.empty((P, 32), np.int64)
@@ -459,7 +460,10 @@ class EABatch:
             m2 = np.array([[x / n.value for x in row] for row in s2])
             m4 = np.array([[x / n.value for x in row] for row in s4])
             out["q2"], out["q4"] = m2, m4
-            out["binder"] = 0.5 * (3.0 - m4.mean(axis=0) / m2.mean(axis=0) ** 2)
+            a2, a4 = m2.mean(axis=0), m4.mean(axis=0)
+            ratio = np.full_like(a2, np.nan)
+            np.divide(a4, a2 ** 2, out=ratio, where=a2 > 0)
+            out["binder"] = 0.5 * (3.0 - ratio)
         return out
 
     def overlap_reset(self):
