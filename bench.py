@@ -65,7 +65,8 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d", "heis3d"], default=None,
+    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d", "heis3d", "batched"],
+                   default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
     p.add_argument("--profile-L", type=int, default=0, help="lattice extent of a 2d / packed2d profile case")
@@ -102,6 +103,16 @@ def run_profile_case(a):
         lat.sweep_dc(1.0 / TEMPS_2D[1], a.profile_sweeps, (64, 64), 4)
         print("profile case dc E, M =", lat.observables(), flush=True)
         lat.close()
+        return
+    if a.profile_case == "batched":  # resident kernel: 456 lattices 2D L = 256 at T_c, 3 per SM
+        jobs = [(spn.SPN_ISING2D, (256, 256), 1.0 / TEMPS_2D[1], a.profile_sweeps, inputs.unit_seed(600 + i), i)
+                for i in range(456)]
+        m = spn.Multi(jobs)
+        for _ in range(2):  # the second run replays the captured graph
+            m.run()
+            m.sync()
+        print("profile case batched E, M of job 0 =", [int(x[-1]) for x in m.result(0, spins=False)[1:]], flush=True)
+        m.close()
         return
     if a.profile_case == "heis3d":  # Heisenberg spins, 3D L = 256 at beta = 0.693
         h = spn.HeisLattice((256, 256, 256), inputs.unit_seed(9))
