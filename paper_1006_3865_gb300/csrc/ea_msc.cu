@@ -16,9 +16,14 @@
 // give the unsatisfied bonds of all 32 replicas; a bit-sliced adder counts them;
 // replicas with dE = 4 (ND - k) > 0 accept iff u < thr(beta of their
 // temperature, dE).  The thresholds of one dE level grow with the temperature index, so the
-// accepting temperatures form a suffix: a 5-step search over the 32 sorted
-// thresholds gives its start and a 33-entry table, kept in step with the slot
-// permutation, turns it into the slot mask.  After every X-th sweep the CTA
+// accepting temperatures form a suffix: the number of thresholds <= u gives its
+// start and a 33-entry table, kept in step with the slot permutation, turns it
+// into the slot mask.  That number comes from a 1024-bucket table over the top
+// 10 bits of u (the counts at both ends of the bucket) and one compare; only a
+// bucket holding two or more thresholds takes the 5-step binary search.  When
+// Lx is a multiple of 8 a thread updates four consecutive same-colour words of
+// a row at once: 16-byte shared-memory loads and stores, and the one Philox
+// call whose four words are the four sites' u.  After every X-th sweep the CTA
 // counts unsatisfied bonds per replica, takes the exchange decisions of the
 // even or odd temperature pairs with host-built tables of
 // floor(exp(dbeta * dE) 2^32), and updates the permutation.
@@ -41,6 +46,9 @@ namespace spn {
 // colour-separated shared-memory word index of site (x, y, z)
 __device__ __forceinline__ int ea_slot(int x, int row, int h) { return (row * 2 + (x & 1)) * h + (x >> 1); }
 
+constexpr int kEaBucketShift = 22;                      // bucket of u = u >> 22
+constexpr int kEaBuckets = 1 << (32 - kEaBucketShift);  // per dE level
+
 // One sample (CTA) of a batch launch, or one served job of a multi-job launch.
 template <int ND>
 __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
@@ -54,6 +62,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   uint8_t* tos = reinterpret_cast<uint8_t*>(ucount + 32);     // 32 temp_of_slot
   uint8_t* sot = tos + 32;                                    // 32 slot_of_temp
   int* xcount = reinterpret_cast<int*>(sot + 32);             // 32 accepted exchanges this launch
+  uint16_t* lut = reinterpret_cast<uint16_t*>(xcount + 32);   // 3 x kEaBuckets: lo | hi << 8
 
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
   const int pair = sample >> 1, half = sample & 1;
@@ -74,6 +83,20 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   }
   __syncthreads();
   if (tid < 32) sot[tos[tid]] = (uint8_t)tid;
+  // bucket table: for u in [b 2^22, (b+1) 2^22 - 1], the number of thresholds
+  // <= u lies between lo = #(thr <= b 2^22) and hi = #(thr <= (b+1) 2^22 - 1)
+  for (int i = tid; i < ND * kEaBuckets; i += nth) {
+    const uint32_t* tl = thr + 32 * (i / kEaBuckets);
+    const uint32_t b = (uint32_t)(i % kEaBuckets);
+    const uint32_t u0 = b << kEaBucketShift, u1 = u0 + ((1u << kEaBucketShift) - 1u);
+    int lo = 0, hi = 0;
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      lo += tl[t] <= u0 ? 1 : 0;
+      hi += tl[t] <= u1 ? 1 : 0;
+    }
+    lut[i] = (uint16_t)(lo | (hi << 8));
+  }
   __syncthreads();
   if (tid < 32) {  // suffix[t0] = slots of temperatures t >= t0
     uint32_t v = 1u << sot[tid];
@@ -88,68 +111,127 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   __syncthreads();
 
   const int halfN = N >> 1;
+  // number of thresholds of level lv that are <= u (the accepting temperatures
+  // are the ones from there up)
+  auto count_le = [&](int lv, uint32_t u) -> int {
+    const uint32_t* tl = thr + 32 * lv;
+    const uint32_t e = lut[lv * kEaBuckets + (u >> kEaBucketShift)];
+    const int lo = (int)(e & 0xffu), hi = (int)(e >> 8);
+    if (hi - lo <= 1) return lo + ((hi > lo && tl[lo & 31] <= u) ? 1 : 0);
+    int cnt = 0;
+    cnt += (tl[cnt + 15] <= u) ? 16 : 0;
+    cnt += (tl[cnt + 7] <= u) ? 8 : 0;
+    cnt += (tl[cnt + 3] <= u) ? 4 : 0;
+    cnt += (tl[cnt + 1] <= u) ? 2 : 0;
+    cnt += (tl[cnt] <= u) ? 1 : 0;
+    cnt += (cnt == 31 && tl[31] <= u) ? 1 : 0;  // all 32 thresholds <= u
+    return cnt;
+  };
+  // new word of a site: s its 32 replicas, bits its bond byte, n* the neighbour
+  // words (x+, x-, y+, y-, z+, z-), u its uniform deviate
+  auto update = [&](uint32_t s, uint32_t bits, uint32_t nxp, uint32_t nxm, uint32_t nyp, uint32_t nym, uint32_t nzp,
+                    uint32_t nzm, uint32_t u) -> uint32_t {
+    // bond masks: bits 0..2 forward, 3..5 backward
+    const uint32_t ux = s ^ nxp ^ (0u - (bits & 1u));
+    const uint32_t uy = s ^ nyp ^ (0u - ((bits >> 1) & 1u));
+    const uint32_t vx = s ^ nxm ^ (0u - ((bits >> 3) & 1u));
+    const uint32_t vy = s ^ nym ^ (0u - ((bits >> 4) & 1u));
+    uint32_t uz = 0, vz = 0;
+    if constexpr (ND == 3) {
+      uz = s ^ nzp ^ (0u - ((bits >> 2) & 1u));
+      vz = s ^ nzm ^ (0u - ((bits >> 5) & 1u));
+    }
+    // bit-sliced count of unsatisfied bonds k = s0 + 2 s1 + 4 s2 (0..2 ND)
+    const uint32_t x1 = ux ^ uy ^ uz, y1 = (ux & uy) | (uz & (ux ^ uy));
+    const uint32_t x2 = vx ^ vy ^ vz, y2 = (vx & vy) | (vz & (vx ^ vy));
+    const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
+    const uint32_t s1 = y1 ^ y2 ^ cc, s2 = (y1 & y2) | (cc & (y1 ^ y2));
+    uint32_t A[ND];
+#pragma unroll
+    for (int lv = 0; lv < ND; ++lv) A[lv] = suffix[count_le(lv, u)];
+    // dE = 4 (ND - k): k >= ND accepts always; k = ND - 1 - lv takes level lv (dE = 4 (lv + 1))
+    const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
+    uint32_t acc;
+    if constexpr (ND == 3) {
+      acc = (s2 | (s0 & s1)) | (k2 & A[0]) | (k1 & A[1]) | (k0 & A[2]);
+    } else {
+      acc = (s1 | s2) | (k1 & A[0]) | (k0 & A[1]);
+    }
+    return s ^ acc;
+  };
+  const bool groups4 = (a.Lx & 7) == 0;  // half-rows of whole 4-word groups
   for (int it = 0; it < a.nsweeps; ++it) {
     const uint32_t sweep = a.sweep0 + (uint32_t)it;
     for (int c = 0; c < 2; ++c) {
-      for (int m = tid; m < halfN; m += nth) {
-        const uint32_t row = fdiv((uint32_t)m, a.div_h);
-        const int k = m - (int)row * h;
-        const uint32_t z = ND == 3 ? fdiv(row, a.div_ly) : 0u;
-        const int y = (int)row - (int)z * a.Ly;
-        const int par = (c ^ (y + (int)z)) & 1;
-        const int x = 2 * k + par;
-        const int q = ea_slot(x, (int)row, h);
-        const uint32_t s = sp[q];
-        const uint32_t bits = bb[q];
-        // neighbours (other parity in the row for x; same parity in rows y +- 1, z +- 1)
-        const int xm = x == 0 ? a.Lx - 1 : x - 1, xp = x + 1 == a.Lx ? 0 : x + 1;
-        const int rym = y == 0 ? (int)row + a.Ly - 1 : (int)row - 1;
-        const int ryp = y + 1 == a.Ly ? (int)row - a.Ly + 1 : (int)row + 1;
-        const uint32_t nxp = sp[ea_slot(xp, (int)row, h)], nxm = sp[ea_slot(xm, (int)row, h)];
-        const uint32_t nyp = sp[ea_slot(x, ryp, h)], nym = sp[ea_slot(x, rym, h)];
-        // bond masks: bits 0..2 forward, 3..5 backward
-        const uint32_t ux = s ^ nxp ^ (0u - (bits & 1u));
-        const uint32_t uy = s ^ nyp ^ (0u - ((bits >> 1) & 1u));
-        const uint32_t vx = s ^ nxm ^ (0u - ((bits >> 3) & 1u));
-        const uint32_t vy = s ^ nym ^ (0u - ((bits >> 4) & 1u));
-        uint32_t uz = 0, vz = 0;
-        if constexpr (ND == 3) {
-          const int rzm = z == 0 ? (int)row + nrow - a.Ly : (int)row - a.Ly;
-          const int rzp = (int)z + 1 == a.Lz ? (int)row - nrow + a.Ly : (int)row + a.Ly;
-          uz = s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u));
-          vz = s ^ sp[ea_slot(x, rzm, h)] ^ (0u - ((bits >> 5) & 1u));
+      const uint32_t c2 = (uint32_t)c | (3u << 1);
+      if (groups4) {
+        // sites m0 .. m0 + 3 of this colour: one row, words k0 .. k0 + 3 of its
+        // colour-c half; the Philox call of counter m0 / 4 gives their four u
+        for (int g = tid; g < (halfN >> 2); g += nth) {
+          const uint32_t m0 = 4u * (uint32_t)g;
+          const uint32_t row = fdiv(m0, a.div_h);
+          const int k0 = (int)m0 - (int)row * h;
+          const uint32_t z = ND == 3 ? fdiv(row, a.div_ly) : 0u;
+          const int y = (int)row - (int)z * a.Ly;
+          const int par = (c ^ (y + (int)z)) & 1;
+          const int q0 = ((int)row * 2 + par) * h + k0;
+          const int o0 = ((int)row * 2 + (par ^ 1)) * h;  // the row's other-parity words
+          const int rym = y == 0 ? (int)row + a.Ly - 1 : (int)row - 1;
+          const int ryp = y + 1 == a.Ly ? (int)row - a.Ly + 1 : (int)row + 1;
+          const uint4 S = *reinterpret_cast<const uint4*>(sp + q0);
+          const uint32_t B = *reinterpret_cast<const uint32_t*>(bb + q0);
+          const uint4 O4 = *reinterpret_cast<const uint4*>(sp + o0 + k0);
+          // the fifth other-parity word: x - 1 of the first site (even x) or
+          // x + 1 of the last site (odd x), periodic in x
+          const uint32_t oe = par ? sp[o0 + (k0 + 4 == h ? 0 : k0 + 4)] : sp[o0 + (k0 == 0 ? h - 1 : k0 - 1)];
+          const uint4 YP = *reinterpret_cast<const uint4*>(sp + (ryp * 2 + par) * h + k0);
+          const uint4 YM = *reinterpret_cast<const uint4*>(sp + (rym * 2 + par) * h + k0);
+          uint4 ZP = make_uint4(0, 0, 0, 0), ZM = ZP;
+          if constexpr (ND == 3) {
+            const int rzm = z == 0 ? (int)row + nrow - a.Ly : (int)row - a.Ly;
+            const int rzp = (int)z + 1 == a.Lz ? (int)row - nrow + a.Ly : (int)row + a.Ly;
+            ZP = *reinterpret_cast<const uint4*>(sp + (rzp * 2 + par) * h + k0);
+            ZM = *reinterpret_cast<const uint4*>(sp + (rzm * 2 + par) * h + k0);
+          }
+          const U4 P = philox10((uint32_t)g, sweep, c2, (uint32_t)sample, a.K);
+          const uint32_t o[4] = {O4.x, O4.y, O4.z, O4.w};
+          // even x: x+1 is other-parity word k, x-1 word k-1; odd x: x-1 word k, x+1 word k+1
+          const uint32_t xp0 = par ? o[1] : o[0], xm0 = par ? o[0] : oe;
+          const uint32_t xp1 = par ? o[2] : o[1], xm1 = par ? o[1] : o[0];
+          const uint32_t xp2 = par ? o[3] : o[2], xm2 = par ? o[2] : o[1];
+          const uint32_t xp3 = par ? oe : o[3], xm3 = par ? o[3] : o[2];
+          uint4 R;
+          R.x = update(S.x, B & 0xffu, xp0, xm0, YP.x, YM.x, ZP.x, ZM.x, P.x);
+          R.y = update(S.y, (B >> 8) & 0xffu, xp1, xm1, YP.y, YM.y, ZP.y, ZM.y, P.y);
+          R.z = update(S.z, (B >> 16) & 0xffu, xp2, xm2, YP.z, YM.z, ZP.z, ZM.z, P.z);
+          R.w = update(S.w, B >> 24, xp3, xm3, YP.w, YM.w, ZP.w, ZM.w, P.w);
+          *reinterpret_cast<uint4*>(sp + q0) = R;
         }
-        // bit-sliced count of unsatisfied bonds k = s0 + 2 s1 + 4 s2 (0..2 ND)
-        const uint32_t x1 = ux ^ uy ^ uz, y1 = (ux & uy) | (uz & (ux ^ uy));
-        const uint32_t x2 = vx ^ vy ^ vz, y2 = (vx & vy) | (vz & (vx ^ vy));
-        const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
-        const uint32_t s1 = y1 ^ y2 ^ cc, s2 = (y1 & y2) | (cc & (y1 ^ y2));
-        // u of this site (one word per site, shared by the 32 replicas)
-        const U4 P = philox10((uint32_t)m >> 2, sweep, (uint32_t)c | (3u << 1), (uint32_t)sample, a.K);
-        const uint32_t u = u4_word(P, m & 3);
-        // accepting temperatures per level: count thresholds <= u (sorted), suffix mask
-        uint32_t A[ND];
-#pragma unroll
-        for (int lv = 0; lv < ND; ++lv) {
-          const uint32_t* tl = thr + 32 * lv;
-          int cnt = 0;
-          cnt += (tl[cnt + 15] <= u) ? 16 : 0;
-          cnt += (tl[cnt + 7] <= u) ? 8 : 0;
-          cnt += (tl[cnt + 3] <= u) ? 4 : 0;
-          cnt += (tl[cnt + 1] <= u) ? 2 : 0;
-          cnt += (tl[cnt] <= u) ? 1 : 0;
-          cnt += (cnt == 31 && tl[31] <= u) ? 1 : 0;  // all 32 thresholds <= u
-          A[lv] = suffix[cnt];
+      } else {
+        for (int m = tid; m < halfN; m += nth) {
+          const uint32_t row = fdiv((uint32_t)m, a.div_h);
+          const int k = m - (int)row * h;
+          const uint32_t z = ND == 3 ? fdiv(row, a.div_ly) : 0u;
+          const int y = (int)row - (int)z * a.Ly;
+          const int par = (c ^ (y + (int)z)) & 1;
+          const int x = 2 * k + par;
+          const int q = ea_slot(x, (int)row, h);
+          // neighbours (other parity in the row for x; same parity in rows y +- 1, z +- 1)
+          const int xm = x == 0 ? a.Lx - 1 : x - 1, xp = x + 1 == a.Lx ? 0 : x + 1;
+          const int rym = y == 0 ? (int)row + a.Ly - 1 : (int)row - 1;
+          const int ryp = y + 1 == a.Ly ? (int)row - a.Ly + 1 : (int)row + 1;
+          uint32_t nzp = 0, nzm = 0;
+          if constexpr (ND == 3) {
+            const int rzm = z == 0 ? (int)row + nrow - a.Ly : (int)row - a.Ly;
+            const int rzp = (int)z + 1 == a.Lz ? (int)row - nrow + a.Ly : (int)row + a.Ly;
+            nzp = sp[ea_slot(x, rzp, h)];
+            nzm = sp[ea_slot(x, rzm, h)];
+          }
+          // u of this site (one word per site, shared by the 32 replicas)
+          const U4 P = philox10((uint32_t)m >> 2, sweep, c2, (uint32_t)sample, a.K);
+          sp[q] = update(sp[q], bb[q], sp[ea_slot(xp, (int)row, h)], sp[ea_slot(xm, (int)row, h)],
+                         sp[ea_slot(x, ryp, h)], sp[ea_slot(x, rym, h)], nzp, nzm, u4_word(P, m & 3));
         }
-        // dE = 4 (ND - k): k >= ND accepts always; k = ND - 1 - lv takes level lv (dE = 4 (lv + 1))
-        const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
-        uint32_t acc;
-        if constexpr (ND == 3) {
-          acc = (s2 | (s0 & s1)) | (k2 & A[0]) | (k1 & A[1]) | (k0 & A[2]);
-        } else {
-          acc = (s1 | s2) | (k1 & A[0]) | (k0 & A[1]);
-        }
-        sp[q] = s ^ acc;
       }
       __syncthreads();
     }
@@ -437,7 +519,9 @@ int ea_fail(int code, const char* msg) {
   return code;
 }
 
-size_t ea_smem(int N) { return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4; }
+size_t ea_smem(int N) {
+  return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4 + 3 * spn::kEaBuckets * 2;
+}
 
 }  // namespace
 

@@ -53,6 +53,29 @@ def test_batch_matches_oracle(dims, ns, X, sweeps):
     b.close()
 
 
+@pytest.mark.parametrize("dims,ladder", [((8, 8, 8), "equal"), ((16, 8, 4), "pairs"), ((8, 6, 4), "cold")])
+def test_tied_and_crowded_thresholds(dims, ladder):
+    """Ladders whose thresholds share buckets of u (equal betas, pairs of equal
+    betas, very low temperatures where many thresholds are near 0): the exact
+    count of thresholds below u then comes from the binary search, on both the
+    four-word groups (Lx a multiple of 8) and the per-site loop."""
+    if ladder == "equal":
+        betas = np.full(32, 0.35)
+    elif ladder == "pairs":
+        betas = np.repeat(inputs.geometric_ladder(0.3, 3.0)[::2], 2)
+    else:
+        betas = inputs.geometric_ladder(0.05, 0.5)
+    ns, X, sweeps, seed = 2, 5, 30, inputs.unit_seed(310)
+    bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(311))
+    b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X)
+    b.sweep(sweeps)
+    w, pi, acc = _oracle_batch(dims, bonds, betas, seed, sweeps, X, range(ns))
+    assert np.array_equal(b.words(), w)
+    assert np.array_equal(b.slots(), pi)
+    assert np.array_equal(b.exchange_counts(), acc)
+    b.close()
+
+
 def test_explicit_state_and_permutation():
     dims, ns, seed = (8, 4, 6), 2, 99
     bonds = inputs.ea_bonds(dims, ns, 5)
