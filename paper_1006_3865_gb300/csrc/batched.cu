@@ -19,6 +19,7 @@
 
 #include "philox.cuh"
 #include "spn_internal.h"
+#include "fastdiv.cuh"
 #include "sweep_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -62,14 +63,18 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
   auto sync_all = [&]() {
     if constexpr (CLUSTER) cg::this_cluster().sync(); else __syncthreads();
   };
+  // divisions by the instance's W, Ly and rows per CTA (set per instance)
+  FastDiv fW{1, 0, 0}, fLy{1, 0, 0}, fRpc{1, 0, 0};
   // word pointer of global row r (possibly in another CTA of the cluster)
   auto row_ptr = [&](int r) -> uint32_t* {
-    const int owner = r / rpc, lr = r - owner * rpc;
-    uint32_t* base = bits + (size_t)lr * 2 * W;
-    if constexpr (CLUSTER) {
+    if constexpr (!CLUSTER) {
+      return bits + (size_t)r * 2 * W;  // one CTA owns every row
+    } else {
+      const int owner = (int)fdiv((uint32_t)r, fRpc), lr = r - owner * rpc;
+      uint32_t* base = bits + (size_t)lr * 2 * W;
       if (owner != rank) return cg::this_cluster().map_shared_rank(base, owner);
+      return base;
     }
-    return base;
   };
 
   while (true) {
@@ -94,6 +99,9 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
     vbl = (Lx - 64 * (W - 1)) >> 1;
     vec_io = (Lx & 63) == 0;
     rpc = (nrow + CS - 1) / CS;  // rows per CTA; the last CTA of a cluster may own fewer
+    fW = fastdiv((uint32_t)W);
+    fLy = fastdiv((uint32_t)Ly);
+    fRpc = fastdiv((uint32_t)rpc);
     const int r0 = rank * rpc;
     own = nrow - r0 < rpc ? (nrow - r0 > 0 ? nrow - r0 : 0) : rpc;
 
@@ -136,7 +144,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
         left = o;
         right = (o >> 1) | ((other[jp] & 1u) << (vbits(j) - 1));
       }
-      const int y = r % Ly, z = r / Ly;
+      const int z = (int)fdiv((uint32_t)r, fLy), y = r - z * Ly;
       const int rym = y == 0 ? r + Ly - 1 : r - 1, ryp = y + 1 == Ly ? r - Ly + 1 : r + 1;
       const uint32_t ym = row_ptr(rym)[par * W + j], yp = row_ptr(ryp)[par * W + j];
       if constexpr (ND == 3) {
@@ -191,9 +199,9 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
           const int it = tid + q * nth;
           const bool live = it < items;
           const int itc = live ? it : 0;
-          const int lr = itc / W, j = itc - lr * W;
+          const int lr = (int)fdiv((uint32_t)itc, fW), j = itc - lr * W;
           const int r = r0 + lr;
-          const int y = r % Ly, z = r / Ly;
+          const int z = (int)fdiv((uint32_t)r, fLy), y = r - z * Ly;
           const int par = (y + z + c) & 1;
           uint32_t* wp = bits + (size_t)lr * 2 * W + par * W + j;
           const uint32_t b = *wp;

@@ -1,6 +1,6 @@
 // Division by a run-time constant d < 2^31 as a multiply-high and a shift
-// (the round-up method of Granlund and Montgomery, PLDI 1994): host-side setup
-// of FastDiv and the device-side quotient.
+// (the round-up method of Granlund and Montgomery, PLDI 1994): the setup of
+// FastDiv (host, or once per work item on the device) and the device-side quotient.
 #pragma once
 #include <cstdint>
 
@@ -8,7 +8,7 @@
 
 namespace spn {
 
-inline FastDiv fastdiv(uint32_t d) {
+__host__ __device__ inline FastDiv fastdiv(uint32_t d) {
   FastDiv f{d, 0, 0};
   if (d <= 1) return f;
   uint32_t l = 0;
