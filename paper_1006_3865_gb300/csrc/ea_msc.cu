@@ -19,8 +19,10 @@
 // accepting temperatures form a suffix: the number of thresholds <= u gives its
 // start and a 33-entry table, kept in step with the slot permutation, turns it
 // into the slot mask.  That number comes from a 1024-bucket table over the top
-// 10 bits of u (the counts at both ends of the bucket) and one compare; only a
-// bucket holding two or more thresholds takes the 5-step binary search.  When
+// 10 bits of u, one 32-bit entry per bucket with a byte per level (the count at
+// the bucket's start and whether 0, 1 or more thresholds fall inside it), and
+// at most one compare per level; only a bucket holding two or more thresholds
+// of some level takes the 5-step binary search.  When
 // Lx is a multiple of 8 a thread updates four consecutive same-colour words of
 // a row at once: 16-byte shared-memory loads and stores, and the one Philox
 // call whose four words are the four sites' u.  After every X-th sweep the CTA
@@ -47,7 +49,7 @@ namespace spn {
 __device__ __forceinline__ int ea_slot(int x, int row, int h) { return (row * 2 + (x & 1)) * h + (x >> 1); }
 
 constexpr int kEaBucketShift = 22;                      // bucket of u = u >> 22
-constexpr int kEaBuckets = 1 << (32 - kEaBucketShift);  // per dE level
+constexpr int kEaBuckets = 1 << (32 - kEaBucketShift);  // one 32-bit entry each
 
 // One sample (CTA) of a batch launch, or one served job of a multi-job launch.
 template <int ND>
@@ -62,7 +64,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   uint8_t* tos = reinterpret_cast<uint8_t*>(ucount + 32);     // 32 temp_of_slot
   uint8_t* sot = tos + 32;                                    // 32 slot_of_temp
   int* xcount = reinterpret_cast<int*>(sot + 32);             // 32 accepted exchanges this launch
-  uint16_t* lut = reinterpret_cast<uint16_t*>(xcount + 32);   // 3 x kEaBuckets: lo | hi << 8
+  uint32_t* lut = reinterpret_cast<uint32_t*>(xcount + 32);   // kEaBuckets entries, a byte per dE level
 
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
   const int pair = sample >> 1, half = sample & 1;
@@ -84,18 +86,23 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   __syncthreads();
   if (tid < 32) sot[tos[tid]] = (uint8_t)tid;
   // bucket table: for u in [b 2^22, (b+1) 2^22 - 1], the number of thresholds
-  // <= u lies between lo = #(thr <= b 2^22) and hi = #(thr <= (b+1) 2^22 - 1)
-  for (int i = tid; i < ND * kEaBuckets; i += nth) {
-    const uint32_t* tl = thr + 32 * (i / kEaBuckets);
-    const uint32_t b = (uint32_t)(i % kEaBuckets);
-    const uint32_t u0 = b << kEaBucketShift, u1 = u0 + ((1u << kEaBucketShift) - 1u);
-    int lo = 0, hi = 0;
+  // of a level that are <= u lies between lo = #(thr <= b 2^22) and
+  // hi = #(thr <= (b+1) 2^22 - 1).  Byte lv of entry b: lo (bits 0-5) and
+  // min(hi - lo, 2) (bits 6-7: 0 settled, 1 one compare, 2 binary search).
+  for (int b = tid; b < kEaBuckets; b += nth) {
+    const uint32_t u0 = (uint32_t)b << kEaBucketShift, u1 = u0 + ((1u << kEaBucketShift) - 1u);
+    uint32_t e = 0;
+    for (int lv = 0; lv < ND; ++lv) {
+      const uint32_t* tl = thr + 32 * lv;
+      int lo = 0, hi = 0;
 #pragma unroll 8
-    for (int t = 0; t < 32; ++t) {
-      lo += tl[t] <= u0 ? 1 : 0;
-      hi += tl[t] <= u1 ? 1 : 0;
+      for (int t = 0; t < 32; ++t) {
+        lo += tl[t] <= u0 ? 1 : 0;
+        hi += tl[t] <= u1 ? 1 : 0;
+      }
+      e |= (uint32_t)(lo | ((hi - lo < 2 ? hi - lo : 2) << 6)) << (8 * lv);
     }
-    lut[i] = (uint16_t)(lo | (hi << 8));
+    lut[b] = e;
   }
   __syncthreads();
   if (tid < 32) {  // suffix[t0] = slots of temperatures t >= t0
@@ -112,12 +119,9 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
 
   const int halfN = N >> 1;
   // number of thresholds of level lv that are <= u (the accepting temperatures
-  // are the ones from there up)
-  auto count_le = [&](int lv, uint32_t u) -> int {
+  // are the ones from there up), by binary search over the 32 sorted ones
+  auto search_le = [&](int lv, uint32_t u) -> int {
     const uint32_t* tl = thr + 32 * lv;
-    const uint32_t e = lut[lv * kEaBuckets + (u >> kEaBucketShift)];
-    const int lo = (int)(e & 0xffu), hi = (int)(e >> 8);
-    if (hi - lo <= 1) return lo + ((hi > lo && tl[lo & 31] <= u) ? 1 : 0);
     int cnt = 0;
     cnt += (tl[cnt + 15] <= u) ? 16 : 0;
     cnt += (tl[cnt + 7] <= u) ? 8 : 0;
@@ -127,6 +131,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
     cnt += (cnt == 31 && tl[31] <= u) ? 1 : 0;  // all 32 thresholds <= u
     return cnt;
   };
+  constexpr uint32_t kSearch = ND == 3 ? 0x808080u : 0x8080u;  // some level needs the search
   // new word of a site: s its 32 replicas, bits its bond byte, n* the neighbour
   // words (x+, x-, y+, y-, z+, z-), u its uniform deviate
   auto update = [&](uint32_t s, uint32_t bits, uint32_t nxp, uint32_t nxm, uint32_t nyp, uint32_t nym, uint32_t nzp,
@@ -147,8 +152,18 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
     const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
     const uint32_t s1 = y1 ^ y2 ^ cc, s2 = (y1 & y2) | (cc & (y1 ^ y2));
     uint32_t A[ND];
+    const uint32_t e = lut[u >> kEaBucketShift];
+    if (e & kSearch) {  // a bucket with two or more thresholds of some level (rare)
 #pragma unroll
-    for (int lv = 0; lv < ND; ++lv) A[lv] = suffix[count_le(lv, u)];
+      for (int lv = 0; lv < ND; ++lv) A[lv] = suffix[search_le(lv, u)];
+    } else {
+#pragma unroll
+      for (int lv = 0; lv < ND; ++lv) {
+        const uint32_t by = e >> (8 * lv);
+        const int lo = (int)(by & 63u);
+        A[lv] = suffix[lo + (((by & 64u) && thr[32 * lv + lo] <= u) ? 1 : 0)];
+      }
+    }
     // dE = 4 (ND - k): k >= ND accepts always; k = ND - 1 - lv takes level lv (dE = 4 (lv + 1))
     const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
     uint32_t acc;
@@ -520,7 +535,7 @@ int ea_fail(int code, const char* msg) {
 }
 
 size_t ea_smem(int N) {
-  return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4 + 3 * spn::kEaBuckets * 2;
+  return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4 + spn::kEaBuckets * 4;
 }
 
 }  // namespace
