@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_idx;
   __shared__ long long s_em[2];
+  __shared__ uint32_t s_tm[3][32];  // 0 / ~0: bit 31 - p of the instance's threshold of class q
   const int tid = threadIdx.x, nth = blockDim.x;
   // Extents of the current instance (instances of one launch may differ).  A
   // row is W words per parity; every word holds 32 sites but the last, which
@@ -104,6 +105,13 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
     fRpc = fastdiv((uint32_t)rpc);
     const int r0 = rank * rpc;
     own = nrow - r0 < rpc ? (nrow - r0 > 0 ? nrow - r0 : 0) : rpc;
+
+    // threshold planes of this instance for the decision (read after the sync below)
+    for (int i = tid; i < ND * 32; i += nth) {
+      const int q = i >> 5;  // class q: dE = 4 (q + 1); selects keep the instance in registers
+      const uint32_t t = q == 0 ? in.T.t[1] : (q == 1 ? in.T.t[2] : in.T.t[3]);
+      s_tm[q][i & 31] = 0u - ((t >> (31 - (i & 31))) & 1u);
+    }
 
     // ---- load: hot start from Philox or the int8 lattice
     const int wordsOwn = own * 2 * W;
@@ -209,9 +217,37 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
           counts(r, j, par, b, s0, s1, s2);
           const uint32_t valid = live ? vmaskj(j) : 0u;
           uint32_t cls[ND];
-          const uint32_t acc0 = classes<ND>(s0, s1, s2, valid, cls);
-          const uint32_t flips = lazy_accept<ND>(acc0, cls, in.T, K, 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)r),
-                                                 sweep, (uint32_t)c | (kMetropolis << 1), in.stream);
+          uint32_t flips = classes<ND>(s0, s1, s2, valid, cls);
+          const uint32_t c0 = 8u * ((uint32_t)j + (uint32_t)W * (uint32_t)r), c2 = (uint32_t)c | (kMetropolis << 1);
+          uint32_t eq[ND];
+#pragma unroll
+          for (int k = 0; k < ND; ++k) {
+            const bool always = (in.T.always >> (k + 1)) & 1u;
+            flips |= always ? cls[k] : 0u;
+            eq[k] = always ? 0u : cls[k];
+          }
+          // Most significant plane first, one Philox call (four planes) at a
+          // time until no site of the warp ties: tied holds the sites whose u
+          // matches their class's threshold on every plane so far; a 0 bit of u
+          // where the threshold has a 1 accepts, the opposite rejects.  The
+          // classes are disjoint, so one selected threshold plane serves them all.
+          uint32_t tied = 0;
+#pragma unroll
+          for (int k = 0; k < ND; ++k) tied |= eq[k];
+#pragma unroll 1
+          for (uint32_t call = 0; call < 8u && __any_sync(0xffffffffu, tied != 0u); ++call) {
+            const U4 P = philox10(c0 + call, sweep, c2, in.stream, K);
+            const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
+            const uint32_t* tm0 = &s_tm[0][4 * call];
+#pragma unroll
+            for (int jp = 0; jp < 4; ++jp) {
+              uint32_t t = tm0[jp];
+#pragma unroll
+              for (int k = 1; k < ND; ++k) t = (eq[k] & tm0[32 * k + jp]) | (~eq[k] & t);
+              flips |= tied & ~pl[jp] & t;
+              tied &= ~(pl[jp] ^ t);
+            }
+          }
           if (live) {
             tally<ND>(flips, b, s0, s1, s2, de, dm);
             *wp = b ^ flips;  // only this thread reads or writes this colour-c word in this phase

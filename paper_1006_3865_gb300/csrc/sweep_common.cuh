@@ -74,73 +74,6 @@ __device__ __forceinline__ uint32_t lazy_accept(uint32_t acc, const uint32_t (&c
   return acc;
 }
 
-// First stage of the decision: planes 0..7 (two Philox calls, drawn together)
-// for every word.  On return acc holds the sites already accepted and eq[q]
-// the sites of class q+1 whose u still ties the threshold on all 8 planes.
-template <int NC>
-__device__ __forceinline__ void decide_first(uint32_t& acc, uint32_t (&eq)[NC], const uint32_t (&cls)[NC],
-                                             const DevThr& T, const PhiloxKeys& K, uint32_t c0, uint32_t sweep,
-                                             uint32_t c2, uint32_t stream_id) {
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    const bool always = (T.always >> (q + 1)) & 1u;
-    acc |= always ? cls[q] : 0u;
-    eq[q] = always ? 0u : cls[q];
-  }
-  const U4 P0 = philox10(c0, sweep, c2, stream_id, K);
-  const U4 P1 = philox10(c0 + 1u, sweep, c2, stream_id, K);
-  const uint32_t planes[8] = {P0.x, P0.y, P0.z, P0.w, P1.x, P1.y, P1.z, P1.w};
-  // Compare the top 8 bits of u with those of the threshold, least significant
-  // plane first: "below" after plane p is maj(~u_p, t_p, below so far); "equal"
-  // keeps the sites whose bits all match.
-#pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    uint32_t below = 0, equal = 0xffffffffu;
-#pragma unroll
-    for (int p = 7; p >= 0; --p) {
-      const uint32_t tm = 0u - ((T.t[q + 1] >> (31 - p)) & 1u);
-      const uint32_t nu = ~planes[p];
-      below = (nu & tm) | (nu & below) | (tm & below);
-      equal &= ~(planes[p] ^ tm);
-    }
-    acc |= eq[q] & below;
-    eq[q] &= equal;
-  }
-}
-
-// Remaining planes 8..31 for sites still tied after the first stage; returns
-// the sites among eq that are accepted.  Called by whole warps (votes).
-template <int NC>
-__device__ __forceinline__ uint32_t decide_tail(uint32_t (&eq)[NC], const DevThr& T, const PhiloxKeys& K,
-                                               uint32_t c0, uint32_t sweep, uint32_t c2, uint32_t stream_id) {
-  uint32_t acc = 0, pend = 0;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) pend |= eq[q];
-#pragma unroll 1
-  for (uint32_t call = 2; call < 8u && __any_sync(0xffffffffu, pend != 0u); ++call) {
-    const U4 P = philox10(c0 + call, sweep, c2, stream_id, K);
-    const uint32_t planes[4] = {P.x, P.y, P.z, P.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t u = planes[j];
-      const uint32_t bit = 31u - (4u * call + (uint32_t)j);
-#pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        if ((T.t[q + 1] >> bit) & 1u) {
-          acc |= eq[q] & ~u;
-          eq[q] &= u;
-        } else {
-          eq[q] &= ~u;
-        }
-      }
-    }
-    pend = 0;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) pend |= eq[q];
-  }
-  return acc;
-}
-
 // u < t on the top NP bit planes for all 32 sites of a word at once, with t
 // the threshold of each site's own class (the class masks eq[k] are disjoint,
 // so one selected threshold plane serves every class).  Least significant
