@@ -1,8 +1,10 @@
 // Checkerboard Metropolis kernels for int8 Ising-type lattices (Weigel, Sec. 3,
 // Eq. 1-2; Sec. 4 for 3D and +-J couplings).
 //
-//   k_init_hot        hot start from Philox (purpose 1, most significant plane).
-//   k_observables     full reduction of E (Eq. 1) and M.
+//   k_init_hot        hot start from Philox (purpose 1, most significant plane);
+//                     k_init_hot_words for rows of whole 64-site words.
+//   k_observables     full reduction of E (Eq. 1) and M; k_observables_chunks
+//                     for Ising rows of whole 16-byte chunks.
 //   k_sweep_generic   one colour of a sweep in place in global memory; a thread
 //                     owns one group of 32 same-colour sites.  Any even extents,
 //                     optional +-J bonds.  Two launches per sweep realise the
@@ -118,7 +120,104 @@ __global__ void k_observables(const int8_t* __restrict__ s, const uint8_t* __res
   block_accumulate(e, m, out2);
 }
 
+// int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
+// (bit set: spin -1)
+__device__ __forceinline__ void fill_pattern_table(uint2* lut) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    uint32_t lo = 0, hi = 0;
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t pair = (((i >> k) & 1) ? 0xffu : 0x01u) | ((((i >> (4 + k)) & 1) ? 0xffu : 0x01u) << 8);
+      if (k < 2) lo |= pair << (16 * k); else hi |= pair << (16 * (k - 2));
+    }
+    lut[i] = make_uint2(lo, hi);
+  }
+}
+
+// Hot start of rows of whole 64-site words (the spins of k_init_hot): a thread
+// per (row r, word j) draws plane 0 of both colour groups of the word and writes
+// its 64 sites with four 16-byte stores.
+__global__ void k_init_hot_words(int8_t* __restrict__ s, int Lx, int Ly, uint32_t nword, PhiloxKeys K,
+                                 uint32_t stream_id) {
+  __shared__ uint2 lut[256];
+  fill_pattern_table(lut);
+  __syncthreads();
+  const uint32_t W = (uint32_t)Lx >> 6;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nword; g += gridDim.x * blockDim.x) {
+    const uint32_t r = g / W, j = g - r * W;
+    const uint32_t z = r / (uint32_t)Ly, y = r - z * (uint32_t)Ly;
+    const uint32_t p0 = philox10(8u * g, 0u, 0u | (kInit << 1), stream_id, K).x;
+    const uint32_t p1 = philox10(8u * g, 0u, 1u | (kInit << 1), stream_id, K).x;
+    // colour c holds the sites of parity (c + y + z) & 1
+    const bool c0_even = ((y + z) & 1u) == 0u;
+    const uint32_t E = c0_even ? p0 : p1, O = c0_even ? p1 : p0;
+    const uint32_t X = (E & 0x0f0f0f0fu) | ((O << 4) & 0xf0f0f0f0u);  // byte v: sites 16v .. 16v + 7
+    const uint32_t Y = ((E >> 4) & 0x0f0f0f0fu) | (O & 0xf0f0f0f0u);  // byte v: sites 16v + 8 .. 16v + 15
+    uint4* dst = reinterpret_cast<uint4*>(s + (size_t)r * (size_t)Lx + 64u * j);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const uint2 lo = lut[(X >> (8 * v)) & 0xffu];
+      const uint2 hi = lut[(Y >> (8 * v)) & 0xffu];
+      dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+    }
+  }
+}
+
+// E and M of an Ising lattice (J = 1) with rows of whole 16-byte chunks: a
+// thread per 16 sites compares them with their x + 1, y + 1 (and z + 1)
+// neighbours through the sign bits of the int8 spins (+1 = 0x01, -1 = 0xff):
+// E = sum over bonds of (2 [unequal] - 1), M = sum of (1 - 2 [negative]).
+__global__ void k_observables_chunks(const int8_t* __restrict__ s, int nd, int Lx, int Ly, int Lz, uint32_t nchunk,
+                                     unsigned long long* out2, int* bad) {
+  const uint32_t C = (uint32_t)Lx >> 4;
+  long long e = 0, m = 0;
+  bool invalid = false;
+  const uint32_t sign = 0x80808080u;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nchunk; q += gridDim.x * blockDim.x) {
+    const uint32_t r = q / C, k = q - r * C;
+    const uint32_t z = r / (uint32_t)Ly, y = r - z * (uint32_t)Ly;
+    const int8_t* row = s + (size_t)r * (size_t)Lx;
+    const uint4 A = *reinterpret_cast<const uint4*>(row + 16u * k);
+    const uint32_t next = (uint8_t)row[k + 1u == C ? 0u : 16u * (k + 1u)];  // site after the chunk, periodic in x
+    const uint32_t ry = y + 1u == (uint32_t)Ly ? r - y : r + 1u;
+    const uint4 B = *reinterpret_cast<const uint4*>(s + (size_t)ry * (size_t)Lx + 16u * k);
+    const uint32_t a[5] = {A.x, A.y, A.z, A.w, next};
+    const uint32_t b[4] = {B.x, B.y, B.z, B.w};
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
+    if (nd == 3) {
+      const uint32_t plane = (uint32_t)Ly;
+      const uint32_t rz = z + 1u == (uint32_t)Lz ? r - z * plane : r + plane;
+      const uint4 Cz = *reinterpret_cast<const uint4*>(s + (size_t)rz * (size_t)Lx + 16u * k);
+      c[0] = Cz.x;
+      c[1] = Cz.y;
+      c[2] = Cz.z;
+      c[3] = Cz.w;
+    }
+    int unequal = 0, neg = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t xn = __byte_perm(a[i], a[i + 1], 0x4321);  // sites n + 1 .. n + 4
+      unequal += __popc((a[i] ^ xn) & sign) + __popc((a[i] ^ b[i]) & sign);
+      if (nd == 3) unequal += __popc((a[i] ^ c[i]) & sign);
+      neg += __popc(a[i] & sign);
+      invalid |= (__vcmpeq4(a[i], 0x01010101u) | __vcmpeq4(a[i], 0xffffffffu)) != 0xffffffffu;
+    }
+    e += 2 * unequal - 16 * nd;
+    m += 16 - 2 * neg;
+  }
+  if (invalid && bad) atomicExch(bad, 1);
+  block_accumulate(e, m, out2);
+}
+
 cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t stream_id, cudaStream_t st) {
+  if (g.Lx % 64 == 0 && ((uintptr_t)s & 15) == 0 && g.N / 64 < ((int64_t)1 << 31)) {
+    const int64_t nword = g.N / 64;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((nword + threads - 1) / threads, (int64_t)device_sm_count() * 16);
+    k_init_hot_words<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(s, g.Lx, g.Ly, (uint32_t)nword,
+                                                                                philox_keys(seed), stream_id);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int64_t nrow = g.N / g.Lx;
   const int64_t work = 2 * nrow * ((g.Lx + 63) / 64);
   const int threads = 256;
@@ -133,6 +232,15 @@ cudaError_t launch_observables(const Lattice& g, const int8_t* s, unsigned long 
                                cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  if (!g.bonds && g.Lx % 16 == 0 && ((uintptr_t)s & 15) == 0 && g.N / 16 < ((int64_t)1 << 31)) {
+    const int64_t nchunk = g.N / 16;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((nchunk + threads - 1) / threads, (int64_t)device_sm_count() * 16);
+    k_observables_chunks<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(
+        s, g.nd, g.Lx, g.Ly, g.Lz, (uint32_t)nchunk, out2, bad);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((g.N + threads - 1) / threads, (int64_t)device_sm_count() * 16);
   k_observables<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(s, g.bonds, g.nd, g.Lx, g.Ly, g.Lz,
