@@ -74,23 +74,25 @@ __device__ __forceinline__ float heis_exp_dev(float x) {
   return __fmul_rn(p, __int_as_float((127 + (int)kf) << 23));
 }
 
-// One Marsaglia try from two words; true and the point if v1^2 + v2^2 < 1.
-__device__ __forceinline__ bool marsaglia_try(uint32_t w1, uint32_t w2, float3& out) {
-  const float v1 = __fsub_rn(__fmul_rn(__uint2float_rn(w1 >> 8), 1.0f / 8388608.0f), 1.0f);
-  const float v2 = __fsub_rn(__fmul_rn(__uint2float_rn(w2 >> 8), 1.0f / 8388608.0f), 1.0f);
-  const float ss = __fadd_rn(__fmul_rn(v1, v1), __fmul_rn(v2, v2));
-  if (!(ss < 1.0f)) return false;
-  const float f = __fmul_rn(2.0f, __fsqrt_rn(__fsub_rn(1.0f, ss)));
-  out = make_float3(__fmul_rn(v1, f), __fmul_rn(v2, f), __fsub_rn(1.0f, __fmul_rn(2.0f, ss)));
-  return true;
-}
-
-// Proposal call k of site m: tries 2k and 2k+1.
+// Proposal call k of site m: tries 2k and 2k+1, the first inside the unit disc
+// taken.  Both pairs are formed and the accepted one selected without a
+// branch, so the square root and the point are computed once (the same
+// operations on the same values as taking the tries one after the other).
 __device__ __forceinline__ bool proposal_call(const PhiloxKeys& K, uint32_t m, uint32_t t, uint32_t c, uint32_t purpose,
                                               uint32_t k, uint32_t stream, float3& out) {
   const U4 P = philox10(m, t, c | (purpose << 1) | (k << 4), stream, K);
-  if (marsaglia_try(P.x, P.y, out)) return true;
-  return marsaglia_try(P.z, P.w, out);
+  const float a1 = __fsub_rn(__fmul_rn(__uint2float_rn(P.x >> 8), 1.0f / 8388608.0f), 1.0f);
+  const float a2 = __fsub_rn(__fmul_rn(__uint2float_rn(P.y >> 8), 1.0f / 8388608.0f), 1.0f);
+  const float b1 = __fsub_rn(__fmul_rn(__uint2float_rn(P.z >> 8), 1.0f / 8388608.0f), 1.0f);
+  const float b2 = __fsub_rn(__fmul_rn(__uint2float_rn(P.w >> 8), 1.0f / 8388608.0f), 1.0f);
+  const float sa = __fadd_rn(__fmul_rn(a1, a1), __fmul_rn(a2, a2));
+  const float sb = __fadd_rn(__fmul_rn(b1, b1), __fmul_rn(b2, b2));
+  const bool first = sa < 1.0f;
+  if (!first && !(sb < 1.0f)) return false;
+  const float v1 = first ? a1 : b1, v2 = first ? a2 : b2, ss = first ? sa : sb;
+  const float f = __fmul_rn(2.0f, __fsqrt_rn(__fsub_rn(1.0f, ss)));
+  out = make_float3(__fmul_rn(v1, f), __fmul_rn(v2, f), __fsub_rn(1.0f, __fmul_rn(2.0f, ss)));
+  return true;
 }
 
 // Site of within-colour index m of colour c.
