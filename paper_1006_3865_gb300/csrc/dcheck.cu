@@ -1,5 +1,5 @@
 // The paper's double-checkerboard sweep with the generalised multi-hit
-// (Sec. 3, steps 1-7): the lattice is cut into coarse tiles coloured like a
+// (Sec. 3): the lattice is cut into coarse tiles coloured like a
 // checkerboard; one launch takes every tile of one parity, a CTA per tile.  The
 // CTA stages its tile plus a one-site boundary layer into shared memory as
 // colour-separated bit words, updates the tile's colour-0 sites, then its
