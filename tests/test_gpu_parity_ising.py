@@ -166,3 +166,27 @@ def test_autotune_keeps_state_and_results(model, dims, path):
     gE, gM = lat.trace()
     assert np.array_equal(lat.get_spins(), s) and np.array_equal(gE, tE) and np.array_equal(gM, tM)
     lat.close()
+
+
+@pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (64, 32)), (spn.SPN_ISING2D, (66, 40)),
+                                        (spn.SPN_ISING2D, (16, 2)), (spn.SPN_ISING3D, (32, 8, 6)),
+                                        (spn.SPN_ISING3D, (10, 6, 4)), (spn.SPN_ISING3D, (16, 2, 2))])
+def test_set_spins_observables_and_invalid_values(model, dims):
+    """E and M of arbitrary states (the full recompute after set_spins, on rows of
+    whole 16-byte chunks and on ragged rows) equal the oracle's; a lattice with a
+    value other than +-1 anywhere in a chunk is refused."""
+    N = int(np.prod(dims))
+    rng = np.random.Generator(np.random.PCG64(inputs.unit_seed(70)))
+    lat = spn.Lattice(model, dims, 5)
+    for frac in (0.5, 0.0, 1.0, 0.1):
+        s = np.where(rng.random(N) < frac, -1, 1).astype(np.int8)
+        lat.set_spins(s)
+        assert lat.observables() == tuple(oracle.observables(dims, s.copy()))
+        assert np.array_equal(lat.get_spins(), s)
+    for pos in (0, 1, 15, 16, N // 2, N - 1):
+        for bad in (0, 2, -3):
+            t = s.copy()
+            t[pos] = bad
+            with pytest.raises(spn.SpnError):
+                lat.set_spins(t)
+    lat.close()
