@@ -258,8 +258,10 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
       __syncthreads();
       uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       for (int n = tid; n < N; n += nth) {
-        const int x = n % a.Lx, r = n / a.Lx;
-        const int y = r % a.Ly, z = r / a.Ly;
+        const int r = (int)fdiv((uint32_t)n >> 1, a.div_h);  // n / Lx (Lx = 2 h)
+        const int x = n - r * a.Lx;
+        const int z = ND == 3 ? (int)fdiv((uint32_t)r, a.div_ly) : 0;
+        const int y = r - z * a.Ly;
         const int q = ea_slot(x, r, h);
         const uint32_t s = sp[q];
         const uint32_t bits = bb[q];
@@ -283,18 +285,34 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
           }
         }
       }
-      // per-replica totals (at most 255 per thread: ND bonds x at most 46 sites per thread)
-      for (int j = 0; j < 32; ++j) {
-        uint32_t v = 0;
+      // per-replica totals (at most 255 per thread: ND bonds x at most 46 sites
+      // per thread).  Bit j of cnt[b] is bit b of replica j's count: byte g of
+      // the eight words is an 8 x 8 bit block (row b, column k = replica 8 g + k),
+      // whose transpose holds the counts of replicas 8 g .. 8 g + 7 as bytes.
+      // Two counts share a word for the warp sum (at most 32 x 255 < 2^16 each).
+      uint32_t pk[16];  // pk[i]: replica 2 i in bits 0-15, replica 2 i + 1 in bits 16-31
 #pragma unroll
-        for (int b = 0; b < 8; ++b) v |= ((cnt[b] >> j) & 1u) << b;
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        if (lane == 0 && v) atomicAdd(&ucount[j], v);
+      for (int g = 0; g < 4; ++g) {
+        unsigned long long mt = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) mt |= (unsigned long long)((cnt[b] >> (8 * g)) & 0xffu) << (8 * b);
+        unsigned long long t = (mt ^ (mt >> 7)) & 0x00AA00AA00AA00AAull;  // swaps within 2 x 2, 4 x 4, 8 x 8 blocks
+        mt = mt ^ t ^ (t << 7);
+        t = (mt ^ (mt >> 14)) & 0x0000CCCC0000CCCCull;
+        mt = mt ^ t ^ (t << 14);
+        t = (mt ^ (mt >> 28)) & 0x00000000F0F0F0F0ull;
+        mt = mt ^ t ^ (t << 28);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          pk[4 * g + i] = ((uint32_t)(mt >> (16 * i)) & 0xffu) | (((uint32_t)(mt >> (16 * i + 8)) & 0xffu) << 16);
       }
+      uint32_t mine = 0;  // lane j: replica j's warp total
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const uint32_t v = __reduce_add_sync(0xffffffffu, pk[i]);
+        if ((lane >> 1) == i) mine = (lane & 1) ? (v >> 16) : (v & 0xffffu);
+      }
+      if (mine) atomicAdd(&ucount[lane], mine);
       __syncthreads();
       if (tid < 32) {
         // pairs (kk, kk+1) with kk = e mod 2, e mod 2 + 2, ...; lane tid takes kk = tid
