@@ -389,13 +389,61 @@ def form_served(n_requests, budget_bytes=120 * 10**9):
     srv.close()
     lat = np.array(lat) * 1e3
     span = last - first
+    subset = _served_vs_loop(reqs[:200], budget_bytes)
     return {"value": att / (span * 1e9), "unit": UNIT, "requests": len(reqs), "attempts": att,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()), "span_s": span, "wall_s": wall, "rounds": st["rounds"],
-            "offered": att / (reqs[-1].arrival_s * 1e9),
+            "offered": att / (reqs[-1].arrival_s * 1e9), "subset": subset,
             "workload": f"first {len(reqs)} of 2000 Poisson requests, mean gap 0.5 ms: 2D Ising L 64..4096, 3D Ising L 16..256, 3D EA "
                         "L 8..32 (32-T ladders on [T, 10T]), T on [0.5, 4.0], sweeps 1e2..1e4 log-uniform; "
                         "120 GB budget; latency = submit -> result on the host"}
+
+
+def _served_vs_loop(reqs, budget_bytes):
+    """The same jobs two ways, each timed from the first call to the last
+    result: one after another through the single-lattice and batch API (a
+    handle per job, its sweeps, its observables; the per-instance baseline), and
+    all submitted at once to the server.  The Ising jobs' final E and M must
+    agree."""
+    import numpy as np
+
+    from paper_1006_3865_gb300 import spn
+
+    att = sum((32 if r.model == 3 else 1) * int(np.prod(r.dims)) * r.nsweeps for r in reqs)
+    loop_em = {}
+    t0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        if r.model == 3:
+            b = spn.EABatch(r.dims, r.bonds, r.betas, r.seed, exchange_every=EA_EVERY)
+            b.sweep(r.nsweeps)
+            b.energies()
+            b.close()
+        else:
+            lat = spn.Lattice(r.model, r.dims, r.seed, stream_id=k)
+            lat.sweep(r.beta, r.nsweeps)
+            loop_em[k] = lat.observables()
+            lat.close()
+    t_loop = time.perf_counter() - t0
+    srv = spn.Server(budget_bytes)
+    t0 = time.perf_counter()
+    tickets = []
+    for k, r in enumerate(reqs):
+        if r.model == 3:
+            tickets.append(srv.submit(spn.SPN_EA3D_PMJ, r.dims, r.nsweeps, r.seed, betas=r.betas,
+                                      couplings=r.bonds[0], exchange_every=EA_EVERY))
+        else:
+            tickets.append(srv.submit(r.model, r.dims, r.nsweeps, r.seed, beta=r.beta, stream=k))
+    pending = set(tickets)
+    while pending:
+        for t in list(pending):
+            if srv.poll(t)[0]:
+                pending.discard(t)
+        time.sleep(0.0005)
+    t_srv = time.perf_counter() - t0
+    same = all((srv.poll(tickets[k])[1].E, srv.poll(tickets[k])[1].M) == loop_em[k] for k in loop_em)
+    srv.close()
+    return {"jobs": len(reqs), "attempts": att, "served": att / (t_srv * 1e9), "loop": att / (t_loop * 1e9),
+            "identical_results": bool(same), "timing": "wall clock from the first call to the last result"}
 
 
 def form_dc(stream, tiles=((256, 64), (512, 128), (64, 64)), hits=(1, 2, 4), sweeps=20):
