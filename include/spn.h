@@ -339,6 +339,20 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
  * replicas of a site share its Philox word) with the exchanges due. */
 int spn_batch_sweep(spn_handle h, int64_t nsweeps);
 
+/* Random numbers of the temperature slots (Sec. 4's multi-spin coding puts
+ * many replicas in one word; which of them share random numbers is a choice).
+ * on = 0 (default): the 32 slots of a site share one u, as above.  With replica
+ * exchange that correlates the replicas and the temperature marginals drift
+ * slightly (about 1% of E on a 4 x 4 ladder).  on = 1: every slot draws its own
+ * u, bit 31 - p of slot j's u being bit j of plane p, plane p = word p & 3 of
+ * Philox(m, sweep, colour | 3 << 1 | (p / 4 + 1) << 4, sample) for site m of its
+ * colour, compared most significant plane first until every slot is decided;
+ * exchange then keeps every temperature Boltzmann-distributed, at the cost of
+ * about two Philox calls per site instead of a quarter.  Takes effect from the
+ * next spn_batch_sweep.  SPN_E_STATE if h is not a batch handle, SPN_E_ARG if
+ * on is not 0 or 1. */
+int spn_batch_set_u_per_slot(spn_handle h, int32_t on);
+
 /* Site words [sample][N] (bit j = replica in slot j, 1 = spin -1). */
 int spn_batch_get_words(spn_handle h, uint32_t* out, size_t count);
 int spn_batch_set_words(spn_handle h, const uint32_t* in, size_t count);

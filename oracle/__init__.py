@@ -82,6 +82,8 @@ def lib():
             L.orc_ea_observables.restype = cint
             L.orc_ea_sweeps.argtypes = [cint, vp, cint, vp, vp, vp, vp, vp, u64, u32, u32, i64, cint, vp]
             L.orc_ea_sweeps.restype = cint
+            L.orc_ea_sweeps_ex.argtypes = [cint, vp, cint, vp, vp, vp, vp, vp, u64, u32, u32, i64, cint, vp, cint]
+            L.orc_ea_sweeps_ex.restype = cint
             L.orc_ea_overlap.argtypes = [cint, vp, cint, vp, vp, vp]
             L.orc_ea_overlap.restype = cint
             flt = ctypes.c_float
@@ -245,8 +247,10 @@ def ea_observables(dims, words: np.ndarray, bonds: np.ndarray):
 
 def ea_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, temp_of_slot: np.ndarray,
               slot_of_temp: np.ndarray, nsweeps: int, seed: int, stream0: int = 0, sweep0: int = 0,
-              exchange_every: int = 0, acc: np.ndarray | None = None):
-    """Multi-spin coded sweeps, in place on ``words`` [nsamples, N] and the slot maps."""
+              exchange_every: int = 0, acc: np.ndarray | None = None, u_per_slot: bool = False):
+    """Multi-spin coded sweeps, in place on ``words`` [nsamples, N] and the slot maps.
+    u_per_slot: every temperature slot draws its own u (32 bit planes, eight
+    Philox calls per site) instead of sharing the site's one u."""
     d = _dims(dims)
     for a, dt in ((words, np.uint32), (temp_of_slot, np.uint8), (slot_of_temp, np.uint8)):
         if a.dtype != dt or not a.flags.c_contiguous:
@@ -256,9 +260,9 @@ def ea_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, temp_of_slot: n
         raise ValueError("ea_sweeps: 32 betas required")
     if acc is not None and (acc.dtype != np.int64 or not acc.flags.c_contiguous):
         raise TypeError("acc must be contiguous int64")
-    _check(lib().orc_ea_sweeps(len(d), _p(d), words.shape[0], _p(words), _p(_bonds(bonds)), _p(be), _p(temp_of_slot),
-                               _p(slot_of_temp), seed, stream0, sweep0, int(nsweeps), int(exchange_every),
-                               _p(acc)), "ea_sweeps")
+    _check(lib().orc_ea_sweeps_ex(len(d), _p(d), words.shape[0], _p(words), _p(_bonds(bonds)), _p(be),
+                                  _p(temp_of_slot), _p(slot_of_temp), seed, stream0, sweep0, int(nsweeps),
+                                  int(exchange_every), _p(acc), 1 if u_per_slot else 0), "ea_sweeps")
 
 
 def ea_overlap(dims, words: np.ndarray, slot_of_temp: np.ndarray) -> np.ndarray:

@@ -136,6 +136,25 @@ uint32_t orc_msc_u(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, u
   return w[m & 3];
 }
 
+/* Per-slot u of the multi-spin coded sweep when every slot draws its own
+ * number (the remedy of the shared u: with replica exchange the 32 slots must
+ * be independent for the ladder to keep its Boltzmann marginals): bit 31 - p
+ * of slot j's u is bit j of plane p, plane p = word p & 3 of the Philox call
+ * (m, sweep, colour | 3 << 1 | (p / 4 + 1) << 4, stream).  planes[32] out. */
+void orc_msc_slot_planes(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, uint64_t m, uint32_t planes[32]) {
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (uint32_t call = 0; call < 8; ++call) {
+    uint32_t ctr[4] = {(uint32_t)m, sweep, (uint32_t)colour | (3u << 1) | ((call + 1u) << 4), stream};
+    orc_philox4x32_10(ctr, key, planes + 4 * call);
+  }
+}
+
+static uint32_t slot_u(const uint32_t planes[32], int j) {
+  uint32_t u = 0;
+  for (int p = 0; p < 32; ++p) u |= ((planes[p] >> j) & 1u) << (31 - p);
+  return u;
+}
+
 /* ------------------------------------------------------- Metropolis rule */
 
 /* Eq. 2: p_acc = min[1, exp(-beta dE)], as the integer threshold
@@ -445,9 +464,9 @@ static void exchange_step(const double* betas, const int64_t* Eslot, uint8_t* sl
  * stream0 + i), from global sweep index sweep0, with replica exchange after every
  * exchange_every-th sweep (0 = never).  temp_of_slot / slot_of_temp: [sample][32],
  * in/out.  acc: [sample][32] exchange acceptance counters (may be NULL). */
-int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
-                  uint8_t* temp_of_slot, uint8_t* slot_of_temp, uint64_t seed, uint32_t stream0,
-                  uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
+int orc_ea_sweeps_ex(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
+                     uint8_t* temp_of_slot, uint8_t* slot_of_temp, uint64_t seed, uint32_t stream0,
+                     uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc, int u_per_slot) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
   uint64_t thr[32][4];
@@ -468,8 +487,11 @@ int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const ui
         for (int64_t n = 0; n < g.N; ++n) {
           if (lat_colour(&g, n) != c) continue;
           uint32_t u = orc_msc_u(seed, stream, sweep, c, (uint64_t)(n >> 1));
+          uint32_t planes[32];
+          if (u_per_slot) orc_msc_slot_planes(seed, stream, sweep, c, (uint64_t)(n >> 1), planes);
           uint32_t flip = 0;
           for (int j = 0; j < 32; ++j) {
+            if (u_per_slot) u = slot_u(planes, j);
             int sn = rep_spin(w[n], j);
             int h = 0;
             for (int d = 0; d < nd; ++d) {
@@ -494,6 +516,13 @@ int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const ui
   free(Eslot);
   free(Mslot);
   return 0;
+}
+
+int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
+                  uint8_t* temp_of_slot, uint8_t* slot_of_temp, uint64_t seed, uint32_t stream0,
+                  uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
+  return orc_ea_sweeps_ex(nd, L, nsamples, sp, bonds, betas, temp_of_slot, slot_of_temp, seed, stream0, sweep0,
+                          nsweeps, exchange_every, acc, 0);
 }
 
 /* Spin-glass overlap of replica pairs (Sec. 4: many disorder realisations at

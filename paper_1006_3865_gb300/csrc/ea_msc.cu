@@ -52,7 +52,7 @@ constexpr int kEaBucketShift = 22;                      // bucket of u = u >> 22
 constexpr int kEaBuckets = 1 << (32 - kEaBucketShift);  // one 32-bit entry each
 
 // One sample (CTA) of a batch launch, or one served job of a multi-job launch.
-template <int ND>
+template <int ND, bool PS = false>  // PS: every temperature slot draws its own u
 __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int N = a.N, h = a.Lx >> 1, nrow = a.Ly * a.Lz;
@@ -65,6 +65,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   uint8_t* sot = tos + 32;                                    // 32 slot_of_temp
   int* xcount = reinterpret_cast<int*>(sot + 32);             // 32 accepted exchanges this launch
   uint32_t* lut = reinterpret_cast<uint32_t*>(xcount + 32);   // kEaBuckets entries, a byte per dE level
+  uint32_t* tmask = lut + kEaBuckets;                          // per-slot u: [level][plane] slot masks
 
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31;
   const int pair = sample >> 1, half = sample & 1;
@@ -85,6 +86,16 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   }
   __syncthreads();
   if (tid < 32) sot[tos[tid]] = (uint8_t)tid;
+  // per-slot u: bit j of tmask[32 lv + p] is bit 31 - p of the level-lv
+  // threshold of slot j's temperature (rebuilt whenever the slot map changes)
+  auto build_tmask = [&]() {
+    for (int i = tid; i < ND * 32; i += nth) {
+      const int lv = i >> 5, p = i & 31;
+      uint32_t wv = 0;
+      for (int j = 0; j < 32; ++j) wv |= ((thr[32 * lv + tos[j]] >> (31 - p)) & 1u) << j;
+      tmask[i] = wv;
+    }
+  };
   // bucket table: for u in [b 2^22, (b+1) 2^22 - 1], the number of thresholds
   // of a level that are <= u lies between lo = #(thr <= b 2^22) and
   // hi = #(thr <= (b+1) 2^22 - 1).  Byte lv of entry b: lo (bits 0-5) and
@@ -116,6 +127,10 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
     if (tid == 0) suffix[32] = 0;
   }
   __syncthreads();
+  if constexpr (PS) {
+    build_tmask();
+    __syncthreads();
+  }
 
   const int halfN = N >> 1;
   // number of thresholds of level lv that are <= u (the accepting temperatures
@@ -135,7 +150,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   // new word of a site: s its 32 replicas, bits its bond byte, n* the neighbour
   // words (x+, x-, y+, y-, z+, z-), u its uniform deviate
   auto update = [&](uint32_t s, uint32_t bits, uint32_t nxp, uint32_t nxm, uint32_t nyp, uint32_t nym, uint32_t nzp,
-                    uint32_t nzm, uint32_t u) -> uint32_t {
+                    uint32_t nzm, uint32_t u, uint32_t m, uint32_t sw, uint32_t c2) -> uint32_t {
     // bond masks: bits 0..2 forward, 3..5 backward
     const uint32_t ux = s ^ nxp ^ (0u - (bits & 1u));
     const uint32_t uy = s ^ nyp ^ (0u - ((bits >> 1) & 1u));
@@ -151,6 +166,29 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
     const uint32_t x2 = vx ^ vy ^ vz, y2 = (vx & vy) | (vz & (vx ^ vy));
     const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
     const uint32_t s1 = y1 ^ y2 ^ cc, s2 = (y1 & y2) | (cc & (y1 ^ y2));
+    if constexpr (PS) {
+      // slot j's u has bit 31 - p = bit j of plane p (word p & 3 of the site's
+      // Philox call p / 4); planes most significant first against the slots'
+      // threshold bits, until no slot ties (strict u < t)
+      const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
+      const uint32_t l0 = ND == 3 ? k2 : k1, l1 = ND == 3 ? k1 : k0, l2 = ND == 3 ? k0 : 0u;
+      uint32_t acc = ND == 3 ? (s2 | (s0 & s1)) : (s1 | s2);
+      uint32_t tied = l0 | l1 | l2;
+#pragma unroll 1
+      for (uint32_t call = 0; call < 8u && tied != 0u; ++call) {
+        const U4 P = philox10(m, sw, c2 | ((call + 1u) << 4), (uint32_t)sample, a.K);
+        const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
+        const uint32_t* t0 = tmask + 4 * call;
+#pragma unroll
+        for (int jp = 0; jp < 4; ++jp) {
+          uint32_t t = (l0 & t0[jp]) | (l1 & t0[32 + jp]);
+          if constexpr (ND == 3) t |= l2 & t0[64 + jp];
+          acc |= tied & ~pl[jp] & t;
+          tied &= ~(pl[jp] ^ t);
+        }
+      }
+      return s ^ acc;
+    }
     uint32_t A[ND];
     const uint32_t e = lut[u >> kEaBucketShift];
     if (e & kSearch) {  // a bucket with two or more thresholds of some level (rare)
@@ -208,7 +246,7 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
             ZP = *reinterpret_cast<const uint4*>(sp + (rzp * 2 + par) * h + k0);
             ZM = *reinterpret_cast<const uint4*>(sp + (rzm * 2 + par) * h + k0);
           }
-          const U4 P = philox10((uint32_t)g, sweep, c2, (uint32_t)sample, a.K);
+          const U4 P = PS ? U4{0u, 0u, 0u, 0u} : philox10((uint32_t)g, sweep, c2, (uint32_t)sample, a.K);
           const uint32_t o[4] = {O4.x, O4.y, O4.z, O4.w};
           // even x: x+1 is other-parity word k, x-1 word k-1; odd x: x-1 word k, x+1 word k+1
           const uint32_t xp0 = par ? o[1] : o[0], xm0 = par ? o[0] : oe;
@@ -216,10 +254,10 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
           const uint32_t xp2 = par ? o[3] : o[2], xm2 = par ? o[2] : o[1];
           const uint32_t xp3 = par ? oe : o[3], xm3 = par ? o[3] : o[2];
           uint4 R;
-          R.x = update(S.x, B & 0xffu, xp0, xm0, YP.x, YM.x, ZP.x, ZM.x, P.x);
-          R.y = update(S.y, (B >> 8) & 0xffu, xp1, xm1, YP.y, YM.y, ZP.y, ZM.y, P.y);
-          R.z = update(S.z, (B >> 16) & 0xffu, xp2, xm2, YP.z, YM.z, ZP.z, ZM.z, P.z);
-          R.w = update(S.w, B >> 24, xp3, xm3, YP.w, YM.w, ZP.w, ZM.w, P.w);
+          R.x = update(S.x, B & 0xffu, xp0, xm0, YP.x, YM.x, ZP.x, ZM.x, P.x, m0, sweep, c2);
+          R.y = update(S.y, (B >> 8) & 0xffu, xp1, xm1, YP.y, YM.y, ZP.y, ZM.y, P.y, m0 + 1u, sweep, c2);
+          R.z = update(S.z, (B >> 16) & 0xffu, xp2, xm2, YP.z, YM.z, ZP.z, ZM.z, P.z, m0 + 2u, sweep, c2);
+          R.w = update(S.w, B >> 24, xp3, xm3, YP.w, YM.w, ZP.w, ZM.w, P.w, m0 + 3u, sweep, c2);
           *reinterpret_cast<uint4*>(sp + q0) = R;
         }
       } else {
@@ -243,9 +281,10 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
             nzm = sp[ea_slot(x, rzm, h)];
           }
           // u of this site (one word per site, shared by the 32 replicas)
-          const U4 P = philox10((uint32_t)m >> 2, sweep, c2, (uint32_t)sample, a.K);
+          const U4 P = PS ? U4{0u, 0u, 0u, 0u} : philox10((uint32_t)m >> 2, sweep, c2, (uint32_t)sample, a.K);
           sp[q] = update(sp[q], bb[q], sp[ea_slot(xp, (int)row, h)], sp[ea_slot(xm, (int)row, h)],
-                         sp[ea_slot(x, ryp, h)], sp[ea_slot(x, rym, h)], nzp, nzm, u4_word(P, m & 3));
+                         sp[ea_slot(x, ryp, h)], sp[ea_slot(x, rym, h)], nzp, nzm, u4_word(P, m & 3), (uint32_t)m,
+                         sweep, c2);
         }
       }
       __syncthreads();
@@ -351,6 +390,10 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
         suffix[tid] = v;
       }
       __syncthreads();
+      if constexpr (PS) {
+        build_tmask();
+        __syncthreads();
+      }
     }
   }
 
@@ -366,8 +409,8 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   }
 }
 
-template <int ND>
-__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) { ea_run<ND>(a, blockIdx.x); }
+template <int ND, bool PS>
+__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) { ea_run<ND, PS>(a, blockIdx.x); }
 
 // Served jobs of one lattice size, one single-sample job per CTA.
 template <int ND>
@@ -553,7 +596,7 @@ int ea_fail(int code, const char* msg) {
 }
 
 size_t ea_smem(int N) {
-  return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4 + spn::kEaBuckets * 4;
+  return (((size_t)N * 5 + 15) & ~(size_t)15) + (96 + 36 + 32) * 4 + 64 + 32 * 4 + spn::kEaBuckets * 4 + 96 * 4;
 }
 
 }  // namespace
@@ -797,12 +840,20 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
   return create_batch(out, model, dims, nsamples, couplings, betas, nbeta, seed, exchange_every, nullptr, false);
 }
 
+int spn_batch_set_u_per_slot(spn_handle h, int32_t on) {
+  if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
+  if (on != 0 && on != 1) return ea_fail(SPN_E_ARG, "on must be 0 or 1");
+  h->ea->args.u_per_slot = on;
+  return SPN_OK;
+}
+
 int spn_batch_sweep(spn_handle h, int64_t nsweeps) {
   if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
   if (nsweeps < 0) return ea_fail(SPN_E_ARG, "nsweeps must be >= 0");
   EaBatch* b = h->ea;
   if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return ea_fail(SPN_E_ARG, "sweep counter would exceed 2^32");
-  auto kern = b->nd == 2 ? spn::k_ea_resident<2> : spn::k_ea_resident<3>;
+  auto kern = b->args.u_per_slot ? (b->nd == 2 ? spn::k_ea_resident<2, true> : spn::k_ea_resident<3, true>)
+                                  : (b->nd == 2 ? spn::k_ea_resident<2, false> : spn::k_ea_resident<3, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   int64_t done = 0;
   while (done < nsweeps) {  // bounded launches keep each kernel well under a second

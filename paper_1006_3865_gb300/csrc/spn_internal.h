@@ -137,6 +137,7 @@ struct EaArgs {
   int nsweeps;
   int exchange_every;
   int nsamples;
+  int u_per_slot;             // 1: every temperature slot draws its own u (32 bit planes per site)
   PhiloxKeys K;
   int* err;
 };

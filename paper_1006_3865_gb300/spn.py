@@ -90,6 +90,7 @@ _SIGNATURES = {
     "spn_server_stats": (_c.c_int, [_vp, _P(_u64), _P(_dbl), _P(_u64), _P(_sz)]),
     "spn_server_destroy": (_c.c_int, [_vp]),
     "spn_create_batch": (_c.c_int, [_P(_vp), _c.c_int, _vp, _c.c_int, _vp, _vp, _c.c_int, _u64, _c.c_int]),
+    "spn_batch_set_u_per_slot": (_c.c_int, [_vp, _c.c_int32]),
     "spn_batch_sweep": (_c.c_int, [_vp, _i64]),
     "spn_batch_get_words": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_set_words": (_c.c_int, [_vp, _vp, _sz]),
@@ -391,7 +392,9 @@ def heis_exp_device(x: np.ndarray) -> np.ndarray:
 class EABatch:
     """Multi-spin coded +-J EA samples with replica exchange (spn_create_batch)."""
 
-    def __init__(self, dims, couplings: np.ndarray, betas, seed: int, exchange_every: int = 10):
+    def __init__(self, dims, couplings: np.ndarray, betas, seed: int, exchange_every: int = 10,
+                 u_per_slot: bool = False):
+        """u_per_slot: every temperature slot draws its own u (spn_batch_set_u_per_slot)."""
         self._lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.N = int(np.prod(self.dims))
@@ -404,6 +407,8 @@ class EABatch:
         _check(self._lib.spn_create_batch(_c.byref(h), model, _ptr(d), self.nsamples, _ptr(J), _ptr(b),
                                           int(b.size), seed, int(exchange_every)))
         self._h = h
+        if u_per_slot:
+            _check(self._lib.spn_batch_set_u_per_slot(self._h, 1))
 
     def sweep(self, nsweeps: int):
         _check(self._lib.spn_batch_sweep(self._h, int(nsweeps)))

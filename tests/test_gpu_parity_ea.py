@@ -19,7 +19,7 @@ def _lib():
     lib()
 
 
-def _oracle_batch(dims, bonds, betas, seed, nsweeps, X, samples, words0=None, slots0=None):
+def _oracle_batch(dims, bonds, betas, seed, nsweeps, X, samples, words0=None, slots0=None, u_per_slot=False):
     out_w, out_pi, out_acc = [], [], []
     for i in samples:
         w = (oracle.ea_init_hot(dims, 1, seed, stream0=i) if words0 is None else words0[i:i + 1].copy())
@@ -27,7 +27,8 @@ def _oracle_batch(dims, bonds, betas, seed, nsweeps, X, samples, words0=None, sl
         tau = np.zeros_like(pi)
         tau[0][pi[0]] = np.arange(32, dtype=np.uint8)
         acc = np.zeros((1, 32), np.int64)
-        oracle.ea_sweeps(dims, w, bonds[i:i + 1], betas, pi, tau, nsweeps, seed, stream0=i, exchange_every=X, acc=acc)
+        oracle.ea_sweeps(dims, w, bonds[i:i + 1], betas, pi, tau, nsweeps, seed, stream0=i, exchange_every=X, acc=acc,
+                         u_per_slot=u_per_slot)
         out_w.append(w[0])
         out_pi.append(pi[0])
         out_acc.append(acc[0])
@@ -73,6 +74,28 @@ def test_tied_and_crowded_thresholds(dims, ladder):
     assert np.array_equal(b.words(), w)
     assert np.array_equal(b.slots(), pi)
     assert np.array_equal(b.exchange_counts(), acc)
+    b.close()
+
+
+@pytest.mark.parametrize("dims,ns,X,sweeps", [((8, 8, 8), 3, 5, 30), ((6, 4, 2), 2, 3, 20), ((16, 8), 2, 10, 40),
+                                             ((4, 4), 2, 5, 30), ((24, 24, 24), 1, 10, 10)])
+def test_u_per_slot_matches_oracle(dims, ns, X, sweeps):
+    """Every temperature slot with its own u (32 bit planes per site), on the
+    four-word groups (Lx a multiple of 8) and the per-site loop, 2D and 3D, with
+    exchange: words, slot maps and exchange counts equal the oracle's."""
+    seed = inputs.unit_seed(320 + ns)
+    bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(321))
+    betas = inputs.geometric_ladder(0.2, 2.0)
+    b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X, u_per_slot=True)
+    b.sweep(sweeps // 2)
+    b.sweep(sweeps - sweeps // 2)
+    w, pi, acc = _oracle_batch(dims, bonds, betas, seed, sweeps, X, range(ns), u_per_slot=True)
+    assert np.array_equal(b.words(), w)
+    assert np.array_equal(b.slots(), pi)
+    assert np.array_equal(b.exchange_counts(), acc)
+    E, M = b.energies()
+    Eo, Mo = oracle.ea_observables(dims, w, bonds)
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo)
     b.close()
 
 

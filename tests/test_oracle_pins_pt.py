@@ -44,7 +44,7 @@ def _energy(spins, J, nb):
     return -sum((J[d] * s * s[..., nb[d]]).sum(axis=-1) for d in range(2))
 
 
-def _ladder_run(exchange, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=200, meas=2000):
+def _ladder_run(exchange, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=200, meas=2000, u_per_slot=False):
     """Per-chain mean energy at each temperature, the exact averages, the final
     words and couplings."""
     packed, J = _couplings(seed)
@@ -61,7 +61,7 @@ def _ladder_run(exchange, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=200
     sums = np.zeros((chains, 32))
     for it in range(burn + meas):
         oracle.ea_sweeps(DIMS, words, bonds, betas, pi, tau, X, seed, sweep0=X * it,
-                         exchange_every=X if exchange else 0)
+                         exchange_every=X if exchange else 0, u_per_slot=u_per_slot)
         if it >= burn:
             E, _ = oracle.ea_observables(DIMS, words, bonds)
             sums += np.take_along_axis(E, tau.astype(np.int64), axis=1)  # column t: the replica at temperature t
@@ -142,3 +142,14 @@ def test_independent_u_per_replica_makes_exchange_exact():
     +0.9, +1.9, -0.3, +1.2 for independent u.)"""
     z = numpy_ladder(shared_u=False)
     assert np.all(np.abs(z) < 5.0), np.round(z, 2)
+
+
+def test_oracle_ladder_with_a_u_per_slot_is_exact_with_exchange():
+    """The oracle's per-slot mode (every temperature slot draws its own u from 32
+    bit planes): with replica exchange every temperature stays Boltzmann-
+    distributed, as the numpy model with independent u does."""
+    means, exact, emin, *_ = _ladder_run(exchange=True, u_per_slot=True)
+    err = means.std(axis=0, ddof=1) / np.sqrt(means.shape[0])
+    z = (means.mean(axis=0) - exact) / np.maximum(err, 1e-3)
+    assert np.all(np.abs(z) < 5.0), np.round(z, 2)
+    assert means.mean(axis=0)[0] < emin + 2.5 and means.mean(axis=0)[-1] > emin + 8
