@@ -356,6 +356,23 @@ def test_onsager_energy_large_lattice(T, cold):
     assert abs(me - onsager_energy_per_spin(T)) < 4 * ee + 2e-3, (me, onsager_energy_per_spin(T), ee)
 
 
+def test_3d_energy_matches_the_high_temperature_series():
+    """3D Ising at small beta against the high-temperature expansion of the
+    simple cubic lattice: with t = tanh(beta), ln Z / N = ln 2 + 3 ln cosh(beta)
+    + 3 t^4 + O(t^6) (3N bonds; the smallest closed graphs are the 3N
+    plaquettes), so u = E / N = -3 t - 12 t^3 (1 - t^2) + O(t^5).  At
+    beta = 0.05 the plaquette term (1.5e-3) is about nine standard errors of
+    8000 sweeps, so a lattice that misses a neighbour or a bond fails."""
+    dims, beta = (32, 32, 32), 0.05
+    t = np.tanh(beta)
+    series = -3 * t - 12 * t ** 3 * (1 - t * t)
+    s = oracle.init_hot(dims, 11)
+    _, _, tE, _ = oracle.sweeps(dims, s, beta, 8200, 11)
+    me, ee = binned_mean_err(tE[200:] / s.size, nbins=20)
+    assert abs(me - series) < 4 * ee + 2e-5, (me, series, ee)
+    assert abs(me - (-3 * t)) > 4 * ee  # the plaquette term is seen
+
+
 def test_acceptance_rate_matches_threshold():
     """Across a run, the flip frequency of colour-0 sites with dE = 8 and dE = 4
     equals thr/2^32 within 5 sigma (the sweep applies the rule of Eq. 2)."""
