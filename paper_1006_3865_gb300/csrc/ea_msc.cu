@@ -29,6 +29,14 @@
 // counts unsatisfied bonds per replica, takes the exchange decisions of the
 // even or odd temperature pairs with host-built tables of
 // floor(exp(dbeta * dE) 2^32), and updates the permutation.
+//
+// Optional (k_ea_resident<ND, true>): every slot draws its own u, bit 31 - p of
+// slot j's u being bit j of plane p of the site's own Philox calls.  A shared
+// u leaves each replica's Metropolis step exact but correlates the replicas,
+// and replica exchange then lets the temperature marginals drift; with a u per
+// slot the ladder stays exact.  The CTA keeps per dE level and plane the mask
+// of slots whose temperature's threshold has that bit set (rebuilt after each
+// exchange) and compares planes most significant first until no slot ties.
 #include <cuda_runtime.h>
 
 #include <algorithm>
