@@ -112,16 +112,6 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps);
  * whose Lx is a multiple of 64; SPN_E_ARG otherwise. */
 int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile, int32_t hits);
 
-/* Test support for failure detection; the paper has no counterpart.  In the
- * next streaming-sweep launch (in any handle of the process) the copy of each
- * CTA's first slice is never issued, so the wait for it runs out after `polls`
- * polls (the bound every wait of that launch uses).  The kernel then records
- * the failure, waits (bounded) for the copies it did issue and returns; no
- * device fault occurs, the context stays usable, and the next spn_observables /
- * spn_trace / spn_sync of that handle returns SPN_E_TIMEOUT.  Only tests call
- * this. */
-int spn_test_expire_next_waits(uint32_t polls);
-
 int spn_observables(spn_handle h, int64_t* E, int64_t* M);
 
 /* Recompute E and M from the spins with a full reduction (independent of the
@@ -476,7 +466,10 @@ int spn_server_destroy(spn_server s);
  * It allocates nothing: its scratch (a second lattice for the ping-pong
  * streaming kernel and an error word) is a fixed 16 MiB static device array
  * that every GPU loading the library holds until the process exits, so N is
- * limited to 16,777,216 sites (SPN_E_ARG beyond).  The first call on a device
+ * limited to 16,777,216 sites (SPN_E_ARG beyond).  A 16-byte aligned lattice
+ * whose rows are whole multiples of 64 sites takes the streaming sweep; any other
+ * lattice (including a pointer into the middle of a caller's buffer) takes the
+ * generic sweep, with identical results.  The first call on a device
  * looks up that array's device address; make it before any stream capture.
  * All calls share the array: calls that overlap on the GPU (other threads or
  * streams) race and corrupt each other's results. */

@@ -15,10 +15,12 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <tuple>
 #include <vector>
 
 #include "spn.h"
+#include "spn_testing.h"
 #include "spn_internal.h"
 
 namespace {
@@ -417,15 +419,15 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
     cudaError_t e;
     if (h->path == spn::kPathPacked) {
       e = spn::launch_sweep_stream(h->g, h->packed[h->pcur], h->packed[h->pcur ^ 1], geo, T, K, h->stream_id, sweep,
-                                   acc, h->d_err, h->st);
+                                   acc, h->d_err, h->st, std::exchange(h->expire_polls, 0u));
       if (e == cudaSuccess) h->pcur ^= 1;
     } else if (staged) {
       e = spn::launch_sweep_stream(gs, h->staged[sc], h->staged[sc ^ 1], geo, T, K, h->stream_id, sweep, acc,
-                                   h->d_err, h->st);
+                                   h->d_err, h->st, std::exchange(h->expire_polls, 0u));
       if (e == cudaSuccess) sc ^= 1;
     } else if (h->path == spn::kPathStream) {
       e = spn::launch_sweep_stream(h->g, h->spins[h->cur], h->spins[h->cur ^ 1], geo, T, K, h->stream_id, sweep,
-                                   acc, h->d_err, h->st);
+                                   acc, h->d_err, h->st, std::exchange(h->expire_polls, 0u));
       if (e == cudaSuccess) h->cur ^= 1;
     } else {
       e = spn::launch_sweep_generic(h->g, h->spins[h->cur], T, K, h->stream_id, sweep, acc, h->st);
@@ -477,8 +479,9 @@ int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile
   return SPN_OK;
 }
 
-int spn_test_expire_next_waits(uint32_t polls) {
-  spn::stream_expire_next_waits(polls);
+int spn_test_expire_next_waits(spn_handle h, uint32_t polls) {
+  if (!h || h->ea || h->heis) return fail(SPN_E_STATE, "an Ising lattice handle is required");
+  h->expire_polls = polls ? polls : 1;
   return SPN_OK;
 }
 

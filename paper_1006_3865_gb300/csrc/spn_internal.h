@@ -61,9 +61,6 @@ bool stream_path_supported(const Lattice& g, int TY, bool packed = false);
 int packed_row_words(int Lx);
 cudaError_t launch_pack(const Lattice& g, const int8_t* s, uint32_t* w, cudaStream_t st);
 cudaError_t launch_unpack(const Lattice& g, const uint32_t* w, int8_t* s, cudaStream_t st);
-// Test support: every bounded wait of the next streaming launch runs out after
-// `polls` polls (its barriers expect more bytes than its copies bring).
-void stream_expire_next_waits(uint32_t polls);
 // Double-checkerboard sweep (tiles Tx x Ty (x Tz), Tx a multiple of 64, an even
 // number of tiles per axis, dense int8 lattice, no bonds): both tile parities
 // of one sweep, `hits` updates of each colour per tile.
@@ -73,9 +70,12 @@ cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz,
                             cudaStream_t st);
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed = false);
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
+// expire_polls (test support, 0 otherwise): the copy of each CTA's first slice
+// is never issued and every bounded wait of the launch gives up after that many
+// polls, so the launch reports a timeout without any device fault.
 cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, const StreamGeom& geo,
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
-                                unsigned long long* acc, int* err, cudaStream_t st);
+                                unsigned long long* acc, int* err, cudaStream_t st, uint32_t expire_polls = 0);
 
 // One instance of a batched resident run (batched.cu).
 struct ResInst {
@@ -192,6 +192,7 @@ struct spn_ctx {
   spn::Lattice g;
   uint64_t seed = 0;
   uint32_t stream_id = 0;
+  uint32_t expire_polls = 0;  // test support: the next streaming launch of this handle gives up its waits
   int8_t* spins[2] = {nullptr, nullptr};
   int cur = 0;
   // streaming sweep of a lattice whose Lx is not a multiple of 64: the lattice

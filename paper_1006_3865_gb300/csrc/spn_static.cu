@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -107,10 +108,14 @@ extern "C" int spn_sweep_noalloc(int model, const int32_t* dims, int8_t* d_spins
   const spn::DevThr T = spn::make_thresholds(beta);
   const spn::PhiloxKeys K = spn::philox_keys(seed);
   // the streaming sweep with the tallest band (3D: even, at most 32 rows, dividing
-  // Ly) whose geometry fits one CTA; otherwise the generic sweep
+  // Ly) whose geometry fits one CTA; otherwise the generic sweep.  The streaming
+  // sweep moves whole rows with bulk copies and 16-byte stores, so it needs a
+  // 16-byte aligned lattice; a caller's pointer into the middle of a buffer that
+  // is not takes the generic sweep (byte accesses), with the same results.
   bool stream = false;
   spn::StreamGeom geo{};
-  for (int ty = g.nd == 3 ? 32 : 1; ty >= 1 && !stream; ty -= (g.nd == 3 ? 2 : 1)) {
+  const bool aligned16 = ((uintptr_t)d_spins & 15u) == 0;
+  for (int ty = g.nd == 3 ? 32 : 1; aligned16 && ty >= 1 && !stream; ty -= (g.nd == 3 ? 2 : 1)) {
     if (g.nd == 3 && (ty < 2 || g.Ly % ty)) continue;
     if (!spn::stream_path_supported(g, ty)) continue;
     geo = spn::stream_geometry(g, ty, 0, 0);

@@ -383,10 +383,13 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
   if (!ok) {  // uniform: every thread saw the same barrier result
     if (tid == 0) {
       atomicExch(a.err, 1);
-      // let the copies still in flight land before the CTA exits (bounded)
+      // let the copies still in flight land before the CTA exits: every issued
+      // slice gets the full poll bound (a shortened test bound applies only to
+      // the wait that gave up), and a slice whose copy was never issued is skipped
       for (int li = issued > nraw ? issued - nraw : 0; li < issued; ++li) {
+        if (a.skip_first && li == 0) continue;
         unsigned n = 0;
-        while (!mbar_try_wait(&bars[li % nraw], (uint32_t)((li / nraw) & 1)) && ++n < a.wait_limit) {
+        while (!mbar_try_wait(&bars[li % nraw], (uint32_t)((li / nraw) & 1)) && ++n < kWaitLimit) {
         }
       }
     }
@@ -401,10 +404,6 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
 static int pitch_of(const Lattice& g) { return g.pitch ? g.pitch : g.Lx; }
 
 int packed_row_words(int Lx) { return (2 * ((Lx + 63) / 64) + 3) & ~3; }
-
-static std::atomic<uint32_t> g_expire_next{0};
-
-void stream_expire_next_waits(uint32_t polls) { g_expire_next.store(polls ? polls : 1); }
 
 namespace {
 
@@ -517,7 +516,7 @@ bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
 
 cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, const StreamGeom& geo,
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
-                                unsigned long long* acc, int* err, cudaStream_t st) {
+                                unsigned long long* acc, int* err, cudaStream_t st, uint32_t expire_polls) {
   if (!stream_geometry_ok(g, geo)) return cudaErrorInvalidConfiguration;
   if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return cudaErrorMisalignedAddress;  // bulk copies, 16-B stores
   StreamArgs a;
@@ -547,12 +546,9 @@ cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, con
   a.err = err;
   a.wait_limit = kWaitLimit;
   a.skip_first = 0;
-  {
-    const uint32_t inj = g_expire_next.exchange(0);
-    if (inj) {  // slice 0 of every CTA is never copied; waits give up after `inj` polls
-      a.skip_first = 1;
-      a.wait_limit = inj;
-    }
+  if (expire_polls) {  // slice 0 of every CTA is never copied; waits give up after `expire_polls` polls
+    a.skip_first = 1;
+    a.wait_limit = expire_polls;
   }
   dim3 grid(g.nd == 3 ? g.Ly / geo.TY : 1, geo.nseg);
   // function attributes are set once per device and raised only when a launch needs more

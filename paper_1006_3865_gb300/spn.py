@@ -16,7 +16,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libspn.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "spn.h")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+HEADER = os.path.join(INCLUDE, "spn.h")
+HEADERS = (HEADER, os.path.join(INCLUDE, "spn_testing.h"))
 
 SPN_OK = 0
 SPN_E_ARG = -1
@@ -61,7 +63,7 @@ _SIGNATURES = {
     "spn_create_ex": (_c.c_int, [_P(_vp), _c.c_int, _vp, _vp, _u64, _u32, _c.c_int]),
     "spn_sweep": (_c.c_int, [_vp, _dbl, _i64]),
     "spn_sweep_dc": (_c.c_int, [_vp, _dbl, _i64, _P(_i32), _i32]),
-    "spn_test_expire_next_waits": (_c.c_int, [_u32]),
+    "spn_test_expire_next_waits": (_c.c_int, [_vp, _u32]),
     "spn_observables": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
     "spn_recompute": (_c.c_int, [_vp, _P(_i64), _P(_i64)]),
     "spn_trace": (_c.c_int, [_vp, _vp, _vp, _i64, _P(_i64)]),
@@ -145,8 +147,8 @@ class SpnError(RuntimeError):
 
 
 def header_functions() -> list[str]:
-    """Names of the functions declared in include/spn.h."""
-    text = open(HEADER).read()
+    """Names of the functions declared in include/spn.h and include/spn_testing.h."""
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(spn_[a-z0-9_]+)\s*\(", text)))
 

@@ -23,7 +23,7 @@ def _lib():
 def test_bounded_wait_runs_out_and_reports_timeout(model, dims, path):
     lat = spn.Lattice(model, dims, 5)
     lat.path = path
-    spn.load().spn_test_expire_next_waits(256)
+    spn.load().spn_test_expire_next_waits(lat._h, 256)
     lat.sweep(0.44, 1)
     with pytest.raises(spn.SpnError) as e:
         lat.observables()

@@ -373,6 +373,31 @@ def test_3d_energy_matches_the_high_temperature_series():
     assert abs(me - (-3 * t)) > 4 * ee  # the plaquette term is seen
 
 
+def test_3d_energy_matches_the_low_temperature_series():
+    """3D Ising deep in the ordered phase against the low-temperature expansion
+    of the simple cubic lattice.  From the all-up ground state (E = -3N), the
+    excitations up to 14 broken bonds are: one flipped spin (6 broken bonds, N
+    ways), two flipped neighbours (10, 3N ways), two flipped non-neighbours (12,
+    N(N-1)/2 - 3N ways) and a flipped path of three sites (14, 15N ways: two of
+    the centre's six neighbours).  With x = exp(-2 beta) the logarithm of the
+    polymer sum gives ln Z / N = 3 beta + x^6 + 3 x^10 - 7/2 x^12 + 15 x^14 +
+    O(x^16), hence u = E / N = -3 + 12 e^(-12 beta) + 60 e^(-20 beta)
+    - 84 e^(-24 beta) + 420 e^(-28 beta).  At beta = 0.6 from a cold start the
+    single-flip term (9.0e-3) is far beyond the error bar and the neighbour-pair
+    term (3.7e-4) is several standard errors, so a sweep that drops or doubles
+    a neighbour, or maps dE = 12 to the wrong threshold, fails."""
+    dims, beta = (24, 24, 24), 0.6
+    N = 24 ** 3
+    e = lambda a: np.exp(-a * beta)
+    series = -3 + 12 * e(12) + 60 * e(20) - 84 * e(24) + 420 * e(28)
+    s = np.ones(N, np.int8)
+    _, _, tE, _ = oracle.sweeps(dims, s, beta, 8200, 23)
+    me, ee = binned_mean_err(tE[200:] / N, nbins=20)
+    assert abs(me - series) < 4 * ee + 1e-5, (me, series, ee)
+    assert abs(me - (-3 + 12 * e(12))) > 4 * ee  # the neighbour-pair excitations are seen
+    assert abs(me + 3) > 100 * ee  # single flips are seen
+
+
 def test_acceptance_rate_matches_threshold():
     """Across a run, the flip frequency of colour-0 sites with dE = 8 and dE = 4
     equals thr/2^32 within 5 sigma (the sweep applies the rule of Eq. 2)."""
