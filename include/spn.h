@@ -31,10 +31,15 @@
  *     site's 32-bit number is its lane's bit of plane q (purpose 0: Metropolis,
  *     1: hot start, which takes bit 31 as "spin -1").  A move with dE > 0 is
  *     accepted iff u < floor(exp(-beta dE) * 2^32) (Eq. 2).  The multi-spin
- *     coded EA sweep uses word m & 3 of R(m >> 2, sweep, colour | 3 << 1,
- *     sample) for within-colour index m; replica exchange word k & 3 of
- *     R(k >> 2, step, 2 << 1, sample).  Results are bit-identical for a given
- *     (seed, stream, sweep index, beta) on every path.
+ *     coded EA sweep of a batch with replica exchange gives every temperature
+ *     slot j of the site with within-colour index m its own u: bit 31 - p of
+ *     it is bit j of plane p = word p & 3 of R(m, sweep, colour | 3 << 1 |
+ *     (p / 4 + 1) << 4, sample).  A batch without exchange (or one switched by
+ *     spn_batch_set_u_per_slot(h, 0)) shares one u per site among the slots:
+ *     word m & 3 of R(m >> 2, sweep, colour | 3 << 1, sample).  Replica
+ *     exchange uses word k & 3 of R(k >> 2, step, 2 << 1, sample).  Results
+ *     are bit-identical for a given (seed, stream, sweep index, beta) on every
+ *     path.
  *   - A handle is not thread-safe; a server is.
  */
 #ifndef SPN_H
@@ -325,22 +330,26 @@ int spn_multi_destroy(spn_multi m);
 int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
                      const double* betas, int nbeta, uint64_t seed, int exchange_every);
 
-/* Run nsweeps multi-spin coded sweeps (colour 0, then colour 1; the 32
- * replicas of a site share its Philox word) with the exchanges due. */
+/* Run nsweeps multi-spin coded sweeps (colour 0, then colour 1) with the
+ * exchanges due; every slot draws its own u, or the 32 replicas of a site share
+ * its Philox word, as spn_batch_set_u_per_slot says. */
 int spn_batch_sweep(spn_handle h, int64_t nsweeps);
 
 /* Random numbers of the temperature slots (Sec. 4's multi-spin coding puts
  * many replicas in one word; which of them share random numbers is a choice).
- * on = 0 (default): the 32 slots of a site share one u, as above.  With replica
- * exchange that correlates the replicas and the temperature marginals drift
- * slightly (about 1% of E on a 4 x 4 ladder).  on = 1: every slot draws its own
- * u, bit 31 - p of slot j's u being bit j of plane p, plane p = word p & 3 of
- * Philox(m, sweep, colour | 3 << 1 | (p / 4 + 1) << 4, sample) for site m of its
- * colour, compared most significant plane first until every slot is decided;
- * exchange then keeps every temperature Boltzmann-distributed, at the cost of
- * about two Philox calls per site instead of a quarter.  Takes effect from the
- * next spn_batch_sweep.  SPN_E_STATE if h is not a batch handle, SPN_E_ARG if
- * on is not 0 or 1. */
+ * on = 1 (the default of a batch with exchange_every > 0): every slot draws its
+ * own u, bit 31 - p of slot j's u being bit j of plane p, plane p = word p & 3
+ * of Philox(m, sweep, colour | 3 << 1 | (p / 4 + 1) << 4, sample) for site m of
+ * its colour, compared most significant plane first until every slot is
+ * decided; replica exchange then keeps every temperature Boltzmann-distributed.
+ * on = 0 (the default without exchange): the 32 slots of a site share one u,
+ * word m & 3 of Philox(m >> 2, sweep, colour | 3 << 1, sample), about eight
+ * times fewer Philox calls.  Each replica is still an exact Metropolis chain,
+ * but the replicas of a sample are correlated, and with replica exchange the
+ * temperature marginals then drift (about 1% of E at the hottest temperature
+ * of a 4 x 4 ladder): choose it with exchange only knowingly.  Takes effect
+ * from the next spn_batch_sweep.  SPN_E_STATE if h is not a batch handle,
+ * SPN_E_ARG if on is not 0 or 1. */
 int spn_batch_set_u_per_slot(spn_handle h, int32_t on);
 
 /* Site words [sample][N] (bit j = replica in slot j, 1 = spin -1). */

@@ -247,10 +247,14 @@ def ea_observables(dims, words: np.ndarray, bonds: np.ndarray):
 
 def ea_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, temp_of_slot: np.ndarray,
               slot_of_temp: np.ndarray, nsweeps: int, seed: int, stream0: int = 0, sweep0: int = 0,
-              exchange_every: int = 0, acc: np.ndarray | None = None, u_per_slot: bool = False):
+              exchange_every: int = 0, acc: np.ndarray | None = None, u_per_slot: bool | None = None):
     """Multi-spin coded sweeps, in place on ``words`` [nsamples, N] and the slot maps.
     u_per_slot: every temperature slot draws its own u (32 bit planes, eight
-    Philox calls per site) instead of sharing the site's one u."""
+    Philox calls per site) instead of sharing the site's one u; None takes the
+    per-slot u with replica exchange (exchange_every > 0) and the shared u
+    without, as a batch does by default."""
+    if u_per_slot is None:
+        u_per_slot = exchange_every > 0
     d = _dims(dims)
     for a, dt in ((words, np.uint32), (temp_of_slot, np.uint8), (slot_of_temp, np.uint8)):
         if a.dtype != dt or not a.flags.c_contiguous:

@@ -30,13 +30,16 @@
 // even or odd temperature pairs with host-built tables of
 // floor(exp(dbeta * dE) 2^32), and updates the permutation.
 //
-// Optional (k_ea_resident<ND, true>): every slot draws its own u, bit 31 - p of
-// slot j's u being bit j of plane p of the site's own Philox calls.  A shared
-// u leaves each replica's Metropolis step exact but correlates the replicas,
-// and replica exchange then lets the temperature marginals drift; with a u per
-// slot the ladder stays exact.  The CTA keeps per dE level and plane the mask
-// of slots whose temperature's threshold has that bit set (rebuilt after each
-// exchange) and compares planes most significant first until no slot ties.
+// With replica exchange (the default there; k_ea_resident<ND, true>) every slot
+// draws its own u, bit 31 - p of slot j's u being bit j of plane p of the
+// site's own Philox calls.  A shared u leaves each replica's Metropolis step
+// exact but correlates the replicas, and replica exchange then lets the
+// temperature marginals drift; with a u per slot the ladder stays exact.  The
+// CTA keeps per dE level and plane the mask of slots whose temperature's
+// threshold has that bit set (rebuilt after each exchange) and compares planes
+// most significant first until no slot ties: planes 0-7 for all four sites of
+// a thread at once (their Philox calls interleaved), then the few sites still
+// tied one call at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -155,11 +158,11 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
     return cnt;
   };
   constexpr uint32_t kSearch = ND == 3 ? 0x808080u : 0x8080u;  // some level needs the search
-  // new word of a site: s its 32 replicas, bits its bond byte, n* the neighbour
-  // words (x+, x-, y+, y-, z+, z-), u its uniform deviate
-  auto update = [&](uint32_t s, uint32_t bits, uint32_t nxp, uint32_t nxm, uint32_t nyp, uint32_t nym, uint32_t nzp,
-                    uint32_t nzm, uint32_t u, uint32_t m, uint32_t sw, uint32_t c2) -> uint32_t {
-    // bond masks: bits 0..2 forward, 3..5 backward
+  // bit-sliced count k = s0 + 2 s1 + 4 s2 (0 .. 2 ND) of the unsatisfied bonds of
+  // a site's 32 replicas: s its word, bits its bond byte (bits 0..2 forward,
+  // 3..5 backward, set iff J = -1), n* the neighbour words (x+, x-, y+, y-, z+, z-)
+  auto unsat_count = [&](uint32_t s, uint32_t bits, uint32_t nxp, uint32_t nxm, uint32_t nyp, uint32_t nym,
+                         uint32_t nzp, uint32_t nzm, uint32_t& s0, uint32_t& s1, uint32_t& s2) {
     const uint32_t ux = s ^ nxp ^ (0u - (bits & 1u));
     const uint32_t uy = s ^ nyp ^ (0u - ((bits >> 1) & 1u));
     const uint32_t vx = s ^ nxm ^ (0u - ((bits >> 3) & 1u));
@@ -169,11 +172,19 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
       uz = s ^ nzp ^ (0u - ((bits >> 2) & 1u));
       vz = s ^ nzm ^ (0u - ((bits >> 5) & 1u));
     }
-    // bit-sliced count of unsatisfied bonds k = s0 + 2 s1 + 4 s2 (0..2 ND)
     const uint32_t x1 = ux ^ uy ^ uz, y1 = (ux & uy) | (uz & (ux ^ uy));
     const uint32_t x2 = vx ^ vy ^ vz, y2 = (vx & vy) | (vz & (vx ^ vy));
-    const uint32_t s0 = x1 ^ x2, cc = x1 & x2;
-    const uint32_t s1 = y1 ^ y2 ^ cc, s2 = (y1 & y2) | (cc & (y1 ^ y2));
+    s0 = x1 ^ x2;
+    const uint32_t cc = x1 & x2;
+    s1 = y1 ^ y2 ^ cc;
+    s2 = (y1 & y2) | (cc & (y1 ^ y2));
+  };
+  // new word of a site: s its 32 replicas, bits its bond byte, n* the neighbour
+  // words, u its uniform deviate (shared u) or m its site index (a u per slot)
+  auto update = [&](uint32_t s, uint32_t bits, uint32_t nxp, uint32_t nxm, uint32_t nyp, uint32_t nym, uint32_t nzp,
+                    uint32_t nzm, uint32_t u, uint32_t m, uint32_t sw, uint32_t c2) -> uint32_t {
+    uint32_t s0, s1, s2;
+    unsat_count(s, bits, nxp, nxm, nyp, nym, nzp, nzm, s0, s1, s2);
     if constexpr (PS) {
       // slot j's u has bit 31 - p = bit j of plane p (word p & 3 of the site's
       // Philox call p / 4); planes most significant first against the slots'
@@ -254,7 +265,6 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
             ZP = *reinterpret_cast<const uint4*>(sp + (rzp * 2 + par) * h + k0);
             ZM = *reinterpret_cast<const uint4*>(sp + (rzm * 2 + par) * h + k0);
           }
-          const U4 P = PS ? U4{0u, 0u, 0u, 0u} : philox10((uint32_t)g, sweep, c2, (uint32_t)sample, a.K);
           const uint32_t o[4] = {O4.x, O4.y, O4.z, O4.w};
           // even x: x+1 is other-parity word k, x-1 word k-1; odd x: x-1 word k, x+1 word k+1
           const uint32_t xp0 = par ? o[1] : o[0], xm0 = par ? o[0] : oe;
@@ -262,10 +272,92 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
           const uint32_t xp2 = par ? o[3] : o[2], xm2 = par ? o[2] : o[1];
           const uint32_t xp3 = par ? oe : o[3], xm3 = par ? o[3] : o[2];
           uint4 R;
-          R.x = update(S.x, B & 0xffu, xp0, xm0, YP.x, YM.x, ZP.x, ZM.x, P.x, m0, sweep, c2);
-          R.y = update(S.y, (B >> 8) & 0xffu, xp1, xm1, YP.y, YM.y, ZP.y, ZM.y, P.y, m0 + 1u, sweep, c2);
-          R.z = update(S.z, (B >> 16) & 0xffu, xp2, xm2, YP.z, YM.z, ZP.z, ZM.z, P.z, m0 + 2u, sweep, c2);
-          R.w = update(S.w, B >> 24, xp3, xm3, YP.w, YM.w, ZP.w, ZM.w, P.w, m0 + 3u, sweep, c2);
+          if constexpr (PS) {
+            // The four sites' own Philox calls run side by side: planes 0-7 (two
+            // calls per site) for every site, then, only for sites with a slot
+            // still tied (about one in twenty), further calls one at a time.
+            const uint32_t sv[4] = {S.x, S.y, S.z, S.w};
+            const uint32_t xp[4] = {xp0, xp1, xp2, xp3}, xm[4] = {xm0, xm1, xm2, xm3};
+            const uint32_t yp[4] = {YP.x, YP.y, YP.z, YP.w}, ym[4] = {YM.x, YM.y, YM.z, YM.w};
+            const uint32_t zp[4] = {ZP.x, ZP.y, ZP.z, ZP.w}, zm[4] = {ZM.x, ZM.y, ZM.z, ZM.w};
+            uint32_t acc[4], tied[4], la[4], lb[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              uint32_t s0, s1, s2;
+              unsat_count(sv[w], (B >> (8 * w)) & 0xffu, xp[w], xm[w], yp[w], ym[w], zp[w], zm[w], s0, s1, s2);
+              const uint32_t k2 = ~s0 & s1 & ~s2, k1 = s0 & ~s1 & ~s2, k0 = ~(s0 | s1 | s2);
+              // level 0 (dE = 4) and level 1 (dE = 8) slots select threshold planes
+              // 0 and 1; the remaining tied slots (3D: dE = 12) select plane 2
+              la[w] = ND == 3 ? k2 : k1;
+              lb[w] = ND == 3 ? k1 : k0;
+              tied[w] = ND == 3 ? (k2 | k1 | k0) : (k1 | k0);
+              acc[w] = ND == 3 ? (s2 | (s0 & s1)) : (s1 | s2);
+            }
+#pragma unroll
+            for (uint32_t call = 0; call < 2u; ++call) {
+              U4 P[4];
+#pragma unroll
+              for (int w = 0; w < 4; ++w)
+                P[w] = philox10(m0 + (uint32_t)w, sweep, c2 | ((call + 1u) << 4), (uint32_t)sample, a.K);
+              const uint4 T0 = *reinterpret_cast<const uint4*>(tmask + 4 * call);
+              const uint4 T1 = *reinterpret_cast<const uint4*>(tmask + 32 + 4 * call);
+              const uint4 T2 = ND == 3 ? *reinterpret_cast<const uint4*>(tmask + 64 + 4 * call) : T1;
+              const uint32_t t0[4] = {T0.x, T0.y, T0.z, T0.w}, t1[4] = {T1.x, T1.y, T1.z, T1.w},
+                             t2[4] = {T2.x, T2.y, T2.z, T2.w};
+#pragma unroll
+              for (int w = 0; w < 4; ++w) {
+                const uint32_t pl[4] = {P[w].x, P[w].y, P[w].z, P[w].w};
+#pragma unroll
+                for (int jp = 0; jp < 4; ++jp) {
+                  const uint32_t t = (la[w] & t0[jp]) | (~la[w] & ((lb[w] & t1[jp]) | (~lb[w] & t2[jp])));
+                  acc[w] |= tied[w] & ~pl[jp] & t;
+                  tied[w] &= ~(pl[jp] ^ t);
+                }
+              }
+            }
+            // Sites still tied after 8 planes (about one in ten): one call at a
+            // time for the lane's first tied site, so the warp runs as many calls
+            // as its busiest lane needs rather than one per site position.
+            uint32_t nxt = 2u | (2u << 4) | (2u << 8) | (2u << 12);  // next call of each site, 4 bits each
+#pragma unroll 1
+            for (int guard = 0; guard < 24; ++guard) {
+              const int w = tied[0] ? 0 : tied[1] ? 1 : tied[2] ? 2 : tied[3] ? 3 : -1;
+              if (w < 0) break;
+              const uint32_t call = (nxt >> (4 * w)) & 15u;
+              const uint32_t lw = w == 0 ? la[0] : w == 1 ? la[1] : w == 2 ? la[2] : la[3];
+              const uint32_t mw = w == 0 ? lb[0] : w == 1 ? lb[1] : w == 2 ? lb[2] : lb[3];
+              uint32_t tw = w == 0 ? tied[0] : w == 1 ? tied[1] : w == 2 ? tied[2] : tied[3];
+              uint32_t aw = 0;
+              const U4 P = philox10(m0 + (uint32_t)w, sweep, c2 | ((call + 1u) << 4), (uint32_t)sample, a.K);
+              const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
+              const uint4 Q0 = *reinterpret_cast<const uint4*>(tmask + 4 * call);
+              const uint4 Q1 = *reinterpret_cast<const uint4*>(tmask + 32 + 4 * call);
+              const uint4 Q2 = ND == 3 ? *reinterpret_cast<const uint4*>(tmask + 64 + 4 * call) : Q1;
+              const uint32_t q0[4] = {Q0.x, Q0.y, Q0.z, Q0.w}, q1[4] = {Q1.x, Q1.y, Q1.z, Q1.w},
+                             q2[4] = {Q2.x, Q2.y, Q2.z, Q2.w};
+#pragma unroll
+              for (int jp = 0; jp < 4; ++jp) {
+                const uint32_t t = (lw & q0[jp]) | (~lw & ((mw & q1[jp]) | (~mw & q2[jp])));
+                aw |= tw & ~pl[jp] & t;
+                tw &= ~(pl[jp] ^ t);
+              }
+              if (call == 7u) tw = 0;  // all 32 planes compared: a tie is u = t, not below
+              nxt += 1u << (4 * w);
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                if (v == w) {
+                  acc[v] |= aw;
+                  tied[v] = tw;
+                }
+            }
+            R = make_uint4(sv[0] ^ acc[0], sv[1] ^ acc[1], sv[2] ^ acc[2], sv[3] ^ acc[3]);
+          } else {
+            const U4 P = philox10((uint32_t)g, sweep, c2, (uint32_t)sample, a.K);
+            R.x = update(S.x, B & 0xffu, xp0, xm0, YP.x, YM.x, ZP.x, ZM.x, P.x, m0, sweep, c2);
+            R.y = update(S.y, (B >> 8) & 0xffu, xp1, xm1, YP.y, YM.y, ZP.y, ZM.y, P.y, m0 + 1u, sweep, c2);
+            R.z = update(S.z, (B >> 16) & 0xffu, xp2, xm2, YP.z, YM.z, ZP.z, ZM.z, P.z, m0 + 2u, sweep, c2);
+            R.w = update(S.w, B >> 24, xp3, xm3, YP.w, YM.w, ZP.w, ZM.w, P.w, m0 + 3u, sweep, c2);
+          }
           *reinterpret_cast<uint4*>(sp + q0) = R;
         }
       } else {
@@ -303,63 +395,67 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
       // unsatisfied forward bonds of every replica, bit-sliced per thread
       if (tid < 32) ucount[tid] = 0;
       __syncthreads();
-      uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int n = tid; n < N; n += nth) {
-        const int r = (int)fdiv((uint32_t)n >> 1, a.div_h);  // n / Lx (Lx = 2 h)
-        const int x = n - r * a.Lx;
-        const int z = ND == 3 ? (int)fdiv((uint32_t)r, a.div_ly) : 0;
-        const int y = r - z * a.Ly;
-        const int q = ea_slot(x, r, h);
-        const uint32_t s = sp[q];
-        const uint32_t bits = bb[q];
-        const int xp = x + 1 == a.Lx ? 0 : x + 1;
-        const int ryp = y + 1 == a.Ly ? r - a.Ly + 1 : r + 1;
-        uint32_t w3[ND];
-        w3[0] = s ^ sp[ea_slot(xp, r, h)] ^ (0u - (bits & 1u));
-        w3[1] = s ^ sp[ea_slot(x, ryp, h)] ^ (0u - ((bits >> 1) & 1u));
-        if constexpr (ND == 3) {
-          const int rzp = z + 1 == a.Lz ? r - nrow + a.Ly : r + a.Ly;
-          w3[2] = s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u));
-        }
+      // chunks of at most 80 sites per thread keep every 8-bit counter <= 240
+      for (int n0 = 0; n0 < N; n0 += 80 * nth) {  // block-uniform
+        uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int n1 = N < n0 + 80 * nth ? N : n0 + 80 * nth;
+        for (int n = n0 + tid; n < n1; n += nth) {
+          const int r = (int)fdiv((uint32_t)n >> 1, a.div_h);  // n / Lx (Lx = 2 h)
+          const int x = n - r * a.Lx;
+          const int z = ND == 3 ? (int)fdiv((uint32_t)r, a.div_ly) : 0;
+          const int y = r - z * a.Ly;
+          const int q = ea_slot(x, r, h);
+          const uint32_t s = sp[q];
+          const uint32_t bits = bb[q];
+          const int xp = x + 1 == a.Lx ? 0 : x + 1;
+          const int ryp = y + 1 == a.Ly ? r - a.Ly + 1 : r + 1;
+          uint32_t w3[ND];
+          w3[0] = s ^ sp[ea_slot(xp, r, h)] ^ (0u - (bits & 1u));
+          w3[1] = s ^ sp[ea_slot(x, ryp, h)] ^ (0u - ((bits >> 1) & 1u));
+          if constexpr (ND == 3) {
+            const int rzp = z + 1 == a.Lz ? r - nrow + a.Ly : r + a.Ly;
+            w3[2] = s ^ sp[ea_slot(x, rzp, h)] ^ (0u - ((bits >> 2) & 1u));
+          }
 #pragma unroll
-        for (int d = 0; d < ND; ++d) {
-          uint32_t carry = w3[d];
+          for (int d = 0; d < ND; ++d) {
+            uint32_t carry = w3[d];
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {
-            const uint32_t t = cnt[b] & carry;
-            cnt[b] ^= carry;
-            carry = t;
+            for (int b = 0; b < 8; ++b) {
+              const uint32_t t = cnt[b] & carry;
+              cnt[b] ^= carry;
+              carry = t;
+            }
           }
         }
+        // per-replica totals of the chunk (at most 255 per thread: ND bonds x at
+        // most 80 sites).  Bit j of cnt[b] is bit b of replica j's count: byte g of
+        // the eight words is an 8 x 8 bit block (row b, column k = replica 8 g + k),
+        // whose transpose holds the counts of replicas 8 g .. 8 g + 7 as bytes.
+        // Two counts share a word for the warp sum (at most 32 x 255 < 2^16 each).
+        uint32_t pk[16];  // pk[i]: replica 2 i in bits 0-15, replica 2 i + 1 in bits 16-31
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          unsigned long long mt = 0;
+#pragma unroll
+          for (int b = 0; b < 8; ++b) mt |= (unsigned long long)((cnt[b] >> (8 * g)) & 0xffu) << (8 * b);
+          unsigned long long t = (mt ^ (mt >> 7)) & 0x00AA00AA00AA00AAull;  // swaps within 2 x 2, 4 x 4, 8 x 8 blocks
+          mt = mt ^ t ^ (t << 7);
+          t = (mt ^ (mt >> 14)) & 0x0000CCCC0000CCCCull;
+          mt = mt ^ t ^ (t << 14);
+          t = (mt ^ (mt >> 28)) & 0x00000000F0F0F0F0ull;
+          mt = mt ^ t ^ (t << 28);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            pk[4 * g + i] = ((uint32_t)(mt >> (16 * i)) & 0xffu) | (((uint32_t)(mt >> (16 * i + 8)) & 0xffu) << 16);
+        }
+        uint32_t mine = 0;  // lane j: replica j's warp total
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const uint32_t v = __reduce_add_sync(0xffffffffu, pk[i]);
+          if ((lane >> 1) == i) mine = (lane & 1) ? (v >> 16) : (v & 0xffffu);
+        }
+        if (mine) atomicAdd(&ucount[lane], mine);
       }
-      // per-replica totals (at most 255 per thread: ND bonds x at most 46 sites
-      // per thread).  Bit j of cnt[b] is bit b of replica j's count: byte g of
-      // the eight words is an 8 x 8 bit block (row b, column k = replica 8 g + k),
-      // whose transpose holds the counts of replicas 8 g .. 8 g + 7 as bytes.
-      // Two counts share a word for the warp sum (at most 32 x 255 < 2^16 each).
-      uint32_t pk[16];  // pk[i]: replica 2 i in bits 0-15, replica 2 i + 1 in bits 16-31
-#pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        unsigned long long mt = 0;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) mt |= (unsigned long long)((cnt[b] >> (8 * g)) & 0xffu) << (8 * b);
-        unsigned long long t = (mt ^ (mt >> 7)) & 0x00AA00AA00AA00AAull;  // swaps within 2 x 2, 4 x 4, 8 x 8 blocks
-        mt = mt ^ t ^ (t << 7);
-        t = (mt ^ (mt >> 14)) & 0x0000CCCC0000CCCCull;
-        mt = mt ^ t ^ (t << 14);
-        t = (mt ^ (mt >> 28)) & 0x00000000F0F0F0F0ull;
-        mt = mt ^ t ^ (t << 28);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          pk[4 * g + i] = ((uint32_t)(mt >> (16 * i)) & 0xffu) | (((uint32_t)(mt >> (16 * i + 8)) & 0xffu) << 16);
-      }
-      uint32_t mine = 0;  // lane j: replica j's warp total
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const uint32_t v = __reduce_add_sync(0xffffffffu, pk[i]);
-        if ((lane >> 1) == i) mine = (lane & 1) ? (v >> 16) : (v & 0xffffu);
-      }
-      if (mine) atomicAdd(&ucount[lane], mine);
       __syncthreads();
       if (tid < 32) {
         // pairs (kk, kk+1) with kk = e mod 2, e mod 2 + 2, ...; lane tid takes kk = tid
@@ -417,13 +513,17 @@ __device__ __forceinline__ void ea_run(const EaArgs& a, int sample) {
   }
 }
 
-template <int ND, bool PS>
-__global__ void __launch_bounds__(1024) k_ea_resident(EaArgs a) { ea_run<ND, PS>(a, blockIdx.x); }
+// Threads per CTA: the per-slot variant keeps four sites' Philox states live
+// and takes up to 128 registers, so its CTAs have at most 512 threads.
+constexpr int ea_max_threads(bool ps) { return ps ? 512 : 1024; }
 
-// Served jobs of one lattice size, one single-sample job per CTA.
-template <int ND>
-__global__ void __launch_bounds__(1024) k_ea_jobs(const EaArgs* __restrict__ list) {
-  ea_run<ND>(list[blockIdx.x], 0);
+template <int ND, bool PS>
+__global__ void __launch_bounds__(ea_max_threads(PS)) k_ea_resident(EaArgs a) { ea_run<ND, PS>(a, blockIdx.x); }
+
+// Served jobs of one lattice size and random-number mode, one single-sample job per CTA.
+template <int ND, bool PS>
+__global__ void __launch_bounds__(ea_max_threads(PS)) k_ea_jobs(const EaArgs* __restrict__ list) {
+  ea_run<ND, PS>(list[blockIdx.x], 0);
 }
 
 // hot start: the replica bits of site n are its 32-bit hot-start word, bit
@@ -642,15 +742,18 @@ int ea_window_args(spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* 
   EaBatch* b = h->ea;
   *out = b->args;
   out->sweep0 = (uint32_t)h->sweeps;
+  if (out->u_per_slot) *threads = std::min(b->threads, ea_max_threads(true));
   out->nsweeps = (int)nsweeps;
   *smem = b->smem;
-  *threads = b->threads;
+  if (!out->u_per_slot) *threads = b->threads;
   h->sweeps += (uint64_t)nsweeps;
   return SPN_OK;
 }
 
-cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, size_t smem, cudaStream_t st) {
-  auto kern = nd == 2 ? k_ea_jobs<2> : k_ea_jobs<3>;
+cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, bool ps, int threads, size_t smem, cudaStream_t st) {
+  auto kern = ps ? (nd == 2 ? k_ea_jobs<2, true> : k_ea_jobs<3, true>)
+                 : (nd == 2 ? k_ea_jobs<2, false> : k_ea_jobs<3, false>);
+  threads = std::min(threads, ea_max_threads(ps));
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n, threads, smem, st>>>(d_list);
@@ -721,6 +824,9 @@ int ea_prepare(spn::EaPrep& p, int model, const int32_t* dims, int nsamples, con
     b->pairs_share_bonds = std::memcmp(&p.bb[(size_t)(2 * q) * N], &p.bb[(size_t)(2 * q + 1) * N], (size_t)N) == 0;
   // exchange tables: pair k, d = 1 .. len: floor(exp((b_k - b_k+1) * (-2d)) 2^32)
   spn::EaArgs& A = b->args;
+  // with replica exchange every slot draws its own u (the exchange rule needs
+  // independent replicas); without it the slots share one u per site
+  A.u_per_slot = exchange_every > 0 ? 1 : 0;
   A.xalways = 0;
   for (int k = 0; k < 31; ++k) {
     const double db = betas[k] - betas[k + 1];
@@ -863,13 +969,14 @@ int spn_batch_sweep(spn_handle h, int64_t nsweeps) {
   auto kern = b->args.u_per_slot ? (b->nd == 2 ? spn::k_ea_resident<2, true> : spn::k_ea_resident<3, true>)
                                   : (b->nd == 2 ? spn::k_ea_resident<2, false> : spn::k_ea_resident<3, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  const int threads = std::min(b->threads, spn::ea_max_threads(b->args.u_per_slot != 0));
   int64_t done = 0;
   while (done < nsweeps) {  // bounded launches keep each kernel well under a second
     const int n = (int)std::min<int64_t>(nsweeps - done, 2000);
     spn::EaArgs a = b->args;
     a.sweep0 = (uint32_t)(h->sweeps + done);
     a.nsweeps = n;
-    kern<<<b->nsamples, b->threads, b->smem, h->st>>>(a);
+    kern<<<b->nsamples, threads, b->smem, h->st>>>(a);
     spn::count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return ea_fail(SPN_E_CUDA, cudaGetErrorString(e));

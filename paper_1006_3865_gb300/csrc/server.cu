@@ -306,27 +306,33 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
       if ((e = spn::launch_resident(a, L.nd, L.cs, L.threads, ctas, L.smem, st)) != cudaSuccess) return SPN_E_CUDA;
     }
   }
-  // EA jobs: one launch per lattice size, one CTA per job (at most 2000 sweeps a launch)
+  // EA jobs: one launch per lattice size and random-number mode (a u per slot
+  // for jobs with replica exchange), one CTA per job (at most 2000 sweeps a launch)
   {
-    std::map<int64_t, std::vector<size_t>> ea_groups;
+    struct EaLaunch {
+      std::vector<spn::EaArgs> args;
+      int threads = 0;  // the same for every job of a group (same N and mode)
+      size_t smem = 0;
+    };
+    std::map<int64_t, EaLaunch> ea_groups;  // key 2 N + (a u per slot)
     for (size_t k = 0; k < act.size(); ++k)
       if (act[k]->ea) {
         win[k] = std::min<int64_t>(win[k], 2000);
         act[k]->window = win[k];
-        ea_groups[act[k]->N].push_back(k);
+        spn::EaArgs a;
+        size_t smem = 0;
+        int threads = 0;
+        if (spn::ea_window_args(act[k]->ea, win[k], &a, &smem, &threads) != SPN_OK) return SPN_E_STATE;
+        EaLaunch& g = ea_groups[2 * act[k]->N + (a.u_per_slot ? 1 : 0)];
+        g.args.push_back(a);
+        g.threads = threads;
+        g.smem = smem;
       }
     std::vector<spn::EaArgs> args;
-    std::vector<std::tuple<size_t, size_t, int, size_t>> el;  // first, count, threads, smem
+    std::vector<std::tuple<size_t, size_t, int, size_t, bool>> el;  // first, count, threads, smem, per-slot
     for (auto& kv : ea_groups) {
-      const size_t first = args.size();
-      int threads = 0;
-      size_t smem = 0;
-      for (size_t k : kv.second) {
-        spn::EaArgs a;
-        if (spn::ea_window_args(act[k]->ea, win[k], &a, &smem, &threads) != SPN_OK) return SPN_E_STATE;
-        args.push_back(a);
-      }
-      el.emplace_back(first, kv.second.size(), threads, smem);
+      el.emplace_back(args.size(), kv.second.args.size(), kv.second.threads, kv.second.smem, (kv.first & 1) != 0);
+      args.insert(args.end(), kv.second.args.begin(), kv.second.args.end());
     }
     if (!args.empty()) {
       if (args.size() > s->ea_cap) {
@@ -341,10 +347,11 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
       for (size_t gi = 0; gi < el.size(); ++gi) {
         size_t first, count, smem;
         int threads;
-        std::tie(first, count, threads, smem) = el[gi];
+        bool ps;
+        std::tie(first, count, threads, smem, ps) = el[gi];
         cudaStream_t st = s->pool[(s->pool.size() - 1 - gi % s->pool.size())];
         cudaStreamWaitEvent(st, s->fork, 0);
-        if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, 3, threads, smem, st)) != cudaSuccess)
+        if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, 3, ps, threads, smem, st)) != cudaSuccess)
           return SPN_E_CUDA;
       }
     }

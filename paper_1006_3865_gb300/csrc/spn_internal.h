@@ -146,7 +146,7 @@ struct EaArgs {
 // parameter block of the next `nsweeps` sweeps of h (its sweep counter
 // advances), and one launch running many such blocks, one CTA each.
 int ea_window_args(struct spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* threads);
-cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, bool ps, int threads, size_t smem, cudaStream_t st);
 // Server admissions of single-sample EA batches in two parts: the host part
 // (validation, bond bytes, exchange tables; no CUDA call, any thread) and the
 // device part, whose allocations, copies and hot start are ordered on st and

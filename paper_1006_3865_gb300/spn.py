@@ -395,8 +395,9 @@ class EABatch:
     """Multi-spin coded +-J EA samples with replica exchange (spn_create_batch)."""
 
     def __init__(self, dims, couplings: np.ndarray, betas, seed: int, exchange_every: int = 10,
-                 u_per_slot: bool = False):
-        """u_per_slot: every temperature slot draws its own u (spn_batch_set_u_per_slot)."""
+                 u_per_slot: bool | None = None):
+        """u_per_slot: every temperature slot draws its own u (spn_batch_set_u_per_slot).  None keeps the
+        library's default: a u per slot with replica exchange (exchange_every > 0), a shared u without."""
         self._lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.N = int(np.prod(self.dims))
@@ -409,8 +410,8 @@ class EABatch:
         _check(self._lib.spn_create_batch(_c.byref(h), model, _ptr(d), self.nsamples, _ptr(J), _ptr(b),
                                           int(b.size), seed, int(exchange_every)))
         self._h = h
-        if u_per_slot:
-            _check(self._lib.spn_batch_set_u_per_slot(self._h, 1))
+        if u_per_slot is not None:
+            _check(self._lib.spn_batch_set_u_per_slot(self._h, 1 if u_per_slot else 0))
 
     def sweep(self, nsweeps: int):
         _check(self._lib.spn_batch_sweep(self._h, int(nsweeps)))

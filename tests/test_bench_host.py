@@ -4,8 +4,10 @@ is taken from the committed ncu summary only while the kernel source and the
 
 from __future__ import annotations
 
+import hashlib
 import importlib.util
 import os
+import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -19,14 +21,24 @@ def _bench():
 
 def test_traffic_only_for_the_profiled_source_and_tiling(tmp_path):
     b = _bench()
-    t = b._profile_traffic((1, 0, 0))
-    assert t is not None and 4e8 < t < 7e8  # bytes per 2D L = 16384 launch
-    assert b._profile_traffic((1, 1, 0)) is None  # another tiling
-    # a kernel source other than the one profiled
     src = tmp_path / "stream.cu"
-    src.write_bytes(open(b.KERNEL_SRC, "rb").read() + b"\n")
-    b.KERNEL_SRC = str(src)
+    src.write_bytes(b"// kernel source as profiled\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "prof.md"
+    prof.write_text(f"source_sha256: {sha}\ntraffic_bytes_per_launch: 5.251e8\ntiling: 1,0,0\n")
+    b.KERNEL_SRC, b.PROFILE_2D = str(src), str(prof)
+    assert b._profile_traffic((1, 0, 0)) == 5.251e8  # bytes per 2D L = 16384 launch
+    assert b._profile_traffic((1, 1, 0)) is None  # another tiling
+    src.write_bytes(b"// kernel source as profiled\n\n")  # a kernel source other than the one profiled
     assert b._profile_traffic((1, 0, 0)) is None
+
+
+def test_committed_profile_names_a_source_and_tiling():
+    b = _bench()
+    text = open(b.PROFILE_2D).read()
+    assert re.search(r"source_sha256:\s*[0-9a-f]{64}", text)
+    assert re.search(r"traffic_bytes_per_launch:\s*[0-9.eE+]+", text)
+    assert re.search(r"tiling:\s*\d+,\d+,\d+", text)
 
 
 def test_attempts_per_step_matches_the_workload():

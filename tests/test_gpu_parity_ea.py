@@ -19,7 +19,7 @@ def _lib():
     lib()
 
 
-def _oracle_batch(dims, bonds, betas, seed, nsweeps, X, samples, words0=None, slots0=None, u_per_slot=False):
+def _oracle_batch(dims, bonds, betas, seed, nsweeps, X, samples, words0=None, slots0=None, u_per_slot=None):
     out_w, out_pi, out_acc = [], [], []
     for i in samples:
         w = (oracle.ea_init_hot(dims, 1, seed, stream0=i) if words0 is None else words0[i:i + 1].copy())
@@ -54,12 +54,14 @@ def test_batch_matches_oracle(dims, ns, X, sweeps):
     b.close()
 
 
+@pytest.mark.parametrize("u_per_slot", [False, None])
 @pytest.mark.parametrize("dims,ladder", [((8, 8, 8), "equal"), ((16, 8, 4), "pairs"), ((8, 6, 4), "cold")])
-def test_tied_and_crowded_thresholds(dims, ladder):
+def test_tied_and_crowded_thresholds(dims, ladder, u_per_slot):
     """Ladders whose thresholds share buckets of u (equal betas, pairs of equal
-    betas, very low temperatures where many thresholds are near 0): the exact
-    count of thresholds below u then comes from the binary search, on both the
-    four-word groups (Lx a multiple of 8) and the per-site loop."""
+    betas, very low temperatures where many thresholds are near 0): with a shared
+    u the exact count of thresholds below u then comes from the binary search,
+    on both the four-word groups (Lx a multiple of 8) and the per-site loop;
+    with the default u per slot, equal thresholds give equal threshold planes."""
     if ladder == "equal":
         betas = np.full(32, 0.35)
     elif ladder == "pairs":
@@ -68,28 +70,33 @@ def test_tied_and_crowded_thresholds(dims, ladder):
         betas = inputs.geometric_ladder(0.05, 0.5)
     ns, X, sweeps, seed = 2, 5, 30, inputs.unit_seed(310)
     bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(311))
-    b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X)
+    b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X, u_per_slot=u_per_slot)
     b.sweep(sweeps)
-    w, pi, acc = _oracle_batch(dims, bonds, betas, seed, sweeps, X, range(ns))
+    w, pi, acc = _oracle_batch(dims, bonds, betas, seed, sweeps, X, range(ns), u_per_slot=u_per_slot)
     assert np.array_equal(b.words(), w)
     assert np.array_equal(b.slots(), pi)
     assert np.array_equal(b.exchange_counts(), acc)
     b.close()
 
 
-@pytest.mark.parametrize("dims,ns,X,sweeps", [((8, 8, 8), 3, 5, 30), ((6, 4, 2), 2, 3, 20), ((16, 8), 2, 10, 40),
-                                             ((4, 4), 2, 5, 30), ((24, 24, 24), 1, 10, 10)])
-def test_u_per_slot_matches_oracle(dims, ns, X, sweeps):
+@pytest.mark.parametrize("dims,ns,X,sweeps,ps", [((8, 8, 8), 3, 5, 30, True), ((6, 4, 2), 2, 3, 20, True),
+                                                ((16, 8), 2, 10, 40, True), ((4, 4), 2, 5, 30, True),
+                                                ((24, 24, 24), 1, 10, 10, True), ((32, 32, 32), 1, 10, 20, True),
+                                                ((40, 32, 34), 1, 5, 10, True), ((8, 8, 8), 2, 0, 20, True),
+                                                ((16, 8, 8), 2, 5, 20, False),
+                                                ((16, 8), 2, 5, 20, False)])
+def test_u_per_slot_matches_oracle(dims, ns, X, sweeps, ps):
     """Every temperature slot with its own u (32 bit planes per site), on the
     four-word groups (Lx a multiple of 8) and the per-site loop, 2D and 3D, with
+    and without exchange; and the shared u chosen explicitly for a run with
     exchange: words, slot maps and exchange counts equal the oracle's."""
     seed = inputs.unit_seed(320 + ns)
     bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(321))
     betas = inputs.geometric_ladder(0.2, 2.0)
-    b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X, u_per_slot=True)
+    b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X, u_per_slot=ps)
     b.sweep(sweeps // 2)
     b.sweep(sweeps - sweeps // 2)
-    w, pi, acc = _oracle_batch(dims, bonds, betas, seed, sweeps, X, range(ns), u_per_slot=True)
+    w, pi, acc = _oracle_batch(dims, bonds, betas, seed, sweeps, X, range(ns), u_per_slot=ps)
     assert np.array_equal(b.words(), w)
     assert np.array_equal(b.slots(), pi)
     assert np.array_equal(b.exchange_counts(), acc)
@@ -125,7 +132,8 @@ def test_equal_betas_always_exchange():
 
 def test_full_batch_sample_subset():
     """The 1024-sample L = 32 batch (64 replicas per uint64 word), 20 sweeps with
-    exchange every 10; four samples compared with the oracle."""
+    exchange every 10 on the default chain (a u per slot); four samples compared
+    with the oracle."""
     dims, ns, seed = (32, 32, 32), 1024, inputs.unit_seed(3)
     bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(4))
     betas = inputs.geometric_ladder(0.2, 2.0)

@@ -95,8 +95,11 @@ def test_late_arrivals_join_running_batch():
     srv.close()
 
 
-def test_ea_job_matches_batch():
-    dims, X, ns = (8, 8, 8), 10, 65
+@pytest.mark.parametrize("X", [10, 0])
+def test_ea_job_matches_batch_and_oracle(X):
+    """A served EA job with exchange (default: a u per slot) and one without
+    (shared u) against a batch handle and the oracle, bit for bit."""
+    dims, ns = (8, 8, 8), 65
     bonds = inputs.ea_bonds(dims, 1, inputs.unit_seed(41))
     betas = inputs.geometric_ladder(0.2, 2.0)
     seed = inputs.unit_seed(42)
@@ -105,6 +108,11 @@ def test_ea_job_matches_batch():
     t2 = _submit_ising(srv, 1, *_MIX[1])
     _wait(srv, [t, t2])
     words, slots = srv.fetch(t)
+    w = oracle.ea_init_hot(dims, 1, seed)
+    pi = np.arange(32, dtype=np.uint8)[None, :].copy()
+    tau = pi.copy()
+    oracle.ea_sweeps(dims, w, bonds, betas, pi, tau, ns, seed, exchange_every=X)
+    assert np.array_equal(words, w[0]) and np.array_equal(slots, pi[0])
     b = spn.EABatch(dims, bonds, betas, seed, exchange_every=X)
     b.sweep(ns)
     assert np.array_equal(words, b.words()[0]) and np.array_equal(slots, b.slots()[0])

@@ -509,14 +509,15 @@ def test_exchange_acceptance_follows_the_replica_exchange_rule():
     """Every attempted pair with D = (beta_k - beta_k+1)(E_k - E_k+1) >= 0 swaps,
     and pairs with D < 0 swap with total frequency sum(exp(D)) within 5 sigma.
     The energies before each exchange come from an identical run without
-    exchange (the dynamics is a deterministic function of the counters)."""
+    exchange (the dynamics is a deterministic function of the counters; both
+    runs draw a u per slot, the default of runs with exchange)."""
     dims, ns, seed, X = (4, 4, 4), 8, 97531, 10
     betas = inputs.geometric_ladder(0.6, 3.0)
     bonds, words, pi, tau = _ea_setup(dims, ns, seed)
     must, expect, var, got = 0, 0.0, 0.0, 0
     for e in range(30):
         w2, pi2, tau2 = words.copy(), pi.copy(), tau.copy()
-        oracle.ea_sweeps(dims, w2, bonds, betas, pi2, tau2, X, seed, sweep0=X * e, exchange_every=0)
+        oracle.ea_sweeps(dims, w2, bonds, betas, pi2, tau2, X, seed, sweep0=X * e, exchange_every=0, u_per_slot=True)
         Eslot, _ = oracle.ea_observables(dims, w2, bonds)
         before = tau.copy()
         oracle.ea_sweeps(dims, words, bonds, betas, pi, tau, X, seed, sweep0=X * e, exchange_every=X)
