@@ -50,11 +50,11 @@ L3D, SWEEPS_3D, BETA_3D = 512, 100, 0.221654
 ATTEMPTS_PER_STEP = len(TEMPS_2D) * SWEEPS_2D * L2D * L2D + SWEEPS_3D * L3D ** 3
 WORKLOAD = ("2D Ising L=16384 (hot start, T in {2.0, 2.269185, 3.0}, 200 sweeps each) + "
             "3D Ising L=512 (hot start, beta=0.221654, 100 sweeps)")
-PROFILE_2D = os.path.join(ROOT, "profiles", "sweep_stream_2d_L16384.md")
+PROFILE_2D = os.path.join(ROOT, "profiles", "sweep_wave_2d_L16384.md")
 EA_L, EA_SAMPLES, EA_SWEEPS, EA_EVERY = 32, 1024, 10000, 10
 SERVED_REQUESTS = 2000  # the whole request stream
 LOOP_SUBSET = 256  # instances of the uneven batch timed through the per-instance launch loop
-KERNEL_SRC = os.path.join(ROOT, "paper_1006_3865_gb300", "csrc", "stream.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1006_3865_gb300", "csrc", "wave.cu")
 
 
 def _args():
@@ -885,7 +885,7 @@ def main():
                    "tiling_2d": tiling2, "tiling_3d": tiling3, "tuning_launches": tuning_launches,
                    "launches_before_tuning": nt0},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_sweep_stream<2> (2D L=16384)", "peak_kind": peak_kind,
+                     "traffic": traffic, "kernel": "k_sweep_wave (2D L=16384)", "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes},
         "clocks": clocks,
         "gpu_launches": launches,

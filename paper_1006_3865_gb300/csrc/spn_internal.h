@@ -34,6 +34,7 @@ enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2, kPathPac
 // the lattice is stored as bit words (rows of packed_row_words(Lx) words).
 struct StreamGeom {
   int packed;
+  int wave;  // 2D int8 rows of at least 2048 sites: the band-parallel kernel (wave.cu); nseg its row segments
   int TY, R, nseg, threads, nraw, nbit;
   int roundsC, roundsA, roundsB, qcap;  // words per thread per phase; tie-queue entries per warp
   size_t smem;
@@ -68,6 +69,15 @@ bool dc_supported(const Lattice& g, int Tx, int Ty, int Tz);
 cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz, int hits, const DevThr& T,
                             const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                             cudaStream_t st);
+// Band-parallel sweep (wave.cu): 2D int8 lattices whose Lx is a multiple of 64
+// and at least 2048, dense rows, no bonds; a warp per (band of 30 words, segment
+// of rows), nseg segments.
+bool wave_supported(const Lattice& g);
+int wave_default_segments(const Lattice& g);
+size_t wave_smem_bytes(const Lattice& g);
+cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, int nseg, const DevThr& T,
+                              const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
+                              int* err, cudaStream_t st, uint32_t expire_polls);
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed = false);
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
 // expire_polls (test support, 0 otherwise): the copy of each CTA's first slice

@@ -454,6 +454,15 @@ void phase_counts(const Lattice& g, int TY, int R, bool packed, int& nC, int& nA
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed) {
   StreamGeom s{};
   s.packed = packed ? 1 : 0;
+  if (!packed && R <= 1 && wave_supported(g)) {  // one row per step: the wavefront kernel
+    s.wave = 1;
+    s.TY = 1;
+    s.R = 1;
+    s.threads = 256;
+    s.nseg = nseg > 0 ? std::min(nseg, g.Ly) : wave_default_segments(g);
+    s.smem = wave_smem_bytes(g);
+    return s;
+  }
   s.TY = g.nd == 3 ? TY : 1;
   const int S = g.nd == 3 ? g.Lz : g.Ly;
   const int maxT = max_threads(g.nd);
@@ -503,6 +512,7 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packe
 
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
   const bool packed = geo.packed != 0;
+  if (geo.wave) return !packed && wave_supported(g) && geo.nseg >= 1 && geo.nseg <= g.Ly;
   if (geo.R < 1 || geo.R > 127 || geo.threads < 32 || geo.threads > max_threads(g.nd) || geo.threads % 32) return false;
   int nC, nA, nB;
   phase_counts(g, geo.TY, geo.R, packed, nC, nA, nB);
@@ -518,6 +528,9 @@ cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, con
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st, uint32_t expire_polls) {
   if (!stream_geometry_ok(g, geo)) return cudaErrorInvalidConfiguration;
+  if (geo.wave)
+    return launch_sweep_wave(g, static_cast<const int8_t*>(in), static_cast<int8_t*>(out), geo.nseg, T, K, stream_id,
+                             sweep, acc, err, st, expire_polls);
   if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return cudaErrorMisalignedAddress;  // bulk copies, 16-B stores
   StreamArgs a;
   a.in = in;

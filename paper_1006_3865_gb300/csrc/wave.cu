@@ -1,0 +1,341 @@
+// Band-parallel streaming sweep of a large 2D Ising lattice (J = 1): one launch
+// is one full sweep in the canonical two-colour order of Sec. 3 (all of colour
+// 0, then all of colour 1), each int8 spin read from HBM once and written once.
+//
+// The lattice is cut into bands of 30 consecutive 64-site words across x and
+// segments of rows along y; a warp owns one (band, segment) and walks down its
+// rows on its own, with no synchronisation with any other warp:
+//
+//   * lane i holds word j0 - 1 + i of every row (j0 the band's first word): the
+//     30 owned words plus one halo word on each side, brought in as int8 by bulk
+//     asynchronous copies (TMA engine) into a private ring of shared-memory
+//     slots, completed on the slot's mbarrier;
+//   * each lane turns its 64 sites into colour-separated bit words (E: even x,
+//     O: odd x, 32 sites per word) in a private ring of four bit rows;
+//   * step k converts row k+3, updates colour 0 of row k+2 and colour 1 of row
+//     k+1, so that colour 1 of a row sees the final colour-0 spins of its row and
+//     of the rows above and below (the tile plus halo of Sec. 3, from shared
+//     memory);
+//   * colour 0 is updated on all 32 lanes: it reads only colour-1 spins from
+//     before the sweep, so the halo lanes compute exactly the new colour-0 spins
+//     next to the band that its owned sites need; colour 1 is kept and written
+//     on the owned lanes only (a halo lane's colour-1 spins stay those from
+//     before the sweep, which its later colour-0 updates need);
+//   * a site's move is decided from its 4 neighbours by bit-sliced adders and the
+//     uint32 compare u < floor(exp(-beta dE) 2^32) of Eq. 2, with u drawn from
+//     Philox4x32-10 bit planes keyed by the site (top 12 planes for every site,
+//     further planes for a warp with a tie), so a word computed by two warps
+//     gets the same result in both;
+//   * each owned row goes back to HBM as int8 (through a 256-entry table) once
+//     both of its colours are final.
+//
+// Rows next to a segment boundary are loaded (and their colour 0 updated) by both
+// neighbouring segments' warps for the same reason.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "philox.cuh"
+#include "spn_internal.h"
+#include "sweep_common.cuh"
+
+namespace spn {
+namespace {
+
+constexpr int kOwned = 30;      // words of a band (plus one halo word on each side = 32 lanes)
+constexpr int kWarps = 8;       // warps per CTA, each an independent (band, segment)
+constexpr int kRing = 3;        // raw band slots per warp
+constexpr int kMinBlocks = 3;   // CTAs per SM the register budget aims at
+constexpr int kBitRows = 4;     // bit rows k .. k+3 live at step k
+constexpr int kBandBytes = 32 * 64;
+constexpr int kFirst = 3;       // Philox calls of the first decision stage (12 planes)
+
+struct WaveArgs {
+  const int8_t* in;
+  int8_t* out;
+  int Ly, W;       // rows; 64-site words per row (at least 32)
+  int nbands, nseg;
+  uint32_t sweep, stream_id;
+  uint32_t always;     // bit q + 1: class q (dE = 4 (q + 1)) is always accepted
+  PhiloxKeys K;
+  uint32_t tm[2][32];  // 0 / ~0: bit 31 - p of the threshold of class q, plane p
+  unsigned long long* acc;
+  int* err;
+  uint32_t wait_limit;  // polls of a bounded wait before it gives up
+  uint32_t skip_first;  // test support: row 0's copies are never issued
+};
+
+constexpr size_t kWaveSmem = (size_t)kWarps * kRing * kBandBytes  // raw slots
+                             + (size_t)kWarps * kBitRows * 64 * 4  // bit rows
+                             + 256 * 8                             // int8 output table
+                             + (size_t)kWarps * kRing * 8;         // mbarriers
+
+template <int FC>  // Philox calls (4 planes each) of the first decision stage
+__global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __grid_constant__ WaveArgs a) {
+  constexpr int NC = 2;  // classes with dE > 0: dE = 4, 8
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int W = a.W, Ly = a.Ly;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint8_t* raw = smem + (size_t)warp * kRing * kBandBytes;  // this warp's slots
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)kWarps * kRing * kBandBytes) + warp * kBitRows * 64;
+  uint2* lut = reinterpret_cast<uint2*>(smem + (size_t)kWarps * kRing * kBandBytes + (size_t)kWarps * kBitRows * 256);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256) + warp * kRing;
+  const uint4* raw16 = reinterpret_cast<const uint4*>(raw);
+
+  // int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
+  for (int i = tid; i < 256; i += blockDim.x) {
+    uint32_t lo = 0, hi = 0;
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t pair = (((i >> k) & 1) ? 0xffu : 0x01u) | ((((i >> (4 + k)) & 1) ? 0xffu : 0x01u) << 8);
+      if (k < 2) lo |= pair << (16 * k); else hi |= pair << (16 * (k - 2));
+    }
+    lut[i] = make_uint2(lo, hi);
+  }
+  if (lane == 0) {
+    for (int b = 0; b < kRing; ++b) mbar_init(&bars[b], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();  // the table and the barriers; warps are independent from here on
+
+  const int unit = blockIdx.x * kWarps + warp;
+  if (unit >= a.nbands * a.nseg) return;
+  const int band = unit % a.nbands, seg = unit / a.nbands;
+  const int zs = (int)(((int64_t)seg * Ly) / a.nseg);
+  const int ze = (int)(((int64_t)(seg + 1) * Ly) / a.nseg);
+  const int H = ze - zs;
+  const int nload = H + 4;  // local rows li = 0 .. H + 3 <-> global zs - 2 + li
+  const int j0 = kOwned * band;
+  int jw = j0 - 1 + lane;  // this lane's word (W >= 32: at most one wrap)
+  jw = jw < 0 ? jw + W : (jw >= W ? jw - W : jw);
+  const bool owned = lane >= 1 && lane <= kOwned && j0 + lane - 1 < W;
+  // the band's 32 words in memory: words j0 - 1 .. W - 1 (at most 32), then from word 0
+  const int first = j0 == 0 ? W - 1 : j0 - 1;
+  const int run1 = min(32, W - first);
+
+  auto grow = [&](int li) {  // global row of local row li
+    int r = zs - 2 + li;
+    r = r < 0 ? r + Ly : r;
+    return r >= Ly ? r - Ly : r;
+  };
+  // request local row li into slot li % kRing (lane 0; the slot's previous
+  // contents were read by the whole warp before this call)
+  auto issue = [&](int li) {
+    if (lane == 0 && li < nload) {
+      uint64_t* bar = &bars[li % kRing];
+      uint8_t* dst = raw + (size_t)(li % kRing) * kBandBytes;
+      const int8_t* src = a.in + (int64_t)grow(li) * (64 * W);
+      fence_proxy_async();  // earlier generic reads of the slot before the async writes
+      mbar_arrive_expect_tx(bar, (uint32_t)kBandBytes);
+      if (!(a.skip_first && li == 0)) {
+        bulk_g2s(dst, src + 64 * first, (uint32_t)(64 * run1), bar);
+        if (run1 < 32) bulk_g2s(dst + 64 * run1, src, (uint32_t)(64 * (32 - run1)), bar);
+      }
+    }
+  };
+  int issued = 0;
+  for (; issued < kRing && issued < nload; ++issued) issue(issued);
+
+  // chunk order of the 64-byte span rotated by lane pair: a quarter warp reads 8
+  // distinct 4-bank groups; rot_sel undoes the rotation on the gathered bytes
+  const int rot = (lane >> 1) & 3;
+  const uint32_t rot_sel = (uint32_t)(((0 - rot) & 3) | (((1 - rot) & 3) << 4) | (((2 - rot) & 3) << 8) |
+                                      (((3 - rot) & 3) << 12));
+  auto row_bits = [&](int li) { return bits + (li & (kBitRows - 1)) * 64; };  // E words 0..31, O words 32..63
+
+  // wait (bounded) for local row li and turn this lane's 64 sites into bit words
+  auto convert = [&](int li) -> bool {
+    unsigned n = 0;
+    while (!mbar_try_wait(&bars[li % kRing], (uint32_t)((li / kRing) & 1))) {
+      if (++n > a.wait_limit) return false;
+    }
+    const uint32_t span = (uint32_t)(li % kRing) * (kBandBytes >> 4) + 4u * (uint32_t)lane;
+    uint32_t pe[4], po[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const uint4 c = raw16[span + (uint32_t)((v + rot) & 3)];
+      pe[v] = gather_e(c.x, c.y, c.z, c.w);
+      po[v] = gather_o(c.x, c.y, c.z, c.w);
+    }
+    uint32_t* row = row_bits(li);
+    row[lane] = __byte_perm(top_bytes(pe[0], pe[1], pe[2], pe[3]), 0u, rot_sel);
+    row[32 + lane] = __byte_perm(top_bytes(po[0], po[1], po[2], po[3]), 0u, rot_sel);
+    return true;
+  };
+
+  int de = 0, dm = 0;
+  // colour c of local row li (global gr): the lane's colour-c word is recomputed
+  // from the other colour's words of its row and the rows above and below;
+  // colour 1 also sends the finished row out as int8
+  auto update = [&](int li, int c) {
+    const int gr = grow(li);
+    const int par = (gr + c) & 1;  // 0: the E word holds colour c, 1: the O word (warp-uniform)
+    const uint32_t* rm = row_bits(li - 1);
+    uint32_t* r0 = row_bits(li);
+    const uint32_t* rp = row_bits(li + 1);
+    const int ws = par ? 32 + lane : lane;
+    const uint32_t b = r0[ws], oj = r0[par ? lane : 32 + lane];
+    // x - 1 of an even site 0 is the last odd site of the previous lane's word;
+    // x + 1 of the odd site 31 is the first even site of the next lane's word
+    // (lanes 0 and 31 get their own word there: the bit it feeds is never used)
+    const uint32_t on = par ? __shfl_down_sync(0xffffffffu, oj, 1) : __shfl_up_sync(0xffffffffu, oj, 1);
+    const uint32_t left = par ? oj : (oj << 1) | (on >> 31);
+    const uint32_t right = par ? (oj >> 1) | (on << 31) : oj;
+    const uint32_t zm = rm[ws], zp = rp[ws];
+    uint32_t s0, s1, s2, cls[NC];
+    count4(b ^ left, b ^ right, b ^ zm, b ^ zp, s0, s1, s2);
+    uint32_t acc = classes<2>(s0, s1, s2, 0xffffffffu, cls);
+    uint32_t eq[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const bool always = (a.always >> (k + 1)) & 1u;
+      acc |= always ? cls[k] : 0u;
+      eq[k] = always ? 0u : cls[k];
+    }
+    const uint32_t c0 = 8u * ((uint32_t)jw + (uint32_t)W * (uint32_t)gr);
+    const uint32_t c2 = (uint32_t)c | (kMetropolis << 1);
+    uint32_t pl[4 * FC];
+#pragma unroll
+    for (int call = 0; call < FC; ++call) {
+      const U4 P = philox10(c0 + (uint32_t)call, a.sweep, c2, a.stream_id, a.K);
+      pl[4 * call + 0] = P.x;
+      pl[4 * call + 1] = P.y;
+      pl[4 * call + 2] = P.z;
+      pl[4 * call + 3] = P.w;
+    }
+    compare_top<NC, 4 * FC>(acc, eq, pl, a.tm);
+    if (__any_sync(0xffffffffu, (eq[0] | eq[1]) != 0u))
+      acc |= rest_planes<NC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id, FC);
+    const uint32_t nb = b ^ acc;
+    if (c == 0 || owned) r0[ws] = nb;
+    if (owned && li >= 2 && li < H + 2) tally<2>(acc, b, s0, s1, s2, de, dm);
+    if (c == 1 && owned) {
+      const uint32_t E = par ? oj : nb, O = par ? nb : oj;
+      const uint32_t X = (E & 0x0f0f0f0fu) | ((O << 4) & 0xf0f0f0f0u);  // byte v: sites 16v .. 16v + 7
+      const uint32_t Y = ((E >> 4) & 0x0f0f0f0fu) | (O & 0xf0f0f0f0u);  // byte v: sites 16v + 8 .. 16v + 15
+      uint4* dst = reinterpret_cast<uint4*>(a.out + (int64_t)gr * (64 * W) + 64 * jw);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint2 lo = lut[(X >> (8 * v)) & 0xffu];
+        const uint2 hi = lut[(Y >> (8 * v)) & 0xffu];
+        dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
+      }
+    }
+  };
+
+  // prologue: rows 0, 1, 2 converted, colour 0 of row 1
+  bool ok = true;
+  for (int li = 0; li < 3 && ok; ++li) {
+    ok = __all_sync(0xffffffffu, convert(li));
+    __syncwarp();
+    if (ok) issue(issued++);
+  }
+  if (ok) update(1, 0);
+  // step k: convert row k + 3, colour 0 of row k + 2, colour 1 of row k + 1
+  // (owned rows 2 .. H + 1 only: row 1 is the halo above the segment)
+  for (int k = 0; ok && k <= H; ++k) {
+    ok = __all_sync(0xffffffffu, convert(k + 3));
+    if (!ok) break;
+    __syncwarp();
+    issue(issued++);
+    update(k + 2, 0);
+    if (k >= 1) update(k + 1, 1);
+  }
+  if (!ok) {  // this warp gives up
+    if (lane == 0) {
+      atomicExch(a.err, 1);
+      // let the copies still in flight land before the warp exits: every issued
+      // row gets the full poll bound, and a row whose copy was never issued is skipped
+      const int last = issued < nload ? issued : nload;  // rows actually requested
+      for (int li = last > kRing ? last - kRing : 0; li < last; ++li) {
+        if (a.skip_first && li == 0) continue;
+        unsigned n = 0;
+        while (!mbar_try_wait(&bars[li % kRing], (uint32_t)((li / kRing) & 1)) && ++n < kWaitLimit) {
+        }
+      }
+    }
+    __syncwarp();
+    return;
+  }
+  block_accumulate(de, dm, a.acc);
+}
+
+int nbands_of(const Lattice& g) { return (g.Lx / 64 + kOwned - 1) / kOwned; }
+
+}  // namespace
+
+bool wave_supported(const Lattice& g) {
+  if (g.nd != 2 || g.bonds) return false;
+  if (g.pitch && g.pitch != g.Lx) return false;
+  if (g.Lx % 64 || g.Lx < 2048 || g.Lx > (1 << 24)) return false;
+  return g.Ly >= 2;
+}
+
+size_t wave_smem_bytes(const Lattice&) { return kWaveSmem; }
+
+int wave_default_segments(const Lattice& g) {
+  static std::mutex mu;
+  static int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!per_sm) {
+      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWaveSmem);
+      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      int blocks = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave<kFirst>, 32 * kWarps, kWaveSmem) !=
+          cudaSuccess)
+        blocks = 1;
+      per_sm = std::max(1, blocks);
+    }
+  }
+  // one resident warp per (band, segment)
+  const int64_t units = (int64_t)device_sm_count() * per_sm * kWarps;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g.Ly, units / nbands_of(g)));
+}
+
+cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, int nseg, const DevThr& T,
+                              const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
+                              int* err, cudaStream_t st, uint32_t expire_polls) {
+  if (!wave_supported(g) || nseg < 1 || nseg > g.Ly) return cudaErrorInvalidConfiguration;
+  if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return cudaErrorMisalignedAddress;  // bulk copies, 16-B stores
+  WaveArgs a;
+  a.in = in;
+  a.out = out;
+  a.Ly = g.Ly;
+  a.W = g.Lx / 64;
+  a.nbands = nbands_of(g);
+  a.nseg = nseg;
+  a.sweep = sweep;
+  a.stream_id = stream_id;
+  a.always = T.always;
+  a.K = K;
+  for (int k = 0; k < 2; ++k)
+    for (int p = 0; p < 32; ++p) a.tm[k][p] = ((T.t[k + 1] >> (31 - p)) & 1u) ? 0xffffffffu : 0u;
+  a.acc = acc;
+  a.err = err;
+  a.wait_limit = kWaitLimit;
+  a.skip_first = 0;
+  if (expire_polls) {  // row 0 of every warp is never copied; waits give up after `expire_polls` polls
+    a.skip_first = 1;
+    a.wait_limit = expire_polls;
+  }
+  {
+    static std::mutex mu;
+    static bool set[128] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!set[dev & 127]) {
+      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWaveSmem);
+      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      set[dev & 127] = true;
+    }
+  }
+  const int64_t units = (int64_t)a.nbands * nseg;
+  k_sweep_wave<kFirst><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWaveSmem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace spn

@@ -1,6 +1,7 @@
-"""Failure detection without a device fault: a streaming launch (int8 or
-bit-packed) whose first slice is never copied gives up its bounded wait, records the failure and
-returns; the host reports SPN_E_TIMEOUT, and the context keeps working."""
+"""Failure detection without a device fault: a streaming launch (int8, bit-packed
+or the 2D wavefront kernel) whose first slice is never copied gives up its
+bounded wait, records the failure and returns; the host reports SPN_E_TIMEOUT,
+and the context keeps working."""
 
 from __future__ import annotations
 
@@ -19,7 +20,8 @@ def _lib():
 
 
 @pytest.mark.parametrize("path", [spn.PATH_STREAM, spn.PATH_PACKED])
-@pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (256, 256)), (spn.SPN_ISING3D, (64, 16, 12))])
+@pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (256, 256)), (spn.SPN_ISING3D, (64, 16, 12)),
+                                        (spn.SPN_ISING2D, (4096, 32))])
 def test_bounded_wait_runs_out_and_reports_timeout(model, dims, path):
     lat = spn.Lattice(model, dims, 5)
     lat.path = path

@@ -61,6 +61,20 @@ def test_ising2d_stream_padded_rows(dims, tiling):
              tiling=tiling, stream=4)
 
 
+@pytest.mark.parametrize("dims,tiling", [((2048, 64), None), ((4096, 30), (0, 1, 7)), ((6144, 10), (0, 1, 10)),
+                                         ((16384, 12), (0, 1, 1)), ((2048, 2), None), ((2048, 4), (0, 1, 3)),
+                                         ((8192, 40), (0, 0, 13)), ((4096, 6), (0, 1, 6)), ((2112, 20), None),
+                                         ((3008, 8), (0, 1, 3)), ((1920 * 4, 10), (0, 1, 2))])
+def test_ising2d_band_parallel(dims, tiling):
+    """Rows of at least 2048 sites in whole 64-site words take the band-parallel
+    kernel (a warp per band of 30 words and segment of rows, with a recomputed
+    halo word on each side): bands that wrap around the row end, a last band of
+    one to 29 words, segments down to one row, two-row lattices, ragged
+    segment splits."""
+    _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(17), [(1.0 / TC, 7), (0.3, 2)], path=spn.PATH_STREAM,
+             tiling=tiling, stream=6)
+
+
 @pytest.mark.parametrize("dims,tiling", [((70, 16, 12), (4, 1, 3)), ((6, 8, 10), (8, 2, 0)), ((202, 4, 6), None)])
 def test_ising3d_stream_padded_rows(dims, tiling):
     _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(14), [(inputs.BETA_C_3D, 6)], path=spn.PATH_STREAM,
@@ -112,6 +126,7 @@ def test_ea3d_int8(dims):
 
 
 @pytest.mark.parametrize("model,dims,path", [(spn.SPN_ISING2D, (64, 32), spn.PATH_STREAM),
+                                             (spn.SPN_ISING2D, (2048, 16), spn.PATH_STREAM),
                                              (spn.SPN_ISING2D, (10, 6), spn.PATH_GENERIC),
                                              (spn.SPN_ISING3D, (64, 8, 6), spn.PATH_STREAM)])
 def test_beta_zero_and_infinity(model, dims, path):
