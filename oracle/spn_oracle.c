@@ -525,6 +525,97 @@ int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const ui
                           nsweeps, exchange_every, acc, 0);
 }
 
+/* ------------------------------------- disorder-parallel multi-spin coding */
+
+/* Sec. 4 runs many disorder realisations at once with asynchronous multi-spin
+ * coding: the bits of a machine word are different samples, updated with one
+ * random number.  Here 32 samples form a group and share the site's u at each
+ * temperature; a sample's 32 temperatures draw independent u (other groups of
+ * the Philox stream), so replica exchange within a sample sees independent
+ * replicas.
+ *
+ *   group     sample s belongs to group g(s) = 2 (s >> 6) + (s & 1); samples 2p
+ *             and 2p + 1 (a replica pair of one realisation, when their
+ *             couplings are equal) fall in different groups.
+ *   random    the Metropolis u of group g at temperature index t, site n of
+ *             colour c, sweep: word m & 3 of R(m >> 2, sweep, c | 3 << 1,
+ *             32 g + t), m = n >> 1 (the multi-spin coded word of stream 32 g + t).
+ *   state     sp[s*N + n], bit t = the configuration at temperature t (1 <=>
+ *             spin -1); bit t runs at beta[t] (ascending temperature).
+ *   sweep     colour 0, then colour 1; bit t of a site of colour c flips iff
+ *             dE <= 0 or u < thr(beta_t, dE).
+ *   exchange  after every X-th sweep (step e = (sweep + 1) / X - 1), for each
+ *             sample the pairs (k, k+1), k = e mod 2, e mod 2 + 2, ...: with
+ *             E_k the energy of the configuration at temperature k, accept iff
+ *             D = (beta_k - beta_{k+1}) (E_k - E_{k+1}) >= 0 or
+ *             u < floor(exp(D) 2^32), u = word k & 3 of R(k >> 2, e, 2 << 1, s);
+ *             an accepted pair swaps the two configurations (bits k and k + 1 of
+ *             every site word) and counts in acc[s*32 + k]. */
+int orc_ea_dp_group(int sample) { return 2 * (sample >> 6) + (sample & 1); }
+
+int orc_ea_dp_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
+                     uint64_t seed, uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
+  lat_t g;
+  if (lat_make(&g, nd, L)) return -1;
+  uint64_t thr[32][4];
+  for (int t = 0; t < 32; ++t)
+    for (int k = 0; k < 4; ++k) thr[t][k] = orc_threshold(betas[t], 4 * k);
+  const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (int i = 0; i < nsamples; ++i) {
+    uint32_t* w = sp + (int64_t)i * g.N;
+    const uint64_t* J = bonds + (int64_t)i * nd * g.nw;
+    const uint32_t group = (uint32_t)orc_ea_dp_group(i);
+    for (int64_t it = 0; it < nsweeps; ++it) {
+      uint32_t sweep = sweep0 + (uint32_t)it;
+      for (int c = 0; c < 2; ++c) {
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < g.N; ++n) {
+          if (lat_colour(&g, n) != c) continue;
+          uint32_t flip = 0;
+          for (int t = 0; t < 32; ++t) {
+            uint32_t u = orc_msc_u(seed, 32u * group + (uint32_t)t, sweep, c, (uint64_t)(n >> 1));
+            int sn = rep_spin(w[n], t);
+            int h = 0;
+            for (int d = 0; d < nd; ++d) {
+              int64_t f = lat_step(&g, n, d, +1), b = lat_step(&g, n, d, -1);
+              h += bond_J(&g, J, n, d) * rep_spin(w[f], t);
+              h += bond_J(&g, J, b, d) * rep_spin(w[b], t);
+            }
+            int dE = 2 * sn * h;
+            if (dE <= 0 || (uint64_t)u < thr[t][dE / 4]) flip |= 1u << t;
+          }
+          w[n] ^= flip;
+        }
+      }
+      if (exchange_every > 0 && ((int64_t)sweep + 1) % exchange_every == 0) {
+        uint32_t e = (uint32_t)(((int64_t)sweep + 1) / exchange_every - 1);
+        int64_t E[32], M[32];
+        orc_ea_observables(nd, L, 1, w, J, E, M);  /* bit t: the configuration at temperature t */
+        for (int k = (int)(e & 1); k + 1 < 32; k += 2) {
+          double D = (betas[k] - betas[k + 1]) * (double)(E[k] - E[k + 1]);
+          int accept;
+          if (D >= 0) {
+            accept = 1;
+          } else {
+            uint32_t ctr[4] = {(uint32_t)k >> 2, e, 2u << 1, (uint32_t)i};
+            uint32_t r[4];
+            orc_philox4x32_10(ctr, key, r);
+            accept = (uint64_t)r[k & 3] < (uint64_t)floor(exp(D) * ORC_TWO32);
+          }
+          if (accept) {
+            for (int64_t n = 0; n < g.N; ++n) {
+              uint32_t d = ((w[n] >> k) ^ (w[n] >> (k + 1))) & 1u;
+              w[n] ^= (d << k) | (d << (k + 1));
+            }
+            if (acc) acc[32 * (int64_t)i + k] += 1;
+          }
+        }
+      }
+    }
+  }
+  return 0;
+}
+
 /* Spin-glass overlap of replica pairs (Sec. 4: many disorder realisations at
  * once; two replicas of one realisation give its overlap): samples 2p and
  * 2p + 1 are two replicas of pair p.  For every temperature index t,
