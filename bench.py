@@ -65,7 +65,8 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "dc", "packed2d", "packed3d", "heis3d", "batched"],
+    p.add_argument("--profile-case", choices=["2d", "3d", "ea", "ea_shared", "ea_dp", "dc", "packed2d", "packed3d",
+                                              "heis3d", "batched"],
                    default=None,
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
@@ -88,10 +89,12 @@ def run_profile_case(a):
 
     spn_build.build()
     spn.load()
-    if a.profile_case == "ea":  # the full 1024-sample L = 32 batch, a few sweeps per launch
+    if a.profile_case in ("ea", "ea_shared", "ea_dp"):  # the full 1024-sample L = 32 batch, a few sweeps per launch
         dims = (EA_L, EA_L, EA_L)
         b = spn.EABatch(dims, inputs.ea_bonds(dims, EA_SAMPLES, inputs.unit_seed(0xEA)),
-                        inputs.geometric_ladder(0.2, 2.0), inputs.unit_seed(0xEB), exchange_every=EA_EVERY)
+                        inputs.geometric_ladder(0.2, 2.0), inputs.unit_seed(0xEB), exchange_every=EA_EVERY,
+                        u_per_slot=False if a.profile_case == "ea_shared" else None,
+                        disorder_parallel=a.profile_case == "ea_dp")
         for _ in range(3):
             b.sweep(a.profile_sweeps)
         b.sync()
@@ -335,20 +338,24 @@ def form_ea(stream, sweeps):
     bonds = inputs.ea_bonds(dims, EA_SAMPLES, inputs.unit_seed(0xEA))
     att = EA_SAMPLES * 32 * EA_L ** 3 * sweeps
     ms = {}
-    # default: a u per temperature slot (exact ladder with exchange); shared u: the
-    # opt-in whose ladder drifts under exchange, timed for comparison
-    for mode, ps in (("per_slot", None), ("shared_u", False)):
+    # disorder-parallel layout (32 samples per word at one temperature, exact
+    # ladder); temperature-per-bit layout with a u per slot (its default with
+    # exchange, exact) and with the shared u (an opt-in whose ladder drifts
+    # under exchange), timed for comparison
+    for mode, ps, dp in (("disorder_parallel", None, True), ("per_slot", None, False), ("shared_u", False, False)):
         b = spn.EABatch(dims, bonds, inputs.geometric_ladder(0.2, 2.0), inputs.unit_seed(0xEB),
-                        exchange_every=EA_EVERY, u_per_slot=ps)
+                        exchange_every=EA_EVERY, u_per_slot=ps, disorder_parallel=dp)
         b.set_stream(stream)
         b.sweep(EA_EVERY)
         ms[mode] = _timed(stream, lambda: b.sweep(sweeps))
         b.close()
-    return {"value": att / (ms["per_slot"] * 1e6), "unit": UNIT, "ms": ms["per_slot"], "attempts": att,
-            "sweeps": sweeps, "shared_u_attempts_per_ns": att / (ms["shared_u"] * 1e6),
+    return {"value": att / (ms["disorder_parallel"] * 1e6), "unit": UNIT, "ms": ms["disorder_parallel"],
+            "attempts": att, "sweeps": sweeps,
+            "per_slot_attempts_per_ns": att / (ms["per_slot"] * 1e6),
+            "shared_u_attempts_per_ns": att / (ms["shared_u"] * 1e6),
             "workload": f"3D +-J EA L={EA_L}, {EA_SAMPLES} samples x 32 temperatures on [0.2, 2.0], multi-spin "
                         f"coded, exchange every {EA_EVERY} sweeps, {sweeps} sweeps (attempts count every replica); "
-                        "value: the default chain (a u per temperature slot, exact with exchange)"}
+                        "value: the disorder-parallel layout (exact ladder)"}
 
 
 def form_served(n_requests, budget_bytes=120 * 10**9):

@@ -330,6 +330,27 @@ int spn_multi_destroy(spn_multi m);
 int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
                      const double* betas, int nbeta, uint64_t seed, int exchange_every);
 
+/* A batch in the disorder-parallel layout (Sec. 4: many disorder realisations
+ * at once with asynchronous multi-spin coding, the bits of a word being
+ * different samples).  Same arguments and results as spn_create_batch, but
+ * Lx must be a multiple of 8 (SPN_E_ARG otherwise), and the device keeps one
+ * 32-bit word per (site, temperature, group of 32 samples): sample s belongs to
+ * group g = 2 (s >> 6) + (s & 1) (so the replicas 2p and 2p + 1 of a
+ * realisation never share a word) and the samples of a group share the
+ * Metropolis u of the site at each temperature t: word m & 3 of
+ * R(m >> 2, sweep, colour | 3 << 1, 32 g + t) for within-colour index m.  A
+ * sample's 32 temperatures draw independent numbers, so the ladder is exact
+ * under replica exchange, and a word lattice has one temperature, so the
+ * acceptance is a scalar compare per site.  Replica exchange swaps the two
+ * configurations of an accepted pair (u as in spn_create_batch), so the slot
+ * map stays the identity: bit t of a sample's word is always temperature t.
+ * spn_batch_* calls work on it as on any batch, except
+ * spn_batch_set_u_per_slot (SPN_E_STATE) and spn_batch_set_slots, which
+ * accepts only identity maps.  Reading words, energies or overlaps converts
+ * the word lattices on the device first. */
+int spn_create_batch_dp(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
+                        const double* betas, int nbeta, uint64_t seed, int exchange_every);
+
 /* Run nsweeps multi-spin coded sweeps (colour 0, then colour 1) with the
  * exchanges due; every slot draws its own u, or the 32 replicas of a site share
  * its Philox word, as spn_batch_set_u_per_slot says. */

@@ -86,7 +86,7 @@ def lib():
             L.orc_ea_sweeps_ex.restype = cint
             L.orc_ea_dp_group.argtypes = [cint]
             L.orc_ea_dp_group.restype = cint
-            L.orc_ea_dp_sweeps.argtypes = [cint, vp, cint, vp, vp, vp, u64, u32, i64, cint, vp]
+            L.orc_ea_dp_sweeps.argtypes = [cint, vp, cint, vp, vp, vp, u64, u32, i64, cint, vp, cint]
             L.orc_ea_dp_sweeps.restype = cint
             L.orc_ea_overlap.argtypes = [cint, vp, cint, vp, vp, vp]
             L.orc_ea_overlap.restype = cint
@@ -279,11 +279,12 @@ def ea_dp_group(sample: int) -> int:
 
 
 def ea_dp_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, nsweeps: int, seed: int, sweep0: int = 0,
-                 exchange_every: int = 0, acc: np.ndarray | None = None):
+                 exchange_every: int = 0, acc: np.ndarray | None = None, sample0: int = 0):
     """Disorder-parallel multi-spin coded sweeps, in place on ``words`` [nsamples, N]
     (bit t = the configuration at temperature t): the samples of a group share
     the site's u at each temperature, replica exchange swaps configurations.
-    acc: [nsamples, 32] int64 exchange counters (optional)."""
+    acc: [nsamples, 32] int64 exchange counters (optional).  Row i is sample
+    sample0 + i of the batch."""
     d = _dims(dims)
     if words.dtype != np.uint32 or not words.flags.c_contiguous:
         raise TypeError("ea_dp_sweeps: words must be contiguous uint32")
@@ -293,7 +294,7 @@ def ea_dp_sweeps(dims, words: np.ndarray, bonds: np.ndarray, betas, nsweeps: int
     if acc is not None and (acc.dtype != np.int64 or not acc.flags.c_contiguous):
         raise TypeError("acc must be contiguous int64")
     _check(lib().orc_ea_dp_sweeps(len(d), _p(d), words.shape[0], _p(words), _p(_bonds(bonds)), _p(be), seed,
-                                  sweep0, int(nsweeps), int(exchange_every), _p(acc)), "ea_dp_sweeps")
+                                  sweep0, int(nsweeps), int(exchange_every), _p(acc), int(sample0)), "ea_dp_sweeps")
 
 
 def ea_overlap(dims, words: np.ndarray, slot_of_temp: np.ndarray) -> np.ndarray:

@@ -550,11 +550,14 @@ int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const ui
  *             D = (beta_k - beta_{k+1}) (E_k - E_{k+1}) >= 0 or
  *             u < floor(exp(D) 2^32), u = word k & 3 of R(k >> 2, e, 2 << 1, s);
  *             an accepted pair swaps the two configurations (bits k and k + 1 of
- *             every site word) and counts in acc[s*32 + k]. */
+ *             every site word) and counts in acc[s*32 + k].
+ *   sample0   row i of sp (and of bonds, acc) is sample sample0 + i of the batch,
+ *             so a subset of a batch can be run alone. */
 int orc_ea_dp_group(int sample) { return 2 * (sample >> 6) + (sample & 1); }
 
 int orc_ea_dp_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
-                     uint64_t seed, uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
+                     uint64_t seed, uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc,
+                     int sample0) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
   uint64_t thr[32][4];
@@ -564,7 +567,8 @@ int orc_ea_dp_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const
   for (int i = 0; i < nsamples; ++i) {
     uint32_t* w = sp + (int64_t)i * g.N;
     const uint64_t* J = bonds + (int64_t)i * nd * g.nw;
-    const uint32_t group = (uint32_t)orc_ea_dp_group(i);
+    const int sample = sample0 + i;  /* the batch index of row i of sp */
+    const uint32_t group = (uint32_t)orc_ea_dp_group(sample);
     for (int64_t it = 0; it < nsweeps; ++it) {
       uint32_t sweep = sweep0 + (uint32_t)it;
       for (int c = 0; c < 2; ++c) {
@@ -597,7 +601,7 @@ int orc_ea_dp_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const
           if (D >= 0) {
             accept = 1;
           } else {
-            uint32_t ctr[4] = {(uint32_t)k >> 2, e, 2u << 1, (uint32_t)i};
+            uint32_t ctr[4] = {(uint32_t)k >> 2, e, 2u << 1, (uint32_t)sample};
             uint32_t r[4];
             orc_philox4x32_10(ctr, key, r);
             accept = (uint64_t)r[k & 3] < (uint64_t)floor(exp(D) * ORC_TWO32);

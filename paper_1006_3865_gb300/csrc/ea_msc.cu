@@ -694,6 +694,14 @@ struct EaBatch {
   spn::EaArgs args{};
   size_t smem = 0;
   int threads = 0;
+  // disorder-parallel layout (spn_create_batch_dp): the word lattices are the
+  // state; d_words holds the per-sample words only after a conversion
+  bool dp = false;
+  int ngroups = 0;
+  uint32_t* d_dp = nullptr;   // [32 ngroups][N]
+  uint32_t* d_bdp = nullptr;  // [ngroups][nd][N]
+  uint32_t* d_U = nullptr;    // [32 ngroups][32]
+  uint32_t* d_X = nullptr;    // [ngroups][32]
 };
 
 namespace {
@@ -729,7 +737,8 @@ void ea_release(EaBatch* b, void* p) {
 void spn_ea_free(EaBatch* b) {
   if (!b) return;
   for (void* p : {(void*)b->d_words, (void*)b->d_bonds, (void*)b->d_tos, (void*)b->d_xacc, (void*)b->d_xtab,
-                  (void*)b->d_err, (void*)b->d_qlast, (void*)b->d_q2, (void*)b->d_q4, (void*)b->d_obs})
+                  (void*)b->d_err, (void*)b->d_qlast, (void*)b->d_q2, (void*)b->d_q4, (void*)b->d_obs,
+                  (void*)b->d_dp, (void*)b->d_bdp, (void*)b->d_U, (void*)b->d_X})
     ea_release(b, p);
   delete b;
 }
@@ -947,7 +956,110 @@ int ea_upload_async(spn_handle* out, EaPrep& p, cudaStream_t st) { return ea_upl
 
 }  // namespace spn
 
+namespace {
+
+// The per-sample words of a disorder-parallel batch into d_words (bit t =
+// temperature t, 2 samples per uint64), ordered on the handle's stream.
+cudaError_t dp_to_words(spn_ctx* h) {
+  EaBatch* b = h->ea;
+  return spn::launch_dp_to_words(b->d_dp, b->d_words, b->L[0], b->N, b->nsamples, b->ngroups, h->st);
+}
+
+int dp_sweep(spn_ctx* h, int64_t nsweeps) {
+  EaBatch* b = h->ea;
+  spn::EaDpArgs A{};
+  A.dp = b->d_dp;
+  A.bdp = b->d_bdp;
+  A.U = b->d_U;
+  A.nd = b->nd;
+  A.Lx = b->L[0];
+  A.Ly = b->L[1];
+  A.Lz = b->L[2];
+  A.N = b->N;
+  A.div_h = spn::fastdiv((uint32_t)(b->L[0] / 2));
+  A.div_ly = spn::fastdiv((uint32_t)b->L[1]);
+  for (int t = 0; t < 32; ++t)
+    for (int lv = 0; lv < 3; ++lv) A.thr[t][lv] = b->args.thr[lv][t];
+  A.K = b->args.K;
+  spn::EaDpExchangeArgs XA{};
+  XA.U = b->d_U;
+  XA.X = b->d_X;
+  XA.xacc = b->d_xacc;
+  XA.xtab = b->d_xtab;
+  for (int k = 0; k < 32; ++k) {
+    XA.xoff[k] = b->args.xoff[k];
+    XA.xlen[k] = b->args.xlen[k];
+  }
+  XA.xalways = b->args.xalways;
+  XA.nsamples = b->nsamples;
+  XA.K = b->args.K;
+  const int X = b->exchange_every;
+  const int threads = b->N >= 16384 ? 1024 : (b->N >= 4096 ? 512 : 256);
+  int64_t done = 0;
+  while (done < nsweeps) {  // one launch per exchange interval (at most 2000 sweeps)
+    const uint64_t sw = h->sweeps + (uint64_t)done;
+    int64_t n = nsweeps - done;
+    if (X > 0) n = std::min<int64_t>(n, X - (int64_t)(sw % (uint64_t)X));
+    n = std::min<int64_t>(n, 2000);
+    A.sweep0 = (uint32_t)sw;
+    A.nsweeps = (int)n;
+    A.need_u = X > 0 && (sw + (uint64_t)n) % (uint64_t)X == 0;
+    cudaError_t e = spn::launch_dp_sweep(A, 32 * b->ngroups, threads, h->st);
+    if (e == cudaSuccess && A.need_u) {
+      XA.e = (uint32_t)((sw + (uint64_t)n) / (uint64_t)X - 1);
+      e = spn::launch_dp_exchange(XA, b->ngroups, h->st);
+      if (e == cudaSuccess) e = spn::launch_dp_swap(b->d_dp, b->d_X, b->N, b->ngroups, h->st);
+    }
+    if (e != cudaSuccess) {
+      h->sweeps += (uint64_t)done;
+      return ea_fail(SPN_E_CUDA, cudaGetErrorString(e));
+    }
+    done += n;
+  }
+  h->sweeps += (uint64_t)nsweeps;
+  return SPN_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int spn_create_batch_dp(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
+                        const double* betas, int nbeta, uint64_t seed, int exchange_every) {
+  if (!out) return ea_fail(SPN_E_ARG, "NULL argument");
+  *out = nullptr;
+  if (dims && dims[0] % 8) return ea_fail(SPN_E_ARG, "the disorder-parallel layout needs Lx a multiple of 8");
+  const int rc = create_batch(out, model, dims, nsamples, couplings, betas, nbeta, seed, exchange_every, nullptr, false);
+  if (rc) return rc;
+  spn_ctx* h = *out;
+  EaBatch* b = h->ea;
+  b->dp = true;
+  b->ngroups = 2 * ((nsamples + 63) / 64);
+  b->args.u_per_slot = 0;
+  const size_t N = (size_t)b->N, nwl = (size_t)32 * b->ngroups;
+  const size_t nw = (N + 63) / 64;
+  uint64_t* d_packed = nullptr;
+  auto bail = [&](int code, const char* msg) {
+    if (d_packed) cudaFree(d_packed);
+    spn_destroy(h);
+    *out = nullptr;
+    return ea_fail(code, msg);
+  };
+  if (cudaMalloc(&b->d_dp, nwl * N * 4) != cudaSuccess || cudaMalloc(&b->d_bdp, (size_t)b->ngroups * b->nd * N * 4) ||
+      cudaMalloc(&b->d_U, nwl * 32 * 4) != cudaSuccess || cudaMalloc(&b->d_X, (size_t)b->ngroups * 32 * 4) ||
+      cudaMalloc(&d_packed, (size_t)nsamples * b->nd * nw * 8) != cudaSuccess)
+    return bail(SPN_E_NOMEM, "allocating the disorder-parallel batch");
+  cudaError_t e = cudaMemcpy(d_packed, couplings, (size_t)nsamples * b->nd * nw * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_X, 0, (size_t)b->ngroups * 32 * 4);
+  if (e == cudaSuccess) e = spn::launch_dp_bonds(d_packed, b->d_bdp, b->nd, b->L[0], b->N, nsamples, b->ngroups, h->st);
+  // the hot start of the per-sample words, in the word lattices
+  if (e == cudaSuccess)
+    e = spn::launch_dp_from_words(b->d_words, b->d_dp, b->L[0], b->N, nsamples, b->ngroups, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return bail(SPN_E_CUDA, cudaGetErrorString(e));
+  cudaFree(d_packed);
+  return SPN_OK;
+}
 
 int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsamples, const void* couplings,
                      const double* betas, int nbeta, uint64_t seed, int exchange_every) {
@@ -957,6 +1069,7 @@ int spn_create_batch(spn_handle* out, int model, const int32_t* dims, int nsampl
 int spn_batch_set_u_per_slot(spn_handle h, int32_t on) {
   if (!h || !h->ea) return ea_fail(SPN_E_STATE, "not a batch handle");
   if (on != 0 && on != 1) return ea_fail(SPN_E_ARG, "on must be 0 or 1");
+  if (h->ea->dp) return ea_fail(SPN_E_STATE, "a disorder-parallel batch draws its own random numbers");
   h->ea->args.u_per_slot = on;
   return SPN_OK;
 }
@@ -966,6 +1079,7 @@ int spn_batch_sweep(spn_handle h, int64_t nsweeps) {
   if (nsweeps < 0) return ea_fail(SPN_E_ARG, "nsweeps must be >= 0");
   EaBatch* b = h->ea;
   if (h->sweeps + (uint64_t)nsweeps > 0xffffffffull) return ea_fail(SPN_E_ARG, "sweep counter would exceed 2^32");
+  if (b->dp) return dp_sweep(h, nsweeps);
   auto kern = b->args.u_per_slot ? (b->nd == 2 ? spn::k_ea_resident<2, true> : spn::k_ea_resident<3, true>)
                                   : (b->nd == 2 ? spn::k_ea_resident<2, false> : spn::k_ea_resident<3, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
@@ -992,6 +1106,7 @@ int spn_batch_get_words(spn_handle h, uint32_t* out, size_t count) {
   if (count != (size_t)b->nsamples * b->N) return ea_fail(SPN_E_ARG, "count must be nsamples * N");
   const int pairs = (b->nsamples + 1) / 2;
   std::vector<uint64_t> w((size_t)pairs * b->N);
+  if (b->dp && dp_to_words(h) != cudaSuccess) return ea_fail(SPN_E_CUDA, "converting the word lattices");
   if (cudaStreamSynchronize(h->st) != cudaSuccess ||
       cudaMemcpy(w.data(), b->d_words, w.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return ea_fail(SPN_E_CUDA, "reading the words");
@@ -1013,6 +1128,10 @@ int spn_batch_set_words(spn_handle h, const uint32_t* in, size_t count) {
   if (cudaStreamSynchronize(h->st) != cudaSuccess ||
       cudaMemcpy(b->d_words, w.data(), w.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
     return ea_fail(SPN_E_CUDA, "writing the words");
+  if (b->dp && (spn::launch_dp_from_words(b->d_words, b->d_dp, b->L[0], b->N, b->nsamples, b->ngroups, h->st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(h->st) != cudaSuccess))
+    return ea_fail(SPN_E_CUDA, "converting the words to word lattices");
   return SPN_OK;
 }
 
@@ -1033,6 +1152,8 @@ int spn_batch_set_slots(spn_handle h, const uint8_t* temp_of_slot, size_t count)
     for (int j = 0; j < 32; ++j) {
       const uint8_t t = temp_of_slot[s * 32 + j];
       if (t >= 32 || ((seen >> t) & 1u)) return ea_fail(SPN_E_ARG, "each sample's map must be a permutation of 0..31");
+      if (h->ea->dp && t != j)
+        return ea_fail(SPN_E_STATE, "a disorder-parallel batch keeps bit t at temperature t (identity maps only)");
       seen |= 1u << t;
     }
   }
@@ -1048,6 +1169,7 @@ int spn_batch_energies(spn_handle h, int64_t* E, int64_t* M, size_t count) {
   if (count != (size_t)b->nsamples * 32) return ea_fail(SPN_E_ARG, "count must be nsamples * 32");
   long long* dE = b->d_obs;
   long long* dM = b->d_obs + count;
+  if (b->dp && dp_to_words(h) != cudaSuccess) return ea_fail(SPN_E_CUDA, "converting the word lattices");
   spn::k_ea_observables<<<b->nsamples, 256, 0, h->st>>>(b->d_words, b->d_bonds, b->nd, b->L[0], b->L[1], b->L[2], b->N, dE,
                                                        dM);
   spn::count_launches(1);
@@ -1081,6 +1203,7 @@ int spn_batch_measure_overlap(spn_handle h) {
         cudaMemsetAsync(b->d_q4, 0, n * 16, h->st) != cudaSuccess)
       return ea_fail(SPN_E_CUDA, "clearing the overlap sums");
   }
+  if (b->dp && dp_to_words(h) != cudaSuccess) return ea_fail(SPN_E_CUDA, "converting the word lattices");
   spn::k_ea_overlap<<<b->nsamples / 2, 256, 0, h->st>>>(b->d_words, b->d_tos, b->N, b->d_qlast, b->d_q2, b->d_q4);
   spn::count_launches(1);
   const cudaError_t e = cudaGetLastError();

@@ -152,6 +152,43 @@ struct EaArgs {
   int* err;
 };
 
+// Disorder-parallel EA batches (ea_dp.cu): word lattice 32 g + t holds the 32
+// samples of group g at temperature t, N uint32 words in colour-separated row
+// order; bonds [g][d][N] words (bit j: J(n, d) = -1 for sample j of the group).
+struct EaDpArgs {
+  uint32_t* dp;          // [32 ngroups][N]
+  const uint32_t* bdp;   // [ngroups][nd][N]
+  uint32_t* U;           // [32 ngroups][32] unsatisfied forward bonds per sample (need_u)
+  int nd, Lx, Ly, Lz, N;
+  FastDiv div_h, div_ly;  // by Lx / 2 and by Ly
+  uint32_t sweep0;
+  int nsweeps;
+  int need_u;             // count unsatisfied bonds after the last sweep (an exchange follows)
+  uint32_t thr[32][3];    // thr[t][lv] for dE = 4 (lv + 1), beta of temperature t
+  PhiloxKeys K;
+};
+struct EaDpExchangeArgs {
+  const uint32_t* U;
+  uint32_t* X;                // [ngroups][32] swap masks of the step's pairs (k, k + 1)
+  unsigned long long* xacc;   // [nsamples][32]
+  const uint32_t* xtab;
+  int xoff[32], xlen[32];
+  uint32_t xalways;
+  int nsamples;
+  uint32_t e;                 // exchange step
+  PhiloxKeys K;
+};
+size_t dp_smem(int N);
+cudaError_t launch_dp_from_words(const uint64_t* pairs, uint32_t* dp, int Lx, int N, int nsamples, int ngroups,
+                                 cudaStream_t st);
+cudaError_t launch_dp_to_words(const uint32_t* dp, uint64_t* pairs, int Lx, int N, int nsamples, int ngroups,
+                               cudaStream_t st);
+cudaError_t launch_dp_bonds(const uint64_t* packed, uint32_t* bdp, int nd, int Lx, int N, int nsamples, int ngroups,
+                            cudaStream_t st);
+cudaError_t launch_dp_sweep(const EaDpArgs& a, int nwl, int threads, cudaStream_t st);
+cudaError_t launch_dp_exchange(const EaDpExchangeArgs& a, int ngroups, cudaStream_t st);
+cudaError_t launch_dp_swap(uint32_t* dp, const uint32_t* X, int N, int ngroups, cudaStream_t st);
+
 // Served multi-spin coded EA jobs (single-sample batch handles): the
 // parameter block of the next `nsweeps` sweeps of h (its sweep counter
 // advances), and one launch running many such blocks, one CTA each.

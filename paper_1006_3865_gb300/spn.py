@@ -93,6 +93,7 @@ _SIGNATURES = {
     "spn_server_destroy": (_c.c_int, [_vp]),
     "spn_create_batch": (_c.c_int, [_P(_vp), _c.c_int, _vp, _c.c_int, _vp, _vp, _c.c_int, _u64, _c.c_int]),
     "spn_batch_set_u_per_slot": (_c.c_int, [_vp, _c.c_int32]),
+    "spn_create_batch_dp": (_c.c_int, [_P(_vp), _c.c_int, _vp, _c.c_int, _vp, _vp, _c.c_int, _u64, _c.c_int]),
     "spn_batch_sweep": (_c.c_int, [_vp, _i64]),
     "spn_batch_get_words": (_c.c_int, [_vp, _vp, _sz]),
     "spn_batch_set_words": (_c.c_int, [_vp, _vp, _sz]),
@@ -395,9 +396,10 @@ class EABatch:
     """Multi-spin coded +-J EA samples with replica exchange (spn_create_batch)."""
 
     def __init__(self, dims, couplings: np.ndarray, betas, seed: int, exchange_every: int = 10,
-                 u_per_slot: bool | None = None):
+                 u_per_slot: bool | None = None, disorder_parallel: bool = False):
         """u_per_slot: every temperature slot draws its own u (spn_batch_set_u_per_slot).  None keeps the
-        library's default: a u per slot with replica exchange (exchange_every > 0), a shared u without."""
+        library's default: a u per slot with replica exchange (exchange_every > 0), a shared u without.
+        disorder_parallel: the layout of spn_create_batch_dp (samples in the bits of a word)."""
         self._lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.N = int(np.prod(self.dims))
@@ -407,8 +409,9 @@ class EABatch:
         d = _dims(dims)
         h = _vp()
         model = SPN_EA2D_PMJ if len(self.dims) == 2 else SPN_EA3D_PMJ
-        _check(self._lib.spn_create_batch(_c.byref(h), model, _ptr(d), self.nsamples, _ptr(J), _ptr(b),
-                                          int(b.size), seed, int(exchange_every)))
+        create = self._lib.spn_create_batch_dp if disorder_parallel else self._lib.spn_create_batch
+        _check(create(_c.byref(h), model, _ptr(d), self.nsamples, _ptr(J), _ptr(b), int(b.size), seed,
+                      int(exchange_every)))
         self._h = h
         if u_per_slot is not None:
             _check(self._lib.spn_batch_set_u_per_slot(self._h, 1 if u_per_slot else 0))
