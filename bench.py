@@ -622,7 +622,8 @@ def form_overlap(stream, sweeps=2000, every=10):
     for name, dims, ladder in (("2d_L128", (128, 128), (0.3, 3.0)), ("3d_L32", (EA_L, EA_L, EA_L), (0.2, 2.0))):
         pairs = EA_SAMPLES // 2
         bonds = np.repeat(inputs.ea_bonds(dims, pairs, inputs.unit_seed(0xE2)), 2, axis=0)
-        b = spn.EABatch(dims, bonds, inputs.geometric_ladder(*ladder), inputs.unit_seed(0xE3), exchange_every=EA_EVERY)
+        b = spn.EABatch(dims, bonds, inputs.geometric_ladder(*ladder), inputs.unit_seed(0xE3), exchange_every=EA_EVERY,
+                        disorder_parallel=True)
         b.set_stream(stream)
         b.sweep(every)
         b.measure_overlap()
@@ -643,7 +644,8 @@ def form_overlap(stream, sweeps=2000, every=10):
                      "binder_lowest_T": float(r["binder"][0]), "binder_highest_T": float(r["binder"][31])}
     return {"value": out["2d_L128"]["attempts_per_ns"], "unit": UNIT, "by_lattice": out,
             "workload": f"+-J EA 2D L=128 and 3D L=32, {EA_SAMPLES // 2} replica pairs x 32 temperatures, "
-                        f"multi-spin coded, exchange every {EA_EVERY}, overlap every {every} sweeps, {sweeps} sweeps"}
+                        f"disorder-parallel multi-spin coding, exchange every {EA_EVERY}, overlap every {every} "
+                        f"sweeps, {sweeps} sweeps"}
 
 
 def form_heis(stream, sweeps=100):
