@@ -34,7 +34,7 @@ enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2, kPathPac
 // the lattice is stored as bit words (rows of packed_row_words(Lx) words).
 struct StreamGeom {
   int packed;
-  int wave;  // 2D int8 rows of at least 2048 sites: the band-parallel kernel (wave.cu); nseg its row segments
+  int wave;  // 1: the 2D band-parallel kernel (wave.cu), nseg row segments; 2: the 3D wavefront kernel (wave3.cu)
   int TY, R, nseg, threads, nraw, nbit;
   int roundsC, roundsA, roundsB, qcap;  // words per thread per phase; tie-queue entries per warp
   size_t smem;
@@ -78,6 +78,15 @@ size_t wave_smem_bytes(const Lattice& g);
 cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, int nseg, const DevThr& T,
                               const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                               int* err, cudaStream_t st, uint32_t expire_polls);
+// Wavefront 3D sweep (wave3.cu): int8 lattices with Lx = 64, 128, 256 or 512,
+// dense rows, no bonds, band height TY a multiple of 32 / (Lx / 64) with at most
+// eight compute warps, dividing Ly; nseg segments along z.
+bool wave3_supported(const Lattice& g, int TY);
+int wave3_default_segments(const Lattice& g, int TY);
+size_t wave3_smem_bytes(const Lattice& g, int TY);
+cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, int TY, int nseg, const DevThr& T,
+                               const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
+                               int* err, cudaStream_t st, uint32_t expire_polls);
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed = false);
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
 // expire_polls (test support, 0 otherwise): the copy of each CTA's first slice

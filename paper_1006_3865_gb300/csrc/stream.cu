@@ -454,7 +454,16 @@ void phase_counts(const Lattice& g, int TY, int R, bool packed, int& nC, int& nA
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed) {
   StreamGeom s{};
   s.packed = packed ? 1 : 0;
-  if (!packed && R <= 1 && wave_supported(g)) {  // one row per step: the wavefront kernel
+  if (!packed && R <= 1 && g.nd == 3 && wave3_supported(g, TY)) {  // one plane per step: the 3D wavefront kernel
+    s.wave = 2;
+    s.TY = TY;
+    s.R = 1;
+    s.threads = 32 * (TY / (32 / (g.Lx / 64)) + 1);
+    s.nseg = nseg > 0 ? std::min(nseg, g.Lz) : wave3_default_segments(g, TY);
+    s.smem = wave3_smem_bytes(g, TY);
+    return s;
+  }
+  if (!packed && R <= 1 && wave_supported(g)) {  // one row per step: the band-parallel kernel
     s.wave = 1;
     s.TY = 1;
     s.R = 1;
@@ -512,6 +521,7 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packe
 
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
   const bool packed = geo.packed != 0;
+  if (geo.wave == 2) return !packed && wave3_supported(g, geo.TY) && geo.nseg >= 1 && geo.nseg <= g.Lz;
   if (geo.wave) return !packed && wave_supported(g) && geo.nseg >= 1 && geo.nseg <= g.Ly;
   if (geo.R < 1 || geo.R > 127 || geo.threads < 32 || geo.threads > max_threads(g.nd) || geo.threads % 32) return false;
   int nC, nA, nB;
@@ -528,6 +538,9 @@ cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, con
                                 const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
                                 unsigned long long* acc, int* err, cudaStream_t st, uint32_t expire_polls) {
   if (!stream_geometry_ok(g, geo)) return cudaErrorInvalidConfiguration;
+  if (geo.wave == 2)
+    return launch_sweep_wave3(g, static_cast<const int8_t*>(in), static_cast<int8_t*>(out), geo.TY, geo.nseg, T, K,
+                              stream_id, sweep, acc, err, st, expire_polls);
   if (geo.wave)
     return launch_sweep_wave(g, static_cast<const int8_t*>(in), static_cast<int8_t*>(out), geo.nseg, T, K, stream_id,
                              sweep, acc, err, st, expire_polls);

@@ -21,7 +21,7 @@ def _lib():
 
 @pytest.mark.parametrize("path", [spn.PATH_STREAM, spn.PATH_PACKED])
 @pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (256, 256)), (spn.SPN_ISING3D, (64, 16, 12)),
-                                        (spn.SPN_ISING2D, (4096, 32))])
+                                        (spn.SPN_ISING2D, (4096, 32)), (spn.SPN_ISING3D, (256, 32, 12))])
 def test_bounded_wait_runs_out_and_reports_timeout(model, dims, path):
     lat = spn.Lattice(model, dims, 5)
     lat.path = path

@@ -75,6 +75,21 @@ def test_ising2d_band_parallel(dims, tiling):
              tiling=tiling, stream=6)
 
 
+@pytest.mark.parametrize("dims,tiling", [((64, 32, 8), (32, 1, 0)), ((128, 16, 6), (16, 1, 3)),
+                                         ((256, 16, 10), (8, 1, 0)), ((256, 16, 10), (16, 0, 10)),
+                                         ((512, 32, 4), (32, 1, 0)), ((512, 32, 6), (4, 1, 5)),
+                                         ((512, 24, 6), (12, 1, 2)), ((256, 24, 12), (24, 1, 7)),
+                                         ((256, 8, 2), (8, 1, 1)), ((512, 8, 4), (8, 1, 4))])
+def test_ising3d_wavefront(dims, tiling):
+    """3D rows of 64 to 512 sites take the wavefront kernel when one plane is
+    streamed per step (a warp per group of rows of a band, a halo warp for the
+    rows next to it, neighbours at most one step apart): one to eight compute
+    warps, a band that is the whole lattice, segments down to one plane, two-plane
+    lattices, ragged segment splits."""
+    _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(18), [(inputs.BETA_C_3D, 6), (0.35, 2)], path=spn.PATH_STREAM,
+             tiling=tiling, stream=8)
+
+
 @pytest.mark.parametrize("dims,tiling", [((70, 16, 12), (4, 1, 3)), ((6, 8, 10), (8, 2, 0)), ((202, 4, 6), None)])
 def test_ising3d_stream_padded_rows(dims, tiling):
     _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(14), [(inputs.BETA_C_3D, 6)], path=spn.PATH_STREAM,
@@ -127,6 +142,7 @@ def test_ea3d_int8(dims):
 
 @pytest.mark.parametrize("model,dims,path", [(spn.SPN_ISING2D, (64, 32), spn.PATH_STREAM),
                                              (spn.SPN_ISING2D, (2048, 16), spn.PATH_STREAM),
+                                             (spn.SPN_ISING3D, (256, 16, 8), spn.PATH_STREAM),
                                              (spn.SPN_ISING2D, (10, 6), spn.PATH_GENERIC),
                                              (spn.SPN_ISING3D, (64, 8, 6), spn.PATH_STREAM)])
 def test_beta_zero_and_infinity(model, dims, path):
