@@ -32,6 +32,10 @@ import argparse
 import hashlib
 import json
 import os
+
+# more hardware work queues than CUDA's default 8, for the concurrent launches
+# of a served round; must be set before the CUDA context exists
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import re
 import statistics
 import subprocess

@@ -28,6 +28,12 @@ namespace spn {
 
 namespace {
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 template <int ND, bool CLUSTER>
 __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -91,6 +97,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
     sync_all();  // everybody has read s_idx before it is overwritten
     if (idx >= a.ninst) break;
     const ResInst in = a.inst[a.order[idx]];
+    if (in.tns && rank == 0 && tid == 0) in.tns[0] = globaltimer_ns();
     const PhiloxKeys K = philox_keys(in.seed);
     Lx = in.Lx;
     Ly = in.Ly;
@@ -286,6 +293,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
       }
     }
     sync_all();  // the bits are reused by the next instance
+    if (in.tns && rank == 0 && tid == 0) in.tns[1] = globaltimer_ns();
   }
 }
 
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
 bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs) {
   if (Lx < 2 || (Lx & 1)) return false;
   const int nrow = Ly * (nd == 3 ? Lz : 1);
-  if (cs < 1 || cs > 8 || nrow < cs) return false;
+  if (cs < 1 || cs > kMaxResidentCluster || nrow < cs) return false;
   return resident_smem(nd, Lx, Ly, Lz, cs) <= 200 * 1024;
 }
 
@@ -304,8 +312,8 @@ size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs) {
   return (size_t)((nrow + cs - 1) / cs) * 2 * W * 4 + 256 * 8;
 }
 
-int resident_cluster_size(int nd, int Lx, int Ly, int Lz) {
-  for (int cs = 1; cs <= 8; cs *= 2)
+int resident_cluster_size(int nd, int Lx, int Ly, int Lz, int max_cs) {
+  for (int cs = 1; cs <= max_cs; cs *= 2)
     if (resident_supported(nd, Lx, Ly, Lz, cs)) return cs;
   return 0;
 }
@@ -317,6 +325,7 @@ cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int c
   else
     fn = cs > 1 ? k_resident<2, true> : k_resident<2, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && cs > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ctas / cs * cs), 1, 1);
@@ -344,6 +353,27 @@ int resident_max_ctas(int nd, int cs, int threads, size_t smem) {
   else
     fn = cs > 1 ? k_resident<2, true> : k_resident<2, false>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cs > 1) {
+    // clusters are placed within one GPC: fewer fit than CTAs per SM x SMs suggests
+    if (cs > 8) cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess || nc <= 0) {
+      cudaGetLastError();
+      nc = 1;
+    }
+    return nc * cs;
+  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (per_sm <= 0) per_sm = 1;

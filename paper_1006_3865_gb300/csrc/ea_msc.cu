@@ -759,6 +759,19 @@ int ea_window_args(spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* 
   return SPN_OK;
 }
 
+int ea_job_per_sm(spn_ctx* h) {
+  if (!h || !h->ea || h->ea->nsamples != 1) return 1;
+  const EaBatch* b = h->ea;
+  const bool ps = b->args.u_per_slot != 0;
+  const int threads = ps ? std::min(b->threads, ea_max_threads(true)) : b->threads;
+  auto kern = ps ? (b->nd == 2 ? k_ea_jobs<2, true> : k_ea_jobs<3, true>)
+                 : (b->nd == 2 ? k_ea_jobs<2, false> : k_ea_jobs<3, false>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, b->smem) != cudaSuccess) cudaGetLastError();
+  return n > 0 ? n : 1;
+}
+
 cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, bool ps, int threads, size_t smem, cudaStream_t st) {
   auto kern = ps ? (nd == 2 ? k_ea_jobs<2, true> : k_ea_jobs<3, true>)
                  : (nd == 2 ? k_ea_jobs<2, false> : k_ea_jobs<3, false>);

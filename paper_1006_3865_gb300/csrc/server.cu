@@ -27,6 +27,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <thread>
 #include <tuple>
 #include <vector>
@@ -35,6 +36,12 @@
 #include "spn_internal.h"
 
 namespace {
+
+// A round runs up to a few dozen launches at once on the stream pool; the
+// default 8 hardware work queues would serialise the ninth launch behind the
+// first.  Set when the library is loaded, before any CUDA context exists (a
+// value the process already has is kept; once a context exists it has no effect).
+__attribute__((constructor)) void more_hardware_queues() { setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0); }
 
 double now_s() {
   using clk = std::chrono::steady_clock;
@@ -76,6 +83,19 @@ struct Job {
   std::unique_ptr<spn::EaPrep> prep;  // EA: host part built on a worker thread before admission
   int prep_rc = SPN_OK;
   int stream_slot = 0;
+  // round planning: the SM equivalents the job's launch shape takes while it
+  // runs, its attempts per ns while running (estimated at first, then
+  // measured per window on the resident path) and the last round that gave it
+  // a window
+  double fsm = 0;
+  double rsm = 0;  // attempts per ns and SM equivalent (0: not yet known)
+  uint64_t last_run = 0;
+  // resident: this round's cluster size (cs or wider) and its launch shape:
+  // threads (a power of two, 64 .. 512), shared memory, CTAs resident at once
+  int rcs = 0;
+  int threads = 64;
+  size_t smem = 0;
+  int occ = 1;
   // results
   int64_t E = 0, M = 0;
   std::vector<int8_t> spins;
@@ -112,13 +132,26 @@ struct spn_server_ctx {
   int* d_counters = nullptr;
   int* d_err = nullptr;
   size_t inst_cap = 0;
-  int64_t window_attempts = (int64_t)1 << 26;  // at least this many attempts per job per round
-  int64_t round_attempts = (int64_t)1 << 35;   // about this many attempts per round in all
+  double round_ns = 3.0e7;  // a window is about this much of its job's own run time
+  // share of the SMs a round plans for: clusters sit within one GPC, so the
+  // GPU holds less than its SM count in mixed launches; lowered when an
+  // instance of a round started late (a second wave), raised otherwise
+  double fill = 0.9;
+  uint64_t round_no = 0;
+  std::map<std::tuple<int, int, int, size_t>, int> max_ctas;  // resident launch shape -> CTAs resident at once
+  unsigned long long* d_tns = nullptr;  // per-round instance clocks [instance][start, end]
+  unsigned long long* h_tns = nullptr;  // pinned copy, read after the round
+  std::vector<Job*> res_jobs;           // per-round instance -> its job
   int64_t stream_sites = (int64_t)1 << 20;     // Ising jobs from this many sites up stream (if not resident)
   std::atomic<unsigned long long> attempts{0};
   std::atomic<unsigned long long> rounds{0};
   double busy = 0;
   std::FILE* trace = nullptr;  // per-round log when SPN_SERVER_TRACE names a file
+  // with a trace: a timing event after each launch group of a round (resident
+  // launch, EA launch, streaming job), its path and attempts, and the round's start
+  std::vector<cudaEvent_t> tev;
+  std::vector<std::pair<int, long long>> tmark;
+  cudaEvent_t tstart = nullptr;
   int* h_err = nullptr;        // pinned: the round's device error word, read back with the round
 };
 
@@ -216,6 +249,59 @@ int finish(spn_server_ctx* s, Job& j) {
   return SPN_OK;
 }
 
+// Trace only: a timing event on st after a launch group of path kind (0
+// resident, 1 EA, 2 streaming / generic) that carries att attempts.
+void trace_mark(spn_server_ctx* s, cudaStream_t st, int kind, long long att) {
+  if (!s->trace) return;
+  const size_t k = s->tmark.size();
+  if (k == s->tev.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return;
+    s->tev.push_back(ev);
+  }
+  cudaEventRecord(s->tev[k], st);
+  s->tmark.emplace_back(kind, att);
+}
+
+// Attempts per ns and SM while a job runs, by path: starting estimates (from
+// single-job and full-GPU runs of each path); resident jobs then carry the rate
+// measured in their last window.
+constexpr double kRateSm2d = 12.0, kRateSm3d = 7.0, kRateSmEa = 16.0;
+
+// Attempts per ns and SM equivalent a job starts with, by path.
+double default_rsm(const Job& j) { return j.ea ? kRateSmEa : (j.nd == 2 ? kRateSm2d : kRateSm3d); }
+
+// SM equivalents of a job that is not resident (scheduler thread).
+void estimate_other(Job& j) {
+  if (j.ea)
+    j.fsm = 1.0 / spn::ea_job_per_sm(j.ea);
+  else  // one launch per sweep over a share of the GPU
+    j.fsm = 0.25 * spn::device_sm_count();
+}
+
+// Launch shape of resident job j on clusters of cs CTAs, and its SM equivalents
+// (a cluster sits within one GPC, so it may take more SMs than it has CTAs).
+void res_shape(spn_server_ctx* s, Job& j, int cs) {
+  const int Lx = j.req.dims[0], Ly = j.req.dims[1], Lz = j.nd == 3 ? j.req.dims[2] : 1;
+  const int items = (Ly * Lz + cs - 1) / cs * ((Lx + 63) / 64);  // words of one parity per CTA
+  int t = 64;
+  while (t < 512 && t < items) t *= 2;
+  j.rcs = cs;
+  j.threads = t;
+  j.smem = spn::resident_smem(j.nd, Lx, Ly, Lz, cs);
+  // a CTA of more than a quarter of an SM's shared memory gets an SM of its own:
+  // CTAs of different launches that would share SMs leave unusable remainders,
+  // and one 512-thread CTA already keeps an SM nearly as busy as three
+  if (cs == 1 && j.smem > 56 * 1024) j.smem = std::max<size_t>(j.smem, 120 * 1024);
+  const auto key = std::make_tuple(j.nd, cs, t, j.smem);
+  auto it = s->max_ctas.find(key);
+  if (it == s->max_ctas.end())
+    it = s->max_ctas.emplace(key, std::max(1, spn::resident_max_ctas(j.nd, cs, t, j.smem))).first;
+  j.occ = it->second;
+  const double sms = spn::device_sm_count();
+  j.fsm = std::min(sms, sms * cs / j.occ);
+}
+
 // One round: a window of sweeps for every active job.  round_launch enqueues it
 // (after the admissions on aux) and returns; round_wait waits for it.
 int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
@@ -224,23 +310,97 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
     return SPN_E_CUDA;
   if ((e = cudaEventRecord(s->fork, s->main)) != cudaSuccess) return SPN_E_CUDA;
   for (cudaStream_t p : s->pool) cudaStreamWaitEvent(p, s->fork, 0);
-  // resident jobs: one persistent launch per (dimension, cluster size), all
-  // shapes together, longest window first; each launch on its own pool stream
-  std::map<std::pair<int, int>, std::vector<Job*>> groups;
-  std::vector<int64_t> win(act.size());
-  // a round is about round_attempts spread over the active jobs (at least
-  // window_attempts each), so a few large jobs still get long windows
-  const int64_t per_job = std::max<int64_t>(s->window_attempts, s->round_attempts / (int64_t)act.size());
-  for (size_t k = 0; k < act.size(); ++k) {
-    Job& j = *act[k];
+  if (s->trace) {
+    s->tmark.clear();
+    if (!s->tstart) cudaEventCreate(&s->tstart);
+    cudaEventRecord(s->tstart, s->main);
+  }
+  // Round plan.  The jobs given a window least recently go first, each a
+  // window of about round_ns of its own run time at its rate, while the SM
+  // equivalents of the windows chosen fit the GPU (a window shorter than
+  // round_ns counts in proportion); the others wait for the next round.  Every
+  // window then takes about as long as the round, so no launch of the round
+  // waits for one long instance, and no cluster waits for a second wave.  When
+  // the chosen windows leave SMs idle (few jobs), resident jobs with the most
+  // work left run on wider clusters (up to 16 CTAs): the lattice lives in HBM
+  // between windows, and the cluster size does not change the result.
+  ++s->round_no;
+  const double sms = spn::device_sm_count(), cap = s->fill * sms;
+  std::vector<int64_t> win(act.size(), 0);
+  std::vector<double> cost(act.size(), 0.0);
+  auto window = [&](Job& j, int64_t* w, double* c) {
     const int64_t units = j.ea ? 32 * j.N : j.N;  // attempts of one sweep (every replica of an EA job)
-    const int64_t per = std::max<int64_t>(1, per_job / std::max<int64_t>(1, units));
-    win[k] = std::min<int64_t>(per, j.req.nsweeps - j.done);
+    const double rate = (j.rsm > 0 ? j.rsm : default_rsm(j)) * j.fsm;  // attempts per ns
+    int64_t n = (int64_t)(s->round_ns * rate / (double)units);
+    n = std::max<int64_t>(1, std::min<int64_t>(n, j.req.nsweeps - j.done));
+    if (j.ea) n = std::min<int64_t>(n, 2000);  // sweeps of one EA launch
+    *w = n;
+    *c = j.fsm * std::min(1.0, (double)n * (double)units / (rate * s->round_ns));
+  };
+  std::vector<size_t> ord(act.size());
+  std::iota(ord.begin(), ord.end(), (size_t)0);
+  std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+    return act[x]->last_run != act[y]->last_run ? act[x]->last_run < act[y]->last_run : act[x]->ticket < act[y]->ticket;
+  });
+  double used = 0;
+  std::vector<size_t> chosen;
+  for (size_t k : ord) {
+    Job& j = *act[k];
+    j.window = 0;
+    if (j.cs > 0)
+      res_shape(s, j, j.cs);
+    else if (j.fsm <= 0)
+      estimate_other(j);
+    int64_t w;
+    double c;
+    window(j, &w, &c);
+    if (used > 0 && used + c > cap) continue;
+    used += c;
+    win[k] = w;
+    cost[k] = c;
+    chosen.push_back(k);
+  }
+  if (chosen.size() == act.size() && used < 0.75 * cap) {  // every job has a window: widen clusters, most work left first
+    std::vector<size_t> wide;
+    for (size_t k : chosen)
+      if (act[k]->cs > 0 && win[k] < act[k]->req.nsweeps - act[k]->done) wide.push_back(k);
+    std::stable_sort(wide.begin(), wide.end(), [&](size_t x, size_t y) {
+      return (act[x]->req.nsweeps - act[x]->done) * act[x]->N > (act[y]->req.nsweeps - act[y]->done) * act[y]->N;
+    });
+    for (size_t k : wide) {
+      Job& j = *act[k];
+      const int Lx = j.req.dims[0], Ly = j.req.dims[1], Lz = j.nd == 3 ? j.req.dims[2] : 1;
+      // at least one word per thread of a 512-thread CTA after the split
+      while (j.rcs * 2 <= spn::kMaxResidentCluster && (Ly * Lz) / (j.rcs * 2) * ((Lx + 63) / 64) >= 512 &&
+             spn::resident_supported(j.nd, Lx, Ly, Lz, j.rcs * 2)) {
+        const int rcs0 = j.rcs;
+        res_shape(s, j, rcs0 * 2);
+        int64_t w;
+        double c;
+        window(j, &w, &c);
+        if (used - cost[k] + c > 0.95 * cap) {
+          res_shape(s, j, rcs0);  // cached: no occupancy query
+          break;
+        }
+        used += c - cost[k];
+        cost[k] = c;
+        win[k] = w;
+      }
+    }
+  }
+  // resident jobs launch by (dimension, cluster size, threads, CTAs resident
+  // at once): a launch takes its group's largest shared memory, and within one
+  // such class that does not lower the occupancy its members were costed at
+  std::map<std::tuple<int, int, int, int>, std::vector<Job*>> groups;
+  for (size_t k : chosen) {
+    Job& j = *act[k];
     j.window = win[k];
-    if (j.cs > 0) groups[{j.nd, j.cs}].push_back(&j);
+    j.last_run = s->round_no;
+    if (j.cs > 0) groups[std::make_tuple(j.nd, j.rcs, j.threads, j.occ)].push_back(&j);
   }
   std::vector<spn::ResInst> inst;
   std::vector<int> order;
+  s->res_jobs.clear();
   struct Launch {
     int nd, cs, threads;
     size_t first, count, smem;
@@ -249,7 +409,7 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   for (auto& kv : groups) {
     std::vector<Job*>& js = kv.second;
     std::stable_sort(js.begin(), js.end(), [](const Job* x, const Job* y) { return x->N * x->window > y->N * y->window; });
-    Launch L{kv.first.first, kv.first.second, 64, inst.size(), js.size(), 0};
+    Launch L{std::get<0>(kv.first), std::get<1>(kv.first), 64, inst.size(), js.size(), 0};
     for (size_t k = 0; k < js.size(); ++k) {
       Job* j = js[k];
       spn::ResInst r{};
@@ -265,101 +425,135 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
       r.Ly = j->req.dims[1];
       r.Lz = j->nd == 3 ? j->req.dims[2] : 1;
       r.T = spn::make_thresholds(j->req.beta);
+      r.tns = nullptr;  // set below, once the clock array holds this round's instances
       inst.push_back(r);
+      s->res_jobs.push_back(j);
       order.push_back((int)k);
-      const int items = (r.Ly * r.Lz + L.cs - 1) / L.cs * ((r.Lx + 63) / 64);
-      L.threads = std::max(L.threads, std::min(512, (items + 31) / 32 * 32));
-      L.smem = std::max(L.smem, spn::resident_smem(L.nd, r.Lx, r.Ly, r.Lz, L.cs));
+      L.threads = std::max(L.threads, j->threads);
+      L.smem = std::max(L.smem, j->smem);
     }
     launches.push_back(L);
+  }
+  // EA jobs: one launch per lattice size and random-number mode (a u per slot
+  // for jobs with replica exchange), one CTA per job (at most 2000 sweeps a launch)
+  struct EaLaunch {
+    std::vector<spn::EaArgs> args;
+    int threads = 0;  // the same for every job of a group (same N and mode)
+    size_t smem = 0;
+    long long att = 0;  // attempts of the group's windows
+  };
+  std::map<int64_t, EaLaunch> ea_groups;  // key 2 N + (a u per slot)
+  for (size_t k = 0; k < act.size(); ++k)
+    if (act[k]->ea && win[k] > 0) {
+      spn::EaArgs a;
+      size_t smem = 0;
+      int threads = 0;
+      if (spn::ea_window_args(act[k]->ea, win[k], &a, &smem, &threads) != SPN_OK) return SPN_E_STATE;
+      EaLaunch& g = ea_groups[2 * act[k]->N + (a.u_per_slot ? 1 : 0)];
+      g.args.push_back(a);
+      g.threads = threads;
+      g.smem = smem;
+      g.att += 32LL * act[k]->N * win[k];
+    }
+  std::vector<spn::EaArgs> args;
+  std::vector<std::tuple<size_t, size_t, int, size_t, bool>> el;  // first, count, threads, smem, per-slot
+  std::vector<long long> el_att;
+  for (auto& kv : ea_groups) {
+    el.emplace_back(args.size(), kv.second.args.size(), kv.second.threads, kv.second.smem, (kv.first & 1) != 0);
+    el_att.push_back(kv.second.att);
+    args.insert(args.end(), kv.second.args.begin(), kv.second.args.end());
   }
   if (!inst.empty()) {
     if (inst.size() > s->inst_cap) {
       cudaFree(s->d_inst);
       cudaFree(s->d_order);
       cudaFree(s->d_counters);
+      cudaFree(s->d_tns);
+      cudaFreeHost(s->h_tns);
+      s->h_tns = nullptr;
       s->inst_cap = inst.size() * 2;
       if (cudaMalloc(&s->d_inst, s->inst_cap * sizeof(spn::ResInst)) != cudaSuccess ||
           cudaMalloc(&s->d_order, s->inst_cap * sizeof(int)) != cudaSuccess ||
-          cudaMalloc(&s->d_counters, s->inst_cap * sizeof(int)) != cudaSuccess)
+          cudaMalloc(&s->d_counters, s->inst_cap * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&s->d_tns, s->inst_cap * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+          cudaMallocHost(&s->h_tns, s->inst_cap * 2 * sizeof(unsigned long long)) != cudaSuccess)
         return SPN_E_NOMEM;
     }
+    for (size_t k = 0; k < inst.size(); ++k) inst[k].tns = s->d_tns + 2 * k;
     if (cudaMemcpyAsync(s->d_inst, inst.data(), inst.size() * sizeof(spn::ResInst), cudaMemcpyHostToDevice,
                         s->main) != cudaSuccess ||
         cudaMemcpyAsync(s->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s->main) !=
             cudaSuccess ||
         cudaMemsetAsync(s->d_counters, 0, launches.size() * sizeof(int), s->main) != cudaSuccess ||
-        cudaEventRecord(s->fork, s->main) != cudaSuccess)
+        cudaMemsetAsync(s->d_tns, 0, inst.size() * 2 * sizeof(unsigned long long), s->main) != cudaSuccess)
       return SPN_E_CUDA;
-    for (size_t li = 0; li < launches.size(); ++li) {
+  }
+  if (!args.empty()) {
+    if (args.size() > s->ea_cap) {
+      cudaFree(s->d_ea);
+      s->ea_cap = args.size() * 2;
+      if (cudaMalloc(&s->d_ea, s->ea_cap * sizeof(spn::EaArgs)) != cudaSuccess) return SPN_E_NOMEM;
+    }
+    if (cudaMemcpyAsync(s->d_ea, args.data(), args.size() * sizeof(spn::EaArgs), cudaMemcpyHostToDevice, s->main) !=
+        cudaSuccess)
+      return SPN_E_CUDA;
+  }
+  if (cudaEventRecord(s->fork, s->main) != cudaSuccess) return SPN_E_CUDA;
+  // Launch order: the largest clusters first, then the largest shared memory
+  // per CTA, on the pool's high-priority streams first.  A cluster needs free
+  // SMs within one GPC and a large CTA a nearly free SM: issued after many
+  // small CTAs, which spread over every SM, they would wait for those to finish.
+  std::vector<std::tuple<int, size_t, int>> issue;  // (cluster size, shared memory per CTA, launch li >= 0 / EA -1 - gi)
+  for (size_t li = 0; li < launches.size(); ++li) issue.emplace_back(launches[li].cs, launches[li].smem, (int)li);
+  for (size_t gi = 0; gi < el.size(); ++gi) issue.emplace_back(1, std::get<3>(el[gi]), -1 - (int)gi);
+  std::stable_sort(issue.begin(), issue.end(),
+                   [](const std::tuple<int, size_t, int>& x, const std::tuple<int, size_t, int>& y) {
+                     return std::get<0>(x) != std::get<0>(y) ? std::get<0>(x) > std::get<0>(y)
+                                                             : std::get<1>(x) > std::get<1>(y);
+                   });
+  size_t n_hi = 0, n_lo = 0;
+  const size_t half = s->pool.size() / 2;
+  for (size_t q = 0; q < issue.size(); ++q) {
+    const bool big = std::get<0>(issue[q]) > 1 || std::get<1>(issue[q]) > 100 * 1024;
+    cudaStream_t st = big ? s->pool[n_hi++ % half] : s->pool[half + n_lo++ % half];
+    cudaStreamWaitEvent(st, s->fork, 0);
+    const int which = std::get<2>(issue[q]);
+    if (which >= 0) {
+      const size_t li = (size_t)which;
       const Launch& L = launches[li];
-      cudaStream_t st = s->pool[li % s->pool.size()];
-      cudaStreamWaitEvent(st, s->fork, 0);
       spn::ResArgs a{};
       a.inst = s->d_inst + L.first;
       a.ninst = (int)L.count;
       a.order = s->d_order + L.first;  // local indices into the launch's slice
       a.counter = s->d_counters + li;
       a.err = s->d_err;
-      const int ctas =
-          std::max(L.cs, std::min<int>(spn::resident_max_ctas(L.nd, L.cs, L.threads, L.smem), (int)L.count * L.cs));
+      const auto key = std::make_tuple(L.nd, L.cs, L.threads, L.smem);
+      auto it = s->max_ctas.find(key);
+      if (it == s->max_ctas.end())
+        it = s->max_ctas.emplace(key, std::max(1, spn::resident_max_ctas(L.nd, L.cs, L.threads, L.smem))).first;
+      const int ctas = std::max(L.cs, std::min<int>(it->second, (int)L.count * L.cs));
       if ((e = spn::launch_resident(a, L.nd, L.cs, L.threads, ctas, L.smem, st)) != cudaSuccess) return SPN_E_CUDA;
-    }
-  }
-  // EA jobs: one launch per lattice size and random-number mode (a u per slot
-  // for jobs with replica exchange), one CTA per job (at most 2000 sweeps a launch)
-  {
-    struct EaLaunch {
-      std::vector<spn::EaArgs> args;
-      int threads = 0;  // the same for every job of a group (same N and mode)
-      size_t smem = 0;
-    };
-    std::map<int64_t, EaLaunch> ea_groups;  // key 2 N + (a u per slot)
-    for (size_t k = 0; k < act.size(); ++k)
-      if (act[k]->ea) {
-        win[k] = std::min<int64_t>(win[k], 2000);
-        act[k]->window = win[k];
-        spn::EaArgs a;
-        size_t smem = 0;
-        int threads = 0;
-        if (spn::ea_window_args(act[k]->ea, win[k], &a, &smem, &threads) != SPN_OK) return SPN_E_STATE;
-        EaLaunch& g = ea_groups[2 * act[k]->N + (a.u_per_slot ? 1 : 0)];
-        g.args.push_back(a);
-        g.threads = threads;
-        g.smem = smem;
+      if (s->trace) {
+        long long att = 0;
+        for (size_t k = L.first; k < L.first + L.count; ++k)
+          att += (long long)inst[k].Lx * inst[k].Ly * inst[k].Lz * inst[k].nsweeps;
+        trace_mark(s, st, 0, att);
       }
-    std::vector<spn::EaArgs> args;
-    std::vector<std::tuple<size_t, size_t, int, size_t, bool>> el;  // first, count, threads, smem, per-slot
-    for (auto& kv : ea_groups) {
-      el.emplace_back(args.size(), kv.second.args.size(), kv.second.threads, kv.second.smem, (kv.first & 1) != 0);
-      args.insert(args.end(), kv.second.args.begin(), kv.second.args.end());
-    }
-    if (!args.empty()) {
-      if (args.size() > s->ea_cap) {
-        cudaFree(s->d_ea);
-        s->ea_cap = args.size() * 2;
-        if (cudaMalloc(&s->d_ea, s->ea_cap * sizeof(spn::EaArgs)) != cudaSuccess) return SPN_E_NOMEM;
-      }
-      if (cudaMemcpyAsync(s->d_ea, args.data(), args.size() * sizeof(spn::EaArgs), cudaMemcpyHostToDevice,
-                          s->main) != cudaSuccess ||
-          cudaEventRecord(s->fork, s->main) != cudaSuccess)
+    } else {
+      const size_t gi = (size_t)(-1 - which);
+      size_t first, count, smem;
+      int threads;
+      bool ps;
+      std::tie(first, count, threads, smem, ps) = el[gi];
+      if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, 3, ps, threads, smem, st)) != cudaSuccess)
         return SPN_E_CUDA;
-      for (size_t gi = 0; gi < el.size(); ++gi) {
-        size_t first, count, smem;
-        int threads;
-        bool ps;
-        std::tie(first, count, threads, smem, ps) = el[gi];
-        cudaStream_t st = s->pool[(s->pool.size() - 1 - gi % s->pool.size())];
-        cudaStreamWaitEvent(st, s->fork, 0);
-        if ((e = spn::launch_ea_jobs(s->d_ea + first, (int)count, 3, ps, threads, smem, st)) != cudaSuccess)
-          return SPN_E_CUDA;
-      }
+      trace_mark(s, st, 1, el_att[gi]);
     }
   }
   // large Ising lattices: own launches on the stream pool
   for (size_t k = 0; k < act.size(); ++k) {
     Job& j = *act[k];
-    if (j.cs > 0 || j.ea) continue;
+    if (j.cs > 0 || j.ea || win[k] == 0) continue;
     cudaStream_t st = s->pool[j.stream_slot];
     const int64_t w = win[k];
     spn::Lattice g;
@@ -381,6 +575,7 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
       }
       if (e != cudaSuccess) return SPN_E_CUDA;
     }
+    trace_mark(s, st, 2, (long long)j.N * w);
   }
   for (size_t p = 0; p < s->pool.size(); ++p) {
     cudaEventRecord(s->pool_done[p], s->pool[p]);
@@ -388,12 +583,38 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   }
   if (cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->main) != cudaSuccess)
     return SPN_E_CUDA;
+  if (!s->res_jobs.empty() &&
+      cudaMemcpyAsync(s->h_tns, s->d_tns, s->res_jobs.size() * 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                      s->main) != cudaSuccess)
+    return SPN_E_CUDA;
   return SPN_OK;
 }
 
 int round_wait(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   if (cudaStreamSynchronize(s->main) != cudaSuccess) return SPN_E_CUDA;
   if (*s->h_err) return SPN_E_TIMEOUT;  // a bounded device wait ran out
+  // the rate each resident job ran at in this window sizes its next one
+  unsigned long long first = ~0ull, last = 0;
+  for (size_t k = 0; k < s->res_jobs.size(); ++k) {
+    Job& j = *s->res_jobs[k];
+    const unsigned long long t0 = s->h_tns[2 * k], t1 = s->h_tns[2 * k + 1];
+    // down at once, up by at most 10% a window: a CTA that ran alone on an SM
+    // it will share next time would otherwise stretch the next round
+    if (t0 && t1 > t0 + 100000ull) {
+      const double measured = (double)j.N * (double)j.window / ((double)(t1 - t0) * j.fsm);
+      j.rsm = std::min(measured, 1.1 * (j.rsm > 0 ? j.rsm : default_rsm(j)));
+    }
+    if (t0) {
+      first = std::min(first, t0);
+      last = std::max(last, t0);
+    }
+  }
+  if (last > first) {  // an instance that started a quarter window late waited for a second wave
+    if ((double)(last - first) > 0.25 * s->round_ns)
+      s->fill = std::max(0.5, 0.9 * s->fill);
+    else
+      s->fill = std::min(1.0, 1.02 * s->fill);
+  }
   std::lock_guard<std::mutex> lock(s->mu);
   for (auto& jp : act) {
     Job& j = *jp;
@@ -498,8 +719,19 @@ void scheduler(spn_server_ctx* s) {
           att += (long long)j->N * j->window * (j->ea ? 32 : 1);
           if (j->ea) ++ne; else if (j->cs > 0) ++nr; else if (j->streaming) ++ns; else ++no;
         }
-        std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d %.4f %.4f %.4f %zu\n", t0, t1 - t0, act.size(), att, nr,
-                     ns, ne, no, t_launched - t0, t_host - t_launched, t1 - t_host, admitted_now.size());
+        // then per path (resident, EA, streaming): the latest completion after the
+        // round's start (ms) and the path's attempts; then the planned share of the SMs
+        float tend[3] = {0, 0, 0};
+        long long tatt[3] = {0, 0, 0};
+        for (size_t k = 0; k < s->tmark.size(); ++k) {
+          float ms = 0;
+          if (cudaEventElapsedTime(&ms, s->tstart, s->tev[k]) == cudaSuccess)
+            tend[s->tmark[k].first] = std::max(tend[s->tmark[k].first], ms);
+          tatt[s->tmark[k].first] += s->tmark[k].second;
+        }
+        std::fprintf(s->trace, "%.4f %.4f %zu %lld %d %d %d %d %.4f %.4f %.4f %zu %.2f %lld %.2f %lld %.2f %lld %.3f\n", t0,
+                     t1 - t0, act.size(), att, nr, ns, ne, no, t_launched - t0, t_host - t_launched, t1 - t_host,
+                     admitted_now.size(), tend[0], tatt[0], tend[1], tatt[1], tend[2], tatt[2], s->fill);
         std::fflush(s->trace);
       }
     }
@@ -539,10 +771,14 @@ int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
     delete s;
     return sfail(SPN_E_CUDA, "server set-up failed");
   }
+  // the first half of the pool at the greatest priority: a round's cluster and
+  // large-CTA launches go there, so the block scheduler places them first
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   for (int i = 0; i < kPoolStreams; ++i) {
     cudaStream_t st;
     cudaEvent_t ev;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i < kPoolStreams / 2 ? prio_greatest : prio_least);
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     s->pool.push_back(st);
     s->pool_done.push_back(ev);
@@ -584,7 +820,7 @@ int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket) {
     g.Lz = ext[2];
     g.N = j->N;
     // the tallest dividing band (3D) whose bit-packed streaming geometry fits one CTA
-    j->cs = spn::resident_cluster_size(j->nd, ext[0], ext[1], ext[2]);
+    j->cs = spn::resident_cluster_size(j->nd, ext[0], ext[1], ext[2], spn::kMaxResidentCluster);
     for (int ty = j->nd == 3 ? 32 : 1; j->cs == 0 && j->N >= s->stream_sites && ty >= 1 && !j->streaming;
          ty -= (j->nd == 3 ? 2 : 1)) {
       if (j->nd == 3 && (ty < 2 || ext[1] % ty)) continue;
@@ -682,11 +918,15 @@ int spn_server_destroy(spn_server s) {
   cudaFree(s->d_ea);
   cudaFree(s->d_order);
   cudaFree(s->d_counters);
+  cudaFree(s->d_tns);
+  cudaFreeHost(s->h_tns);
   cudaFree(s->d_err);
   cudaEventDestroy(s->fork);
   cudaEventDestroy(s->aux_ev);
   cudaFreeHost(s->h_err);
   if (s->trace) std::fclose(s->trace);
+  for (cudaEvent_t ev : s->tev) cudaEventDestroy(ev);
+  if (s->tstart) cudaEventDestroy(s->tstart);
   cudaStreamDestroy(s->main);
   cudaStreamDestroy(s->aux);
   delete s;

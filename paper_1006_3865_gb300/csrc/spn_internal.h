@@ -108,6 +108,7 @@ struct ResInst {
   int init_hot;                // 1: hot start from Philox; 0: start from `spins`
   int Lx, Ly, Lz;              // extents (Lz = 1 in 2D); the launch's shared memory fits the largest
   DevThr T;
+  unsigned long long* tns;     // [2] device clock (ns) at the instance's start and end; may be null
 };
 
 struct ResArgs {
@@ -120,8 +121,10 @@ struct ResArgs {
 
 bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs);
 size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs);
-int resident_cluster_size(int nd, int Lx, int Ly, int Lz);  // 0: does not fit a cluster of <= 8 CTAs
-int resident_max_ctas(int nd, int cs, int threads, size_t smem);
+constexpr int kMaxResidentCluster = 16;  // 9 .. 16: non-portable cluster sizes
+// smallest cluster size (1, 2, 4, ..., max_cs) whose CTAs hold the lattice; 0: none
+int resident_cluster_size(int nd, int Lx, int Ly, int Lz, int max_cs = 8);
+int resident_max_ctas(int nd, int cs, int threads, size_t smem);  // CTAs resident at once (whole clusters)
 cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, size_t smem, cudaStream_t st);
 
 int device_sm_count();
@@ -202,6 +205,7 @@ cudaError_t launch_dp_swap(uint32_t* dp, const uint32_t* X, int N, int ngroups, 
 // parameter block of the next `nsweeps` sweeps of h (its sweep counter
 // advances), and one launch running many such blocks, one CTA each.
 int ea_window_args(struct spn_ctx* h, int64_t nsweeps, EaArgs* out, size_t* smem, int* threads);
+int ea_job_per_sm(struct spn_ctx* h);  // CTAs of a one-sample EA handle's job kernel resident per SM
 cudaError_t launch_ea_jobs(const EaArgs* d_list, int n, int nd, bool ps, int threads, size_t smem, cudaStream_t st);
 // Server admissions of single-sample EA batches in two parts: the host part
 // (validation, bond bytes, exchange tables; no CUDA call, any thread) and the

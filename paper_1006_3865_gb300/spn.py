@@ -154,6 +154,11 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"\b(spn_[a-z0-9_]+)\s*\(", text)))
 
 
+# A server round runs more concurrent launches than CUDA's default 8 hardware
+# work queues; this takes effect only if no CUDA context exists yet.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+
 def load(path: str | None = None):
     """Load libspn.so (build it first with paper_1006_3865_gb300.build.build())."""
     global _lib

@@ -38,7 +38,8 @@ _MIX = [((32, 32), 2.2, 37), ((64, 64), 2.4, 50), ((128, 64), 1.9, 20), ((16, 8)
         ((1024, 256), 2.27, 12), ((16, 16, 16), 1 / 4.5, 25), ((64, 16, 8), 1 / 4.4, 9), ((256, 64), 2.1, 700),
         ((8192, 64), 2.3, 3), ((192, 128), 2.0, 6), ((6, 4), 2.5, 41), ((6, 4, 2), 1 / 4.0, 33),
         ((4096, 4096), 2.27, 3), ((256, 256, 256), 1 / 4.51, 2), ((1030, 1026), 2.27, 4),
-        ((102, 104, 100), 1 / 4.51, 3), ((1998, 3000), 3.0, 2), ((3650, 3650), 2.27, 2)]
+        ((102, 104, 100), 1 / 4.51, 3), ((1998, 3000), 3.0, 2), ((3650, 3650), 2.27, 2),
+        ((6002, 5000), 2.27, 2)]  # 3.8 MB of bits: more than 16 CTAs hold, so it streams
 
 
 def _submit_ising(srv, k, dims, T, ns):
@@ -65,7 +66,7 @@ def test_mix_matches_oracle_and_alone():
         E, M = oracle.observables(d, so)
         assert (res.E, res.M) == (E, M)
     # the same jobs alone, one at a time
-    for k in (0, 4, 7, 10, 12, 14, 15, 17):
+    for k in (0, 4, 7, 10, 12, 13, 14, 15, 17, 18):
         d, T, ns = _MIX[k]
         alone = spn.Server(1 << 30)
         t = _submit_ising(alone, k, d, T, ns)
