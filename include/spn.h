@@ -449,10 +449,15 @@ typedef struct spn_result {
 typedef struct spn_server_ctx* spn_server;
 
 /* Start a server that admits jobs while their device memory (lattices, ping-
- * pong buffers, accumulators) fits hbm_budget_bytes.  A scheduler thread
- * advances every admitted job by a window of sweeps per round; jobs of the same
- * lattice shape share one persistent resident launch, the others run on a pool
- * of streams, and jobs arriving during a round join the next one. */
+ * pong buffers, accumulators) fits hbm_budget_bytes.  A scheduler thread runs
+ * rounds: each job chosen for a round (least recently run first, while their
+ * SM equivalents fit the GPU) advances by a window of about 30 ms of its own run
+ * time.  Ising lattices whose bits fit a cluster of up to 16 CTAs share
+ * persistent resident launches, larger ones stream, EA jobs take one CTA each;
+ * the launches run on a pool of streams, and jobs arriving during a round join
+ * a later one.  Loading the library sets CUDA_DEVICE_MAX_CONNECTIONS to 32
+ * unless the process has set it (effective only before a CUDA context exists):
+ * a round runs more concurrent launches than the default 8 hardware queues. */
 int spn_server_create(spn_server* out, size_t hbm_budget_bytes);
 
 /* Queue a request (copied) and return its ticket at once; never waits for the

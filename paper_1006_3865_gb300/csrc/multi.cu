@@ -476,7 +476,7 @@ int spn_multi_groups(spn_multi m, int32_t* out, size_t count) {
 int spn_multi_set_launch(spn_multi m, int32_t group, int32_t cs, int32_t threads) {
   if (!m || group < 0 || group >= (int)m->groups.size()) return mfail(SPN_E_ARG, "bad group index");
   Group& g = m->groups[group];
-  if (threads < 32 || threads > 512 || threads % 32 || !spn::resident_supported(g.nd, g.Lx, g.Ly, g.Lz, cs) ||
+  if (threads < 32 || threads > 512 || threads % 32 || cs > 8 || !spn::resident_supported(g.nd, g.Lx, g.Ly, g.Lz, cs) ||
       (cs & (cs - 1)))
     return mfail(SPN_E_ARG, "cluster size must be 1, 2, 4 or 8 and fit; threads a multiple of 32 up to 512");
   if (cudaStreamSynchronize(m->st) != cudaSuccess) return mfail(SPN_E_CUDA, "synchronising");
