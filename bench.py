@@ -75,6 +75,7 @@ def _args():
                    help="run only a few sweeps of one lattice (for ncu captures) and exit")
     p.add_argument("--profile-sweeps", type=int, default=3)
     p.add_argument("--profile-L", type=int, default=0, help="lattice extent of a 2d / packed2d profile case")
+    p.add_argument("--profile-tiling", default="", help="TY,R,SEG streaming tiling of a 2d / 3d profile case")
     p.add_argument("--forms", default="batched,ea,served,dc,dc_tau,packed,overlap,heis",
                    help="extra forms measured after the plain step (comma list; empty for none)")
     p.add_argument("--forms-only", action="store_true", help="measure only the extra forms")
@@ -136,6 +137,8 @@ def run_profile_case(a):
         beta = BETA_3D
     if a.profile_case.startswith("packed"):
         lat.path = spn.PATH_PACKED
+    if a.profile_tiling:
+        lat.set_tiling(*(int(x) for x in a.profile_tiling.split(",")))
     lat.sweep(beta, a.profile_sweeps)
     print("profile case", a.profile_case, "E, M =", lat.observables(), flush=True)
     lat.close()
