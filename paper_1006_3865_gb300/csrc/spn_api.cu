@@ -465,6 +465,27 @@ int spn_sweep_dc(spn_handle h, double beta, int64_t nsweeps, const int32_t* tile
   if ((rc = unpack_if_live(h))) return rc;
   const spn::DevThr T = spn::make_thresholds(beta);
   const spn::PhiloxKeys K = spn::philox_keys(h->seed);
+  // one hit on rows of at least 2048 sites in whole words: the band-parallel
+  // wavefront form (one read and one write of every spin a sweep, ping-pong
+  // buffers); otherwise a CTA per tile, in place, one launch per tile parity
+  if (spn::dcwave_supported(h->g, tile[0], tile[1], hits)) {
+    if ((rc = ensure_stream_buffers(h))) return rc;
+    const int nseg = spn::dcwave_default_segments(h->g, hits);
+    for (int64_t t = 0; t < nsweeps; ++t) {
+      const uint32_t sweep = (uint32_t)(h->sweeps + t);
+      unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);
+      const cudaError_t e = spn::launch_sweep_dcwave(h->g, h->spins[h->cur], h->spins[h->cur ^ 1], tile[0], tile[1],
+                                                     hits, nseg, T, K, h->stream_id, sweep, acc, h->d_err, h->st,
+                                                     std::exchange(h->expire_polls, 0u));
+      if (e != cudaSuccess) {
+        h->sweeps += (uint64_t)t;
+        return cuda_fail(e, "double-checkerboard launch");
+      }
+      h->cur ^= 1;
+    }
+    h->sweeps += (uint64_t)nsweeps;
+    return SPN_OK;
+  }
   for (int64_t t = 0; t < nsweeps; ++t) {
     const uint32_t sweep = (uint32_t)(h->sweeps + t);
     unsigned long long* acc = h->d_acc + 2 * (int64_t)(sweep - h->folded);

@@ -66,6 +66,12 @@ cudaError_t launch_unpack(const Lattice& g, const uint32_t* w, int8_t* s, cudaSt
 // number of tiles per axis, dense int8 lattice, no bonds): both tile parities
 // of one sweep, `hits` updates of each colour per tile.
 bool dc_supported(const Lattice& g, int Tx, int Ty, int Tz);
+// the band-parallel form of the double checkerboard (dcwave.cu): 2D rows of >= 2048 sites in whole words, one hit
+bool dcwave_supported(const Lattice& g, int Tx, int Ty, int hits);
+int dcwave_default_segments(const Lattice& g, int hits);
+cudaError_t launch_sweep_dcwave(const Lattice& g, const int8_t* in, int8_t* out, int Tx, int Ty, int hits, int nseg,
+                                const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                unsigned long long* acc, int* err, cudaStream_t st, uint32_t expire_polls = 0);
 cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz, int hits, const DevThr& T,
                             const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                             cudaStream_t st);

@@ -56,7 +56,9 @@ def _run(dims, seed, plan, stream=0):
 
 @pytest.mark.parametrize("dims,tile,hits", [((128, 64), (64, 8), 1), ((128, 64), (64, 8), 3), ((256, 96), (64, 12), 2),
                                             ((256, 40), (128, 10), 4), ((128, 6), (64, 3), 2),
-                                            ((128, 128), (64, 64), 4), ((128, 128), (64, 16), 2)])
+                                            ((128, 128), (64, 64), 4), ((128, 128), (64, 16), 2),
+                                            ((2048, 40), (128, 2), 2), ((3200, 48), (320, 6), 2),
+                                            ((3072, 48), (768, 12), 3), ((4096, 32), (256, 4), 4)])
 def test_dc_2d(dims, tile, hits):
     _run(dims, inputs.unit_seed(31), [("dc", 1.0 / inputs.TC_2D, 7, tile, hits)], stream=3)
 
@@ -88,6 +90,34 @@ def test_dc_rejects_bad_tiles():
     lat.close()
 
 
+# one hit on rows of >= 2048 sites in whole words takes the band-parallel
+# wavefront form: one-row and 2-row tiles (every other step straddles a tile
+# row), bands of 30 words with a ragged last band (50 words), segments of one
+# row (the default for 40 rows: more warps than rows) and of many
+@pytest.mark.parametrize("dims,tile,hits", [((2048, 64), (64, 8), 1), ((2048, 40), (64, 2), 1), ((2048, 40), (128, 2), 1),
+                                            ((2048, 32), (64, 1), 1), ((3200, 40), (64, 4), 1), ((3200, 48), (320, 6), 1),
+                                            ((3072, 48), (768, 12), 1), ((4096, 32), (256, 4), 1),
+                                            ((2048, 256), (1024, 32), 1), ((4096, 512), (256, 64), 1)])
+def test_dc_wavefront_2d(dims, tile, hits):
+    _run(dims, inputs.unit_seed(35), [("dc", 1.0 / inputs.TC_2D, 3, tile, hits)], stream=5)
+
+
+def test_dc_wavefront_special_temperatures_and_mix():
+    dims, tile = (2048, 48), (64, 6)
+    s0 = oracle.init_hot(dims, 11)
+    s = _run(dims, 11, [("dc", 0.0, 1, tile, 1)])
+    assert np.array_equal(s, -s0)  # beta = 0: every site flips once
+    _run(dims, 11, [("dc", float("inf"), 2, tile, 1)])
+    # the two dc kernels (one hit: wavefront; three: tile) and the canonical sweep in one chain
+    plan = [("sweep", 0.44, 2), ("dc", 0.5, 2, (128, 8), 1), ("sweep", 0.3, 1), ("dc", 0.41, 2, (64, 4), 3)]
+    _run((2048, 64), inputs.unit_seed(36), plan, stream=2)
+
+
 def test_dc_full_size_2d_L16384():
     """Full 2D L = 16384 lattice with the benchmark's tiling."""
     _run((16384, 16384), inputs.unit_seed(34), [("dc", 1.0 / inputs.TC_2D, 2, (256, 64), 2)])
+
+
+def test_dc_full_size_2d_L16384_one_hit():
+    """The benchmark's k = 1 case on the wavefront form."""
+    _run((16384, 16384), inputs.unit_seed(37), [("dc", 1.0 / inputs.TC_2D, 2, (64, 64), 1)])
