@@ -172,11 +172,7 @@ __global__ void __launch_bounds__(512) k_sweep_dc(const __grid_constant__ DcArgs
           }
           compare_top<NC, 4 * kDcFirstCalls>(acc, eq, pl, a.tm);
         }
-        uint32_t pend = 0;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) pend |= eq[k];
-        if (__any_sync(0xffffffffu, pend != 0u))
-          acc |= rest_planes<NC>(eq, a.tm, a.K, c0, c1, c2, a.stream_id, kDcFirstCalls);
+        acc |= tail_planes<NC, kDcFirstCalls>(eq, a.tm, a.K, c0, c1, c2, a.stream_id);
         if (live) {
           *wp = b ^ acc;  // only this thread touches this colour-c word in this step
           tally<ND>(acc, b, s0, s1, s2, de, dm);

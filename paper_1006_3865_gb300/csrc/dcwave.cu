@@ -219,8 +219,7 @@ __global__ void __launch_bounds__(32 * kDwWarps, 3) k_sweep_dcwave(const __grid_
     }
     if (!store) eq[0] = eq[1] = 0u;  // a lane without an update asks for no further planes
     compare_top<NC, 4 * kDwFirst>(acc, eq, pl, a.tm);
-    if (__any_sync(0xffffffffu, (eq[0] | eq[1]) != 0u))
-      acc |= rest_planes<NC>(eq, a.tm, a.K, c0, c1, c2, a.stream_id, kDwFirst);
+    acc |= tail_planes<NC, kDwFirst>(eq, a.tm, a.K, c0, c1, c2, a.stream_id);
     if (!store) return;
     const uint32_t nb = b ^ acc;
     r0[ws] = nb;

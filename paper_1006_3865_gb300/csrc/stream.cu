@@ -311,11 +311,7 @@ __global__ void __launch_bounds__(max_threads(ND), min_ctas(ND)) k_sweep_stream(
         }
         compare_top<NC, 4 * kFirstCalls>(acc, eq, pl, a.tm);
       }
-      uint32_t pend = 0;
-#pragma unroll
-      for (int k = 0; k < NC; ++k) pend |= eq[k];
-      if (__any_sync(0xffffffffu, pend != 0u))
-        acc |= rest_planes<NC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id, kFirstCalls);
+      acc |= tail_planes<NC, kFirstCalls>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id);
       if (live) {
         const uint32_t nb = b ^ acc;
         bits[woff] = nb;

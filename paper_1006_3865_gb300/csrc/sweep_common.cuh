@@ -270,4 +270,56 @@ __device__ __noinline__ uint32_t rest_planes(uint32_t (&eq)[NC], const uint32_t 
   return acc;
 }
 
+
+// Philox4x32-10 with the rounds in a loop and the round keys formed as it goes
+// (k0 + r * 0x9E3779B9, k1 + r * 0xBB67AE85, as philox_keys): the same words as
+// philox10 in a handful of registers, for rarely taken paths.
+__device__ __forceinline__ U4 philox10_rolled(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1) {
+#pragma unroll 1
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// The decision for the sites still tied after FIRST first-stage calls (whole
+// warps).  The next call, which a warp with a tie nearly always needs alone, is
+// inlined with constant plane indices and a rolled Philox (few registers, so
+// the hot path does not spill); only a tie left after it (about 2^-16 of a
+// class's sites) takes the function call for the planes beyond.
+template <int NC, int FIRST>
+__device__ __forceinline__ uint32_t tail_planes(uint32_t (&eq)[NC], const uint32_t (*tm)[32], const PhiloxKeys& K,
+                                                uint32_t c0, uint32_t c1, uint32_t c2, uint32_t stream_id) {
+  uint32_t pend = 0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) pend |= eq[k];
+  if (!__any_sync(0xffffffffu, pend != 0u)) return 0u;
+  const U4 P = philox10_rolled(c0 + (uint32_t)FIRST, c1, c2, stream_id, K.k0[0], K.k1[0]);
+  const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
+  uint32_t acc = 0;
+  pend = 0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t t = tm[k][4 * FIRST + j];
+      acc |= eq[k] & ~pl[j] & t;
+      eq[k] &= ~(pl[j] ^ t);
+    }
+    pend |= eq[k];
+  }
+  if (__any_sync(0xffffffffu, pend != 0u)) acc |= rest_planes<NC>(eq, tm, K, c0, c1, c2, stream_id, FIRST + 1);
+  return acc;
+}
+
 }  // namespace spn

@@ -205,8 +205,7 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
       pl[4 * call + 3] = P.w;
     }
     compare_top<NC, 4 * FC>(acc, eq, pl, a.tm);
-    if (__any_sync(0xffffffffu, (eq[0] | eq[1]) != 0u))
-      acc |= rest_planes<NC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id, FC);
+    acc |= tail_planes<NC, FC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id);
     const uint32_t nb = b ^ acc;
     if (c == 0 || owned) r0[ws] = nb;
     if (owned && li >= 2 && li < H + 2) tally<2>(acc, b, s0, s1, s2, de, dm);

@@ -234,8 +234,7 @@ __global__ void __launch_bounds__(32 * kW3Warps, 3) k_sweep_wave3(const __grid_c
       pl[4 * call + 3] = P.w;
     }
     compare_top<NC, 4 * kW3First>(acc, eq, pl, a.tm);
-    if (__any_sync(0xffffffffu, (eq[0] | eq[1] | eq[2]) != 0u))
-      acc |= rest_planes<NC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id, kW3First);
+    acc |= tail_planes<NC, kW3First>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id);
     const uint32_t nb = b ^ acc;
     if (ustore) p0[ws] = nb;
     if (!halo && li >= 2 && li < H + 2) tally<3>(acc, b, s0, s1, s2, de, dm);
