@@ -35,7 +35,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 template <int ND, bool CLUSTER>
-__global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
+__global__ void __launch_bounds__(512) k_resident(ResArgs a) {  // every caller launches at most 512 threads
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_idx;
   __shared__ long long s_em[2];
@@ -233,28 +233,20 @@ __global__ void __launch_bounds__(1024) k_resident(ResArgs a) {
             flips |= always ? cls[k] : 0u;
             eq[k] = always ? 0u : cls[k];
           }
-          // Most significant plane first, one Philox call (four planes) at a
-          // time until no site of the warp ties: tied holds the sites whose u
-          // matches their class's threshold on every plane so far; a 0 bit of u
-          // where the threshold has a 1 accepts, the opposite rejects.  The
-          // classes are disjoint, so one selected threshold plane serves them all.
-          uint32_t tied = 0;
+          // u < t on the top 12 planes of u (three Philox calls, drawn together
+          // so their rounds interleave) with the threshold plane of each site's
+          // class, then the planes beyond for a warp with a tie
+          uint32_t pl[12];
 #pragma unroll
-          for (int k = 0; k < ND; ++k) tied |= eq[k];
-#pragma unroll 1
-          for (uint32_t call = 0; call < 8u && __any_sync(0xffffffffu, tied != 0u); ++call) {
-            const U4 P = philox10(c0 + call, sweep, c2, in.stream, K);
-            const uint32_t pl[4] = {P.x, P.y, P.z, P.w};
-            const uint32_t* tm0 = &s_tm[0][4 * call];
-#pragma unroll
-            for (int jp = 0; jp < 4; ++jp) {
-              uint32_t t = tm0[jp];
-#pragma unroll
-              for (int k = 1; k < ND; ++k) t = (eq[k] & tm0[32 * k + jp]) | (~eq[k] & t);
-              flips |= tied & ~pl[jp] & t;
-              tied &= ~(pl[jp] ^ t);
-            }
+          for (int call = 0; call < 3; ++call) {
+            const U4 P = philox10(c0 + (uint32_t)call, sweep, c2, in.stream, K);
+            pl[4 * call + 0] = P.x;
+            pl[4 * call + 1] = P.y;
+            pl[4 * call + 2] = P.z;
+            pl[4 * call + 3] = P.w;
           }
+          compare_top<ND, 12>(flips, eq, pl, s_tm);
+          flips |= tail_planes<ND, 3>(eq, s_tm, K, c0, sweep, c2, in.stream);
           if (live) {
             tally<ND>(flips, b, s0, s1, s2, de, dm);
             *wp = b ^ flips;  // only this thread reads or writes this colour-c word in this phase
