@@ -153,6 +153,14 @@ struct spn_server_ctx {
   std::vector<std::pair<int, long long>> tmark;
   cudaEvent_t tstart = nullptr;
   int* h_err = nullptr;        // pinned: the round's device error word, read back with the round
+  // Finished jobs are read back on a thread and a high-priority stream of
+  // their own: the next round starts at once, the read-back's small kernels
+  // slip in beside it, and its copies to the host overlap the round.
+  std::thread reader;
+  std::deque<std::shared_ptr<Job>> rb_queue;  // guarded by mu
+  std::condition_variable rb_cv;
+  bool rb_stop = false;
+  cudaStream_t rb = nullptr;
 };
 
 namespace {
@@ -164,14 +172,14 @@ size_t job_bytes(const Job& j) {
   return b;
 }
 
-// A job's device memory goes back in stream order on aux: its last kernels ran
-// in a round that has completed, or on aux itself (read-back).
-void release(spn_server_ctx* s, Job& j) {
-  if (j.d_spins) cudaFreeAsync(j.d_spins, s->aux);
-  if (j.d_scratch) cudaFreeAsync(j.d_scratch, s->aux);
-  if (j.d_p0) cudaFreeAsync(j.d_p0, s->aux);
-  if (j.d_p1) cudaFreeAsync(j.d_p1, s->aux);
-  if (j.d_acc) cudaFreeAsync(j.d_acc, s->aux);
+// A job's device memory goes back in stream order on st: its last kernels ran
+// in a round that has completed, or on st itself (read-back, admission).
+void release(Job& j, cudaStream_t st) {
+  if (j.d_spins) cudaFreeAsync(j.d_spins, st);
+  if (j.d_scratch) cudaFreeAsync(j.d_scratch, st);
+  if (j.d_p0) cudaFreeAsync(j.d_p0, st);
+  if (j.d_p1) cudaFreeAsync(j.d_p1, st);
+  if (j.d_acc) cudaFreeAsync(j.d_acc, st);
   j.d_spins = j.d_scratch = nullptr;
   j.d_p0 = j.d_p1 = nullptr;
   j.d_acc = nullptr;
@@ -211,9 +219,9 @@ int admit(spn_server_ctx* s, Job& j) {
   return SPN_OK;
 }
 
-// Final E, M and the host copies of a finished job (its rounds have completed;
-// the read-back is ordered on aux, so it overlaps the next round).
-int finish(spn_server_ctx* s, Job& j) {
+// Final E, M and the host copies of a finished job (its rounds have completed),
+// ordered on st.
+int finish(Job& j, cudaStream_t st) {
   if (j.ea) {
     const size_t n = (size_t)j.N;
     j.words.resize(n);
@@ -236,13 +244,13 @@ int finish(spn_server_ctx* s, Job& j) {
   g.Ly = j.req.dims[1];
   g.Lz = j.nd == 3 ? j.req.dims[2] : 1;
   g.N = j.N;
-  if (j.streaming && spn::launch_unpack(g, j.d_p0, j.d_spins, s->aux) != cudaSuccess) return SPN_E_CUDA;
-  if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, s->aux) != cudaSuccess) return SPN_E_CUDA;
+  if (j.streaming && spn::launch_unpack(g, j.d_p0, j.d_spins, st) != cudaSuccess) return SPN_E_CUDA;
+  if (spn::launch_observables(g, j.d_spins, j.d_acc, nullptr, st) != cudaSuccess) return SPN_E_CUDA;
   unsigned long long em[2];
   j.spins.resize((size_t)j.N);
-  if (cudaMemcpyAsync(em, j.d_acc, 16, cudaMemcpyDeviceToHost, s->aux) != cudaSuccess ||
-      cudaMemcpyAsync(j.spins.data(), j.d_spins, (size_t)j.N, cudaMemcpyDeviceToHost, s->aux) != cudaSuccess ||
-      cudaStreamSynchronize(s->aux) != cudaSuccess)
+  if (cudaMemcpyAsync(em, j.d_acc, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(j.spins.data(), j.d_spins, (size_t)j.N, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return SPN_E_CUDA;
   j.E = (int64_t)em[0];
   j.M = (int64_t)em[1];
@@ -624,10 +632,10 @@ int round_wait(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
   return SPN_OK;
 }
 
-// Mark a finished (or failed) job done and give its bytes back.
-void retire(spn_server_ctx* s, const std::shared_ptr<Job>& j, int rc) {
-  int frc = rc ? rc : finish(s, *j);
-  release(s, *j);
+// Mark a finished (or failed) job done and give its bytes back, ordered on st.
+void retire(spn_server_ctx* s, const std::shared_ptr<Job>& j, int rc, cudaStream_t st) {
+  int frc = rc ? rc : finish(*j, st);
+  release(*j, st);
   std::lock_guard<std::mutex> lock(s->mu);
   j->status = frc;
   j->state = frc ? kFailed : kDone;
@@ -662,10 +670,15 @@ void scheduler(spn_server_ctx* s) {
       }
       act = s->active;
     }
-    // read back the jobs the last round completed while the device is idle: the
-    // read-back launches a small kernel, which would wait behind a running round
-    for (auto& j : completed) retire(s, j, SPN_OK);
-    completed.clear();
+    // the jobs the last round completed go to the read-back thread
+    if (!completed.empty()) {
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (auto& j : completed) s->rb_queue.push_back(j);
+      }
+      s->rb_cv.notify_one();
+      completed.clear();
+    }
     const double t0 = now_s();
     int rc = SPN_OK;
     if (!act.empty()) rc = round_launch(s, act);
@@ -700,7 +713,7 @@ void scheduler(spn_server_ctx* s) {
       j->stream_slot = (int)(j->ticket % s->pool.size());
       const int arc = admit(s, *j);
       if (arc) {
-        retire(s, j, arc);
+        retire(s, j, arc, s->aux);
       } else {
         joined.push_back(j);
       }
@@ -738,7 +751,7 @@ void scheduler(spn_server_ctx* s) {
     std::vector<std::shared_ptr<Job>> still;
     for (auto& j : act) {
       if (rc != SPN_OK) {
-        retire(s, j, rc);
+        retire(s, j, rc, s->aux);
       } else if (j->done < j->req.nsweeps) {
         still.push_back(j);
       } else {
@@ -748,6 +761,23 @@ void scheduler(spn_server_ctx* s) {
     for (auto& j : joined) still.push_back(j);
     std::lock_guard<std::mutex> lock(s->mu);
     s->active = still;
+  }
+}
+
+// The read-back thread: final E, M and host copies of finished jobs, one after
+// another on the read-back stream, then their bytes back to the budget.
+void reader(spn_server_ctx* s) {
+  cudaSetDevice(s->device);
+  while (true) {
+    std::shared_ptr<Job> j;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->rb_cv.wait(lock, [&] { return s->rb_stop || !s->rb_queue.empty(); });
+      if (s->rb_queue.empty()) return;  // stopped and drained
+      j = s->rb_queue.front();
+      s->rb_queue.pop_front();
+    }
+    retire(s, j, SPN_OK, s->rb);
   }
 }
 
@@ -775,6 +805,10 @@ int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
   // large-CTA launches go there, so the block scheduler places them first
   int prio_least = 0, prio_greatest = 0;
   cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (cudaStreamCreateWithPriority(&s->rb, cudaStreamNonBlocking, prio_greatest) != cudaSuccess) {
+    delete s;
+    return sfail(SPN_E_CUDA, "server set-up failed");
+  }
   for (int i = 0; i < kPoolStreams; ++i) {
     cudaStream_t st;
     cudaEvent_t ev;
@@ -785,6 +819,7 @@ int spn_server_create(spn_server* out, size_t hbm_budget_bytes) {
   }
   if (const char* path = std::getenv("SPN_SERVER_TRACE")) s->trace = std::fopen(path, "w");
   s->worker = std::thread(scheduler, s);
+  s->reader = std::thread(reader, s);
   *out = s;
   return SPN_OK;
 }
@@ -907,9 +942,16 @@ int spn_server_destroy(spn_server s) {
     s->cv.notify_one();
   }
   if (s->worker.joinable()) s->worker.join();
-  for (auto& kv : s->all) release(s, *kv.second);
+  {  // the scheduler has handed over its last finished jobs; the reader drains them
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->rb_stop = true;
+  }
+  s->rb_cv.notify_one();
+  if (s->reader.joinable()) s->reader.join();
+  for (auto& kv : s->all) release(*kv.second, s->aux);
   cudaStreamSynchronize(s->main);
   cudaStreamSynchronize(s->aux);
+  cudaStreamSynchronize(s->rb);
   for (size_t i = 0; i < s->pool.size(); ++i) {
     cudaStreamDestroy(s->pool[i]);
     cudaEventDestroy(s->pool_done[i]);
@@ -929,6 +971,7 @@ int spn_server_destroy(spn_server s) {
   if (s->tstart) cudaEventDestroy(s->tstart);
   cudaStreamDestroy(s->main);
   cudaStreamDestroy(s->aux);
+  cudaStreamDestroy(s->rb);
   delete s;
   return SPN_OK;
 }
