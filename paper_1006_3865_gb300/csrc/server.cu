@@ -271,10 +271,11 @@ void trace_mark(spn_server_ctx* s, cudaStream_t st, int kind, long long att) {
   s->tmark.emplace_back(kind, att);
 }
 
-// Attempts per ns and SM while a job runs, by path: starting estimates (from
-// single-job and full-GPU runs of each path); resident jobs then carry the rate
-// measured in their last window.
-constexpr double kRateSm2d = 12.0, kRateSm3d = 7.0, kRateSmEa = 16.0;
+// Attempts per ns and SM while a job runs, by path: starting estimates, on the
+// low side of what a job reaches with the GPU full (a first window that
+// overruns stretches the whole round; one that falls short only leaves its
+// SMs early); resident jobs then carry the rate measured in their last window.
+constexpr double kRateSm2d = 9.0, kRateSm3d = 5.0, kRateSmEa = 16.0;
 
 // Attempts per ns and SM equivalent a job starts with, by path.
 double default_rsm(const Job& j) { return j.ea ? kRateSmEa : (j.nd == 2 ? kRateSm2d : kRateSm3d); }
