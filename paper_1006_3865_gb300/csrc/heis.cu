@@ -17,9 +17,13 @@
 //
 // One launch updates one colour; a warp takes 128 consecutive within-colour
 // indices, a site per lane at a time: a lane's seven 16-byte loads are issued
-// together, a proposal try that fails for some lanes is retried for those
-// lanes only, and each Metropolis Philox call (four sites' words) is drawn
-// once per warp and passed to the lanes by shuffles.  The
+// together, and each Metropolis Philox call (four sites' words) is drawn once
+// per warp and passed to the lanes by shuffles.  A site whose first proposal
+// call misses both tries (about 4.6% of sites) is not retried at once, which
+// would run the warp through a second call for one or two lanes in most
+// steps: it waits in a per-warp queue until 32 such sites have gathered, and
+// the warp then finishes them together (same-colour sites are independent, so
+// the order of their updates does not change the result).  The
 // energy and magnetisation changes of accepted moves are added as 64-bit
 // fixed-point integers in units of 2^-40 (each binary32 dE, dS rounded once to
 // that grid), so the per-sweep sums are exact and independent of the order of
@@ -159,11 +163,92 @@ __device__ __forceinline__ void block_add4(double v[4], double* acc) {
   }
 }
 
+// Neighbour sum h and own spin s of the site n of within-colour index m of
+// colour c: the seven 16-byte loads are issued together (32-bit site indices:
+// N < 2^31).
 template <int ND>
-__global__ void __launch_bounds__(256, 5) k_heis_half(const HeisArgs a) {
+__device__ __forceinline__ uint32_t heis_gather(const HeisArgs& a, uint32_t m, uint32_t c, float4& s, float3& h) {
+  int x, y, z;
+  const uint32_t n = site_of<ND>(a, m, c, x, y, z);
+  const uint32_t sx = (uint32_t)a.Lx - 1u, sy = (uint32_t)a.Lx, wy = (uint32_t)(a.Ly - 1) * sy;
+  const float4 bx = a.s[x == 0 ? n + sx : n - 1u];
+  const float4 fx = a.s[x + 1 == a.Lx ? n - sx : n + 1u];
+  const float4 by = a.s[y == 0 ? n + wy : n - sy];
+  const float4 fy = a.s[y + 1 == a.Ly ? n - wy : n + sy];
+  float4 bz = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fz = bz;
+  if constexpr (ND == 3) {
+    const uint32_t sz = sy * (uint32_t)a.Ly, wz = (uint32_t)(a.Lz - 1) * sz;
+    bz = a.s[z == 0 ? n + wz : n - sz];
+    fz = a.s[z + 1 == a.Lz ? n - wz : n + sz];
+  }
+  s = a.s[n];
+  h = make_float3(0.0f, 0.0f, 0.0f);
+  add3(h, bx);
+  add3(h, fx);
+  add3(h, by);
+  add3(h, fy);
+  if constexpr (ND == 3) {
+    add3(h, bz);
+    add3(h, fz);
+  }
+  return n;
+}
+
+// Metropolis decision of Eq. 2 for the proposal prop of site n (own spin s,
+// neighbour sum h, Metropolis word uw) and, if taken, the store and the
+// fixed-point sums of dE and dS.
+__device__ __forceinline__ void heis_decide(const HeisArgs& a, uint32_t n, const float4& s, const float3& h,
+                                            const float3& prop, uint32_t uw, long long (&sum)[4]) {
+  const float dx = __fsub_rn(prop.x, s.x), dy = __fsub_rn(prop.y, s.y), dz = __fsub_rn(prop.z, s.z);
+  float dot = __fmul_rn(dx, h.x);
+  dot = __fadd_rn(dot, __fmul_rn(dy, h.y));
+  dot = __fadd_rn(dot, __fmul_rn(dz, h.z));
+  const float de = -dot;
+  bool accept = de <= 0.0f;
+  if (!accept) {
+    const float u = __fmul_rn(__uint2float_rn(uw >> 8), 1.0f / 16777216.0f);
+    accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
+  }
+  if (accept) {
+    a.s[n] = make_float4(prop.x, prop.y, prop.z, 0.0f);
+    sum[0] += fixed40(de);
+    sum[1] += fixed40(dx);
+    sum[2] += fixed40(dy);
+    sum[3] += fixed40(dz);
+  }
+}
+
+constexpr int kHeisThreads = 256;
+constexpr int kHeisQueue = 64;  // deferred sites per warp: fewer than 32 left after a drain, plus one pass
+
+template <int ND>
+__global__ void __launch_bounds__(kHeisThreads, 5) k_heis_half(const HeisArgs a) {
+  // sites whose first proposal call missed twice, waiting for a full warp of
+  // them: (m, Metropolis word) per entry
+  __shared__ uint2 queue[kHeisThreads / 32][kHeisQueue];
   const uint32_t c = a.colour, lane = threadIdx.x & 31u;
   const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
+  uint2* q = queue[threadIdx.x >> 5];
+  const uint32_t below = (1u << lane) - 1u;
   long long sum[4] = {0, 0, 0, 0};
+  uint32_t qn = 0;  // warp-uniform
+  // a deferred site, on the lanes below `count`: its proposal calls 1 .. 7 (16
+  // misses in all: no move), then the decision.  Same-colour sites are
+  // independent, so the order of their updates changes nothing.
+  auto drain = [&](uint32_t first, uint32_t count) {
+    __syncwarp();
+    if (lane < count) {
+      const uint2 e = q[first + lane];
+      float4 s;
+      float3 h;
+      const uint32_t n = heis_gather<ND>(a, e.x, c, s, h);
+      float3 prop = make_float3(0.0f, 0.0f, 1.0f);
+      bool got = false;
+      for (uint32_t k = 1; k < 8u && !got; ++k) got = proposal_call(a.K, e.x, a.sweep, c, kHeisPropose, k, a.stream_id, prop);
+      if (got) heis_decide(a, n, s, h, prop, e.y, sum);
+    }
+    __syncwarp();
+  };
   // a warp takes 128 consecutive within-colour indices, 32 at a time; lane l
   // draws the Metropolis call of indices base + 4l .. base + 4l + 3 once
   for (uint32_t base = gwarp * 128u; base < a.half; base += nwarp * 128u) {
@@ -175,68 +260,25 @@ __global__ void __launch_bounds__(256, 5) k_heis_half(const HeisArgs a) {
       const uint32_t w0 = __shfl_sync(0xffffffffu, U.x, src), w1 = __shfl_sync(0xffffffffu, U.y, src);
       const uint32_t w2 = __shfl_sync(0xffffffffu, U.z, src), w3 = __shfl_sync(0xffffffffu, U.w, src);
       const uint32_t uw = (m & 2u) ? ((m & 1u) ? w3 : w2) : ((m & 1u) ? w1 : w0);
-      bool live = m < a.half;
+      const bool live = m < a.half;
       uint32_t n = 0;
-      float3 h = make_float3(0.0f, 0.0f, 0.0f);
       float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (live) {
-        int x, y, z;
-        n = site_of<ND>(a, m, c, x, y, z);
-        // all loads first: seven independent 16-byte reads in flight per thread
-        // (32-bit site indices: N < 2^31)
-        const uint32_t sx = (uint32_t)a.Lx - 1u, sy = (uint32_t)a.Lx, wy = (uint32_t)(a.Ly - 1) * sy;
-        const float4 bx = a.s[x == 0 ? n + sx : n - 1u];
-        const float4 fx = a.s[x + 1 == a.Lx ? n - sx : n + 1u];
-        const float4 by = a.s[y == 0 ? n + wy : n - sy];
-        const float4 fy = a.s[y + 1 == a.Ly ? n - wy : n + sy];
-        float4 bz = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fz = bz;
-        if constexpr (ND == 3) {
-          const uint32_t sz = sy * (uint32_t)a.Ly, wz = (uint32_t)(a.Lz - 1) * sz;
-          bz = a.s[z == 0 ? n + wz : n - sz];
-          fz = a.s[z + 1 == a.Lz ? n - wz : n + sz];
-        }
-        s = a.s[n];
-        add3(h, bx);
-        add3(h, fx);
-        add3(h, by);
-        add3(h, fy);
-        if constexpr (ND == 3) {
-          add3(h, bz);
-          add3(h, fz);
-        }
-      }
-      // proposal: the first call's two tries, then one more call per round for the lanes still without one
+      float3 h = make_float3(0.0f, 0.0f, 0.0f);
+      if (live) n = heis_gather<ND>(a, m, c, s, h);
+      // the first call's two tries; a site that misses both waits in the queue
       float3 prop = make_float3(0.0f, 0.0f, 1.0f);
-      bool need = live && !proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop);
-      for (uint32_t k = 1; __any_sync(0xffffffffu, need); ++k) {
-        if (need) {
-          need = !proposal_call(a.K, m, a.sweep, c, kHeisPropose, k, a.stream_id, prop);
-          if (need && k == 7u) {  // sixteen misses: no move for this site
-            need = false;
-            live = false;
-          }
-        }
-      }
-      if (!live) continue;
-      const float dx = __fsub_rn(prop.x, s.x), dy = __fsub_rn(prop.y, s.y), dz = __fsub_rn(prop.z, s.z);
-      float dot = __fmul_rn(dx, h.x);
-      dot = __fadd_rn(dot, __fmul_rn(dy, h.y));
-      dot = __fadd_rn(dot, __fmul_rn(dz, h.z));
-      const float de = -dot;
-      bool accept = de <= 0.0f;
-      if (!accept) {
-        const float u = __fmul_rn(__uint2float_rn(uw >> 8), 1.0f / 16777216.0f);
-        accept = u < heis_exp_dev(-__fmul_rn(a.beta, de));
-      }
-      if (accept) {
-        a.s[n] = make_float4(prop.x, prop.y, prop.z, 0.0f);
-        sum[0] += fixed40(de);
-        sum[1] += fixed40(dx);
-        sum[2] += fixed40(dy);
-        sum[3] += fixed40(dz);
+      const bool got = live && proposal_call(a.K, m, a.sweep, c, kHeisPropose, 0u, a.stream_id, prop);
+      const uint32_t miss = __ballot_sync(0xffffffffu, live && !got);
+      if (live && !got) q[qn + __popc(miss & below)] = make_uint2(m, uw);
+      qn += (uint32_t)__popc(miss);
+      if (got) heis_decide(a, n, s, h, prop, uw, sum);
+      if (qn >= 32u) {
+        qn -= 32u;
+        drain(qn, 32u);
       }
     }
   }
+  if (qn) drain(0u, qn);
   block_add4_fixed(sum, a.acc);
 }
 
