@@ -27,7 +27,14 @@
 //     further planes for a warp with a tie), so a word computed by two warps
 //     gets the same result in both;
 //   * each owned row goes back to HBM as int8 (through a 256-entry table) once
-//     both of its colours are final.
+//     both of its colours are final;
+//   * a colour-1 site still tied after the first 12 planes is not decided at
+//     once: nothing else in the sweep reads the new colour-1 spins (colour 0
+//     reads those from before the sweep), so it waits in a per-warp queue with
+//     its word's spins and class masks until 32 have gathered or the segment
+//     ends, and a flip then rewrites its int8 byte after the row went out.  The
+//     decision is the same, so the results are too; the warp no longer runs the
+//     further planes for one lane in one step out of eight.
 //
 // Rows next to a segment boundary are loaded (and their colour 0 updated) by both
 // neighbouring segments' warps for the same reason.
@@ -51,6 +58,7 @@ constexpr int kMinBlocks = 3;   // CTAs per SM the register budget aims at
 constexpr int kBitRows = 4;     // bit rows k .. k+3 live at step k
 constexpr int kBandBytes = 32 * 64;
 constexpr int kFirst = 3;       // Philox calls of the first decision stage (12 planes)
+constexpr int kTieQueue = 64;   // deferred colour-1 words per warp: fewer than 32 after a drain, plus one step
 
 struct WaveArgs {
   const int8_t* in;
@@ -70,7 +78,8 @@ struct WaveArgs {
 constexpr size_t kWaveSmem = (size_t)kWarps * kRing * kBandBytes  // raw slots
                              + (size_t)kWarps * kBitRows * 64 * 4  // bit rows
                              + 256 * 8                             // int8 output table
-                             + (size_t)kWarps * kRing * 8;         // mbarriers
+                             + (size_t)kWarps * kRing * 8          // mbarriers
+                             + (size_t)kWarps * kTieQueue * 24;    // tie queues: (c0, eq0, eq1, b), (row, word)
 
 template <int FC>  // Philox calls (4 planes each) of the first decision stage
 __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __grid_constant__ WaveArgs a) {
@@ -82,6 +91,10 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
   uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)kWarps * kRing * kBandBytes) + warp * kBitRows * 64;
   uint2* lut = reinterpret_cast<uint2*>(smem + (size_t)kWarps * kRing * kBandBytes + (size_t)kWarps * kBitRows * 256);
   uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256) + warp * kRing;
+  uint4* tq = reinterpret_cast<uint4*>(reinterpret_cast<uint64_t*>(lut + 256) + kWarps * kRing) + warp * kTieQueue;
+  uint2* tq_at = reinterpret_cast<uint2*>(reinterpret_cast<uint4*>(reinterpret_cast<uint64_t*>(lut + 256) +
+                                                                   kWarps * kRing) + kWarps * kTieQueue) +
+                 warp * kTieQueue;
   const uint4* raw16 = reinterpret_cast<const uint4*>(raw);
 
   // int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
@@ -165,6 +178,8 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
   };
 
   int de = 0, dm = 0;
+  const uint32_t below = (1u << lane) - 1u;
+  uint32_t tn = 0;  // queued colour-1 words (warp-uniform)
   // colour c of local row li (global gr): the lane's colour-c word is recomputed
   // from the other colour's words of its row and the rows above and below;
   // colour 1 also sends the finished row out as int8
@@ -205,7 +220,18 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
       pl[4 * call + 3] = P.w;
     }
     compare_top<NC, 4 * FC>(acc, eq, pl, a.tm);
-    acc |= tail_planes<NC, FC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id);
+    if (c == 0) {
+      acc |= tail_planes<NC, FC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id);
+    } else {  // owned ties wait in the queue; a halo lane's colour 1 is not kept
+      const bool tie = owned && (eq[0] | eq[1]) != 0u;
+      const uint32_t ties = __ballot_sync(0xffffffffu, tie);
+      if (tie) {
+        const uint32_t q = tn + (uint32_t)__popc(ties & below);
+        tq[q] = make_uint4(c0, eq[0], eq[1], b);
+        tq_at[q] = make_uint2((uint32_t)gr, (uint32_t)jw);
+      }
+      tn += (uint32_t)__popc(ties);
+    }
     const uint32_t nb = b ^ acc;
     if (c == 0 || owned) r0[ws] = nb;
     if (owned && li >= 2 && li < H + 2) tally<2>(acc, b, s0, s1, s2, de, dm);
@@ -221,6 +247,32 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
         dst[v] = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
     }
+  };
+
+  // the queued colour-1 words [first, first + count), a word per lane: planes
+  // 12 .. 31 as far as a site is still tied, then the flipped sites' int8 bytes
+  // (after the rows' 16-byte stores of this warp) and their dE, dM
+  auto drain = [&](uint32_t first, uint32_t count) {
+    __syncwarp();
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    uint2 at = make_uint2(0u, 0u);
+    if (lane < count) {
+      e = tq[first + lane];
+      at = tq_at[first + lane];
+    }
+    uint32_t eq[NC] = {e.y, e.z};
+    const uint32_t fl = rest_planes<NC>(eq, a.tm, a.K, e.x, a.sweep, 1u | (kMetropolis << 1), a.stream_id, FC);
+    if (fl) {
+      de += 4 * __popc(fl & e.y) + 8 * __popc(fl & e.z);  // class 0: dE = 4, class 1: dE = 8
+      dm += 2 * (2 * __popc(fl & e.w) - __popc(fl));
+      const uint32_t par = (at.x + 1u) & 1u;  // colour-1 sites at x = 2 j + par of the word
+      int8_t* row = a.out + (int64_t)at.x * (64 * W) + 64 * (int64_t)at.y;
+      for (uint32_t f = fl; f; f &= f - 1u) {
+        const int j = __ffs((int)f) - 1;
+        row[2 * j + (int)par] = ((e.w >> j) & 1u) ? (int8_t)1 : (int8_t)-1;
+      }
+    }
+    __syncwarp();
   };
 
   // prologue: rows 0, 1, 2 converted, colour 0 of row 1
@@ -240,6 +292,10 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
     issue(issued++);
     update(k + 2, 0);
     if (k >= 1) update(k + 1, 1);
+    if (tn >= 32u) {
+      tn -= 32u;
+      drain(tn, 32u);
+    }
   }
   if (!ok) {  // this warp gives up
     if (lane == 0) {
@@ -257,6 +313,7 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
     __syncwarp();
     return;
   }
+  if (tn) drain(0u, tn);
   block_accumulate(de, dm, a.acc);
 }
 
