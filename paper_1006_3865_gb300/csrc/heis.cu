@@ -15,8 +15,10 @@
 //   hot start: the same with purpose 7 and sweep 0;
 //   Metropolis u: word m & 3 of R(m >> 2, sweep, c | 6 << 1, stream).
 //
-// One launch updates one colour; a warp takes 128 consecutive within-colour
-// indices, a site per lane at a time: a lane's seven 16-byte loads are issued
+// One launch updates one colour; a warp takes groups of 128 consecutive
+// within-colour indices from a counter in global memory until none is left (the
+// schedulers of an SM favour the warps of its first CTA, so a fixed share per
+// warp left the last CTAs running alone at the end), a site per lane at a time: a lane's seven 16-byte loads are issued
 // together, and each Metropolis Philox call (four sites' words) is drawn once
 // per warp and passed to the lanes by shuffles.  A site whose first proposal
 // call misses both tries (about 4.6% of sites) is not retried at once, which
@@ -55,6 +57,9 @@ struct HeisArgs {
   uint32_t sweep, stream_id, colour;
   PhiloxKeys K;
   unsigned long long* acc;  // [4]: dE, dMx, dMy, dMz of this sweep, two's complement in units of 2^-40
+  unsigned long long* work;  // group counter: a warp takes group (counter - work_base) until none is left
+  unsigned long long work_base;
+  uint32_t ngroups;  // groups of 128 within-colour indices
 };
 
 __device__ __forceinline__ float heis_exp_dev(float x) {
@@ -227,7 +232,6 @@ __global__ void __launch_bounds__(kHeisThreads, 5) k_heis_half(const HeisArgs a)
   // them: (m, Metropolis word) per entry
   __shared__ uint2 queue[kHeisThreads / 32][kHeisQueue];
   const uint32_t c = a.colour, lane = threadIdx.x & 31u;
-  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
   uint2* q = queue[threadIdx.x >> 5];
   const uint32_t below = (1u << lane) - 1u;
   long long sum[4] = {0, 0, 0, 0};
@@ -250,8 +254,15 @@ __global__ void __launch_bounds__(kHeisThreads, 5) k_heis_half(const HeisArgs a)
     __syncwarp();
   };
   // a warp takes 128 consecutive within-colour indices, 32 at a time; lane l
-  // draws the Metropolis call of indices base + 4l .. base + 4l + 3 once
-  for (uint32_t base = gwarp * 128u; base < a.half; base += nwarp * 128u) {
+  // draws the Metropolis call of indices base + 4l .. base + 4l + 3 once.
+  // Every warp ends after one add that finds no group left, so a launch adds
+  // exactly ngroups + (warps of the grid) to the counter.
+  for (;;) {
+    uint32_t grp = 0;
+    if (lane == 0) grp = (uint32_t)(atomicAdd(a.work, 1ull) - a.work_base);
+    grp = __shfl_sync(0xffffffffu, grp, 0);
+    if (grp >= a.ngroups) break;
+    const uint32_t base = 128u * grp;
     const U4 U = philox10((base >> 2) + lane, a.sweep, c | (kHeisMetropolis << 1), a.stream_id, a.K);
 #pragma unroll 1
     for (uint32_t i = 0; i < 4; ++i) {
@@ -349,7 +360,8 @@ cudaError_t launch_heis_init(float4* s, int nd, const int* L, int64_t N, uint64_
 }
 
 cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float beta, uint64_t seed,
-                              uint32_t stream, uint32_t sweep, unsigned long long* acc, cudaStream_t st) {
+                              uint32_t stream, uint32_t sweep, unsigned long long* acc, unsigned long long* work,
+                              unsigned long long* work_base, cudaStream_t st) {
   HeisArgs a;
   a.s = s;
   a.nd = nd;
@@ -365,8 +377,12 @@ cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float 
   a.K = philox_keys(seed);
   a.acc = acc;
   const int grid = grid_for(((int64_t)a.half + 3) / 4, 5);  // a thread per four sites (a warp per 128)
+  a.work = work;
+  a.ngroups = (a.half + 127u) / 128u;
   for (uint32_t c = 0; c < 2; ++c) {
     a.colour = c;
+    a.work_base = *work_base;
+    *work_base += a.ngroups + (unsigned long long)grid * 8u;
     if (nd == 3)
       k_heis_half<3><<<grid, 256, 0, st>>>(a);
     else
@@ -405,6 +421,7 @@ struct HeisState {
   int64_t acc_cap = 0;
   uint64_t folded = 0;
   double* d_obs = nullptr;
+  unsigned long long* d_work = nullptr;  // group counter of the sweep kernel
   double E = 0.0, M[3] = {0.0, 0.0, 0.0};
   std::vector<double> traceE, traceM;
 };
@@ -487,6 +504,7 @@ void heis_free(HeisState* s) {
   cudaFree(s->d_s);
   cudaFree(s->d_acc);
   cudaFree(s->d_obs);
+  cudaFree(s->d_work);
   delete s;
 }
 
@@ -502,7 +520,8 @@ int heis_create(spn_ctx* h, const int32_t* dims, int init) {
     s->N *= dims[d];
   }
   if (cudaMalloc(&s->d_s, (size_t)s->N * sizeof(float4)) != cudaSuccess ||
-      cudaMalloc(&s->d_obs, 4 * sizeof(double)) != cudaSuccess)
+      cudaMalloc(&s->d_obs, 4 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s->d_work, sizeof(unsigned long long)) != cudaSuccess)
     return heis_fail(SPN_E_NOMEM, "cudaMalloc(Heisenberg lattice)");
   int rc = heis_ensure_acc(h, 1024);
   if (rc) return rc;
@@ -514,10 +533,14 @@ int heis_sweep(spn_ctx* h, double beta, int64_t nsweeps) {
   int rc = heis_ensure_acc(h, nsweeps);
   if (rc) return rc;
   const float bf = (float)beta;
+  unsigned long long work_base = 0;
+  if (nsweeps > 0 && cudaMemsetAsync(s->d_work, 0, sizeof(unsigned long long), h->st) != cudaSuccess)
+    return heis_fail(SPN_E_CUDA, "clearing the Heisenberg group counter");
   for (int64_t t = 0; t < nsweeps; ++t) {
     const uint32_t sweep = (uint32_t)(h->sweeps + t);
     unsigned long long* acc = s->d_acc + 4 * (int64_t)(sweep - s->folded);
-    const cudaError_t e = launch_heis_sweep(s->d_s, s->nd, s->L, s->N, bf, h->seed, h->stream_id, sweep, acc, h->st);
+    const cudaError_t e =
+        launch_heis_sweep(s->d_s, s->nd, s->L, s->N, bf, h->seed, h->stream_id, sweep, acc, s->d_work, &work_base, h->st);
     if (e != cudaSuccess) {
       h->sweeps += (uint64_t)t;
       return heis_fail(SPN_E_CUDA, cudaGetErrorString(e));

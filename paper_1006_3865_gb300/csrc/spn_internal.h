@@ -245,7 +245,8 @@ void heis_free(HeisState* s);
 cudaError_t launch_heis_init(float4* s, int nd, const int* L, int64_t N, uint64_t seed, uint32_t stream, bool cold,
                              cudaStream_t st);
 cudaError_t launch_heis_sweep(float4* s, int nd, const int* L, int64_t N, float beta, uint64_t seed,
-                              uint32_t stream, uint32_t sweep, unsigned long long* acc, cudaStream_t st);
+                              uint32_t stream, uint32_t sweep, unsigned long long* acc, unsigned long long* work,
+                              unsigned long long* work_base, cudaStream_t st);
 cudaError_t launch_heis_observables(const float4* s, int nd, const int* L, int64_t N, double* out4,
                                     cudaStream_t st);
 cudaError_t launch_heis_exp(const float* x, float* y, int n, cudaStream_t st);

@@ -52,9 +52,13 @@ namespace spn {
 namespace {
 
 constexpr int kOwned = 30;      // words of a band (plus one halo word on each side = 32 lanes)
-constexpr int kWarps = 8;       // warps per CTA, each an independent (band, segment)
+// warps per CTA, each an independent (band, segment).  One CTA of 24 warps per
+// SM rather than three of 8: with three, the SM's schedulers favoured the warps
+// of the first CTA, which finished in 55% of the time of the last, and the last
+// third of a sweep ran on 8 warps per SM.
+constexpr int kWarps = 24;
 constexpr int kRing = 3;        // raw band slots per warp
-constexpr int kMinBlocks = 3;   // CTAs per SM the register budget aims at
+constexpr int kMinBlocks = 1;   // CTAs per SM the register budget aims at
 constexpr int kBitRows = 4;     // bit rows k .. k+3 live at step k
 constexpr int kBandBytes = 32 * 64;
 constexpr int kFirst = 3;       // Philox calls of the first decision stage (12 planes)
