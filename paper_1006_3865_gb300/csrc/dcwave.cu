@@ -47,7 +47,10 @@ namespace spn {
 namespace {
 
 constexpr int kDwOwned = 30;     // words of a band (plus one halo word on each side = 32 lanes)
-constexpr int kDwWarps = 8;      // warps per CTA, each an independent (band, segment)
+// warps per CTA, each an independent (band, segment): one CTA per SM, since an
+// SM's schedulers favour the warps of its first CTA and with several CTAs the
+// last one ran alone at the end of the sweep
+constexpr int kDwWarps = 24;
 constexpr int kDwRing = 3;       // raw band slots per warp
 constexpr int kDwBandBytes = 32 * 64;
 constexpr int kDwFirst = 3;      // Philox calls of the first decision stage (12 planes)
@@ -84,7 +87,7 @@ size_t dw_smem(int hits) {
 }
 
 template <int HITS>
-__global__ void __launch_bounds__(32 * kDwWarps, 3) k_sweep_dcwave(const __grid_constant__ DwArgs a) {
+__global__ void __launch_bounds__(32 * kDwWarps, 1) k_sweep_dcwave(const __grid_constant__ DwArgs a) {
   constexpr int NC = 2;  // classes with dE > 0: dE = 4, 8
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr int Q = 4 * HITS, half = 2 * HITS, R = Q + 3 <= 8 ? 8 : (Q + 3 <= 16 ? 16 : 32);

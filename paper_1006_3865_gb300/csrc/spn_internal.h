@@ -81,6 +81,7 @@ cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz,
 bool wave_supported(const Lattice& g);
 int wave_default_segments(const Lattice& g);
 size_t wave_smem_bytes(const Lattice& g);
+int wave_cta_threads();
 cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, int nseg, const DevThr& T,
                               const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                               int* err, cudaStream_t st, uint32_t expire_polls);
@@ -89,7 +90,8 @@ cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, i
 // eight compute warps, dividing Ly; nseg segments along z.
 bool wave3_supported(const Lattice& g, int TY);
 int wave3_default_segments(const Lattice& g, int TY);
-size_t wave3_smem_bytes(const Lattice& g, int TY);
+size_t wave3_smem_bytes(const Lattice& g, int TY);  // of one CTA
+int wave3_cta_threads(const Lattice& g, int TY);
 cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, int TY, int nseg, const DevThr& T,
                                const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                                int* err, cudaStream_t st, uint32_t expire_polls);

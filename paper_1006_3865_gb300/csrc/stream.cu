@@ -454,7 +454,7 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packe
     s.wave = 2;
     s.TY = TY;
     s.R = 1;
-    s.threads = 32 * (TY / (32 / (g.Lx / 64)) + 1);
+    s.threads = wave3_cta_threads(g, TY);
     s.nseg = nseg > 0 ? std::min(nseg, g.Lz) : wave3_default_segments(g, TY);
     s.smem = wave3_smem_bytes(g, TY);
     return s;
@@ -463,7 +463,7 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packe
     s.wave = 1;
     s.TY = 1;
     s.R = 1;
-    s.threads = 256;
+    s.threads = wave_cta_threads();
     s.nseg = nseg > 0 ? std::min(nseg, g.Ly) : wave_default_segments(g);
     s.smem = wave_smem_bytes(g);
     return s;

@@ -334,6 +334,8 @@ bool wave_supported(const Lattice& g) {
 
 size_t wave_smem_bytes(const Lattice&) { return kWaveSmem; }
 
+int wave_cta_threads() { return 32 * kWarps; }
+
 int wave_default_segments(const Lattice& g) {
   static std::mutex mu;
   static int per_sm = 0;

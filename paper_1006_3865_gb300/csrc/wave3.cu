@@ -51,12 +51,19 @@ constexpr int kW3Ring = 3;                     // raw slots per warp
 constexpr int kW3Planes = 4;                   // bit planes k .. k+3 live at step k
 constexpr int kW3Slot = 2048;                  // bytes of one raw slot
 constexpr int kW3First = 3;                    // Philox calls of the first decision stage (12 planes)
+// A CTA holds several units (band, segment) side by side, as many as one SM
+// keeps resident, so that an SM runs one CTA: its schedulers favour the warps
+// of the first of several CTAs, and the last CTA then ran alone at the end of
+// the sweep.
+constexpr int kW3MaxThreads = 3 * 32 * kW3Warps;  // three units of the largest band
 
 struct Wave3Args {
   const int8_t* in;
   int8_t* out;
   int Lx, Ly, Lz, W;  // W: 64-site words per row (1, 2, 4 or 8)
   int TY, nwc, nseg;  // band rows, compute warps (TY = nwc * 32 / W), segments along z
+  int units;          // units per CTA
+  unsigned unit_smem;  // shared-memory bytes of one unit
   uint32_t sweep, stream_id;
   uint32_t always;     // bit q + 1: class q (dE = 4 (q + 1)) is always accepted
   PhiloxKeys K;
@@ -80,12 +87,16 @@ __device__ __forceinline__ void mbar_arrive3(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__global__ void __launch_bounds__(32 * kW3Warps, 3) k_sweep_wave3(const __grid_constant__ Wave3Args a) {
+__global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_constant__ Wave3Args a) {
   constexpr int NC = 3;  // classes with dE > 0: dE = 4, 8, 12
-  extern __shared__ __align__(128) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem_all[];
   const int W = a.W, Lx = a.Lx, Ly = a.Ly, Lz = a.Lz, TY = a.TY, nwc = a.nwc;
   const int nw = nwc + 1, RPW = 32 / W, W2 = 2 * W, rows = TY + 4;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31;
+  const int sub = (int)(threadIdx.x >> 5) / nw;        // unit of this warp within the CTA
+  const int warp = (int)(threadIdx.x >> 5) - sub * nw;  // warp within its unit
+  const int tid = (int)threadIdx.x - 32 * nw * sub;     // thread within its unit
+  uint8_t* smem = smem_all + (size_t)sub * a.unit_smem;
   const bool halo = warp == nwc;
   uint8_t* raw = smem + (size_t)warp * kW3Ring * kW3Slot;  // this warp's slots
   uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)nw * kW3Ring * kW3Slot);
@@ -94,9 +105,12 @@ __global__ void __launch_bounds__(32 * kW3Warps, 3) k_sweep_wave3(const __grid_c
   uint64_t* steps = reinterpret_cast<uint64_t*>(lut + 256) + nw * kW3Ring;  // [warp][2]
   const uint4* raw16 = reinterpret_cast<const uint4*>(raw);
 
-  const int y0 = blockIdx.x * TY;
-  const int zs = (int)(((int64_t)blockIdx.y * Lz) / a.nseg);
-  const int ze = (int)(((int64_t)(blockIdx.y + 1) * Lz) / a.nseg);
+  const int bands = Ly / TY;
+  const int unit = (int)blockIdx.x * a.units + sub;  // (band, segment), band fastest
+  const int useg = unit / bands;
+  const int y0 = (unit - useg * bands) * TY;
+  const int zs = (int)(((int64_t)useg * Lz) / a.nseg);
+  const int ze = (int)(((int64_t)(useg + 1) * Lz) / a.nseg);
   const int H = ze - zs;
   const int nload = H + 4;  // local planes li = 0 .. H + 3 <-> global zs - 2 + li
   // warps to the left (smaller y) and right of this one: the halo warp sits
@@ -105,7 +119,7 @@ __global__ void __launch_bounds__(32 * kW3Warps, 3) k_sweep_wave3(const __grid_c
   const int wr = halo ? nwc - 1 : (warp == nwc - 1 ? nwc : warp + 1);
 
   // int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
-  for (int i = tid; i < 256; i += blockDim.x) {
+  for (int i = tid; i < 256; i += 32 * nw) {
     uint32_t lo = 0, hi = 0;
     for (int k = 0; k < 4; ++k) {
       const uint32_t pair = (((i >> k) & 1) ? 0xffu : 0x01u) | ((((i >> (4 + k)) & 1) ? 0xffu : 0x01u) << 8);
@@ -120,6 +134,7 @@ __global__ void __launch_bounds__(32 * kW3Warps, 3) k_sweep_wave3(const __grid_c
     fence_mbar_init();
   }
   __syncthreads();  // the table and the barriers; from here on warps only wait for their neighbours
+  if (unit >= bands * a.nseg) return;  // an empty place of the last CTA
 
   auto gz = [&](int li) {  // global plane of local plane li
     int z = zs - 2 + li;
@@ -340,33 +355,50 @@ bool wave3_supported(const Lattice& g, int TY) {
   return g.Lz >= 2;
 }
 
+
+namespace {
+
+size_t unit_smem_of(int TY, int W, int nwc) { return (wave3_smem(TY, W, nwc) + 127) & ~(size_t)127; }
+
+// Units one SM holds at once (from the occupancy of a one-unit CTA, within the
+// thread and shared-memory limits of one CTA): the units of a CTA.
+int units_per_cta(int TY, int W, int nwc) {
+  static std::mutex mu;
+  static int per_sm[kW3Compute + 1][4] = {};  // [compute warps][log2 W]
+  const int lw = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!per_sm[nwc][lw]) {
+    const size_t sm = unit_smem_of(TY, W, nwc);
+    cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave3, 32 * (nwc + 1), sm) != cudaSuccess)
+      blocks = 1;
+    int u = std::max(1, blocks);
+    u = std::min(u, kW3MaxThreads / (32 * (nwc + 1)));
+    u = std::min<int>(u, (int)((227 * 1024) / sm));
+    per_sm[nwc][lw] = std::max(1, u);
+  }
+  return per_sm[nwc][lw];
+}
+
+}  // namespace
+
 size_t wave3_smem_bytes(const Lattice& g, int TY) {
-  const int W = g.Lx / 64;
-  return wave3_smem(TY, W, TY / (32 / W));
+  const int W = g.Lx / 64, nwc = TY / (32 / W);
+  return (size_t)units_per_cta(TY, W, nwc) * unit_smem_of(TY, W, nwc);
+}
+
+int wave3_cta_threads(const Lattice& g, int TY) {
+  const int W = g.Lx / 64, nwc = TY / (32 / W);
+  return 32 * (nwc + 1) * units_per_cta(TY, W, nwc);
 }
 
 int wave3_default_segments(const Lattice& g, int TY) {
-  static std::mutex mu;
-  static int per_sm[kW3Compute + 1][4] = {};  // [compute warps][log2 W]
   const int W = g.Lx / 64, nwc = TY / (32 / W);
-  const int lw = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3;
-  int occ = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!per_sm[nwc][lw]) {
-      const size_t sm = wave3_smem(TY, W, nwc);
-      cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      int blocks = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave3, 32 * (nwc + 1), sm) != cudaSuccess)
-        blocks = 1;
-      per_sm[nwc][lw] = std::max(1, blocks);
-    }
-    occ = per_sm[nwc][lw];
-  }
-  // one wave of resident CTAs: a partial second wave would run alone at the end
+  // one wave: a CTA per SM holding as many units as the SM keeps resident
   const int bands = g.Ly / TY;
-  const int want = device_sm_count() * occ;
+  const int want = device_sm_count() * units_per_cta(TY, W, nwc);
   return std::max(1, std::min(g.Lz, want / bands));
 }
 
@@ -399,7 +431,9 @@ cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, 
     a.skip_first = 1;
     a.wait_limit = expire_polls;
   }
-  const size_t sm = wave3_smem(TY, a.W, a.nwc);
+  a.units = units_per_cta(TY, a.W, a.nwc);
+  a.unit_smem = (unsigned)unit_smem_of(TY, a.W, a.nwc);
+  const size_t sm = (size_t)a.units * a.unit_smem;
   {
     static std::mutex mu;
     static bool set[128] = {};
@@ -412,8 +446,8 @@ cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, 
       set[dev & 127] = true;
     }
   }
-  dim3 grid(g.Ly / TY, nseg);
-  k_sweep_wave3<<<grid, 32 * (a.nwc + 1), sm, st>>>(a);
+  const int64_t units = (int64_t)(g.Ly / TY) * nseg;
+  k_sweep_wave3<<<(unsigned)((units + a.units - 1) / a.units), 32 * (a.nwc + 1) * a.units, sm, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
