@@ -34,7 +34,8 @@ enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2, kPathPac
 // the lattice is stored as bit words (rows of packed_row_words(Lx) words).
 struct StreamGeom {
   int packed;
-  int wave;  // 1: the 2D band-parallel kernel (wave.cu), nseg row segments; 2: the 3D wavefront kernel (wave3.cu)
+  int wave;  // 1: the 2D band-parallel kernel (wave.cu), nseg row segments; 2: the 3D wavefront kernel (wave3.cu);
+            // 3: the 2D band-parallel kernel on a bit-packed lattice (wave.cu)
   int TY, R, nseg, threads, nraw, nbit;
   int roundsC, roundsA, roundsB, qcap;  // words per thread per phase; tie-queue entries per warp
   size_t smem;
@@ -81,6 +82,11 @@ cudaError_t launch_sweep_dc(const Lattice& g, int8_t* s, int Tx, int Ty, int Tz,
 bool wave_supported(const Lattice& g);
 int wave_default_segments(const Lattice& g);
 size_t wave_smem_bytes(const Lattice& g);
+bool wave_packed_supported(const Lattice& g);
+size_t wave_packed_smem_bytes();
+cudaError_t launch_sweep_wave_packed(const Lattice& g, const uint32_t* in, uint32_t* out, int nseg, const DevThr& T,
+                                     const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                     unsigned long long* acc, cudaStream_t st);
 int wave_cta_threads();
 cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, int nseg, const DevThr& T,
                               const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,

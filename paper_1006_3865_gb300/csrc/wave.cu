@@ -321,6 +321,188 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
   block_accumulate(de, dm, a.acc);
 }
 
+// ------------------------------------------------------------------ bit-packed lattices
+//
+// The same band-parallel sweep for a lattice stored one bit per spin (row r:
+// the W words of its even-x sites, then the W words of its odd-x sites; a set
+// bit is spin -1).  A lane's E and O words of a row are its two words of the
+// packed row, so a row arrives by two 4-byte asynchronous copies per lane
+// (cp.async, completed by commit groups) straight into the warp's ring of bit
+// rows, and goes back as two 4-byte stores: no conversion and no int8 table.
+// A flipped deferred colour-1 site is patched into the written word by an
+// atomic XOR.  Nothing here spins on a flag: the copies' groups complete in
+// hardware.
+
+constexpr int kPkRing = 8;   // bit rows per warp: rows k .. k+3 in use, four more on their way
+constexpr int kPkAhead = 4;  // row k + 3 + kPkAhead is requested at step k
+constexpr size_t kWavePkSmem = (size_t)kWarps * kPkRing * 64 * 4  // bit rows
+                               + (size_t)kWarps * kTieQueue * 24;  // tie queues
+
+struct WavePkArgs {
+  const uint32_t* in;
+  uint32_t* out;
+  int Ly, W;  // rows; words per colour and row (even, at least 32); a packed row is 2 W words
+  int nbands, nseg;
+  uint32_t sweep, stream_id;
+  uint32_t always;
+  PhiloxKeys K;
+  uint32_t tm[2][32];
+  unsigned long long* acc;
+};
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int FC>
+__global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave_packed(const __grid_constant__ WavePkArgs a) {
+  constexpr int NC = 2;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int W = a.W, Ly = a.Ly, RS = 2 * a.W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem) + warp * kPkRing * 64;
+  uint4* tq = reinterpret_cast<uint4*>(smem + (size_t)kWarps * kPkRing * 256) + warp * kTieQueue;
+  uint2* tq_at =
+      reinterpret_cast<uint2*>(smem + (size_t)kWarps * kPkRing * 256 + (size_t)kWarps * kTieQueue * 16) +
+      warp * kTieQueue;
+
+  const int unit = blockIdx.x * kWarps + warp;
+  if (unit >= a.nbands * a.nseg) return;  // warps are independent: no CTA barrier in this kernel
+  const int band = unit % a.nbands, seg = unit / a.nbands;
+  const int zs = (int)(((int64_t)seg * Ly) / a.nseg);
+  const int ze = (int)(((int64_t)(seg + 1) * Ly) / a.nseg);
+  const int H = ze - zs;
+  const int nload = H + 4;  // local rows li = 0 .. H + 3 <-> global zs - 2 + li
+  const int j0 = kOwned * band;
+  int jw = j0 - 1 + lane;
+  jw = jw < 0 ? jw + W : (jw >= W ? jw - W : jw);
+  const bool owned = lane >= 1 && lane <= kOwned && j0 + lane - 1 < W;
+
+  auto grow = [&](int li) {
+    int r = zs - 2 + li;
+    r = r < 0 ? r + Ly : r;
+    return r >= Ly ? r - Ly : r;
+  };
+  auto row_bits = [&](int li) { return bits + (li & (kPkRing - 1)) * 64; };  // E words 0..31, O words 32..63
+  // request local row li: this lane's E and O words into its ring row; one
+  // commit group per call (an empty one past the last row keeps the count)
+  auto issue = [&](int li) {
+    if (li < nload) {
+      const uint32_t* src = a.in + (int64_t)grow(li) * RS;
+      uint32_t* dst = row_bits(li);
+      cp_async4(dst + lane, src + jw);
+      cp_async4(dst + 32 + lane, src + W + jw);
+    }
+    cp_async_commit();
+  };
+
+  int de = 0, dm = 0;
+  const uint32_t below = (1u << lane) - 1u;
+  uint32_t tn = 0;
+  auto update = [&](int li, int c) {
+    const int gr = grow(li);
+    const int par = (gr + c) & 1;
+    const uint32_t* rm = row_bits(li - 1);
+    uint32_t* r0 = row_bits(li);
+    const uint32_t* rp = row_bits(li + 1);
+    const int ws = par ? 32 + lane : lane;
+    const uint32_t b = r0[ws], oj = r0[par ? lane : 32 + lane];
+    const uint32_t on = par ? __shfl_down_sync(0xffffffffu, oj, 1) : __shfl_up_sync(0xffffffffu, oj, 1);
+    const uint32_t left = par ? oj : (oj << 1) | (on >> 31);
+    const uint32_t right = par ? (oj >> 1) | (on << 31) : oj;
+    const uint32_t zm = rm[ws], zp = rp[ws];
+    uint32_t s0, s1, s2, cls[NC];
+    count4(b ^ left, b ^ right, b ^ zm, b ^ zp, s0, s1, s2);
+    uint32_t acc = classes<2>(s0, s1, s2, 0xffffffffu, cls);
+    uint32_t eq[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const bool always = (a.always >> (k + 1)) & 1u;
+      acc |= always ? cls[k] : 0u;
+      eq[k] = always ? 0u : cls[k];
+    }
+    const uint32_t c0 = 8u * ((uint32_t)jw + (uint32_t)W * (uint32_t)gr);
+    const uint32_t c2 = (uint32_t)c | (kMetropolis << 1);
+    uint32_t pl[4 * FC];
+#pragma unroll
+    for (int call = 0; call < FC; ++call) {
+      const U4 P = philox10(c0 + (uint32_t)call, a.sweep, c2, a.stream_id, a.K);
+      pl[4 * call + 0] = P.x;
+      pl[4 * call + 1] = P.y;
+      pl[4 * call + 2] = P.z;
+      pl[4 * call + 3] = P.w;
+    }
+    compare_top<NC, 4 * FC>(acc, eq, pl, a.tm);
+    if (c == 0) {
+      acc |= tail_planes<NC, FC>(eq, a.tm, a.K, c0, a.sweep, c2, a.stream_id);
+    } else {
+      const bool tie = owned && (eq[0] | eq[1]) != 0u;
+      const uint32_t ties = __ballot_sync(0xffffffffu, tie);
+      if (tie) {
+        const uint32_t q = tn + (uint32_t)__popc(ties & below);
+        tq[q] = make_uint4(c0, eq[0], eq[1], b);
+        tq_at[q] = make_uint2((uint32_t)gr, (uint32_t)jw);
+      }
+      tn += (uint32_t)__popc(ties);
+    }
+    const uint32_t nb = b ^ acc;
+    if (c == 0 || owned) r0[ws] = nb;
+    if (owned && li >= 2 && li < H + 2) tally<2>(acc, b, s0, s1, s2, de, dm);
+    if (c == 1 && owned) {
+      uint32_t* o = a.out + (int64_t)gr * RS;
+      o[jw] = par ? oj : nb;
+      o[W + jw] = par ? nb : oj;
+    }
+  };
+  // the queued colour-1 words, a word per lane: planes 12 .. 31 as far as a
+  // site is still tied, then the flipped bits XOR-ed into the written word
+  auto drain = [&](uint32_t first, uint32_t count) {
+    __syncwarp();
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    uint2 at = make_uint2(0u, 0u);
+    if (lane < count) {
+      e = tq[first + lane];
+      at = tq_at[first + lane];
+    }
+    uint32_t eq[NC] = {e.y, e.z};
+    const uint32_t fl = rest_planes<NC>(eq, a.tm, a.K, e.x, a.sweep, 1u | (kMetropolis << 1), a.stream_id, FC);
+    if (fl) {
+      de += 4 * __popc(fl & e.y) + 8 * __popc(fl & e.z);
+      dm += 2 * (2 * __popc(fl & e.w) - __popc(fl));
+      const uint32_t par = (at.x + 1u) & 1u;  // 0: the E word holds colour 1
+      atomicXor(a.out + (int64_t)at.x * RS + (par ? W : 0) + (int64_t)at.y, fl);
+    }
+    __syncwarp();
+  };
+
+  // rows 0 .. 2 + kPkAhead requested, then the prologue: colour 0 of row 1
+  for (int li = 0; li < 3 + kPkAhead; ++li) issue(li);
+  cp_async_wait<kPkAhead>();  // rows 0, 1, 2 have landed
+  __syncwarp();
+  update(1, 0);
+  // step k: row k + 3 has landed; colour 0 of row k + 2, colour 1 of row k + 1
+  for (int k = 0; k <= H; ++k) {
+    __syncwarp();             // row k - 1 is read no more: its ring row takes row k + 3 + kPkAhead
+    issue(k + 3 + kPkAhead);
+    cp_async_wait<kPkAhead>();
+    __syncwarp();
+    update(k + 2, 0);
+    if (k >= 1) update(k + 1, 1);
+    if (tn >= 32u) {
+      tn -= 32u;
+      drain(tn, 32u);
+    }
+  }
+  cp_async_wait<0>();
+  if (tn) drain(0u, tn);
+  block_accumulate(de, dm, a.acc);
+}
+
 int nbands_of(const Lattice& g) { return (g.Lx / 64 + kOwned - 1) / kOwned; }
 
 }  // namespace
@@ -331,6 +513,14 @@ bool wave_supported(const Lattice& g) {
   if (g.Lx % 64 || g.Lx < 2048 || g.Lx > (1 << 24)) return false;
   return g.Ly >= 2;
 }
+
+bool wave_packed_supported(const Lattice& g) {
+  if (g.nd != 2 || g.bonds) return false;
+  if (g.Lx % 128 || g.Lx < 2048 || g.Lx > (1 << 24)) return false;  // W even: a packed row is exactly 2 W words
+  return g.Ly >= 2;
+}
+
+size_t wave_packed_smem_bytes() { return kWavePkSmem; }
 
 size_t wave_smem_bytes(const Lattice&) { return kWaveSmem; }
 
@@ -396,6 +586,43 @@ cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, i
   }
   const int64_t units = (int64_t)a.nbands * nseg;
   k_sweep_wave<kFirst><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWaveSmem, st>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_wave_packed(const Lattice& g, const uint32_t* in, uint32_t* out, int nseg, const DevThr& T,
+                                     const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                     unsigned long long* acc, cudaStream_t st) {
+  if (!wave_packed_supported(g) || nseg < 1 || nseg > g.Ly) return cudaErrorInvalidConfiguration;
+  if (((uintptr_t)in & 3) || ((uintptr_t)out & 3)) return cudaErrorMisalignedAddress;
+  WavePkArgs a;
+  a.in = in;
+  a.out = out;
+  a.Ly = g.Ly;
+  a.W = g.Lx / 64;
+  a.nbands = nbands_of(g);
+  a.nseg = nseg;
+  a.sweep = sweep;
+  a.stream_id = stream_id;
+  a.always = T.always;
+  a.K = K;
+  for (int k = 0; k < 2; ++k)
+    for (int p = 0; p < 32; ++p) a.tm[k][p] = ((T.t[k + 1] >> (31 - p)) & 1u) ? 0xffffffffu : 0u;
+  a.acc = acc;
+  {
+    static std::mutex mu;
+    static bool set[128] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!set[dev & 127]) {
+      cudaFuncSetAttribute(k_sweep_wave_packed<kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWavePkSmem);
+      cudaFuncSetAttribute(k_sweep_wave_packed<kFirst>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      set[dev & 127] = true;
+    }
+  }
+  const int64_t units = (int64_t)a.nbands * nseg;
+  k_sweep_wave_packed<kFirst><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWavePkSmem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -137,3 +137,11 @@ def test_int8_calls_are_refused():
 
 def test_larger_3d_lattice():
     _compare((64, 64, 64), inputs.unit_seed(503), [(0.69, 3)])
+
+
+def test_lattice_where_warps_drain_their_queue_midway():
+    """2D 3072 x 3072: 36864 groups of 128 sites per colour for about 6000 warps,
+    so a warp collects 32 sites whose first proposal call missed several times
+    over a launch and finishes them before its last group."""
+    _compare((3072, 3072), inputs.unit_seed(504), [(0.9, 2)])
+

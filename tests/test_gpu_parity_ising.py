@@ -75,6 +75,15 @@ def test_ising2d_band_parallel(dims, tiling):
              tiling=tiling, stream=6)
 
 
+@pytest.mark.parametrize("dims,tiling", [((2048, 2048), (0, 1, 1)), ((4096, 1024), (0, 1, 2))])
+def test_ising2d_band_parallel_long_segments(dims, tiling):
+    """Segments of 512 to 2048 rows: a warp defers a few hundred colour-1 words
+    still tied after 12 planes, so its queue is drained many times in the
+    middle of the segment (32 words at a time) as well as at the end."""
+    _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(19), [(1.0 / TC, 3), (0.3, 1)], path=spn.PATH_STREAM,
+             tiling=tiling, stream=7)
+
+
 @pytest.mark.parametrize("dims,tiling", [((64, 32, 8), (32, 1, 0)), ((128, 16, 6), (16, 1, 3)),
                                          ((256, 16, 10), (8, 1, 0)), ((256, 16, 10), (16, 0, 10)),
                                          ((512, 32, 4), (32, 1, 0)), ((512, 32, 6), (4, 1, 5)),

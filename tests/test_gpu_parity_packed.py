@@ -53,6 +53,18 @@ def test_packed_2d_ragged_rows(dims, tiling):
     _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(42), [(1.0 / TC, 9), (0.3, 2)], tiling=tiling, stream=4)
 
 
+@pytest.mark.parametrize("dims,tiling", [((2048, 64), None), ((4096, 30), (0, 1, 7)), ((16384, 12), (0, 1, 1)),
+                                         ((2048, 2), None), ((2048, 4), (0, 1, 3)), ((8192, 40), (0, 0, 13)),
+                                         ((2176, 20), None), ((3072, 8), (0, 1, 3)), ((2048, 2048), (0, 1, 1))])
+def test_packed_2d_band_parallel(dims, tiling):
+    """Bit-packed rows of at least 2048 sites in an even number of 64-site words
+    take the band-parallel kernel, each lane copying its two words of a row:
+    bands that wrap around the row end, a last band of one to 29 words, segments
+    down to one row, two-row lattices, and 2048-row segments whose warps drain
+    their queue of tied colour-1 words many times."""
+    _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(45), [(1.0 / TC, 7), (0.3, 2)], tiling=tiling, stream=6)
+
+
 @pytest.mark.parametrize("tiling", [(2, 1, 1), (4, 2, 5), (8, 1, 12), (16, 3, 2), (16, 1, 0)])
 def test_packed_3d_tilings(tiling):
     _compare(spn.SPN_ISING3D, (64, 16, 12), inputs.unit_seed(43), [(inputs.BETA_C_3D, 6)], tiling=tiling)
