@@ -86,7 +86,8 @@ size_t dw_smem(int hits) {
          (size_t)kDwWarps * kDwRing * 8;
 }
 
-template <int HITS>
+// AL: some class with dE > 0 may be always accepted (beta = 0 or tiny), else that test is left out
+template <int HITS, bool AL>
 __global__ void __launch_bounds__(32 * kDwWarps, 1) k_sweep_dcwave(const __grid_constant__ DwArgs a) {
   constexpr int NC = 2;  // classes with dE > 0: dE = 4, 8
   extern __shared__ __align__(128) uint8_t smem[];
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(32 * kDwWarps, 1) k_sweep_dcwave(const __grid_
     uint32_t eq[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const bool always = (a.always >> (k + 1)) & 1u;
+      const bool always = AL && ((a.always >> (k + 1)) & 1u);  // AL false: no class is (compile time)
       acc |= always ? cls[k] : 0u;
       eq[k] = always ? 0u : cls[k];
     }
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(32 * kDwWarps, 1) k_sweep_dcwave(const __grid_
 int dw_nbands(const Lattice& g) { return (g.Lx / 64 + kDwOwned - 1) / kDwOwned; }
 
 using DwKernel = void (*)(DwArgs);
-DwKernel dw_kernel(int) { return k_sweep_dcwave<1>; }
+DwKernel dw_kernel(int, bool al) { return al ? k_sweep_dcwave<1, true> : k_sweep_dcwave<1, false>; }
 
 // the shared-memory attributes of the kernel for `hits`, once per device
 void dw_prepare(int hits) {
@@ -304,8 +305,10 @@ void dw_prepare(int hits) {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(mu);
   if (!set[dev & 127][hits]) {
-    cudaFuncSetAttribute(dw_kernel(hits), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(hits));
-    cudaFuncSetAttribute(dw_kernel(hits), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    for (bool al : {false, true}) {
+      cudaFuncSetAttribute(dw_kernel(hits, al), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(hits));
+      cudaFuncSetAttribute(dw_kernel(hits, al), cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     set[dev & 127][hits] = true;
   }
 }
@@ -329,7 +332,7 @@ int dcwave_default_segments(const Lattice& g, int hits) {
     std::lock_guard<std::mutex> lock(mu);
     if (!per_sm[hits]) {
       int blocks = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dw_kernel(hits), 32 * kDwWarps, dw_smem(hits)) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dw_kernel(hits, false), 32 * kDwWarps, dw_smem(hits)) !=
           cudaSuccess)
         blocks = 1;
       per_sm[hits] = std::max(1, blocks);
@@ -371,7 +374,8 @@ cudaError_t launch_sweep_dcwave(const Lattice& g, const int8_t* in, int8_t* out,
   }
   dw_prepare(hits);
   const int64_t units = (int64_t)a.nbands * nseg;
-  dw_kernel(hits)<<<(unsigned)((units + kDwWarps - 1) / kDwWarps), 32 * kDwWarps, dw_smem(hits), st>>>(a);
+  dw_kernel(hits, (T.always & 6u) != 0)<<<(unsigned)((units + kDwWarps - 1) / kDwWarps), 32 * kDwWarps, dw_smem(hits),
+                                          st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -85,7 +85,9 @@ constexpr size_t kWaveSmem = (size_t)kWarps * kRing * kBandBytes  // raw slots
                              + (size_t)kWarps * kRing * 8          // mbarriers
                              + (size_t)kWarps * kTieQueue * 24;    // tie queues: (c0, eq0, eq1, b), (row, word)
 
-template <int FC>  // Philox calls (4 planes each) of the first decision stage
+// FC: Philox calls (4 planes each) of the first decision stage; AL: some class
+// with dE > 0 may be always accepted (beta = 0 or tiny), else that test is left out
+template <int FC, bool AL>
 __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __grid_constant__ WaveArgs a) {
   constexpr int NC = 2;  // classes with dE > 0: dE = 4, 8
   extern __shared__ __align__(128) uint8_t smem[];
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave(const __
     uint32_t eq[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const bool always = (a.always >> (k + 1)) & 1u;
+      const bool always = AL && ((a.always >> (k + 1)) & 1u);  // AL false: no class is (compile time)
       acc |= always ? cls[k] : 0u;
       eq[k] = always ? 0u : cls[k];
     }
@@ -359,7 +361,7 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int FC>
+template <int FC, bool AL>
 __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave_packed(const __grid_constant__ WavePkArgs a) {
   constexpr int NC = 2;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave_packed(c
     uint32_t eq[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const bool always = (a.always >> (k + 1)) & 1u;
+      const bool always = AL && ((a.always >> (k + 1)) & 1u);  // AL false: no class is (compile time)
       acc |= always ? cls[k] : 0u;
       eq[k] = always ? 0u : cls[k];
     }
@@ -505,6 +507,13 @@ __global__ void __launch_bounds__(32 * kWarps, kMinBlocks) k_sweep_wave_packed(c
 
 int nbands_of(const Lattice& g) { return (g.Lx / 64 + kOwned - 1) / kOwned; }
 
+void set_wave_attributes() {
+  for (auto k : {k_sweep_wave<kFirst, false>, k_sweep_wave<kFirst, true>}) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWaveSmem);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
+}
+
 }  // namespace
 
 bool wave_supported(const Lattice& g) {
@@ -532,10 +541,9 @@ int wave_default_segments(const Lattice& g) {
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!per_sm) {
-      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWaveSmem);
-      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      set_wave_attributes();
       int blocks = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave<kFirst>, 32 * kWarps, kWaveSmem) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave<kFirst, false>, 32 * kWarps, kWaveSmem) !=
           cudaSuccess)
         blocks = 1;
       per_sm = std::max(1, blocks);
@@ -579,13 +587,15 @@ cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, i
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (!set[dev & 127]) {
-      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWaveSmem);
-      cudaFuncSetAttribute(k_sweep_wave<kFirst>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      set_wave_attributes();
       set[dev & 127] = true;
     }
   }
   const int64_t units = (int64_t)a.nbands * nseg;
-  k_sweep_wave<kFirst><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWaveSmem, st>>>(a);
+  if (T.always & 6u)
+    k_sweep_wave<kFirst, true><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWaveSmem, st>>>(a);
+  else
+    k_sweep_wave<kFirst, false><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWaveSmem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -616,13 +626,18 @@ cudaError_t launch_sweep_wave_packed(const Lattice& g, const uint32_t* in, uint3
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (!set[dev & 127]) {
-      cudaFuncSetAttribute(k_sweep_wave_packed<kFirst>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWavePkSmem);
-      cudaFuncSetAttribute(k_sweep_wave_packed<kFirst>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      for (auto k : {k_sweep_wave_packed<kFirst, false>, k_sweep_wave_packed<kFirst, true>}) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWavePkSmem);
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
       set[dev & 127] = true;
     }
   }
   const int64_t units = (int64_t)a.nbands * nseg;
-  k_sweep_wave_packed<kFirst><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWavePkSmem, st>>>(a);
+  if (T.always & 6u)
+    k_sweep_wave_packed<kFirst, true><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWavePkSmem, st>>>(a);
+  else
+    k_sweep_wave_packed<kFirst, false><<<(unsigned)((units + kWarps - 1) / kWarps), 32 * kWarps, kWavePkSmem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

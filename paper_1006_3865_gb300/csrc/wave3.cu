@@ -87,6 +87,8 @@ __device__ __forceinline__ void mbar_arrive3(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// AL: some class with dE > 0 may be always accepted (beta = 0 or tiny), else that test is left out
+template <bool AL>
 __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_constant__ Wave3Args a) {
   constexpr int NC = 3;  // classes with dE > 0: dE = 4, 8, 12
   extern __shared__ __align__(128) uint8_t smem_all[];
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
     uint32_t eq[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      const bool always = (a.always >> (k + 1)) & 1u;
+      const bool always = AL && ((a.always >> (k + 1)) & 1u);  // AL false: no class is (compile time)
       acc |= always ? cls[k] : 0u;
       eq[k] = always ? 0u : cls[k];
     }
@@ -358,6 +360,13 @@ bool wave3_supported(const Lattice& g, int TY) {
 
 namespace {
 
+void set_wave3_attributes() {
+  for (auto k : {k_sweep_wave3<false>, k_sweep_wave3<true>}) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
+}
+
 size_t unit_smem_of(int TY, int W, int nwc) { return (wave3_smem(TY, W, nwc) + 127) & ~(size_t)127; }
 
 // Units one SM holds at once (from the occupancy of a one-unit CTA, within the
@@ -369,10 +378,9 @@ int units_per_cta(int TY, int W, int nwc) {
   std::lock_guard<std::mutex> lock(mu);
   if (!per_sm[nwc][lw]) {
     const size_t sm = unit_smem_of(TY, W, nwc);
-    cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    set_wave3_attributes();
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave3, 32 * (nwc + 1), sm) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave3<false>, 32 * (nwc + 1), sm) != cudaSuccess)
       blocks = 1;
     int u = std::max(1, blocks);
     u = std::min(u, kW3MaxThreads / (32 * (nwc + 1)));
@@ -441,13 +449,16 @@ cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, 
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (!set[dev & 127]) {
-      cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-      cudaFuncSetAttribute(k_sweep_wave3, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      set_wave3_attributes();
       set[dev & 127] = true;
     }
   }
   const int64_t units = (int64_t)(g.Ly / TY) * nseg;
-  k_sweep_wave3<<<(unsigned)((units + a.units - 1) / a.units), 32 * (a.nwc + 1) * a.units, sm, st>>>(a);
+  const unsigned grid = (unsigned)((units + a.units - 1) / a.units), block = 32 * (a.nwc + 1) * a.units;
+  if (T.always & 14u)
+    k_sweep_wave3<true><<<grid, block, sm, st>>>(a);
+  else
+    k_sweep_wave3<false><<<grid, block, sm, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -77,7 +77,7 @@ def test_packed_3d_ragged_rows(dims, tiling):
 
 
 @pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (64, 32)), (spn.SPN_ISING2D, (130, 6)),
-                                        (spn.SPN_ISING3D, (64, 8, 6))])
+                                        (spn.SPN_ISING3D, (64, 8, 6)), (spn.SPN_ISING2D, (2048, 16))])
 def test_packed_beta_zero_and_infinity(model, dims):
     s = _compare(model, dims, 11, [(0.0, 3)])
     assert np.array_equal(s, -oracle.init_hot(dims, 11))
