@@ -34,7 +34,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-template <int ND, bool CLUSTER>
+// AL: an instance may have a class with dE > 0 that is always accepted; else
+// that test is left out (ResArgs.no_always)
+template <int ND, bool CLUSTER, bool AL>
 __global__ void __launch_bounds__(512) k_resident(ResArgs a) {  // every caller launches at most 512 threads
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_idx;
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(512) k_resident(ResArgs a) {  // every caller 
           uint32_t eq[ND];
 #pragma unroll
           for (int k = 0; k < ND; ++k) {
-            const bool always = (in.T.always >> (k + 1)) & 1u;
+            const bool always = AL && ((in.T.always >> (k + 1)) & 1u);
             flips |= always ? cls[k] : 0u;
             eq[k] = always ? 0u : cls[k];
           }
@@ -310,12 +312,21 @@ int resident_cluster_size(int nd, int Lx, int Ly, int Lz, int max_cs) {
   return 0;
 }
 
-cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, size_t smem, cudaStream_t st) {
-  void (*fn)(ResArgs) = nullptr;
+namespace {
+
+using ResKernel = void (*)(ResArgs);
+ResKernel resident_kernel(int nd, int cs, bool al) {
   if (nd == 3)
-    fn = cs > 1 ? k_resident<3, true> : k_resident<3, false>;
-  else
-    fn = cs > 1 ? k_resident<2, true> : k_resident<2, false>;
+    return cs > 1 ? (al ? k_resident<3, true, true> : k_resident<3, true, false>)
+                  : (al ? k_resident<3, false, true> : k_resident<3, false, false>);
+  return cs > 1 ? (al ? k_resident<2, true, true> : k_resident<2, true, false>)
+                : (al ? k_resident<2, false, true> : k_resident<2, false, false>);
+}
+
+}  // namespace
+
+cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int ctas, size_t smem, cudaStream_t st) {
+  const ResKernel fn = resident_kernel(nd, cs, !a.no_always);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && cs > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
@@ -338,12 +349,9 @@ cudaError_t launch_resident(const ResArgs& a, int nd, int cs, int threads, int c
   return e;
 }
 
-int resident_max_ctas(int nd, int cs, int threads, size_t smem) {
-  void (*fn)(ResArgs) = nullptr;
-  if (nd == 3)
-    fn = cs > 1 ? k_resident<3, true> : k_resident<3, false>;
-  else
-    fn = cs > 1 ? k_resident<2, true> : k_resident<2, false>;
+namespace {
+
+int max_ctas_of(ResKernel fn, int cs, int threads, size_t smem) {
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (cs > 1) {
     // clusters are placed within one GPC: fewer fit than CTAs per SM x SMs suggests
@@ -370,6 +378,14 @@ int resident_max_ctas(int nd, int cs, int threads, size_t smem) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
   if (per_sm <= 0) per_sm = 1;
   return per_sm * device_sm_count();
+}
+
+}  // namespace
+
+// the fewer of the two kernels (with and without the always-accepted test)
+int resident_max_ctas(int nd, int cs, int threads, size_t smem) {
+  return std::min(max_ctas_of(resident_kernel(nd, cs, true), cs, threads, smem),
+                  max_ctas_of(resident_kernel(nd, cs, false), cs, threads, smem));
 }
 
 }  // namespace spn

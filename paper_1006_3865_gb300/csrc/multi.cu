@@ -39,6 +39,7 @@ struct Group {
   int nd, Lx, Ly, Lz, cs, threads, ctas;
   size_t smem = 0;
   double tuned_rate = 0.0;  // attempts/ns of the autotuner's trial (0: not tuned)
+  bool no_always = true;    // no instance has an always-accepted class with dE > 0
   std::vector<int> jobs;  // job indices, longest first
   spn::ResInst* d_inst = nullptr;
   int* d_order = nullptr;
@@ -116,6 +117,7 @@ cudaError_t enqueue_batched(spn_multi_ctx* m) {
     a.order = g.d_order;
     a.counter = m->d_counters + gi;
     a.err = m->d_err;
+    a.no_always = g.no_always;
     if ((e = spn::launch_resident(a, g.nd, g.cs, g.threads, g.ctas, g.smem, g.st)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(g.done, g.st)) != cudaSuccess) return e;
   }
@@ -245,6 +247,7 @@ int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs) {
       r.Ly = g.Ly;
       r.Lz = g.Lz;
       r.T = spn::make_thresholds(j.beta);
+      g.no_always = g.no_always && spn::no_always_class(r.T);
       order[k] = (int)k;
     }
     if (cudaMalloc(&g.d_inst, inst.size() * sizeof(spn::ResInst)) != cudaSuccess ||
@@ -408,6 +411,7 @@ int spn_multi_autotune(spn_multi m, int32_t trial_sweeps, double* rates, size_t 
         a.order = g.d_order;
         a.counter = m->d_counters + gi;
         a.err = m->d_err;
+        a.no_always = g.no_always;
         if (cudaStreamWaitEvent(g.st, m->fork, 0) != cudaSuccess ||
             spn::launch_resident(a, g.nd, g.cs, g.threads, g.ctas, g.smem, g.st) != cudaSuccess ||
             cudaEventRecord(g.done, g.st) != cudaSuccess || cudaStreamWaitEvent(m->st, g.done, 0) != cudaSuccess)

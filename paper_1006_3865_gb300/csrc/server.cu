@@ -536,6 +536,8 @@ int round_launch(spn_server_ctx* s, std::vector<std::shared_ptr<Job>>& act) {
       a.order = s->d_order + L.first;  // local indices into the launch's slice
       a.counter = s->d_counters + li;
       a.err = s->d_err;
+      a.no_always = true;
+      for (size_t k = L.first; k < L.first + L.count; ++k) a.no_always = a.no_always && spn::no_always_class(inst[k].T);
       const auto key = std::make_tuple(L.nd, L.cs, L.threads, L.smem);
       auto it = s->max_ctas.find(key);
       if (it == s->max_ctas.end())

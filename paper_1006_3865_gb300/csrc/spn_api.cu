@@ -392,6 +392,7 @@ int spn_sweep(spn_handle h, double beta, int64_t nsweeps) {
       a.order = h->d_resq;
       a.counter = h->d_resq + 1;
       a.err = h->d_err;
+      a.no_always = spn::no_always_class(T);
       // r is pageable: the copy is staged before the call returns
       cudaError_t e = cudaMemcpyAsync(h->d_res, &r, sizeof r, cudaMemcpyHostToDevice, h->st);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->d_resq + 1, 0, sizeof(int), h->st);

@@ -131,7 +131,14 @@ struct ResArgs {
   const int* order;     // queue order (longest first)
   int* counter;         // queue head, zeroed by the caller
   int* err;
+  // set by a caller that knows no instance has a class with dE > 0 that is
+  // always accepted (DevThr.always & 14 == 0): the kernel is then compiled
+  // without that test; left false, the general kernel runs
+  bool no_always;
 };
+
+// true iff no class with dE > 0 of these thresholds is always accepted
+inline bool no_always_class(const DevThr& T) { return (T.always & 14u) == 0; }
 
 bool resident_supported(int nd, int Lx, int Ly, int Lz, int cs);
 size_t resident_smem(int nd, int Lx, int Ly, int Lz, int cs);
