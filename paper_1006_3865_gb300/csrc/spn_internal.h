@@ -35,7 +35,8 @@ enum Path : int { kPathGeneric = 0, kPathStream = 1, kPathResident = 2, kPathPac
 struct StreamGeom {
   int packed;
   int wave;  // 1: the 2D band-parallel kernel (wave.cu), nseg row segments; 2: the 3D wavefront kernel (wave3.cu);
-            // 3: the 2D band-parallel kernel on a bit-packed lattice (wave.cu)
+            // 3: the 2D band-parallel kernel on a bit-packed lattice (wave.cu); 4: the 3D wavefront kernel on a
+            // bit-packed lattice (wave3.cu)
   int TY, R, nseg, threads, nraw, nbit;
   int roundsC, roundsA, roundsB, qcap;  // words per thread per phase; tie-queue entries per warp
   size_t smem;
@@ -95,12 +96,15 @@ cudaError_t launch_sweep_wave(const Lattice& g, const int8_t* in, int8_t* out, i
 // dense rows, no bonds, band height TY a multiple of 32 / (Lx / 64) with at most
 // eight compute warps, dividing Ly; nseg segments along z.
 bool wave3_supported(const Lattice& g, int TY);
-int wave3_default_segments(const Lattice& g, int TY);
-size_t wave3_smem_bytes(const Lattice& g, int TY);  // of one CTA
-int wave3_cta_threads(const Lattice& g, int TY);
+int wave3_default_segments(const Lattice& g, int TY, bool packed = false);
+size_t wave3_smem_bytes(const Lattice& g, int TY, bool packed = false);  // of one CTA
+int wave3_cta_threads(const Lattice& g, int TY, bool packed = false);
 cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, int TY, int nseg, const DevThr& T,
                                const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
                                int* err, cudaStream_t st, uint32_t expire_polls);
+cudaError_t launch_sweep_wave3_packed(const Lattice& g, const uint32_t* in, uint32_t* out, int TY, int nseg,
+                                      const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                      unsigned long long* acc, int* err, cudaStream_t st);
 StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packed = false);
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo);
 // expire_polls (test support, 0 otherwise): the copy of each CTA's first slice

@@ -459,6 +459,15 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packe
     s.smem = wave3_smem_bytes(g, TY);
     return s;
   }
+  if (packed && R <= 1 && g.nd == 3 && wave3_supported(g, TY)) {  // one plane per step: the 3D wavefront, bit-packed
+    s.wave = 4;
+    s.TY = TY;
+    s.R = 1;
+    s.threads = wave3_cta_threads(g, TY, true);
+    s.nseg = nseg > 0 ? std::min(nseg, g.Lz) : wave3_default_segments(g, TY, true);
+    s.smem = wave3_smem_bytes(g, TY, true);
+    return s;
+  }
   if (packed && R <= 1 && wave_packed_supported(g)) {  // one row per step: the band-parallel kernel, bit-packed
     s.wave = 3;
     s.TY = 1;
@@ -527,6 +536,7 @@ StreamGeom stream_geometry(const Lattice& g, int TY, int R, int nseg, bool packe
 bool stream_geometry_ok(const Lattice& g, const StreamGeom& geo) {
   const bool packed = geo.packed != 0;
   if (geo.wave == 2) return !packed && wave3_supported(g, geo.TY) && geo.nseg >= 1 && geo.nseg <= g.Lz;
+  if (geo.wave == 4) return packed && wave3_supported(g, geo.TY) && geo.nseg >= 1 && geo.nseg <= g.Lz;
   if (geo.wave == 3) return packed && wave_packed_supported(g) && geo.nseg >= 1 && geo.nseg <= g.Ly;
   if (geo.wave) return !packed && wave_supported(g) && geo.nseg >= 1 && geo.nseg <= g.Ly;
   if (geo.R < 1 || geo.R > 127 || geo.threads < 32 || geo.threads > max_threads(g.nd) || geo.threads % 32) return false;
@@ -547,6 +557,14 @@ cudaError_t launch_sweep_stream(const Lattice& g, const void* in, void* out, con
   if (geo.wave == 2)
     return launch_sweep_wave3(g, static_cast<const int8_t*>(in), static_cast<int8_t*>(out), geo.TY, geo.nseg, T, K,
                               stream_id, sweep, acc, err, st, expire_polls);
+  if (geo.wave == 4) {
+    if (expire_polls) {  // test support: armed launches go to the CTA pipeline, as for wave 3
+      const StreamGeom alt = stream_geometry(g, geo.TY, 2, 0, true);
+      return launch_sweep_stream(g, in, out, alt, T, K, stream_id, sweep, acc, err, st, expire_polls);
+    }
+    return launch_sweep_wave3_packed(g, static_cast<const uint32_t*>(in), static_cast<uint32_t*>(out), geo.TY, geo.nseg,
+                                     T, K, stream_id, sweep, acc, err, st);
+  }
   if (geo.wave == 3) {
     if (expire_polls) {  // test support: that kernel has no bounded wait to give up; the CTA pipeline takes the launch
       const StreamGeom alt = stream_geometry(g, 1, 2, 0, true);

@@ -49,6 +49,8 @@ constexpr int kW3Compute = 8;                  // compute warps at most (TY = 32
 constexpr int kW3Warps = kW3Compute + 1;       // plus the halo warp
 constexpr int kW3Ring = 3;                     // raw slots per warp
 constexpr int kW3Planes = 4;                   // bit planes k .. k+3 live at step k
+constexpr int kW3PkPlanes = 8;                 // bit-packed lattices: four more planes on their way
+constexpr int kW3PkAhead = 4;                  // bit-packed: plane k + 3 + kW3PkAhead is requested at step k
 constexpr int kW3Slot = 2048;                  // bytes of one raw slot
 constexpr int kW3First = 3;                    // Philox calls of the first decision stage (12 planes)
 // A CTA holds several units (band, segment) side by side, as many as one SM
@@ -72,7 +74,14 @@ struct Wave3Args {
   int* err;
   uint32_t wait_limit;  // polls of a bounded wait before it gives up
   uint32_t skip_first;  // test support: plane 0's copies are never issued
+  const uint32_t* in_pk;  // bit-packed lattices: rows of RS words (W words of even-x sites, W of odd-x)
+  uint32_t* out_pk;
+  int RS;
 };
+
+size_t wave3_smem_packed(int TY, int W, int nwc) {
+  return (size_t)kW3PkPlanes * (TY + 4) * 2 * W * 4 + (size_t)(nwc + 1) * 2 * 8;  // bit planes, step mbarriers
+}
 
 size_t wave3_smem(int TY, int W, int nwc) {
   const int nw = nwc + 1;
@@ -87,8 +96,15 @@ __device__ __forceinline__ void mbar_arrive3(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// AL: some class with dE > 0 may be always accepted (beta = 0 or tiny), else that test is left out
-template <bool AL>
+__device__ __forceinline__ void cp_async4_w3(uint32_t* dst, const uint32_t* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// AL: some class with dE > 0 may be always accepted (beta = 0 or tiny), else that test is left out.
+// PK: the lattice is bit-packed; a lane copies its E and O word of each of its
+// rows straight into the plane ring (cp.async, a commit group per plane) and
+// writes them back as they are, so no raw slots, no conversion, no int8 table.
+template <bool AL, bool PK>
 __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_constant__ Wave3Args a) {
   constexpr int NC = 3;  // classes with dE > 0: dE = 4, 8, 12
   extern __shared__ __align__(128) uint8_t smem_all[];
@@ -100,11 +116,14 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
   const int tid = (int)threadIdx.x - 32 * nw * sub;     // thread within its unit
   uint8_t* smem = smem_all + (size_t)sub * a.unit_smem;
   const bool halo = warp == nwc;
-  uint8_t* raw = smem + (size_t)warp * kW3Ring * kW3Slot;  // this warp's slots
-  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + (size_t)nw * kW3Ring * kW3Slot);
-  uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)kW3Planes * rows * W2);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256) + warp * kW3Ring;
-  uint64_t* steps = reinterpret_cast<uint64_t*>(lut + 256) + nw * kW3Ring;  // [warp][2]
+  constexpr int NPL = PK ? kW3PkPlanes : kW3Planes;  // planes of the ring
+  uint8_t* raw = smem + (size_t)warp * kW3Ring * kW3Slot;  // this warp's slots (int8)
+  uint32_t* bits = PK ? reinterpret_cast<uint32_t*>(smem)
+                      : reinterpret_cast<uint32_t*>(smem + (size_t)nw * kW3Ring * kW3Slot);
+  uint2* lut = reinterpret_cast<uint2*>(bits + (size_t)kW3Planes * rows * W2);  // int8 only
+  uint64_t* bars = reinterpret_cast<uint64_t*>(lut + 256) + warp * kW3Ring;   // int8 only
+  uint64_t* steps = PK ? reinterpret_cast<uint64_t*>(bits + (size_t)kW3PkPlanes * rows * W2)
+                       : reinterpret_cast<uint64_t*>(lut + 256) + nw * kW3Ring;  // [warp][2]
   const uint4* raw16 = reinterpret_cast<const uint4*>(raw);
 
   const int bands = Ly / TY;
@@ -121,7 +140,7 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
   const int wr = halo ? nwc - 1 : (warp == nwc - 1 ? nwc : warp + 1);
 
   // int8 pattern of 8 sites [e0 o0 e1 o1 e2 o2 e3 o3] for index e | o << 4
-  for (int i = tid; i < 256; i += 32 * nw) {
+  for (int i = tid; !PK && i < 256; i += 32 * nw) {
     uint32_t lo = 0, hi = 0;
     for (int k = 0; k < 4; ++k) {
       const uint32_t pair = (((i >> k) & 1) ? 0xffu : 0x01u) | ((((i >> (4 + k)) & 1) ? 0xffu : 0x01u) << 8);
@@ -130,7 +149,7 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
     lut[i] = make_uint2(lo, hi);
   }
   if (lane == 0) {
-    for (int b = 0; b < kW3Ring; ++b) mbar_init(&bars[b], 1);
+    for (int b = 0; !PK && b < kW3Ring; ++b) mbar_init(&bars[b], 1);
     mbar_init(&steps[2 * warp], 1);
     mbar_init(&steps[2 * warp + 1], 1);
     fence_mbar_init();
@@ -153,7 +172,7 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
   const int r0 = halo ? -2 : RPW * warp;
   const int slotBytes = halo ? 4 * Lx : RPW * Lx;
   auto issue = [&](int li) {
-    if (lane == 0 && li < nload) {
+    if (!PK && lane == 0 && li < nload) {
       uint64_t* bar = &bars[li % kW3Ring];
       uint8_t* dst = raw + (size_t)(li % kW3Ring) * kW3Slot;
       const int8_t* plane = a.in + (int64_t)gz(li) * Ly * Lx;
@@ -170,16 +189,28 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
     }
   };
   int issued = 0;
-  for (; issued < kW3Ring && issued < nload; ++issued) issue(issued);
+  if constexpr (!PK)
+    for (; issued < kW3Ring && issued < nload; ++issued) issue(issued);
 
   const int rot = (lane >> 1) & 3;
   const uint32_t rot_sel = (uint32_t)(((0 - rot) & 3) | (((1 - rot) & 3) << 4) | (((2 - rot) & 3) << 8) |
                                       (((3 - rot) & 3) << 12));
-  auto plane_bits = [&](int li) { return bits + (size_t)(li & (kW3Planes - 1)) * rows * W2; };
+  auto plane_bits = [&](int li) { return bits + (size_t)(li & (NPL - 1)) * rows * W2; };
   // conversion: lane -> (row of the slot, word); the halo warp's slot holds rows -2, -1, TY, TY + 1
   const int cslot_row = lane / W, cj = lane - (lane / W) * W;
   const bool cvalid = halo ? lane < 4 * W : true;
   const int crr = halo ? (cslot_row < 2 ? cslot_row - 2 : TY + cslot_row - 2) : r0 + cslot_row;
+  // bit-packed: request plane li, this lane's E and O word of its row; one commit
+  // group per call (an empty one past the last plane keeps the count)
+  auto issue_pk = [&](int li) {
+    if (cvalid && li < nload) {
+      const uint32_t* src = a.in_pk + ((int64_t)gz(li) * Ly + gy(crr)) * a.RS;
+      uint32_t* dst = plane_bits(li) + (size_t)(crr + 2) * W2;
+      cp_async4_w3(dst + cj, src + cj);
+      cp_async4_w3(dst + W + cj, src + W + cj);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
 
   auto convert = [&](int li) -> bool {
     unsigned n = 0;
@@ -255,7 +286,11 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
     const uint32_t nb = b ^ acc;
     if (ustore) p0[ws] = nb;
     if (!halo && li >= 2 && li < H + 2) tally<3>(acc, b, s0, s1, s2, de, dm);
-    if (c == 1) {
+    if (c == 1 && PK) {
+      uint32_t* o = a.out_pk + ((int64_t)z * Ly + y) * a.RS;
+      o[uj] = par ? oj : nb;
+      o[W + uj] = par ? nb : oj;
+    } else if (c == 1) {
       const uint32_t E = par ? oj : nb, O = par ? nb : oj;
       const uint32_t X = (E & 0x0f0f0f0fu) | ((O << 4) & 0xf0f0f0f0u);  // byte v: sites 16v .. 16v + 7
       const uint32_t Y = ((E >> 4) & 0x0f0f0f0fu) | (O & 0xf0f0f0f0u);  // byte v: sites 16v + 8 .. 16v + 15
@@ -297,12 +332,18 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
     return __all_sync(0xffffffffu, ok);
   };
 
-  // prologue (counts as step 1): planes 0, 1, 2 converted; then colour 0 of plane 1
+  // prologue (counts as step 1): planes 0, 1, 2 converted (bit-packed: landed); then colour 0 of plane 1
   bool ok = true;
-  for (int li = 0; li < 3 && ok; ++li) {
-    ok = __all_sync(0xffffffffu, convert(li));
+  if constexpr (PK) {
+    for (int li = 0; li < 3 + kW3PkAhead; ++li) issue_pk(li);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kW3PkAhead) : "memory");
     __syncwarp();
-    if (ok) issue(issued++);
+  } else {
+    for (int li = 0; li < 3 && ok; ++li) {
+      ok = __all_sync(0xffffffffu, convert(li));
+      __syncwarp();
+      if (ok) issue(issued++);
+    }
   }
   if (ok) {
     publish(1);
@@ -317,13 +358,28 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
   for (int k = 0; ok && k <= H; ++k) {
     ok = wait_neighbours(k + 2);
     if (!ok) break;
-    ok = __all_sync(0xffffffffu, convert(k + 3));
-    if (!ok) break;
-    __syncwarp();
-    issue(issued++);
+    if constexpr (PK) {
+      // the neighbours have finished step k - 1, the last to read plane k - 1:
+      // its ring plane takes plane k + 3 + kW3PkAhead; plane k + 3 has landed
+      __syncwarp();
+      issue_pk(k + 3 + kW3PkAhead);
+      asm volatile("cp.async.wait_group %0;" ::"n"(kW3PkAhead) : "memory");
+      __syncwarp();
+    } else {
+      ok = __all_sync(0xffffffffu, convert(k + 3));
+      if (!ok) break;
+      __syncwarp();
+      issue(issued++);
+    }
     update(k + 2, 0);
     if (k >= 1 && !halo) update(k + 1, 1);
     publish(k + 3);
+  }
+  if (!ok && PK) {  // this warp gives up; its copies land before it exits
+    if (lane == 0) atomicExch(a.err, 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    return;
   }
   if (!ok) {  // this warp gives up; its neighbours' waits then run out as well
     if (lane == 0) {
@@ -341,6 +397,7 @@ __global__ void __launch_bounds__(kW3MaxThreads, 1) k_sweep_wave3(const __grid_c
     __syncwarp();
     return;
   }
+  if constexpr (PK) asm volatile("cp.async.wait_group 0;" ::: "memory");
   block_accumulate(de, dm, a.acc);
 }
 
@@ -361,63 +418,78 @@ bool wave3_supported(const Lattice& g, int TY) {
 namespace {
 
 void set_wave3_attributes() {
-  for (auto k : {k_sweep_wave3<false>, k_sweep_wave3<true>}) {
+  using W3Kernel = void (*)(Wave3Args);
+  const W3Kernel ks[4] = {k_sweep_wave3<false, false>, k_sweep_wave3<true, false>, k_sweep_wave3<false, true>,
+                          k_sweep_wave3<true, true>};
+  for (W3Kernel k : ks) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
 }
 
-size_t unit_smem_of(int TY, int W, int nwc) { return (wave3_smem(TY, W, nwc) + 127) & ~(size_t)127; }
+size_t unit_smem_of(int TY, int W, int nwc, bool pk) {
+  return ((pk ? wave3_smem_packed(TY, W, nwc) : wave3_smem(TY, W, nwc)) + 127) & ~(size_t)127;
+}
 
 // Units one SM holds at once (from the occupancy of a one-unit CTA, within the
 // thread and shared-memory limits of one CTA): the units of a CTA.
-int units_per_cta(int TY, int W, int nwc) {
+int units_per_cta(int TY, int W, int nwc, bool pk) {
   static std::mutex mu;
-  static int per_sm[kW3Compute + 1][4] = {};  // [compute warps][log2 W]
+  static int per_sm[2][kW3Compute + 1][4] = {};  // [packed][compute warps][log2 W]
   const int lw = W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3;
   std::lock_guard<std::mutex> lock(mu);
-  if (!per_sm[nwc][lw]) {
-    const size_t sm = unit_smem_of(TY, W, nwc);
+  int& cached = per_sm[pk ? 1 : 0][nwc][lw];
+  if (!cached) {
+    const size_t sm = unit_smem_of(TY, W, nwc, pk);
     set_wave3_attributes();
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_wave3<false>, 32 * (nwc + 1), sm) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pk ? k_sweep_wave3<false, true> : k_sweep_wave3<false, false>,
+                                                      32 * (nwc + 1), sm) != cudaSuccess)
       blocks = 1;
     int u = std::max(1, blocks);
     u = std::min(u, kW3MaxThreads / (32 * (nwc + 1)));
     u = std::min<int>(u, (int)((227 * 1024) / sm));
-    per_sm[nwc][lw] = std::max(1, u);
+    cached = std::max(1, u);
   }
-  return per_sm[nwc][lw];
+  return cached;
 }
 
 }  // namespace
 
-size_t wave3_smem_bytes(const Lattice& g, int TY) {
+size_t wave3_smem_bytes(const Lattice& g, int TY, bool packed) {
   const int W = g.Lx / 64, nwc = TY / (32 / W);
-  return (size_t)units_per_cta(TY, W, nwc) * unit_smem_of(TY, W, nwc);
+  return (size_t)units_per_cta(TY, W, nwc, packed) * unit_smem_of(TY, W, nwc, packed);
 }
 
-int wave3_cta_threads(const Lattice& g, int TY) {
+int wave3_cta_threads(const Lattice& g, int TY, bool packed) {
   const int W = g.Lx / 64, nwc = TY / (32 / W);
-  return 32 * (nwc + 1) * units_per_cta(TY, W, nwc);
+  return 32 * (nwc + 1) * units_per_cta(TY, W, nwc, packed);
 }
 
-int wave3_default_segments(const Lattice& g, int TY) {
+int wave3_default_segments(const Lattice& g, int TY, bool packed) {
   const int W = g.Lx / 64, nwc = TY / (32 / W);
   // one wave: a CTA per SM holding as many units as the SM keeps resident
   const int bands = g.Ly / TY;
-  const int want = device_sm_count() * units_per_cta(TY, W, nwc);
+  const int want = device_sm_count() * units_per_cta(TY, W, nwc, packed);
   return std::max(1, std::min(g.Lz, want / bands));
 }
 
-cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, int TY, int nseg, const DevThr& T,
-                               const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
-                               int* err, cudaStream_t st, uint32_t expire_polls) {
+namespace {
+
+// shared by the int8 and the bit-packed launch: in / out are int8 lattices or
+// bit-packed rows (pk), the rest of the arguments as for launch_sweep_wave3
+cudaError_t launch_w3(const Lattice& g, const void* in, void* out, bool pk, int TY, int nseg, const DevThr& T,
+                      const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc, int* err,
+                      cudaStream_t st, uint32_t expire_polls) {
   if (!wave3_supported(g, TY) || nseg < 1 || nseg > g.Lz) return cudaErrorInvalidConfiguration;
-  if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return cudaErrorMisalignedAddress;  // bulk copies, 16-B stores
+  if (pk ? (((uintptr_t)in & 3) || ((uintptr_t)out & 3)) : (((uintptr_t)in & 15) || ((uintptr_t)out & 15)))
+    return cudaErrorMisalignedAddress;  // int8: bulk copies and 16-byte stores; bit-packed: 4-byte copies
   Wave3Args a;
-  a.in = in;
-  a.out = out;
+  a.in = pk ? nullptr : static_cast<const int8_t*>(in);
+  a.out = pk ? nullptr : static_cast<int8_t*>(out);
+  a.in_pk = pk ? static_cast<const uint32_t*>(in) : nullptr;
+  a.out_pk = pk ? static_cast<uint32_t*>(out) : nullptr;
+  a.RS = packed_row_words(g.Lx);
   a.Lx = g.Lx;
   a.Ly = g.Ly;
   a.Lz = g.Lz;
@@ -439,8 +511,8 @@ cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, 
     a.skip_first = 1;
     a.wait_limit = expire_polls;
   }
-  a.units = units_per_cta(TY, a.W, a.nwc);
-  a.unit_smem = (unsigned)unit_smem_of(TY, a.W, a.nwc);
+  a.units = units_per_cta(TY, a.W, a.nwc, pk);
+  a.unit_smem = (unsigned)unit_smem_of(TY, a.W, a.nwc, pk);
   const size_t sm = (size_t)a.units * a.unit_smem;
   {
     static std::mutex mu;
@@ -455,12 +527,27 @@ cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, 
   }
   const int64_t units = (int64_t)(g.Ly / TY) * nseg;
   const unsigned grid = (unsigned)((units + a.units - 1) / a.units), block = 32 * (a.nwc + 1) * a.units;
-  if (T.always & 14u)
-    k_sweep_wave3<true><<<grid, block, sm, st>>>(a);
+  const bool al = (T.always & 14u) != 0;
+  if (pk)
+    (al ? k_sweep_wave3<true, true> : k_sweep_wave3<false, true>)<<<grid, block, sm, st>>>(a);
   else
-    k_sweep_wave3<false><<<grid, block, sm, st>>>(a);
+    (al ? k_sweep_wave3<true, false> : k_sweep_wave3<false, false>)<<<grid, block, sm, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_wave3(const Lattice& g, const int8_t* in, int8_t* out, int TY, int nseg, const DevThr& T,
+                               const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep, unsigned long long* acc,
+                               int* err, cudaStream_t st, uint32_t expire_polls) {
+  return launch_w3(g, in, out, false, TY, nseg, T, K, stream_id, sweep, acc, err, st, expire_polls);
+}
+
+cudaError_t launch_sweep_wave3_packed(const Lattice& g, const uint32_t* in, uint32_t* out, int TY, int nseg,
+                                      const DevThr& T, const PhiloxKeys& K, uint32_t stream_id, uint32_t sweep,
+                                      unsigned long long* acc, int* err, cudaStream_t st) {
+  return launch_w3(g, in, out, true, TY, nseg, T, K, stream_id, sweep, acc, err, st, 0);
 }
 
 }  // namespace spn

@@ -65,6 +65,20 @@ def test_packed_2d_band_parallel(dims, tiling):
     _compare(spn.SPN_ISING2D, dims, inputs.unit_seed(45), [(1.0 / TC, 7), (0.3, 2)], tiling=tiling, stream=6)
 
 
+@pytest.mark.parametrize("dims,tiling", [((64, 32, 8), (32, 1, 0)), ((128, 16, 6), (16, 1, 3)),
+                                         ((256, 16, 10), (8, 1, 0)), ((256, 16, 10), (16, 0, 10)),
+                                         ((512, 32, 4), (32, 1, 0)), ((512, 32, 6), (4, 1, 5)),
+                                         ((512, 24, 6), (12, 1, 2)), ((256, 24, 12), (24, 1, 7)),
+                                         ((256, 8, 2), (8, 1, 1)), ((512, 8, 4), (8, 1, 4))])
+def test_packed_3d_wavefront(dims, tiling):
+    """Bit-packed 3D rows of 64 to 512 sites take the wavefront kernel when one
+    plane is streamed per step, each lane copying its two words of a row of
+    every plane: one to eight compute warps, rows of one word (padded to four in
+    the stored row), a band that is the whole lattice, segments down to one
+    plane, two-plane lattices, ragged segment splits."""
+    _compare(spn.SPN_ISING3D, dims, inputs.unit_seed(46), [(inputs.BETA_C_3D, 6), (0.35, 2)], tiling=tiling, stream=8)
+
+
 @pytest.mark.parametrize("tiling", [(2, 1, 1), (4, 2, 5), (8, 1, 12), (16, 3, 2), (16, 1, 0)])
 def test_packed_3d_tilings(tiling):
     _compare(spn.SPN_ISING3D, (64, 16, 12), inputs.unit_seed(43), [(inputs.BETA_C_3D, 6)], tiling=tiling)
@@ -77,7 +91,8 @@ def test_packed_3d_ragged_rows(dims, tiling):
 
 
 @pytest.mark.parametrize("model,dims", [(spn.SPN_ISING2D, (64, 32)), (spn.SPN_ISING2D, (130, 6)),
-                                        (spn.SPN_ISING3D, (64, 8, 6)), (spn.SPN_ISING2D, (2048, 16))])
+                                        (spn.SPN_ISING3D, (64, 8, 6)), (spn.SPN_ISING2D, (2048, 16)),
+                                        (spn.SPN_ISING3D, (256, 16, 8))])
 def test_packed_beta_zero_and_infinity(model, dims):
     s = _compare(model, dims, 11, [(0.0, 3)])
     assert np.array_equal(s, -oracle.init_hot(dims, 11))
