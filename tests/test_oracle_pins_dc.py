@@ -1,9 +1,12 @@
 """Pins of the oracle's double-checkerboard sweep with generalised multi-hit
 (Sec. 3): the special case beta = 0, a plain restatement of the update order on
-tiny lattices, exact stationarity of one tile-parity / colour step, and long
-runs against exact enumeration and Kaufman's finite-lattice energy."""
+tiny lattices, exact stationarity of one tile-parity / colour step, long runs
+against exact enumeration and Kaufman's finite-lattice energy, and the 32 x 32
+decomposition of Fig. 1 from its text fixture under golden/."""
 
 from __future__ import annotations
+
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -137,3 +140,55 @@ def test_rejects_tilings_without_an_even_tile_count():
         oracle.sweeps_dc((12, 8), s, (4, 2), 1, 0.4, 1, 1)  # three tiles along x
     with pytest.raises(ValueError):
         oracle.sweeps_dc((12, 8), s, (5, 2), 1, 0.4, 1, 1)
+
+
+def _fig1_map():
+    """The phase map of Fig. 1 (Sec. 3), read from its text fixture."""
+    path = Path(__file__).parent / "golden" / "fig1_double_checkerboard_32x32.txt"
+    rows = [ln.strip() for ln in path.read_text().splitlines() if ln.strip() and not ln.startswith("#")]
+    return np.array([[int(ch) for ch in r] for r in rows], dtype=np.int64)
+
+
+def test_fig1_decomposition_counts():
+    """Fig. 1 has B^2 / 2 = 8 even and 8 odd tiles, and the procedure of Sec. 3
+    gives each tile T^2 / 2 = 32 sites of either sub-lattice."""
+    ph = _fig1_map()
+    assert ph.shape == (32, 32)
+    for P in (0, 1):
+        tiles = [(ty, tx) for ty in range(4) for tx in range(4)
+                 if np.all(ph[8 * ty:8 * ty + 8, 8 * tx:8 * tx + 8] // 2 == P)]
+        assert len(tiles) == 8
+        for ty, tx in tiles:
+            blk = ph[8 * ty:8 * ty + 8, 8 * tx:8 * tx + 8] % 2
+            assert np.count_nonzero(blk == 0) == 32 and np.count_nonzero(blk == 1) == 32
+    # the two sub-lattices of the fine level are each an independent set of the torus
+    for c in (0, 1):
+        m = (ph % 2) == c
+        assert not np.any(m & np.roll(m, 1, 0)) and not np.any(m & np.roll(m, 1, 1))
+
+
+@pytest.mark.parametrize("hits,beta", [(1, 0.44), (3, 0.3)])
+def test_fig1_lattice_follows_the_figure(hits, beta):
+    """The oracle's sweep of the 32 x 32 lattice of Fig. 1 with 8 x 8 tiles equals a
+    site-by-site sweep in the order the figure's phase map gives."""
+    ph = _fig1_map()
+    dims = (32, 32)
+    s1 = oracle.init_hot(dims, 77, 1)
+    s2 = s1.copy()
+    a = oracle.sweeps_dc(dims, s1, (8, 8), hits, beta, 2, 77, stream=1)
+    thr = {dE: oracle.threshold(beta, dE) for dE in (4, 8)}
+    for t in range(2):
+        for P in (0, 1):
+            for h in range(hits):
+                for c in (0, 1):
+                    for y, x in zip(*np.nonzero(ph == 2 * P + c)):
+                        n = int(x) + 32 * int(y)
+                        nb = s2[(x + 1) % 32 + 32 * y] + s2[(x - 1) % 32 + 32 * y] \
+                            + s2[x + 32 * ((y + 1) % 32)] + s2[x + 32 * ((y - 1) % 32)]
+                        dE = 2 * int(s2[n]) * int(nb)
+                        u = oracle.site_word(77, 1, t * hits + h, c, 4, 32 * int(y) + int(x) // 2)
+                        if dE <= 0 or u < thr[dE]:
+                            s2[n] = -s2[n]
+    assert np.array_equal(s1, s2)
+    E, M = oracle.observables(dims, s2)
+    assert a[0] == E and a[1] == M
