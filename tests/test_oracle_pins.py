@@ -18,8 +18,8 @@ import numpy as np
 import pytest
 
 import oracle
-from exact_ising import (binned_mean_err, enumerate_2d, exact_averages, kaufman_energy,
-                         kaufman_log_z, log_z_enumerated, onsager_energy_per_spin)
+from exact_ising import (binned_mean_err, binned_variance_err, enumerate_2d, exact_averages, kaufman_energy,
+                         kaufman_energy_variance, kaufman_log_z, log_z_enumerated, onsager_energy_per_spin)
 from paper_1006_3865_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -344,6 +344,31 @@ def test_long_run_matches_kaufman_L16():
     me, ee = binned_mean_err(tE[2000:])
     ex = kaufman_energy(16, 16, beta)
     assert abs(me - ex) < 4 * ee, (me, ex, ee)
+
+
+@pytest.mark.parametrize("T", [1.5, 2.269185, 3.5])
+def test_kaufman_variance_matches_enumeration(T):
+    """Var(E) from the second beta-derivative of Kaufman's ln Z equals the
+    variance over all 2^16 states of the 4x4 torus."""
+    En, Mn = enumerate_2d(4, 4)
+    e, _, e2 = exact_averages(En, Mn, 1.0 / T)
+    v = kaufman_energy_variance(4, 4, 1.0 / T)
+    assert abs(v - (e2 - e * e)) < 1e-9 * v, (v, e2 - e * e)
+
+
+@pytest.mark.parametrize("T", [2.269185, 2.5])
+def test_long_run_specific_heat_matches_kaufman_L16(T):
+    """The paper finds its 2D runs consistent with the exact internal energy and
+    specific heat of the finite lattice (Sec. 4): c = beta^2 Var(E) / N of a
+    16x16 run matches Kaufman's value (4 jackknife sigma)."""
+    dims, beta = (16, 16), 1.0 / T
+    s = oracle.init_hot(dims, 3)
+    _, _, tE, _ = oracle.sweeps(dims, s, beta, 100000, 3)
+    v, ev = binned_variance_err(tE[5000:])
+    ex = kaufman_energy_variance(16, 16, beta)
+    assert abs(v - ex) < 4 * ev, (v, ex, ev)
+    c, cex = beta ** 2 * v / 256, beta ** 2 * ex / 256
+    assert abs(c - cex) < 0.05 * cex, (c, cex)
 
 
 @pytest.mark.parametrize("T,cold", [(3.0, False), (2.0, True)])
