@@ -706,6 +706,14 @@ def run_forms(a, stream):
     return out
 
 
+def _config(ws: int) -> dict:
+    """The workload of one step, the same object in both arms' lines (the
+    measured per-step figures of this arm go under "step")."""
+    return {"workload": WORKLOAD, "attempts_per_step": ATTEMPTS_PER_STEP,
+            "l2": "inputs larger than L2: the 2D lattice is 256 MiB and the 3D lattice 128 MiB at 1 B per spin",
+            "parallelism": f"replicas{ws}"}
+
+
 def run_reference(a):
     dist, rank, ws, _ = _dist()
     if rank != 0:
@@ -727,8 +735,8 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "i8", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample_per_step": f"hot start + {sample} sweep of each lattice",
-                      "parallelism": f"replicas{ws}"},
+           "config": _config(ws),
+           "sample_per_step": f"hot start + {sample} sweep of each lattice ({step_att} attempts)",
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                             "sample": f"hot start + {sample} sweep of 2D L=16384 and 3D L=512 per step"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -897,14 +905,14 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "attempts_per_step": ATTEMPTS_PER_STEP,
-                   "l2": "inputs larger than L2 (ping-pong buffers 2 x 256 MiB and 2 x 128 MiB)",
-                   "parallelism": f"replicas{ws}", "launches_per_step": launches // a.steps,
-                   "sweep_ms_2d": launch_ms, "sweep_ms_3d": launch3_ms,
-                   "attempts_per_ns_2d": L2D * L2D / (launch_ms * 1e6),
-                   "attempts_per_ns_3d": L3D ** 3 / (launch3_ms * 1e6),
-                   "tiling_2d": tiling2, "tiling_3d": tiling3, "tuning_launches": tuning_launches,
-                   "launches_before_tuning": nt0},
+        "config": _config(ws),
+        "step": {"buffers": "ping-pong lattices 2 x 256 MiB (2D) and 2 x 128 MiB (3D) on the device",
+                 "launches_per_step": launches // a.steps,
+                 "sweep_ms_2d": launch_ms, "sweep_ms_3d": launch3_ms,
+                 "attempts_per_ns_2d": L2D * L2D / (launch_ms * 1e6),
+                 "attempts_per_ns_3d": L3D ** 3 / (launch3_ms * 1e6),
+                 "tiling_2d": tiling2, "tiling_3d": tiling3, "tuning_launches": tuning_launches,
+                 "launches_before_tuning": nt0},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "k_sweep_wave (2D L=16384)", "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes},

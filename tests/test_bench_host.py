@@ -44,3 +44,21 @@ def test_committed_profile_names_a_source_and_tiling():
 def test_attempts_per_step_matches_the_workload():
     b = _bench()
     assert b.ATTEMPTS_PER_STEP == 3 * 200 * 16384 ** 2 + 100 * 512 ** 3
+
+
+def test_reference_line_carries_the_same_config(capsys, monkeypatch):
+    """Both arms print `_config(ws)`: the workload of a step and nothing
+    measured, so the two lines name the same configuration."""
+    import argparse
+    import json
+
+    b = _bench()
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(b, "_cpu_baseline", lambda sample=1: {"value": 1.0})
+    b.run_reference(argparse.Namespace(steps=2, warmup=1))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"] == b._config(1)
+    assert set(b._config(1)) == {"workload", "attempts_per_step", "l2", "parallelism"}
+    assert line["metric"] == b.METRIC and line["unit"] == b.UNIT and line["higher_is_better"] is True
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert src.count('"config": _config(ws)') == 2  # the reference line and this arm's line
