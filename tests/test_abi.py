@@ -59,3 +59,13 @@ def test_bad_model_and_couplings_are_rejected(lib):
 
 def test_version_string(lib):
     assert b"sm_103a" in lib.spn_version()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libspn.so the binding raises; nothing falls back to a CPU path."""
+    monkeypatch.setattr(spn, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        spn.load(str(tmp_path / "libspn.so"))
+    monkeypatch.setattr(spn, "LIB_PATH", str(tmp_path / "libspn.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        spn.load()
