@@ -17,6 +17,10 @@
  *     No C++ exception crosses this boundary.
  *   - dims: int32[2] (2D) or int32[3] (3D), x fastest; every extent even, >= 2.
  *     Site n = x + Lx*(y + Ly*z); colour c(n) = (x+y+z) & 1; m = n >> 1.
+ *     An Ising or EA lattice holds at most 2^29 row words, ceil(Lx / 64) * Ly
+ *     * Lz <= 2^29 (so N <= 2^35), because 8 g + q / 4 below is one 32-bit
+ *     counter word; spn_create(_ex), spn_multi_create and spn_submit refuse a
+ *     larger one with SPN_E_ARG before any device work.
  *   - Spins on the host are int8 +-1 in site order.  Couplings ("bonds") are
  *     bit-packed uint64 words [sample][dir][ceil(N/64)], bit (n % 64) of word
  *     n / 64 set iff J(n, dir) = -1 for the bond from n to n + e_dir.
@@ -89,8 +93,8 @@ const char* spn_version(void);
 /* Create a lattice of `model` with extents `dims`, hot start from Philox
  * (stream 0).  couplings: NULL for the Ising models; for SPN_EA3D_PMJ one
  * sample of bit-packed bonds [3][ceil(N/64)] (copied).  Errors: SPN_E_ARG for
- * odd/too small extents or a missing/unexpected coupling array, SPN_E_NOMEM,
- * SPN_E_CUDA. */
+ * odd/too small extents, a lattice past the counter range (above), or a
+ * missing/unexpected coupling array, SPN_E_NOMEM, SPN_E_CUDA. */
 int spn_create(spn_handle* out, int model, const int32_t* dims, const void* couplings, uint64_t seed);
 
 /* As spn_create with an explicit Philox stream id and start (SPN_INIT_HOT or

@@ -191,6 +191,8 @@ int spn_multi_create(spn_multi* out, const spn_job* jobs, int njobs) {
     const int ext[3] = {j.dims[0], j.dims[1], nd == 3 ? j.dims[2] : 1};
     for (int d = 0; d < nd; ++d)
       if (ext[d] < 2 || (ext[d] & 1)) return bail(SPN_E_ARG, "every extent must be even and >= 2");
+    if (!spn::counter_range_ok(ext[0], ext[1], ext[2]))
+      return bail(SPN_E_ARG, "lattice too large for the random-number counter (more than 2^29 row words)");
     if (!(j.beta >= 0.0)) return bail(SPN_E_ARG, "beta must be >= 0");
     if (j.nsweeps < 0 || j.nsweeps > 0xffffffffLL) return bail(SPN_E_ARG, "bad nsweeps");
     const int64_t N = (int64_t)ext[0] * ext[1] * ext[2];

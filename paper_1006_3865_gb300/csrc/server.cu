@@ -840,6 +840,8 @@ int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket) {
   const int ext[3] = {req->dims[0], req->dims[1], j->nd == 3 ? req->dims[2] : 1};
   for (int d = 0; d < j->nd; ++d)
     if (ext[d] < 2 || (ext[d] & 1)) return sfail(SPN_E_ARG, "every extent must be even and >= 2");
+  if (!spn::counter_range_ok(ext[0], ext[1], ext[2]))
+    return sfail(SPN_E_ARG, "lattice too large for the random-number counter (more than 2^29 row words)");
   if (req->nsweeps < 1 || req->nsweeps > 0xffffffffLL) return sfail(SPN_E_ARG, "nsweeps must be >= 1");
   j->N = (int64_t)ext[0] * ext[1] * ext[2];
   if (model == SPN_EA3D_PMJ) {

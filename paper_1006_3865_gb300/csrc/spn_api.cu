@@ -60,6 +60,8 @@ int check_dims(int model, const int32_t* dims, spn::Lattice& g) {
     if (ext[d] < 2 || (ext[d] & 1)) return fail(SPN_E_ARG, "extent %d along axis %d must be even and >= 2", ext[d], d);
   g.N = (int64_t)g.Lx * g.Ly * g.Lz;
   if (g.N >= ((int64_t)1 << 35)) return fail(SPN_E_ARG, "lattice too large (%lld sites)", (long long)g.N);
+  if (!spn::counter_range_ok(g.Lx, g.Ly, g.Lz))
+    return fail(SPN_E_ARG, "lattice too large for the random-number counter (more than 2^29 row words)");
   return SPN_OK;
 }
 

@@ -50,6 +50,15 @@ struct Lattice {
   int pitch = 0;                   // streaming sweep only: bytes per row in memory (0: Lx, dense)
 };
 
+// A site's random planes come from the Philox counter whose first word is the
+// 32-bit 8 g + call, g = j + ceil(Lx / 64) r the site's 64-site word of row r.
+// Past 2^29 such words the first word would wrap and sites far apart would draw
+// the same numbers, so no lattice holds more (this also keeps N <= 2^35).
+constexpr int64_t kMaxRowWords = (int64_t)1 << 29;
+inline bool counter_range_ok(int Lx, int Ly, int Lz) {
+  return (int64_t)((Lx + 63) / 64) * Ly * Lz <= kMaxRowWords;
+}
+
 // Launchers (all asynchronous on `st`).  acc points at two int64 (dE, dM) that
 // the sweep adds its accepted moves to; err is a device error word.
 cudaError_t launch_init_hot(const Lattice& g, int8_t* s, uint64_t seed, uint32_t stream_id, cudaStream_t st);

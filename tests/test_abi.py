@@ -69,3 +69,20 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(spn, "LIB_PATH", str(tmp_path / "libspn.so"))
     with pytest.raises(RuntimeError, match="not found"):
         spn.load()
+
+
+@pytest.mark.parametrize("model,dims", [(spn.SPN_ISING3D, (2, 32768, 16386)), (spn.SPN_ISING2D, (66, (1 << 28) + 2))])
+def test_lattices_beyond_the_counter_range_are_rejected(lib, model, dims):
+    """A site's Philox counter word is 8 g + call with g its 64-site row word;
+    past 2^29 row words it would wrap, so such lattices are refused (here with
+    fewer than 2^35 sites) by every entry point that takes a lattice, before any
+    device work."""
+    rc, msg = _create(lib, model, dims)
+    assert rc == spn.SPN_E_ARG and "counter" in msg
+    job = spn.Job(model=model, beta=0.4, nsweeps=1, seed=1)
+    for i, e in enumerate(dims):
+        job.dims[i] = e
+    arr = (spn.Job * 1)(job)
+    m = ctypes.c_void_p()
+    assert lib.spn_multi_create(ctypes.byref(m), ctypes.cast(arr, ctypes.c_void_p), 1) == spn.SPN_E_ARG
+    assert "counter" in lib.spn_last_error().decode()

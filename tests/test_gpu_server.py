@@ -165,4 +165,7 @@ def test_poll_unknown_and_early_fetch():
     _wait(srv, [t])
     with pytest.raises(spn.SpnError):
         srv.submit(spn.SPN_ISING2D, (5, 4), 3, 1, beta=0.4)
+    with pytest.raises(spn.SpnError) as e:  # 2^28 + 2 rows of two 64-site words: past the counter range
+        srv.submit(spn.SPN_ISING2D, (66, (1 << 28) + 2), 3, 1, beta=0.4)
+    assert e.value.code == spn.SPN_E_ARG and "counter" in str(e.value)
     srv.close()
