@@ -29,43 +29,78 @@ DIMS = (4, 4)
 N = 16
 
 
-def _couplings(seed):
-    packed = inputs.ea_bonds(DIMS, 1, seed)
-    return packed, inputs.unpack_bonds(packed, N)[0].astype(np.int64)  # J[d][n], d = 0 (x), 1 (y)
+def _couplings(seed, dims=DIMS):
+    packed = inputs.ea_bonds(dims, 1, seed)
+    return packed, inputs.unpack_bonds(packed, int(np.prod(dims)))[0].astype(np.int64)  # J[d][n], d = x, y (, z)
 
 
-def _neighbours():
-    n = np.arange(N)
-    x, y = n % 4, n // 4
-    return np.stack([(x + 1) % 4 + 4 * y, x + 4 * ((y + 1) % 4)])  # forward neighbour along x, y
+def _neighbours(dims=DIMS, step=-1):
+    """Forward (step -1 of the roll) or backward (+1) neighbour of every site along each axis."""
+    idx = np.arange(int(np.prod(dims))).reshape(dims[::-1])  # [z][y][x] or [y][x], x fastest
+    nd = len(dims)
+    return np.stack([np.roll(idx, step, axis=nd - 1 - d).reshape(-1) for d in range(nd)])
 
 
 def _energy(spins, J, nb):
     """E = -sum_n sum_d J[d][n] s_n s_{n + e_d} for spins [..., N] in {+1, -1}."""
     s = spins.astype(np.int64)
-    return -sum((J[d] * s * s[..., nb[d]]).sum(axis=-1) for d in range(2))
+    return -sum((J[d] * s * s[..., nb[d]]).sum(axis=-1) for d in range(len(nb)))
 
 
-def _ladder_run(exchange, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=200, meas=2000, u_per_slot=None):
+def _reachable(dims, J, start):
+    """States the checkerboard sweep (colour 0, then colour 1, a move with
+    dE <= 0 always taken, one with dE > 0 taken with probability in (0, 1))
+    can reach from `start`, as a boolean mask over all 2^N states."""
+    n_sites, nd = int(np.prod(dims)), len(dims)
+    nb, bk = _neighbours(dims), _neighbours(dims, +1)
+    colour = np.stack(np.unravel_index(np.arange(n_sites), dims[::-1])).sum(axis=0) & 1
+    S = 1 - 2 * ((np.arange(1 << n_sites)[:, None] >> np.arange(n_sites)) & 1)
+    dE = 2 * S * sum(J[d] * S[:, nb[d]] + J[d][bk[d]] * S[:, bk[d]] for d in range(nd))
+    bits = np.int64(1) << np.arange(n_sites, dtype=np.int64)
+    forced = [((dE <= 0) & (colour == c)) @ bits for c in (0, 1)]
+    optional = [((dE > 0) & (colour == c)) @ bits for c in (0, 1)]
+
+    def half(front, c):
+        s = np.nonzero(front)[0]
+        sites = np.nonzero(colour == c)[0]
+        out = np.zeros(1 << n_sites, bool)
+        for F in range(1 << len(sites)):
+            m = int(sum(bits[sites[j]] for j in range(len(sites)) if (F >> j) & 1))
+            out[s ^ forced[c][s] ^ (m & optional[c][s])] = True
+        return out
+
+    R = np.zeros(1 << n_sites, bool)
+    R[start] = True
+    front = R.copy()
+    while front.any():
+        nxt = half(half(front, 0), 1)
+        front = nxt & ~R
+        R |= nxt
+    return R
+
+
+def _ladder_run(exchange, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=200, meas=2000, u_per_slot=None,
+                dims=DIMS):
     """Per-chain mean energy at each temperature, the exact averages, the final
     words and couplings."""
-    packed, J = _couplings(seed)
-    nb = _neighbours()
-    states = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
+    packed, J = _couplings(seed, dims)
+    nb = _neighbours(dims)
+    n_sites = int(np.prod(dims))
+    states = 1 - 2 * ((np.arange(1 << n_sites)[:, None] >> np.arange(n_sites)) & 1)
     E_all = _energy(states, J, nb)
     betas = inputs.geometric_ladder(0.5, 3.0)
     w = np.exp(-np.outer(betas, E_all - E_all.min()))
     exact = (w * E_all).sum(axis=1) / w.sum(axis=1)
     bonds = np.repeat(packed, chains, axis=0)  # every chain samples the same couplings
-    words = oracle.ea_init_hot(DIMS, chains, seed)
+    words = oracle.ea_init_hot(dims, chains, seed)
     pi = np.tile(np.arange(32, dtype=np.uint8), (chains, 1))
     tau = pi.copy()
     sums = np.zeros((chains, 32))
     for it in range(burn + meas):
-        oracle.ea_sweeps(DIMS, words, bonds, betas, pi, tau, X, seed, sweep0=X * it,
+        oracle.ea_sweeps(dims, words, bonds, betas, pi, tau, X, seed, sweep0=X * it,
                          exchange_every=X if exchange else 0, u_per_slot=u_per_slot)
         if it >= burn:
-            E, _ = oracle.ea_observables(DIMS, words, bonds)
+            E, _ = oracle.ea_observables(dims, words, bonds)
             sums += np.take_along_axis(E, tau.astype(np.int64), axis=1)  # column t: the replica at temperature t
     return sums / meas, exact, E_all.min(), words, bonds, J, nb
 
@@ -157,3 +192,50 @@ def test_oracle_ladder_with_a_u_per_slot_and_no_exchange_is_boltzmann():
     err = means.std(axis=0, ddof=1) / np.sqrt(means.shape[0])
     z = (means.mean(axis=0) - exact) / np.maximum(err, 1e-3)
     assert np.all(np.abs(z) < 5.0), np.round(z, 2)
+
+
+# ---------------------------------------------------------------- 3D ladder
+
+DIMS3 = (4, 2, 2)  # 16 sites of the simple cubic lattice (the EA batches' model), small enough to enumerate
+SEED3 = inputs.unit_seed(0x5B)  # couplings on which the checkerboard chain is irreducible (checked below)
+
+
+def _z(means, exact):
+    err = means.std(axis=0, ddof=1) / np.sqrt(means.shape[0])
+    return (means.mean(axis=0) - exact) / np.maximum(err, 1e-3)
+
+
+def test_3d_ladder_energies_match_enumeration():
+    """The 3D +-J ladder: the oracle's per-replica energies equal the numpy
+    energy of Eq. 1 over the three bond directions, and without exchange every
+    temperature's mean energy matches the exact Boltzmann average."""
+    _, J = _couplings(SEED3, DIMS3)
+    for s0 in (0, 12345):
+        assert _reachable(DIMS3, J, s0).all()
+    means, exact, emin, words, bonds, J, nb = _ladder_run(exchange=False, seed=SEED3, meas=1000, dims=DIMS3)
+    E, _ = oracle.ea_observables(DIMS3, words, bonds)
+    for i in range(words.shape[0]):
+        spins = 1 - 2 * ((words[i][:, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.int64).T
+        assert np.array_equal(_energy(spins, J, nb), E[i])
+    z = _z(means, exact)
+    assert np.all(np.abs(z) < 5.0), np.round(z, 2)
+
+
+def test_3d_default_ladder_with_exchange_is_boltzmann_at_every_temperature():
+    means, exact, *_ = _ladder_run(exchange=True, seed=SEED3, meas=1000, dims=DIMS3)
+    z = _z(means, exact)
+    assert np.all(np.abs(z) < 5.0), np.round(z, 2)
+
+
+def test_checkerboard_chain_can_be_reducible_with_two_site_axes():
+    """Why the 3D pins check irreducibility first: with an extent of 2 along y
+    and z, each neighbour pair there is joined by two bonds, and on the 0x5A
+    couplings the checkerboard sweep (fixed colour order, dE <= 0 always taken)
+    splits the 2^16 states into closed classes, so a run's averages depend on its
+    start.  Random-site order, or any of twelve other coupling draws, has one
+    class; the 2D 4 x 4 lattice of the pins above has one class too."""
+    _, J3 = _couplings(inputs.unit_seed(0x5A), DIMS3)
+    sizes = {int(_reachable(DIMS3, J3, s0).sum()) for s0 in (0, 1, 2, 3, 40000, 65535)}
+    assert len(sizes) > 1 and max(sizes) < 1 << 16, sizes
+    _, J2 = _couplings(inputs.unit_seed(0x5A))
+    assert _reachable(DIMS, J2, 0).all()
