@@ -20,7 +20,10 @@
  *     An Ising or EA lattice holds at most 2^29 row words, ceil(Lx / 64) * Ly
  *     * Lz <= 2^29 (so N <= 2^35), because 8 g + q / 4 below is one 32-bit
  *     counter word; spn_create(_ex), spn_multi_create and spn_submit refuse a
- *     larger one with SPN_E_ARG before any device work.
+ *     larger one with SPN_E_ARG before any device work.  An extent of 2 is
+ *     allowed, but there each pair of sites is joined by two bonds, and with
+ *     +-J couplings the checkerboard chain can then be reducible (averages that
+ *     depend on the start); extents >= 4 avoid it.
  *   - Spins on the host are int8 +-1 in site order.  Couplings ("bonds") are
  *     bit-packed uint64 words [sample][dir][ceil(N/64)], bit (n % 64) of word
  *     n / 64 set iff J(n, dir) = -1 for the bond from n to n + e_dir.
