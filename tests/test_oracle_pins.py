@@ -423,6 +423,31 @@ def test_3d_energy_matches_the_low_temperature_series():
     assert abs(me + 3) > 100 * ee  # single flips are seen
 
 
+@pytest.mark.parametrize("beta", [0.221654, 0.4])
+def test_3d_long_run_matches_enumeration_4x2x2(beta):
+    """<E> and <|M|> of a 4 x 2 x 2 simple cubic torus (16 sites, every state
+    enumerated in numpy; the extent-2 axes join each pair by two bonds) match a
+    long oracle run within 4 binned sigma.  The checkerboard chain from a hot
+    start cannot leave its class; the states outside it (eight zero-field
+    two-state cycles) carry under 1e-4 of the Boltzmann weight here."""
+    from test_oracle_pins_pt import _energy, _neighbours, _reachable
+
+    dims, N = (4, 2, 2), 16
+    J = inputs.unpack_bonds(inputs.uniform_bonds(dims, 1, +1), N)[0].astype(np.int64)
+    S = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
+    E, M = _energy(S, J, _neighbours(dims)), S.sum(axis=1)
+    w = np.exp(-beta * (E - E.min()))
+    s = oracle.init_hot(dims, 11)
+    start = int(((s < 0).astype(np.int64) << np.arange(N)).sum())  # bit n set iff spin n is -1
+    assert w[~_reachable(dims, J, start)].sum() / w.sum() < 1e-4
+    _, _, tE, tM = oracle.sweeps(dims, s, beta, 100000, 11)
+    me, ee = binned_mean_err(tE[2000:])
+    mm, em = binned_mean_err(np.abs(tM[2000:]))
+    e, am = (w * E).sum() / w.sum(), (w * np.abs(M)).sum() / w.sum()
+    assert abs(me - e) < 4 * ee, (me, e, ee)
+    assert abs(mm - am) < 4 * em, (mm, am, em)
+
+
 def test_acceptance_rate_matches_threshold():
     """Across a run, the flip frequency of colour-0 sites with dE = 8 and dE = 4
     equals thr/2^32 within 5 sigma (the sweep applies the rule of Eq. 2)."""
