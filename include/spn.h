@@ -468,7 +468,10 @@ typedef struct spn_server_ctx* spn_server;
 int spn_server_create(spn_server* out, size_t hbm_budget_bytes);
 
 /* Queue a request (copied) and return its ticket at once; never waits for the
- * GPU.  SPN_E_BUDGET if the job alone exceeds the budget. */
+ * GPU.  SPN_E_BUDGET if the job alone exceeds the budget; SPN_E_ARG for odd
+ * extents or a lattice past the counter range.  An EA sample must fit one
+ * CTA's shared memory, as in spn_create_batch (about 44,000 sites); a larger
+ * one is queued and then fails at admission (state 3, status SPN_E_ARG). */
 int spn_submit(spn_server s, const spn_request* req, uint64_t* ticket);
 
 /* Non-blocking: *done = 1 once the ticket's job is finished or failed; out
