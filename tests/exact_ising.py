@@ -129,3 +129,25 @@ def binned_variance_err(x: np.ndarray, nbins: int = 32):
     loo2 = (b2.sum() - b2) / (nbins - 1)
     jk = loo2 - loo1 ** 2
     return full, float(math.sqrt((nbins - 1) / nbins * ((jk - jk.mean()) ** 2).sum()))
+
+
+def energy_histogram_pvalue(levels: np.ndarray, probs: np.ndarray, samples: np.ndarray, min_expected: float = 10.0):
+    """Pearson chi-square p-value of sampled energies against exact level
+    probabilities (levels ascending); adjacent levels are merged, in energy
+    order, until each merged bin expects at least min_expected samples."""
+    from scipy import stats
+
+    n = len(samples)
+    obs = np.array([(samples == e).sum() for e in levels], dtype=np.float64)
+    assert obs.sum() == n, "a sampled energy is not an exact level"
+    merged_o, merged_e, co, ce = [], [], 0.0, 0.0
+    for o, e in zip(obs, n * probs):
+        co, ce = co + o, ce + e
+        if ce >= min_expected:
+            merged_o.append(co)
+            merged_e.append(ce)
+            co = ce = 0.0
+    merged_o[-1] += co
+    merged_e[-1] += ce
+    o, e = np.array(merged_o), np.array(merged_e)
+    return float(stats.chisquare(o, e * o.sum() / e.sum()).pvalue)

@@ -18,8 +18,9 @@ import numpy as np
 import pytest
 
 import oracle
-from exact_ising import (binned_mean_err, binned_variance_err, enumerate_2d, exact_averages, kaufman_energy,
-                         kaufman_energy_variance, kaufman_log_z, log_z_enumerated, onsager_energy_per_spin)
+from exact_ising import (binned_mean_err, binned_variance_err, energy_histogram_pvalue, enumerate_2d, exact_averages,
+                         kaufman_energy, kaufman_energy_variance, kaufman_log_z, log_z_enumerated,
+                         onsager_energy_per_spin)
 from paper_1006_3865_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -446,6 +447,42 @@ def test_3d_long_run_matches_enumeration_4x2x2(beta):
     e, am = (w * E).sum() / w.sum(), (w * np.abs(M)).sum() / w.sum()
     assert abs(me - e) < 4 * ee, (me, e, ee)
     assert abs(mm - am) < 4 * em, (mm, am, em)
+
+
+@pytest.mark.parametrize("T", [1.5, 2.269185, 3.5])
+def test_energy_histogram_matches_exact_density_of_states_L4(T):
+    """The whole energy distribution of a 4 x 4 run, not only its mean: energies
+    of every 20th sweep (about ten autocorrelation times apart) against
+    P(E) = g(E) e^(-beta E) / Z with g(E) counted over all 2^16 states (Pearson
+    chi-square).  The same samples fail against the distribution at a beta 5%
+    off (p <= 1e-8 at all three temperatures; 3% off is resolved at T = 2.27
+    and 3.5, not in the mostly frozen run at T = 1.5)."""
+    En, _ = enumerate_2d(4, 4)
+    levels, g = np.unique(En, return_counts=True)
+
+    def probs(b):
+        w = g * np.exp(-b * (levels - levels.min()))
+        return w / w.sum()
+
+    s = oracle.init_hot((4, 4), 1)
+    _, _, tE, _ = oracle.sweeps((4, 4), s, 1.0 / T, 200000, 1)
+    samples = tE[1000::20]
+    assert energy_histogram_pvalue(levels, probs(1.0 / T), samples) > 1e-3
+    assert energy_histogram_pvalue(levels, probs(1.05 / T), samples) < 1e-4
+
+
+def test_energy_histogram_matches_exact_density_of_states_3d_4x2x2():
+    """The same on the 4 x 2 x 2 simple cubic torus at the bulk critical coupling."""
+    from test_oracle_pins_pt import _energy, _neighbours
+
+    dims, N, beta = (4, 2, 2), 16, 0.221654
+    J = inputs.unpack_bonds(inputs.uniform_bonds(dims, 1, +1), N)[0].astype(np.int64)
+    S = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
+    levels, g = np.unique(_energy(S, J, _neighbours(dims)), return_counts=True)
+    w = g * np.exp(-beta * (levels - levels.min()))
+    s = oracle.init_hot(dims, 2)
+    _, _, tE, _ = oracle.sweeps(dims, s, beta, 200000, 2)
+    assert energy_histogram_pvalue(levels, w / w.sum(), tE[1000::20]) > 1e-3
 
 
 def test_acceptance_rate_matches_threshold():
