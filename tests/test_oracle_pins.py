@@ -160,6 +160,22 @@ def test_energy_spectrum_matches_kaufman(dims):
     assert all(oracle.observables(dims, s)[1] == int(s.sum()) for s in S[::97])
 
 
+@pytest.mark.parametrize("dims,bonded", [((2, 2, 4), False), ((2, 2, 2), True), ((4, 2, 2), True)])
+def test_3d_energy_of_every_state_matches_numpy(dims, bonded):
+    """E and M of every state of a tiny simple cubic torus (Ising, or +-J bonds
+    as the input generator draws them) against Eq. 1 written out in numpy over
+    the three forward bonds of each site."""
+    from test_oracle_pins_pt import _energy, _neighbours
+
+    N = int(np.prod(dims))
+    packed = inputs.ea_bonds(dims, 1, 77) if bonded else None
+    J = (inputs.unpack_bonds(packed, N)[0] if bonded else np.ones((3, N))).astype(np.int64)
+    S = (1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)).astype(np.int8)
+    E = _energy(S, J, _neighbours(dims))
+    for i in range(len(S)):
+        assert oracle.observables(dims, S[i], bonds=packed) == (int(E[i]), int(S[i].sum()))
+
+
 def test_3d_energy_reduces_to_2d_planes():
     """A z-uniform 3D state has E = Lz * E_2D(plane) - N (all z-bonds satisfied)."""
     rng = np.random.default_rng(11)
