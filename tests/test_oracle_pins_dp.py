@@ -11,6 +11,9 @@ u, so replica exchange within a sample sees independent replicas).
   temperature: 16 samples of a 4 x 4 +-J lattice with 16 different coupling
   sets, eight per group (so they share u), against the exact averages of each
   sample's own couplings from an enumeration of all 2^16 states in numpy.
+* The same on the 3D model the EA batches run: 8 samples of a 4 x 2 x 2 +-J
+  cube, each sample's couplings first checked to give an irreducible
+  checkerboard chain (an extent of 2 can split it into closed classes).
 * The exchange follows the replica-exchange rule: pairs with
   D = (beta_k - beta_k+1)(E_k - E_k+1) >= 0 always swap, the others with total
   frequency sum(exp(D)).
@@ -85,6 +88,38 @@ def test_ladder_with_exchange_is_boltzmann_for_every_sample():
     z = np.zeros((ns, 32))
     for s in range(ns):
         exact = _exact_energies(J[s])
+        for t in range(32):
+            m, e = binned_mean_err(series[:, s, t], nbins=15)
+            z[s, t] = (m - exact[t]) / max(e, 1e-3)
+    assert np.all(np.abs(z) < 5.5), np.round(z, 1)
+    assert np.mean(z ** 2) < 1.6, np.mean(z ** 2)
+
+
+def test_3d_ladder_with_exchange_is_boltzmann_for_every_sample():
+    from test_oracle_pins_pt import _energy, _neighbours, _reachable
+
+    dims, n_sites, ns, X, burn, meas = (4, 2, 2), 16, 8, 10, 100, 1500
+    seed = inputs.unit_seed(0xD3)
+    bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(0xD6))
+    J = inputs.unpack_bonds(bonds, n_sites).astype(np.int64)  # [sample][d][n]
+    for s in range(ns):  # one class: every state reachable from one start (all states are recurrent)
+        assert _reachable(dims, J[s], 0).all(), s
+    betas = inputs.geometric_ladder(0.5, 3.0)
+    words = oracle.ea_init_hot(dims, ns, seed)
+    series = np.zeros((meas, ns, 32))
+    acc = np.zeros((ns, 32), np.int64)
+    for it in range(burn + meas):
+        oracle.ea_dp_sweeps(dims, words, bonds, betas, X, seed, sweep0=X * it, exchange_every=X, acc=acc)
+        if it >= burn:
+            series[it - burn] = oracle.ea_observables(dims, words, bonds)[0]
+    assert acc.sum() > 0
+    S = 1 - 2 * ((np.arange(1 << n_sites)[:, None] >> np.arange(n_sites)) & 1)
+    nb = _neighbours(dims)
+    z = np.zeros((ns, 32))
+    for s in range(ns):
+        E = _energy(S, J[s], nb)
+        w = np.exp(-np.outer(betas, E - E.min()))
+        exact = (w * E).sum(axis=1) / w.sum(axis=1)
         for t in range(32):
             m, e = binned_mean_err(series[:, s, t], nbins=15)
             z[s, t] = (m - exact[t]) / max(e, 1e-3)
