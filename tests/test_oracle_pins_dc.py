@@ -1,8 +1,9 @@
 """Pins of the oracle's double-checkerboard sweep with generalised multi-hit
 (Sec. 3): the special case beta = 0, a plain restatement of the update order on
 tiny lattices, exact stationarity of one tile-parity / colour step, long runs
-against exact enumeration and Kaufman's finite-lattice energy, and the 32 x 32
-decomposition of Fig. 1 from its text fixture under golden/."""
+against exact enumeration (2D, and the 3D 4 x 2 x 2 torus) and Kaufman's
+finite-lattice energy, and the 32 x 32 decomposition of Fig. 1 from its text
+fixture under golden/."""
 
 from __future__ import annotations
 
@@ -132,6 +133,25 @@ def test_long_run_matches_kaufman_L16():
     me, ee = binned_mean_err(tE[2000:])
     ex = kaufman_energy(16, 16, beta)
     assert abs(me - ex) < 4 * ee, (me, ex, ee)
+
+
+@pytest.mark.parametrize("hits,beta", [(1, 0.3), (3, 0.221654)])
+def test_3d_long_run_matches_enumeration_4x2x2(hits, beta):
+    """<E> and <|M|> of the 4 x 2 x 2 simple cubic torus with 2 x 1 x 1 tiles
+    (two tiles along every axis) against all 2^16 states enumerated in numpy."""
+    from test_oracle_pins_pt import _energy, _neighbours
+
+    dims, N = (4, 2, 2), 16
+    S = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
+    E, M = _energy(S, np.ones((3, N), np.int64), _neighbours(dims)), S.sum(axis=1)
+    w = np.exp(-beta * (E - E.min()))
+    s = oracle.init_hot(dims, 5)
+    _, _, tE, tM = oracle.sweeps_dc(dims, s, (2, 1, 1), hits, beta, 60000, 5)
+    me, ee = binned_mean_err(tE[2000:])
+    mm, em = binned_mean_err(np.abs(tM[2000:]))
+    e, am = (w * E).sum() / w.sum(), (w * np.abs(M)).sum() / w.sum()
+    assert abs(me - e) < 4 * ee, (me, e, ee)
+    assert abs(mm - am) < 4 * em, (mm, am, em)
 
 
 def test_rejects_tilings_without_an_even_tile_count():
