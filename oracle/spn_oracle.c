@@ -55,8 +55,9 @@
  * Multi-spin coded EA (Sec. 4, "asynchronous multi-spin coding"), on the
  *   square (nd = 2) or simple cubic (nd = 3) lattice:
  *   one uint32 per (sample, site); bit j is the replica held in temperature slot
- *   j (1 <=> spin -1).  All 32 replicas of a sample share the site's u (purpose
- *   3 words, stream = sample).  Slot j
+ *   j (1 <=> spin -1).  Without u_per_slot all 32 replicas of a sample share the
+ *   site's u (purpose 3 words, stream = sample); with it every slot draws its
+ *   own (orc_msc_slot_planes), which replica exchange needs.  Slot j
  *   runs at beta[temp_of_slot[j]]; betas are indexed by ascending temperature
  *   (non-increasing beta).  Hot start: the replica bits are the hot-start word.
  *   Replica exchange after every X-th sweep (step e = (t+1)/X - 1): for the
@@ -242,6 +243,7 @@ static int local_field(const lat_t* g, const int8_t* s, const uint64_t* bonds, i
   return h;
 }
 
+/* Energy change of flipping s_n under Eq. 1: dE = 2 s_n h_n (Sec. 3). */
 int orc_delta_e(int nd, const int64_t* L, const int8_t* s, const uint64_t* bonds, int64_t n) {
   lat_t g;
   if (lat_make(&g, nd, L)) return 0;
@@ -305,7 +307,8 @@ static void half_sweep(const lat_t* g, int8_t* s, const uint64_t* bonds, const u
   *dMsum += dm;
 }
 
-/* nsweeps sweeps starting at global sweep index sweep0.  E and M are the running
+/* The sub-lattice procedure of Sec. 3 with the acceptance of Eq. 2:
+ * nsweeps sweeps starting at global sweep index sweep0.  E and M are the running
  * sums (in/out); traceE/traceM, if given, receive E and M after each sweep.
  * umode 0 draws u from the Ising bit planes (purpose 0), umode 1 from the
  * multi-spin coded words (purpose 3) -- the latter lets a scalar run reproduce
@@ -406,8 +409,8 @@ int orc_ea_init_hot(int nd, const int64_t* L, int nsamples, uint64_t seed, uint3
   return 0;
 }
 
-/* Energy and magnetisation of every replica of every sample, indexed by slot:
- * E[i*32 + j], M[i*32 + j]. */
+/* Eq. 1 with the +-J bonds of the Sec. 4 spin glass, for every replica of
+ * every sample, indexed by slot: E[i*32 + j], M[i*32 + j]. */
 int orc_ea_observables(int nd, const int64_t* L, int nsamples, const uint32_t* sp, const uint64_t* bonds,
                        int64_t* E, int64_t* M) {
   lat_t g;
@@ -460,7 +463,8 @@ static void exchange_step(const double* betas, const int64_t* Eslot, uint8_t* sl
   }
 }
 
-/* nsweeps multi-spin coded sweeps of nsamples samples (sample i uses stream
+/* Sec. 4's multi-spin coded sweep (Eq. 2 per replica bit) with replica exchange:
+ * nsweeps multi-spin coded sweeps of nsamples samples (sample i uses stream
  * stream0 + i), from global sweep index sweep0, with replica exchange after every
  * exchange_every-th sweep (0 = never).  temp_of_slot / slot_of_temp: [sample][32],
  * in/out.  acc: [sample][32] exchange acceptance counters (may be NULL). */
@@ -730,7 +734,8 @@ int orc_heis_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, 
   return 0;
 }
 
-/* E = -sum_n sum_d S_n . S_{n+e_d} and M = sum_n S_n, in binary64 in site order
+/* Eq. 1 for the continuous spins of Sec. 4's outlook (classical Heisenberg):
+ * E = -sum_n sum_d S_n . S_{n+e_d} and M = sum_n S_n, in binary64 in site order
  * (products of two binary32 values are exact in binary64). */
 int orc_heis_observables(int nd, const int64_t* L, const float* S, double* E, double* M) {
   lat_t g;
@@ -752,7 +757,8 @@ int orc_heis_observables(int nd, const int64_t* L, const float* S, double* E, do
   return 0;
 }
 
-/* nsweeps sweeps from global sweep index sweep0.  E and M (in/out) are advanced
+/* The sub-lattice procedure of Sec. 3 and Eq. 2 for Heisenberg spins:
+ * nsweeps sweeps from global sweep index sweep0.  E and M (in/out) are advanced
  * by the accepted moves, in site order; traceE[s], traceM[3 s ..] after sweep s. */
 int orc_heis_sweeps(int nd, const int64_t* L, float* S, double beta, uint64_t seed, uint32_t stream, uint32_t sweep0,
                     int64_t nsweeps, double* E, double* M, double* traceE, double* traceM) {
