@@ -102,7 +102,9 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Site word of site key m for purpose p: bit 31 - q is bit (m & 31) of plane q
+/* The random-number reading of the header: the paper's per-thread LCG (Sec. 4)
+ * is replaced by Philox4x32-10 (Salmon et al.) keyed by site, sweep and stream.
+ * Site word of site key m for purpose p: bit 31 - q is bit (m & 31) of plane q
  * = word q & 3 of R(8 (m >> 5) + (q >> 2), t, c | (p << 1), stream). */
 uint32_t orc_site_word(uint64_t seed, uint32_t stream, uint32_t t, int colour, int purpose, uint64_t m) {
   const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
@@ -120,15 +122,18 @@ uint32_t orc_site_word(uint64_t seed, uint32_t stream, uint32_t t, int colour, i
   return u;
 }
 
+/* The u compared with the threshold of Eq. 2 (purpose 0). */
 uint32_t orc_metropolis_u(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, uint64_t m) {
   return orc_site_word(seed, stream, sweep, colour, 0, m);
 }
 
+/* The word of the seeded hot start (purpose 1; the paper does not state its start). */
 uint32_t orc_hot_word(uint64_t seed, uint32_t stream, int colour, uint64_t m) {
   return orc_site_word(seed, stream, 0, colour, 1, m);
 }
 
-/* Multi-spin coded Metropolis u: word m & 3 of R(m >> 2, sweep, c | 3 << 1, stream). */
+/* Multi-spin coded Metropolis u (Sec. 4: one random number for all bits of a
+ * word): word m & 3 of R(m >> 2, sweep, c | 3 << 1, stream). */
 uint32_t orc_msc_u(uint64_t seed, uint32_t stream, uint32_t sweep, int colour, uint64_t m) {
   const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
   uint32_t ctr[4] = {(uint32_t)(m >> 2), sweep, (uint32_t)colour | (3u << 1), stream};
@@ -267,6 +272,7 @@ int orc_observables(int nd, const int64_t* L, const int8_t* s, const uint64_t* b
   return 0;
 }
 
+/* Seeded hot start of every site from its hot-start word (the header's reading). */
 int orc_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, int8_t* s) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
@@ -333,6 +339,7 @@ int orc_sweeps_ex(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, do
   return 0;
 }
 
+/* orc_sweeps_ex (Sec. 3, Eq. 2) drawing u from the Ising bit planes. */
 int orc_sweeps(int nd, const int64_t* L, int8_t* s, const uint64_t* bonds, double beta, uint64_t seed,
                uint32_t stream, uint32_t sweep0, int64_t nsweeps, int64_t* E, int64_t* M,
                int64_t* traceE, int64_t* traceM) {
@@ -400,6 +407,8 @@ int orc_sweeps_dc(int nd, const int64_t* L, int8_t* s, const int64_t* T, int hit
 /* Replica bit j of a site word, as a spin +-1. */
 static int rep_spin(uint32_t w, int j) { return ((w >> j) & 1) ? -1 : 1; }
 
+/* Seeded hot start of the multi-spin coded samples: every replica bit of a site
+ * word is the hot-start word (sample i uses stream stream0 + i). */
 int orc_ea_init_hot(int nd, const int64_t* L, int nsamples, uint64_t seed, uint32_t stream0, uint32_t* sp) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
@@ -522,6 +531,7 @@ int orc_ea_sweeps_ex(int nd, const int64_t* L, int nsamples, uint32_t* sp, const
   return 0;
 }
 
+/* orc_ea_sweeps_ex (Sec. 4) with the shared u of every slot. */
 int orc_ea_sweeps(int nd, const int64_t* L, int nsamples, uint32_t* sp, const uint64_t* bonds, const double* betas,
                   uint8_t* temp_of_slot, uint8_t* slot_of_temp, uint64_t seed, uint32_t stream0,
                   uint32_t sweep0, int64_t nsweeps, int exchange_every, int64_t* acc) {
@@ -721,6 +731,9 @@ int orc_heis_proposal(uint64_t seed, uint32_t stream, uint32_t t, int colour, in
   return 0;
 }
 
+/* Seeded hot start of Heisenberg spins: each site a uniform point on the sphere
+ * from orc_heis_proposal with purpose 7 at t = 0, or (0, 0, 1) if its 16 tries
+ * all miss. */
 int orc_heis_init_hot(int nd, const int64_t* L, uint64_t seed, uint32_t stream, float* S) {
   lat_t g;
   if (lat_make(&g, nd, L)) return -1;
