@@ -419,7 +419,9 @@ int spn_batch_overlap(spn_handle h, int64_t* nmeas, int64_t* q_last, uint64_t* q
 int spn_batch_overlap_reset(spn_handle h);
 
 /* ------------------------------------------------------------------------
- * Served requests with continuous batching
+ * Served requests with continuous batching (the paper serves nothing: each job
+ * is the Sec. 3 procedure, or the Sec. 4 multi-spin coded ladder, run to
+ * completion bit for bit as it would run alone)
  * ---------------------------------------------------------------------- */
 
 /* A simulation request.  Ising (SPN_ISING2D / SPN_ISING3D): beta, nsweeps from
