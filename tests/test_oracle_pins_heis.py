@@ -26,7 +26,7 @@ import scipy.special as sp
 import scipy.stats as st
 
 import oracle
-from exact_ising import binned_mean_err
+from exact_ising import binned_mean_err, binned_variance_err
 
 
 def test_exp_within_four_ulp():
@@ -84,8 +84,44 @@ def test_two_by_two_torus_matches_exact_ring(beta):
 def test_ring_formula_limits():
     # beta -> 0: <E> -> 0; small K: each of 4 doubled bonds has <S.S'> = K/3
     assert abs(_ring_energy(1e-4) - (-4 * 2 * (2e-4) / 3)) < 1e-9
-    # large beta: the ring orders, E -> -8 + (degrees of freedom) / beta
-    assert _ring_energy(50.0) == pytest.approx(-8 + 4 / 50.0, abs=0.02)
+    # large beta: the ring orders; 4 spins x 2 angles less the 2 of the common
+    # direction leave 6 quadratic modes of 1 / (2 beta) each: E -> -8 + 3 / beta
+    assert _ring_energy(50.0) == pytest.approx(-8 + 3 / 50.0, abs=1e-3)
+    assert _ring_energy(20.0) == pytest.approx(-8 + 3 / 20.0, abs=1e-3)
+
+
+def _ring_energy_variance(beta, N=4, J=2.0, lmax=60):
+    """Var(E) = d^2 ln Z / d beta^2 of the same ring; i_l'' from the modified
+    spherical Bessel equation x^2 i'' + 2 x i' - l (l + 1) i = x^2 i."""
+    K = J * beta
+    l = np.arange(lmax)
+    i = sp.spherical_in(l, K)
+    d1 = sp.spherical_in(l, K, derivative=True)
+    d2 = i * (1 + l * (l + 1) / K ** 2) - 2 * d1 / K
+    w = 2 * l + 1
+    Z = (w * i ** N).sum()
+    Z1 = (w * N * i ** (N - 1) * d1).sum() * J
+    Z2 = (w * (N * (N - 1) * i ** (N - 2) * d1 ** 2 + N * i ** (N - 1) * d2)).sum() * J ** 2
+    return Z2 / Z - (Z1 / Z) ** 2
+
+
+def test_ring_variance_limits():
+    # beta -> 0: four uncorrelated doubled bonds, -2 S.S' with S.S' uniform on [-1, 1]
+    assert _ring_energy_variance(1e-3) == pytest.approx(16 / 3, rel=1e-5)
+    # large beta: six quadratic modes, Var(E) = -d<E>/d beta -> 3 / beta^2
+    assert _ring_energy_variance(50.0) == pytest.approx(3 / 50.0 ** 2, rel=0.02)
+
+
+@pytest.mark.parametrize("beta", [0.3, 1.0, 2.5])
+def test_two_by_two_torus_specific_heat_matches_exact_ring(beta):
+    """The energy fluctuations of the same runs (c = beta^2 Var(E) / N)
+    against the exact ring, within 4 jackknife sigma."""
+    dims, seed = (2, 2), 1000 + int(10 * beta)
+    S = oracle.heis_init_hot(dims, seed)
+    _, _, tE, _ = oracle.heis_sweeps(dims, S, beta, 200000, seed)
+    v, ev = binned_variance_err(tE[2000:], nbins=50)
+    exact = _ring_energy_variance(beta)
+    assert abs(v - exact) < 4 * ev, (beta, v, exact, ev)
 
 
 def test_3d_high_temperature_bond_correlation():
