@@ -264,6 +264,36 @@ def test_half_sweep_kernel_is_exactly_stationary():
         assert np.max(np.abs(new - pi) / pi) < 16 * 2.0**-32 / p_min
 
 
+def test_half_sweep_kernel_is_exactly_stationary_3d_pmj():
+    """The same on a 4 x 2 x 2 +-J cube with the couplings on which the
+    checkerboard chain splits into closed classes: every half-sweep still keeps
+    the Boltzmann distribution, so the split is a failure of irreducibility,
+    not of the update."""
+    dims, N, beta = (4, 2, 2), 16, 0.37
+    packed = inputs.ea_bonds(dims, 1, inputs.unit_seed(0x5A))
+    S = _all_states(N)
+    E = np.array([oracle.observables(dims, s, bonds=packed)[0] for s in S], dtype=np.float64)
+    pi = np.exp(-beta * (E - E.min()))
+    pi /= pi.sum()
+    colour = np.array([(n % 4 + (n // 4) % 2 + n // 8) & 1 for n in range(N)])
+    thr = {dE: oracle.threshold(beta, dE) for dE in (4, 8, 12)}
+    for c in (0, 1):
+        sites = np.nonzero(colour == c)[0]
+        P = np.zeros((len(S), len(sites)))
+        for i, s in enumerate(S):
+            for j, n in enumerate(sites):
+                dE = oracle.delta_e(dims, s, int(n), bonds=packed)
+                P[i, j] = 1.0 if dE <= 0 else thr[dE] / 2.0**32
+        new = np.zeros(len(S))
+        idx = np.arange(len(S), dtype=np.int64)
+        for F in range(1 << len(sites)):
+            flip = np.array([(F >> j) & 1 for j in range(len(sites))], dtype=bool)
+            prob = np.prod(np.where(flip, P, 1.0 - P), axis=1)
+            mask = int(sum(1 << int(sites[j]) for j in range(len(sites)) if flip[j]))
+            np.add.at(new, idx ^ mask, pi * prob)
+        assert np.max(np.abs(new - pi) / pi) < 16 * 2.0**-32 / (thr[12] / 2.0**32)
+
+
 def test_beta_zero_flips_every_spin():
     """beta = 0: every proposal is accepted, so each sweep maps s -> -s."""
     for dims in ((8, 6), (4, 4, 6)):
