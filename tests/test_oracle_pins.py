@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_lattice import energy, neighbours, reachable
 from exact_ising import (binned_mean_err, binned_variance_err, energy_histogram_pvalue, enumerate_2d, exact_averages,
                          kaufman_energy, kaufman_energy_variance, kaufman_log_z, log_z_enumerated,
                          onsager_energy_per_spin)
@@ -165,13 +166,12 @@ def test_3d_energy_of_every_state_matches_numpy(dims, bonded):
     """E and M of every state of a tiny simple cubic torus (Ising, or +-J bonds
     as the input generator draws them) against Eq. 1 written out in numpy over
     the three forward bonds of each site."""
-    from test_oracle_pins_pt import _energy, _neighbours
 
     N = int(np.prod(dims))
     packed = inputs.ea_bonds(dims, 1, 77) if bonded else None
     J = (inputs.unpack_bonds(packed, N)[0] if bonded else np.ones((3, N))).astype(np.int64)
     S = (1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)).astype(np.int8)
-    E = _energy(S, J, _neighbours(dims))
+    E = energy(S, J, neighbours(dims))
     for i in range(len(S)):
         assert oracle.observables(dims, S[i], bonds=packed) == (int(E[i]), int(S[i].sum()))
 
@@ -477,16 +477,15 @@ def test_3d_long_run_matches_enumeration_4x2x2(beta):
     long oracle run within 4 binned sigma.  The checkerboard chain from a hot
     start cannot leave its class; the states outside it (eight zero-field
     two-state cycles) carry under 1e-4 of the Boltzmann weight here."""
-    from test_oracle_pins_pt import _energy, _neighbours, _reachable
 
     dims, N = (4, 2, 2), 16
     J = inputs.unpack_bonds(inputs.uniform_bonds(dims, 1, +1), N)[0].astype(np.int64)
     S = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
-    E, M = _energy(S, J, _neighbours(dims)), S.sum(axis=1)
+    E, M = energy(S, J, neighbours(dims)), S.sum(axis=1)
     w = np.exp(-beta * (E - E.min()))
     s = oracle.init_hot(dims, 11)
     start = int(((s < 0).astype(np.int64) << np.arange(N)).sum())  # bit n set iff spin n is -1
-    assert w[~_reachable(dims, J, start)].sum() / w.sum() < 1e-4
+    assert w[~reachable(dims, J, start)].sum() / w.sum() < 1e-4
     _, _, tE, tM = oracle.sweeps(dims, s, beta, 100000, 11)
     me, ee = binned_mean_err(tE[2000:])
     mm, em = binned_mean_err(np.abs(tM[2000:]))
@@ -519,12 +518,11 @@ def test_energy_histogram_matches_exact_density_of_states_L4(T):
 
 def test_energy_histogram_matches_exact_density_of_states_3d_4x2x2():
     """The same on the 4 x 2 x 2 simple cubic torus at the bulk critical coupling."""
-    from test_oracle_pins_pt import _energy, _neighbours
 
     dims, N, beta = (4, 2, 2), 16, 0.221654
     J = inputs.unpack_bonds(inputs.uniform_bonds(dims, 1, +1), N)[0].astype(np.int64)
     S = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
-    levels, g = np.unique(_energy(S, J, _neighbours(dims)), return_counts=True)
+    levels, g = np.unique(energy(S, J, neighbours(dims)), return_counts=True)
     w = g * np.exp(-beta * (levels - levels.min()))
     s = oracle.init_hot(dims, 2)
     _, _, tE, _ = oracle.sweeps(dims, s, beta, 200000, 2)

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_lattice import energy, neighbours
 from exact_ising import binned_mean_err, enumerate_2d, exact_averages, kaufman_energy
 
 
@@ -139,11 +140,10 @@ def test_long_run_matches_kaufman_L16():
 def test_3d_long_run_matches_enumeration_4x2x2(hits, beta):
     """<E> and <|M|> of the 4 x 2 x 2 simple cubic torus with 2 x 1 x 1 tiles
     (two tiles along every axis) against all 2^16 states enumerated in numpy."""
-    from test_oracle_pins_pt import _energy, _neighbours
 
     dims, N = (4, 2, 2), 16
     S = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
-    E, M = _energy(S, np.ones((3, N), np.int64), _neighbours(dims)), S.sum(axis=1)
+    E, M = energy(S, np.ones((3, N), np.int64), neighbours(dims)), S.sum(axis=1)
     w = np.exp(-beta * (E - E.min()))
     s = oracle.init_hot(dims, 5)
     _, _, tE, tM = oracle.sweeps_dc(dims, s, (2, 1, 1), hits, beta, 60000, 5)

@@ -24,6 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from exact_lattice import energy, neighbours, reachable
 from exact_ising import binned_mean_err
 from paper_1006_3865_gb300 import inputs
 
@@ -96,14 +97,13 @@ def test_ladder_with_exchange_is_boltzmann_for_every_sample():
 
 
 def test_3d_ladder_with_exchange_is_boltzmann_for_every_sample():
-    from test_oracle_pins_pt import _energy, _neighbours, _reachable
 
     dims, n_sites, ns, X, burn, meas = (4, 2, 2), 16, 8, 10, 100, 1500
     seed = inputs.unit_seed(0xD3)
     bonds = inputs.ea_bonds(dims, ns, inputs.unit_seed(0xD6))
     J = inputs.unpack_bonds(bonds, n_sites).astype(np.int64)  # [sample][d][n]
     for s in range(ns):  # one class: every state reachable from one start (all states are recurrent)
-        assert _reachable(dims, J[s], 0).all(), s
+        assert reachable(dims, J[s], 0).all(), s
     betas = inputs.geometric_ladder(0.5, 3.0)
     words = oracle.ea_init_hot(dims, ns, seed)
     series = np.zeros((meas, ns, 32))
@@ -114,10 +114,10 @@ def test_3d_ladder_with_exchange_is_boltzmann_for_every_sample():
             series[it - burn] = oracle.ea_observables(dims, words, bonds)[0]
     assert acc.sum() > 0
     S = 1 - 2 * ((np.arange(1 << n_sites)[:, None] >> np.arange(n_sites)) & 1)
-    nb = _neighbours(dims)
+    nb = neighbours(dims)
     z = np.zeros((ns, 32))
     for s in range(ns):
-        E = _energy(S, J[s], nb)
+        E = energy(S, J[s], nb)
         w = np.exp(-np.outer(betas, E - E.min()))
         exact = (w * E).sum(axis=1) / w.sum(axis=1)
         for t in range(32):

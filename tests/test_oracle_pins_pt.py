@@ -23,6 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
+from exact_lattice import energy, neighbours, reachable
 from paper_1006_3865_gb300 import inputs
 
 DIMS = (4, 4)
@@ -34,60 +35,15 @@ def _couplings(seed, dims=DIMS):
     return packed, inputs.unpack_bonds(packed, int(np.prod(dims)))[0].astype(np.int64)  # J[d][n], d = x, y (, z)
 
 
-def _neighbours(dims=DIMS, step=-1):
-    """Forward (step -1 of the roll) or backward (+1) neighbour of every site along each axis."""
-    idx = np.arange(int(np.prod(dims))).reshape(dims[::-1])  # [z][y][x] or [y][x], x fastest
-    nd = len(dims)
-    return np.stack([np.roll(idx, step, axis=nd - 1 - d).reshape(-1) for d in range(nd)])
-
-
-def _energy(spins, J, nb):
-    """E = -sum_n sum_d J[d][n] s_n s_{n + e_d} for spins [..., N] in {+1, -1}."""
-    s = spins.astype(np.int64)
-    return -sum((J[d] * s * s[..., nb[d]]).sum(axis=-1) for d in range(len(nb)))
-
-
-def _reachable(dims, J, start):
-    """States the checkerboard sweep (colour 0, then colour 1, a move with
-    dE <= 0 always taken, one with dE > 0 taken with probability in (0, 1))
-    can reach from `start`, as a boolean mask over all 2^N states."""
-    n_sites, nd = int(np.prod(dims)), len(dims)
-    nb, bk = _neighbours(dims), _neighbours(dims, +1)
-    colour = np.stack(np.unravel_index(np.arange(n_sites), dims[::-1])).sum(axis=0) & 1
-    S = 1 - 2 * ((np.arange(1 << n_sites)[:, None] >> np.arange(n_sites)) & 1)
-    dE = 2 * S * sum(J[d] * S[:, nb[d]] + J[d][bk[d]] * S[:, bk[d]] for d in range(nd))
-    bits = np.int64(1) << np.arange(n_sites, dtype=np.int64)
-    forced = [((dE <= 0) & (colour == c)) @ bits for c in (0, 1)]
-    optional = [((dE > 0) & (colour == c)) @ bits for c in (0, 1)]
-
-    def half(front, c):
-        s = np.nonzero(front)[0]
-        sites = np.nonzero(colour == c)[0]
-        out = np.zeros(1 << n_sites, bool)
-        for F in range(1 << len(sites)):
-            m = int(sum(bits[sites[j]] for j in range(len(sites)) if (F >> j) & 1))
-            out[s ^ forced[c][s] ^ (m & optional[c][s])] = True
-        return out
-
-    R = np.zeros(1 << n_sites, bool)
-    R[start] = True
-    front = R.copy()
-    while front.any():
-        nxt = half(half(front, 0), 1)
-        front = nxt & ~R
-        R |= nxt
-    return R
-
-
 def _ladder_run(exchange, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=200, meas=2000, u_per_slot=None,
                 dims=DIMS):
     """Per-chain mean energy at each temperature, the exact averages, the final
     words and couplings."""
     packed, J = _couplings(seed, dims)
-    nb = _neighbours(dims)
+    nb = neighbours(dims)
     n_sites = int(np.prod(dims))
     states = 1 - 2 * ((np.arange(1 << n_sites)[:, None] >> np.arange(n_sites)) & 1)
-    E_all = _energy(states, J, nb)
+    E_all = energy(states, J, nb)
     betas = inputs.geometric_ladder(0.5, 3.0)
     w = np.exp(-np.outer(betas, E_all - E_all.min()))
     exact = (w * E_all).sum(axis=1) / w.sum(axis=1)
@@ -115,7 +71,7 @@ def test_ladder_without_exchange_is_boltzmann_at_every_temperature():
     E, _ = oracle.ea_observables(DIMS, words, bonds)
     for i in range(words.shape[0]):
         spins = 1 - 2 * ((words[i][:, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.int64).T  # [slot][site]
-        assert np.array_equal(_energy(spins, J, nb), E[i])
+        assert np.array_equal(energy(spins, J, nb), E[i])
 
 
 def test_default_ladder_with_exchange_is_boltzmann_at_every_temperature():
@@ -137,9 +93,9 @@ def numpy_ladder(shared_u, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=10
     otherwise one per slot and site.  Returns the z-scores of each temperature's
     mean energy against the exact average."""
     packed, J = _couplings(seed)
-    nb = _neighbours()
+    nb = neighbours(DIMS)
     states = 1 - 2 * ((np.arange(1 << N)[:, None] >> np.arange(N)) & 1)
-    E_all = _energy(states, J, nb)
+    E_all = energy(states, J, nb)
     betas = inputs.geometric_ladder(0.5, 3.0)
     w = np.exp(-np.outer(betas, E_all - E_all.min()))
     exact = (w * E_all).sum(axis=1) / w.sum(axis=1)
@@ -160,7 +116,7 @@ def numpy_ladder(shared_u, seed=inputs.unit_seed(0x5A), chains=16, X=10, burn=10
                 b = betas[temp_of_slot][:, :, None]
                 flip = ((dE <= 0) | (u < np.exp(-b * np.maximum(dE, 0)))) & (colour == c)
                 S = np.where(flip, -S, S)
-        E = _energy(S, J, nb)  # by slot
+        E = energy(S, J, nb)  # by slot
         slot_of_temp = np.argsort(temp_of_slot, axis=1)
         Et = np.take_along_axis(E, slot_of_temp, axis=1)
         for k in range(blk & 1, 31, 2):  # the pairs of this exchange step
@@ -211,12 +167,12 @@ def test_3d_ladder_energies_match_enumeration():
     temperature's mean energy matches the exact Boltzmann average."""
     _, J = _couplings(SEED3, DIMS3)
     for s0 in (0, 12345):
-        assert _reachable(DIMS3, J, s0).all()
+        assert reachable(DIMS3, J, s0).all()
     means, exact, emin, words, bonds, J, nb = _ladder_run(exchange=False, seed=SEED3, meas=1000, dims=DIMS3)
     E, _ = oracle.ea_observables(DIMS3, words, bonds)
     for i in range(words.shape[0]):
         spins = 1 - 2 * ((words[i][:, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.int64).T
-        assert np.array_equal(_energy(spins, J, nb), E[i])
+        assert np.array_equal(energy(spins, J, nb), E[i])
     z = _z(means, exact)
     assert np.all(np.abs(z) < 5.0), np.round(z, 2)
 
@@ -235,7 +191,7 @@ def test_checkerboard_chain_can_be_reducible_with_two_site_axes():
     start.  Random-site order, or any of twelve other coupling draws, has one
     class; the 2D 4 x 4 lattice of the pins above has one class too."""
     _, J3 = _couplings(inputs.unit_seed(0x5A), DIMS3)
-    sizes = {int(_reachable(DIMS3, J3, s0).sum()) for s0 in (0, 1, 2, 3, 40000, 65535)}
+    sizes = {int(reachable(DIMS3, J3, s0).sum()) for s0 in (0, 1, 2, 3, 40000, 65535)}
     assert len(sizes) > 1 and max(sizes) < 1 << 16, sizes
     _, J2 = _couplings(inputs.unit_seed(0x5A))
-    assert _reachable(DIMS, J2, 0).all()
+    assert reachable(DIMS, J2, 0).all()
